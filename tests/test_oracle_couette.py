@@ -1,0 +1,85 @@
+"""Pins of the oracle's chi-formulation Couette stage (Secs. III, VI)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import analytic as an
+from oracle.couette import TAU_AOKI, TAU_KN_OVER_N, TAU_KN_OVER_NT, CouetteGrid, CouetteOracle, Wall
+from paper_1708_05944_gb300.inputs import perturbation
+
+
+@pytest.mark.parametrize("spec", ["HH(3;4)xH(3;4)", "HH(4;8)xH(4;20)", "H(4;5)xH(4;5)", "HH(2;3)xH(2;3)"])
+@pytest.mark.parametrize("A", [0.0, 0.95])
+def test_rest_state_is_exact(spec, A):
+    # cylinders at rest, f = f_eq(1, 0, T_w): L[f] = 0 (Sec. VI.C.2)
+    o = CouetteOracle(spec, CouetteGrid(16, A=A), Wall(0.0), Wall(0.0), 0.05, TAU_KN_OVER_N)
+    F = o.initial_equilibrium()
+    assert np.abs(o.L(F)).max() < 1e-13
+    assert o.last_nw[0] == pytest.approx(1.0, abs=1e-14) and o.last_nw[1] == pytest.approx(1.0, abs=1e-14)
+
+
+@pytest.mark.parametrize("A", [0.0, 0.95])
+def test_mass_is_conserved_with_diffuse_walls(A):
+    # only wall fluxes change N_tot, and n_w cancels them (Sec. III.D, Eq. nw)
+    o = CouetteOracle("HH(3;4)xH(3;4)", CouetteGrid(24, A=A), Wall(0.2), Wall(-0.1), 0.1, TAU_AOKI)
+    F = o.initial_equilibrium() * perturbation((2, 24, 8, 4), seed=3, amplitude=0.02)
+    N0 = o.n_tot(F)
+    for _ in range(60):
+        F = o.step(F, 2e-3)
+    assert abs(o.n_tot(F) / N0 - 1.0) < 1e-13
+
+
+def test_wall_flux_vanishes():
+    # with n_w from Eq. (nw) the wall mass flux is zero: check through dN/dt of one L
+    o = CouetteOracle("HH(4;8)xH(4;20)", CouetteGrid(12), Wall(0.3), Wall(0.0), 0.3, TAU_KN_OVER_NT)
+    F = o.initial_equilibrium() * perturbation((2, 12, 16, 20), seed=5)
+    L = o.L(F)
+    assert abs((o.g.dchi * L[0].sum(axis=(1, 2))).sum()) < 1e-13
+
+
+@pytest.mark.slow
+def test_rigid_rotation_is_held():
+    # f = f_eq(n(R), Omega R, T_w) with Eq. (rigid_density) solves the kinetic equation for all tau
+    # (Sec. VI.C.3); the scheme keeps it up to velocity truncation and O(dR^2)
+    Om, N = 0.3, 32
+    g = CouetteGrid(N)
+    o = CouetteOracle("H(4;5)xH(4;5)", g, Wall(Om * 1.0), Wall(Om * 2.0), 0.1, TAU_KN_OVER_N)
+    n = an.rigid_density(g.Rc, Om, 1.0, 1.0, 2.0)
+    f1, f2 = o.m.feq(n, np.zeros(N), Om * g.Rc, np.ones(N))
+    F = np.stack([f1, f2])
+    dt = 0.4 / N / 4
+    for _ in range(int(2.0 / dt)):
+        F = o.step(F, dt)
+    nn, u0, u1, T = o.m.moments(F)
+    assert np.abs(nn / n - 1).max() < 2e-3
+    assert np.abs(u1 / (Om * g.Rc) - 1).max() < 3e-3
+    assert np.abs(T - 1).max() < 2e-3
+
+
+def test_navier_stokes_closed_forms_are_consistent():
+    # the printed NS profiles satisfy their defining relations (Sec. VI.D.1)
+    ri, ro, Om, mu, Tw = 1.0, 2.0, 0.5, 1e-3, 1.0
+    kappa = 2.5 * mu  # Eq. (CE_tcoeff), m = 1
+    R = np.linspace(ri, ro, 2001)
+    u = an.ns_u_phi(R, Om, ri, ro)
+    assert u[0] == pytest.approx(Om * ri, abs=1e-14) and u[-1] == pytest.approx(0.0, abs=1e-14)
+    # T^{R phi} = -mu R d/dR (u/R) (Eq. NS_TRph_aux)
+    Trp = -mu * R * np.gradient(u / R, R, edge_order=2)
+    np.testing.assert_allclose(Trp, an.ns_T_Rphi(R, mu, Om, ri, ro), rtol=1e-5)
+    T = an.ns_T(R, mu / kappa, Om, Tw, ri, ro)
+    assert T[0] == pytest.approx(Tw, abs=1e-14) and T[-1] == pytest.approx(Tw, abs=1e-14)
+    qR = an.ns_qR(R, mu, Om, ri, ro)
+    np.testing.assert_allclose(qR, -kappa * np.gradient(T, R, edge_order=2), rtol=0, atol=1e-5 * np.abs(qR).max())
+    # q^R + u^phi T^{R phi} = Q / R (Eq. Q_def)
+    np.testing.assert_allclose(R * (qR + u * an.ns_T_Rphi(R, mu, Om, ri, ro)), an.ns_Q(mu, Om, ri, ro), rtol=1e-12)
+    # temperature maximum (Eq. NS_Rmax)
+    assert R[np.argmax(T)] == pytest.approx(an.ns_R_Tmax(ri, ro), abs=1e-3)
+
+
+def test_rigid_density_normalisation():
+    ri, ro, Om = 1.0, 2.0, 0.7
+    R = np.linspace(ri, ro, 20001)
+    n = an.rigid_density(R, Om, 1.0, ri, ro)
+    total = 2 * math.pi * np.trapezoid(n * R, R)
+    assert total == pytest.approx(math.pi * (ro ** 2 - ri ** 2), rel=1e-8)
