@@ -1,0 +1,325 @@
+"""Benchmark of the chi-formulation circular Couette TVD-RK3 step on GB300.
+
+Workload (one "step" = one full TVD-RK3 step, three fused stage kernels, over
+one batch): the circular Couette scale-up case -- 1024 equidistant cells between
+R_in = 1 and R_out = 2, model HH(4;8)xH(4;20) (16 x 20 = 320 velocities), inner
+wall speed 0.1, outer wall at rest, T_w = 1, one instance for each
+Kn in {1e-3, 1e-2, 0.1, 1, 10} (Aoki relaxation time), FP32-bulk storage and
+stencil arithmetic with FP64 moment and wall-flux reductions.  The FP64 path is
+timed on the same batch and reported beside it.  Input: seeded perturbed
+equilibrium, synthetic.
+
+Metric: cell-velocity updates per second (cells x velocities advanced by one
+RK3 step / wall time).  The working set (13 MB) fits in L2, so L2 is flushed
+(a 512 MB write) between timed steps; each step is timed alone with CUDA
+events on the launching stream.
+
+--impl reference times the fp64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MODEL = "HH(4;8)xH(4;20)"
+N_CELLS = 1024
+KNS = [1e-3, 1e-2, 0.1, 1.0, 10.0]
+U_WALL = 0.1
+DT = 5e-5  # CFL 0.4 with max |p^R| = 5.21 and dR = 1/1024, and below tau_min
+METRIC = "cell-velocity updates/s"
+WORKLOAD = "circular Couette scale-up: 1024 cells x HH(4;8)xH(4;20) (320 velocities), Kn in {1e-3,1e-2,0.1,1,10}"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def make_inputs(dtype):
+    """Perturbed equilibrium f_eq(1, 0, 1) * (1 + 0.01 U(-1, 1)) in the library layout.
+    f_eq(1, 0, 1) has weighted populations w_i w_j (f'') and w_i w_j (f'); the
+    weights come from the library's own quadrature."""
+    from paper_1708_05944_gb300 import vlb
+    from paper_1708_05944_gb300.inputs import perturbation
+    m = vlb.vlb_parse_model(MODEL)
+    _, w0 = vlb.vlb_quadrature(m, 0)
+    _, w1 = vlb.vlb_quadrature(m, 1)
+    ww = np.outer(w0, w1)
+    cells = N_CELLS * len(KNS)
+    F = np.broadcast_to(ww, (cells, 2) + ww.shape) * perturbation((cells, 2) + ww.shape)
+    return np.ascontiguousarray(F.astype(dtype))
+
+
+def make_ctx(prec, stream_ptr):
+    from paper_1708_05944_gb300 import vlb
+    n = len(KNS)
+    return vlb.Couette(MODEL, prec, [dict(n_cells=N_CELLS)] * n, [(U_WALL, 1.0)] * n, [(0.0, 1.0)] * n, KNS,
+                       [vlb.VLB_TAU_AOKI] * n, stream=stream_ptr)
+
+
+def time_device(ctx, torch, stream, steps, warmup, flush):
+    """Per-step and per-stage-launch device times with CUDA events on the launching stream."""
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            ctx.step(DT, 1)
+        stream.synchronize()
+        step_ms, stage_ms = [], []
+        for _ in range(steps):
+            flush.fill_(1.0)  # evict L2 between timed steps (outside the events)
+            marks = [ev() for _ in range(4)]
+            marks[0].record(stream)
+            for k in (1, 2, 3):
+                ctx.stage(DT, k)
+                marks[k].record(stream)
+            stream.synchronize()
+            t = [marks[0].elapsed_time(marks[k]) for k in (1, 2, 3)]
+            step_ms.append(t[2])
+            stage_ms += [t[0], t[1] - t[0], t[2] - t[1]]
+    return np.array(step_ms), np.array(stage_ms)
+
+
+def time_e2e(ctx, torch, stream, host_in, host_out, steps):
+    """Same metric through the C ABI with host buffers: H2D of the step's input,
+    one RK3 step, D2H of the result, all inside the timed region."""
+    with torch.cuda.stream(stream):
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            ctx.set_f(host_in)
+            ctx.step(DT, 1)
+            ctx.read_f(host_out)
+        stream.synchronize()
+        return time.perf_counter() - t0
+
+
+def oracle_sample(seconds_target=15.0):
+    """The fp64 CPU oracle, as it stands, on a bounded sample: one Kn = 0.1 instance
+    of the workload (1024 cells x 320 velocities), whole RK3 steps until the
+    target time is reached."""
+    from oracle.couette import TAU_AOKI, CouetteGrid, CouetteOracle, Wall
+    from paper_1708_05944_gb300.inputs import perturbation
+    o = CouetteOracle(MODEL, CouetteGrid(N_CELLS), Wall(U_WALL), Wall(0.0), 0.1, TAU_AOKI)
+    F = o.initial_equilibrium()
+    F = F * perturbation(F.shape)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds_target or steps == 0:
+        F = o.step(F, DT)
+        steps += 1
+    dt = time.perf_counter() - t0
+    units = N_CELLS * 320 * steps
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return units / dt, steps, dt, cores
+
+
+def threads_used():
+    # numpy element-wise work and einsum without BLAS run on one thread
+    return 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    per = []
+    for _ in range(args.warmup):
+        oracle_sample(seconds_target=0.0)
+    for _ in range(args.steps):  # each step: one RK3 step of one instance (about 0.5 s)
+        v, steps, dt, _ = oracle_sample(seconds_target=0.0)
+        per.append((v, steps, dt))
+    value = float(np.mean([p[0] for p in per]))
+    units = N_CELLS * 320
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-velocity updates/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * units / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "one Kn=0.1 instance, whole RK3 steps", "model": MODEL},
+            "cpu_baseline": {"value": value, "unit": "cell-velocity updates/s", "cores": threads_used(),
+                             "kind": "oracle",
+                             "sample": f"{sum(p[1] for p in per)} RK3 steps of one 1024-cell Kn=0.1 instance"},
+            "e2e": {"value": value, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_1708_05944_gb300 import vlb
+
+    stream = torch.cuda.Stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    units = N_CELLS * len(KNS) * 320  # cell-velocities of one batch
+
+    # FP32-bulk (headline)
+    ctx = make_ctx(vlb.VLB_FP32_BULK, sptr)
+    ctx.set_f(make_inputs(np.float32))
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    step_ms, stage_ms = time_device(ctx, torch, stream, args.steps, args.warmup, flush)
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    value = units * world * args.steps / (total_ms * 1e-3)
+    launches = 3 * args.steps
+
+    # roofline of the stage kernel: algorithmic bytes per launch / mean launch time
+    esize = 4
+    bytes_per_step = units * 2 * esize * (2 + 3 + 3)  # stage 1: r+w; stages 2, 3: 2 reads + w
+    bytes_per_launch = bytes_per_step / 3.0
+    launch_ms = float(stage_ms.mean())
+    hbm, peak_kind = peaks()
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers
+    host_in = torch.from_numpy(make_inputs(np.float32)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    e2e_s = time_e2e(ctx, torch, stream, host_in, host_out, e2e_steps)
+    e2e_value = units * world * e2e_steps / e2e_s
+    ctx.close()
+
+    # FP64 path on the same batch
+    ctx64 = make_ctx(vlb.VLB_FP64, sptr)
+    ctx64.set_f(make_inputs(np.float64))
+    s64, _ = time_device(ctx64, torch, stream, max(3, min(args.steps, 20)), 2, flush)
+    fp64_value = units * world * len(s64) / (float(s64.sum()) * 1e-3)
+    ctx64.close()
+
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        v, steps, dt, cores = oracle_sample(seconds_target=args.cpu_seconds)
+        cpu = {"value": v, "unit": "cell-velocity updates/s", "cores": threads_used(), "kind": "oracle",
+               "sample": f"{steps} RK3 steps of one 1024-cell Kn=0.1 instance in {dt:.1f} s "
+                         f"({cores} host cores visible, numpy single-threaded)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-velocity updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "model": MODEL, "cells": N_CELLS, "velocities": 320,
+                   "instances_per_gpu": len(KNS), "kn": KNS, "precision": "fp32-bulk (fp64 reductions)",
+                   "dt": DT, "l2": "flushed (512 MB write) between timed steps"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                     "frac": achieved / hbm, "traffic": None,
+                     "kernel": "couette_stage_kernel<float,16,16,20,256>",
+                     "peak_source": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "cell-velocity updates/s",
+                "h2d_bytes_per_step": int(host_in.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "fp64": {"value": fp64_value, "unit": "cell-velocity updates/s", "ms_per_step": float(s64.mean())},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

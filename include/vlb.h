@@ -1,0 +1,178 @@
+/*
+ * vlb.h -- C ABI of libvlb, a GB300 (sm_103a) solver for the vielbein
+ * finite-difference lattice Boltzmann method of Busuioc & Ambrus,
+ * "Lattice Boltzmann models based on the vielbein formalism for the
+ * simulation of flows in curvilinear geometries" (arXiv:1708.05944).
+ *
+ * The hot path is one TVD-RK3 stage (Sec. III.A, Eq. rk3) of the reduced
+ * distributions f', f'' (Sec. IV.A, Eq. fred) over every (cell, momentum)
+ * pair: chi-formulation WENO-5 advection (Secs. III.B-C, Eqs. chi_def,
+ * flux_def, weno5_flux), the Hermite-projected momentum-derivative term
+ * (Sec. IV.C, Eqs. df_K_H, dfp_K_H, df_K_hh, dfp_K_hh), BGK relaxation to the
+ * truncated Hermite equilibrium (Sec. IV.D, Eqs. feq_red, eq_gak_H,
+ * eq_gak_hh), the moment reduction (Eq. macro_red) and diffuse-reflection
+ * walls whose density n_w balances the wall mass flux (Sec. III.E, Eq. nw).
+ *
+ * Conventions
+ *  - m = k_B = 1.  Axis 0 of momentum space is the wall-normal one (p^R for
+ *    circular Couette flow), axis 1 the tangential one (p^phi).
+ *  - Populations are the weighted ones of Sec. IV.B,
+ *    f_ij = w_i w_j f(p_i, p_j) / (omega(p_i) omega(p_j)), so moments are plain sums.
+ *  - Distribution layout (host or device, as passed): contiguous
+ *    [cell][field][i][j], field 0 = f', field 1 = f'', cell running over the
+ *    instances of a context in order, i over nq0 axis-0 nodes, j over nq1
+ *    axis-1 nodes; real type double (VLB_FP64) or float (VLB_FP32_BULK).
+ *  - Every call returns a vlb_status; vlb_last_error() gives the message.
+ *  - Calls run on the CUDA stream given at creation (a cudaStream_t passed as
+ *    void*, NULL = legacy default stream).  Compute calls are asynchronous;
+ *    read calls synchronise that stream.
+ *  - The library owns the device memory it allocates and frees it in
+ *    vlb_destroy.  Pointers passed in with on_device = 1 stay owned by the
+ *    caller and are only read or written during the call.
+ *  - Compute calls need a CUDA device; without one they return VLB_ERR_CUDA.
+ *    Model and quadrature queries (vlb_parse_model, vlb_quadrature) run on
+ *    the host only.
+ */
+#ifndef VLB_H
+#define VLB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct vlb_ctx vlb_ctx;
+
+typedef enum {
+  VLB_OK = 0,
+  VLB_ERR_INVALID = -1,     /* argument out of range or malformed */
+  VLB_ERR_UNSUPPORTED = -2, /* valid in the method but not built (e.g. > 32 nodes on an axis) */
+  VLB_ERR_CUDA = -3,        /* CUDA runtime failure (message holds cudaGetErrorString) */
+  VLB_ERR_NONFINITE = -4,   /* a moment or wall density came out NaN or Inf */
+  VLB_ERR_TIMEOUT = -5,     /* a bounded device wait ran out; results of that call are invalid */
+  VLB_ERR_STATE = -6        /* call not allowed in the context's current state */
+} vlb_status;
+
+typedef enum { VLB_FULL = 0, VLB_HALF = 1 } vlb_quad_kind;           /* H(N;Q) or HH(N;Q) */
+typedef enum { VLB_FP64 = 0, VLB_FP32_BULK = 1 } vlb_precision;
+typedef enum {
+  VLB_TAU_KN_OVER_NT = 0, /* tau = Kn / (n T), Eq. (hydro_tau) and Eq. (canalie_tau) */
+  VLB_TAU_AOKI = 1,       /* tau = sqrt(pi/8) Kn / n, Eq. (tau_aoki) */
+  VLB_TAU_KN_OVER_N = 2   /* tau = Kn / n (Sec. VI.C and VI.G runs) */
+} vlb_tau_mode;
+
+/* Model HH(N;Q) x H(N;Q) of Eq. (model): per axis the quadrature kind, the
+ * expansion order N of the equilibrium (0 <= N < Q, Eq. norder_limit) and
+ * the order Q.  An axis has Q nodes (full range) or 2Q nodes (half range). */
+typedef struct {
+  int kind[2];
+  int N[2];
+  int Q[2];
+} vlb_model;
+
+/* Circular Couette grid (Sec. VI.A.1): n_cells cells between r_in < r_out,
+ * equidistant when stretch_A == 0, else tanh-stretched per Eq. (eta_def) with
+ * amplitude 0 < stretch_A < 1 and centre 0 <= stretch_delta <= 1. */
+typedef struct {
+  int n_cells;
+  double r_in, r_out;
+  double stretch_A, stretch_delta;
+} vlb_couette_grid;
+
+/* Wall of a Couette instance: tangential velocity u^phi (= Omega R) and temperature. */
+typedef struct {
+  double u_tangential;
+  double T;
+} vlb_wall;
+
+/* Parse the paper's model notation, e.g. "HH(4;8)xH(4;20)" (Eq. model).
+ * Returns VLB_ERR_INVALID for malformed strings or N >= Q. */
+vlb_status vlb_parse_model(const char* text, vlb_model* out);
+
+/* Nodes and weights of one axis (Sec. IV.B): full range -- roots of H_Q with
+ * the Gauss weights of Eq. (w_H); half range -- the Q roots of h_Q followed by
+ * their negatives, with the weights of Eq. (w_hh).  p and w are host arrays of
+ * nq = Q or 2Q doubles, written in the node order used for populations. */
+vlb_status vlb_quadrature(const vlb_model* model, int axis, double* p, double* w);
+
+/* Nodes, weights and the force kernels of one axis as built by the library:
+ * K[k*nq + k'] (Eqs. df_K_H / df_K_hh, d/dp f) and Kt[k*nq + k'] (Eqs.
+ * dfp_K_H / dfp_K_hh, d/dp (p f)), nq*nq doubles each; any output may be
+ * NULL.  Host only; lets callers check the library's tables. */
+vlb_status vlb_axis_tables(const vlb_model* model, int axis, double* p, double* w, double* K, double* Kt);
+
+/* Number of nodes of an axis (Q or 2Q); negative vlb_status on error. */
+int vlb_axis_nodes(const vlb_model* model, int axis);
+
+/* Create a context of n_inst independent circular Couette instances (chi
+ * formulation, Sec. VI.A) sharing one model and precision.  grids, inner and
+ * outer walls, kn and tau_mode are host arrays of n_inst entries.  Allocates
+ * the distribution buffers (three RK3 copies) on the current device.  The
+ * distribution starts as f_eq(n=1, u=0, T=1).  Errors: VLB_ERR_INVALID
+ * (n_cells < 3, r_in >= r_out, kn <= 0, bad model),
+ * VLB_ERR_UNSUPPORTED (more than 32 nodes on an axis), VLB_ERR_CUDA. */
+vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_inst,
+                              const vlb_couette_grid* grids, const vlb_wall* inner,
+                              const vlb_wall* outer, const double* kn, const int* tau_mode,
+                              void* cuda_stream, vlb_ctx** out);
+
+/* Total number of cells over all instances, nodes per cell (nq0 * nq1), and
+ * the size in bytes of one distribution copy in the layout documented above. */
+vlb_status vlb_sizes(const vlb_ctx* ctx, long long* total_cells, int* nvel, long long* f_bytes);
+
+/* Overwrite the walls (host arrays of n_inst entries). */
+vlb_status vlb_set_walls(vlb_ctx* ctx, const vlb_wall* inner, const vlb_wall* outer);
+
+/* Set every cell of every instance to f_eq(n0, (u0, u1), T0) (Eq. feq_red). */
+vlb_status vlb_init_equilibrium(vlb_ctx* ctx, double n0, double u0, double u1, double T0);
+
+/* Copy a distribution in (vlb_set_f: becomes the current F_l) or out
+ * (vlb_read_f: the most recently written one -- after vlb_stage(k) that
+ * stage's output, after vlb_step the new F_l).  f has the documented layout
+ * and the context's real type; on_device selects a device or host pointer. */
+vlb_status vlb_set_f(vlb_ctx* ctx, const void* f, int on_device);
+vlb_status vlb_read_f(vlb_ctx* ctx, void* f, int on_device);
+
+/* One RK3 stage k in {1, 2, 3} (Eq. rk3) on the context buffers, with time
+ * step dt (> 0: the same for all instances; 0: per-instance steps set by
+ * vlb_set_dt).  Stage 1 reads F_l and writes F^(1); stage 2 reads F_l and
+ * F^(1) and writes F^(2); stage 3 reads F_l and F^(2) and writes F_{l+1},
+ * which then becomes the current distribution.  For parity tests. */
+vlb_status vlb_stage(vlb_ctx* ctx, double dt, int k);
+
+/* nsteps full TVD-RK3 steps (3 stages each), asynchronous on the stream. */
+vlb_status vlb_step(vlb_ctx* ctx, double dt, long long nsteps);
+
+/* Per-instance time steps (host array of n_inst doubles > 0) used when dt = 0. */
+vlb_status vlb_set_dt(vlb_ctx* ctx, const double* dt);
+
+/* Macroscopic fields per cell (Eqs. macro_red): n, u^0, u^1, T, and optionally
+ * T^{ab} (3 per cell: 00, 01, 11) and q^a (2 per cell), computed in FP64 from
+ * the most recently written distribution (as for vlb_read_f).  Arrays hold total_cells (x3, x2) doubles; any
+ * pointer may be NULL.  Synchronises the stream; VLB_ERR_NONFINITE if a
+ * moment is NaN or Inf. */
+vlb_status vlb_read_moments(vlb_ctx* ctx, double* n, double* u0, double* u1, double* T,
+                            double* Tab, double* q, int on_device);
+
+/* Wall densities n_w (Eq. nw) of the last stage: 2 per instance (inner, outer). */
+vlb_status vlb_wall_density(vlb_ctx* ctx, double* nw);
+
+/* Steady-state norms of Eq. (msites_steady) between the current moments and
+ * those of the previous call (the first call only stores them and returns
+ * zeros): per instance L2_u, L2_n, L2_T (host arrays of n_inst, NULL allowed). */
+vlb_status vlb_residual(vlb_ctx* ctx, double* l2_u, double* l2_n, double* l2_T);
+
+/* Write / restore the distribution and step counter to / from a file
+ * (little-endian; a header records model, precision and sizes, checked on load). */
+vlb_status vlb_save(vlb_ctx* ctx, const char* path);
+vlb_status vlb_load(vlb_ctx* ctx, const char* path);
+
+/* Number of kernels the last vlb_step / vlb_stage call launched. */
+long long vlb_kernel_launches(const vlb_ctx* ctx);
+
+const char* vlb_last_error(const vlb_ctx* ctx);
+void vlb_destroy(vlb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VLB_H */

@@ -1,0 +1,697 @@
+// C ABI of libvlb (declared in include/vlb.h): contexts, buffers, launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/vlb.h"
+#include "vlb_launch.h"
+#include "vlb_stage.cuh"
+#include "vlb_tables.h"
+
+using namespace vlb;
+
+struct vlb_ctx {
+  vlb_model model{};
+  int prec = 0;
+  int n_inst = 0;
+  cudaStream_t stream = nullptr;
+  AxisTables ax[2];
+  int nq0 = 0, nq1 = 0, V = 0, Vp = 0;
+  long long total_cells = 0;
+  size_t esize = 8;
+  std::vector<InstDesc> inst;
+  std::vector<TileDesc> tiles;
+  std::vector<GeoCell> geo;
+  std::vector<vlb_couette_grid> grids;
+  ModelArgs margs{};
+  std::unique_ptr<KArgs<float>> k32;
+  std::unique_ptr<KArgs<double>> k64;
+  void* F[3] = {nullptr, nullptr, nullptr};
+  int cur = 0;   // buffer holding F_l
+  int last = 0;  // buffer written by the most recent stage
+  int stage_done = 0;
+  InstDesc* d_inst = nullptr;
+  TileDesc* d_tiles = nullptr;
+  GeoCell* d_geo = nullptr;
+  double* d_nw = nullptr;
+  unsigned* d_err = nullptr;
+  double* d_mom = nullptr;
+  double* d_prev = nullptr;
+  double* d_res = nullptr;
+  bool have_prev = false;
+  long long launches = 0;
+  long long steps = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+vlb_status fail(vlb_ctx* c, vlb_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  g_err = msg;
+  return s;
+}
+
+vlb_status cuda_fail(vlb_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, VLB_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define VLB_CUDA(c, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail((c), e_, #call); \
+  } while (0)
+
+bool valid_model(const vlb_model* m, std::string* why) {
+  for (int a = 0; a < 2; ++a) {
+    if (m->kind[a] != VLB_FULL && m->kind[a] != VLB_HALF) {
+      *why = "quadrature kind must be VLB_FULL or VLB_HALF";
+      return false;
+    }
+    if (m->Q[a] < 1 || m->N[a] < 0 || m->N[a] >= m->Q[a]) {
+      *why = "each axis needs 0 <= N < Q (Eq. norder_limit)";
+      return false;
+    }
+  }
+  return true;
+}
+
+int axis_nodes(const vlb_model* m, int a) { return m->kind[a] == VLB_HALF ? 2 * m->Q[a] : m->Q[a]; }
+
+// geometry of one Couette instance: chi-formulation factors per cell
+void couette_geometry(const vlb_couette_grid& g, GeoCell* out) {
+  const int n = g.n_cells;
+  std::vector<double> Rf(n + 1), Rc(n), wres(n);
+  const double L = g.r_out - g.r_in;
+  if (g.stretch_A == 0.0) {
+    for (int s = 0; s <= n; ++s) Rf[s] = g.r_in + L * s / n;
+    for (int s = 0; s < n; ++s) {
+      Rc[s] = g.r_in + (s + 0.5) / n * L;
+      wres[s] = Rc[s] * L / n;
+    }
+  } else {
+    const double A = g.stretch_A, dl = g.stretch_delta;
+    const double A0 = dl > 1.0 - dl ? dl : 1.0 - dl;
+    const double e_in = -atanh(A * dl / A0), e_out = atanh(A * (1.0 - dl) / A0);
+    const double de = (e_out - e_in) / n;
+    auto R = [&](double eta) { return g.r_in + L * (dl + A0 / A * tanh(eta)); };
+    for (int s = 0; s <= n; ++s) Rf[s] = R(e_in + s * de);
+    Rf[0] = g.r_in;
+    Rf[n] = g.r_out;
+    for (int s = 0; s < n; ++s) {
+      const double ec = e_in + (s + 0.5) * de;
+      Rc[s] = R(ec);
+      wres[s] = A0 / A * L * Rc[s] * de / (cosh(ec) * cosh(ec));
+    }
+  }
+  for (int s = 0; s < n; ++s) {
+    const double rp = Rf[s + 1], rm = Rf[s];
+    const double den = (rp - rm) * (rp + rm);
+    out[s].cp = 2.0 * rp / den;
+    out[s].cm = 2.0 * rm / den;
+    out[s].inv_rbar = 2.0 / (rp + rm);
+    out[s].wres = wres[s];
+  }
+}
+
+template <typename real>
+vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
+  StageArgs<real> a{};
+  a.Fprev = static_cast<const real*>(c->F[prev]);
+  a.Fl = static_cast<const real*>(c->F[c->cur]);
+  a.Fout = static_cast<real*>(c->F[out]);
+  if (k == 1) {
+    a.ca = 0.0, a.cb = 1.0, a.cc = 1.0;
+  } else if (k == 2) {
+    a.ca = 0.75, a.cb = 0.25, a.cc = 0.25;
+  } else {
+    a.ca = 1.0 / 3.0, a.cb = 2.0 / 3.0, a.cc = 2.0 / 3.0;
+  }
+  a.inst = c->d_inst;
+  a.tiles = c->d_tiles;
+  a.n_tiles = int(c->tiles.size());
+  a.geo = c->d_geo;
+  a.nw = c->d_nw;
+  a.err = c->d_err;
+  a.Vp = c->Vp;
+  a.max_polls = 1ull << 26;
+  const KArgs<real>* kk;
+  if constexpr (sizeof(real) == 4) kk = c->k32.get(); else kk = c->k64.get();
+  cudaError_t e = launch_stage<real>(a, c->margs, *kk, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
+  c->launches += 1;
+  return VLB_OK;
+}
+
+vlb_status run_stage(vlb_ctx* c, int k) {
+  // buffers: cur = F_l; stage 1 -> (cur+1); stage 2 reads (cur+1) -> (cur+2); stage 3 reads (cur+2) -> (cur+1)
+  const int b1 = (c->cur + 1) % 3, b2 = (c->cur + 2) % 3;
+  int prev, out;
+  if (k == 1) {
+    prev = c->cur, out = b1;
+  } else if (k == 2) {
+    prev = b1, out = b2;
+  } else {
+    prev = b2, out = b1;
+  }
+  vlb_status st = c->prec == VLB_FP64 ? do_stage<double>(c, k, prev, out) : do_stage<float>(c, k, prev, out);
+  if (st != VLB_OK) return st;
+  c->last = out;
+  c->stage_done = k;
+  if (k == 3) {
+    c->cur = out;
+    c->steps += 1;
+  }
+  return VLB_OK;
+}
+
+vlb_status check_err(vlb_ctx* c) {
+  unsigned h = 0;
+  VLB_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (h & ERR_TIMEOUT) return fail(c, VLB_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (h & ERR_NONFINITE) return fail(c, VLB_ERR_NONFINITE, "a wall density came out non-finite");
+  return VLB_OK;
+}
+
+vlb_status compute_moments(vlb_ctx* c, double* dst) {
+  cudaError_t e = c->prec == VLB_FP64
+                      ? launch_moments<double>(static_cast<const double*>(c->F[c->last]), c->total_cells, c->Vp,
+                                               c->margs, dst, c->stream)
+                      : launch_moments<float>(static_cast<const float*>(c->F[c->last]), c->total_cells, c->Vp,
+                                              c->margs, dst, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel launch");
+  return VLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vlb_status vlb_parse_model(const char* text, vlb_model* out) {
+  if (!text || !out) return fail(nullptr, VLB_ERR_INVALID, "null argument");
+  vlb_model m{};
+  const char* s = text;
+  for (int a = 0; a < 2; ++a) {
+    while (*s == ' ') ++s;
+    int kind;
+    if (s[0] == 'H' && s[1] == 'H') {
+      kind = VLB_HALF;
+      s += 2;
+    } else if (s[0] == 'H') {
+      kind = VLB_FULL;
+      s += 1;
+    } else {
+      return fail(nullptr, VLB_ERR_INVALID, "model component must start with H or HH");
+    }
+    int N, Q, used = 0;
+    if (sscanf(s, "(%d;%d)%n", &N, &Q, &used) != 2 || used == 0)
+      return fail(nullptr, VLB_ERR_INVALID, "expected (N;Q) after H or HH");
+    s += used;
+    m.kind[a] = kind;
+    m.N[a] = N;
+    m.Q[a] = Q;
+    while (*s == ' ') ++s;
+    if (a == 0) {
+      if (*s == 'x' || *s == 'X') {
+        ++s;
+      } else if ((unsigned char)s[0] == 0xC3 && (unsigned char)s[1] == 0x97) {  // UTF-8 multiplication sign
+        s += 2;
+      } else {
+        return fail(nullptr, VLB_ERR_INVALID, "expected 'x' between the two axes");
+      }
+    }
+  }
+  while (*s == ' ') ++s;
+  if (*s) return fail(nullptr, VLB_ERR_INVALID, "trailing characters after the model");
+  std::string why;
+  if (!valid_model(&m, &why)) return fail(nullptr, VLB_ERR_INVALID, why);
+  *out = m;
+  return VLB_OK;
+}
+
+int vlb_axis_nodes(const vlb_model* m, int axis) {
+  std::string why;
+  if (!m || axis < 0 || axis > 1 || !valid_model(m, &why)) return VLB_ERR_INVALID;
+  return axis_nodes(m, axis);
+}
+
+vlb_status vlb_axis_tables(const vlb_model* m, int axis, double* p, double* w, double* K, double* Kt) {
+  std::string why;
+  if (!m || axis < 0 || axis > 1) return fail(nullptr, VLB_ERR_INVALID, "bad axis");
+  if (!valid_model(m, &why)) return fail(nullptr, VLB_ERR_INVALID, why);
+  AxisTables t;
+  if (!build_axis(m->kind[axis] == VLB_HALF ? 1 : 0, m->N[axis], m->Q[axis], &t, &why))
+    return fail(nullptr, VLB_ERR_INVALID, why);
+  const int nq = t.nq;
+  for (int k = 0; k < nq; ++k) {
+    if (p) p[k] = t.p[k];
+    if (w) w[k] = t.w[k];
+  }
+  for (int k = 0; k < nq * nq; ++k) {
+    if (K) K[k] = t.K[k];
+    if (Kt) Kt[k] = t.Kt[k];
+  }
+  return VLB_OK;
+}
+
+vlb_status vlb_quadrature(const vlb_model* m, int axis, double* p, double* w) {
+  if (!p || !w) return fail(nullptr, VLB_ERR_INVALID, "null output");
+  return vlb_axis_tables(m, axis, p, w, nullptr, nullptr);
+}
+
+vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_inst,
+                              const vlb_couette_grid* grids, const vlb_wall* inner, const vlb_wall* outer,
+                              const double* kn, const int* tau_mode, void* cuda_stream, vlb_ctx** out) {
+  if (!model || !grids || !inner || !outer || !kn || !tau_mode || !out || n_inst < 1)
+    return fail(nullptr, VLB_ERR_INVALID, "null or empty argument");
+  *out = nullptr;
+  std::string why;
+  if (!valid_model(model, &why)) return fail(nullptr, VLB_ERR_INVALID, why);
+  if (prec != VLB_FP64 && prec != VLB_FP32_BULK) return fail(nullptr, VLB_ERR_INVALID, "bad precision");
+  for (int i = 0; i < n_inst; ++i) {
+    const vlb_couette_grid& g = grids[i];
+    if (g.n_cells < 3) return fail(nullptr, VLB_ERR_INVALID, "a Couette instance needs at least 3 cells");
+    if (!(g.r_in > 0.0) || !(g.r_out > g.r_in)) return fail(nullptr, VLB_ERR_INVALID, "need 0 < r_in < r_out");
+    if (!(g.stretch_A >= 0.0 && g.stretch_A < 1.0) || !(g.stretch_delta >= 0.0 && g.stretch_delta <= 1.0))
+      return fail(nullptr, VLB_ERR_INVALID, "stretching needs 0 <= A < 1, 0 <= delta <= 1");
+    if (!(kn[i] > 0.0)) return fail(nullptr, VLB_ERR_INVALID, "Kn must be positive");
+    if (tau_mode[i] < 0 || tau_mode[i] > 2) return fail(nullptr, VLB_ERR_INVALID, "bad tau mode");
+    if (!(inner[i].T > 0.0) || !(outer[i].T > 0.0)) return fail(nullptr, VLB_ERR_INVALID, "wall temperature must be > 0");
+  }
+  const int nq0 = axis_nodes(model, 0), nq1 = axis_nodes(model, 1);
+  if (nq0 > MAXQ || nq1 > MAXQ) return fail(nullptr, VLB_ERR_UNSUPPORTED, "more than 32 nodes on an axis");
+  if (model->N[0] + 1 > MAXN || model->N[1] + 1 > MAXN)
+    return fail(nullptr, VLB_ERR_UNSUPPORTED, "expansion order above 7");
+
+  std::unique_ptr<vlb_ctx> c(new vlb_ctx);
+  c->model = *model;
+  c->prec = prec;
+  c->n_inst = n_inst;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  for (int a = 0; a < 2; ++a)
+    if (!build_axis(model->kind[a] == VLB_HALF ? 1 : 0, model->N[a], model->Q[a], &c->ax[a], &why))
+      return fail(nullptr, VLB_ERR_INVALID, why);
+  c->nq0 = nq0;
+  c->nq1 = nq1;
+  c->V = nq0 * nq1;
+  c->Vp = (c->V + 3) / 4 * 4;
+  c->esize = prec == VLB_FP64 ? 8 : 4;
+  const size_t smem = prec == VLB_FP64 ? stage_smem_bytes<double>(nq0, nq1, c->Vp)
+                                       : stage_smem_bytes<float>(nq0, nq1, c->Vp);
+  if (smem > 227 * 1024) return fail(nullptr, VLB_ERR_UNSUPPORTED, "velocity set too large for one tile");
+
+  ModelArgs& m = c->margs;
+  m.nq0 = nq0;
+  m.nq1 = nq1;
+  m.N0 = model->N[0];
+  m.N1 = model->N[1];
+  m.kind0 = model->kind[0] == VLB_HALF ? 1 : 0;
+  m.kind1 = model->kind[1] == VLB_HALF ? 1 : 0;
+  for (int k = 0; k < nq0; ++k) {
+    m.p0[k] = c->ax[0].p[k];
+    for (int s = 0; s <= m.N0; ++s) m.tab0[k * MAXN + s] = c->ax[0].eqtab[k * (m.N0 + 1) + s];
+  }
+  for (int k = 0; k < nq1; ++k) {
+    m.p1[k] = c->ax[1].p[k];
+    for (int s = 0; s <= m.N1; ++s) m.tab1[k * MAXN + s] = c->ax[1].eqtab[k * (m.N1 + 1) + s];
+  }
+  c->k32.reset(new KArgs<float>());
+  c->k64.reset(new KArgs<double>());
+  memset(c->k32.get(), 0, sizeof(KArgs<float>));
+  memset(c->k64.get(), 0, sizeof(KArgs<double>));
+  for (int i = 0; i < nq0; ++i)
+    for (int ip = 0; ip < nq0; ++ip) {
+      c->k64->K0[i * MAXQ + ip] = c->ax[0].K[i * nq0 + ip];
+      c->k32->K0[i * MAXQ + ip] = float(c->ax[0].K[i * nq0 + ip]);
+    }
+  for (int j = 0; j < nq1; ++j)
+    for (int jp = 0; jp < nq1; ++jp) {
+      c->k64->Kt1[j * MAXQ + jp] = c->ax[1].Kt[j * nq1 + jp];
+      c->k32->Kt1[j * MAXQ + jp] = float(c->ax[1].Kt[j * nq1 + jp]);
+    }
+
+  const int TC = prec == VLB_FP64 ? stage_tile_cells<double>() : stage_tile_cells<float>();
+  long long cell0 = 0;
+  for (int i = 0; i < n_inst; ++i) {
+    InstDesc d{};
+    d.cell0 = cell0;
+    d.n_cells = grids[i].n_cells;
+    d.tau_mode = tau_mode[i];
+    d.kn = kn[i];
+    d.dt = 0.0;
+    d.u_in = inner[i].u_tangential;
+    d.T_in = inner[i].T;
+    d.u_out = outer[i].u_tangential;
+    d.T_out = outer[i].T;
+    c->inst.push_back(d);
+    c->grids.push_back(grids[i]);
+    for (int c0 = 0; c0 < d.n_cells; c0 += TC) c->tiles.push_back(TileDesc{i, c0});
+    cell0 += d.n_cells;
+  }
+  c->total_cells = cell0;
+  c->geo.resize(cell0);
+  for (int i = 0; i < n_inst; ++i) couette_geometry(grids[i], c->geo.data() + c->inst[i].cell0);
+
+  vlb_ctx* cp = c.get();
+  const size_t fbytes = size_t(c->total_cells) * 2 * c->Vp * c->esize;
+  for (int b = 0; b < 3; ++b) {
+    VLB_CUDA(cp, cudaMalloc(&c->F[b], fbytes));
+    VLB_CUDA(cp, cudaMemsetAsync(c->F[b], 0, fbytes, c->stream));
+  }
+  VLB_CUDA(cp, cudaMalloc(&c->d_inst, sizeof(InstDesc) * n_inst));
+  VLB_CUDA(cp, cudaMalloc(&c->d_tiles, sizeof(TileDesc) * c->tiles.size()));
+  VLB_CUDA(cp, cudaMalloc(&c->d_geo, sizeof(GeoCell) * c->total_cells));
+  VLB_CUDA(cp, cudaMalloc(&c->d_nw, sizeof(double) * 2 * n_inst));
+  VLB_CUDA(cp, cudaMalloc(&c->d_err, sizeof(unsigned)));
+  VLB_CUDA(cp, cudaMalloc(&c->d_mom, sizeof(double) * 9 * c->total_cells));
+  VLB_CUDA(cp, cudaMalloc(&c->d_prev, sizeof(double) * 9 * c->total_cells));
+  VLB_CUDA(cp, cudaMalloc(&c->d_res, sizeof(double) * 3 * n_inst));
+  VLB_CUDA(cp, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * n_inst, cudaMemcpyHostToDevice, c->stream));
+  VLB_CUDA(cp, cudaMemcpyAsync(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * c->tiles.size(),
+                               cudaMemcpyHostToDevice, c->stream));
+  VLB_CUDA(cp, cudaMemcpyAsync(c->d_geo, c->geo.data(), sizeof(GeoCell) * c->total_cells, cudaMemcpyHostToDevice,
+                               c->stream));
+  VLB_CUDA(cp, cudaMemsetAsync(c->d_nw, 0, sizeof(double) * 2 * n_inst, c->stream));
+  VLB_CUDA(cp, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+  VLB_CUDA(cp, cudaStreamSynchronize(c->stream));
+  vlb_status st = vlb_init_equilibrium(cp, 1.0, 0.0, 0.0, 1.0);
+  if (st != VLB_OK) return st;
+  *out = c.release();
+  return VLB_OK;
+}
+
+vlb_status vlb_sizes(const vlb_ctx* c, long long* total_cells, int* nvel, long long* f_bytes) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (total_cells) *total_cells = c->total_cells;
+  if (nvel) *nvel = c->V;
+  if (f_bytes) *f_bytes = c->total_cells * 2LL * c->V * (long long)c->esize;
+  return VLB_OK;
+}
+
+vlb_status vlb_set_walls(vlb_ctx* c, const vlb_wall* inner, const vlb_wall* outer) {
+  if (!c || !inner || !outer) return fail(c, VLB_ERR_INVALID, "null argument");
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (!(inner[i].T > 0.0) || !(outer[i].T > 0.0)) return fail(c, VLB_ERR_INVALID, "wall temperature must be > 0");
+    c->inst[i].u_in = inner[i].u_tangential;
+    c->inst[i].T_in = inner[i].T;
+    c->inst[i].u_out = outer[i].u_tangential;
+    c->inst[i].T_out = outer[i].T;
+  }
+  VLB_CUDA(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice,
+                              c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_init_equilibrium(vlb_ctx* c, double n0, double u0, double u1, double T0) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (!(n0 > 0.0) || !(T0 > 0.0)) return fail(c, VLB_ERR_INVALID, "need n0 > 0 and T0 > 0");
+  cudaError_t e = c->prec == VLB_FP64
+                      ? launch_init_equilibrium<double>(static_cast<double*>(c->F[c->cur]), c->total_cells, c->Vp,
+                                                        c->margs, n0, u0, u1, T0, c->stream)
+                      : launch_init_equilibrium<float>(static_cast<float*>(c->F[c->cur]), c->total_cells, c->Vp,
+                                                       c->margs, n0, u0, u1, T0, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "init kernel launch");
+  c->last = c->cur;
+  c->stage_done = 0;
+  c->have_prev = false;
+  return VLB_OK;
+}
+
+vlb_status vlb_set_f(vlb_ctx* c, const void* f, int on_device) {
+  if (!c || !f) return fail(c, VLB_ERR_INVALID, "null argument");
+  const size_t w = size_t(c->V) * c->esize, pitch = size_t(c->Vp) * c->esize;
+  VLB_CUDA(c, cudaMemcpy2DAsync(c->F[c->cur], pitch, f, w, w, size_t(c->total_cells) * 2,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->last = c->cur;
+  c->stage_done = 0;
+  c->have_prev = false;
+  return VLB_OK;
+}
+
+vlb_status vlb_read_f(vlb_ctx* c, void* f, int on_device) {
+  if (!c || !f) return fail(c, VLB_ERR_INVALID, "null argument");
+  const size_t w = size_t(c->V) * c->esize, pitch = size_t(c->Vp) * c->esize;
+  VLB_CUDA(c, cudaMemcpy2DAsync(f, w, c->F[c->last], pitch, w, size_t(c->total_cells) * 2,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  return check_err(c);
+}
+
+vlb_status vlb_set_dt(vlb_ctx* c, const double* dt) {
+  if (!c || !dt) return fail(c, VLB_ERR_INVALID, "null argument");
+  for (int i = 0; i < c->n_inst; ++i)
+    if (!(dt[i] > 0.0)) return fail(c, VLB_ERR_INVALID, "time steps must be positive");
+  for (int i = 0; i < c->n_inst; ++i) c->inst[i].dt = dt[i];
+  VLB_CUDA(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice,
+                              c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VLB_OK;
+}
+
+static vlb_status apply_dt(vlb_ctx* c, double dt) {
+  if (dt < 0.0 || std::isnan(dt)) return fail(c, VLB_ERR_INVALID, "dt must be >= 0");
+  if (dt > 0.0) {
+    bool change = false;
+    for (int i = 0; i < c->n_inst; ++i) change |= c->inst[i].dt != dt;
+    if (change) {
+      std::vector<double> v(c->n_inst, dt);
+      return vlb_set_dt(c, v.data());
+    }
+    return VLB_OK;
+  }
+  for (int i = 0; i < c->n_inst; ++i)
+    if (!(c->inst[i].dt > 0.0)) return fail(c, VLB_ERR_STATE, "dt = 0 needs per-instance steps from vlb_set_dt");
+  return VLB_OK;
+}
+
+vlb_status vlb_stage(vlb_ctx* c, double dt, int k) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (k < 1 || k > 3) return fail(c, VLB_ERR_INVALID, "stage must be 1, 2 or 3");
+  if (k != c->stage_done % 3 + 1) return fail(c, VLB_ERR_STATE, "stages must run in the order 1, 2, 3");
+  vlb_status st = apply_dt(c, dt);
+  if (st != VLB_OK) return st;
+  c->launches = 0;
+  return run_stage(c, k);
+}
+
+vlb_status vlb_step(vlb_ctx* c, double dt, long long nsteps) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (nsteps < 0) return fail(c, VLB_ERR_INVALID, "nsteps must be >= 0");
+  if (c->stage_done % 3 != 0) return fail(c, VLB_ERR_STATE, "a partial RK3 step is pending");
+  vlb_status st = apply_dt(c, dt);
+  if (st != VLB_OK) return st;
+  c->launches = 0;
+  for (long long s = 0; s < nsteps; ++s)
+    for (int k = 1; k <= 3; ++k) {
+      st = run_stage(c, k);
+      if (st != VLB_OK) return st;
+    }
+  return VLB_OK;
+}
+
+vlb_status vlb_read_moments(vlb_ctx* c, double* n, double* u0, double* u1, double* T, double* Tab, double* q,
+                            int on_device) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  vlb_status st = compute_moments(c, c->d_mom);
+  if (st != VLB_OK) return st;
+  std::vector<double> h(size_t(9) * c->total_cells);
+  VLB_CUDA(c, cudaMemcpyAsync(h.data(), c->d_mom, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  st = check_err(c);
+  if (st != VLB_OK) return st;
+  const long long N = c->total_cells;
+  std::vector<double> tmp[6];
+  double* dst[6] = {n, u0, u1, T, Tab, q};
+  bool bad = false;
+  for (long long i = 0; i < N; ++i) {
+    const double* o = &h[size_t(9) * i];
+    for (int k = 0; k < 9; ++k) bad |= !std::isfinite(o[k]);
+  }
+  if (on_device) {
+    for (int a = 0; a < 6; ++a) {
+      if (!dst[a]) continue;
+      const int width = a == 4 ? 3 : a == 5 ? 2 : 1;
+      tmp[a].resize(size_t(N) * width);
+      for (long long i = 0; i < N; ++i)
+        for (int k = 0; k < width; ++k) {
+          const int src = a < 4 ? a : (a == 4 ? 4 + k : 7 + k);
+          tmp[a][size_t(i) * width + k] = h[size_t(9) * i + src];
+        }
+      VLB_CUDA(c, cudaMemcpyAsync(dst[a], tmp[a].data(), tmp[a].size() * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->stream));
+    }
+    VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  } else {
+    for (long long i = 0; i < N; ++i) {
+      const double* o = &h[size_t(9) * i];
+      if (n) n[i] = o[0];
+      if (u0) u0[i] = o[1];
+      if (u1) u1[i] = o[2];
+      if (T) T[i] = o[3];
+      if (Tab) Tab[3 * i] = o[4], Tab[3 * i + 1] = o[5], Tab[3 * i + 2] = o[6];
+      if (q) q[2 * i] = o[7], q[2 * i + 1] = o[8];
+    }
+  }
+  if (bad) return fail(c, VLB_ERR_NONFINITE, "a moment is NaN or Inf");
+  return VLB_OK;
+}
+
+vlb_status vlb_wall_density(vlb_ctx* c, double* nw) {
+  if (!c || !nw) return fail(c, VLB_ERR_INVALID, "null argument");
+  VLB_CUDA(c, cudaMemcpyAsync(nw, c->d_nw, sizeof(double) * 2 * c->n_inst, cudaMemcpyDeviceToHost, c->stream));
+  return check_err(c);
+}
+
+vlb_status vlb_residual(vlb_ctx* c, double* l2u, double* l2n, double* l2T) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  vlb_status st = compute_moments(c, c->d_mom);
+  if (st != VLB_OK) return st;
+  std::vector<double> res(3 * size_t(c->n_inst), 0.0);
+  if (c->have_prev) {
+    cudaError_t e = launch_residual(c->d_mom, c->d_prev, c->d_inst, c->d_geo, c->n_inst, c->d_res, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "residual kernel launch");
+    VLB_CUDA(c, cudaMemcpyAsync(res.data(), c->d_res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  VLB_CUDA(c, cudaMemcpyAsync(c->d_prev, c->d_mom, sizeof(double) * 9 * c->total_cells, cudaMemcpyDeviceToDevice,
+                              c->stream));
+  st = check_err(c);
+  if (st != VLB_OK) return st;
+  c->have_prev = true;
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (l2u) l2u[i] = res[3 * i];
+    if (l2n) l2n[i] = res[3 * i + 1];
+    if (l2T) l2T[i] = res[3 * i + 2];
+  }
+  return VLB_OK;
+}
+
+struct SaveHeader {
+  char magic[8];
+  int model[6];
+  int prec, n_inst, V, pad;
+  long long total_cells, steps;
+};
+
+vlb_status vlb_save(vlb_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, VLB_ERR_INVALID, "null argument");
+  if (c->stage_done % 3 != 0) return fail(c, VLB_ERR_STATE, "save between full steps only");
+  SaveHeader h{};
+  memcpy(h.magic, "VLBSAVE1", 8);
+  for (int a = 0; a < 2; ++a) {
+    h.model[3 * a] = c->model.kind[a];
+    h.model[3 * a + 1] = c->model.N[a];
+    h.model[3 * a + 2] = c->model.Q[a];
+  }
+  h.prec = c->prec;
+  h.n_inst = c->n_inst;
+  h.V = c->V;
+  h.total_cells = c->total_cells;
+  h.steps = c->steps;
+  std::vector<char> buf(size_t(c->total_cells) * 2 * c->V * c->esize);
+  vlb_status st = vlb_read_f(c, buf.data(), 0);
+  if (st != VLB_OK) return st;
+  FILE* fp = fopen(path, "wb");
+  if (!fp) return fail(c, VLB_ERR_INVALID, std::string("cannot open ") + path);
+  bool ok = fwrite(&h, sizeof(h), 1, fp) == 1;
+  for (int i = 0; i < c->n_inst && ok; ++i) ok = fwrite(&c->inst[i].n_cells, sizeof(int), 1, fp) == 1;
+  ok = ok && fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+  ok = (fclose(fp) == 0) && ok;
+  if (!ok) return fail(c, VLB_ERR_INVALID, "write failed");
+  return VLB_OK;
+}
+
+vlb_status vlb_load(vlb_ctx* c, const char* path) {
+  if (!c || !path) return fail(c, VLB_ERR_INVALID, "null argument");
+  FILE* fp = fopen(path, "rb");
+  if (!fp) return fail(c, VLB_ERR_INVALID, std::string("cannot open ") + path);
+  SaveHeader h{};
+  bool ok = fread(&h, sizeof(h), 1, fp) == 1 && memcmp(h.magic, "VLBSAVE1", 8) == 0;
+  for (int a = 0; a < 2 && ok; ++a)
+    ok = h.model[3 * a] == c->model.kind[a] && h.model[3 * a + 1] == c->model.N[a] &&
+         h.model[3 * a + 2] == c->model.Q[a];
+  ok = ok && h.prec == c->prec && h.n_inst == c->n_inst && h.V == c->V && h.total_cells == c->total_cells;
+  for (int i = 0; i < c->n_inst && ok; ++i) {
+    int nc = 0;
+    ok = fread(&nc, sizeof(int), 1, fp) == 1 && nc == c->inst[i].n_cells;
+  }
+  std::vector<char> buf(size_t(c->total_cells) * 2 * c->V * c->esize);
+  ok = ok && fread(buf.data(), 1, buf.size(), fp) == buf.size();
+  fclose(fp);
+  if (!ok) return fail(c, VLB_ERR_INVALID, "file does not match this context");
+  vlb_status st = vlb_set_f(c, buf.data(), 0);
+  if (st != VLB_OK) return st;
+  c->steps = h.steps;
+  return VLB_OK;
+}
+
+long long vlb_kernel_launches(const vlb_ctx* c) { return c ? c->launches : 0; }
+
+const char* vlb_last_error(const vlb_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+void vlb_destroy(vlb_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (int b = 0; b < 3; ++b) cudaFree(c->F[b]);
+  cudaFree(c->d_inst);
+  cudaFree(c->d_tiles);
+  cudaFree(c->d_geo);
+  cudaFree(c->d_nw);
+  cudaFree(c->d_err);
+  cudaFree(c->d_mom);
+  cudaFree(c->d_prev);
+  cudaFree(c->d_res);
+  delete c;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- residual kernel
+namespace vlb {
+
+// One block per instance: L2 norms of Eq. (msites_steady) with the weights R dR
+// (equidistant grid) or the rectangle rule in eta (stretched grid).
+__global__ void residual_kernel(const double* mom, const double* prev, const InstDesc* inst, const GeoCell* geo,
+                                double* res) {
+  __shared__ double red[3][32];
+  const InstDesc in = inst[blockIdx.x];
+  const double uw = in.u_in != 0.0 ? fabs(in.u_in) : 1.0;
+  double su = 0, sn = 0, sT = 0;
+  for (int s = threadIdx.x; s < in.n_cells; s += blockDim.x) {
+    const long long c = in.cell0 + s;
+    const double w = geo[c].wres;
+    const double* a = mom + 9 * c;
+    const double* b = prev + 9 * c;
+    const double du = (a[2] - b[2]) / uw, dn = a[0] / b[0] - 1.0, dT = a[3] / b[3] - 1.0;
+    su += w * du * du;
+    sn += w * dn * dn;
+    sT += w * dT * dT;
+  }
+  su = warp_sum<double>(su);
+  sn = warp_sum<double>(sn);
+  sT = warp_sum<double>(sT);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) red[0][warp] = su, red[1][warp] = sn, red[2][warp] = sT;
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double t = 0;
+    for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
+    res[3 * blockIdx.x + threadIdx.x] = sqrt(t);
+  }
+}
+
+cudaError_t launch_residual(const double* mom, const double* prev, const InstDesc* inst, const GeoCell* geo,
+                            int n_inst, double* res, cudaStream_t s) {
+  residual_kernel<<<n_inst, 256, 0, s>>>(mom, prev, inst, geo, res);
+  return cudaGetLastError();
+}
+
+}  // namespace vlb

@@ -1,0 +1,173 @@
+// Device-side building blocks shared by the libvlb kernels: descriptors,
+// WENO-5 interface values, equilibrium moment vectors, bounded mbarrier waits.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vlb {
+
+constexpr int MAXQ = 32;  // nodes per momentum axis
+constexpr int MAXN = 8;   // equilibrium expansion order + 1
+
+// Error bits set by kernels in a device word the host reads back.
+enum : unsigned { ERR_TIMEOUT = 1u, ERR_NONFINITE = 2u };
+
+struct InstDesc {
+  long long cell0;  // first global cell of the instance
+  int n_cells;
+  int tau_mode;     // vlb_tau_mode
+  double kn, dt;
+  double u_in, T_in, u_out, T_out;  // walls: tangential speed, temperature
+};
+
+struct TileDesc {
+  int inst;
+  int c0;  // first cell (within the instance) owned by the tile
+};
+
+// Per-cell chi-formulation factors (Eqs. flux_kom_R, flux_kom_eta):
+//   advection = p^R (cp * Flux_{s+1/2} - cm * Flux_{s-1/2}),
+//   cp = 2 R_{s+1/2} / (R_{s+1/2}^2 - R_{s-1/2}^2), cm = 2 R_{s-1/2} / (...),
+//   inv_rbar = 2 / (R_{s+1/2} + R_{s-1/2}) multiplies the inertial force.
+struct GeoCell {
+  double cp, cm, inv_rbar, wres;
+};
+
+// Momentum-space tables of the model (copied into shared memory by each CTA).
+struct ModelArgs {
+  int nq0, nq1, N0, N1, kind0, kind1;
+  double p0[MAXQ], p1[MAXQ];
+  double tab0[MAXQ * MAXN], tab1[MAXQ * MAXN];  // [k][s] with stride MAXN
+};
+
+template <typename real>
+struct KArgs {
+  real K0[MAXQ * MAXQ];   // d/dp^0 kernel on axis 0, [i][i'] stride MAXQ
+  real Kt1[MAXQ * MAXQ];  // d/dp^1 (p^1 .) kernel on axis 1, [j][j'] stride MAXQ
+};
+
+// ---------------------------------------------------------------- WENO-5
+// Interface value from the upwind-ordered stencil (a, b, c, d, e) =
+// (F_{s-2}, F_{s-1}, F_s, F_{s+1}, F_{s+2}) (Eqs. weno5_flux, weno5_omega,
+// weno_sigma); exact zeros of the smoothness indicators take Table IV's limits.
+// The weights delta_q / sigma_q^2, normalised, equal
+// delta_q prod_{r != q} sigma_r^2 / sum_q' (...); that division-light form is
+// used, with the indicators scaled by their maximum in single precision.
+template <typename real>
+__device__ __forceinline__ real weno5(real a, real b, real c, real d, real e) {
+  const real k1312 = real(13) / real(12), q = real(0.25);
+  const real d1 = real(0.1), d2 = real(0.6), d3 = real(0.3);
+  real t;
+  t = a - real(2) * b + c;
+  real u = a - real(4) * b + real(3) * c;
+  real s1 = k1312 * t * t + q * u * u;
+  t = b - real(2) * c + d;
+  u = b - d;
+  real s2 = k1312 * t * t + q * u * u;
+  t = c - real(2) * d + e;
+  u = real(3) * c - real(4) * d + e;
+  real s3 = k1312 * t * t + q * u * u;
+  const real F1 = a * (real(1) / real(3)) - b * (real(7) / real(6)) + c * (real(11) / real(6));
+  const real F2 = -b * (real(1) / real(6)) + c * (real(5) / real(6)) + d * (real(1) / real(3));
+  const real F3 = c * (real(1) / real(3)) + d * (real(5) / real(6)) - e * (real(1) / real(6));
+  real w1, w2, w3;
+  if (s1 == real(0) || s2 == real(0) || s3 == real(0)) {
+    w1 = s1 == real(0) ? d1 : real(0);
+    w2 = s2 == real(0) ? d2 : real(0);
+    w3 = s3 == real(0) ? d3 : real(0);
+  } else {
+    if (sizeof(real) == 4) {
+      const real r = real(1) / fmax(s1, fmax(s2, s3));
+      s1 *= r;
+      s2 *= r;
+      s3 *= r;
+    }
+    const real A = s1 * s1, B = s2 * s2, C = s3 * s3;
+    w1 = d1 * B * C;
+    w2 = d2 * A * C;
+    w3 = d3 * A * B;
+    if (!(w1 + w2 + w3 > real(0))) {  // products underflowed: weights delta_q (s_min / s_q)^2
+      const real m = fmin(s1, fmin(s2, s3));
+      const real r1 = m / s1, r2 = m / s2, r3 = m / s3;
+      w1 = d1 * r1 * r1;
+      w2 = d2 * r2 * r2;
+      w3 = d3 * r3 * r3;
+    }
+  }
+  return (w1 * F1 + w2 * F2 + w3 * F3) / (w1 + w2 + w3);
+}
+
+// ---------------------------------------------------------------- equilibrium
+// Moment vector m_s of the truncated equilibrium factor g_{a,k} = sum_s tab[k][s] m_s
+// (Sec. IV.D).  Full range (Eq. eq_gak_H): m_l = E[He_l(X)] / l!, X ~ N(u, T),
+// from l m_l = u m_{l-1} + (T - 1) m_{l-2} (generating function
+// exp(t u + t^2 (T - 1) / 2)).  Half range (Eq. eq_gak_hh): m_s are the
+// half-line moments int_0^inf x^s N(x; u, T) dx, from
+// M_0 = (1 + erf(u / sqrt(2T))) / 2, M_1 = u M_0 + T N(0; u, T),
+// M_s = u M_{s-1} + (s - 1) T M_{s-2} (integration by parts); the negative
+// semi-axis uses u -> -u.
+__device__ __forceinline__ void eq_moment_vector(int kind, int N, double u, double T, double* m) {
+  if (kind == 0) {
+    m[0] = 1.0;
+    if (N >= 1) m[1] = u;
+    for (int l = 2; l <= N; ++l) m[l] = (u * m[l - 1] + (T - 1.0) * m[l - 2]) / l;
+  } else {
+    const double g0 = exp(-u * u / (2.0 * T)) * rsqrt(2.0 * 3.14159265358979323846 * T);
+    m[0] = 0.5 * (1.0 + erf(u * rsqrt(2.0 * T)));
+    if (N >= 1) m[1] = u * m[0] + T * g0;
+    for (int s = 2; s <= N; ++s) m[s] = u * m[s - 1] + (s - 1) * T * m[s - 2];
+  }
+}
+
+__device__ __forceinline__ double relaxation_time(int mode, double kn, double n, double T) {
+  if (mode == 0) return kn / (n * T);
+  if (mode == 1) return 0.62665706865775012560 * kn / n;  // sqrt(pi / 8)
+  return kn / n;
+}
+
+// ---------------------------------------------------------------- bulk copy + mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One-dimensional bulk copy global -> shared completing on the mbarrier (16-byte
+// aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long max_polls) {
+  uint32_t done = 0;
+  for (unsigned long long it = 0; it < max_polls; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+template <typename real>
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace vlb

@@ -1,0 +1,173 @@
+// Kernels and launchers instantiated once per precision by vlb_f32.cu / vlb_f64.cu.
+#pragma once
+#include "vlb_launch.h"
+#include "vlb_stage.cuh"
+
+namespace vlb {
+
+// ---------------------------------------------------------------- stage dispatch
+template <typename real>
+struct StageCfg;
+template <>
+struct StageCfg<float> {
+  static constexpr int TC = 16;
+};
+template <>
+struct StageCfg<double> {
+  static constexpr int TC = 8;
+};
+
+template <typename real>
+int stage_tile_cells() {
+  return StageCfg<real>::TC;
+}
+
+template <typename real, int Q0, int Q1, int NT, bool EXACT>
+static cudaError_t launch_stage_inst(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k,
+                                     cudaStream_t s) {
+  constexpr int TC = StageCfg<real>::TC;
+  auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
+  const size_t smem = StageSmem<real, TC, NT>::bytes(a.Vp);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  kern<<<a.n_tiles, NT, smem, s>>>(a, m, k);
+  return cudaGetLastError();
+}
+
+template <typename real>
+size_t stage_smem_bytes(int nq0, int nq1, int Vp) {
+  constexpr int TC = StageCfg<real>::TC;
+  const int NT = (nq0 * nq1 <= 64) ? 64 : 256;
+  return NT == 64 ? StageSmem<real, TC, 64>::bytes(Vp) : StageSmem<real, TC, 256>::bytes(Vp);
+}
+
+template <typename real>
+cudaError_t launch_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, cudaStream_t s) {
+  if (m.nq0 == 16 && m.nq1 == 20) return launch_stage_inst<real, 16, 20, 256, true>(a, m, k, s);
+  if (m.nq0 == 16 && m.nq1 == 12) return launch_stage_inst<real, 16, 12, 256, true>(a, m, k, s);
+  if (m.nq0 == 8 && m.nq1 == 4) return launch_stage_inst<real, 8, 4, 64, true>(a, m, k, s);
+  if (m.nq0 * m.nq1 <= 64) return launch_stage_inst<real, MAXQ, MAXQ, 64, false>(a, m, k, s);
+  return launch_stage_inst<real, MAXQ, MAXQ, 256, false>(a, m, k, s);
+}
+
+// ---------------------------------------------------------------- equilibrium fill
+template <typename real>
+__global__ void init_equilibrium_kernel(real* F, long long cells, int Vp, const __grid_constant__ ModelArgs m,
+                                        double n0, double u0, double u1, double T0) {
+  __shared__ double g0[MAXQ], g1[MAXQ];
+  if (threadIdx.x < 2) {
+    const int ax = threadIdx.x;
+    double mp[MAXN], mm[MAXN];
+    const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0, nq = ax ? m.nq1 : m.nq0;
+    const double u = ax ? u1 : u0;
+    eq_moment_vector(kind, N, u, T0, mp);
+    eq_moment_vector(kind, N, -u, T0, mm);
+    for (int k = 0; k < nq; ++k) {
+      const double pk = ax ? m.p1[k] : m.p0[k];
+      const double* mv = (kind == 1 && pk < 0.0) ? mm : mp;
+      double g = 0;
+      for (int s = 0; s <= N; ++s) g += (ax ? m.tab1 : m.tab0)[k * MAXN + s] * mv[s];
+      (ax ? g1 : g0)[k] = g;
+    }
+  }
+  __syncthreads();
+  const int V = m.nq0 * m.nq1;
+  const long long total = cells * 2 * Vp;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total; x += (long long)gridDim.x * blockDim.x) {
+    const int v = int(x % Vp);
+    const int d = int((x / Vp) & 1);
+    real val = real(0);
+    if (v < V) {
+      const int i = v / m.nq1, j = v - i * m.nq1;
+      val = real(n0 * g0[i] * g1[j] * (d ? T0 : 1.0));
+    }
+    F[x] = val;
+  }
+}
+
+template <typename real>
+cudaError_t launch_init_equilibrium(real* F, long long cells, int Vp, const ModelArgs& m, double n0, double u0,
+                                    double u1, double T0, cudaStream_t s) {
+  const long long total = cells * 2 * Vp;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  init_equilibrium_kernel<real><<<int(blocks), 256, 0, s>>>(F, cells, Vp, m, n0, u0, u1, T0);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- moments (FP64), one warp per cell
+template <typename real>
+__global__ void moments_kernel(const real* F, long long cells, int Vp, const __grid_constant__ ModelArgs m,
+                               double* out) {
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int nq1 = m.nq1, V = m.nq0 * m.nq1;
+  for (long long c = warp0; c < cells; c += nwarps) {
+    const real* f = F + c * 2 * Vp;
+    double sn = 0, s0 = 0, s1 = 0;
+    for (int v = lane; v < V; v += 32) {
+      const int i = v / nq1, j = v - i * nq1;
+      const double f1 = f[v];
+      sn += f1;
+      s0 += m.p0[i] * f1;
+      s1 += m.p1[j] * f1;
+    }
+    sn = warp_sum<real>(sn);
+    s0 = warp_sum<real>(s0);
+    s1 = warp_sum<real>(s1);
+    const double n = sn, u0 = s0 / n, u1 = s1 / n;
+    double t00 = 0, t01 = 0, t11 = 0, tr2 = 0, q0 = 0, q1 = 0;
+    for (int v = lane; v < V; v += 32) {
+      const int i = v / nq1, j = v - i * nq1;
+      const double f1 = f[v], f2 = f[Vp + v];
+      const double x0 = m.p0[i] - u0, x1 = m.p1[j] - u1;
+      t00 += x0 * x0 * f1;
+      t01 += x0 * x1 * f1;
+      t11 += x1 * x1 * f1;
+      tr2 += f2;
+      const double e = 0.5 * (x0 * x0 + x1 * x1) * f1 + 0.5 * f2;
+      q0 += e * x0;
+      q1 += e * x1;
+    }
+    t00 = warp_sum<real>(t00);
+    t01 = warp_sum<real>(t01);
+    t11 = warp_sum<real>(t11);
+    tr2 = warp_sum<real>(tr2);
+    q0 = warp_sum<real>(q0);
+    q1 = warp_sum<real>(q1);
+    if (lane == 0) {
+      double* o = out + c * 9;
+      o[0] = n;
+      o[1] = u0;
+      o[2] = u1;
+      o[3] = (t00 + t11 + tr2) / (3.0 * n);
+      o[4] = t00;
+      o[5] = t01;
+      o[6] = t11;
+      o[7] = q0;
+      o[8] = q1;
+    }
+  }
+}
+
+template <typename real>
+cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelArgs& m, double* out, cudaStream_t s) {
+  long long blocks = (cells * 32 + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  moments_kernel<real><<<int(blocks), 256, 0, s>>>(F, cells, Vp, m, out);
+  return cudaGetLastError();
+}
+
+template int stage_tile_cells<VLB_REAL>();
+template size_t stage_smem_bytes<VLB_REAL>(int, int, int);
+template cudaError_t launch_stage<VLB_REAL>(const StageArgs<VLB_REAL>&, const ModelArgs&, const KArgs<VLB_REAL>&,
+                                            cudaStream_t);
+template cudaError_t launch_init_equilibrium<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, double, double,
+                                                       double, double, cudaStream_t);
+template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,
+                                              cudaStream_t);
+
+}  // namespace vlb

@@ -1,0 +1,233 @@
+"""Thin ctypes binding of libvlb (include/vlb.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays
+and torch tensors to pointers and status codes to exceptions.  Importing it
+without the compiled library raises immediately: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvlb.so")
+
+VLB_OK, VLB_ERR_INVALID, VLB_ERR_UNSUPPORTED, VLB_ERR_CUDA, VLB_ERR_NONFINITE, VLB_ERR_TIMEOUT, VLB_ERR_STATE = (
+    0, -1, -2, -3, -4, -5, -6)
+VLB_FULL, VLB_HALF = 0, 1
+VLB_FP64, VLB_FP32_BULK = 0, 1
+VLB_TAU_KN_OVER_NT, VLB_TAU_AOKI, VLB_TAU_KN_OVER_N = 0, 1, 2
+
+_STATUS = {VLB_ERR_INVALID: "INVALID", VLB_ERR_UNSUPPORTED: "UNSUPPORTED", VLB_ERR_CUDA: "CUDA",
+           VLB_ERR_NONFINITE: "NONFINITE", VLB_ERR_TIMEOUT: "TIMEOUT", VLB_ERR_STATE: "STATE"}
+
+
+class VlbError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libvlb {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vlb_model(C.Structure):
+    _fields_ = [("kind", C.c_int * 2), ("N", C.c_int * 2), ("Q", C.c_int * 2)]
+
+
+class vlb_couette_grid(C.Structure):
+    _fields_ = [("n_cells", C.c_int), ("r_in", C.c_double), ("r_out", C.c_double),
+                ("stretch_A", C.c_double), ("stretch_delta", C.c_double)]
+
+
+class vlb_wall(C.Structure):
+    _fields_ = [("u_tangential", C.c_double), ("T", C.c_double)]
+
+
+EXPORTS = {
+    "vlb_parse_model": (C.c_int, [C.c_char_p, C.POINTER(vlb_model)]),
+    "vlb_quadrature": (C.c_int, [C.POINTER(vlb_model), C.c_int, C.c_void_p, C.c_void_p]),
+    "vlb_axis_tables": (C.c_int, [C.POINTER(vlb_model), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vlb_axis_nodes": (C.c_int, [C.POINTER(vlb_model), C.c_int]),
+    "vlb_create_couette": (C.c_int, [C.POINTER(vlb_model), C.c_int, C.c_int, C.POINTER(vlb_couette_grid),
+                                     C.POINTER(vlb_wall), C.POINTER(vlb_wall), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_int), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vlb_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    "vlb_set_walls": (C.c_int, [C.c_void_p, C.POINTER(vlb_wall), C.POINTER(vlb_wall)]),
+    "vlb_init_equilibrium": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "vlb_set_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "vlb_read_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "vlb_stage": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "vlb_step": (C.c_int, [C.c_void_p, C.c_double, C.c_longlong]),
+    "vlb_set_dt": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "vlb_read_moments": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_int]),
+    "vlb_wall_density": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "vlb_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vlb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "vlb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "vlb_kernel_launches": (C.c_longlong, [C.c_void_p]),
+    "vlb_last_error": (C.c_char_p, [C.c_void_p]),
+    "vlb_destroy": (None, [C.c_void_p]),
+}
+
+
+def load_library(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"libvlb is not built ({path} missing): run __graft_entry__.build()")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(status, ctx=None):
+    if status != VLB_OK:
+        msg = _lib.vlb_last_error(ctx)
+        raise VlbError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Pointer of a C-contiguous numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _on_device(a):
+    return int(hasattr(a, "is_cuda") and a.is_cuda)
+
+
+def vlb_parse_model(text: str) -> vlb_model:
+    m = vlb_model()
+    _check(_lib.vlb_parse_model(text.encode(), C.byref(m)))
+    return m
+
+
+def vlb_axis_nodes(model: vlb_model, axis: int) -> int:
+    n = _lib.vlb_axis_nodes(C.byref(model), axis)
+    if n < 0:
+        _check(n)
+    return n
+
+
+def vlb_quadrature(model: vlb_model, axis: int):
+    nq = vlb_axis_nodes(model, axis)
+    p, w = np.zeros(nq), np.zeros(nq)
+    _check(_lib.vlb_quadrature(C.byref(model), axis, _ptr(p), _ptr(w)))
+    return p, w
+
+
+def vlb_axis_tables(model: vlb_model, axis: int):
+    nq = vlb_axis_nodes(model, axis)
+    p, w, K, Kt = np.zeros(nq), np.zeros(nq), np.zeros((nq, nq)), np.zeros((nq, nq))
+    _check(_lib.vlb_axis_tables(C.byref(model), axis, _ptr(p), _ptr(w), _ptr(K), _ptr(Kt)))
+    return p, w, K, Kt
+
+
+class Couette:
+    """A context of circular Couette instances (vlb_create_couette)."""
+
+    def __init__(self, model, precision, grids, inner, outer, kn, tau_mode, stream=None):
+        if isinstance(model, str):
+            model = vlb_parse_model(model)
+        self.model = model
+        self.precision = precision
+        n = len(grids)
+        G = (vlb_couette_grid * n)(*[vlb_couette_grid(g["n_cells"], g.get("r_in", 1.0), g.get("r_out", 2.0),
+                                                      g.get("stretch_A", 0.0), g.get("stretch_delta", 0.5))
+                                     for g in grids])
+        Wi = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in inner])
+        Wo = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in outer])
+        K = (C.c_double * n)(*kn)
+        T = (C.c_int * n)(*tau_mode)
+        h = C.c_void_p()
+        st = _lib.vlb_create_couette(C.byref(model), precision, n, G, Wi, Wo, K, T,
+                                     C.c_void_p(stream) if stream else None, C.byref(h))
+        _check(st)
+        self.h = h
+        self.n_inst = n
+        cells, nv, nb = C.c_longlong(), C.c_int(), C.c_longlong()
+        _check(_lib.vlb_sizes(h, C.byref(cells), C.byref(nv), C.byref(nb)), h)
+        self.total_cells, self.nvel, self.f_bytes = cells.value, nv.value, nb.value
+        self.nq = (vlb_axis_nodes(model, 0), vlb_axis_nodes(model, 1))
+        self.dtype = np.float64 if precision == VLB_FP64 else np.float32
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.vlb_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def f_shape(self):
+        return (self.total_cells, 2, self.nq[0], self.nq[1])
+
+    def set_walls(self, inner, outer):
+        n = self.n_inst
+        Wi = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in inner])
+        Wo = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in outer])
+        _check(_lib.vlb_set_walls(self.h, Wi, Wo), self.h)
+
+    def init_equilibrium(self, n0=1.0, u0=0.0, u1=0.0, T0=1.0):
+        _check(_lib.vlb_init_equilibrium(self.h, n0, u0, u1, T0), self.h)
+
+    def set_f(self, f):
+        if isinstance(f, np.ndarray):
+            f = np.ascontiguousarray(f, dtype=self.dtype)
+        _check(_lib.vlb_set_f(self.h, _ptr(f), _on_device(f)), self.h)
+
+    def read_f(self, out=None):
+        if out is None:
+            out = np.empty(self.f_shape(), dtype=self.dtype)
+        _check(_lib.vlb_read_f(self.h, _ptr(out), _on_device(out)), self.h)
+        return out
+
+    def stage(self, dt, k):
+        _check(_lib.vlb_stage(self.h, dt, k), self.h)
+
+    def step(self, dt, nsteps=1):
+        _check(_lib.vlb_step(self.h, dt, nsteps), self.h)
+
+    def set_dt(self, dt):
+        arr = (C.c_double * self.n_inst)(*dt)
+        _check(_lib.vlb_set_dt(self.h, arr), self.h)
+
+    def read_moments(self, full=False):
+        N = self.total_cells
+        n, u0, u1, T = (np.empty(N) for _ in range(4))
+        Tab = np.empty((N, 3)) if full else None
+        q = np.empty((N, 2)) if full else None
+        _check(_lib.vlb_read_moments(self.h, _ptr(n), _ptr(u0), _ptr(u1), _ptr(T), _ptr(Tab), _ptr(q), 0), self.h)
+        return (n, u0, u1, T, Tab, q) if full else (n, u0, u1, T)
+
+    def wall_density(self):
+        nw = np.empty((self.n_inst, 2))
+        _check(_lib.vlb_wall_density(self.h, _ptr(nw)), self.h)
+        return nw
+
+    def residual(self):
+        a, b, c = (np.empty(self.n_inst) for _ in range(3))
+        _check(_lib.vlb_residual(self.h, _ptr(a), _ptr(b), _ptr(c)), self.h)
+        return a, b, c
+
+    def save(self, path):
+        _check(_lib.vlb_save(self.h, path.encode()), self.h)
+
+    def load(self, path):
+        _check(_lib.vlb_load(self.h, path.encode()), self.h)
+
+    def kernel_launches(self):
+        return _lib.vlb_kernel_launches(self.h)

@@ -1,0 +1,67 @@
+"""CPU checks of libvlb: it loads, exports every function include/vlb.h declares,
+parses the paper's model notation, validates arguments before touching the GPU,
+and builds quadrature and force tables equal to the oracle's."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lbmodel as lb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+vlb = pytest.importorskip("paper_1708_05944_gb300.vlb", reason="libvlb not built")
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "vlb.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vlb_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol():
+    import ctypes
+    lib = ctypes.CDLL(vlb.LIB_PATH)
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(vlb.EXPORTS), set(names) ^ set(vlb.EXPORTS)
+
+
+def test_parse_model():
+    m = vlb.vlb_parse_model("HH(4;8)xH(4;20)")
+    assert list(m.kind) == [1, 0] and list(m.N) == [4, 4] and list(m.Q) == [8, 20]
+    m = vlb.vlb_parse_model("H(2;3) x HH(3;4)")
+    assert list(m.kind) == [0, 1] and list(m.Q) == [3, 4]
+    for bad in ("HH(4;4)xH(2;3)", "HH(4;8)", "X(1;2)xH(1;2)", "HH(4;8)xH(4;20)junk", "HH(-1;3)xH(1;2)"):
+        with pytest.raises(vlb.VlbError):
+            vlb.vlb_parse_model(bad)
+
+
+@pytest.mark.parametrize("spec", ["HH(4;8)xH(4;20)", "HH(3;4)xH(3;4)", "H(4;5)xH(2;3)", "HH(4;8)xH(4;12)",
+                                  "HH(4;16)xH(4;5)"])
+def test_tables_equal_oracle(spec):
+    m = vlb.vlb_parse_model(spec)
+    om = lb.Model(spec)
+    for a in (0, 1):
+        p, w, K, Kt = vlb.vlb_axis_tables(m, a)
+        np.testing.assert_allclose(p, om.p[a], rtol=1e-14, atol=1e-15)
+        np.testing.assert_allclose(w, om.w[a], rtol=1e-13, atol=0)
+        np.testing.assert_allclose(K, om.K[a], rtol=0, atol=1e-13 * np.abs(om.K[a]).max())
+        np.testing.assert_allclose(Kt, om.Kt[a], rtol=0, atol=1e-13 * np.abs(om.Kt[a]).max())
+
+
+def test_invalid_arguments_rejected_without_gpu():
+    bad = [
+        dict(grids=[dict(n_cells=2)]),
+        dict(grids=[dict(n_cells=8, r_in=2.0, r_out=1.0)]),
+        dict(kn=[0.0]),
+        dict(tau=[7]),
+        dict(model="HH(4;40)xH(4;20)"),
+    ]
+    for b in bad:
+        with pytest.raises(vlb.VlbError) as e:
+            vlb.Couette(b.get("model", "HH(3;4)xH(3;4)"), vlb.VLB_FP64, b.get("grids", [dict(n_cells=8)]),
+                        [(0.1, 1.0)], [(0.0, 1.0)], b.get("kn", [0.1]), b.get("tau", [1]))
+        assert e.value.status in (vlb.VLB_ERR_INVALID, vlb.VLB_ERR_UNSUPPORTED)
