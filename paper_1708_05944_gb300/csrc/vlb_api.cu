@@ -318,10 +318,12 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   m.kind1 = model->kind[1] == VLB_HALF ? 1 : 0;
   for (int k = 0; k < nq0; ++k) {
     m.p0[k] = c->ax[0].p[k];
+    m.w0[k] = c->ax[0].w[k];
     for (int s = 0; s <= m.N0; ++s) m.tab0[k * MAXN + s] = c->ax[0].eqtab[k * (m.N0 + 1) + s];
   }
   for (int k = 0; k < nq1; ++k) {
     m.p1[k] = c->ax[1].p[k];
+    m.w1[k] = c->ax[1].w[k];
     for (int s = 0; s <= m.N1; ++s) m.tab1[k * MAXN + s] = c->ax[1].eqtab[k * (m.N1 + 1) + s];
   }
   c->k32.reset(new KArgs<float>());

@@ -37,6 +37,7 @@ struct GeoCell {
 struct ModelArgs {
   int nq0, nq1, N0, N1, kind0, kind1;
   double p0[MAXQ], p1[MAXQ];
+  double w0[MAXQ], w1[MAXQ];  // quadrature weights
   double tab0[MAXQ * MAXN], tab1[MAXQ * MAXN];  // [k][s] with stride MAXN
 };
 
@@ -50,48 +51,62 @@ struct KArgs {
 // Interface value from the upwind-ordered stencil (a, b, c, d, e) =
 // (F_{s-2}, F_{s-1}, F_s, F_{s+1}, F_{s+2}) (Eqs. weno5_flux, weno5_omega,
 // weno_sigma); exact zeros of the smoothness indicators take Table IV's limits.
-// The weights delta_q / sigma_q^2, normalised, equal
-// delta_q prod_{r != q} sigma_r^2 / sum_q' (...); that division-light form is
-// used, with the indicators scaled by their maximum in single precision.
+// The normalised weights delta_q / sigma_q^2 do not change when the stencil is
+// multiplied by a constant, so the indicators are computed on the stencil
+// times sc (the caller passes 1 / (w_i w_j), which brings the weighted
+// populations of every velocity to order one and keeps sigma_q inside the
+// single-precision range).  The weights are evaluated in the division-light
+// form delta_q prod_{r != q} sigma_r^2 / sum_q' (...), with the indicators
+// scaled by their maximum in single precision.
 template <typename real>
-__device__ __forceinline__ real weno5(real a, real b, real c, real d, real e) {
+__device__ __forceinline__ real weno5(real a, real b, real c, real d, real e, real sc) {
   const real k1312 = real(13) / real(12), q = real(0.25);
   const real d1 = real(0.1), d2 = real(0.6), d3 = real(0.3);
-  real t;
-  t = a - real(2) * b + c;
-  real u = a - real(4) * b + real(3) * c;
-  real s1 = k1312 * t * t + q * u * u;
-  t = b - real(2) * c + d;
-  u = b - d;
-  real s2 = k1312 * t * t + q * u * u;
-  t = c - real(2) * d + e;
-  u = real(3) * c - real(4) * d + e;
-  real s3 = k1312 * t * t + q * u * u;
   const real F1 = a * (real(1) / real(3)) - b * (real(7) / real(6)) + c * (real(11) / real(6));
   const real F2 = -b * (real(1) / real(6)) + c * (real(5) / real(6)) + d * (real(1) / real(3));
   const real F3 = c * (real(1) / real(3)) + d * (real(5) / real(6)) - e * (real(1) / real(6));
+  const real A = a * sc, B = b * sc, Cc = c * sc, D = d * sc, E = e * sc;
+  real t = A - real(2) * B + Cc;
+  real u = A - real(4) * B + real(3) * Cc;
+  real s1 = k1312 * t * t + q * u * u;
+  t = B - real(2) * Cc + D;
+  u = B - D;
+  real s2 = k1312 * t * t + q * u * u;
+  t = Cc - real(2) * D + E;
+  u = real(3) * Cc - real(4) * D + E;
+  real s3 = k1312 * t * t + q * u * u;
   real w1, w2, w3;
   if (s1 == real(0) || s2 == real(0) || s3 == real(0)) {
     w1 = s1 == real(0) ? d1 : real(0);
     w2 = s2 == real(0) ? d2 : real(0);
     w3 = s3 == real(0) ? d3 : real(0);
   } else {
+    bool ideal = false;
     if (sizeof(real) == 4) {
-      const real r = real(1) / fmax(s1, fmax(s2, s3));
-      s1 *= r;
-      s2 *= r;
-      s3 *= r;
+      const real smax = fmax(s1, fmax(s2, s3));
+      if (smax < real(1e-30)) {
+        ideal = true;  // stencil uniform to ~1e-15 relative: every candidate gives the same value
+      } else {
+        const real r = real(1) / smax;
+        s1 *= r;
+        s2 *= r;
+        s3 *= r;
+      }
     }
-    const real A = s1 * s1, B = s2 * s2, C = s3 * s3;
-    w1 = d1 * B * C;
-    w2 = d2 * A * C;
-    w3 = d3 * A * B;
-    if (!(w1 + w2 + w3 > real(0))) {  // products underflowed: weights delta_q (s_min / s_q)^2
-      const real m = fmin(s1, fmin(s2, s3));
-      const real r1 = m / s1, r2 = m / s2, r3 = m / s3;
-      w1 = d1 * r1 * r1;
-      w2 = d2 * r2 * r2;
-      w3 = d3 * r3 * r3;
+    if (ideal) {
+      w1 = d1, w2 = d2, w3 = d3;
+    } else {
+      const real P = s1 * s1, Qv = s2 * s2, R = s3 * s3;
+      w1 = d1 * Qv * R;
+      w2 = d2 * P * R;
+      w3 = d3 * P * Qv;
+      if (!(w1 + w2 + w3 > real(0))) {  // products underflowed: weights delta_q (s_min / s_q)^2
+        const real m = fmin(s1, fmin(s2, s3));
+        const real r1 = m / s1, r2 = m / s2, r3 = m / s3;
+        w1 = d1 * r1 * r1;
+        w2 = d2 * r2 * r2;
+        w3 = d3 * r3 * r3;
+      }
     }
   }
   return (w1 * F1 + w2 * F2 + w3 * F3) / (w1 + w2 + w3);

@@ -43,8 +43,8 @@ struct StageSmem {
   // moment vectors (TC*4*MAXN), reduction (NW*4), wall scratch (2*MAXQ + 16)
   static constexpr size_t n_dbl = 2 * MAXQ + 2 * MAXQ * MAXN + 4 * TC + TC * 4 * MAXN + NW * 4 + 2 * MAXQ + 16;
   __host__ __device__ static size_t real_off(int Vp) { return dbl_off(Vp) + n_dbl * sizeof(double); }
-  // reals: p0, p1 (MAXQ each), n g_R and g_phi (TC*MAXQ each), T, 1/tau, cp, cm, 1/Rbar (TC each)
-  static constexpr size_t n_real = 2 * MAXQ + 2 * TC * MAXQ + 5 * TC;
+  // reals: p0, p1, 1/w0, 1/w1 (MAXQ each), n g_R and g_phi (TC*MAXQ each), T, 1/tau, cp, cm, 1/Rbar (TC each)
+  static constexpr size_t n_real = 4 * MAXQ + 2 * TC * MAXQ + 5 * TC;
   __host__ __device__ static size_t bytes(int Vp) { return real_off(Vp) + n_real * sizeof(real); }
 };
 
@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   real* rp = reinterpret_cast<real*>(smem + L::real_off(Vp));
   real* p0r = rp;
   real* p1r = p0r + MAXQ;
-  real* gRn = p1r + MAXQ;  // [t][i] n_t g_{R,i}
+  real* iw0 = p1r + MAXQ;  // 1 / w_i
+  real* iw1 = iw0 + MAXQ;  // 1 / w_j
+  real* gRn = iw1 + MAXQ;  // [t][i] n_t g_{R,i}
   real* gP = gRn + TC * MAXQ;
   real* cTr = gP + TC * MAXQ;
   real* cItau = cTr + TC;
@@ -112,6 +114,8 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     p1d[x] = m.p1[x];
     p0r[x] = real(m.p0[x]);
     p1r[x] = real(m.p1[x]);
+    iw0[x] = m.w0[x] > 0.0 ? real(1.0 / m.w0[x]) : real(0);
+    iw1[x] = m.w1[x] > 0.0 ? real(1.0 / m.w1[x]) : real(0);
   }
   for (int x = tid; x < MAXQ * MAXN; x += NT) {
     tab0[x] = m.tab0[x];
@@ -224,14 +228,14 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     const int dir = wall == 0 ? 1 : -1;                // towards the interior
     double num = 0;
     for (int v = tid; v < V; v += NT) {
-      const int i = v / nq1;
+      const int i = v / nq1, j = v - i * nq1;
       if (!(sgn * p0d[i] < 0.0)) continue;
       const real F0 = tile[size_t(sA) * row + v];
       const real F1 = tile[size_t(sA + dir) * row + v];
       const real F2 = tile[size_t(sA + 2 * dir) * row + v];
       const real G0 = real(3) * F0 - real(3) * F1 + F2;
       const real G1 = real(6) * F0 - real(8) * F1 + real(3) * F2;
-      num += double(weno5<real>(F2, F1, F0, G0, G1)) * p0d[i];
+      num += double(weno5<real>(F2, F1, F0, G0, G1, iw0[i] * iw1[j])) * p0d[i];
     }
     num = warp_sum<real>(num);
     if (lane == 0) red[warp] = num;
@@ -319,14 +323,15 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     const int i = v / nq1, j = v - i * nq1;
     const real pr = p0r[i];
     const bool up = pr >= real(0);
+    const real sc = iw0[i] * iw1[j];
     const real* S = tile + d * Vp + v;
     real w0 = S[0], w1 = S[row], w2 = S[2 * row], w3 = S[3 * row], w4 = S[4 * row], w5 = S[5 * row];
-    real fm = up ? weno5<real>(w0, w1, w2, w3, w4) : weno5<real>(w5, w4, w3, w2, w1);
+    real fm = up ? weno5<real>(w0, w1, w2, w3, w4, sc) : weno5<real>(w5, w4, w3, w2, w1, sc);
     real* out = a.Fout + size_t(in.cell0 + c0) * row + d * Vp + v;
     const real* Fl = a.Fl + size_t(in.cell0 + c0) * row + d * Vp + v;
     for (int t = 0; t < TCe; ++t) {
       const real w6 = S[size_t(t + 6) * row];
-      const real fp = up ? weno5<real>(w1, w2, w3, w4, w5) : weno5<real>(w6, w5, w4, w3, w2);
+      const real fp = up ? weno5<real>(w1, w2, w3, w4, w5, sc) : weno5<real>(w6, w5, w4, w3, w2, sc);
       const real adv = pr * (ccp[t] * fp - ccm[t] * fm);
       const real feq = gRn[t * MAXQ + i] * gP[t * MAXQ + j] * (d ? cTr[t] : real(1));
       const real Lv = -adv + lbuf[size_t(t * 2 + d) * Vp + v] * cIR[t] - (w3 - feq) * cItau[t];
