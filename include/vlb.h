@@ -166,6 +166,22 @@ vlb_status vlb_residual(vlb_ctx* ctx, double* l2_u, double* l2_n, double* l2_T);
 vlb_status vlb_save(vlb_ctx* ctx, const char* path);
 vlb_status vlb_load(vlb_ctx* ctx, const char* path);
 
+/* Launch shapes of the fused stage kernel available for this context (cells
+ * per tile and threads per CTA), written to tc[] and nt[] (up to max
+ * entries, NULL allowed); returns their number (negative vlb_status on error).
+ * Every shape computes the same stage; they differ in occupancy and load balance. */
+int vlb_variants(const vlb_ctx* ctx, int* tc, int* nt, int max);
+
+/* Select a launch shape by index (0 = default). */
+vlb_status vlb_set_variant(vlb_ctx* ctx, int variant);
+
+/* Time every launch shape on this context's own workload (reps launches of
+ * stage 1 each, with time step dt as in vlb_stage, CUDA events on the
+ * context stream; stage 1 only writes scratch, so the distribution is
+ * unchanged), keep the fastest and report its index and mean time per launch
+ * (either pointer may be NULL). */
+vlb_status vlb_autotune(vlb_ctx* ctx, double dt, int reps, int* chosen, double* best_ms);
+
 /* Number of kernels the last vlb_step / vlb_stage call launched. */
 long long vlb_kernel_launches(const vlb_ctx* ctx);
 

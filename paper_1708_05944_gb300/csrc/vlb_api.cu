@@ -33,6 +33,9 @@ struct vlb_ctx {
   std::unique_ptr<KArgs<float>> k32;
   std::unique_ptr<KArgs<double>> k64;
   void* F[3] = {nullptr, nullptr, nullptr};
+  StageVariant variants[8];
+  int n_variants = 0;
+  int variant = 0;
   int cur = 0;   // buffer holding F_l
   int last = 0;  // buffer written by the most recent stage
   int stage_done = 0;
@@ -45,6 +48,7 @@ struct vlb_ctx {
   double* d_prev = nullptr;
   double* d_res = nullptr;
   bool have_prev = false;
+  size_t tile_cap = 0;
   long long launches = 0;
   long long steps = 0;
   std::string err;
@@ -122,6 +126,14 @@ void couette_geometry(const vlb_couette_grid& g, GeoCell* out) {
   }
 }
 
+// tiles of the current variant's size over every instance
+void build_tiles(vlb_ctx* c) {
+  const int TC = c->variants[c->variant].tc;
+  c->tiles.clear();
+  for (int i = 0; i < c->n_inst; ++i)
+    for (int c0 = 0; c0 < c->inst[i].n_cells; c0 += TC) c->tiles.push_back(TileDesc{i, c0});
+}
+
 template <typename real>
 vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   StageArgs<real> a{};
@@ -145,7 +157,7 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   a.max_polls = 1ull << 26;
   const KArgs<real>* kk;
   if constexpr (sizeof(real) == 4) kk = c->k32.get(); else kk = c->k64.get();
-  cudaError_t e = launch_stage<real>(a, c->margs, *kk, c->stream);
+  cudaError_t e = launch_stage<real>(c->variants[c->variant], a, c->margs, *kk, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
   c->launches += 1;
   return VLB_OK;
@@ -305,9 +317,16 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   c->V = nq0 * nq1;
   c->Vp = (c->V + 3) / 4 * 4;
   c->esize = prec == VLB_FP64 ? 8 : 4;
-  const size_t smem = prec == VLB_FP64 ? stage_smem_bytes<double>(nq0, nq1, c->Vp)
-                                       : stage_smem_bytes<float>(nq0, nq1, c->Vp);
-  if (smem > 227 * 1024) return fail(nullptr, VLB_ERR_UNSUPPORTED, "velocity set too large for one tile");
+  {
+    StageVariant all[8];
+    const int n = prec == VLB_FP64 ? stage_variants<double>(nq0, nq1, all) : stage_variants<float>(nq0, nq1, all);
+    for (int i = 0; i < n; ++i) {
+      const size_t smem = prec == VLB_FP64 ? stage_smem_bytes<double>(all[i], c->Vp)
+                                           : stage_smem_bytes<float>(all[i], c->Vp);
+      if (smem > 0 && smem <= 227 * 1024) c->variants[c->n_variants++] = all[i];
+    }
+    if (c->n_variants == 0) return fail(nullptr, VLB_ERR_UNSUPPORTED, "velocity set too large for one tile");
+  }
 
   ModelArgs& m = c->margs;
   m.nq0 = nq0;
@@ -341,7 +360,6 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
       c->k32->Kt1[j * MAXQ + jp] = float(c->ax[1].Kt[j * nq1 + jp]);
     }
 
-  const int TC = prec == VLB_FP64 ? stage_tile_cells<double>() : stage_tile_cells<float>();
   long long cell0 = 0;
   for (int i = 0; i < n_inst; ++i) {
     InstDesc d{};
@@ -356,10 +374,10 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     d.T_out = outer[i].T;
     c->inst.push_back(d);
     c->grids.push_back(grids[i]);
-    for (int c0 = 0; c0 < d.n_cells; c0 += TC) c->tiles.push_back(TileDesc{i, c0});
     cell0 += d.n_cells;
   }
   c->total_cells = cell0;
+  build_tiles(c.get());
   c->geo.resize(cell0);
   for (int i = 0; i < n_inst; ++i) couette_geometry(grids[i], c->geo.data() + c->inst[i].cell0);
 
@@ -370,7 +388,17 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     VLB_CUDA(cp, cudaMemsetAsync(c->F[b], 0, fbytes, c->stream));
   }
   VLB_CUDA(cp, cudaMalloc(&c->d_inst, sizeof(InstDesc) * n_inst));
-  VLB_CUDA(cp, cudaMalloc(&c->d_tiles, sizeof(TileDesc) * c->tiles.size()));
+  // room for the tile list of the smallest tile size among the variants
+  {
+    size_t most = 0;
+    for (int v = 0; v < c->n_variants; ++v) {
+      size_t cnt = 0;
+      for (int i = 0; i < n_inst; ++i) cnt += (grids[i].n_cells + c->variants[v].tc - 1) / c->variants[v].tc;
+      most = cnt > most ? cnt : most;
+    }
+    c->tile_cap = most;
+    VLB_CUDA(cp, cudaMalloc(&c->d_tiles, sizeof(TileDesc) * most));
+  }
   VLB_CUDA(cp, cudaMalloc(&c->d_geo, sizeof(GeoCell) * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_nw, sizeof(double) * 2 * n_inst));
   VLB_CUDA(cp, cudaMalloc(&c->d_err, sizeof(unsigned)));
@@ -632,6 +660,65 @@ vlb_status vlb_load(vlb_ctx* c, const char* path) {
   vlb_status st = vlb_set_f(c, buf.data(), 0);
   if (st != VLB_OK) return st;
   c->steps = h.steps;
+  return VLB_OK;
+}
+
+int vlb_variants(const vlb_ctx* c, int* tc, int* nt, int max) {
+  if (!c) return VLB_ERR_INVALID;
+  for (int v = 0; v < c->n_variants && v < max; ++v) {
+    if (tc) tc[v] = c->variants[v].tc;
+    if (nt) nt[v] = c->variants[v].nt;
+  }
+  return c->n_variants;
+}
+
+vlb_status vlb_set_variant(vlb_ctx* c, int v) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (v < 0 || v >= c->n_variants) return fail(c, VLB_ERR_INVALID, "no such launch shape");
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->variant = v;
+  build_tiles(c);
+  VLB_CUDA(c, cudaMemcpyAsync(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * c->tiles.size(),
+                              cudaMemcpyHostToDevice, c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_autotune(vlb_ctx* c, double dt, int reps, int* chosen, double* best_ms) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (reps < 1) return fail(c, VLB_ERR_INVALID, "reps must be >= 1");
+  if (c->stage_done % 3 != 0) return fail(c, VLB_ERR_STATE, "a partial RK3 step is pending");
+  vlb_status st = apply_dt(c, dt);
+  if (st != VLB_OK) return st;
+  cudaEvent_t e0, e1;
+  VLB_CUDA(c, cudaEventCreate(&e0));
+  VLB_CUDA(c, cudaEventCreate(&e1));
+  int best = 0;
+  float best_t = 1e30f;
+  const int keep_last = c->last;
+  for (int v = 0; v < c->n_variants; ++v) {
+    st = vlb_set_variant(c, v);
+    if (st != VLB_OK) break;
+    // stage 1 only reads F_l and writes the scratch buffer F^(1): the state is unchanged
+    for (int w = 0; w < 2 && st == VLB_OK; ++w) st = run_stage(c, 1);
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < reps && st == VLB_OK; ++r) st = run_stage(c, 1);
+    cudaEventRecord(e1, c->stream);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= reps;
+    if (ms < best_t) best_t = ms, best = v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->stage_done = 0;
+  c->last = keep_last;
+  if (st != VLB_OK) return st;
+  st = vlb_set_variant(c, best);
+  if (st != VLB_OK) return st;
+  if (chosen) *chosen = best;
+  if (best_ms) *best_ms = best_t;
   return VLB_OK;
 }
 

@@ -47,6 +47,16 @@ struct KArgs {
   real Kt1[MAXQ * MAXQ];  // d/dp^1 (p^1 .) kernel on axis 1, [j][j'] stride MAXQ
 };
 
+// Type-exact helpers: float arguments must not be promoted to double (the
+// FP64 pipe of GB300 runs at a small fraction of the FP32 rate).
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+// x / y; single precision uses the fast divide (2 ulp), valid for |y| < 2^126.
+__device__ __forceinline__ float vdiv(float x, float y) { return __fdividef(x, y); }
+__device__ __forceinline__ double vdiv(double x, double y) { return x / y; }
+
 // ---------------------------------------------------------------- WENO-5
 // Interface value from the upwind-ordered stencil (a, b, c, d, e) =
 // (F_{s-2}, F_{s-1}, F_s, F_{s+1}, F_{s+2}) (Eqs. weno5_flux, weno5_omega,
@@ -83,11 +93,11 @@ __device__ __forceinline__ real weno5(real a, real b, real c, real d, real e, re
   } else {
     bool ideal = false;
     if (sizeof(real) == 4) {
-      const real smax = fmax(s1, fmax(s2, s3));
+      const real smax = vmax(s1, vmax(s2, s3));
       if (smax < real(1e-30)) {
         ideal = true;  // stencil uniform to ~1e-15 relative: every candidate gives the same value
       } else {
-        const real r = real(1) / smax;
+        const real r = vdiv(real(1), smax);
         s1 *= r;
         s2 *= r;
         s3 *= r;
@@ -101,15 +111,15 @@ __device__ __forceinline__ real weno5(real a, real b, real c, real d, real e, re
       w2 = d2 * P * R;
       w3 = d3 * P * Qv;
       if (!(w1 + w2 + w3 > real(0))) {  // products underflowed: weights delta_q (s_min / s_q)^2
-        const real m = fmin(s1, fmin(s2, s3));
-        const real r1 = m / s1, r2 = m / s2, r3 = m / s3;
+        const real m = vmin(s1, vmin(s2, s3));
+        const real r1 = vdiv(m, s1), r2 = vdiv(m, s2), r3 = vdiv(m, s3);
         w1 = d1 * r1 * r1;
         w2 = d2 * r2 * r2;
         w3 = d3 * r3 * r3;
       }
     }
   }
-  return (w1 * F1 + w2 * F2 + w3 * F3) / (w1 + w2 + w3);
+  return vdiv(w1 * F1 + w2 * F2 + w3 * F3, w1 + w2 + w3);
 }
 
 // ---------------------------------------------------------------- equilibrium

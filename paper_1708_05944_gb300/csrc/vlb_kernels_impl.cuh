@@ -6,26 +6,12 @@
 namespace vlb {
 
 // ---------------------------------------------------------------- stage dispatch
-template <typename real>
-struct StageCfg;
-template <>
-struct StageCfg<float> {
-  static constexpr int TC = 16;
-};
-template <>
-struct StageCfg<double> {
-  static constexpr int TC = 8;
-};
-
-template <typename real>
-int stage_tile_cells() {
-  return StageCfg<real>::TC;
-}
-
-template <typename real, int Q0, int Q1, int NT, bool EXACT>
-static cudaError_t launch_stage_inst(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k,
-                                     cudaStream_t s) {
-  constexpr int TC = StageCfg<real>::TC;
+// Launch shapes ("variants") of the stage kernel: cells per tile TC and threads
+// per CTA NT.  Exact instantiations exist for the node counts of the
+// configured models; anything else takes the generic kernel.  The autotuner
+// (vlb_autotune) times the variants of a context's shape and keeps the best.
+template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
+static cudaError_t go_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, cudaStream_t s) {
   auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
   const size_t smem = StageSmem<real, TC, NT>::bytes(a.Vp);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -34,20 +20,88 @@ static cudaError_t launch_stage_inst(const StageArgs<real>& a, const ModelArgs& 
   return cudaGetLastError();
 }
 
+enum Shape { SH_16x20 = 0, SH_16x12 = 1, SH_8x4 = 2, SH_SMALL = 3, SH_GENERIC = 4 };
+
+static int shape_of(int nq0, int nq1) {
+  if (nq0 == 16 && nq1 == 20) return SH_16x20;
+  if (nq0 == 16 && nq1 == 12) return SH_16x12;
+  if (nq0 == 8 && nq1 == 4) return SH_8x4;
+  if (nq0 * nq1 <= 64) return SH_SMALL;
+  return SH_GENERIC;
+}
+
+// variant tables per precision and shape: {TC, NT}
 template <typename real>
-size_t stage_smem_bytes(int nq0, int nq1, int Vp) {
-  constexpr int TC = StageCfg<real>::TC;
-  const int NT = (nq0 * nq1 <= 64) ? 64 : 256;
-  return NT == 64 ? StageSmem<real, TC, 64>::bytes(Vp) : StageSmem<real, TC, 256>::bytes(Vp);
+struct VariantTable;
+template <>
+struct VariantTable<float> {
+  static constexpr StageVariant v16x20[] = {{16, 256}, {8, 256}, {16, 512}, {8, 128}};
+  static constexpr StageVariant v16x12[] = {{16, 256}, {8, 256}, {16, 384}};
+  static constexpr StageVariant v8x4[] = {{16, 64}, {8, 64}};
+  static constexpr StageVariant vsmall[] = {{16, 64}};
+  static constexpr StageVariant vgen[] = {{16, 256}};
+};
+template <>
+struct VariantTable<double> {
+  static constexpr StageVariant v16x20[] = {{8, 256}, {4, 256}, {8, 128}, {4, 128}};
+  static constexpr StageVariant v16x12[] = {{8, 256}, {4, 256}, {8, 384}};
+  static constexpr StageVariant v8x4[] = {{8, 64}, {16, 64}};
+  static constexpr StageVariant vsmall[] = {{8, 64}};
+  static constexpr StageVariant vgen[] = {{8, 256}};
+};
+
+template <typename real>
+int stage_variants(int nq0, int nq1, StageVariant* out) {
+  using T = VariantTable<real>;
+  const StageVariant* v;
+  int n;
+  switch (shape_of(nq0, nq1)) {
+    case SH_16x20: v = T::v16x20, n = int(sizeof(T::v16x20) / sizeof(StageVariant)); break;
+    case SH_16x12: v = T::v16x12, n = int(sizeof(T::v16x12) / sizeof(StageVariant)); break;
+    case SH_8x4: v = T::v8x4, n = int(sizeof(T::v8x4) / sizeof(StageVariant)); break;
+    case SH_SMALL: v = T::vsmall, n = 1; break;
+    default: v = T::vgen, n = 1; break;
+  }
+  for (int i = 0; i < n; ++i) out[i] = v[i];
+  return n;
 }
 
 template <typename real>
-cudaError_t launch_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, cudaStream_t s) {
-  if (m.nq0 == 16 && m.nq1 == 20) return launch_stage_inst<real, 16, 20, 256, true>(a, m, k, s);
-  if (m.nq0 == 16 && m.nq1 == 12) return launch_stage_inst<real, 16, 12, 256, true>(a, m, k, s);
-  if (m.nq0 == 8 && m.nq1 == 4) return launch_stage_inst<real, 8, 4, 64, true>(a, m, k, s);
-  if (m.nq0 * m.nq1 <= 64) return launch_stage_inst<real, MAXQ, MAXQ, 64, false>(a, m, k, s);
-  return launch_stage_inst<real, MAXQ, MAXQ, 256, false>(a, m, k, s);
+size_t stage_smem_bytes(StageVariant v, int Vp) {
+#define VLB_SMEM_CASE(TC_, NT_) \
+  if (v.tc == TC_ && v.nt == NT_) return StageSmem<real, TC_, NT_>::bytes(Vp);
+  VLB_SMEM_CASE(16, 256) VLB_SMEM_CASE(8, 256) VLB_SMEM_CASE(16, 512) VLB_SMEM_CASE(8, 128)
+  VLB_SMEM_CASE(16, 384) VLB_SMEM_CASE(16, 64) VLB_SMEM_CASE(8, 64) VLB_SMEM_CASE(4, 256)
+  VLB_SMEM_CASE(4, 128) VLB_SMEM_CASE(8, 384)
+#undef VLB_SMEM_CASE
+  return 0;
+}
+
+template <typename real>
+cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k,
+                         cudaStream_t s) {
+  const int sh = shape_of(m.nq0, m.nq1);
+#define VLB_CASE(SH, TC_, NT_, q0, q1, ex) \
+  if (sh == SH && v.tc == TC_ && v.nt == NT_) return go_stage<real, TC_, NT_, q0, q1, ex>(a, m, k, s);
+  if constexpr (sizeof(real) == 4) {
+    VLB_CASE(SH_16x20, 16, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
+    VLB_CASE(SH_16x20, 16, 512, 16, 20, true) VLB_CASE(SH_16x20, 8, 128, 16, 20, true)
+    VLB_CASE(SH_16x12, 16, 256, 16, 12, true) VLB_CASE(SH_16x12, 8, 256, 16, 12, true)
+    VLB_CASE(SH_16x12, 16, 384, 16, 12, true)
+    VLB_CASE(SH_8x4, 16, 64, 8, 4, true) VLB_CASE(SH_8x4, 8, 64, 8, 4, true)
+    VLB_CASE(SH_SMALL, 16, 64, MAXQ, MAXQ, false)
+    VLB_CASE(SH_GENERIC, 16, 256, MAXQ, MAXQ, false)
+  } else {
+    VLB_CASE(SH_16x20, 8, 256, 16, 20, true) VLB_CASE(SH_16x20, 4, 256, 16, 20, true)
+    VLB_CASE(SH_16x20, 8, 128, 16, 20, true) VLB_CASE(SH_16x20, 4, 128, 16, 20, true)
+    VLB_CASE(SH_16x12, 8, 256, 16, 12, true) VLB_CASE(SH_16x12, 4, 256, 16, 12, true)
+    VLB_CASE(SH_16x12, 8, 384, 16, 12, true)
+    VLB_CASE(SH_8x4, 8, 64, 8, 4, true) VLB_CASE(SH_8x4, 16, 64, 8, 4, true)
+    VLB_CASE(SH_SMALL, 8, 64, MAXQ, MAXQ, false)
+    VLB_CASE(SH_GENERIC, 8, 256, MAXQ, MAXQ, false)
+  }
+#undef VLB_CASE
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------- equilibrium fill
@@ -161,10 +215,10 @@ cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelAr
   return cudaGetLastError();
 }
 
-template int stage_tile_cells<VLB_REAL>();
-template size_t stage_smem_bytes<VLB_REAL>(int, int, int);
-template cudaError_t launch_stage<VLB_REAL>(const StageArgs<VLB_REAL>&, const ModelArgs&, const KArgs<VLB_REAL>&,
-                                            cudaStream_t);
+template int stage_variants<VLB_REAL>(int, int, StageVariant*);
+template size_t stage_smem_bytes<VLB_REAL>(StageVariant, int);
+template cudaError_t launch_stage<VLB_REAL>(StageVariant, const StageArgs<VLB_REAL>&, const ModelArgs&,
+                                            const KArgs<VLB_REAL>&, cudaStream_t);
 template cudaError_t launch_init_equilibrium<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, double, double,
                                                        double, double, cudaStream_t);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,

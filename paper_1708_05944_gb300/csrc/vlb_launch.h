@@ -9,17 +9,23 @@ namespace vlb {
 template <typename real>
 struct StageArgs;
 
-// Tile size (cells per CTA) used by the stage kernel for a precision.
-template <typename real>
-int stage_tile_cells();
+// Launch shape of the stage kernel: cells per tile and threads per CTA.
+struct StageVariant {
+  int tc, nt;
+};
 
-// Dynamic shared memory the stage kernel needs for a per-field stride Vp.
+// The launch shapes available for a model shape (at most 8); the first is the default.
 template <typename real>
-size_t stage_smem_bytes(int nq0, int nq1, int Vp);
+int stage_variants(int nq0, int nq1, StageVariant* out);
 
-// Launch one RK3 stage over a.n_tiles tiles.
+// Dynamic shared memory the stage kernel needs for a variant and per-field stride Vp.
 template <typename real>
-cudaError_t launch_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, cudaStream_t s);
+size_t stage_smem_bytes(StageVariant v, int Vp);
+
+// Launch one RK3 stage over a.n_tiles tiles of v.tc cells.
+template <typename real>
+cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k,
+                         cudaStream_t s);
 
 // f_eq(n0, (u0, u1), T0) in every cell.
 template <typename real>

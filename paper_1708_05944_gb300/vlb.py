@@ -64,6 +64,9 @@ EXPORTS = {
     "vlb_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vlb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "vlb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "vlb_variants": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "vlb_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
+    "vlb_autotune": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "vlb_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "vlb_last_error": (C.c_char_p, [C.c_void_p]),
     "vlb_destroy": (None, [C.c_void_p]),
@@ -228,6 +231,21 @@ class Couette:
 
     def load(self, path):
         _check(_lib.vlb_load(self.h, path.encode()), self.h)
+
+    def variants(self):
+        tc, nt = np.zeros(8, dtype=np.int32), np.zeros(8, dtype=np.int32)
+        n = _lib.vlb_variants(self.h, _ptr(tc), _ptr(nt), 8)
+        if n < 0:
+            _check(n, self.h)
+        return [(int(tc[i]), int(nt[i])) for i in range(n)]
+
+    def set_variant(self, v):
+        _check(_lib.vlb_set_variant(self.h, v), self.h)
+
+    def autotune(self, dt, reps=20):
+        ch, ms = C.c_int(), C.c_double()
+        _check(_lib.vlb_autotune(self.h, dt, reps, C.byref(ch), C.byref(ms)), self.h)
+        return ch.value, ms.value
 
     def kernel_launches(self):
         return _lib.vlb_kernel_launches(self.h)

@@ -149,3 +149,39 @@ def test_kernel_launch_count():
     c.step(1e-3, 7)
     assert c.kernel_launches() == 21
     c.close()
+
+
+@pytest.mark.parametrize("prec", [vlb.VLB_FP64, vlb.VLB_FP32_BULK])
+def test_every_launch_shape_matches_oracle(prec):
+    # 37 cells: a remainder tile for every tile size; two instances
+    cases = [make_case(CONFIG2, 37, u_in=0.2, kn=0.05, seed=9), make_case(CONFIG2, 21, u_in=0.1, kn=2.0, seed=10)]
+    c = ctx_for(CONFIG2, prec, [g for _, _, g in cases], [(0.2, 1.0), (0.1, 1.0)], [(0.0, 1.0)] * 2, [0.05, 2.0],
+                [1, 1])
+    dtype = np.float64 if prec == vlb.VLB_FP64 else np.float32
+    f0 = np.concatenate([to_lib(F0) for _, F0, _ in cases]).astype(dtype)
+    refs = []
+    for o, F0, _ in cases:
+        F = F0
+        for _ in range(2):
+            F = o.step(F, 1e-4)
+        refs.append(F)
+    shapes = c.variants()
+    assert len(shapes) >= 1
+    for v in range(len(shapes)):
+        c.set_variant(v)
+        c.set_f(f0)
+        c.step(1e-4, 2)
+        got = c.read_f()
+        off = 0
+        for (o, F0, g), ref in zip(cases, refs):
+            n = g["n_cells"]
+            if prec == vlb.VLB_FP64:
+                assert rel_err(to_oracle(got[off:off + n]), ref) < 1e-12, shapes[v]
+            else:
+                c_n = to_oracle(got[off:off + n]).astype(np.float64)
+                on = o.m.moments(ref)[0]
+                assert np.abs(o.m.moments(c_n)[0] / on - 1).max() < 1e-5, shapes[v]
+            off += n
+    best, ms = c.autotune(1e-4, reps=5)
+    assert 0 <= best < len(shapes) and ms > 0
+    c.close()
