@@ -35,7 +35,7 @@ template <typename real>
 struct VariantTable;
 template <>
 struct VariantTable<float> {
-  static constexpr StageVariant v16x20[] = {{16, 256}, {8, 256}, {16, 512}, {8, 128}};
+  static constexpr StageVariant v16x20[] = {{8, 256}, {4, 256}, {16, 256}, {8, 128}};
   static constexpr StageVariant v16x12[] = {{16, 256}, {8, 256}, {16, 384}};
   static constexpr StageVariant v8x4[] = {{16, 64}, {8, 64}};
   static constexpr StageVariant vsmall[] = {{16, 64}};
@@ -43,7 +43,7 @@ struct VariantTable<float> {
 };
 template <>
 struct VariantTable<double> {
-  static constexpr StageVariant v16x20[] = {{8, 256}, {4, 256}, {8, 128}, {4, 128}};
+  static constexpr StageVariant v16x20[] = {{4, 256}, {8, 256}, {4, 128}, {8, 128}};
   static constexpr StageVariant v16x12[] = {{8, 256}, {4, 256}, {8, 384}};
   static constexpr StageVariant v8x4[] = {{8, 64}, {16, 64}};
   static constexpr StageVariant vsmall[] = {{8, 64}};
@@ -84,16 +84,16 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
 #define VLB_CASE(SH, TC_, NT_, q0, q1, ex) \
   if (sh == SH && v.tc == TC_ && v.nt == NT_) return go_stage<real, TC_, NT_, q0, q1, ex>(a, m, k, s);
   if constexpr (sizeof(real) == 4) {
-    VLB_CASE(SH_16x20, 16, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
-    VLB_CASE(SH_16x20, 16, 512, 16, 20, true) VLB_CASE(SH_16x20, 8, 128, 16, 20, true)
+    VLB_CASE(SH_16x20, 8, 256, 16, 20, true) VLB_CASE(SH_16x20, 4, 256, 16, 20, true)
+    VLB_CASE(SH_16x20, 16, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 128, 16, 20, true)
     VLB_CASE(SH_16x12, 16, 256, 16, 12, true) VLB_CASE(SH_16x12, 8, 256, 16, 12, true)
     VLB_CASE(SH_16x12, 16, 384, 16, 12, true)
     VLB_CASE(SH_8x4, 16, 64, 8, 4, true) VLB_CASE(SH_8x4, 8, 64, 8, 4, true)
     VLB_CASE(SH_SMALL, 16, 64, MAXQ, MAXQ, false)
     VLB_CASE(SH_GENERIC, 16, 256, MAXQ, MAXQ, false)
   } else {
-    VLB_CASE(SH_16x20, 8, 256, 16, 20, true) VLB_CASE(SH_16x20, 4, 256, 16, 20, true)
-    VLB_CASE(SH_16x20, 8, 128, 16, 20, true) VLB_CASE(SH_16x20, 4, 128, 16, 20, true)
+    VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
+    VLB_CASE(SH_16x20, 4, 128, 16, 20, true) VLB_CASE(SH_16x20, 8, 128, 16, 20, true)
     VLB_CASE(SH_16x12, 8, 256, 16, 12, true) VLB_CASE(SH_16x12, 4, 256, 16, 12, true)
     VLB_CASE(SH_16x12, 8, 384, 16, 12, true)
     VLB_CASE(SH_8x4, 8, 64, 8, 4, true) VLB_CASE(SH_8x4, 16, 64, 8, 4, true)

@@ -35,8 +35,9 @@ struct StageSmem {
   static constexpr int NW = NT / 32;
   __host__ __device__ static size_t tile_off() { return 16; }
   __host__ __device__ static size_t lbuf_off(int Vp) { return tile_off() + size_t(TC + 6) * 2 * Vp * sizeof(real); }
+  __host__ __device__ static size_t fl_off(int Vp) { return lbuf_off(Vp) + size_t(TC) * 2 * Vp * sizeof(real); }
   __host__ __device__ static size_t dbl_off(int Vp) {
-    size_t o = lbuf_off(Vp) + size_t(TC) * 2 * Vp * sizeof(real);
+    size_t o = fl_off(Vp) + size_t(TC) * 2 * Vp * sizeof(real);
     return (o + 15) & ~size_t(15);
   }
   // doubles: p0, p1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each), cell n,T,u0,u1 (TC each),
@@ -65,6 +66,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   real* tile = reinterpret_cast<real*>(smem + L::tile_off());
   real* lbuf = reinterpret_cast<real*>(smem + L::lbuf_off(Vp));
+  real* flb = reinterpret_cast<real*>(smem + L::fl_off(Vp));  // F_l of the owned cells (stages 2, 3)
   double* dp = reinterpret_cast<double*>(smem + L::dbl_off(Vp));
   double* p0d = dp;
   double* p1d = p0d + MAXQ;
@@ -102,12 +104,16 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
+  const bool need_fl = a.ca != 0.0;
   if (warp == 0) {
     const unsigned rbytes = unsigned(row * sizeof(real));
-    if (lane == 0) mbar_expect_tx(bar, rbytes * unsigned(hi - lo));
+    if (lane == 0) mbar_expect_tx(bar, rbytes * unsigned(hi - lo + (need_fl ? TCe : 0)));
     __syncwarp();
     for (int c = lo + lane; c < hi; c += 32)
       bulk_g2s(tile + size_t(c - c0 + 3) * row, a.Fprev + size_t(in.cell0 + c) * row, rbytes, bar);
+    if (need_fl)
+      for (int t = lane; t < TCe; t += 32)
+        bulk_g2s(flb + size_t(t) * row, a.Fl + size_t(in.cell0 + c0 + t) * row, rbytes, bar);
   }
   for (int x = tid; x < MAXQ; x += NT) {
     p0d[x] = m.p0[x];
@@ -324,20 +330,20 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     const real pr = p0r[i];
     const bool up = pr >= real(0);
     const real sc = iw0[i] * iw1[j];
-    const real* S = tile + d * Vp + v;
+    real* S = tile + d * Vp + v;
+    const real* Fl = flb + d * Vp + v;
     real w0 = S[0], w1 = S[row], w2 = S[2 * row], w3 = S[3 * row], w4 = S[4 * row], w5 = S[5 * row];
-    real fm = up ? weno5<real>(w0, w1, w2, w3, w4, sc) : weno5<real>(w5, w4, w3, w2, w1, sc);
-    real* out = a.Fout + size_t(in.cell0 + c0) * row + d * Vp + v;
-    const real* Fl = a.Fl + size_t(in.cell0 + c0) * row + d * Vp + v;
+    // upwind stencil: (w0..w4) for p^R >= 0, mirrored (w5..w1) otherwise
+    real fm = weno5<real>(up ? w0 : w5, up ? w1 : w4, up ? w2 : w3, up ? w3 : w2, up ? w4 : w1, sc);
     for (int t = 0; t < TCe; ++t) {
       const real w6 = S[size_t(t + 6) * row];
-      const real fp = up ? weno5<real>(w1, w2, w3, w4, w5, sc) : weno5<real>(w6, w5, w4, w3, w2, sc);
+      const real fp = weno5<real>(up ? w1 : w6, up ? w2 : w5, up ? w3 : w4, up ? w4 : w3, up ? w5 : w2, sc);
       const real adv = pr * (ccp[t] * fp - ccm[t] * fm);
       const real feq = gRn[t * MAXQ + i] * gP[t * MAXQ + j] * (d ? cTr[t] : real(1));
       const real Lv = -adv + lbuf[size_t(t * 2 + d) * Vp + v] * cIR[t] - (w3 - feq) * cItau[t];
       real o = cb * w3 + cc * Lv;
-      if (ca != real(0)) o += ca * Fl[size_t(t) * row];
-      out[size_t(t) * row] = o;
+      if (need_fl) o += ca * Fl[size_t(t) * row];
+      S[size_t(t + 3) * row] = o;  // in place: this column's slot t+3 is not read again
       w0 = w1;
       w1 = w2;
       w2 = w3;
@@ -346,6 +352,13 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       w5 = w6;
       fm = fp;
     }
+  }
+  // ---- bulk store of the owned cells (generic-proxy writes made visible to the async proxy first)
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid == 0) {
+    bulk_s2g(a.Fout + size_t(in.cell0 + c0) * row, tile + 3 * row, unsigned(TCe * row * sizeof(real)));
+    bulk_commit_and_wait_read();
   }
 }
 
