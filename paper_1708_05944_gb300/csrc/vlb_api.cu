@@ -338,12 +338,18 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   for (int k = 0; k < nq0; ++k) {
     m.p0[k] = c->ax[0].p[k];
     m.w0[k] = c->ax[0].w[k];
-    for (int s = 0; s <= m.N0; ++s) m.tab0[k * MAXN + s] = c->ax[0].eqtab[k * (m.N0 + 1) + s];
+    for (int s = 0; s <= m.N0; ++s) {
+      m.tab0[k * MAXN + s] = c->ax[0].eqtab[k * (m.N0 + 1) + s];
+      m.tab0f[k * MAXN + s] = float(m.tab0[k * MAXN + s]);
+    }
   }
   for (int k = 0; k < nq1; ++k) {
     m.p1[k] = c->ax[1].p[k];
     m.w1[k] = c->ax[1].w[k];
-    for (int s = 0; s <= m.N1; ++s) m.tab1[k * MAXN + s] = c->ax[1].eqtab[k * (m.N1 + 1) + s];
+    for (int s = 0; s <= m.N1; ++s) {
+      m.tab1[k * MAXN + s] = c->ax[1].eqtab[k * (m.N1 + 1) + s];
+      m.tab1f[k * MAXN + s] = float(m.tab1[k * MAXN + s]);
+    }
   }
   c->k32.reset(new KArgs<float>());
   c->k64.reset(new KArgs<double>());

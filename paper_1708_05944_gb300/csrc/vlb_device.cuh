@@ -39,6 +39,7 @@ struct ModelArgs {
   double p0[MAXQ], p1[MAXQ];
   double w0[MAXQ], w1[MAXQ];  // quadrature weights
   double tab0[MAXQ * MAXN], tab1[MAXQ * MAXN];  // [k][s] with stride MAXN
+  float tab0f[MAXQ * MAXN], tab1f[MAXQ * MAXN];  // single-precision copies for the FP32-bulk path
 };
 
 template <typename real>
@@ -131,22 +132,35 @@ __device__ __forceinline__ real weno5(real a, real b, real c, real d, real e, re
 // M_0 = (1 + erf(u / sqrt(2T))) / 2, M_1 = u M_0 + T N(0; u, T),
 // M_s = u M_{s-1} + (s - 1) T M_{s-2} (integration by parts); the negative
 // semi-axis uses u -> -u.
-__device__ __forceinline__ void eq_moment_vector(int kind, int N, double u, double T, double* m) {
+template <typename T_>
+__device__ __forceinline__ T_ erf_t(T_ x);
+template <>
+__device__ __forceinline__ float erf_t<float>(float x) { return erff(x); }
+template <>
+__device__ __forceinline__ double erf_t<double>(double x) { return erf(x); }
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+__device__ __forceinline__ float rsqrt_t(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_t(double x) { return rsqrt(x); }
+
+template <typename R>
+__device__ __forceinline__ void eq_moment_vector(int kind, int N, R u, R T, R* m) {
   if (kind == 0) {
-    m[0] = 1.0;
+    m[0] = R(1);
     if (N >= 1) m[1] = u;
-    for (int l = 2; l <= N; ++l) m[l] = (u * m[l - 1] + (T - 1.0) * m[l - 2]) / l;
+    for (int l = 2; l <= N; ++l) m[l] = (u * m[l - 1] + (T - R(1)) * m[l - 2]) * (R(1) / R(l));
   } else {
-    const double g0 = exp(-u * u / (2.0 * T)) * rsqrt(2.0 * 3.14159265358979323846 * T);
-    m[0] = 0.5 * (1.0 + erf(u * rsqrt(2.0 * T)));
+    const R g0 = exp_t(-u * u / (R(2) * T)) * rsqrt_t(R(2) * R(3.14159265358979323846) * T);
+    m[0] = R(0.5) * (R(1) + erf_t<R>(u * rsqrt_t(R(2) * T)));
     if (N >= 1) m[1] = u * m[0] + T * g0;
-    for (int s = 2; s <= N; ++s) m[s] = u * m[s - 1] + (s - 1) * T * m[s - 2];
+    for (int s = 2; s <= N; ++s) m[s] = u * m[s - 1] + R(s - 1) * T * m[s - 2];
   }
 }
 
-__device__ __forceinline__ double relaxation_time(int mode, double kn, double n, double T) {
+template <typename R>
+__device__ __forceinline__ R relaxation_time(int mode, R kn, R n, R T) {
   if (mode == 0) return kn / (n * T);
-  if (mode == 1) return 0.62665706865775012560 * kn / n;  // sqrt(pi / 8)
+  if (mode == 1) return R(0.62665706865775012560) * kn / n;  // sqrt(pi / 8)
   return kn / n;
 }
 

@@ -114,8 +114,8 @@ __global__ void init_equilibrium_kernel(real* F, long long cells, int Vp, const 
     double mp[MAXN], mm[MAXN];
     const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0, nq = ax ? m.nq1 : m.nq0;
     const double u = ax ? u1 : u0;
-    eq_moment_vector(kind, N, u, T0, mp);
-    eq_moment_vector(kind, N, -u, T0, mm);
+    eq_moment_vector<double>(kind, N, u, T0, mp);
+    eq_moment_vector<double>(kind, N, -u, T0, mm);
     for (int k = 0; k < nq; ++k) {
       const double pk = ax ? m.p1[k] : m.p0[k];
       const double* mv = (kind == 1 && pk < 0.0) ? mm : mp;

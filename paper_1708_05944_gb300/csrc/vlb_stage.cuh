@@ -40,12 +40,13 @@ struct StageSmem {
     size_t o = fl_off(Vp) + size_t(TC) * 2 * Vp * sizeof(real);
     return (o + 15) & ~size_t(15);
   }
-  // doubles: p0, p1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each), cell n,T,u0,u1 (TC each),
-  // moment vectors (TC*4*MAXN), reduction (NW*4), wall scratch (2*MAXQ + 16)
-  static constexpr size_t n_dbl = 2 * MAXQ + 2 * MAXQ * MAXN + 4 * TC + TC * 4 * MAXN + NW * 4 + 2 * MAXQ + 16;
+  // doubles: p0, p1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each, wall equilibria), reduction (NW*4),
+  // wall scratch (2*MAXQ + 16)
+  static constexpr size_t n_dbl = 2 * MAXQ + 2 * MAXQ * MAXN + NW * 4 + 2 * MAXQ + 16;
   __host__ __device__ static size_t real_off(int Vp) { return dbl_off(Vp) + n_dbl * sizeof(double); }
-  // reals: p0, p1, 1/w0, 1/w1 (MAXQ each), n g_R and g_phi (TC*MAXQ each), T, 1/tau, cp, cm, 1/Rbar (TC each)
-  static constexpr size_t n_real = 4 * MAXQ + 2 * TC * MAXQ + 5 * TC;
+  // reals: p0, p1, 1/w0, 1/w1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each), n g_R and g_phi (TC*MAXQ each),
+  // cell n, T, u0, u1, 1/tau, cp, cm, 1/Rbar (TC each), moment vectors (TC*4*MAXN)
+  static constexpr size_t n_real = 4 * MAXQ + 2 * MAXQ * MAXN + 2 * TC * MAXQ + 8 * TC + TC * 4 * MAXN;
   __host__ __device__ static size_t bytes(int Vp) { return real_off(Vp) + n_real * sizeof(real); }
 };
 
@@ -72,25 +73,26 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   double* p1d = p0d + MAXQ;
   double* tab0 = p1d + MAXQ;
   double* tab1 = tab0 + MAXQ * MAXN;
-  double* cn = tab1 + MAXQ * MAXN;
-  double* cT = cn + TC;
-  double* cu0 = cT + TC;
-  double* cu1 = cu0 + TC;
-  double* mv = cu1 + TC;          // [t][axis*2 + side][s]
-  double* red = mv + TC * 4 * MAXN;
+  double* red = tab1 + MAXQ * MAXN;
   double* wl = red + NW * 4;      // wall scratch
   real* rp = reinterpret_cast<real*>(smem + L::real_off(Vp));
   real* p0r = rp;
   real* p1r = p0r + MAXQ;
   real* iw0 = p1r + MAXQ;  // 1 / w_i
   real* iw1 = iw0 + MAXQ;  // 1 / w_j
-  real* gRn = iw1 + MAXQ;  // [t][i] n_t g_{R,i}
+  real* tabr0 = iw1 + MAXQ;  // equilibrium tables in the bulk type
+  real* tabr1 = tabr0 + MAXQ * MAXN;
+  real* gRn = tabr1 + MAXQ * MAXN;  // [t][i] n_t g_{R,i}
   real* gP = gRn + TC * MAXQ;
-  real* cTr = gP + TC * MAXQ;
-  real* cItau = cTr + TC;
+  real* cn = gP + TC * MAXQ;
+  real* cTr = cn + TC;
+  real* cu0 = cTr + TC;
+  real* cu1 = cu0 + TC;
+  real* cItau = cu1 + TC;
   real* ccp = cItau + TC;
   real* ccm = ccp + TC;
   real* cIR = ccm + TC;
+  real* mv = cIR + TC;  // [t][axis*2 + side][s]
 
   const TileDesc td = a.tiles[blockIdx.x];
   const InstDesc in = a.inst[td.inst];
@@ -120,12 +122,14 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     p1d[x] = m.p1[x];
     p0r[x] = real(m.p0[x]);
     p1r[x] = real(m.p1[x]);
-    iw0[x] = m.w0[x] > 0.0 ? real(1.0 / m.w0[x]) : real(0);
-    iw1[x] = m.w1[x] > 0.0 ? real(1.0 / m.w1[x]) : real(0);
+    iw0[x] = m.w0[x] > 0.0 ? real(1) / real(m.w0[x]) : real(0);
+    iw1[x] = m.w1[x] > 0.0 ? real(1) / real(m.w1[x]) : real(0);
   }
   for (int x = tid; x < MAXQ * MAXN; x += NT) {
     tab0[x] = m.tab0[x];
     tab1[x] = m.tab1[x];
+    tabr0[x] = sizeof(real) == 4 ? real(m.tab0f[x]) : real(m.tab0[x]);
+    tabr1[x] = sizeof(real) == 4 ? real(m.tab1f[x]) : real(m.tab1[x]);
   }
   for (int t = tid; t < TCe; t += NT) {
     const GeoCell g = a.geo[in.cell0 + c0 + t];
@@ -155,40 +159,39 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     }
     const double dn = warp_sum<real>(double(sn)), dr = warp_sum<real>(double(sr));
     const double dpp = warp_sum<real>(double(sp)), de = warp_sum<real>(double(se));
-    if (lane == 0) {
-      const double u0 = dr / dn, u1 = dpp / dn;
-      const double T = (de - dn * (u0 * u0 + u1 * u1)) / (3.0 * dn);
-      cn[t] = dn;
+    if (lane == 0) {  // the sums are FP64; the derived fields are formed in the bulk type
+      const real n = real(dn), u0 = real(dr) / n, u1 = real(dpp) / n;
+      const real T = (real(de) - n * (u0 * u0 + u1 * u1)) / (real(3) * n);
+      cn[t] = n;
       cu0[t] = u0;
       cu1[t] = u1;
-      cT[t] = T;
-      cTr[t] = real(T);
-      cItau[t] = real(1.0 / relaxation_time(in.tau_mode, in.kn, dn, T));
+      cTr[t] = T;
+      cItau[t] = real(1) / relaxation_time<real>(in.tau_mode, real(in.kn), n, T);
     }
   }
   __syncthreads();
   for (int x = tid; x < TCe * 4; x += NT) {
     const int t = x >> 2, ax = (x >> 1) & 1, side = x & 1;
-    const double u = (ax ? cu1[t] : cu0[t]) * (side ? -1.0 : 1.0);
-    eq_moment_vector(ax ? m.kind1 : m.kind0, ax ? m.N1 : m.N0, u, cT[t], mv + (t * 4 + ax * 2 + side) * MAXN);
+    const real u = (ax ? cu1[t] : cu0[t]) * (side ? real(-1) : real(1));
+    eq_moment_vector<real>(ax ? m.kind1 : m.kind0, ax ? m.N1 : m.N0, u, cTr[t], mv + (t * 4 + ax * 2 + side) * MAXN);
   }
   __syncthreads();
   for (int x = tid; x < TCe * (nq0 + nq1); x += NT) {
     const int t = x / (nq0 + nq1);
     int k = x - t * (nq0 + nq1);
     if (k < nq0) {
-      const int side = (m.kind0 == 1 && p0d[k] < 0.0) ? 1 : 0;
-      const double* mm = mv + (t * 4 + side) * MAXN;
-      double g = 0;
-      for (int s = 0; s <= m.N0; ++s) g += tab0[k * MAXN + s] * mm[s];
-      gRn[t * MAXQ + k] = real(cn[t] * g);
+      const int side = (m.kind0 == 1 && p0r[k] < real(0)) ? 1 : 0;
+      const real* mm = mv + (t * 4 + side) * MAXN;
+      real g = 0;
+      for (int s = 0; s <= m.N0; ++s) g += tabr0[k * MAXN + s] * mm[s];
+      gRn[t * MAXQ + k] = cn[t] * g;
     } else {
       k -= nq0;
-      const int side = (m.kind1 == 1 && p1d[k] < 0.0) ? 1 : 0;
-      const double* mm = mv + (t * 4 + 2 + side) * MAXN;
-      double g = 0;
-      for (int s = 0; s <= m.N1; ++s) g += tab1[k * MAXN + s] * mm[s];
-      gP[t * MAXQ + k] = real(g);
+      const int side = (m.kind1 == 1 && p1r[k] < real(0)) ? 1 : 0;
+      const real* mm = mv + (t * 4 + 2 + side) * MAXN;
+      real g = 0;
+      for (int s = 0; s <= m.N1; ++s) g += tabr1[k * MAXN + s] * mm[s];
+      gP[t * MAXQ + k] = g;
     }
   }
 
@@ -205,10 +208,10 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     __syncthreads();
     if (tid == 0) {
       double m0p[MAXN], m0m[MAXN], m1p[MAXN], m1m[MAXN];
-      eq_moment_vector(m.kind0, m.N0, 0.0, Tw, m0p);
-      eq_moment_vector(m.kind0, m.N0, -0.0, Tw, m0m);
-      eq_moment_vector(m.kind1, m.N1, uw, Tw, m1p);
-      eq_moment_vector(m.kind1, m.N1, -uw, Tw, m1m);
+      eq_moment_vector<double>(m.kind0, m.N0, 0.0, Tw, m0p);
+      eq_moment_vector<double>(m.kind0, m.N0, -0.0, Tw, m0m);
+      eq_moment_vector<double>(m.kind1, m.N1, uw, Tw, m1p);
+      eq_moment_vector<double>(m.kind1, m.N1, -uw, Tw, m1m);
       for (int k = 0; k < nq0; ++k) {
         const double* mm = (m.kind0 == 1 && p0d[k] < 0.0) ? m0m : m0p;
         double g = 0;
