@@ -42,6 +42,7 @@ struct vlb_ctx {
   InstDesc* d_inst = nullptr;
   TileDesc* d_tiles = nullptr;
   GeoCell* d_geo = nullptr;
+  GeoCellF* d_geof = nullptr;
   double* d_nw = nullptr;
   unsigned* d_err = nullptr;
   double* d_mom = nullptr;
@@ -147,6 +148,8 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   } else {
     a.ca = 1.0 / 3.0, a.cb = 2.0 / 3.0, a.cc = 2.0 / 3.0;
   }
+  a.caf = float(a.ca), a.cbf = float(a.cb), a.ccf = float(a.cc);
+  a.geof = c->d_geof;
   a.inst = c->d_inst;
   a.tiles = c->d_tiles;
   a.n_tiles = int(c->tiles.size());
@@ -338,6 +341,9 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   for (int k = 0; k < nq0; ++k) {
     m.p0[k] = c->ax[0].p[k];
     m.w0[k] = c->ax[0].w[k];
+    m.iw0[k] = 1.0 / m.w0[k];
+    m.p0f[k] = float(m.p0[k]);
+    m.iw0f[k] = float(m.iw0[k]);
     for (int s = 0; s <= m.N0; ++s) {
       m.tab0[k * MAXN + s] = c->ax[0].eqtab[k * (m.N0 + 1) + s];
       m.tab0f[k * MAXN + s] = float(m.tab0[k * MAXN + s]);
@@ -346,6 +352,9 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   for (int k = 0; k < nq1; ++k) {
     m.p1[k] = c->ax[1].p[k];
     m.w1[k] = c->ax[1].w[k];
+    m.iw1[k] = 1.0 / m.w1[k];
+    m.p1f[k] = float(m.p1[k]);
+    m.iw1f[k] = float(m.iw1[k]);
     for (int s = 0; s <= m.N1; ++s) {
       m.tab1[k * MAXN + s] = c->ax[1].eqtab[k * (m.N1 + 1) + s];
       m.tab1f[k * MAXN + s] = float(m.tab1[k * MAXN + s]);
@@ -374,6 +383,8 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     d.tau_mode = tau_mode[i];
     d.kn = kn[i];
     d.dt = 0.0;
+    d.kn_f = float(kn[i]);
+    d.dt_f = 0.0f;
     d.u_in = inner[i].u_tangential;
     d.T_in = inner[i].T;
     d.u_out = outer[i].u_tangential;
@@ -406,6 +417,7 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     VLB_CUDA(cp, cudaMalloc(&c->d_tiles, sizeof(TileDesc) * most));
   }
   VLB_CUDA(cp, cudaMalloc(&c->d_geo, sizeof(GeoCell) * c->total_cells));
+  VLB_CUDA(cp, cudaMalloc(&c->d_geof, sizeof(GeoCellF) * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_nw, sizeof(double) * 2 * n_inst));
   VLB_CUDA(cp, cudaMalloc(&c->d_err, sizeof(unsigned)));
   VLB_CUDA(cp, cudaMalloc(&c->d_mom, sizeof(double) * 9 * c->total_cells));
@@ -416,6 +428,12 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
                                cudaMemcpyHostToDevice, c->stream));
   VLB_CUDA(cp, cudaMemcpyAsync(c->d_geo, c->geo.data(), sizeof(GeoCell) * c->total_cells, cudaMemcpyHostToDevice,
                                c->stream));
+  {
+    std::vector<GeoCellF> gf(c->total_cells);
+    for (long long i = 0; i < c->total_cells; ++i)
+      gf[i] = GeoCellF{float(c->geo[i].cp), float(c->geo[i].cm), float(c->geo[i].inv_rbar), 0.0f};
+    VLB_CUDA(cp, cudaMemcpy(c->d_geof, gf.data(), sizeof(GeoCellF) * c->total_cells, cudaMemcpyHostToDevice));
+  }
   VLB_CUDA(cp, cudaMemsetAsync(c->d_nw, 0, sizeof(double) * 2 * n_inst, c->stream));
   VLB_CUDA(cp, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
   VLB_CUDA(cp, cudaStreamSynchronize(c->stream));
@@ -487,7 +505,10 @@ vlb_status vlb_set_dt(vlb_ctx* c, const double* dt) {
   if (!c || !dt) return fail(c, VLB_ERR_INVALID, "null argument");
   for (int i = 0; i < c->n_inst; ++i)
     if (!(dt[i] > 0.0)) return fail(c, VLB_ERR_INVALID, "time steps must be positive");
-  for (int i = 0; i < c->n_inst; ++i) c->inst[i].dt = dt[i];
+  for (int i = 0; i < c->n_inst; ++i) {
+    c->inst[i].dt = dt[i];
+    c->inst[i].dt_f = float(dt[i]);
+  }
   VLB_CUDA(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice,
                               c->stream));
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -739,6 +760,7 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_inst);
   cudaFree(c->d_tiles);
   cudaFree(c->d_geo);
+  cudaFree(c->d_geof);
   cudaFree(c->d_nw);
   cudaFree(c->d_err);
   cudaFree(c->d_mom);

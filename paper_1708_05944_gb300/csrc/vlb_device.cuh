@@ -18,6 +18,7 @@ struct InstDesc {
   int tau_mode;     // vlb_tau_mode
   double kn, dt;
   double u_in, T_in, u_out, T_out;  // walls: tangential speed, temperature
+  float kn_f, dt_f;                 // single-precision copies
 };
 
 struct TileDesc {
@@ -33,6 +34,11 @@ struct GeoCell {
   double cp, cm, inv_rbar, wres;
 };
 
+// Single-precision copy of the advection and force factors (cp, cm, inv_rbar, unused).
+struct GeoCellF {
+  float cp, cm, inv_rbar, pad;
+};
+
 // Momentum-space tables of the model (copied into shared memory by each CTA).
 struct ModelArgs {
   int nq0, nq1, N0, N1, kind0, kind1;
@@ -40,6 +46,8 @@ struct ModelArgs {
   double w0[MAXQ], w1[MAXQ];  // quadrature weights
   double tab0[MAXQ * MAXN], tab1[MAXQ * MAXN];  // [k][s] with stride MAXN
   float tab0f[MAXQ * MAXN], tab1f[MAXQ * MAXN];  // single-precision copies for the FP32-bulk path
+  float p0f[MAXQ], p1f[MAXQ], iw0f[MAXQ], iw1f[MAXQ];  // nodes and inverse weights, single precision
+  double iw0[MAXQ], iw1[MAXQ];                         // inverse weights, double precision
 };
 
 template <typename real>
@@ -61,14 +69,34 @@ __device__ __forceinline__ double vdiv(double x, double y) { return x / y; }
 // ---------------------------------------------------------------- WENO-5
 // Interface value from the upwind-ordered stencil (a, b, c, d, e) =
 // (F_{s-2}, F_{s-1}, F_s, F_{s+1}, F_{s+2}) (Eqs. weno5_flux, weno5_omega,
-// weno_sigma); exact zeros of the smoothness indicators take Table IV's limits.
-// The normalised weights delta_q / sigma_q^2 do not change when the stencil is
-// multiplied by a constant, so the indicators are computed on the stencil
-// times sc (the caller passes 1 / (w_i w_j), which brings the weighted
-// populations of every velocity to order one and keeps sigma_q inside the
-// single-precision range).  The weights are evaluated in the division-light
-// form delta_q prod_{r != q} sigma_r^2 / sum_q' (...), with the indicators
-// scaled by their maximum in single precision.
+// weno_sigma) with the epsilon-free weights delta_q / sigma_q^2.
+//
+// The normalised weights do not change when the stencil is multiplied by a
+// constant, so the indicators are computed on the stencil times sc (callers
+// pass 1 / (w_i w_j), which brings the weighted populations of every velocity
+// to order one and keeps sigma_q inside the single-precision range).  The
+// weights are evaluated as delta_q prod_{r != q} sigma_r^2 over their sum,
+// with the indicators scaled by their maximum; this form is exact for one
+// vanishing indicator (Table IV: that stencil gets weight one).  When the
+// products all vanish or are not finite -- two or three zero indicators
+// (Table IV), or products below the single-precision range -- a slow path
+// uses Table IV for exact zeros and delta_q (sigma_min / sigma_q)^2 otherwise.
+template <typename real>
+__device__ __noinline__ void weno5_weights_slow(real s1, real s2, real s3, real* w) {
+  const real d1 = real(0.1), d2 = real(0.6), d3 = real(0.3);
+  if (s1 == real(0) || s2 == real(0) || s3 == real(0)) {
+    w[0] = s1 == real(0) ? d1 : real(0);
+    w[1] = s2 == real(0) ? d2 : real(0);
+    w[2] = s3 == real(0) ? d3 : real(0);
+  } else {
+    const real mn = vmin(s1, vmin(s2, s3));
+    const real r1 = mn / s1, r2 = mn / s2, r3 = mn / s3;
+    w[0] = d1 * r1 * r1;
+    w[1] = d2 * r2 * r2;
+    w[2] = d3 * r3 * r3;
+  }
+}
+
 template <typename real>
 __device__ __forceinline__ real weno5(real a, real b, real c, real d, real e, real sc) {
   const real k1312 = real(13) / real(12), q = real(0.25);
@@ -86,41 +114,18 @@ __device__ __forceinline__ real weno5(real a, real b, real c, real d, real e, re
   t = Cc - real(2) * D + E;
   u = real(3) * Cc - real(4) * D + E;
   real s3 = k1312 * t * t + q * u * u;
-  real w1, w2, w3;
-  if (s1 == real(0) || s2 == real(0) || s3 == real(0)) {
-    w1 = s1 == real(0) ? d1 : real(0);
-    w2 = s2 == real(0) ? d2 : real(0);
-    w3 = s3 == real(0) ? d3 : real(0);
-  } else {
-    bool ideal = false;
-    if (sizeof(real) == 4) {
-      const real smax = vmax(s1, vmax(s2, s3));
-      if (smax < real(1e-30)) {
-        ideal = true;  // stencil uniform to ~1e-15 relative: every candidate gives the same value
-      } else {
-        const real r = vdiv(real(1), smax);
-        s1 *= r;
-        s2 *= r;
-        s3 *= r;
-      }
-    }
-    if (ideal) {
-      w1 = d1, w2 = d2, w3 = d3;
-    } else {
-      const real P = s1 * s1, Qv = s2 * s2, R = s3 * s3;
-      w1 = d1 * Qv * R;
-      w2 = d2 * P * R;
-      w3 = d3 * P * Qv;
-      if (!(w1 + w2 + w3 > real(0))) {  // products underflowed: weights delta_q (s_min / s_q)^2
-        const real m = vmin(s1, vmin(s2, s3));
-        const real r1 = vdiv(m, s1), r2 = vdiv(m, s2), r3 = vdiv(m, s3);
-        w1 = d1 * r1 * r1;
-        w2 = d2 * r2 * r2;
-        w3 = d3 * r3 * r3;
-      }
-    }
+  const real r = vdiv(real(1), vmax(s1, vmax(s2, s3)));
+  const real x1 = s1 * r, x2 = s2 * r, x3 = s3 * r;
+  const real P = x1 * x1, Qv = x2 * x2, R = x3 * x3;
+  real w1 = d1 * (Qv * R), w2 = d2 * (P * R), w3 = d3 * (P * Qv);
+  real den = w1 + w2 + w3;
+  if (!(den > real(0)) || !(den < real(1e30))) {
+    real w[3];
+    weno5_weights_slow<real>(s1, s2, s3, w);
+    w1 = w[0], w2 = w[1], w3 = w[2];
+    den = w1 + w2 + w3;
   }
-  return vdiv(w1 * F1 + w2 * F2 + w3 * F3, w1 + w2 + w3);
+  return vdiv(w1 * F1 + w2 * F2 + w3 * F3, den);
 }
 
 // ---------------------------------------------------------------- equilibrium

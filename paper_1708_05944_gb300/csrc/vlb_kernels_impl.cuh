@@ -35,7 +35,7 @@ template <typename real>
 struct VariantTable;
 template <>
 struct VariantTable<float> {
-  static constexpr StageVariant v16x20[] = {{8, 256}, {4, 256}, {16, 256}, {8, 128}};
+  static constexpr StageVariant v16x20[] = {{4, 256}, {8, 256}, {4, 320}, {8, 320}, {16, 320}};
   static constexpr StageVariant v16x12[] = {{16, 256}, {8, 256}, {16, 384}};
   static constexpr StageVariant v8x4[] = {{16, 64}, {8, 64}};
   static constexpr StageVariant vsmall[] = {{16, 64}};
@@ -72,7 +72,8 @@ size_t stage_smem_bytes(StageVariant v, int Vp) {
   if (v.tc == TC_ && v.nt == NT_) return StageSmem<real, TC_, NT_>::bytes(Vp);
   VLB_SMEM_CASE(16, 256) VLB_SMEM_CASE(8, 256) VLB_SMEM_CASE(16, 512) VLB_SMEM_CASE(8, 128)
   VLB_SMEM_CASE(16, 384) VLB_SMEM_CASE(16, 64) VLB_SMEM_CASE(8, 64) VLB_SMEM_CASE(4, 256)
-  VLB_SMEM_CASE(4, 128) VLB_SMEM_CASE(8, 384)
+  VLB_SMEM_CASE(4, 128) VLB_SMEM_CASE(8, 384) VLB_SMEM_CASE(4, 320) VLB_SMEM_CASE(8, 320)
+  VLB_SMEM_CASE(16, 320)
 #undef VLB_SMEM_CASE
   return 0;
 }
@@ -84,8 +85,9 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
 #define VLB_CASE(SH, TC_, NT_, q0, q1, ex) \
   if (sh == SH && v.tc == TC_ && v.nt == NT_) return go_stage<real, TC_, NT_, q0, q1, ex>(a, m, k, s);
   if constexpr (sizeof(real) == 4) {
-    VLB_CASE(SH_16x20, 8, 256, 16, 20, true) VLB_CASE(SH_16x20, 4, 256, 16, 20, true)
-    VLB_CASE(SH_16x20, 16, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 128, 16, 20, true)
+    VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
+    VLB_CASE(SH_16x20, 4, 320, 16, 20, true) VLB_CASE(SH_16x20, 8, 320, 16, 20, true)
+    VLB_CASE(SH_16x20, 16, 320, 16, 20, true)
     VLB_CASE(SH_16x12, 16, 256, 16, 12, true) VLB_CASE(SH_16x12, 8, 256, 16, 12, true)
     VLB_CASE(SH_16x12, 16, 384, 16, 12, true)
     VLB_CASE(SH_8x4, 16, 64, 8, 4, true) VLB_CASE(SH_8x4, 8, 64, 8, 4, true)

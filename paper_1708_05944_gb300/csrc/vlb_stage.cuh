@@ -19,10 +19,12 @@ struct StageArgs {
   const real* Fl;     // F_l of the step (read when ca != 0)
   real* Fout;
   double ca, cb, cc;  // Fout = ca F_l + cb F_prev + cc dt L[F_prev]
+  float caf, cbf, ccf;  // single-precision copies
   const InstDesc* inst;
   const TileDesc* tiles;
   int n_tiles;
-  const GeoCell* geo;  // per global cell
+  const GeoCell* geo;    // per global cell
+  const GeoCellF* geof;  // single-precision copy
   double* nw;          // 2 per instance: inner, outer wall density
   unsigned* err;
   int Vp;              // per-field stride of a cell row (>= nq0 nq1, multiple of 4)
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const bool need_fl = a.ca != 0.0;
+  const bool need_fl = a.caf != 0.0f;
   if (warp == 0) {
     const unsigned rbytes = unsigned(row * sizeof(real));
     if (lane == 0) mbar_expect_tx(bar, rbytes * unsigned(hi - lo + (need_fl ? TCe : 0)));
@@ -120,13 +122,21 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       for (int t = lane; t < TCe; t += 32)
         bulk_g2s(flb + t * row, a.Fl + size_t(in.cell0 + c0 + t) * row, rbytes, bar);
   }
+  constexpr bool F32 = sizeof(real) == 4;
   for (int x = tid; x < MAXQ; x += NT) {
     p0d[x] = m.p0[x];
     p1d[x] = m.p1[x];
-    p0r[x] = real(m.p0[x]);
-    p1r[x] = real(m.p1[x]);
-    iw0[x] = m.w0[x] > 0.0 ? real(1) / real(m.w0[x]) : real(0);
-    iw1[x] = m.w1[x] > 0.0 ? real(1) / real(m.w1[x]) : real(0);
+    if constexpr (F32) {
+      p0r[x] = m.p0f[x];
+      p1r[x] = m.p1f[x];
+      iw0[x] = m.iw0f[x];
+      iw1[x] = m.iw1f[x];
+    } else {
+      p0r[x] = m.p0[x];
+      p1r[x] = m.p1[x];
+      iw0[x] = m.iw0[x];
+      iw1[x] = m.iw1[x];
+    }
   }
   for (int x = tid; x < MAXQ * MAXN; x += NT) {
     tab0[x] = m.tab0[x];
@@ -135,10 +145,17 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     tabr1[x] = sizeof(real) == 4 ? real(m.tab1f[x]) : real(m.tab1[x]);
   }
   for (int t = tid; t < TCe; t += NT) {
-    const GeoCell g = a.geo[in.cell0 + c0 + t];
-    ccp[t] = real(g.cp);
-    ccm[t] = real(g.cm);
-    cIR[t] = real(g.inv_rbar);
+    if constexpr (F32) {
+      const GeoCellF g = a.geof[in.cell0 + c0 + t];
+      ccp[t] = g.cp;
+      ccm[t] = g.cm;
+      cIR[t] = g.inv_rbar;
+    } else {
+      const GeoCell g = a.geo[in.cell0 + c0 + t];
+      ccp[t] = g.cp;
+      ccm[t] = g.cm;
+      cIR[t] = g.inv_rbar;
+    }
   }
   bool ok = mbar_wait(bar, 0, a.max_polls);
   ok = __syncthreads_and(ok);
@@ -183,7 +200,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       cu0[t] = u0;
       cu1[t] = u1;
       cTr[t] = T;
-      cItau[t] = real(1) / relaxation_time<real>(in.tau_mode, real(in.kn), nn, T);
+      cItau[t] = real(1) / relaxation_time<real>(in.tau_mode, F32 ? real(in.kn_f) : real(in.kn), nn, T);
     }
   }
   // lbuf = -(p^phi)^2 K^R f (one task per (cell, field, j): a column of nq0 values)
@@ -342,8 +359,19 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   __syncthreads();
 
   // ==== phase D: WENO-5 fluxes along the cells, flux difference, BGK, RK3 combine (in place)
-  const real dtr = real(in.dt);
-  const real ca = real(a.ca), cb = real(a.cb), cc = real(a.cc) * dtr;
+  const real dtr = F32 ? real(in.dt_f) : real(in.dt);
+  const real ca = F32 ? real(a.caf) : real(a.ca), cb = F32 ? real(a.cbf) : real(a.cb);
+  const real cc = (F32 ? real(a.ccf) : real(a.cc)) * dtr;
+  // per-cell factors of this tile in registers
+  real rcp[TC], rcm[TC], rir[TC], rit[TC], rT[TC];
+#pragma unroll
+  for (int t = 0; t < TC; ++t) {
+    rcp[t] = ccp[t];
+    rcm[t] = ccm[t];
+    rir[t] = cIR[t];
+    rit[t] = cItau[t];
+    rT[t] = cTr[t];
+  }
   for (int x = tid; x < 2 * V; x += NT) {
     const int d = x >= V, v = x - d * V;
     const int i = v / nq1, j = v - i * nq1;
@@ -360,9 +388,9 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       if (t < TCe) {
         const real w6 = S[(t + 6) * row];
         const real fp = weno5<real>(up ? w1 : w6, up ? w2 : w5, up ? w3 : w4, up ? w4 : w3, up ? w5 : w2, sc);
-        const real adv = pr * (ccp[t] * fp - ccm[t] * fm);
-        const real feq = gRn[t * MAXQ + i] * gP[t * MAXQ + j] * (d ? cTr[t] : real(1));
-        const real Lv = -adv + lbuf[(t * 2 + d) * Vp + v] * cIR[t] - (w3 - feq) * cItau[t];
+        const real adv = pr * (rcp[t] * fp - rcm[t] * fm);
+        const real feq = gRn[t * MAXQ + i] * gP[t * MAXQ + j] * (d ? rT[t] : real(1));
+        const real Lv = -adv + lbuf[(t * 2 + d) * Vp + v] * rir[t] - (w3 - feq) * rit[t];
         real o = cb * w3 + cc * Lv;
         if (need_fl) o += ca * Fl[t * row];
         S[(t + 3) * row] = o;  // in place: this column's slot t+3 is not read again
