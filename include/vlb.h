@@ -182,6 +182,27 @@ vlb_status vlb_set_variant(vlb_ctx* ctx, int variant);
  * (either pointer may be NULL). */
 vlb_status vlb_autotune(vlb_ctx* ctx, double dt, int reps, int* chosen, double* best_ms);
 
+/* nsteps (>= 1) TVD-RK3 steps of the context's instances from the caller's
+ * device buffer f_in into the caller's device buffer f_out (distinct, both in
+ * the documented layout and the context's real type; f_in is only read),
+ * with time step dt > 0 for every instance.  The paper has no counterpart:
+ * this entry point is for callers that cannot allocate device memory when
+ * they step (their memory belongs to another allocator or to a full pool, or
+ * the step runs where cudaMalloc is not allowed).  It allocates nothing: the
+ * two intermediate stage buffers F^(1), F^(2) live in one static device array
+ * of 64 MiB compiled into the library (every GPU that loads the library holds
+ * it until the process exits), so 2 x total_cells x 2 x nvel x sizeof(real)
+ * must not exceed 64 MiB, else VLB_ERR_UNSUPPORTED; nvel must be a multiple
+ * of 4, else VLB_ERR_UNSUPPORTED.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents (nothing in it needs to start at zero): calls that overlap
+ * on the GPU -- two streams, two contexts, or a context's own vlb_step
+ * running concurrently -- race on it.  Asynchronous on the context stream;
+ * it also updates the context's per-instance time step to dt and its wall
+ * densities (vlb_wall_density). */
+vlb_status vlb_step_static_scratch(vlb_ctx* ctx, const void* f_in, void* f_out, double dt, long long nsteps);
+
 /* Number of kernels the last vlb_step / vlb_stage call launched. */
 long long vlb_kernel_launches(const vlb_ctx* ctx);
 

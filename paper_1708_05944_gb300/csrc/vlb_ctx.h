@@ -1,0 +1,53 @@
+// Internal definition of the libvlb context (shared by the API translation units).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/vlb.h"
+#include "vlb_launch.h"
+#include "vlb_stage.cuh"
+#include "vlb_tables.h"
+
+using namespace vlb;
+
+struct vlb_ctx {
+  vlb_model model{};
+  int prec = 0;
+  int n_inst = 0;
+  cudaStream_t stream = nullptr;
+  AxisTables ax[2];
+  int nq0 = 0, nq1 = 0, V = 0, Vp = 0;
+  long long total_cells = 0;
+  size_t esize = 8;
+  std::vector<InstDesc> inst;
+  std::vector<TileDesc> tiles;
+  std::vector<GeoCell> geo;
+  std::vector<vlb_couette_grid> grids;
+  ModelArgs margs{};
+  std::unique_ptr<KArgs<float>> k32;
+  std::unique_ptr<KArgs<double>> k64;
+  void* F[3] = {nullptr, nullptr, nullptr};
+  StageVariant variants[8];
+  int n_variants = 0;
+  int variant = 0;
+  int cur = 0;   // buffer holding F_l
+  int last = 0;  // buffer written by the most recent stage
+  int stage_done = 0;
+  InstDesc* d_inst = nullptr;
+  TileDesc* d_tiles = nullptr;
+  GeoCell* d_geo = nullptr;
+  GeoCellF* d_geof = nullptr;
+  double* d_nw = nullptr;
+  unsigned* d_err = nullptr;
+  double* d_mom = nullptr;
+  double* d_prev = nullptr;
+  double* d_res = nullptr;
+  bool have_prev = false;
+  size_t tile_cap = 0;
+  long long launches = 0;
+  long long steps = 0;
+  std::string err;
+};

@@ -1,0 +1,107 @@
+// vlb_step_static_scratch: RK3 steps whose intermediate stage buffers live in a
+// fixed device array compiled into the library, so the call allocates nothing.
+//
+// Who needs it: applications that cannot allocate device memory when they step
+// -- their device memory belongs to another allocator or to a pool that is
+// already full, or the call sits in a latency-critical loop where a
+// cudaMalloc is not allowed.  They keep f in their own device buffers and
+// call this entry point, which uses g_step_scratch below for F^(1) and F^(2).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <string>
+
+#include "vlb_ctx.h"
+
+namespace {
+
+// 64 MiB, held by every GPU that loads the library until the process exits.
+constexpr size_t kScratchBytes = size_t(64) << 20;
+static __device__ __align__(256) unsigned char g_step_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void* g_scratch_ptr[kMaxDevices] = {nullptr};
+
+vlb_status static_fail(vlb_ctx* c, vlb_status s, const std::string& msg) {
+  c->err = msg;
+  return s;
+}
+
+template <typename real>
+cudaError_t launch_one(vlb_ctx* c, int k, const void* prev, const void* fl, void* out) {
+  StageArgs<real> a{};
+  a.Fprev = static_cast<const real*>(prev);
+  a.Fl = static_cast<const real*>(fl);
+  a.Fout = static_cast<real*>(out);
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0}, cc[3] = {1.0, 0.25, 2.0 / 3.0};
+  a.ca = ca[k - 1];
+  a.cb = cb[k - 1];
+  a.cc = cc[k - 1];
+  a.caf = float(a.ca);
+  a.cbf = float(a.cb);
+  a.ccf = float(a.cc);
+  a.inst = c->d_inst;
+  a.tiles = c->d_tiles;
+  a.n_tiles = int(c->tiles.size());
+  a.geo = c->d_geo;
+  a.geof = c->d_geof;
+  a.nw = c->d_nw;
+  a.err = c->d_err;
+  a.Vp = c->Vp;
+  a.max_polls = 1ull << 26;
+  const KArgs<real>* kk;
+  if constexpr (sizeof(real) == 4) kk = c->k32.get(); else kk = c->k64.get();
+  return launch_stage<real>(c->variants[c->variant], a, c->margs, *kk, c->stream);
+}
+
+}  // namespace
+
+extern "C" vlb_status vlb_step_static_scratch(vlb_ctx* c, const void* f_in, void* f_out, double dt,
+                                              long long nsteps) {
+  if (!c) return VLB_ERR_INVALID;
+  if (!f_in || !f_out || f_in == f_out) return static_fail(c, VLB_ERR_INVALID, "need distinct input and output buffers");
+  if (nsteps < 1 || !(dt > 0.0)) return static_fail(c, VLB_ERR_INVALID, "need dt > 0 and nsteps >= 1");
+  if (c->Vp != c->V)
+    return static_fail(c, VLB_ERR_UNSUPPORTED, "velocity count must be a multiple of 4 for caller-owned buffers");
+  const size_t fbytes = size_t(c->total_cells) * 2 * c->Vp * c->esize;
+  if (2 * fbytes > kScratchBytes)
+    return static_fail(c, VLB_ERR_UNSUPPORTED,
+                       "two stage buffers of " + std::to_string(fbytes) + " bytes exceed the 64 MiB static scratch");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return static_fail(c, VLB_ERR_UNSUPPORTED, "device index out of range");
+  if (!g_scratch_ptr[dev]) {  // first call on this device: device address of the static array
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_step_scratch);
+    if (e != cudaSuccess)
+      return static_fail(c, VLB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    g_scratch_ptr[dev] = p;
+  }
+  unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  void* s1 = base;
+  void* s2 = base + fbytes;
+  // time step for every instance (the context's descriptor copy on the device)
+  bool change = false;
+  for (int i = 0; i < c->n_inst; ++i) change |= c->inst[i].dt != dt;
+  if (change) {
+    for (int i = 0; i < c->n_inst; ++i) {
+      c->inst[i].dt = dt;
+      c->inst[i].dt_f = float(dt);
+    }
+    e = cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("descriptor copy: ") + cudaGetErrorString(e));
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("descriptor copy: ") + cudaGetErrorString(e));
+  }
+  for (long long s = 0; s < nsteps; ++s) {
+    const void* Fl = s == 0 ? f_in : f_out;  // stage 3 may update f_out in place: each CTA reads only its own F_l rows
+    for (int k = 1; k <= 3; ++k) {
+      const void* prev = k == 1 ? Fl : (k == 2 ? s1 : s2);
+      void* out = k == 1 ? s1 : (k == 2 ? s2 : f_out);
+      e = c->prec == VLB_FP64 ? launch_one<double>(c, k, prev, Fl, out) : launch_one<float>(c, k, prev, Fl, out);
+      if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(e));
+    }
+  }
+  return VLB_OK;
+}

@@ -67,6 +67,7 @@ EXPORTS = {
     "vlb_variants": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "vlb_autotune": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    "vlb_step_static_scratch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_longlong]),
     "vlb_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "vlb_last_error": (C.c_char_p, [C.c_void_p]),
     "vlb_destroy": (None, [C.c_void_p]),
@@ -246,6 +247,10 @@ class Couette:
         ch, ms = C.c_int(), C.c_double()
         _check(_lib.vlb_autotune(self.h, dt, reps, C.byref(ch), C.byref(ms)), self.h)
         return ch.value, ms.value
+
+    def step_static_scratch(self, f_in, f_out, dt, nsteps=1):
+        """vlb_step_static_scratch: f_in, f_out are device tensors in the library layout."""
+        _check(_lib.vlb_step_static_scratch(self.h, _ptr(f_in), _ptr(f_out), dt, nsteps), self.h)
 
     def kernel_launches(self):
         return _lib.vlb_kernel_launches(self.h)
