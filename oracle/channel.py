@@ -1,0 +1,212 @@
+"""Gradually expanding channel stage in the vielbein frame (oracle; test infrastructure only).
+
+Sec. VII.A-B.  Coordinates lambda = x / (1 + phi(xi)), xi = y; the wall is at
+lambda = H/2 = 1 and only the upper half 0 < lambda < 1 is simulated.
+Momenta (p^lambda-hat, p^xi-hat) in the orthogonal triad of Eq. (canalie_phat):
+half-range Gauss-Hermite on the wall-normal axis (index i), full range on the
+tangential axis (index j).
+
+Eq. (canalie_boltz) in the chi form, with V^lambda = a p^lambda,
+a = sqrt(1 + lambda^2 phi'^2) / (1 + phi), and V^xi = b p^xi - c p^lambda,
+b = (1 + phi) / sqrt(1 + lambda^2 phi'^2), c = lambda phi' b (Eq. canalie_V),
+d chi^xi = (1 + phi) d xi (Eq. chi_canalie, closed form Eq. chi_canalie_exp):
+
+  L[f] = -[a_{s+1/2} p^l F_{s+1/2} - a_{s-1/2} p^l F_{s-1/2}] / d lambda_s
+         -[V^xi_{p+1/2} F_{p+1/2} - V^xi_{p-1/2} F_{p-1/2}] / d chi^xi_p
+         + G_lxx [(p^xi)^2 K^l f - p^l K~^xi f] - G_lxl [(p^l)^2 K^xi f - p^xi K~^l f]
+         - (f - f_eq) / tau,
+
+with the discrete connection coefficients of Sec. VII.A (Gamma_{l x l} and
+Gamma_{l x x} built from interface values so that f = const is an exact
+solution) and tau = Kn / (n T) (Eq. canalie_tau).  The sign of the force
+term follows from Eq. (boltz_noncons) with Gamma_{x l l} = -Gamma_{l x l}.
+
+Boundaries:
+* centreline lambda = 0: specular reflection, ghosts f_{1-k, i} = f_{k, ibar}
+  with p_ibar = -p_i (Sec. VII.C.3);
+* wall lambda = 1: diffuse reflection at rest and T_0, per-column n_w from the
+  zero-mass-flux balance, outgoing ghosts by quadratic extrapolation
+  (Sec. VII.C.4, Eqs. extrapol, weno_populate);
+* inlet and outlet: the paper prescribes parabolic flow-rate profiles
+  (Sec. VII.C.1-2); the pressure-ratio workload is read here as two particle
+  reservoirs.  Per (row, momentum), the populations entering the domain
+  (V^xi > 0 at the inlet, V^xi < 0 at the outlet) see ghosts
+  f_eq(n_res, (0, u_x), T_0), with u_x the u^xi of the adjacent cell; those
+  leaving see ghosts equal to the adjacent cell (zeroth-order extrapolation,
+  as the paper does for its inlet).
+
+Array layout: F has shape (2, N_lambda, N_xi, nq0, nq1).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .lbmodel import Model
+from .weno import weno5
+
+
+def phi(xi, re_c=100.0):
+    """Eq. (canalie_phi) with H = 2."""
+    return 0.5 * (math.tanh(2.0) - np.tanh(2.0 - 30.0 * np.asarray(xi) / re_c))
+
+
+def dphi(xi, re_c=100.0):
+    return 0.5 * (30.0 / re_c) / np.cosh(2.0 - 30.0 * np.asarray(xi) / re_c) ** 2
+
+
+def chi_xi(xi, re_c=100.0):
+    """Eq. (chi_canalie_exp) with H = 2 (chi = 0 at xi = 0)."""
+    xi = np.asarray(xi, dtype=np.float64)
+    return (1.0 + math.tanh(2.0) / 2.0) * xi + re_c / 60.0 * np.log(np.cosh(2.0 - 30.0 * xi / re_c) / math.cosh(2.0))
+
+
+class ChannelGrid:
+    """N_lambda x N_xi cells; lambda(eta) = tanh(eta) / A (Eq. canalie_stretch, H/2 = 1),
+    eta equidistant on [0, artanh A]; xi equidistant on [xi_in, xi_out]."""
+
+    def __init__(self, n_lambda, n_xi, xi_in=-10.0, xi_out=40.0, re_c=100.0, A=0.95):
+        self.nl, self.nx, self.re_c, self.A = n_lambda, n_xi, re_c, A
+        ea = math.atanh(A)
+        self.lf = np.tanh(np.arange(n_lambda + 1) / n_lambda * ea) / A  # interfaces lambda_{s+1/2}
+        self.lf[-1] = 1.0
+        self.lc = np.tanh((np.arange(1, n_lambda + 1) - 0.5) / n_lambda * ea) / A
+        self.dl = self.lf[1:] - self.lf[:-1]
+        self.xf = xi_in + (xi_out - xi_in) * np.arange(n_xi + 1) / n_xi
+        self.xc = xi_in + (xi_out - xi_in) * (np.arange(1, n_xi + 1) - 0.5) / n_xi
+        self.dchi = chi_xi(self.xf[1:], re_c) - chi_xi(self.xf[:-1], re_c)
+        phc, dpc = phi(self.xc, re_c), dphi(self.xc, re_c)
+        phf, dpf = phi(self.xf, re_c), dphi(self.xf, re_c)
+        # lambda-interfaces (s+1/2, p): a = sqrt(1 + lambda^2 phi'^2) / (1 + phi), shape (nl+1, nx)
+        self.a = np.sqrt(1.0 + self.lf[:, None] ** 2 * dpc[None, :] ** 2) / (1.0 + phc[None, :])
+        # xi-interfaces (s, p+1/2): b, c, shape (nl, nx+1)
+        root = np.sqrt(1.0 + self.lc[:, None] ** 2 * dpf[None, :] ** 2)
+        self.b = (1.0 + phf[None, :]) / root
+        self.c = self.lc[:, None] * dpf[None, :] * (1.0 + phf[None, :]) / root
+        # discrete connection coefficients per cell (Sec. VII.A), shape (nl, nx)
+        self.G_lxl = (self.b[:, 1:] - self.b[:, :-1]) / self.dchi[None, :]
+        self.G_lxx = -(self.a[1:, :] - self.a[:-1, :]) / self.dl[:, None] + (self.c[:, 1:] - self.c[:, :-1]) / self.dchi[None, :]
+        self.vol = self.dl[:, None] * self.dchi[None, :]
+
+
+class ChannelOracle:
+    def __init__(self, model, grid: ChannelGrid, kn, n_in=2.0, n_out=1.0, T0=1.0):
+        self.m = model if isinstance(model, Model) else Model(model)
+        self.g = grid
+        self.kn, self.n_in, self.n_out, self.T0 = kn, n_in, n_out, T0
+        Q = self.m.spec[0][2]
+        nq0 = self.m.nq[0]
+        self.ibar = np.where(np.arange(nq0) < Q, np.arange(nq0) + Q, np.arange(nq0) - Q)
+        self.last_nw = None
+
+    def feq_cells(self, n, u0, u1, T):
+        """f_eq per cell for arrays of any shape S -> (2,) + S + (nq0, nq1)."""
+        shape = np.shape(n)
+        f1, f2 = self.m.feq(np.ravel(n), np.ravel(u0), np.ravel(u1), np.ravel(T))
+        return np.stack([f1, f2]).reshape((2,) + shape + f1.shape[1:])
+
+    def initial_state(self, n_profile=None, T0=None):
+        g = self.g
+        T0 = self.T0 if T0 is None else T0
+        if n_profile is None:
+            x = (g.xc - g.xf[0]) / (g.xf[-1] - g.xf[0])
+            n_profile = self.n_in + (self.n_out - self.n_in) * x
+        n = np.broadcast_to(n_profile[None, :], (g.nl, g.nx))
+        z = np.zeros((g.nl, g.nx))
+        return self.feq_cells(n, z, z, np.full((g.nl, g.nx), T0))
+
+    def moments(self, F):
+        nl, nx = F.shape[1], F.shape[2]
+        flat = F.reshape((2, nl * nx) + F.shape[3:])
+        return tuple(x.reshape(nl, nx) for x in self.m.moments(flat))
+
+    def L(self, F):
+        m, g = self.m, self.g
+        nl, nx = g.nl, g.nx
+        pl, px = m.p[0], m.p[1]  # p^lambda-hat (half range), p^xi-hat (full range)
+        PL = pl[:, None]
+        PX = px[None, :]
+
+        n, ul, ux, T = self.moments(F)
+        Feq = self.feq_cells(n, ul, ux, T)
+        tau = self.kn / (n * T)
+
+        # ---- lambda direction: G[:, s+2, p] holds cell s (1-based), s = -2 .. nl+3
+        Gl = np.zeros((2, nl + 6, nx) + F.shape[3:])
+        Gl[:, 3:nl + 3] = F
+        # centreline: specular, ghost 1-k mirrors cell k
+        for k in (1, 2, 3):
+            Gl[:, 3 - k] = F[:, k - 1][:, :, self.ibar, :]
+        # wall: outgoing (p^lambda > 0) quadratic extrapolation, flux, n_w per column, incoming equilibrium
+        pos = pl > 0
+        FN, FN1, FN2 = F[:, nl - 1], F[:, nl - 2], F[:, nl - 3]
+        e1 = 3 * FN - 3 * FN1 + FN2
+        e2 = 6 * FN - 8 * FN1 + 3 * FN2
+        flux_w = weno5(FN2, FN1, FN, e1, e2)  # (2, nx, nq0, nq1), valid for p^lambda > 0
+        weq = self.feq_cells(np.ones(1), np.zeros(1), np.zeros(1), np.full(1, self.T0))[:, 0]
+        den = (weq[0][~pos] * PL[~pos]).sum()
+        num = (flux_w[0][:, pos] * PL[pos][None]).sum(axis=(1, 2))
+        nw = -num / den  # (nx,)
+        self.last_nw = nw
+        for k, e in ((1, e1), (2, e2), (3, e2)):
+            inc = nw[None, :, None, None] * weq[:, None]  # (2, nx, nq0, nq1)
+            Gl[:, nl + 2 + k] = np.where(pos[None, None, :, None], e, inc)
+        jl = np.arange(2, nl + 3)  # interfaces s+1/2, s = 0..nl, between Gl[j] and Gl[j+1]
+        upl = weno5(Gl[:, jl - 2], Gl[:, jl - 1], Gl[:, jl], Gl[:, jl + 1], Gl[:, jl + 2])
+        dnl = weno5(Gl[:, jl + 3], Gl[:, jl + 2], Gl[:, jl + 1], Gl[:, jl], Gl[:, jl - 1])
+        Fl_ = np.where((pl >= 0)[None, None, None, :, None], upl, dnl)  # (2, nl+1, nx, nq0, nq1)
+        fluxl = g.a[None, :, :, None, None] * PL[None, None, None] * Fl_
+        adv = (fluxl[:, 1:] - fluxl[:, :-1]) / g.dl[None, :, None, None, None]
+
+        # ---- xi direction: H[:, s, p+2] holds cell p (1-based), p = -2 .. nx+3
+        Vx = g.b[:, :, None, None] * PX[None, None] - g.c[:, :, None, None] * PL[None, None]  # (nl, nx+1, nq0, nq1)
+        Hx = np.zeros((2, nl, nx + 6) + F.shape[3:])
+        Hx[:, :, 3:nx + 3] = F
+        f_in = self.feq_cells(np.full(nl, self.n_in), np.zeros(nl), ux[:, 0], np.full(nl, self.T0))  # (2, nl, nq0, nq1)
+        f_out = self.feq_cells(np.full(nl, self.n_out), np.zeros(nl), ux[:, -1], np.full(nl, self.T0))
+        into_in = Vx[:, 0] > 0  # (nl, nq0, nq1)
+        into_out = Vx[:, nx] < 0
+        for k in (0, 1, 2):
+            Hx[:, :, k] = np.where(into_in[None], f_in, F[:, :, 0])
+            Hx[:, :, nx + 3 + k] = np.where(into_out[None], f_out, F[:, :, nx - 1])
+        jx = np.arange(2, nx + 3)
+        upx = weno5(Hx[:, :, jx - 2], Hx[:, :, jx - 1], Hx[:, :, jx], Hx[:, :, jx + 1], Hx[:, :, jx + 2])
+        dnx = weno5(Hx[:, :, jx + 3], Hx[:, :, jx + 2], Hx[:, :, jx + 1], Hx[:, :, jx], Hx[:, :, jx - 1])
+        Fx = np.where((Vx >= 0)[None], upx, dnx)  # (2, nl, nx+1, nq0, nq1)
+        fluxx = Vx[None] * Fx
+        adv = adv + (fluxx[:, :, 1:] - fluxx[:, :, :-1]) / g.dchi[None, None, :, None, None]
+
+        # ---- inertial force with the discrete connection coefficients
+        Kl, Ktl = m.K[0], m.Kt[0]
+        Kx, Ktx = m.K[1], m.Kt[1]
+        dl_f = np.einsum("ik,dspkj->dspij", Kl, F)    # d/dp^l f
+        dlp_f = np.einsum("ik,dspkj->dspij", Ktl, F)  # d/dp^l (p^l f)
+        dx_f = np.einsum("jk,dspik->dspij", Kx, F)    # d/dp^x f
+        dxp_f = np.einsum("jk,dspik->dspij", Ktx, F)  # d/dp^x (p^x f)
+        Glxx = g.G_lxx[None, :, :, None, None]
+        Glxl = g.G_lxl[None, :, :, None, None]
+        PLb, PXb = PL[None, None, None], PX[None, None, None]
+        force = Glxx * (PXb ** 2 * dl_f - PLb * dxp_f) - Glxl * (PLb ** 2 * dx_f - PXb * dlp_f)
+
+        coll = -(F - Feq) / tau[None, :, :, None, None]
+        self.last_boundary_flux = dict(
+            inlet=(g.dl[:, None, None] * fluxx[0, :, 0]).sum(), outlet=(g.dl[:, None, None] * fluxx[0, :, nx]).sum(),
+            wall=(g.dchi[:, None, None] * fluxl[0, nl]).sum(), centre=(g.dchi[:, None, None] * fluxl[0, 0]).sum())
+        return -adv + force + coll
+
+    def stage(self, k, dt, F_l, F_prev):
+        Lp = self.L(F_prev)
+        if k == 1:
+            return F_l + dt * Lp
+        if k == 2:
+            return 0.75 * F_l + 0.25 * F_prev + 0.25 * dt * Lp
+        return F_l / 3.0 + 2.0 / 3.0 * F_prev + 2.0 / 3.0 * dt * Lp
+
+    def step(self, F, dt):
+        F1 = self.stage(1, dt, F, F)
+        F2 = self.stage(2, dt, F, F1)
+        return self.stage(3, dt, F, F2)
+
+    def n_tot(self, F):
+        return float((self.g.vol * F[0].sum(axis=(2, 3))).sum())

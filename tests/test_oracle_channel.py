@@ -1,0 +1,64 @@
+"""Pins of the oracle's gradually-expanding-channel stage (Sec. VII.A-C)."""
+import math
+
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+from oracle.channel import ChannelGrid, ChannelOracle, chi_xi, dphi, phi
+from paper_1708_05944_gb300.inputs import perturbation
+
+MODEL = "HH(4;8)xH(4;12)"
+
+
+def test_wall_shape_limits_and_chi_closed_form():
+    # phi(-inf) = (tanh 2 - 1)/2 ~ -0.018, phi(+inf) = (tanh 2 + 1)/2 ~ 0.982, phi(0) = 0 (Sec. VII.B)
+    assert phi(-1e4) == pytest.approx((math.tanh(2) - 1) / 2, abs=1e-15)
+    assert phi(1e4) == pytest.approx((math.tanh(2) + 1) / 2, abs=1e-15)
+    assert phi(0.0) == pytest.approx(0.0, abs=1e-16)
+    # Eq. (chi_canalie_exp) against a numerical integral of d chi = (1 + phi) d xi
+    for x in (-10.0, -3.0, 5.0, 17.0, 40.0):
+        num = quad(lambda t: 1.0 + phi(t), 0.0, x, epsabs=1e-13, epsrel=1e-13)[0]
+        assert chi_xi(x) == pytest.approx(num, rel=1e-11, abs=1e-12)
+    # phi' by central differences
+    h = 1e-5
+    for x in (-2.0, 3.0, 10.0):
+        assert dphi(x) == pytest.approx((phi(x + h) - phi(x - h)) / (2 * h), rel=1e-7)
+
+
+def test_stretched_lambda_grid():
+    g = ChannelGrid(16, 8)
+    assert g.lf[0] == 0.0 and g.lf[-1] == 1.0 and np.all(np.diff(g.lf) > 0)
+    # finer near the wall (A = 0.95 pushes points to lambda = 1)
+    assert g.dl[-1] < g.dl[0]
+
+
+@pytest.mark.parametrize("nl,nx", [(8, 16), (6, 10)])
+def test_uniform_rest_state_is_exact(nl, nx):
+    # f = f_eq(1, 0, 1) everywhere with both reservoirs at n = 1: the discrete connection
+    # coefficients of Sec. VII.A make the constant state an exact solution
+    o = ChannelOracle(MODEL, ChannelGrid(nl, nx), 0.05, n_in=1.0, n_out=1.0)
+    F = o.initial_state()
+    assert np.abs(o.L(F)).max() < 1e-13
+    np.testing.assert_allclose(o.last_nw, 1.0, rtol=0, atol=1e-14)
+
+
+def test_particle_balance_is_telescoping():
+    # sum over cells of vol * L[f'] equals inlet minus outlet flux: the wall flux vanishes
+    # by n_w, the centreline flux by specular symmetry, force and collision carry no mass
+    o = ChannelOracle(MODEL, ChannelGrid(8, 12), 0.05)
+    F = o.initial_state()
+    F = F * perturbation(F.shape, seed=4, amplitude=0.02)
+    L = o.L(F)
+    b = o.last_boundary_flux
+    dN = float((o.g.vol * L[0].sum(axis=(2, 3))).sum())
+    assert abs(b["wall"]) < 1e-14 and abs(b["centre"]) < 1e-14
+    assert dN == pytest.approx(b["inlet"] - b["outlet"], rel=1e-9, abs=1e-14)
+
+
+def test_specular_centreline_keeps_mirror_symmetry_of_rest():
+    # a state even in p^lambda stays even-balanced: the centreline flux of f' vanishes
+    o = ChannelOracle(MODEL, ChannelGrid(6, 8), 0.1)
+    F = o.initial_state()
+    o.L(F)
+    assert abs(o.last_boundary_flux["centre"]) < 1e-15
