@@ -78,6 +78,16 @@ typedef struct {
   double stretch_A, stretch_delta;
 } vlb_couette_grid;
 
+/* Gradually expanding channel grid (Sec. VII.A-B, H/2 = 1): n_lambda cells in
+ * the wall-normal coordinate lambda in [0, 1], stretched as
+ * lambda = tanh(eta) / stretch_A with eta equidistant (Eq. canalie_stretch),
+ * times n_xi equidistant cells in xi in [xi_in, xi_out]; wall shape
+ * phi(xi) of Eq. (canalie_phi) with parameter re_c. */
+typedef struct {
+  int n_lambda, n_xi;
+  double xi_in, xi_out, re_c, stretch_A;
+} vlb_channel_grid;
+
 /* Wall of a Couette instance: tangential velocity u^phi (= Omega R) and temperature. */
 typedef struct {
   double u_tangential;
@@ -114,6 +124,26 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
                               const vlb_couette_grid* grids, const vlb_wall* inner,
                               const vlb_wall* outer, const double* kn, const int* tau_mode,
                               void* cuda_stream, vlb_ctx** out);
+
+/* Create a gradually expanding channel context (Sec. VII): the upper half of
+ * the channel in the vielbein frame of Eq. (canalie_phat), Eq. (canalie_boltz)
+ * in the chi form with the discrete connection coefficients of Sec. VII.A
+ * and tau = Kn / (n T) (Eq. canalie_tau).  Boundaries: specular reflection at
+ * lambda = 0, diffuse reflection at rest and temperature T0 at lambda = 1
+ * with a zero-mass-flux density n_w per column (Eq. nw), and particle
+ * reservoirs at both ends: populations entering the domain see
+ * f_eq(n_in or n_out, (0, u^xi of the adjacent cell), T0), those leaving
+ * see the adjacent cell (zeroth-order extrapolation).  Cell (s, p) is cell
+ * index p * n_lambda + s of the distribution layout.  Axis 0 must be half
+ * range; kernels exist for 16 x 12 and 8 x 4 nodes (VLB_ERR_UNSUPPORTED
+ * otherwise); n_lambda >= 3, n_xi >= 4.  Starts at f_eq(1, 0, T0). */
+vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const vlb_channel_grid* grid, double kn,
+                              double n_in, double n_out, double T0, void* cuda_stream, vlb_ctx** out);
+
+/* Launch shapes of a channel context's stage kernel: cells per tile along
+ * lambda (ts) and xi (tp) and threads per CTA; returns their number (0 for
+ * Couette contexts, negative on error). */
+int vlb_channel_variants(const vlb_ctx* ctx, int* ts, int* tp, int* nt, int max);
 
 /* Total number of cells over all instances, nodes per cell (nq0 * nq1), and
  * the size in bytes of one distribution copy in the layout documented above. */
@@ -153,7 +183,8 @@ vlb_status vlb_set_dt(vlb_ctx* ctx, const double* dt);
 vlb_status vlb_read_moments(vlb_ctx* ctx, double* n, double* u0, double* u1, double* T,
                             double* Tab, double* q, int on_device);
 
-/* Wall densities n_w (Eq. nw) of the last stage: 2 per instance (inner, outer). */
+/* Wall densities n_w (Eq. nw) of the last stage: 2 per instance (inner, outer)
+ * for Couette contexts, one per xi column for the channel. */
 vlb_status vlb_wall_density(vlb_ctx* ctx, double* nw);
 
 /* Steady-state norms of Eq. (msites_steady) between the current moments and

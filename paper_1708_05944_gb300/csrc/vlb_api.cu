@@ -123,6 +123,30 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   return VLB_OK;
 }
 
+template <typename real>
+vlb_status do_chan_stage(vlb_ctx* c, int k, int prev, int out) {
+  ChanArgs<real> a{};
+  a.Fprev = static_cast<const real*>(c->F[prev]);
+  a.Fl = static_cast<const real*>(c->F[c->cur]);
+  a.Fout = static_cast<real*>(c->F[out]);
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0}, cc[3] = {1.0, 0.25, 2.0 / 3.0};
+  a.ca = ca[k - 1], a.cb = cb[k - 1], a.cc = cc[k - 1];
+  a.caf = float(a.ca), a.cbf = float(a.cb), a.ccf = float(a.cc);
+  a.cd = c->cdesc;
+  a.cd.dt = c->inst[0].dt;
+  a.cd.dtf = float(a.cd.dt);
+  a.geo = c->d_cgeo;
+  a.geof = c->d_cgeof;
+  a.nw = c->d_nw;
+  a.err = c->d_err;
+  a.max_polls = 1ull << 26;
+  const void* kb = sizeof(real) == 4 ? (const void*)c->chanK32.data() : (const void*)c->chanK64.data();
+  cudaError_t e = launch_channel<real>(c->cvariants[c->variant], a, c->margs, kb, c->nq0, c->nq1, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "channel stage kernel launch");
+  c->launches += 1;
+  return VLB_OK;
+}
+
 vlb_status run_stage(vlb_ctx* c, int k) {
   // buffers: cur = F_l; stage 1 -> (cur+1); stage 2 reads (cur+1) -> (cur+2); stage 3 reads (cur+2) -> (cur+1)
   const int b1 = (c->cur + 1) % 3, b2 = (c->cur + 2) % 3;
@@ -134,7 +158,11 @@ vlb_status run_stage(vlb_ctx* c, int k) {
   } else {
     prev = b2, out = b1;
   }
-  vlb_status st = c->prec == VLB_FP64 ? do_stage<double>(c, k, prev, out) : do_stage<float>(c, k, prev, out);
+  vlb_status st;
+  if (c->kind == 1)
+    st = c->prec == VLB_FP64 ? do_chan_stage<double>(c, k, prev, out) : do_chan_stage<float>(c, k, prev, out);
+  else
+    st = c->prec == VLB_FP64 ? do_stage<double>(c, k, prev, out) : do_stage<float>(c, k, prev, out);
   if (st != VLB_OK) return st;
   c->last = out;
   c->stage_done = k;
@@ -400,6 +428,146 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   return VLB_OK;
 }
 
+vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const vlb_channel_grid* grid, double kn,
+                              double n_in, double n_out, double T0, void* cuda_stream, vlb_ctx** out) {
+  if (!model || !grid || !out) return fail(nullptr, VLB_ERR_INVALID, "null argument");
+  *out = nullptr;
+  std::string why;
+  if (!valid_model(model, &why)) return fail(nullptr, VLB_ERR_INVALID, why);
+  if (prec != VLB_FP64 && prec != VLB_FP32_BULK) return fail(nullptr, VLB_ERR_INVALID, "bad precision");
+  if (model->kind[0] != VLB_HALF) return fail(nullptr, VLB_ERR_INVALID, "the wall-normal axis must be half range");
+  const int nl = grid->n_lambda, nx = grid->n_xi;
+  if (nl < 3 || nx < 4) return fail(nullptr, VLB_ERR_INVALID, "need n_lambda >= 3 and n_xi >= 4");
+  if (!(grid->xi_out > grid->xi_in) || !(grid->re_c > 0.0) || !(grid->stretch_A > 0.0 && grid->stretch_A < 1.0))
+    return fail(nullptr, VLB_ERR_INVALID, "need xi_in < xi_out, re_c > 0, 0 < stretch_A < 1");
+  if (!(kn > 0.0) || !(n_in > 0.0) || !(n_out > 0.0) || !(T0 > 0.0))
+    return fail(nullptr, VLB_ERR_INVALID, "need Kn, reservoir densities and T0 positive");
+  const int nq0 = axis_nodes(model, 0), nq1 = axis_nodes(model, 1);
+  std::unique_ptr<vlb_ctx> c(new vlb_ctx);
+  c->kind = 1;
+  c->model = *model;
+  c->prec = prec;
+  c->n_inst = 1;
+  c->stream = static_cast<cudaStream_t>(cuda_stream);
+  {
+    ChanVariant all[8];
+    const int n = channel_variants(nq0, nq1, all);
+    for (int i = 0; i < n; ++i) {
+      const size_t sm = prec == VLB_FP64 ? channel_smem_bytes<double>(all[i], nq0, nq1)
+                                         : channel_smem_bytes<float>(all[i], nq0, nq1);
+      if (sm > 0 && sm <= 227 * 1024 && nx % all[i].tp == 0) c->cvariants[c->n_cvariants++] = all[i];
+    }
+    if (c->n_cvariants == 0)
+      return fail(nullptr, VLB_ERR_UNSUPPORTED, "no channel kernel for this velocity set and n_xi (16x12 or 8x4 nodes)");
+  }
+  for (int a = 0; a < 2; ++a)
+    if (!build_axis(model->kind[a] == VLB_HALF ? 1 : 0, model->N[a], model->Q[a], &c->ax[a], &why))
+      return fail(nullptr, VLB_ERR_INVALID, why);
+  c->nq0 = nq0;
+  c->nq1 = nq1;
+  c->V = nq0 * nq1;
+  c->Vp = (c->V + 3) / 4 * 4;
+  c->esize = prec == VLB_FP64 ? 8 : 4;
+  ModelArgs& m = c->margs;
+  m.nq0 = nq0, m.nq1 = nq1, m.N0 = model->N[0], m.N1 = model->N[1];
+  m.kind0 = 1, m.kind1 = model->kind[1] == VLB_HALF ? 1 : 0;
+  for (int ax = 0; ax < 2; ++ax) {
+    const AxisTables& t = c->ax[ax];
+    const int N = model->N[ax];
+    for (int k = 0; k < t.nq; ++k) {
+      (ax ? m.p1 : m.p0)[k] = t.p[k];
+      (ax ? m.w1 : m.w0)[k] = t.w[k];
+      (ax ? m.iw1 : m.iw0)[k] = 1.0 / t.w[k];
+      (ax ? m.p1f : m.p0f)[k] = float(t.p[k]);
+      (ax ? m.iw1f : m.iw0f)[k] = float(1.0 / t.w[k]);
+      for (int s = 0; s <= N; ++s) {
+        (ax ? m.tab1 : m.tab0)[k * MAXN + s] = t.eqtab[k * (N + 1) + s];
+        (ax ? m.tab1f : m.tab0f)[k * MAXN + s] = float(t.eqtab[k * (N + 1) + s]);
+      }
+    }
+  }
+  {
+    std::vector<double> kd;
+    for (const std::vector<double>* v : {&c->ax[0].K, &c->ax[0].Kt, &c->ax[1].K, &c->ax[1].Kt})
+      kd.insert(kd.end(), v->begin(), v->end());
+    c->chanK64.resize(kd.size() * sizeof(double));
+    memcpy(c->chanK64.data(), kd.data(), c->chanK64.size());
+    std::vector<float> kf(kd.begin(), kd.end());
+    c->chanK32.resize(kf.size() * sizeof(float));
+    memcpy(c->chanK32.data(), kf.data(), c->chanK32.size());
+  }
+  // geometry (Sec. VII.A-B): lambda(eta) = tanh(eta) / A, eta equidistant; xi equidistant; H/2 = 1
+  const double A = grid->stretch_A, ea = atanh(A), re = grid->re_c;
+  auto phi = [&](double x) { return 0.5 * (tanh(2.0) - tanh(2.0 - 30.0 * x / re)); };
+  auto dphi = [&](double x) { const double ch = cosh(2.0 - 30.0 * x / re); return 0.5 * (30.0 / re) / (ch * ch); };
+  auto chi = [&](double x) { return (1.0 + tanh(2.0) / 2.0) * x + re / 60.0 * log(cosh(2.0 - 30.0 * x / re) / cosh(2.0)); };
+  std::vector<double> lf(nl + 1), lc(nl), xf(nx + 1), xc(nx);
+  for (int s = 0; s <= nl; ++s) lf[s] = tanh(double(s) / nl * ea) / A;
+  lf[nl] = 1.0;
+  for (int s = 0; s < nl; ++s) lc[s] = tanh((s + 0.5) / nl * ea) / A;
+  const double L = grid->xi_out - grid->xi_in;
+  for (int p = 0; p <= nx; ++p) xf[p] = grid->xi_in + L * p / nx;
+  for (int p = 0; p < nx; ++p) xc[p] = grid->xi_in + L * (p + 0.5) / nx;
+  std::vector<ChanCell<double>> gd(size_t(nl) * nx);
+  std::vector<ChanCell<float>> gf(size_t(nl) * nx);
+  for (int p = 0; p < nx; ++p) {
+    const double ph = phi(xc[p]), dp = dphi(xc[p]);
+    const double phm = phi(xf[p]), dpm = dphi(xf[p]), php = phi(xf[p + 1]), dpp = dphi(xf[p + 1]);
+    const double dchi = chi(xf[p + 1]) - chi(xf[p]);
+    for (int s = 0; s < nl; ++s) {
+      ChanCell<double> g{};
+      g.am = sqrt(1.0 + lf[s] * lf[s] * dp * dp) / (1.0 + ph);
+      g.ap = sqrt(1.0 + lf[s + 1] * lf[s + 1] * dp * dp) / (1.0 + ph);
+      const double rm = sqrt(1.0 + lc[s] * lc[s] * dpm * dpm), rp = sqrt(1.0 + lc[s] * lc[s] * dpp * dpp);
+      g.bm = (1.0 + phm) / rm;
+      g.bp = (1.0 + php) / rp;
+      g.cm = lc[s] * dpm * (1.0 + phm) / rm;
+      g.cp = lc[s] * dpp * (1.0 + php) / rp;
+      const double dl = lf[s + 1] - lf[s];
+      g.idl = 1.0 / dl;
+      g.idx = 1.0 / dchi;
+      g.glxl = (g.bp - g.bm) / dchi;
+      g.glxx = -(g.ap - g.am) / dl + (g.cp - g.cm) / dchi;
+      gd[size_t(p) * nl + s] = g;
+      const double* src = &g.am;
+      float* dst = &gf[size_t(p) * nl + s].am;
+      for (int k = 0; k < 12; ++k) dst[k] = float(src[k]);
+    }
+  }
+  ChanDesc& cd = c->cdesc;
+  cd.nl = nl, cd.nx = nx, cd.kn = kn, cd.n_in = n_in, cd.n_out = n_out, cd.T0 = T0, cd.dt = 0.0;
+  cd.knf = float(kn), cd.n_inf = float(n_in), cd.n_outf = float(n_out), cd.T0f = float(T0), cd.dtf = 0.0f;
+  InstDesc d{};
+  d.cell0 = 0;
+  d.n_cells = nl * nx;
+  d.kn = kn;
+  d.kn_f = float(kn);
+  c->inst.push_back(d);
+  c->total_cells = (long long)nl * nx;
+  vlb_ctx* cp = c.get();
+  const size_t fbytes = size_t(c->total_cells) * 2 * c->Vp * c->esize;
+  for (int b = 0; b < 3; ++b) {
+    VLB_CUDA(cp, cudaMalloc(&c->F[b], fbytes));
+    VLB_CUDA(cp, cudaMemsetAsync(c->F[b], 0, fbytes, c->stream));
+  }
+  VLB_CUDA(cp, cudaMalloc(&c->d_inst, sizeof(InstDesc)));
+  VLB_CUDA(cp, cudaMalloc(&c->d_nw, sizeof(double) * nx));
+  VLB_CUDA(cp, cudaMalloc(&c->d_err, sizeof(unsigned)));
+  VLB_CUDA(cp, cudaMalloc(&c->d_mom, sizeof(double) * 9 * c->total_cells));
+  VLB_CUDA(cp, cudaMalloc(&c->d_cgeo, sizeof(ChanCell<double>) * gd.size()));
+  VLB_CUDA(cp, cudaMalloc(&c->d_cgeof, sizeof(ChanCell<float>) * gf.size()));
+  VLB_CUDA(cp, cudaMemcpy(c->d_inst, c->inst.data(), sizeof(InstDesc), cudaMemcpyHostToDevice));
+  VLB_CUDA(cp, cudaMemcpy(c->d_cgeo, gd.data(), sizeof(ChanCell<double>) * gd.size(), cudaMemcpyHostToDevice));
+  VLB_CUDA(cp, cudaMemcpy(c->d_cgeof, gf.data(), sizeof(ChanCell<float>) * gf.size(), cudaMemcpyHostToDevice));
+  VLB_CUDA(cp, cudaMemsetAsync(c->d_nw, 0, sizeof(double) * nx, c->stream));
+  VLB_CUDA(cp, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+  VLB_CUDA(cp, cudaStreamSynchronize(c->stream));
+  vlb_status st = vlb_init_equilibrium(cp, 1.0, 0.0, 0.0, T0);
+  if (st != VLB_OK) return st;
+  *out = c.release();
+  return VLB_OK;
+}
+
 vlb_status vlb_sizes(const vlb_ctx* c, long long* total_cells, int* nvel, long long* f_bytes) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
   if (total_cells) *total_cells = c->total_cells;
@@ -410,6 +578,7 @@ vlb_status vlb_sizes(const vlb_ctx* c, long long* total_cells, int* nvel, long l
 
 vlb_status vlb_set_walls(vlb_ctx* c, const vlb_wall* inner, const vlb_wall* outer) {
   if (!c || !inner || !outer) return fail(c, VLB_ERR_INVALID, "null argument");
+  if (c->kind != 0) return fail(c, VLB_ERR_UNSUPPORTED, "walls are set at creation for the channel");
   for (int i = 0; i < c->n_inst; ++i) {
     if (!(inner[i].T > 0.0) || !(outer[i].T > 0.0)) return fail(c, VLB_ERR_INVALID, "wall temperature must be > 0");
     c->inst[i].u_in = inner[i].u_tangential;
@@ -561,12 +730,14 @@ vlb_status vlb_read_moments(vlb_ctx* c, double* n, double* u0, double* u1, doubl
 
 vlb_status vlb_wall_density(vlb_ctx* c, double* nw) {
   if (!c || !nw) return fail(c, VLB_ERR_INVALID, "null argument");
-  VLB_CUDA(c, cudaMemcpyAsync(nw, c->d_nw, sizeof(double) * 2 * c->n_inst, cudaMemcpyDeviceToHost, c->stream));
+  const size_t cnt = c->kind == 1 ? size_t(c->cdesc.nx) : size_t(2) * c->n_inst;
+  VLB_CUDA(c, cudaMemcpyAsync(nw, c->d_nw, sizeof(double) * cnt, cudaMemcpyDeviceToHost, c->stream));
   return check_err(c);
 }
 
 vlb_status vlb_residual(vlb_ctx* c, double* l2u, double* l2n, double* l2T) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (c->kind != 0) return fail(c, VLB_ERR_UNSUPPORTED, "steady-state norms are defined for Couette contexts");
   vlb_status st = compute_moments(c, c->d_mom);
   if (st != VLB_OK) return st;
   std::vector<double> res(3 * size_t(c->n_inst), 0.0);
@@ -647,8 +818,26 @@ vlb_status vlb_load(vlb_ctx* c, const char* path) {
   return VLB_OK;
 }
 
+int vlb_channel_variants(const vlb_ctx* c, int* ts, int* tp, int* nt, int max) {
+  if (!c) return VLB_ERR_INVALID;
+  if (c->kind != 1) return 0;
+  for (int v = 0; v < c->n_cvariants && v < max; ++v) {
+    if (ts) ts[v] = c->cvariants[v].ts;
+    if (tp) tp[v] = c->cvariants[v].tp;
+    if (nt) nt[v] = c->cvariants[v].nt;
+  }
+  return c->n_cvariants;
+}
+
 int vlb_variants(const vlb_ctx* c, int* tc, int* nt, int max) {
   if (!c) return VLB_ERR_INVALID;
+  if (c->kind == 1) {
+    for (int v = 0; v < c->n_cvariants && v < max; ++v) {
+      if (tc) tc[v] = c->cvariants[v].ts * c->cvariants[v].tp;
+      if (nt) nt[v] = c->cvariants[v].nt;
+    }
+    return c->n_cvariants;
+  }
   for (int v = 0; v < c->n_variants && v < max; ++v) {
     if (tc) tc[v] = c->variants[v].tc;
     if (nt) nt[v] = c->variants[v].nt;
@@ -658,9 +847,10 @@ int vlb_variants(const vlb_ctx* c, int* tc, int* nt, int max) {
 
 vlb_status vlb_set_variant(vlb_ctx* c, int v) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
-  if (v < 0 || v >= c->n_variants) return fail(c, VLB_ERR_INVALID, "no such launch shape");
+  if (v < 0 || v >= (c->kind == 1 ? c->n_cvariants : c->n_variants)) return fail(c, VLB_ERR_INVALID, "no such launch shape");
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->variant = v;
+  if (c->kind == 1) return VLB_OK;
   build_tiles(c);
   VLB_CUDA(c, cudaMemcpyAsync(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * c->tiles.size(),
                               cudaMemcpyHostToDevice, c->stream));
@@ -680,7 +870,8 @@ vlb_status vlb_autotune(vlb_ctx* c, double dt, int reps, int* chosen, double* be
   int best = 0;
   float best_t = 1e30f;
   const int keep_last = c->last;
-  for (int v = 0; v < c->n_variants; ++v) {
+  const int nvar = c->kind == 1 ? c->n_cvariants : c->n_variants;
+  for (int v = 0; v < nvar; ++v) {
     st = vlb_set_variant(c, v);
     if (st != VLB_OK) break;
     // stage 1 only reads F_l and writes the scratch buffer F^(1): the state is unchanged
@@ -718,6 +909,8 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_tiles);
   cudaFree(c->d_geo);
   cudaFree(c->d_geof);
+  cudaFree(c->d_cgeo);
+  cudaFree(c->d_cgeof);
   cudaFree(c->d_nw);
   cudaFree(c->d_err);
   cudaFree(c->d_mom);

@@ -9,11 +9,13 @@
 #include "../../include/vlb.h"
 #include "vlb_launch.h"
 #include "vlb_stage.cuh"
+#include "vlb_channel.cuh"
 #include "vlb_tables.h"
 
 using namespace vlb;
 
 struct vlb_ctx {
+  int kind = 0;  // 0 circular Couette instances, 1 gradually expanding channel
   vlb_model model{};
   int prec = 0;
   int n_inst = 0;
@@ -47,6 +49,13 @@ struct vlb_ctx {
   double* d_res = nullptr;
   bool have_prev = false;
   size_t tile_cap = 0;
+  // channel
+  ChanDesc cdesc{};
+  ChanVariant cvariants[8];
+  int n_cvariants = 0;
+  ChanCell<double>* d_cgeo = nullptr;
+  ChanCell<float>* d_cgeof = nullptr;
+  std::vector<unsigned char> chanK32, chanK64;
   long long launches = 0;
   long long steps = 0;
   std::string err;

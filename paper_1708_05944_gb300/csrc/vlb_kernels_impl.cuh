@@ -1,7 +1,9 @@
 // Kernels and launchers instantiated once per precision by vlb_f32.cu / vlb_f64.cu.
 #pragma once
+#include <cstring>
 #include "vlb_launch.h"
 #include "vlb_stage.cuh"
+#include "vlb_channel.cuh"
 
 namespace vlb {
 
@@ -103,6 +105,57 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
     VLB_CASE(SH_GENERIC, 8, 256, MAXQ, MAXQ, false)
   }
 #undef VLB_CASE
+  return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- channel dispatch
+template <typename real, int TS, int TP, int Q0, int Q1, int NT>
+static cudaError_t go_channel(const ChanArgs<real>& a, const ModelArgs& m, const void* kbytes, cudaStream_t s) {
+  using L = ChanSmem<real, TS, TP, Q0, Q1, NT>;
+  auto kern = channel_stage_kernel<real, TS, TP, Q0, Q1, NT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::bytes));
+  if (e != cudaSuccess) return e;
+  ChanK<real, Q0, Q1> k;
+  memcpy(&k, kbytes, sizeof(k));
+  const int nts = (a.cd.nl + TS - 1) / TS;
+  const int blocks = nts * (a.cd.nx / TP);
+  kern<<<blocks, NT, L::bytes, s>>>(a, m, k);
+  return cudaGetLastError();
+}
+
+#ifdef VLB_DEFINE_SHARED
+static const ChanVariant kChanVariants[] = {{4, 2, 192}, {2, 4, 192}, {4, 4, 192}, {8, 2, 192}, {4, 2, 384}};
+
+int channel_variants(int nq0, int nq1, ChanVariant* out) {
+  if (!((nq0 == 16 && nq1 == 12) || (nq0 == 8 && nq1 == 4))) return 0;
+  const int n = int(sizeof(kChanVariants) / sizeof(ChanVariant));
+  for (int i = 0; i < n; ++i) out[i] = kChanVariants[i];
+  return n;
+}
+#endif
+
+template <typename real>
+size_t channel_smem_bytes(ChanVariant v, int nq0, int nq1) {
+#define VLB_CSM(TS_, TP_, NT_)                                                       \
+  if (v.ts == TS_ && v.tp == TP_ && v.nt == NT_) {                                   \
+    if (nq0 == 16 && nq1 == 12) return ChanSmem<real, TS_, TP_, 16, 12, NT_>::bytes; \
+    if (nq0 == 8 && nq1 == 4) return ChanSmem<real, TS_, TP_, 8, 4, NT_>::bytes;     \
+  }
+  VLB_CSM(4, 2, 192) VLB_CSM(2, 4, 192) VLB_CSM(4, 4, 192) VLB_CSM(8, 2, 192) VLB_CSM(4, 2, 384)
+#undef VLB_CSM
+  return 0;
+}
+
+template <typename real>
+cudaError_t launch_channel(ChanVariant v, const ChanArgs<real>& a, const ModelArgs& m, const void* kbytes, int nq0,
+                           int nq1, cudaStream_t s) {
+#define VLB_CL(TS_, TP_, NT_)                                                                   \
+  if (v.ts == TS_ && v.tp == TP_ && v.nt == NT_) {                                              \
+    if (nq0 == 16 && nq1 == 12) return go_channel<real, TS_, TP_, 16, 12, NT_>(a, m, kbytes, s); \
+    if (nq0 == 8 && nq1 == 4) return go_channel<real, TS_, TP_, 8, 4, NT_>(a, m, kbytes, s);     \
+  }
+  VLB_CL(4, 2, 192) VLB_CL(2, 4, 192) VLB_CL(4, 4, 192) VLB_CL(8, 2, 192) VLB_CL(4, 2, 384)
+#undef VLB_CL
   return cudaErrorInvalidValue;
 }
 
@@ -223,6 +276,9 @@ template cudaError_t launch_stage<VLB_REAL>(StageVariant, const StageArgs<VLB_RE
                                             const KArgs<VLB_REAL>&, cudaStream_t);
 template cudaError_t launch_init_equilibrium<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, double, double,
                                                        double, double, cudaStream_t);
+template size_t channel_smem_bytes<VLB_REAL>(ChanVariant, int, int);
+template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_REAL>&, const ModelArgs&, const void*, int,
+                                              int, cudaStream_t);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,
                                               cudaStream_t);
 

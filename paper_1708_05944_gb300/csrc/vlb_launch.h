@@ -27,6 +27,22 @@ template <typename real>
 cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k,
                          cudaStream_t s);
 
+// Launch shapes of the channel stage kernel: cells per tile in lambda (ts) and xi (tp), threads.
+struct ChanVariant {
+  int ts, tp, nt;
+};
+template <typename real>
+struct ChanArgs;
+
+// Channel launch shapes for a model shape (at most 8); 0 if the shape has no channel kernel.
+int channel_variants(int nq0, int nq1, ChanVariant* out);
+template <typename real>
+size_t channel_smem_bytes(ChanVariant v, int nq0, int nq1);
+// kbytes points to the packed K0, Kt0 (nq0 x nq0) and K1, Kt1 (nq1 x nq1) tables in the bulk type.
+template <typename real>
+cudaError_t launch_channel(ChanVariant v, const ChanArgs<real>& a, const ModelArgs& m, const void* kbytes, int nq0,
+                           int nq1, cudaStream_t s);
+
 // f_eq(n0, (u0, u1), T0) in every cell.
 template <typename real>
 cudaError_t launch_init_equilibrium(real* F, long long cells, int Vp, const ModelArgs& m, double n0, double u0,

@@ -39,6 +39,11 @@ class vlb_couette_grid(C.Structure):
                 ("stretch_A", C.c_double), ("stretch_delta", C.c_double)]
 
 
+class vlb_channel_grid(C.Structure):
+    _fields_ = [("n_lambda", C.c_int), ("n_xi", C.c_int), ("xi_in", C.c_double), ("xi_out", C.c_double),
+                ("re_c", C.c_double), ("stretch_A", C.c_double)]
+
+
 class vlb_wall(C.Structure):
     _fields_ = [("u_tangential", C.c_double), ("T", C.c_double)]
 
@@ -51,6 +56,9 @@ EXPORTS = {
     "vlb_create_couette": (C.c_int, [C.POINTER(vlb_model), C.c_int, C.c_int, C.POINTER(vlb_couette_grid),
                                      C.POINTER(vlb_wall), C.POINTER(vlb_wall), C.POINTER(C.c_double),
                                      C.POINTER(C.c_int), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vlb_create_channel": (C.c_int, [C.POINTER(vlb_model), C.c_int, C.POINTER(vlb_channel_grid), C.c_double,
+                                     C.c_double, C.c_double, C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vlb_channel_variants": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "vlb_set_walls": (C.c_int, [C.c_void_p, C.POINTER(vlb_wall), C.POINTER(vlb_wall)]),
     "vlb_init_equilibrium": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]),
@@ -140,33 +148,8 @@ def vlb_axis_tables(model: vlb_model, axis: int):
     return p, w, K, Kt
 
 
-class Couette:
-    """A context of circular Couette instances (vlb_create_couette)."""
-
-    def __init__(self, model, precision, grids, inner, outer, kn, tau_mode, stream=None):
-        if isinstance(model, str):
-            model = vlb_parse_model(model)
-        self.model = model
-        self.precision = precision
-        n = len(grids)
-        G = (vlb_couette_grid * n)(*[vlb_couette_grid(g["n_cells"], g.get("r_in", 1.0), g.get("r_out", 2.0),
-                                                      g.get("stretch_A", 0.0), g.get("stretch_delta", 0.5))
-                                     for g in grids])
-        Wi = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in inner])
-        Wo = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in outer])
-        K = (C.c_double * n)(*kn)
-        T = (C.c_int * n)(*tau_mode)
-        h = C.c_void_p()
-        st = _lib.vlb_create_couette(C.byref(model), precision, n, G, Wi, Wo, K, T,
-                                     C.c_void_p(stream) if stream else None, C.byref(h))
-        _check(st)
-        self.h = h
-        self.n_inst = n
-        cells, nv, nb = C.c_longlong(), C.c_int(), C.c_longlong()
-        _check(_lib.vlb_sizes(h, C.byref(cells), C.byref(nv), C.byref(nb)), h)
-        self.total_cells, self.nvel, self.f_bytes = cells.value, nv.value, nb.value
-        self.nq = (vlb_axis_nodes(model, 0), vlb_axis_nodes(model, 1))
-        self.dtype = np.float64 if precision == VLB_FP64 else np.float32
+class _Context:
+    """Operations shared by every context kind (Couette instances, channel)."""
 
     def close(self):
         if getattr(self, "h", None):
@@ -176,14 +159,15 @@ class Couette:
     def __del__(self):
         self.close()
 
+    def _sizes(self):
+        cells, nv, nb = C.c_longlong(), C.c_int(), C.c_longlong()
+        _check(_lib.vlb_sizes(self.h, C.byref(cells), C.byref(nv), C.byref(nb)), self.h)
+        self.total_cells, self.nvel, self.f_bytes = cells.value, nv.value, nb.value
+        self.nq = (vlb_axis_nodes(self.model, 0), vlb_axis_nodes(self.model, 1))
+        self.dtype = np.float64 if self.precision == VLB_FP64 else np.float32
+
     def f_shape(self):
         return (self.total_cells, 2, self.nq[0], self.nq[1])
-
-    def set_walls(self, inner, outer):
-        n = self.n_inst
-        Wi = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in inner])
-        Wo = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in outer])
-        _check(_lib.vlb_set_walls(self.h, Wi, Wo), self.h)
 
     def init_equilibrium(self, n0=1.0, u0=0.0, u1=0.0, T0=1.0):
         _check(_lib.vlb_init_equilibrium(self.h, n0, u0, u1, T0), self.h)
@@ -217,16 +201,6 @@ class Couette:
         _check(_lib.vlb_read_moments(self.h, _ptr(n), _ptr(u0), _ptr(u1), _ptr(T), _ptr(Tab), _ptr(q), 0), self.h)
         return (n, u0, u1, T, Tab, q) if full else (n, u0, u1, T)
 
-    def wall_density(self):
-        nw = np.empty((self.n_inst, 2))
-        _check(_lib.vlb_wall_density(self.h, _ptr(nw)), self.h)
-        return nw
-
-    def residual(self):
-        a, b, c = (np.empty(self.n_inst) for _ in range(3))
-        _check(_lib.vlb_residual(self.h, _ptr(a), _ptr(b), _ptr(c)), self.h)
-        return a, b, c
-
     def save(self, path):
         _check(_lib.vlb_save(self.h, path.encode()), self.h)
 
@@ -254,3 +228,74 @@ class Couette:
 
     def kernel_launches(self):
         return _lib.vlb_kernel_launches(self.h)
+
+
+class Couette(_Context):
+    """A context of circular Couette instances (vlb_create_couette)."""
+
+    def __init__(self, model, precision, grids, inner, outer, kn, tau_mode, stream=None):
+        if isinstance(model, str):
+            model = vlb_parse_model(model)
+        self.model = model
+        self.precision = precision
+        n = len(grids)
+        G = (vlb_couette_grid * n)(*[vlb_couette_grid(g["n_cells"], g.get("r_in", 1.0), g.get("r_out", 2.0),
+                                                      g.get("stretch_A", 0.0), g.get("stretch_delta", 0.5))
+                                     for g in grids])
+        Wi = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in inner])
+        Wo = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in outer])
+        K = (C.c_double * n)(*kn)
+        T = (C.c_int * n)(*tau_mode)
+        h = C.c_void_p()
+        st = _lib.vlb_create_couette(C.byref(model), precision, n, G, Wi, Wo, K, T,
+                                     C.c_void_p(stream) if stream else None, C.byref(h))
+        _check(st)
+        self.h = h
+        self.n_inst = n
+        self._sizes()
+
+    def set_walls(self, inner, outer):
+        n = self.n_inst
+        Wi = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in inner])
+        Wo = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in outer])
+        _check(_lib.vlb_set_walls(self.h, Wi, Wo), self.h)
+
+    def wall_density(self):
+        nw = np.empty((self.n_inst, 2))
+        _check(_lib.vlb_wall_density(self.h, _ptr(nw)), self.h)
+        return nw
+
+    def residual(self):
+        a, b, c = (np.empty(self.n_inst) for _ in range(3))
+        _check(_lib.vlb_residual(self.h, _ptr(a), _ptr(b), _ptr(c)), self.h)
+        return a, b, c
+
+
+class Channel(_Context):
+    """A gradually expanding channel context (vlb_create_channel)."""
+
+    def __init__(self, model, precision, n_lambda, n_xi, kn, n_in=2.0, n_out=1.0, T0=1.0, xi_in=-10.0, xi_out=40.0,
+                 re_c=100.0, stretch_A=0.95, stream=None):
+        if isinstance(model, str):
+            model = vlb_parse_model(model)
+        self.model, self.precision = model, precision
+        g = vlb_channel_grid(n_lambda, n_xi, xi_in, xi_out, re_c, stretch_A)
+        h = C.c_void_p()
+        _check(_lib.vlb_create_channel(C.byref(model), precision, C.byref(g), kn, n_in, n_out, T0,
+                                       C.c_void_p(stream) if stream else None, C.byref(h)))
+        self.h = h
+        self.n_inst = 1
+        self.n_lambda, self.n_xi = n_lambda, n_xi
+        self._sizes()
+
+    def channel_variants(self):
+        ts, tp, nt = (np.zeros(8, dtype=np.int32) for _ in range(3))
+        n = _lib.vlb_channel_variants(self.h, _ptr(ts), _ptr(tp), _ptr(nt), 8)
+        if n < 0:
+            _check(n, self.h)
+        return [(int(ts[i]), int(tp[i]), int(nt[i])) for i in range(n)]
+
+    def wall_density(self):
+        nw = np.empty(self.n_xi)
+        _check(_lib.vlb_wall_density(self.h, _ptr(nw)), self.h)
+        return nw

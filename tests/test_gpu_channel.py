@@ -1,0 +1,120 @@
+"""GPU parity of the gradually-expanding-channel RK3 stage (libvlb through the C ABI)
+against the fp64 CPU oracle on the same seeded inputs (FP64 path within 1e-12,
+FP32-bulk moments within 1e-5), plus the exact rest state at the full
+2048 x 512 x 192 size."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle.channel import ChannelGrid, ChannelOracle  # noqa: E402
+from paper_1708_05944_gb300 import vlb  # noqa: E402
+from paper_1708_05944_gb300.inputs import perturbation  # noqa: E402
+from tests.helpers import rel_err  # noqa: E402
+
+MODEL = "HH(4;8)xH(4;12)"
+SMALL = "HH(3;4)xH(3;4)"
+
+
+def to_lib(F):
+    nl, nx = F.shape[1], F.shape[2]
+    return np.ascontiguousarray(np.asarray(F).transpose(2, 1, 0, 3, 4).reshape(nx * nl, 2, F.shape[3], F.shape[4]))
+
+
+def to_oracle(f, nl, nx):
+    f = np.asarray(f, dtype=np.float64).reshape(nx, nl, 2, f.shape[2], f.shape[3])
+    return np.ascontiguousarray(f.transpose(2, 1, 0, 3, 4))
+
+
+def case(spec, nl, nx, kn=0.05, seed=21, amp=0.02, n_in=2.0, n_out=1.0):
+    o = ChannelOracle(spec, ChannelGrid(nl, nx), kn, n_in=n_in, n_out=n_out)
+    F = o.initial_state()
+    F = F * perturbation(F.shape, seed=seed, amplitude=amp)
+    return o, F
+
+
+@pytest.mark.parametrize("spec,nl,nx", [(MODEL, 7, 8), (MODEL, 9, 12), (SMALL, 13, 16), (SMALL, 3, 4)])
+def test_fp64_stages_match_oracle(spec, nl, nx):
+    o, F0 = case(spec, nl, nx)
+    c = vlb.Channel(spec, vlb.VLB_FP64, nl, nx, 0.05)
+    c.set_f(to_lib(F0))
+    dt = 2e-3
+    F1 = o.stage(1, dt, F0, F0)
+    c.stage(dt, 1)
+    assert rel_err(to_oracle(c.read_f(), nl, nx), F1) < 1e-12
+    np.testing.assert_allclose(c.wall_density(), o.last_nw, rtol=1e-12, atol=0)
+    F2 = o.stage(2, dt, F0, F1)
+    c.stage(dt, 2)
+    assert rel_err(to_oracle(c.read_f(), nl, nx), F2) < 1e-12
+    F3 = o.stage(3, dt, F0, F2)
+    c.stage(dt, 3)
+    assert rel_err(to_oracle(c.read_f(), nl, nx), F3) < 1e-12
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [vlb.VLB_FP64, vlb.VLB_FP32_BULK])
+def test_every_channel_launch_shape(prec):
+    nl, nx = 10, 16
+    o, F0 = case(MODEL, nl, nx, seed=5)
+    ref = o.step(o.step(F0, 1e-3), 1e-3)
+    c = vlb.Channel(MODEL, prec, nl, nx, 0.05)
+    dtype = np.float64 if prec == vlb.VLB_FP64 else np.float32
+    shapes = c.channel_variants()
+    assert len(shapes) >= 3
+    for v in range(len(shapes)):
+        c.set_variant(v)
+        c.set_f(to_lib(F0).astype(dtype))
+        c.step(1e-3, 2)
+        got = to_oracle(c.read_f(), nl, nx)
+        if prec == vlb.VLB_FP64:
+            assert rel_err(got, ref) < 1e-12, shapes[v]
+        else:
+            gn = o.moments(got)[0]
+            rn = o.moments(ref)[0]
+            assert np.abs(gn / rn - 1).max() < 1e-5, shapes[v]
+    best, ms = c.autotune(1e-3, reps=3)
+    assert 0 <= best < len(shapes)
+    c.close()
+
+
+def test_fp32_bulk_moments_after_steps():
+    nl, nx = 12, 24
+    o, F0 = case(MODEL, nl, nx, seed=8)
+    F = F0
+    for _ in range(5):
+        F = o.step(F, 1e-3)
+    c = vlb.Channel(MODEL, vlb.VLB_FP32_BULK, nl, nx, 0.05)
+    c.set_f(to_lib(F0).astype(np.float32))
+    c.step(1e-3, 5)
+    n, ul, ux, T = (x.reshape(nx, nl).T for x in c.read_moments())
+    on, oul, oux, oT = o.moments(F)
+    assert np.abs(n / on - 1).max() < 1e-5
+    assert np.abs(T / oT - 1).max() < 1e-5
+    assert np.abs(ux - oux).max() < 1e-5
+    assert np.abs(ul - oul).max() < 1e-5
+    c.close()
+
+
+@pytest.mark.parametrize("prec", [vlb.VLB_FP32_BULK, vlb.VLB_FP64])
+def test_full_size_rest_state_is_exact(prec):
+    # 512 x 2048 cells x 192 velocities: f_eq(1, 0, 1) with both reservoirs at n = 1 is
+    # an exact discrete solution (discrete connection coefficients of Sec. VII.A)
+    nl, nx = 512, 2048
+    c = vlb.Channel(MODEL, prec, nl, nx, 0.05, n_in=1.0, n_out=1.0)
+    c.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+    dtype = torch.float64 if prec == vlb.VLB_FP64 else torch.float32
+    f0 = torch.empty((nl * nx, 2, 16, 12), dtype=dtype, device="cuda")
+    c.read_f(f0)
+    dt = 2e-4
+    c.step(dt, 1)
+    f1 = torch.empty_like(f0)
+    c.read_f(f1)
+    scale = f0.abs().max()
+    tol = 1e-13 if prec == vlb.VLB_FP64 else 2e-6
+    assert float((f1 - f0).abs().max() / scale) < tol
+    np.testing.assert_allclose(c.wall_density(), 1.0, rtol=0, atol=1e-5 if prec else 1e-12)
+    c.close()
