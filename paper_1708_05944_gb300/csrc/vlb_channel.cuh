@@ -323,13 +323,14 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
     }
   }
   // centreline lambda = 0: specular reflection, ghost 1-k mirrors cell k (p^lambda -> -p^lambda)
-  if (s0 == 0) {
+  if (s0 < 3) {  // the lambda halo reaches the ghost cells s = -1, -2, -3 (s = -k mirrors cell k - 1)
     constexpr int QH = Q0 / 2;
     for (int x = tid; x < TP * 3 * 2 * V; x += NT) {
       const int v = x % V, r = x / V, d = r & 1, kc = r >> 1, k = kc % 3 + 1, c = kc / 3;
       const int i = v / Q1, j = v - i * Q1;
       const int ib = i < QH ? i + QH : i - QH;
-      tile[slot(-k, c) * ROW + d * VP + v] = tile[slot(k - 1, c) * ROW + d * VP + ib * Q1 + j];
+      const int rg = -k - s0, rc = k - 1 - s0;  // tile rows of the ghost and of its mirror cell
+      if (rg >= -3) tile[slot(rg, c) * ROW + d * VP + v] = tile[slot(rc, c) * ROW + d * VP + ib * Q1 + j];
     }
   }
   // wall lambda = 1: per column, outgoing flux (p^lambda > 0), n_w, incoming ghosts f_eq(n_w, 0, T0)
