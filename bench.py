@@ -39,6 +39,9 @@ KNS = [1e-3, 1e-2, 0.1, 1.0, 10.0]
 U_WALL = 0.1
 DT = 5e-5  # CFL 0.4 with max |p^R| = 5.21 and dR = 1/1024, and below tau_min
 METRIC = "cell-velocity updates/s"
+CH_MODEL = "HH(4;8)xH(4;12)"
+CH_KN, CH_NIN, CH_NOUT = 0.05, 2.0, 1.0
+CH_DT = 2e-5  # CFL 0.4 on the wall-adjacent cell of the stretched lambda grid (d lambda = 3.7e-4)
 WORKLOAD = "circular Couette scale-up: 1024 cells x HH(4;8)xH(4;20) (320 velocities), Kn in {1e-3,1e-2,0.1,1,10}"
 
 
@@ -216,6 +219,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_channel(args, torch, stream, vlb):
+    """Gradually expanding channel, 512 (lambda) x 2048 (xi) cells x 192 velocities, FP32 bulk.
+    One distribution copy is 1.6 GB, larger than L2, so no flush is needed."""
+    nl, nx = (int(x) for x in args.channel_cells.split("x"))
+    ctx = vlb.Channel(CH_MODEL, vlb.VLB_FP32_BULK, nl, nx, CH_KN, n_in=CH_NIN, n_out=CH_NOUT,
+                      stream=stream.cuda_stream)
+    ctx.init_equilibrium(1.5, 0.0, 0.0, 1.0)
+    tuned, _ = ctx.autotune(CH_DT, reps=3)
+    shape = ctx.channel_variants()[tuned]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(args.channel_warmup):
+            ctx.step(CH_DT, 1)
+        stream.synchronize()
+        step_ms, stage_ms = [], []
+        for _ in range(args.channel_steps):
+            marks = [ev() for _ in range(4)]
+            marks[0].record(stream)
+            for k in (1, 2, 3):
+                ctx.stage(CH_DT, k)
+                marks[k].record(stream)
+            stream.synchronize()
+            t = [marks[0].elapsed_time(marks[k]) for k in (1, 2, 3)]
+            step_ms.append(t[2])
+            stage_ms += [t[0], t[1] - t[0], t[2] - t[1]]
+    n = ctx.read_moments()[0]
+    ctx.close()
+    units = nl * nx * 192
+    total = float(np.sum(step_ms))
+    bytes_per_launch = units * 2 * 4 * (2 + 3 + 3) / 3.0
+    launch_ms = float(np.mean(stage_ms))
+    hbm, kind = peaks()
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    return {"workload": f"gradually expanding channel {nx} (xi) x {nl} (lambda) x {CH_MODEL} (192 velocities), "
+                        f"Kn={CH_KN}, reservoirs n_in/n_out = {CH_NIN}/{CH_NOUT}, FP32 bulk",
+            "value": units * len(step_ms) / (total * 1e-3), "unit": "cell-velocity updates/s",
+            "ms_per_step": total / len(step_ms), "steps": len(step_ms),
+            "launch_shape": {"cells_lambda": shape[0], "cells_xi": shape[1], "threads": shape[2], "autotuned": True},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": "channel_stage_kernel<float>", "peak_source": f"{kind} hbm_gbs",
+                         "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms},
+            "density_finite": bool(np.all(np.isfinite(n)))}
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -278,6 +325,8 @@ def run_gpu(args):
     fp64_value = units * world * len(s64) / (float(s64.sum()) * 1e-3)
     ctx64.close()
 
+    channel = bench_channel(args, torch, stream, vlb) if args.workload in ("all", "channel") else None
+
     if rank != 0:
         return
     cpu = None
@@ -306,6 +355,7 @@ def run_gpu(args):
         "clocks": clocks,
         "fp64": {"value": fp64_value, "unit": "cell-velocity updates/s", "ms_per_step": float(s64.mean()),
                  "launch_shape": {"cells_per_cta": shape64[0], "threads": shape64[1]}},
+        "channel": channel,
     }
     print(json.dumps(line), flush=True)
 
@@ -318,6 +368,11 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="all", choices=["all", "couette"],
+                    help="all: the Couette scale-up line plus the channel measurement")
+    ap.add_argument("--channel-cells", default="512x2048", help="lambda x xi cells of the channel measurement")
+    ap.add_argument("--channel-steps", type=int, default=5)
+    ap.add_argument("--channel-warmup", type=int, default=3)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
