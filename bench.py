@@ -342,7 +342,8 @@ def run_gpu(args):
         "config": {"workload": WORKLOAD, "model": MODEL, "cells": N_CELLS, "velocities": 320,
                    "instances_per_gpu": len(KNS), "kn": KNS, "precision": "fp32-bulk (fp64 reductions)",
                    "dt": DT, "l2": "flushed (512 MB write) between timed steps",
-                   "launch_shape": {"cells_per_cta": shape32[0], "threads": shape32[1], "autotuned": True}},
+                   "launch_shape": {"cells_per_cta": shape32[0], "threads": shape32[1], "persistent": bool(shape32[2]),
+                                    "autotuned": True}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None,
                      "kernel": f"couette_stage_kernel<float, TC={shape32[0]}, 16x20 nodes, NT={shape32[1]}>",

@@ -172,6 +172,24 @@ vlb_status vlb_stage(vlb_ctx* ctx, double dt, int k);
 /* nsteps full TVD-RK3 steps (3 stages each), asynchronous on the stream. */
 vlb_status vlb_step(vlb_ctx* ctx, double dt, long long nsteps);
 
+/* nsteps full RK3 steps like vlb_step, but launched as a CUDA graph: three
+ * steps (nine stage launches) are captured once per launch shape and
+ * replayed nsteps / 3 times; the remaining steps are launched directly.
+ * Results are identical to vlb_step.  The first call after a change of
+ * launch shape captures (on the context stream, or on a private stream when
+ * the context uses the legacy default stream), so make it before any
+ * capture of your own. */
+vlb_status vlb_step_graph(vlb_ctx* ctx, double dt, long long nsteps);
+
+/* Run a Couette context towards its steady state: repeat (check_steps
+ * graph-launched steps, then the L2 norms of Eq. msites_steady against the
+ * previous check) until every instance has max(L2_u, L2_n, L2_T) < threshold
+ * or max_steps steps were taken.  Reports the steps taken, each instance's
+ * last residual and the step count at which it first fell below the
+ * threshold (-1 if it never did); any output pointer may be NULL. */
+vlb_status vlb_run_to_steady(vlb_ctx* ctx, double dt, long long check_steps, double threshold, long long max_steps,
+                             long long* steps_taken, double* residual, long long* converged_step);
+
 /* Per-instance time steps (host array of n_inst doubles > 0) used when dt = 0. */
 vlb_status vlb_set_dt(vlb_ctx* ctx, const double* dt);
 
@@ -197,11 +215,13 @@ vlb_status vlb_residual(vlb_ctx* ctx, double* l2_u, double* l2_n, double* l2_T);
 vlb_status vlb_save(vlb_ctx* ctx, const char* path);
 vlb_status vlb_load(vlb_ctx* ctx, const char* path);
 
-/* Launch shapes of the fused stage kernel available for this context (cells
- * per tile and threads per CTA), written to tc[] and nt[] (up to max
- * entries, NULL allowed); returns their number (negative vlb_status on error).
- * Every shape computes the same stage; they differ in occupancy and load balance. */
-int vlb_variants(const vlb_ctx* ctx, int* tc, int* nt, int max);
+/* Launch shapes of the fused stage kernel available for this context: cells
+ * per tile, threads per CTA and whether the launch is persistent (as many
+ * CTAs as fit on the device, each walking the (instance, tile) list) or has
+ * one CTA per tile; written to tc[], nt[], persistent[] (up to max entries,
+ * NULL allowed).  Returns their number (negative vlb_status on error).  Every
+ * shape computes the same stage; they differ in occupancy and load balance. */
+int vlb_variants(const vlb_ctx* ctx, int* tc, int* nt, int* persistent, int max);
 
 /* Select a launch shape by index (0 = default). */
 vlb_status vlb_set_variant(vlb_ctx* ctx, int variant);

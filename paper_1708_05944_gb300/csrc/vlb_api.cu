@@ -1,6 +1,7 @@
 // C ABI of libvlb (declared in include/vlb.h): contexts, buffers, launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -311,7 +312,10 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     for (int i = 0; i < n; ++i) {
       const size_t smem = prec == VLB_FP64 ? stage_smem_bytes<double>(all[i], c->Vp)
                                            : stage_smem_bytes<float>(all[i], c->Vp);
-      if (smem > 0 && smem <= 227 * 1024) c->variants[c->n_variants++] = all[i];
+      if (smem > 0 && smem <= 227 * 1024 && c->n_variants + 2 <= 16) {
+        c->variants[c->n_variants++] = StageVariant{all[i].tc, all[i].nt, 0};
+        c->variants[c->n_variants++] = StageVariant{all[i].tc, all[i].nt, 1};
+      }
     }
     if (c->n_variants == 0) return fail(nullptr, VLB_ERR_UNSUPPORTED, "velocity set too large for one tile");
   }
@@ -829,18 +833,20 @@ int vlb_channel_variants(const vlb_ctx* c, int* ts, int* tp, int* nt, int max) {
   return c->n_cvariants;
 }
 
-int vlb_variants(const vlb_ctx* c, int* tc, int* nt, int max) {
+int vlb_variants(const vlb_ctx* c, int* tc, int* nt, int* persistent, int max) {
   if (!c) return VLB_ERR_INVALID;
   if (c->kind == 1) {
     for (int v = 0; v < c->n_cvariants && v < max; ++v) {
       if (tc) tc[v] = c->cvariants[v].ts * c->cvariants[v].tp;
       if (nt) nt[v] = c->cvariants[v].nt;
+      if (persistent) persistent[v] = 0;
     }
     return c->n_cvariants;
   }
   for (int v = 0; v < c->n_variants && v < max; ++v) {
     if (tc) tc[v] = c->variants[v].tc;
     if (nt) nt[v] = c->variants[v].nt;
+    if (persistent) persistent[v] = c->variants[v].persist;
   }
   return c->n_variants;
 }
@@ -897,6 +903,96 @@ vlb_status vlb_autotune(vlb_ctx* c, double dt, int reps, int* chosen, double* be
   return VLB_OK;
 }
 
+vlb_status vlb_step_graph(vlb_ctx* c, double dt, long long nsteps) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (nsteps < 0) return fail(c, VLB_ERR_INVALID, "nsteps must be >= 0");
+  if (c->stage_done % 3 != 0) return fail(c, VLB_ERR_STATE, "a partial RK3 step is pending");
+  vlb_status st = apply_dt(c, dt);
+  if (st != VLB_OK) return st;
+  c->launches = 0;
+  const long long groups = nsteps / 3;
+  if (groups > 0 && (!c->graph_exec || c->graph_variant != c->variant)) {
+    // capture three steps: the buffer rotation returns to the same F_l after three steps
+    if (c->graph_exec) {
+      cudaGraphExecDestroy(c->graph_exec);
+      c->graph_exec = nullptr;
+    }
+    cudaStream_t s = c->stream;
+    if (!s) {
+      if (!c->capture_stream) VLB_CUDA(c, cudaStreamCreateWithFlags(&c->capture_stream, cudaStreamNonBlocking));
+      s = c->capture_stream;
+    }
+    const int keep_cur = c->cur, keep_last = c->last, keep_done = c->stage_done;
+    const long long keep_steps = c->steps;
+    cudaStream_t keep_stream = c->stream;
+    c->stream = s;
+    VLB_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    vlb_status cst = VLB_OK;
+    for (int r = 0; r < 3 && cst == VLB_OK; ++r)
+      for (int k = 1; k <= 3 && cst == VLB_OK; ++k) cst = run_stage(c, k);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    c->stream = keep_stream;
+    c->cur = keep_cur, c->last = keep_last, c->stage_done = keep_done, c->steps = keep_steps;
+    if (cst != VLB_OK) {
+      if (g) cudaGraphDestroy(g);
+      return cst;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    c->graph_variant = c->variant;
+  }
+  for (long long r = 0; r < groups; ++r) {
+    VLB_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    c->steps += 3;
+  }
+  c->launches = groups * 9;
+  if (groups > 0) c->last = c->cur;  // three steps bring F_l back to the same buffer
+  for (long long s = 0; s < nsteps - 3 * groups; ++s)
+    for (int k = 1; k <= 3; ++k) {
+      st = run_stage(c, k);
+      if (st != VLB_OK) return st;
+    }
+  return VLB_OK;
+}
+
+vlb_status vlb_run_to_steady(vlb_ctx* c, double dt, long long check_steps, double threshold, long long max_steps,
+                             long long* steps_taken, double* residual, long long* converged_step) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (c->kind != 0) return fail(c, VLB_ERR_UNSUPPORTED, "steady-state norms are defined for Couette contexts");
+  if (check_steps < 1 || !(threshold > 0.0) || max_steps < check_steps)
+    return fail(c, VLB_ERR_INVALID, "need check_steps >= 1, threshold > 0, max_steps >= check_steps");
+  const int ni = c->n_inst;
+  std::vector<double> l2u(ni), l2n(ni), l2T(ni);
+  std::vector<long long> conv(ni, -1);
+  c->have_prev = false;
+  vlb_status st = vlb_residual(c, nullptr, nullptr, nullptr);  // stores the starting moments
+  if (st != VLB_OK) return st;
+  long long done = 0;
+  int left = ni;
+  while (done < max_steps && left > 0) {
+    st = vlb_step_graph(c, dt, check_steps);
+    if (st != VLB_OK) return st;
+    done += check_steps;
+    st = vlb_residual(c, l2u.data(), l2n.data(), l2T.data());
+    if (st != VLB_OK) return st;
+    for (int i = 0; i < ni; ++i) {
+      const double r = std::max(l2u[i], std::max(l2n[i], l2T[i]));
+      if (residual) residual[i] = r;
+      if (conv[i] < 0 && r < threshold) {
+        conv[i] = done;
+        --left;
+      }
+    }
+  }
+  if (steps_taken) *steps_taken = done;
+  for (int i = 0; i < ni; ++i)
+    if (converged_step) converged_step[i] = conv[i];
+  return VLB_OK;
+}
+
 long long vlb_kernel_launches(const vlb_ctx* c) { return c ? c->launches : 0; }
 
 const char* vlb_last_error(const vlb_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
@@ -911,6 +1007,8 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_geof);
   cudaFree(c->d_cgeo);
   cudaFree(c->d_cgeof);
+  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   cudaFree(c->d_nw);
   cudaFree(c->d_err);
   cudaFree(c->d_mom);

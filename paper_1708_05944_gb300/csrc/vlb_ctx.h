@@ -32,7 +32,7 @@ struct vlb_ctx {
   std::unique_ptr<KArgs<float>> k32;
   std::unique_ptr<KArgs<double>> k64;
   void* F[3] = {nullptr, nullptr, nullptr};
-  StageVariant variants[8];
+  StageVariant variants[16];
   int n_variants = 0;
   int variant = 0;
   int cur = 0;   // buffer holding F_l
@@ -56,6 +56,10 @@ struct vlb_ctx {
   ChanCell<double>* d_cgeo = nullptr;
   ChanCell<float>* d_cgeof = nullptr;
   std::vector<unsigned char> chanK32, chanK64;
+  // CUDA graph of three RK3 steps (nine stage launches), replayed by vlb_step_graph
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  int graph_variant = -1;
   long long launches = 0;
   long long steps = 0;
   std::string err;

@@ -13,12 +13,22 @@ namespace vlb {
 // configured models; anything else takes the generic kernel.  The autotuner
 // (vlb_autotune) times the variants of a context's shape and keeps the best.
 template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
-static cudaError_t go_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, cudaStream_t s) {
+static cudaError_t go_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int persist,
+                            cudaStream_t s) {
   auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
   const size_t smem = StageSmem<real, TC, NT>::bytes(a.Vp);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
-  kern<<<a.n_tiles, NT, smem, s>>>(a, m, k);
+  int grid = a.n_tiles;
+  if (persist) {  // persistent: as many CTAs as fit on the device at once, each walking the tile list
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess) return e;
+    const int cap = per_sm * sms;
+    if (cap > 0 && cap < grid) grid = cap;
+  }
+  kern<<<grid, NT, smem, s>>>(a, m, k);
   return cudaGetLastError();
 }
 
@@ -37,19 +47,19 @@ template <typename real>
 struct VariantTable;
 template <>
 struct VariantTable<float> {
-  static constexpr StageVariant v16x20[] = {{4, 256}, {8, 256}, {4, 320}, {8, 320}, {16, 320}};
-  static constexpr StageVariant v16x12[] = {{16, 256}, {8, 256}, {16, 384}};
-  static constexpr StageVariant v8x4[] = {{16, 64}, {8, 64}};
-  static constexpr StageVariant vsmall[] = {{16, 64}};
-  static constexpr StageVariant vgen[] = {{16, 256}};
+  static constexpr StageVariant v16x20[] = {{4, 256, 0}, {8, 256, 0}, {4, 320, 0}, {8, 320, 0}, {16, 320, 0}};
+  static constexpr StageVariant v16x12[] = {{16, 256, 0}, {8, 256, 0}, {16, 384, 0}};
+  static constexpr StageVariant v8x4[] = {{16, 64, 0}, {8, 64, 0}};
+  static constexpr StageVariant vsmall[] = {{16, 64, 0}};
+  static constexpr StageVariant vgen[] = {{16, 256, 0}};
 };
 template <>
 struct VariantTable<double> {
-  static constexpr StageVariant v16x20[] = {{4, 256}, {8, 256}, {4, 128}, {8, 128}};
-  static constexpr StageVariant v16x12[] = {{8, 256}, {4, 256}, {8, 384}};
-  static constexpr StageVariant v8x4[] = {{8, 64}, {16, 64}};
-  static constexpr StageVariant vsmall[] = {{8, 64}};
-  static constexpr StageVariant vgen[] = {{8, 256}};
+  static constexpr StageVariant v16x20[] = {{4, 256, 0}, {8, 256, 0}, {4, 128, 0}, {8, 128, 0}};
+  static constexpr StageVariant v16x12[] = {{8, 256, 0}, {4, 256, 0}, {8, 384, 0}};
+  static constexpr StageVariant v8x4[] = {{8, 64, 0}, {16, 64, 0}};
+  static constexpr StageVariant vsmall[] = {{8, 64, 0}};
+  static constexpr StageVariant vgen[] = {{8, 256, 0}};
 };
 
 template <typename real>
@@ -85,7 +95,7 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
                          cudaStream_t s) {
   const int sh = shape_of(m.nq0, m.nq1);
 #define VLB_CASE(SH, TC_, NT_, q0, q1, ex) \
-  if (sh == SH && v.tc == TC_ && v.nt == NT_) return go_stage<real, TC_, NT_, q0, q1, ex>(a, m, k, s);
+  if (sh == SH && v.tc == TC_ && v.nt == NT_) return go_stage<real, TC_, NT_, q0, q1, ex>(a, m, k, v.persist, s);
   if constexpr (sizeof(real) == 4) {
     VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
     VLB_CASE(SH_16x20, 4, 320, 16, 20, true) VLB_CASE(SH_16x20, 8, 320, 16, 20, true)

@@ -12,6 +12,7 @@ struct StageArgs;
 // Launch shape of the stage kernel: cells per tile and threads per CTA.
 struct StageVariant {
   int tc, nt;
+  int persist;  // 0: one CTA per tile; 1: persistent CTAs walk the tile list
 };
 
 // The launch shapes available for a model shape (at most 8); the first is the default.

@@ -99,28 +99,9 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   real* cIR = ccm + TC;
   real* mv = cIR + TC;  // [t][axis*2 + side][s]
 
-  const TileDesc td = a.tiles[blockIdx.x];
-  const InstDesc in = a.inst[td.inst];
-  const int n = in.n_cells, c0 = td.c0;
-  const int TCe = min(TC, n - c0);
-  const int lo = max(c0 - 3, 0), hi = min(c0 + TC + 3, n);
-
-  // ---- stage the tile (cells lo..hi-1 at slots lo-c0+3 ...) and F_l with bulk copies
   if (tid == 0) {
     mbar_init(bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  const bool need_fl = a.caf != 0.0f;
-  if (warp == 0) {
-    const unsigned rbytes = unsigned(row * sizeof(real));
-    if (lane == 0) mbar_expect_tx(bar, rbytes * unsigned(hi - lo + (need_fl ? TCe : 0)));
-    __syncwarp();
-    for (int c = lo + lane; c < hi; c += 32)
-      bulk_g2s(tile + (c - c0 + 3) * row, a.Fprev + size_t(in.cell0 + c) * row, rbytes, bar);
-    if (need_fl)
-      for (int t = lane; t < TCe; t += 32)
-        bulk_g2s(flb + t * row, a.Fl + size_t(in.cell0 + c0 + t) * row, rbytes, bar);
   }
   constexpr bool F32 = sizeof(real) == 4;
   for (int x = tid; x < MAXQ; x += NT) {
@@ -144,6 +125,29 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     tabr0[x] = sizeof(real) == 4 ? real(m.tab0f[x]) : real(m.tab0[x]);
     tabr1[x] = sizeof(real) == 4 ? real(m.tab1f[x]) : real(m.tab1[x]);
   }
+  __syncthreads();
+  const bool need_fl = a.caf != 0.0f;
+  unsigned parity = 0;
+  // one tile per iteration: a launch with one CTA per tile runs the body once, a persistent
+  // launch (grid sized by occupancy) walks the tile list
+  for (int tix = blockIdx.x; tix < a.n_tiles; tix += gridDim.x) {
+  const TileDesc td = a.tiles[tix];
+  const InstDesc in = a.inst[td.inst];
+  const int n = in.n_cells, c0 = td.c0;
+  const int TCe = min(TC, n - c0);
+  const int lo = max(c0 - 3, 0), hi = min(c0 + TC + 3, n);
+
+  // ---- stage the tile (cells lo..hi-1 at slots lo-c0+3 ...) and F_l with bulk copies
+  if (warp == 0) {
+    const unsigned rbytes = unsigned(row * sizeof(real));
+    if (lane == 0) mbar_expect_tx(bar, rbytes * unsigned(hi - lo + (need_fl ? TCe : 0)));
+    __syncwarp();
+    for (int c = lo + lane; c < hi; c += 32)
+      bulk_g2s(tile + (c - c0 + 3) * row, a.Fprev + size_t(in.cell0 + c) * row, rbytes, bar);
+    if (need_fl)
+      for (int t = lane; t < TCe; t += 32)
+        bulk_g2s(flb + t * row, a.Fl + size_t(in.cell0 + c0 + t) * row, rbytes, bar);
+  }
   for (int t = tid; t < TCe; t += NT) {
     if constexpr (F32) {
       const GeoCellF g = a.geof[in.cell0 + c0 + t];
@@ -157,13 +161,14 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       cIR[t] = g.inv_rbar;
     }
   }
-  bool ok = mbar_wait(bar, 0, a.max_polls);
+  bool ok = mbar_wait(bar, parity, a.max_polls);
   ok = __syncthreads_and(ok);
   if (!ok) {
     if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
-    mbar_wait(bar, 0, a.max_polls);  // let the copies land before the CTA exits
+    mbar_wait(bar, parity, a.max_polls);  // let the copies land before the CTA exits
     return;
   }
+  parity ^= 1u;
 
   // ==== phase A: moment sums per cell (one warp per cell) and the K^R part of the force
   for (int t = warp; t < TCe; t += NW) {
@@ -410,6 +415,8 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   if (tid == 0) {
     bulk_s2g(a.Fout + size_t(in.cell0 + c0) * row, tile + 3 * row, unsigned(TCe * row * sizeof(real)));
     bulk_commit_and_wait_read();
+  }
+  __syncthreads();  // shared memory is reused by the next tile
   }
 }
 

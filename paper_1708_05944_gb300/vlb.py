@@ -72,10 +72,13 @@ EXPORTS = {
     "vlb_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "vlb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "vlb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
-    "vlb_variants": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "vlb_variants": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_set_variant": (C.c_int, [C.c_void_p, C.c_int]),
     "vlb_autotune": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     "vlb_step_static_scratch": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_longlong]),
+    "vlb_step_graph": (C.c_int, [C.c_void_p, C.c_double, C.c_longlong]),
+    "vlb_run_to_steady": (C.c_int, [C.c_void_p, C.c_double, C.c_longlong, C.c_double, C.c_longlong,
+                                    C.POINTER(C.c_longlong), C.c_void_p, C.c_void_p]),
     "vlb_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "vlb_last_error": (C.c_char_p, [C.c_void_p]),
     "vlb_destroy": (None, [C.c_void_p]),
@@ -189,6 +192,9 @@ class _Context:
     def step(self, dt, nsteps=1):
         _check(_lib.vlb_step(self.h, dt, nsteps), self.h)
 
+    def step_graph(self, dt, nsteps=1):
+        _check(_lib.vlb_step_graph(self.h, dt, nsteps), self.h)
+
     def set_dt(self, dt):
         arr = (C.c_double * self.n_inst)(*dt)
         _check(_lib.vlb_set_dt(self.h, arr), self.h)
@@ -208,11 +214,12 @@ class _Context:
         _check(_lib.vlb_load(self.h, path.encode()), self.h)
 
     def variants(self):
-        tc, nt = np.zeros(8, dtype=np.int32), np.zeros(8, dtype=np.int32)
-        n = _lib.vlb_variants(self.h, _ptr(tc), _ptr(nt), 8)
+        """[(cells per tile, threads, persistent)] of the stage kernel's launch shapes."""
+        tc, nt, ps = (np.zeros(16, dtype=np.int32) for _ in range(3))
+        n = _lib.vlb_variants(self.h, _ptr(tc), _ptr(nt), _ptr(ps), 16)
         if n < 0:
             _check(n, self.h)
-        return [(int(tc[i]), int(nt[i])) for i in range(n)]
+        return [(int(tc[i]), int(nt[i]), int(ps[i])) for i in range(n)]
 
     def set_variant(self, v):
         _check(_lib.vlb_set_variant(self.h, v), self.h)
@@ -264,6 +271,15 @@ class Couette(_Context):
         nw = np.empty((self.n_inst, 2))
         _check(_lib.vlb_wall_density(self.h, _ptr(nw)), self.h)
         return nw
+
+    def run_to_steady(self, dt, check_steps, threshold, max_steps):
+        """(steps taken, last residual per instance, first converged step per instance or -1)."""
+        taken = C.c_longlong()
+        res = np.zeros(self.n_inst)
+        conv = np.zeros(self.n_inst, dtype=np.int64)
+        _check(_lib.vlb_run_to_steady(self.h, dt, check_steps, threshold, max_steps, C.byref(taken), _ptr(res),
+                                      _ptr(conv)), self.h)
+        return taken.value, res, conv
 
     def residual(self):
         a, b, c = (np.empty(self.n_inst) for _ in range(3))

@@ -1,0 +1,106 @@
+"""Batched Couette production pattern: ragged instances in one context, persistent
+and graph-captured launches, per-instance time steps, run to a steady residual.
+Each instance of a batch must be bitwise equal to the same instance run alone
+with the same launch shape."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_1708_05944_gb300 import vlb  # noqa: E402
+from paper_1708_05944_gb300.inputs import couette_instances, perturbation  # noqa: E402
+
+MODEL = "HH(4;8)xH(4;20)"
+PMAX = 5.2128  # largest |p^R| of the half-range rule of order 8
+
+
+def stable_dt(inst):
+    # CFL 0.4 on the radial spacing, and half the smallest relaxation time (RK3 on the stiff BGK term)
+    dr = (inst["r_out"] - inst["r_in"]) / inst["n_cells"]
+    tau = np.sqrt(np.pi / 8) * inst["kn"] / 1.2
+    return min(0.4 * dr / PMAX, 0.5 * tau)
+
+
+def make_batch(insts, prec=vlb.VLB_FP32_BULK):
+    grids = [dict(n_cells=i["n_cells"], r_in=i["r_in"], r_out=i["r_out"]) for i in insts]
+    return vlb.Couette(MODEL, prec, grids, [(i["u_wall"], 1.0) for i in insts], [(0.0, 1.0)] * len(insts),
+                       [i["kn"] for i in insts], [vlb.VLB_TAU_AOKI] * len(insts))
+
+
+def seeded_f(ctx, seed):
+    m = ctx.model
+    _, w0 = vlb.vlb_quadrature(m, 0)
+    _, w1 = vlb.vlb_quadrature(m, 1)
+    ww = np.outer(w0, w1)
+    F = np.broadcast_to(ww, ctx.f_shape()) * perturbation(ctx.f_shape(), seed=seed)
+    return np.ascontiguousarray(F.astype(ctx.dtype))
+
+
+def test_graph_and_persistent_launches_are_bitwise_equal_to_plain():
+    insts = couette_instances(6, n_min=20, n_max=90)
+    a, b = make_batch(insts), make_batch(insts)
+    f0 = seeded_f(a, 3)
+    dts = [stable_dt(i) for i in insts]
+    for c in (a, b):
+        c.set_dt(dts)
+        c.set_f(f0)
+    a.step(0.0, 7)
+    b.step_graph(0.0, 7)
+    assert np.array_equal(a.read_f(), b.read_f())
+    shapes = a.variants()
+    pairs = [(v, w) for v in range(len(shapes)) for w in range(len(shapes))
+             if shapes[v][:2] == shapes[w][:2] and shapes[v][2] == 0 and shapes[w][2] == 1]
+    assert pairs
+    for v, w in pairs:
+        a.set_variant(v)
+        b.set_variant(w)
+        a.set_f(f0)
+        b.set_f(f0)
+        a.step(0.0, 2)
+        b.step_graph(0.0, 4)
+        a.step(0.0, 2)
+        assert np.array_equal(a.read_f(), b.read_f()), shapes[w]
+    a.close()
+    b.close()
+
+
+def test_256_instance_batch_matches_instances_run_alone():
+    insts = couette_instances(256)
+    c = make_batch(insts)
+    dts = [stable_dt(i) for i in insts]
+    c.set_dt(dts)
+    f0 = seeded_f(c, 11)
+    c.set_f(f0)
+    c.step_graph(0.0, 3)
+    got = c.read_f()
+    offs = np.concatenate([[0], np.cumsum([i["n_cells"] for i in insts])])
+    for k in (0, 17, 128, 255):
+        one = make_batch([insts[k]])
+        one.set_variant(0)
+        c.set_variant(0)
+        one.set_dt([dts[k]])
+        one.set_f(f0[offs[k]:offs[k + 1]])
+        one.step(0.0, 3)
+        c.set_f(f0)
+        c.step(0.0, 3)
+        assert np.array_equal(c.read_f()[offs[k]:offs[k + 1]], one.read_f()), k
+        one.close()
+    assert np.all(np.isfinite(got))
+    c.close()
+
+
+def test_run_to_steady_reaches_threshold():
+    insts = [dict(n_cells=24, kn=5.0, u_wall=0.1, r_in=1.0, r_out=1.5),
+             dict(n_cells=32, kn=2.0, u_wall=0.3, r_in=1.0, r_out=2.0)]
+    c = make_batch(insts)
+    c.set_dt([stable_dt(i) for i in insts])
+    taken, res, conv = c.run_to_steady(0.0, 300, 1e-6, 300 * 400)
+    assert np.all(conv > 0), (taken, res, conv)
+    assert np.all(res < 1e-6)
+    n, u0, u1, T = c.read_moments()
+    assert np.all(np.isfinite(n)) and np.abs(u0).max() < 1e-3  # u^R vanishes at steady state (Sec. VI.B)
+    c.close()
