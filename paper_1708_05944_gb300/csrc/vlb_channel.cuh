@@ -474,12 +474,10 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
 #pragma unroll
           for (int k = 0; k < 7; ++k) h[k] = tile[slot(sr, c - 3 + k) * ROW + d * VP + v];
           const real Vm = gq[2] * px - gq[4] * pl, Vp_ = gq[3] * px - gq[5] * pl;
-          // upwind stencils by the sign of V^xi (selected inputs, one WENO evaluation each)
-          const bool um = Vm >= real(0), up = Vp_ >= real(0);
-          const real Fm = weno5<real>(um ? h[0] : h[5], um ? h[1] : h[4], um ? h[2] : h[3], um ? h[3] : h[2],
-                                      um ? h[4] : h[1], sc);
-          const real Fp = weno5<real>(up ? h[1] : h[6], up ? h[2] : h[5], up ? h[3] : h[4], up ? h[4] : h[3],
-                                      up ? h[5] : h[2], sc);
+          const real Fm = Vm >= real(0) ? weno5<real>(h[0], h[1], h[2], h[3], h[4], sc)
+                                        : weno5<real>(h[5], h[4], h[3], h[2], h[1], sc);
+          const real Fp = Vp_ >= real(0) ? weno5<real>(h[1], h[2], h[3], h[4], h[5], sc)
+                                         : weno5<real>(h[6], h[5], h[4], h[3], h[2], sc);
           adv += (Vp_ * Fp - Vm * Fm) * gq[7];
           const real feq = g0n[q * Q0 + i] * g1[q * Q1 + j] * (d ? cT[q] : real(1));
           const real Lv = -adv + lbuf[q * ROW + d * VP + v] - (w3 - feq) * citau[q];
