@@ -257,6 +257,50 @@ vlb_status vlb_step_static_scratch(vlb_ctx* ctx, const void* f_in, void* f_out, 
 /* Number of kernels the last vlb_step / vlb_stage call launched. */
 long long vlb_kernel_launches(const vlb_ctx* ctx);
 
+/* Seed every cell of a context from macroscopic fields (host or device arrays
+ * of total_cells doubles): f' = n g_0(u0, T) g_1(u1, T), f'' = T f', the
+ * truncated Hermite equilibrium of Sec. IV.D.  q0 (the radial heat flux) is
+ * accepted for the warm-start interface and may be NULL; the seed does not
+ * use it. */
+vlb_status vlb_init_from_moments(vlb_ctx* ctx, const double* n, const double* u0, const double* u1, const double* T,
+                                 const double* q0, int on_device);
+
+/* ---- Learned warm start (no counterpart in the paper) -------------------
+ * A 1D spectral neural operator over the normalised radius s in (0, 1) on
+ * grid_points uniform points, mapping (Kn, inner wall speed, R_out/R_in) to
+ * n, u^phi, T, q^R at every point.
+ * Features per point: [(log10 Kn + 1)/2, (u_w - 0.255)/0.245, (R_out/R_in - 2.75)/1.25, 2s - 1].
+ * Lift to `width` channels, then `layers` layers of h <- act(S(h) + h W + b)
+ * (GELU, none on the last layer).  S is a truncated real DFT over `modes`
+ * modes, a general real (2 width x 2 width) map per mode on its (Re, Im)
+ * channel pair, and the inverse truncated DFT.  Projection: GELU(h P1 + c1) P2 + c2.
+ * Parameters form one FP32 vector, ordered:
+ *   W_in (4 x width), b_in (width),
+ *   per layer: S (modes x 2width x 2width), W (width x width), b (width),
+ *   P1 (width x hidden), c1 (hidden), P2 (hidden x 4), c2 (4);
+ * matrices are [in][out], row-major.
+ * GEMMs are BF16 tensor-core MMAs with FP32 accumulation.  Master weights
+ * and the Adam state are FP32.  Outputs and targets are in physical units,
+ * normalised inside by vlb_no_set_target_scaling.  cond arrays hold B rows
+ * of (Kn, u_w, R_out/R_in); outputs and targets hold B x grid_points x 4
+ * values.  The operator is resolution invariant: parameters trained at one
+ * grid_points serve any other with 2 modes <= grid_points. */
+typedef struct vlb_no vlb_no;
+vlb_status vlb_no_create(int grid_points, int width, int modes, int layers, int hidden, void* cuda_stream,
+                         vlb_no** out);
+long long vlb_no_num_params(const vlb_no* no);
+vlb_status vlb_no_set_params(vlb_no* no, const float* theta);  /* host array; resets the Adam state */
+vlb_status vlb_no_get_params(vlb_no* no, float* theta);
+vlb_status vlb_no_set_target_scaling(vlb_no* no, const double* mean4, const double* std4);
+vlb_status vlb_no_predict(vlb_no* no, const double* cond, int B, double* out);
+/* Mean squared error of the normalised outputs and its gradient (either output may be NULL). */
+vlb_status vlb_no_loss_and_grad(vlb_no* no, const double* cond, const double* targets, int B, double* loss,
+                                float* grad);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on the batch; reports the loss before the step. */
+vlb_status vlb_no_train_step(vlb_no* no, const double* cond, const double* targets, int B, double lr, double* loss);
+const char* vlb_no_last_error(const vlb_no* no);
+void vlb_no_destroy(vlb_no* no);
+
 const char* vlb_last_error(const vlb_ctx* ctx);
 void vlb_destroy(vlb_ctx* ctx);
 

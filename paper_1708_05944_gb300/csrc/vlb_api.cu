@@ -611,6 +611,31 @@ vlb_status vlb_init_equilibrium(vlb_ctx* c, double n0, double u0, double u1, dou
   return VLB_OK;
 }
 
+vlb_status vlb_init_from_moments(vlb_ctx* c, const double* n, const double* u0, const double* u1, const double* T,
+                                 const double* q0, int on_device) {
+  (void)q0;
+  if (!c || !n || !u0 || !u1 || !T) return fail(c, VLB_ERR_INVALID, "null argument");
+  const size_t N = size_t(c->total_cells);
+  const double* src[4] = {n, u0, u1, T};
+  double* dev = c->d_mom;  // 9 doubles per cell of room: use four of them as staging
+  for (int a = 0; a < 4; ++a) {
+    VLB_CUDA(c, cudaMemcpyAsync(dev + a * N, src[a], sizeof(double) * N,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  }
+  if (!on_device) VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  cudaError_t e = c->prec == VLB_FP64
+                      ? launch_seed<double>(static_cast<double*>(c->F[c->cur]), c->total_cells, c->Vp, c->margs, dev,
+                                            dev + N, dev + 2 * N, dev + 3 * N, c->stream)
+                      : launch_seed<float>(static_cast<float*>(c->F[c->cur]), c->total_cells, c->Vp, c->margs, dev,
+                                           dev + N, dev + 2 * N, dev + 3 * N, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "seed kernel launch");
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->last = c->cur;
+  c->stage_done = 0;
+  c->have_prev = false;
+  return VLB_OK;
+}
+
 vlb_status vlb_set_f(vlb_ctx* c, const void* f, int on_device) {
   if (!c || !f) return fail(c, VLB_ERR_INVALID, "null argument");
   const size_t w = size_t(c->V) * c->esize, pitch = size_t(c->Vp) * c->esize;

@@ -215,6 +215,50 @@ cudaError_t launch_init_equilibrium(real* F, long long cells, int Vp, const Mode
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- seeding from moments, one CTA per cell
+template <typename real>
+__global__ void seed_kernel(real* F, long long cells, int Vp, const __grid_constant__ ModelArgs m, const double* n,
+                            const double* u0, const double* u1, const double* T) {
+  __shared__ double g0[MAXQ], g1[MAXQ];
+  for (long long c = blockIdx.x; c < cells; c += gridDim.x) {
+    if (threadIdx.x < 2) {
+      const int ax = threadIdx.x;
+      double mp[MAXN], mm[MAXN];
+      const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0, nq = ax ? m.nq1 : m.nq0;
+      const double u = ax ? u1[c] : u0[c];
+      eq_moment_vector<double>(kind, N, u, T[c], mp);
+      eq_moment_vector<double>(kind, N, -u, T[c], mm);
+      for (int k = 0; k < nq; ++k) {
+        const double pk = ax ? m.p1[k] : m.p0[k];
+        const double* mv = (kind == 1 && pk < 0.0) ? mm : mp;
+        double g = 0;
+        for (int s = 0; s <= N; ++s) g += (ax ? m.tab1 : m.tab0)[k * MAXN + s] * mv[s];
+        (ax ? g1 : g0)[k] = g;
+      }
+    }
+    __syncthreads();
+    const int V = m.nq0 * m.nq1;
+    for (int x = threadIdx.x; x < 2 * Vp; x += blockDim.x) {
+      const int d = x >= Vp, v = x - d * Vp;
+      real val = real(0);
+      if (v < V) {
+        const int i = v / m.nq1, j = v - i * m.nq1;
+        val = real(n[c] * g0[i] * g1[j] * (d ? T[c] : 1.0));
+      }
+      F[c * 2 * Vp + x] = val;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename real>
+cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, const double* n, const double* u0,
+                        const double* u1, const double* T, cudaStream_t s) {
+  const long long blocks = cells < 152 * 16 ? cells : 152 * 16;
+  seed_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(F, cells, Vp, m, n, u0, u1, T);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- moments (FP64), one warp per cell
 template <typename real>
 __global__ void moments_kernel(const real* F, long long cells, int Vp, const __grid_constant__ ModelArgs m,
@@ -289,6 +333,8 @@ template cudaError_t launch_init_equilibrium<VLB_REAL>(VLB_REAL*, long long, int
 template size_t channel_smem_bytes<VLB_REAL>(ChanVariant, int, int);
 template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_REAL>&, const ModelArgs&, const void*, int,
                                               int, cudaStream_t);
+template cudaError_t launch_seed<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
+                                           const double*, const double*, const double*, cudaStream_t);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,
                                               cudaStream_t);
 

@@ -79,6 +79,19 @@ EXPORTS = {
     "vlb_step_graph": (C.c_int, [C.c_void_p, C.c_double, C.c_longlong]),
     "vlb_run_to_steady": (C.c_int, [C.c_void_p, C.c_double, C.c_longlong, C.c_double, C.c_longlong,
                                     C.POINTER(C.c_longlong), C.c_void_p, C.c_void_p]),
+    "vlb_init_from_moments": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5 + [C.c_int]),
+    "vlb_no_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]),
+    "vlb_no_num_params": (C.c_longlong, [C.c_void_p]),
+    "vlb_no_set_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "vlb_no_get_params": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "vlb_no_set_target_scaling": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vlb_no_predict": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "vlb_no_loss_and_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double),
+                                       C.c_void_p]),
+    "vlb_no_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                    C.POINTER(C.c_double)]),
+    "vlb_no_last_error": (C.c_char_p, [C.c_void_p]),
+    "vlb_no_destroy": (None, [C.c_void_p]),
     "vlb_kernel_launches": (C.c_longlong, [C.c_void_p]),
     "vlb_last_error": (C.c_char_p, [C.c_void_p]),
     "vlb_destroy": (None, [C.c_void_p]),
@@ -207,6 +220,11 @@ class _Context:
         _check(_lib.vlb_read_moments(self.h, _ptr(n), _ptr(u0), _ptr(u1), _ptr(T), _ptr(Tab), _ptr(q), 0), self.h)
         return (n, u0, u1, T, Tab, q) if full else (n, u0, u1, T)
 
+    def init_from_moments(self, n, u0, u1, T, q0=None):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (n, u0, u1, T)]
+        q = None if q0 is None else np.ascontiguousarray(q0, dtype=np.float64)
+        _check(_lib.vlb_init_from_moments(self.h, *[_ptr(a) for a in arrs], _ptr(q), 0), self.h)
+
     def save(self, path):
         _check(_lib.vlb_save(self.h, path.encode()), self.h)
 
@@ -315,3 +333,65 @@ class Channel(_Context):
         nw = np.empty(self.n_xi)
         _check(_lib.vlb_wall_density(self.h, _ptr(nw)), self.h)
         return nw
+
+
+class NeuralOperator:
+    """The learned warm-start operator (vlb_no_*)."""
+
+    def __init__(self, grid_points=64, width=64, modes=32, layers=4, hidden=128, stream=None):
+        h = C.c_void_p()
+        st = _lib.vlb_no_create(grid_points, width, modes, layers, hidden, C.c_void_p(stream) if stream else None,
+                                C.byref(h))
+        if st != VLB_OK:
+            raise VlbError(st, "vlb_no_create failed")
+        self.h = h
+        self.grid_points = grid_points
+        self.size = _lib.vlb_no_num_params(h)
+
+    def _chk(self, st):
+        if st != VLB_OK:
+            raise VlbError(st, (_lib.vlb_no_last_error(self.h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.vlb_no_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.size
+        self._chk(_lib.vlb_no_set_params(self.h, _ptr(t)))
+
+    def get_params(self):
+        t = np.empty(self.size, dtype=np.float32)
+        self._chk(_lib.vlb_no_get_params(self.h, _ptr(t)))
+        return t
+
+    def set_target_scaling(self, mean, std):
+        m = np.ascontiguousarray(mean, dtype=np.float64)
+        s = np.ascontiguousarray(std, dtype=np.float64)
+        self._chk(_lib.vlb_no_set_target_scaling(self.h, _ptr(m), _ptr(s)))
+
+    def predict(self, cond):
+        c = np.ascontiguousarray(cond, dtype=np.float64)
+        out = np.empty((c.shape[0], self.grid_points, 4))
+        self._chk(_lib.vlb_no_predict(self.h, _ptr(c), c.shape[0], _ptr(out)))
+        return out
+
+    def loss_and_grad(self, cond, targets):
+        c = np.ascontiguousarray(cond, dtype=np.float64)
+        t = np.ascontiguousarray(targets, dtype=np.float64)
+        loss = C.c_double()
+        g = np.empty(self.size, dtype=np.float32)
+        self._chk(_lib.vlb_no_loss_and_grad(self.h, _ptr(c), _ptr(t), c.shape[0], C.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train_step(self, cond, targets, lr):
+        c = np.ascontiguousarray(cond, dtype=np.float64)
+        t = np.ascontiguousarray(targets, dtype=np.float64)
+        loss = C.c_double()
+        self._chk(_lib.vlb_no_train_step(self.h, _ptr(c), _ptr(t), c.shape[0], lr, C.byref(loss)))
+        return loss.value
