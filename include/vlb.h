@@ -258,10 +258,15 @@ vlb_status vlb_step_static_scratch(vlb_ctx* ctx, const void* f_in, void* f_out, 
 long long vlb_kernel_launches(const vlb_ctx* ctx);
 
 /* Seed every cell of a context from macroscopic fields (host or device arrays
- * of total_cells doubles): f' = n g_0(u0, T) g_1(u1, T), f'' = T f', the
- * truncated Hermite equilibrium of Sec. IV.D.  q0 (the radial heat flux) is
- * accepted for the warm-start interface and may be NULL; the seed does not
- * use it. */
+ * of total_cells doubles; q0 may be NULL, meaning zero).  The seed is Grad's
+ * distribution with its heat-flux part only, the flux along axis 0,
+ *   f = f_M(n, u, T) [1 + q0 xi_0 / (n T^2) (xi^2 / (5 T) - 1)],  xi = p - u,
+ * reduced over p^z (Sec. II) and projected on the model's basis axis by axis
+ * as the equilibrium of Sec. IV.D is; with q0 = 0 it is that truncated
+ * equilibrium, f' = n g_0 g_1 and f'' = T f'.  When both expansion orders are
+ * at least 3 the model moments of the seed return n, u, T and q0 exactly.
+ * Host arrays are checked (finite, n > 0, T > 0; VLB_ERR_INVALID otherwise);
+ * device arrays are used as given.  Synchronises the stream. */
 vlb_status vlb_init_from_moments(vlb_ctx* ctx, const double* n, const double* u0, const double* u1, const double* T,
                                  const double* q0, int on_device);
 

@@ -613,21 +613,27 @@ vlb_status vlb_init_equilibrium(vlb_ctx* c, double n0, double u0, double u1, dou
 
 vlb_status vlb_init_from_moments(vlb_ctx* c, const double* n, const double* u0, const double* u1, const double* T,
                                  const double* q0, int on_device) {
-  (void)q0;
   if (!c || !n || !u0 || !u1 || !T) return fail(c, VLB_ERR_INVALID, "null argument");
   const size_t N = size_t(c->total_cells);
-  const double* src[4] = {n, u0, u1, T};
-  double* dev = c->d_mom;  // 9 doubles per cell of room: use four of them as staging
-  for (int a = 0; a < 4; ++a) {
+  if (!on_device)
+    for (size_t i = 0; i < N; ++i)
+      if (!(n[i] > 0.0) || !(T[i] > 0.0) || !std::isfinite(u0[i]) || !std::isfinite(u1[i]) ||
+          (q0 && !std::isfinite(q0[i])))
+        return fail(c, VLB_ERR_INVALID, "fields must be finite with n > 0 and T > 0");
+  const double* src[5] = {n, u0, u1, T, q0};
+  double* dev = c->d_mom;  // 9 doubles per cell of room: five of them stage the fields
+  for (int a = 0; a < 5; ++a) {
+    if (!src[a]) continue;
     VLB_CUDA(c, cudaMemcpyAsync(dev + a * N, src[a], sizeof(double) * N,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
   }
   if (!on_device) VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  const double* dq = q0 ? dev + 4 * N : nullptr;
   cudaError_t e = c->prec == VLB_FP64
                       ? launch_seed<double>(static_cast<double*>(c->F[c->cur]), c->total_cells, c->Vp, c->margs, dev,
-                                            dev + N, dev + 2 * N, dev + 3 * N, c->stream)
+                                            dev + N, dev + 2 * N, dev + 3 * N, dq, c->stream)
                       : launch_seed<float>(static_cast<float*>(c->F[c->cur]), c->total_cells, c->Vp, c->margs, dev,
-                                           dev + N, dev + 2 * N, dev + 3 * N, c->stream);
+                                           dev + N, dev + 2 * N, dev + 3 * N, dq, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "seed kernel launch");
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->last = c->cur;

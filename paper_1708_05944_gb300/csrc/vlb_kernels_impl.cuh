@@ -216,34 +216,90 @@ cudaError_t launch_init_equilibrium(real* F, long long cells, int Vp, const Mode
 }
 
 // ---------------------------------------------------------------- seeding from moments, one CTA per cell
+// Table input vector of the one-axis function xi^k g(p) (xi = p - u, g the
+// unit-mass Gaussian of mean u and variance T) for k <= 3, on the semi-axis of
+// sign `side` (half range) or the whole line (full range, side ignored).
+// Full range: the table takes E[He_l h] / l!, and (p - u) acts on that sequence
+// as a_l -> (l + 1) a_{l+1} + a_{l-1} - u a_l (from p He_l = He_{l+1} + l He_{l-1}).
+// Half range: the table takes the raw moments int_0^inf p^s h(side p) dp; with
+// h(-p) = (-1)^k (p + u)^k g_{-u}(p) both sides are the binomial expansion of
+// (p - v)^k, v = side u, over the raw moments of g_v on [0, inf).
+__device__ inline void xi_power_vector(int kind, int N, double u, double T, int k, int side, double* out) {
+  double m[MAXN + 3];
+  if (kind == 0) {
+    eq_moment_vector<double>(0, N + k, u, T, m);
+    for (int it = 0; it < k; ++it) {
+      const int top = N + k - it - 1;  // entries 0..top stay valid after this application
+      double prev = 0.0;                // old m[l - 1]
+      for (int l = 0; l <= top; ++l) {
+        const double cur = m[l];
+        m[l] = double(l + 1) * m[l + 1] + prev - u * cur;
+        prev = cur;
+      }
+    }
+    for (int l = 0; l <= N; ++l) out[l] = m[l];
+    return;
+  }
+  const double v = side > 0 ? u : -u;
+  eq_moment_vector<double>(1, N + k, v, T, m);
+  // binomial coefficients C(k, i) (-v)^(k - i)
+  double c[4] = {1, 0, 0, 0};
+  for (int it = 0; it < k; ++it)
+    for (int i = it + 1; i >= 0; --i) c[i] = (i ? c[i - 1] : 0.0) - v * c[i];
+  const double sgn = (side < 0 && (k & 1)) ? -1.0 : 1.0;
+  for (int s = 0; s <= N; ++s) {
+    double acc = 0;
+    for (int i = 0; i <= k; ++i) acc += c[i] * m[s + i];
+    out[s] = sgn * acc;
+  }
+}
+
+// Populations of xi^k g on one axis: pop[j] = sum_s tab[j][s] vec_side(j)[s].
+__device__ inline void xi_power_populations(int kind, int N, int nq, const double* p, const double* tab, double u, double T,
+                                     int k, double* pop) {
+  double vp[MAXN], vm[MAXN];
+  xi_power_vector(kind, N, u, T, k, 1, vp);
+  if (kind == 1) xi_power_vector(kind, N, u, T, k, -1, vm);
+  for (int j = 0; j < nq; ++j) {
+    const double* v = (kind == 1 && p[j] < 0.0) ? vm : vp;
+    double g = 0;
+    for (int s = 0; s <= N; ++s) g += tab[j * MAXN + s] * v[s];
+    pop[j] = g;
+  }
+}
+
+// f' = n g0 g1 + q0/T^2 g0 g1 xi0 [(xi0^2 + xi1^2)/(5T) - 4/5],
+// f'' = T n g0 g1 + q0/T^2 g0 g1 xi0 [(xi0^2 + xi1^2)/5 - 2T/5]:
+// Grad's distribution with the heat-flux part only (along axis 0), p^z
+// integrated out, projected on the model basis axis by axis.
 template <typename real>
 __global__ void seed_kernel(real* F, long long cells, int Vp, const __grid_constant__ ModelArgs m, const double* n,
-                            const double* u0, const double* u1, const double* T) {
-  __shared__ double g0[MAXQ], g1[MAXQ];
+                            const double* u0, const double* u1, const double* T, const double* q0) {
+  __shared__ double A[3][MAXQ], B[2][MAXQ];  // axis 0: xi^0, xi^1, xi^3; axis 1: xi^0, xi^2
   for (long long c = blockIdx.x; c < cells; c += gridDim.x) {
-    if (threadIdx.x < 2) {
-      const int ax = threadIdx.x;
-      double mp[MAXN], mm[MAXN];
-      const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0, nq = ax ? m.nq1 : m.nq0;
-      const double u = ax ? u1[c] : u0[c];
-      eq_moment_vector<double>(kind, N, u, T[c], mp);
-      eq_moment_vector<double>(kind, N, -u, T[c], mm);
-      for (int k = 0; k < nq; ++k) {
-        const double pk = ax ? m.p1[k] : m.p0[k];
-        const double* mv = (kind == 1 && pk < 0.0) ? mm : mp;
-        double g = 0;
-        for (int s = 0; s <= N; ++s) g += (ax ? m.tab1 : m.tab0)[k * MAXN + s] * mv[s];
-        (ax ? g1 : g0)[k] = g;
+    const double Tc = T[c], qc = q0 ? q0[c] : 0.0;
+    if (threadIdx.x < 5) {
+      const int t = threadIdx.x;
+      if (t < 3) {
+        const int k = t == 2 ? 3 : t;
+        xi_power_populations(m.kind0, m.N0, m.nq0, m.p0, m.tab0, u0[c], Tc, k, A[t]);
+      } else {
+        xi_power_populations(m.kind1, m.N1, m.nq1, m.p1, m.tab1, u1[c], Tc, 2 * (t - 3), B[t - 3]);
       }
     }
     __syncthreads();
     const int V = m.nq0 * m.nq1;
+    const double cq = qc / (Tc * Tc);
     for (int x = threadIdx.x; x < 2 * Vp; x += blockDim.x) {
       const int d = x >= Vp, v = x - d * Vp;
       real val = real(0);
       if (v < V) {
         const int i = v / m.nq1, j = v - i * m.nq1;
-        val = real(n[c] * g0[i] * g1[j] * (d ? T[c] : 1.0));
+        const double base = n[c] * A[0][i] * B[0][j];
+        const double t3 = A[2][i] * B[0][j] + A[1][i] * B[1][j];
+        const double t1 = A[1][i] * B[0][j];
+        val = d ? real(Tc * base + cq * (0.2 * t3 - 0.4 * Tc * t1))
+                : real(base + cq * (t3 / (5.0 * Tc) - 0.8 * t1));
       }
       F[c * 2 * Vp + x] = val;
     }
@@ -253,9 +309,9 @@ __global__ void seed_kernel(real* F, long long cells, int Vp, const __grid_const
 
 template <typename real>
 cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, const double* n, const double* u0,
-                        const double* u1, const double* T, cudaStream_t s) {
+                        const double* u1, const double* T, const double* q0, cudaStream_t s) {
   const long long blocks = cells < 152 * 16 ? cells : 152 * 16;
-  seed_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(F, cells, Vp, m, n, u0, u1, T);
+  seed_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(F, cells, Vp, m, n, u0, u1, T, q0);
   return cudaGetLastError();
 }
 
@@ -334,7 +390,7 @@ template size_t channel_smem_bytes<VLB_REAL>(ChanVariant, int, int);
 template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_REAL>&, const ModelArgs&, const void*, int,
                                               int, cudaStream_t);
 template cudaError_t launch_seed<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
-                                           const double*, const double*, const double*, cudaStream_t);
+                                           const double*, const double*, const double*, const double*, cudaStream_t);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,
                                               cudaStream_t);
 

@@ -49,10 +49,11 @@ template <typename real>
 cudaError_t launch_init_equilibrium(real* F, long long cells, int Vp, const ModelArgs& m, double n0, double u0,
                                     double u1, double T0, cudaStream_t s);
 
-// f_eq(n_c, (u0_c, u1_c), T_c) per cell from device arrays.
+// Grad heat-flux form of n_c, (u0_c, u1_c), T_c, q0_c (q0 may be null: zero
+// flux, the truncated equilibrium) projected on the model, per cell from device arrays.
 template <typename real>
 cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, const double* n, const double* u0,
-                        const double* u1, const double* T, cudaStream_t s);
+                        const double* u1, const double* T, const double* q0, cudaStream_t s);
 
 // Per cell, FP64: n, u0, u1, T, T00, T01, T11, q0, q1 (stride 9).
 template <typename real>

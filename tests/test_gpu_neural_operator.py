@@ -11,6 +11,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 from oracle.couette import CouetteGrid, CouetteOracle, Wall  # noqa: E402
+from oracle import seeding  # noqa: E402
 from oracle.neural_operator import NeuralOperator as RefNO  # noqa: E402
 from paper_1708_05944_gb300 import vlb  # noqa: E402
 from tests.helpers import to_oracle  # noqa: E402
@@ -80,19 +81,35 @@ def test_training_lowers_the_loss():
 
 
 @pytest.mark.parametrize("prec", [vlb.VLB_FP64, vlb.VLB_FP32_BULK])
-def test_seed_from_moments_is_the_truncated_equilibrium(prec):
-    spec, N = "HH(4;8)xH(4;20)", 40
+@pytest.mark.parametrize("spec", ["HH(4;8)xH(4;20)", "H(4;6)xHH(3;5)"])
+@pytest.mark.parametrize("with_q", [False, True])
+def test_seed_from_moments_matches_oracle(prec, spec, with_q):
+    N = 40
     o = CouetteOracle(spec, CouetteGrid(N), Wall(0.1), Wall(0.0), 0.1)
     rng = np.random.default_rng(3)
     n = 1 + 0.1 * rng.uniform(-1, 1, N)
     u1 = 0.2 * rng.uniform(-1, 1, N)
     u0 = 0.05 * rng.uniform(-1, 1, N)
     T = 1 + 0.1 * rng.uniform(-1, 1, N)
-    f1, f2 = o.m.feq(n, u0, u1, T)
+    q0 = 0.05 * rng.uniform(-1, 1, N) if with_q else None
+    f1, f2 = seeding.seed(o.m, n, u0, u1, T, q0)
     c = vlb.Couette(spec, prec, [dict(n_cells=N)], [(0.1, 1.0)], [(0.0, 1.0)], [0.1], [1])
-    c.init_from_moments(n, u0, u1, T, q0=np.zeros(N))
+    c.init_from_moments(n, u0, u1, T, q0=q0)
     got = to_oracle(c.read_f())
     ref = np.stack([f1, f2])
     tol = 1e-13 if prec == vlb.VLB_FP64 else 1e-6
     assert np.abs(got - ref).max() / np.abs(ref).max() < tol
+    if with_q:
+        mom = o.m.full_moments(got.astype(np.float64))
+        assert np.abs(mom["q0"] - q0).max() < (1e-13 if prec == vlb.VLB_FP64 else 1e-6)
+    c.close()
+
+
+def test_seed_rejects_invalid_fields():
+    c = vlb.Couette("HH(3;4)xH(4;8)", vlb.VLB_FP64, [dict(n_cells=8)], [(0.1, 1.0)], [(0.0, 1.0)], [0.1], [1])
+    ones, zeros = np.ones(8), np.zeros(8)
+    with pytest.raises(vlb.VlbError):
+        c.init_from_moments(ones, zeros, zeros, -ones)
+    with pytest.raises(vlb.VlbError):
+        c.init_from_moments(zeros, zeros, zeros, ones)
     c.close()
