@@ -158,7 +158,11 @@ vlb_status vlb_init_equilibrium(vlb_ctx* ctx, double n0, double u0, double u1, d
 /* Copy a distribution in (vlb_set_f: becomes the current F_l) or out
  * (vlb_read_f: the most recently written one -- after vlb_stage(k) that
  * stage's output, after vlb_step the new F_l).  f has the documented layout
- * and the context's real type; on_device selects a device or host pointer. */
+ * and the context's real type; on_device selects a device or host pointer.
+ * The device buffers hold the deviation F - R from the rest state
+ * R = f_eq(1, 0, 1) (populations w0_i w1_j): a kernel converts on the way in
+ * and out, each element summed in double and rounded once.  A host copy is
+ * staged in a distribution buffer that holds nothing live at the time. */
 vlb_status vlb_set_f(vlb_ctx* ctx, const void* f, int on_device);
 vlb_status vlb_read_f(vlb_ctx* ctx, void* f, int on_device);
 
@@ -211,7 +215,10 @@ vlb_status vlb_wall_density(vlb_ctx* ctx, double* nw);
 vlb_status vlb_residual(vlb_ctx* ctx, double* l2_u, double* l2_n, double* l2_T);
 
 /* Write / restore the distribution and step counter to / from a file
- * (little-endian; a header records model, precision and sizes, checked on load). */
+ * (little-endian; a header records model, precision and sizes, checked on load).
+ * The file holds the device representation -- the deviation F - R from the
+ * rest state in the context's real type -- so a run continued from it is
+ * bitwise the run that wrote it. */
 vlb_status vlb_save(vlb_ctx* ctx, const char* path);
 vlb_status vlb_load(vlb_ctx* ctx, const char* path);
 

@@ -193,6 +193,54 @@ vlb_status compute_moments(vlb_ctx* c, double* dst) {
   return VLB_OK;
 }
 
+// Weights in single precision and the sums of the rest state R_ij = w0_i w1_j
+// that the kernels add back to the deviation sums (see ModelArgs).
+void fill_reference(ModelArgs& m) {
+  double s0 = 0, s1 = 0, sp0 = 0, sp1 = 0, sq0 = 0, sq1 = 0, sf0 = 0, sf1 = 0, pos = 0, neg = 0;
+  for (int k = 0; k < m.nq0; ++k) {
+    m.w0f[k] = float(m.w0[k]);
+    s0 += m.w0[k];
+    sp0 += m.p0[k] * m.w0[k];
+    sq0 += m.p0[k] * m.p0[k] * m.w0[k];
+    sf0 += double(m.w0f[k]);
+    if (m.p0[k] > 0.0) pos += m.p0[k] * m.w0[k];
+    if (m.p0[k] < 0.0) neg += m.p0[k] * m.w0[k];
+  }
+  for (int k = 0; k < m.nq1; ++k) {
+    m.w1f[k] = float(m.w1[k]);
+    s1 += m.w1[k];
+    sp1 += m.p1[k] * m.w1[k];
+    sq1 += m.p1[k] * m.p1[k] * m.w1[k];
+    sf1 += double(m.w1f[k]);
+  }
+  m.ref_n = s0 * s1;
+  m.ref_r = sp0 * s1;
+  m.ref_p = s0 * sp1;
+  m.ref_e = sq0 * s1 + s0 * sq1 + s0 * s1;
+  m.ref_sum_f = sf0 * sf1;
+  m.ref_flux_pos = pos * s1;
+  m.ref_flux_neg = neg * s1;
+}
+
+// The buffer that holds neither F_l nor the last result: free between calls.
+int spare_buffer(const vlb_ctx* c) {
+  for (int b = 0; b < 3; ++b)
+    if (b != c->cur && b != c->last) return b;
+  return -1;
+}
+
+// F (caller layout, V per field) <-> D = F - R (device layout, Vp per field).
+vlb_status convert(vlb_ctx* c, const void* src, int src_pitch, void* dst, int dst_pitch, int to_deviation) {
+  cudaError_t e = c->prec == VLB_FP64
+                      ? launch_deviation<double>(static_cast<const double*>(src), src_pitch,
+                                                 static_cast<double*>(dst), dst_pitch, c->total_cells, c->margs,
+                                                 to_deviation, c->stream)
+                      : launch_deviation<float>(static_cast<const float*>(src), src_pitch, static_cast<float*>(dst),
+                                                dst_pitch, c->total_cells, c->margs, to_deviation, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "conversion kernel launch");
+  return VLB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -349,6 +397,7 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
       m.tab1f[k * MAXN + s] = float(m.tab1[k * MAXN + s]);
     }
   }
+  fill_reference(m);
   c->k32.reset(new KArgs<float>());
   c->k64.reset(new KArgs<double>());
   memset(c->k32.get(), 0, sizeof(KArgs<float>));
@@ -490,6 +539,7 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
       }
     }
   }
+  fill_reference(m);
   {
     std::vector<double> kd;
     for (const std::vector<double>* v : {&c->ax[0].K, &c->ax[0].Kt, &c->ax[1].K, &c->ax[1].Kt})
@@ -644,9 +694,15 @@ vlb_status vlb_init_from_moments(vlb_ctx* c, const double* n, const double* u0, 
 
 vlb_status vlb_set_f(vlb_ctx* c, const void* f, int on_device) {
   if (!c || !f) return fail(c, VLB_ERR_INVALID, "null argument");
-  const size_t w = size_t(c->V) * c->esize, pitch = size_t(c->Vp) * c->esize;
-  VLB_CUDA(c, cudaMemcpy2DAsync(c->F[c->cur], pitch, f, w, w, size_t(c->total_cells) * 2,
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  const void* src = f;
+  if (!on_device) {  // stage the host array in a buffer that holds nothing live
+    void* stage = c->F[(c->cur + 1) % 3];
+    VLB_CUDA(c, cudaMemcpyAsync(stage, f, size_t(c->total_cells) * 2 * c->V * c->esize, cudaMemcpyHostToDevice,
+                                c->stream));
+    src = stage;
+  }
+  vlb_status st = convert(c, src, c->V, c->F[c->cur], c->Vp, 1);
+  if (st != VLB_OK) return st;
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->last = c->cur;
   c->stage_done = 0;
@@ -656,9 +712,16 @@ vlb_status vlb_set_f(vlb_ctx* c, const void* f, int on_device) {
 
 vlb_status vlb_read_f(vlb_ctx* c, void* f, int on_device) {
   if (!c || !f) return fail(c, VLB_ERR_INVALID, "null argument");
-  const size_t w = size_t(c->V) * c->esize, pitch = size_t(c->Vp) * c->esize;
-  VLB_CUDA(c, cudaMemcpy2DAsync(f, w, c->F[c->last], pitch, w, size_t(c->total_cells) * 2,
-                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (on_device) {
+    vlb_status st = convert(c, c->F[c->last], c->Vp, f, c->V, 0);
+    if (st != VLB_OK) return st;
+  } else {
+    void* stage = c->F[spare_buffer(c)];
+    vlb_status st = convert(c, c->F[c->last], c->Vp, stage, c->V, 0);
+    if (st != VLB_OK) return st;
+    VLB_CUDA(c, cudaMemcpyAsync(f, stage, size_t(c->total_cells) * 2 * c->V * c->esize, cudaMemcpyDeviceToHost,
+                                c->stream));
+  }
   return check_err(c);
 }
 
@@ -805,7 +868,7 @@ vlb_status vlb_save(vlb_ctx* c, const char* path) {
   if (!c || !path) return fail(c, VLB_ERR_INVALID, "null argument");
   if (c->stage_done % 3 != 0) return fail(c, VLB_ERR_STATE, "save between full steps only");
   SaveHeader h{};
-  memcpy(h.magic, "VLBSAVE1", 8);
+  memcpy(h.magic, "VLBSAVE2", 8);
   for (int a = 0; a < 2; ++a) {
     h.model[3 * a] = c->model.kind[a];
     h.model[3 * a + 1] = c->model.N[a];
@@ -816,8 +879,13 @@ vlb_status vlb_save(vlb_ctx* c, const char* path) {
   h.V = c->V;
   h.total_cells = c->total_cells;
   h.steps = c->steps;
+  // the device buffer as stored (the deviation from the rest state), so that a run
+  // continued from the file is bitwise the run that wrote it
   std::vector<char> buf(size_t(c->total_cells) * 2 * c->V * c->esize);
-  vlb_status st = vlb_read_f(c, buf.data(), 0);
+  const size_t w = size_t(c->V) * c->esize, pitch = size_t(c->Vp) * c->esize;
+  VLB_CUDA(c, cudaMemcpy2DAsync(buf.data(), w, c->F[c->last], pitch, w, size_t(c->total_cells) * 2,
+                                cudaMemcpyDeviceToHost, c->stream));
+  vlb_status st = check_err(c);
   if (st != VLB_OK) return st;
   FILE* fp = fopen(path, "wb");
   if (!fp) return fail(c, VLB_ERR_INVALID, std::string("cannot open ") + path);
@@ -834,7 +902,7 @@ vlb_status vlb_load(vlb_ctx* c, const char* path) {
   FILE* fp = fopen(path, "rb");
   if (!fp) return fail(c, VLB_ERR_INVALID, std::string("cannot open ") + path);
   SaveHeader h{};
-  bool ok = fread(&h, sizeof(h), 1, fp) == 1 && memcmp(h.magic, "VLBSAVE1", 8) == 0;
+  bool ok = fread(&h, sizeof(h), 1, fp) == 1 && memcmp(h.magic, "VLBSAVE2", 8) == 0;
   for (int a = 0; a < 2 && ok; ++a)
     ok = h.model[3 * a] == c->model.kind[a] && h.model[3 * a + 1] == c->model.N[a] &&
          h.model[3 * a + 2] == c->model.Q[a];
@@ -847,8 +915,13 @@ vlb_status vlb_load(vlb_ctx* c, const char* path) {
   ok = ok && fread(buf.data(), 1, buf.size(), fp) == buf.size();
   fclose(fp);
   if (!ok) return fail(c, VLB_ERR_INVALID, "file does not match this context");
-  vlb_status st = vlb_set_f(c, buf.data(), 0);
-  if (st != VLB_OK) return st;
+  const size_t w = size_t(c->V) * c->esize, pitch = size_t(c->Vp) * c->esize;
+  VLB_CUDA(c, cudaMemcpy2DAsync(c->F[c->cur], pitch, buf.data(), w, w, size_t(c->total_cells) * 2,
+                                cudaMemcpyHostToDevice, c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->last = c->cur;
+  c->stage_done = 0;
+  c->have_prev = false;
   c->steps = h.steps;
   return VLB_OK;
 }

@@ -10,6 +10,9 @@
 //   -> WENO-5 in lambda (walking the column) and in xi, chi flux differences,
 //      BGK, RK3 combine -> bulk store.
 //
+// Distribution buffers hold the deviation D = F - R from the rest state
+// (ModelArgs), as in the Couette kernel.
+//
 // Cell (s, p) of the grid has global index p * n_lambda + s (lambda fastest).
 #pragma once
 #include "vlb_device.cuh"
@@ -67,14 +70,14 @@ struct ChanSmem {
   static constexpr size_t lbuf_off = tile_off + size_t(NCS) * ROW * sizeof(real);
   static constexpr size_t fl_off = lbuf_off + size_t(NC) * ROW * sizeof(real);
   static constexpr size_t dbl_off = (fl_off + size_t(NC) * ROW * sizeof(real) + 15) & ~size_t(15);
-  // doubles: reduction (NW*4 + TP*NW), wall n_w (TP), scalars (16)
-  static constexpr size_t n_dbl = NW * 4 + TP * NW + TP + 16;
+  // doubles: reduction (NW*4 + TP*NW), wall n_w (TP), scalars (16), equilibrium sum targets (NC)
+  static constexpr size_t n_dbl = NW * 4 + TP * NW + TP + 16 + NC;
   static constexpr size_t real_off = dbl_off + n_dbl * sizeof(double);
   // reals: p0, p1, 1/w0, 1/w1 (Q each), tables (Q*MAXN each), per cell: 10 geometry + n, T, u0, u1, 1/tau,
   // g0 (Q0), g1 (Q1), moment vectors (4*MAXN); boundary: wall factors (Q0 + Q1), inlet/outlet factors (TS*Q1 each),
-  // rest factors (Q0)
+  // weights (Q0 + Q1)
   static constexpr size_t n_real = 2 * Q0 + 2 * Q1 + (Q0 + Q1) * MAXN + size_t(NC) * (15 + Q0 + Q1 + 4 * MAXN) +
-                                   (Q0 + Q1) + 2 * size_t(TS) * Q1 + Q0 + 2 * TS + 8;
+                                   (Q0 + Q1) + 2 * size_t(TS) * Q1 + Q0 + Q1 + 2 * TS + 8;
   static constexpr size_t bytes = real_off + n_real * sizeof(real);
 };
 
@@ -96,6 +99,7 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
   double* red = reinterpret_cast<double*>(smem + L::dbl_off);  // NW*4 + TP*NW
   double* nwv = red + NW * 4 + TP * NW;                           // TP
   double* dsc = nwv + TP;                                         // 16 scalars
+  double* cnd = dsc + 16;                                         // [q] target of sum g0n * sum g1
   real* rp = reinterpret_cast<real*>(smem + L::real_off);
   real* p0r = rp;
   real* p1r = p0r + Q0;
@@ -116,10 +120,10 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
   real* gw1 = gw0 + Q0;               // wall xi factor g_xi(0, T0)
   real* gin = gw1 + Q1;               // [TS][Q1] inlet xi factor per row
   real* gout = gin + TS * Q1;         // [TS][Q1]
-  real* gr0 = gout + TS * Q1;         // spare [Q0]
-  real* uin = gr0 + Q0;               // [TS] inlet / outlet u^xi of the adjacent cell
+  real* w0r = gout + TS * Q1;         // [Q0] weights: R_ij = w0_i w1_j in the bulk type
+  real* w1r = w0r + Q0;               // [Q1]
+  real* uin = w1r + Q1;               // [TS] inlet / outlet u^xi of the adjacent cell
   real* uout = uin + TS;
-  (void)gr0;
 
   const int nts = (nl + TS - 1) / TS;
   const int s0 = (blockIdx.x % nts) * TS, p0 = (blockIdx.x / nts) * TP;
@@ -166,10 +170,12 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
   for (int x = tid; x < Q0; x += NT) {
     p0r[x] = F32 ? real(m.p0f[x]) : real(m.p0[x]);
     iw0[x] = F32 ? real(m.iw0f[x]) : real(m.iw0[x]);
+    w0r[x] = F32 ? real(m.w0f[x]) : real(m.w0[x]);
   }
   for (int x = tid; x < Q1; x += NT) {
     p1r[x] = F32 ? real(m.p1f[x]) : real(m.p1[x]);
     iw1[x] = F32 ? real(m.iw1f[x]) : real(m.iw1[x]);
+    w1r[x] = F32 ? real(m.w1f[x]) : real(m.w1[x]);
   }
   for (int x = tid; x < Q0 * MAXN; x += NT) tb0[x] = F32 ? real(m.tab0f[x]) : real(m.tab0[x]);
   for (int x = tid; x < Q1 * MAXN; x += NT) tb1[x] = F32 ? real(m.tab1f[x]) : real(m.tab1[x]);
@@ -217,10 +223,11 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
     kq += __shfl_xor_sync(0xffffffffu, kq, 1);
     const double d0 = __shfl_sync(0xffffffffu, kq, 8), d1 = __shfl_sync(0xffffffffu, kq, 16);
     const double de = __shfl_sync(0xffffffffu, kq, 24);
-    if (lane == 0) {
-      const real nn = real(kq), u0 = real(d0) / nn, u1 = real(d1) / nn;
-      const real T = (real(de) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
+    if (lane == 0) {  // sums of D plus those of R
+      const real nn = real(kq + m.ref_n), u0 = real(d0 + m.ref_r) / nn, u1 = real(d1 + m.ref_p) / nn;
+      const real T = (real(de + m.ref_e) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
       cn[q] = nn;
+      cnd[q] = kq + (F32 ? m.ref_sum_f : m.ref_n);
       cu0[q] = u0;
       cu1[q] = u1;
       cT[q] = T;
@@ -322,6 +329,8 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
       g1[q * Q1 + k] = g;
     }
   }
+  __syncthreads();
+  if (tid < NC && tid % TS < TSe) normalise_equilibrium<real>(g0n + tid * Q0, g1 + tid * Q1, Q0, Q1, cnd[tid]);
   // centreline lambda = 0: specular reflection, ghost 1-k mirrors cell k (p^lambda -> -p^lambda)
   if (s0 < 3) {  // the lambda halo reaches the ghost cells s = -1, -2, -3 (s = -k mirrors cell k - 1)
     constexpr int QH = Q0 / 2;
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
     }
     __syncthreads();
     if (tid < TP) {
-      double s = 0;
+      double s = m.ref_flux_pos;  // the outgoing flux of R
       for (int w = 0; w < NW; ++w) s += red[NW * 4 + tid * NW + w];
       double den0 = 0, den1 = 0;  // incoming flux of f_eq(1, 0, T0): sum_{p^l<0} g p^l * sum_j g
       for (int k = 0; k < Q0; ++k)
@@ -380,7 +389,8 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
         g2v = real(6) * F0 - real(8) * F1 + real(3) * F2;
         g3v = g2v;
       } else {
-        g1v = g2v = g3v = real(nwv[c]) * gw0[i] * gw1[j] * (d ? T0 : real(1));
+        g1v = g2v = g3v = real(nwv[c] * double(gw0[i]) * double(gw1[j]) * (d ? double(T0) : 1.0) -
+                               m.w0[i] * m.w1[j]);  // f_eq(n_w, 0, T0) - R
       }
       if (sA + 1 < TS + 3) tile[slot(sA + 1, c) * ROW + d * VP + v] = g1v;
       if (sA + 2 < TS + 3) tile[slot(sA + 2, c) * ROW + d * VP + v] = g2v;
@@ -403,7 +413,7 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
         sn += F[v];
         sx += p1r[j] * F[v];
       }
-      const double dn = warp_sum<real>(double(sn)), dx = warp_sum<real>(double(sx));
+      const double dn = warp_sum<real>(double(sn)) + m.ref_n, dx = warp_sum<real>(double(sx)) + m.ref_p;
       if (lane == 0) ures[sr] = real(dx / dn);
     }
     __syncthreads();
@@ -436,7 +446,7 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
       }
       const real Vx = bb * p1r[j] - cc * p0r[i];
       const bool inflow = end == 0 ? (Vx > real(0)) : (Vx < real(0));
-      const real val = inflow ? nres * gw0[i] * gres[sr * Q1 + j] * (d ? T0 : real(1))
+      const real val = inflow ? nres * gw0[i] * gres[sr * Q1 + j] * (d ? T0 : real(1)) - w0r[i] * w1r[j]
                               : tile[slot(sr, cA) * ROW + d * VP + v];
       for (int k = 1; k <= 3; ++k) {
         const int c = end == 0 ? cA - k : cA + k;
@@ -448,7 +458,7 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
 
   // ==== phase D: WENO-5 in lambda (walking each column) and in xi, flux differences, BGK, RK3
   const real dtr = F32 ? real(a.cd.dtf) : real(a.cd.dt);
-  const real ca = F32 ? real(a.caf) : real(a.ca), cb = F32 ? real(a.cbf) : real(a.cb);
+  const real ca = F32 ? real(a.caf) : real(a.ca);  // cb = 1 - ca: see StageArgs
   const real ccoef = (F32 ? real(a.ccf) : real(a.cc)) * dtr;
   for (int x = tid; x < 2 * V; x += NT) {
     const int d = x >= V, v = x - d * V;
@@ -479,11 +489,11 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
           const real Fp = Vp_ >= real(0) ? weno5<real>(h[1], h[2], h[3], h[4], h[5], sc)
                                          : weno5<real>(h[6], h[5], h[4], h[3], h[2], sc);
           adv += (Vp_ * Fp - Vm * Fm) * gq[7];
-          const real feq = g0n[q * Q0 + i] * g1[q * Q1 + j] * (d ? cT[q] : real(1));
-          const real Lv = -adv + lbuf[q * ROW + d * VP + v] - (w3 - feq) * citau[q];
-          real o = cb * w3 + ccoef * Lv;
+          const real deq = g0n[q * Q0 + i] * g1[q * Q1 + j] * (d ? cT[q] : real(1)) - w0r[i] * w1r[j];
+          const real Lv = -adv + lbuf[q * ROW + d * VP + v] - (w3 - deq) * citau[q];
+          real o = w3 + ccoef * Lv;
           real* dst = flb + q * ROW + d * VP + v;
-          if (need_fl) o += ca * *dst;
+          if (need_fl) o += ca * (*dst - w3);
           *dst = o;  // this (cell, field, momentum) entry of F_l is not read again
           w0 = w1;
           w1 = w2;

@@ -48,6 +48,16 @@ struct ModelArgs {
   float tab0f[MAXQ * MAXN], tab1f[MAXQ * MAXN];  // single-precision copies for the FP32-bulk path
   float p0f[MAXQ], p1f[MAXQ], iw0f[MAXQ], iw1f[MAXQ];  // nodes and inverse weights, single precision
   double iw0[MAXQ], iw1[MAXQ];                         // inverse weights, double precision
+  float w0f[MAXQ], w1f[MAXQ];                          // weights, single precision
+  // Device distributions hold the deviation D = F - R from the rest state
+  // R_ij = w0_i w1_j (f_eq(1, 0, 1), the same for f' and f'').  R is a steady
+  // state of the discrete equations (advection and force cancel on it, BGK
+  // vanishes) and WENO-5 is unchanged by adding a constant, so the stage
+  // operator applied to D is the operator applied to F; storing D keeps the
+  // rounding of each update relative to |F - R| instead of |F|.  Sums of R:
+  double ref_n, ref_r, ref_p, ref_e;  // sum R, sum p0 R, sum p1 R, sum (p0^2 + p1^2) R + sum R
+  double ref_sum_f;                   // sum of the single-precision products float(w0_i) float(w1_j)
+  double ref_flux_pos, ref_flux_neg;  // sum over p0 > 0 (p0 < 0) of p0 R
 };
 
 template <typename real>
@@ -160,6 +170,21 @@ __device__ __forceinline__ void eq_moment_vector(int kind, int N, R u, R T, R* m
     if (N >= 1) m[1] = u * m[0] + T * g0;
     for (int s = 2; s <= N; ++s) m[s] = u * m[s - 1] + R(s - 1) * T * m[s - 2];
   }
+}
+
+// Rescale the axis-0 equilibrium factor (which carries n) so that the stored
+// factors reproduce the cell density exactly: sum_i gn_i sum_j g1_j = n.  In
+// exact arithmetic the truncated equilibrium already has this sum (Sec. IV.D);
+// in single precision the table contraction misses it by some 1e-7, and the
+// BGK term would turn that into a mass source of (dt / tau) 1e-7 n every step.
+// The sums are taken in double.
+template <typename R>
+__device__ __forceinline__ void normalise_equilibrium(R* gn, const R* g1, int nq0, int nq1, double n) {
+  double s0 = 0.0, s1 = 0.0;
+  for (int k = 0; k < nq0; ++k) s0 += double(gn[k]);
+  for (int k = 0; k < nq1; ++k) s1 += double(g1[k]);
+  const R sc = R(n / (s0 * s1));
+  for (int k = 0; k < nq0; ++k) gn[k] *= sc;
 }
 
 template <typename R>

@@ -198,7 +198,7 @@ __global__ void init_equilibrium_kernel(real* F, long long cells, int Vp, const 
     real val = real(0);
     if (v < V) {
       const int i = v / m.nq1, j = v - i * m.nq1;
-      val = real(n0 * g0[i] * g1[j] * (d ? T0 : 1.0));
+      val = real(n0 * g0[i] * g1[j] * (d ? T0 : 1.0) - m.w0[i] * m.w1[j]);  // stored as the deviation from R
     }
     F[x] = val;
   }
@@ -298,8 +298,8 @@ __global__ void seed_kernel(real* F, long long cells, int Vp, const __grid_const
         const double base = n[c] * A[0][i] * B[0][j];
         const double t3 = A[2][i] * B[0][j] + A[1][i] * B[1][j];
         const double t1 = A[1][i] * B[0][j];
-        val = d ? real(Tc * base + cq * (0.2 * t3 - 0.4 * Tc * t1))
-                : real(base + cq * (t3 / (5.0 * Tc) - 0.8 * t1));
+        const double full = d ? Tc * base + cq * (0.2 * t3 - 0.4 * Tc * t1) : base + cq * (t3 / (5.0 * Tc) - 0.8 * t1);
+        val = real(full - m.w0[i] * m.w1[j]);  // stored as the deviation from R
       }
       F[c * 2 * Vp + x] = val;
     }
@@ -312,6 +312,37 @@ cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, co
                         const double* u1, const double* T, const double* q0, cudaStream_t s) {
   const long long blocks = cells < 152 * 16 ? cells : 152 * 16;
   seed_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(F, cells, Vp, m, n, u0, u1, T, q0);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- caller layout <-> deviation from R
+template <typename real>
+__global__ void deviation_kernel(const real* src, int sp, real* dst, int dp, long long cells,
+                                 const __grid_constant__ ModelArgs m, int to_dev) {
+  const int V = m.nq0 * m.nq1;
+  const long long total = cells * 2 * dp;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total; x += (long long)gridDim.x * blockDim.x) {
+    const long long row = x / dp;  // (cell, field)
+    const int v = int(x - row * dp);
+    real val = real(0);
+    if (v < V) {
+      const int i = v / m.nq1, j = v - i * m.nq1;
+      const double r = m.w0[i] * m.w1[j];
+      const double s = double(src[row * sp + v]);
+      val = real(to_dev ? s - r : s + r);
+    }
+    if (v < V || to_dev) dst[row * dp + v] = val;
+  }
+}
+
+template <typename real>
+cudaError_t launch_deviation(const real* src, int src_pitch, real* dst, int dst_pitch, long long cells,
+                             const ModelArgs& m, int to_deviation, cudaStream_t s) {
+  const long long total = cells * 2 * dst_pitch;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  deviation_kernel<real><<<int(blocks), 256, 0, s>>>(src, src_pitch, dst, dst_pitch, cells, m, to_deviation);
   return cudaGetLastError();
 }
 
@@ -328,7 +359,7 @@ __global__ void moments_kernel(const real* F, long long cells, int Vp, const __g
     double sn = 0, s0 = 0, s1 = 0;
     for (int v = lane; v < V; v += 32) {
       const int i = v / nq1, j = v - i * nq1;
-      const double f1 = f[v];
+      const double f1 = double(f[v]) + m.w0[i] * m.w1[j];  // F = D + R
       sn += f1;
       s0 += m.p0[i] * f1;
       s1 += m.p1[j] * f1;
@@ -340,7 +371,8 @@ __global__ void moments_kernel(const real* F, long long cells, int Vp, const __g
     double t00 = 0, t01 = 0, t11 = 0, tr2 = 0, q0 = 0, q1 = 0;
     for (int v = lane; v < V; v += 32) {
       const int i = v / nq1, j = v - i * nq1;
-      const double f1 = f[v], f2 = f[Vp + v];
+      const double r = m.w0[i] * m.w1[j];
+      const double f1 = double(f[v]) + r, f2 = double(f[Vp + v]) + r;
       const double x0 = m.p0[i] - u0, x1 = m.p1[j] - u1;
       t00 += x0 * x0 * f1;
       t01 += x0 * x1 * f1;
@@ -391,6 +423,8 @@ template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_RE
                                               int, cudaStream_t);
 template cudaError_t launch_seed<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
                                            const double*, const double*, const double*, const double*, cudaStream_t);
+template cudaError_t launch_deviation<VLB_REAL>(const VLB_REAL*, int, VLB_REAL*, int, long long, const ModelArgs&, int,
+                                                cudaStream_t);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,
                                               cudaStream_t);
 

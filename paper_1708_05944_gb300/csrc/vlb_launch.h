@@ -55,6 +55,14 @@ template <typename real>
 cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, const double* n, const double* u0,
                         const double* u1, const double* T, const double* q0, cudaStream_t s);
 
+// Caller layout F (src_pitch or dst_pitch values per field) to and from the device
+// deviation D = F - R (to_deviation = 1: dst = src - R; 0: dst = src + R), the sum
+// taken in double.  Padding entries of a wider destination row are zeroed.  src and
+// dst may be the same buffer when the pitches agree.
+template <typename real>
+cudaError_t launch_deviation(const real* src, int src_pitch, real* dst, int dst_pitch, long long cells,
+                             const ModelArgs& m, int to_deviation, cudaStream_t s);
+
 // Per cell, FP64: n, u0, u1, T, T00, T01, T11, q0, q1 (stride 9).
 template <typename real>
 cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelArgs& m, double* out, cudaStream_t s);

@@ -8,6 +8,9 @@
 //   -> inertial force (1/R)[(p^phi)^2 K^R f - p^R K~^phi f] (Eq. boltz_couette_kom)
 //   -> WENO-5 fluxes along the cells, chi flux difference, BGK, RK3 combine
 //      (Eqs. weno5_flux, flux_kom_R / flux_kom_eta, BGK, rk3) -> global.
+//
+// Every distribution buffer holds the deviation D = F - R from the rest state
+// (ModelArgs): the operator is linear in R's part, which it leaves unchanged.
 #pragma once
 #include "vlb_device.cuh"
 
@@ -18,7 +21,11 @@ struct StageArgs {
   const real* Fprev;  // distribution L acts on
   const real* Fl;     // F_l of the step (read when ca != 0)
   real* Fout;
-  double ca, cb, cc;  // Fout = ca F_l + cb F_prev + cc dt L[F_prev]
+  // Fout = ca F_l + cb F_prev + cc dt L[F_prev] with cb = 1 - ca, evaluated as
+  // F_prev + ca (F_l - F_prev) + cc dt L so that the weights on F sum to exactly
+  // one in any precision (float(1/3) + float(2/3) = 1 + 3e-8 would add that much
+  // mass every step).
+  double ca, cb, cc;
   float caf, cbf, ccf;  // single-precision copies
   const InstDesc* inst;
   const TileDesc* tiles;
@@ -43,12 +50,12 @@ struct StageSmem {
     return (o + 15) & ~size_t(15);
   }
   // doubles: p0, p1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each, wall equilibria), reduction (NW*4),
-  // wall scratch: equilibrium factors (2*MAXQ), moment vectors (4*MAXN), scalars (16)
-  static constexpr size_t n_dbl = 2 * MAXQ + 2 * MAXQ * MAXN + NW * 4 + 2 * MAXQ + 4 * MAXN + 16;
+  // wall scratch: equilibrium factors (2*MAXQ), moment vectors (4*MAXN), scalars (16), cell n (TC)
+  static constexpr size_t n_dbl = 2 * MAXQ + 2 * MAXQ * MAXN + NW * 4 + 2 * MAXQ + 4 * MAXN + 16 + TC;
   __host__ __device__ static size_t real_off(int Vp) { return dbl_off(Vp) + n_dbl * sizeof(double); }
   // reals: p0, p1, 1/w0, 1/w1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each), n g_R and g_phi (TC*MAXQ each),
-  // cell n, T, u0, u1, 1/tau, cp, cm, 1/Rbar (TC each), moment vectors (TC*4*MAXN)
-  static constexpr size_t n_real = 4 * MAXQ + 2 * MAXQ * MAXN + 2 * TC * MAXQ + 8 * TC + TC * 4 * MAXN;
+  // cell n, T, u0, u1, 1/tau, cp, cm, 1/Rbar (TC each), moment vectors (TC*4*MAXN), w0, w1 (MAXQ each)
+  static constexpr size_t n_real = 4 * MAXQ + 2 * MAXQ * MAXN + 2 * TC * MAXQ + 8 * TC + TC * 4 * MAXN + 2 * MAXQ;
   __host__ __device__ static size_t bytes(int Vp) { return real_off(Vp) + n_real * sizeof(real); }
 };
 
@@ -81,6 +88,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   double* gw1 = gw0 + MAXQ;
   double* wmv = gw1 + MAXQ;    // wall moment vectors [axis*2 + side][s]
   double* mw = wmv + 4 * MAXN;  // [0] incoming equilibrium flux, [1] n_w
+  double* cnd = mw + 16;       // [t] cell density as summed (FP64)
   real* p0r = reinterpret_cast<real*>(smem + L::real_off(Vp));
   real* p1r = p0r + MAXQ;
   real* iw0 = p1r + MAXQ;  // 1 / w_i
@@ -98,6 +106,8 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   real* ccm = ccp + TC;
   real* cIR = ccm + TC;
   real* mv = cIR + TC;  // [t][axis*2 + side][s]
+  real* w0r = mv + TC * 4 * MAXN;  // weights: R_ij = w0_i w1_j in the bulk type
+  real* w1r = w0r + MAXQ;
 
   if (tid == 0) {
     mbar_init(bar, 1);
@@ -112,11 +122,15 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       p1r[x] = m.p1f[x];
       iw0[x] = m.iw0f[x];
       iw1[x] = m.iw1f[x];
+      w0r[x] = m.w0f[x];
+      w1r[x] = m.w1f[x];
     } else {
       p0r[x] = m.p0[x];
       p1r[x] = m.p1[x];
       iw0[x] = m.iw0[x];
       iw1[x] = m.iw1[x];
+      w0r[x] = m.w0[x];
+      w1r[x] = m.w1[x];
     }
   }
   for (int x = tid; x < MAXQ * MAXN; x += NT) {
@@ -198,10 +212,12 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     const double dr = __shfl_sync(0xffffffffu, kq, 8);
     const double dpp = __shfl_sync(0xffffffffu, kq, 16);
     const double de = __shfl_sync(0xffffffffu, kq, 24);
-    if (lane == 0) {  // the sums are FP64; the derived fields are formed in the bulk type
-      const real nn = real(kq), u0 = real(dr) / nn, u1 = real(dpp) / nn;
-      const real T = (real(de) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
+    if (lane == 0) {  // sums of D (FP64) plus those of R; the derived fields are formed in the bulk type
+      const real nn = real(kq + m.ref_n), u0 = real(dr + m.ref_r) / nn, u1 = real(dpp + m.ref_p) / nn;
+      const real T = (real(de + m.ref_e) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
       cn[t] = nn;
+      // target of sum_i gRn_i sum_j gP_j: the f_eq - R of phase D must sum to sum D
+      cnd[t] = kq + (F32 ? m.ref_sum_f : m.ref_n);
       cu0[t] = u0;
       cu1[t] = u1;
       cTr[t] = T;
@@ -277,6 +293,8 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       gP[t * MAXQ + k] = g;
     }
   }
+  __syncthreads();
+  if (tid < TCe) normalise_equilibrium<real>(gRn + tid * MAXQ, gP + tid * MAXQ, nq0, nq1, cnd[tid]);
   for (int wall = 0; wall < 2; ++wall) {
     const bool active = wall == 0 ? (c0 == 0) : (c0 + TC + 3 > n);
     if (!active) continue;  // uniform across the CTA
@@ -332,7 +350,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     if (lane == 0) red[warp] = num;
     __syncthreads();
     if (tid == 0) {
-      double sacc = 0;
+      double sacc = wall == 0 ? m.ref_flux_neg : m.ref_flux_pos;  // the outgoing flux of R
       for (int w = 0; w < NW; ++w) sacc += red[w];
       const double nwv = -sacc / mw[0];
       mw[1] = nwv;
@@ -340,7 +358,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       if (!isfinite(nwv)) atomicOr(a.err, ERR_NONFINITE);
     }
     __syncthreads();
-    const real nwr = real(mw[1]), Twr = real(Tw);
+    const double nwd = mw[1];
     for (int x = tid; x < 2 * V; x += NT) {
       const int d = x >= V, v = x - d * V;
       const int i = v / nq1, j = v - i * nq1;
@@ -352,8 +370,8 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
         g1 = real(3) * F0 - real(3) * F1 + F2;
         g2 = real(6) * F0 - real(8) * F1 + real(3) * F2;
         g3 = g2;  // never read by an outgoing stencil
-      } else {
-        g1 = g2 = g3 = nwr * real(gw0[i]) * real(gw1[j]) * (d ? Twr : real(1));
+      } else {  // f_eq(n_w, u_w, T_w) - R
+        g1 = g2 = g3 = real(nwd * gw0[i] * gw1[j] * (d ? Tw : 1.0) - m.w0[i] * m.w1[j]);
       }
       const int s1 = sA - dir, s2 = sA - 2 * dir, s3 = sA - 3 * dir;
       if (s1 >= 0 && s1 < TC + 6) tile[s1 * row + d * Vp + v] = g1;
@@ -365,7 +383,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
 
   // ==== phase D: WENO-5 fluxes along the cells, flux difference, BGK, RK3 combine (in place)
   const real dtr = F32 ? real(in.dt_f) : real(in.dt);
-  const real ca = F32 ? real(a.caf) : real(a.ca), cb = F32 ? real(a.cbf) : real(a.cb);
+  const real ca = F32 ? real(a.caf) : real(a.ca);
   const real cc = (F32 ? real(a.ccf) : real(a.cc)) * dtr;
   // per-cell factors of this tile in registers
   real rcp[TC], rcm[TC], rir[TC], rit[TC], rT[TC];
@@ -394,10 +412,10 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
         const real w6 = S[(t + 6) * row];
         const real fp = weno5<real>(up ? w1 : w6, up ? w2 : w5, up ? w3 : w4, up ? w4 : w3, up ? w5 : w2, sc);
         const real adv = pr * (rcp[t] * fp - rcm[t] * fm);
-        const real feq = gRn[t * MAXQ + i] * gP[t * MAXQ + j] * (d ? rT[t] : real(1));
-        const real Lv = -adv + lbuf[(t * 2 + d) * Vp + v] * rir[t] - (w3 - feq) * rit[t];
-        real o = cb * w3 + cc * Lv;
-        if (need_fl) o += ca * Fl[t * row];
+        const real deq = gRn[t * MAXQ + i] * gP[t * MAXQ + j] * (d ? rT[t] : real(1)) - w0r[i] * w1r[j];
+        const real Lv = -adv + lbuf[(t * 2 + d) * Vp + v] * rir[t] - (w3 - deq) * rit[t];
+        real o = w3 + cc * Lv;
+        if (need_fl) o += ca * (Fl[t * row] - w3);
         S[(t + 3) * row] = o;  // in place: this column's slot t+3 is not read again
         w0 = w1;
         w1 = w2;

@@ -94,8 +94,17 @@ extern "C" vlb_status vlb_step_static_scratch(vlb_ctx* c, const void* f_in, void
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("descriptor copy: ") + cudaGetErrorString(e));
   }
+  // the stage kernels work on the deviation D = F - R from the rest state: convert f_in into
+  // f_out, step f_out (stage 3 updates it in place: each CTA reads only its own F_l rows), and
+  // convert f_out back at the end
+  e = c->prec == VLB_FP64
+          ? launch_deviation<double>(static_cast<const double*>(f_in), c->V, static_cast<double*>(f_out), c->Vp,
+                                     c->total_cells, c->margs, 1, c->stream)
+          : launch_deviation<float>(static_cast<const float*>(f_in), c->V, static_cast<float*>(f_out), c->Vp,
+                                    c->total_cells, c->margs, 1, c->stream);
+  if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("conversion launch: ") + cudaGetErrorString(e));
   for (long long s = 0; s < nsteps; ++s) {
-    const void* Fl = s == 0 ? f_in : f_out;  // stage 3 may update f_out in place: each CTA reads only its own F_l rows
+    const void* Fl = f_out;
     for (int k = 1; k <= 3; ++k) {
       const void* prev = k == 1 ? Fl : (k == 2 ? s1 : s2);
       void* out = k == 1 ? s1 : (k == 2 ? s2 : f_out);
@@ -103,5 +112,11 @@ extern "C" vlb_status vlb_step_static_scratch(vlb_ctx* c, const void* f_in, void
       if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("stage launch: ") + cudaGetErrorString(e));
     }
   }
+  e = c->prec == VLB_FP64
+          ? launch_deviation<double>(static_cast<const double*>(f_out), c->Vp, static_cast<double*>(f_out), c->V,
+                                     c->total_cells, c->margs, 0, c->stream)
+          : launch_deviation<float>(static_cast<const float*>(f_out), c->Vp, static_cast<float*>(f_out), c->V,
+                                    c->total_cells, c->margs, 0, c->stream);
+  if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("conversion launch: ") + cudaGetErrorString(e));
   return VLB_OK;
 }

@@ -20,15 +20,16 @@ def perturbation(shape, seed: int = PARITY_SEED, amplitude: float = 0.01) -> np.
     return 1.0 + amplitude * rng.uniform(-1.0, 1.0, size=shape)
 
 
-def couette_instances(n_inst: int, seed: int = BATCH_SEED, n_min: int = 64, n_max: int = 1024):
-    """Circular Couette instances: cells ~ U{n_min..n_max}, log10 Kn ~ U[-3, 1],
+def couette_instances(n_inst: int, seed: int = BATCH_SEED, n_min: int = 64, n_max: int = 1024,
+                      log10_kn=(-3.0, 1.0)):
+    """Circular Couette instances: cells ~ U{n_min..n_max}, log10 Kn ~ U[log10_kn],
     inner wall speed ~ U[0.01, 0.5], R_out/R_in ~ U[1.5, 4] with R_in = 1."""
     rng = np.random.default_rng(seed)
     out = []
     for _ in range(n_inst):
         out.append(dict(
             n_cells=int(rng.integers(n_min, n_max + 1)),
-            kn=float(10.0 ** rng.uniform(-3.0, 1.0)),
+            kn=float(10.0 ** rng.uniform(*log10_kn)),
             u_wall=float(rng.uniform(0.01, 0.5)),
             r_in=1.0,
             r_out=float(rng.uniform(1.5, 4.0)),

@@ -106,3 +106,25 @@ def test_run_to_steady_reaches_threshold():
     n, u0, u1, T = c.read_moments()
     assert np.all(np.isfinite(n)) and np.abs(u0).max() < 1e-3  # u^R vanishes at steady state (Sec. VI.B)
     c.close()
+
+
+@pytest.mark.parametrize("prec,tol", [(vlb.VLB_FP32_BULK, 1e-5), (vlb.VLB_FP64, 1e-12)])
+def test_mass_is_conserved_with_flow(prec, tol):
+    # diffuse walls with the n_w balance of Eq. (nw) let no mass through, and the
+    # flux form moves it only between cells: total mass stays put in either
+    # precision (the RK3 weights on F must sum to exactly one in FP32 too)
+    insts = [dict(n_cells=64, kn=6.6, u_wall=0.48, r_in=1.0, r_out=3.6),
+             dict(n_cells=48, kn=0.1, u_wall=0.3, r_in=1.0, r_out=2.0),
+             dict(n_cells=32, kn=1.0, u_wall=0.1, r_in=1.0, r_out=1.5)]
+    c = make_batch(insts, prec=prec)
+    # 656: spectral radius of this model's force operator at R = 1 (RK3 needs |lambda dt| < sqrt(3))
+    c.set_dt([min(stable_dt(i), 1.2 / 656.0) for i in insts])
+    c.init_equilibrium()
+    c.step_graph(0.0, 12000)
+    n = c.read_moments()[0]
+    o = np.concatenate([[0], np.cumsum([i["n_cells"] for i in insts])])
+    for k, i in enumerate(insts):
+        f = np.linspace(i["r_in"], i["r_out"], i["n_cells"] + 1)
+        V = f[1:] ** 2 - f[:-1] ** 2
+        assert abs((n[o[k]:o[k + 1]] * V).sum() / V.sum() - 1) < tol, (k, prec)
+    c.close()
