@@ -44,9 +44,8 @@ struct StageSmem {
   static constexpr int NW = NT / 32;
   __host__ __device__ static size_t tile_off() { return 16; }
   __host__ __device__ static size_t lbuf_off(int Vp) { return tile_off() + size_t(TC + 6) * 2 * Vp * sizeof(real); }
-  __host__ __device__ static size_t fl_off(int Vp) { return lbuf_off(Vp) + size_t(TC) * 2 * Vp * sizeof(real); }
   __host__ __device__ static size_t dbl_off(int Vp) {
-    size_t o = fl_off(Vp) + size_t(TC) * 2 * Vp * sizeof(real);
+    size_t o = lbuf_off(Vp) + size_t(TC) * 2 * Vp * sizeof(real);
     return (o + 15) & ~size_t(15);
   }
   // doubles: p0, p1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each, wall equilibria), reduction (NW*4),
@@ -78,7 +77,6 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   real* tile = reinterpret_cast<real*>(smem + L::tile_off());
   real* lbuf = reinterpret_cast<real*>(smem + L::lbuf_off(Vp));
-  real* flb = reinterpret_cast<real*>(smem + L::fl_off(Vp));  // F_l of the owned cells (stages 2, 3)
   double* p0d = reinterpret_cast<double*>(smem + L::dbl_off(Vp));
   double* p1d = p0d + MAXQ;
   double* tab0 = p1d + MAXQ;
@@ -154,13 +152,10 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   // ---- stage the tile (cells lo..hi-1 at slots lo-c0+3 ...) and F_l with bulk copies
   if (warp == 0) {
     const unsigned rbytes = unsigned(row * sizeof(real));
-    if (lane == 0) mbar_expect_tx(bar, rbytes * unsigned(hi - lo + (need_fl ? TCe : 0)));
+    if (lane == 0) mbar_expect_tx(bar, rbytes * unsigned(hi - lo));
     __syncwarp();
     for (int c = lo + lane; c < hi; c += 32)
       bulk_g2s(tile + (c - c0 + 3) * row, a.Fprev + size_t(in.cell0 + c) * row, rbytes, bar);
-    if (need_fl)
-      for (int t = lane; t < TCe; t += 32)
-        bulk_g2s(flb + t * row, a.Fl + size_t(in.cell0 + c0 + t) * row, rbytes, bar);
   }
   for (int t = tid; t < TCe; t += NT) {
     if constexpr (F32) {
@@ -402,7 +397,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     const bool up = pr >= real(0);
     const real sc = iw0[i] * iw1[j];
     real* S = tile + d * Vp + v;
-    const real* Fl = flb + d * Vp + v;
+    const real* Fl = a.Fl + size_t(in.cell0 + c0) * row + d * Vp + v;  // F_l of the owned cells, read once
     real w0 = S[0], w1 = S[row], w2 = S[2 * row], w3 = S[3 * row], w4 = S[4 * row], w5 = S[5 * row];
     // upwind stencil: (w0..w4) for p^R >= 0, mirrored (w5..w1) otherwise
     real fm = weno5<real>(up ? w0 : w5, up ? w1 : w4, up ? w2 : w3, up ? w3 : w2, up ? w4 : w1, sc);
