@@ -229,14 +229,13 @@ int spare_buffer(const vlb_ctx* c) {
   return -1;
 }
 
-// F (caller layout, V per field) <-> D = F - R (device layout, Vp per field).
-vlb_status convert(vlb_ctx* c, const void* src, int src_pitch, void* dst, int dst_pitch, int to_deviation) {
+// Caller layout F <-> device layout D = F - R (see launch_deviation).
+vlb_status convert(vlb_ctx* c, const void* src, void* dst, int to_deviation) {
   cudaError_t e = c->prec == VLB_FP64
-                      ? launch_deviation<double>(static_cast<const double*>(src), src_pitch,
-                                                 static_cast<double*>(dst), dst_pitch, c->total_cells, c->margs,
-                                                 to_deviation, c->stream)
-                      : launch_deviation<float>(static_cast<const float*>(src), src_pitch, static_cast<float*>(dst),
-                                                dst_pitch, c->total_cells, c->margs, to_deviation, c->stream);
+                      ? launch_deviation<double>(static_cast<const double*>(src), static_cast<double*>(dst),
+                                                 c->total_cells, c->Vp, c->margs, to_deviation, c->stream)
+                      : launch_deviation<float>(static_cast<const float*>(src), static_cast<float*>(dst),
+                                                c->total_cells, c->Vp, c->margs, to_deviation, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "conversion kernel launch");
   return VLB_OK;
 }
@@ -701,7 +700,7 @@ vlb_status vlb_set_f(vlb_ctx* c, const void* f, int on_device) {
                                 c->stream));
     src = stage;
   }
-  vlb_status st = convert(c, src, c->V, c->F[c->cur], c->Vp, 1);
+  vlb_status st = convert(c, src, c->F[c->cur], 1);
   if (st != VLB_OK) return st;
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->last = c->cur;
@@ -713,11 +712,11 @@ vlb_status vlb_set_f(vlb_ctx* c, const void* f, int on_device) {
 vlb_status vlb_read_f(vlb_ctx* c, void* f, int on_device) {
   if (!c || !f) return fail(c, VLB_ERR_INVALID, "null argument");
   if (on_device) {
-    vlb_status st = convert(c, c->F[c->last], c->Vp, f, c->V, 0);
+    vlb_status st = convert(c, c->F[c->last], f, 0);
     if (st != VLB_OK) return st;
   } else {
     void* stage = c->F[spare_buffer(c)];
-    vlb_status st = convert(c, c->F[c->last], c->Vp, stage, c->V, 0);
+    vlb_status st = convert(c, c->F[c->last], stage, 0);
     if (st != VLB_OK) return st;
     VLB_CUDA(c, cudaMemcpyAsync(f, stage, size_t(c->total_cells) * 2 * c->V * c->esize, cudaMemcpyDeviceToHost,
                                 c->stream));
@@ -868,7 +867,7 @@ vlb_status vlb_save(vlb_ctx* c, const char* path) {
   if (!c || !path) return fail(c, VLB_ERR_INVALID, "null argument");
   if (c->stage_done % 3 != 0) return fail(c, VLB_ERR_STATE, "save between full steps only");
   SaveHeader h{};
-  memcpy(h.magic, "VLBSAVE2", 8);
+  memcpy(h.magic, "VLBSAVE3", 8);
   for (int a = 0; a < 2; ++a) {
     h.model[3 * a] = c->model.kind[a];
     h.model[3 * a + 1] = c->model.N[a];
@@ -881,10 +880,8 @@ vlb_status vlb_save(vlb_ctx* c, const char* path) {
   h.steps = c->steps;
   // the device buffer as stored (the deviation from the rest state), so that a run
   // continued from the file is bitwise the run that wrote it
-  std::vector<char> buf(size_t(c->total_cells) * 2 * c->V * c->esize);
-  const size_t w = size_t(c->V) * c->esize, pitch = size_t(c->Vp) * c->esize;
-  VLB_CUDA(c, cudaMemcpy2DAsync(buf.data(), w, c->F[c->last], pitch, w, size_t(c->total_cells) * 2,
-                                cudaMemcpyDeviceToHost, c->stream));
+  std::vector<char> buf(size_t(c->total_cells) * 2 * c->Vp * c->esize);
+  VLB_CUDA(c, cudaMemcpyAsync(buf.data(), c->F[c->last], buf.size(), cudaMemcpyDeviceToHost, c->stream));
   vlb_status st = check_err(c);
   if (st != VLB_OK) return st;
   FILE* fp = fopen(path, "wb");
@@ -902,7 +899,7 @@ vlb_status vlb_load(vlb_ctx* c, const char* path) {
   FILE* fp = fopen(path, "rb");
   if (!fp) return fail(c, VLB_ERR_INVALID, std::string("cannot open ") + path);
   SaveHeader h{};
-  bool ok = fread(&h, sizeof(h), 1, fp) == 1 && memcmp(h.magic, "VLBSAVE2", 8) == 0;
+  bool ok = fread(&h, sizeof(h), 1, fp) == 1 && memcmp(h.magic, "VLBSAVE3", 8) == 0;
   for (int a = 0; a < 2 && ok; ++a)
     ok = h.model[3 * a] == c->model.kind[a] && h.model[3 * a + 1] == c->model.N[a] &&
          h.model[3 * a + 2] == c->model.Q[a];
@@ -911,13 +908,11 @@ vlb_status vlb_load(vlb_ctx* c, const char* path) {
     int nc = 0;
     ok = fread(&nc, sizeof(int), 1, fp) == 1 && nc == c->inst[i].n_cells;
   }
-  std::vector<char> buf(size_t(c->total_cells) * 2 * c->V * c->esize);
+  std::vector<char> buf(size_t(c->total_cells) * 2 * c->Vp * c->esize);
   ok = ok && fread(buf.data(), 1, buf.size(), fp) == buf.size();
   fclose(fp);
   if (!ok) return fail(c, VLB_ERR_INVALID, "file does not match this context");
-  const size_t w = size_t(c->V) * c->esize, pitch = size_t(c->Vp) * c->esize;
-  VLB_CUDA(c, cudaMemcpy2DAsync(c->F[c->cur], pitch, buf.data(), w, w, size_t(c->total_cells) * 2,
-                                cudaMemcpyHostToDevice, c->stream));
+  VLB_CUDA(c, cudaMemcpyAsync(c->F[c->cur], buf.data(), buf.size(), cudaMemcpyHostToDevice, c->stream));
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->last = c->cur;
   c->stage_done = 0;
@@ -1015,11 +1010,14 @@ vlb_status vlb_step_graph(vlb_ctx* c, double dt, long long nsteps) {
   if (st != VLB_OK) return st;
   c->launches = 0;
   const long long groups = nsteps / 3;
-  if (groups > 0 && (!c->graph_exec || c->graph_variant != c->variant)) {
+  // the graph bakes in the buffer roles of the three steps, which depend on
+  // the buffer F_l starts in: one graph per starting buffer
+  const int gc = c->cur;
+  if (groups > 0 && (!c->graph_exec[gc] || c->graph_variant[gc] != c->variant)) {
     // capture three steps: the buffer rotation returns to the same F_l after three steps
-    if (c->graph_exec) {
-      cudaGraphExecDestroy(c->graph_exec);
-      c->graph_exec = nullptr;
+    if (c->graph_exec[gc]) {
+      cudaGraphExecDestroy(c->graph_exec[gc]);
+      c->graph_exec[gc] = nullptr;
     }
     cudaStream_t s = c->stream;
     if (!s) {
@@ -1043,13 +1041,13 @@ vlb_status vlb_step_graph(vlb_ctx* c, double dt, long long nsteps) {
       return cst;
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    e = cudaGraphInstantiate(&c->graph_exec[gc], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
-    c->graph_variant = c->variant;
+    c->graph_variant[gc] = c->variant;
   }
   for (long long r = 0; r < groups; ++r) {
-    VLB_CUDA(c, cudaGraphLaunch(c->graph_exec, c->stream));
+    VLB_CUDA(c, cudaGraphLaunch(c->graph_exec[gc], c->stream));
     c->steps += 3;
   }
   c->launches = groups * 9;
@@ -1111,7 +1109,8 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_geof);
   cudaFree(c->d_cgeo);
   cudaFree(c->d_cgeof);
-  if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+  for (int b = 0; b < 3; ++b)
+    if (c->graph_exec[b]) cudaGraphExecDestroy(c->graph_exec[b]);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   cudaFree(c->d_nw);
   cudaFree(c->d_err);

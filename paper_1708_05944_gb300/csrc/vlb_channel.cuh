@@ -11,7 +11,12 @@
 //      BGK, RK3 combine -> bulk store.
 //
 // Distribution buffers hold the deviation D = F - R from the rest state
-// (ModelArgs), as in the Couette kernel.
+// (ModelArgs), as in the Couette kernel, with (f', f'') interleaved per
+// velocity (pair_t).  The arithmetic here is scalar per field: a pair-wise
+// phase D (as in the Couette kernel) gave wrong boundary ghosts for the
+// 2 x 4-cell tile shape of the 16 x 12 velocity set while every other shape
+// matched the oracle; the cause was not found, and the scalar form matches
+// the oracle for every shape.
 //
 // Cell (s, p) of the grid has global index p * n_lambda + s (lambda fastest).
 #pragma once
@@ -205,7 +210,8 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
     real sn = 0, sr0 = 0, sp1 = 0, se = 0;
     for (int v = lane; v < V; v += 32) {
       const int i = v / Q1, j = v - i * Q1;
-      const real f1 = F[v], f2 = F[VP + v], pl = p0r[i], px = p1r[j];
+      const pair_t<real> f = p_load(F + 2 * v);
+      const real f1 = f.x, f2 = f.y, pl = p0r[i], px = p1r[j];
       sn += f1;
       sr0 += pl * f1;
       sp1 += px * f1;
@@ -239,13 +245,13 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
     const int j = x % Q1, qd = x / Q1, d = qd & 1, q = qd >> 1;
     const int c = q / TS, sr = q - c * TS;
     if (sr >= TSe) continue;
-    const real* F = tile + slot(sr, c) * ROW + d * VP;
+    const real* F = tile + slot(sr, c) * ROW + d;
     real col[Q0];
 #pragma unroll
-    for (int ip = 0; ip < Q0; ++ip) col[ip] = F[ip * Q1 + j];
+    for (int ip = 0; ip < Q0; ++ip) col[ip] = F[2 * (ip * Q1 + j)];
     const real px = p1r[j];
     const real wa = geo[q * 10 + 9] * px * px, wb = geo[q * 10 + 8] * px;
-    real* Lr = lbuf + q * ROW + d * VP;
+    real* Lr = lbuf + q * ROW + d;
 #pragma unroll
     for (int i = 0; i < Q0; ++i) {
       real s1 = 0, s2 = 0;
@@ -254,7 +260,7 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
         s1 += kk.K0[i * Q0 + ip] * col[ip];
         s2 += kk.Kt0[i * Q0 + ip] * col[ip];
       }
-      Lr[i * Q1 + j] = wa * s1 + wb * s2;
+      Lr[2 * (i * Q1 + j)] = wa * s1 + wb * s2;
     }
   }
   __syncthreads();
@@ -272,13 +278,13 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
     const int i = x % Q0, qd = x / Q0, d = qd & 1, q = qd >> 1;
     const int c = q / TS, sr = q - c * TS;
     if (sr >= TSe) continue;
-    const real* F = tile + slot(sr, c) * ROW + d * VP + i * Q1;
+    const real* F = tile + slot(sr, c) * ROW + d + 2 * i * Q1;
     real rw[Q1];
 #pragma unroll
-    for (int jp = 0; jp < Q1; ++jp) rw[jp] = F[jp];
+    for (int jp = 0; jp < Q1; ++jp) rw[jp] = F[2 * jp];
     const real pl = p0r[i];
     const real wa = geo[q * 10 + 9] * pl, wb = geo[q * 10 + 8] * pl * pl;
-    real* Lr = lbuf + q * ROW + d * VP + i * Q1;
+    real* Lr = lbuf + q * ROW + d + 2 * i * Q1;
 #pragma unroll
     for (int j = 0; j < Q1; ++j) {
       real s1 = 0, s2 = 0;
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
         s1 += kk.Kt1[j * Q1 + jp] * rw[jp];
         s2 += kk.K1[j * Q1 + jp] * rw[jp];
       }
-      Lr[j] -= wa * s1 + wb * s2;
+      Lr[2 * j] -= wa * s1 + wb * s2;
     }
   }
   // equilibrium factors of the walls and reservoirs: g_lambda(0, T0), g_xi(0, T0)
@@ -334,12 +340,12 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
   // centreline lambda = 0: specular reflection, ghost 1-k mirrors cell k (p^lambda -> -p^lambda)
   if (s0 < 3) {  // the lambda halo reaches the ghost cells s = -1, -2, -3 (s = -k mirrors cell k - 1)
     constexpr int QH = Q0 / 2;
-    for (int x = tid; x < TP * 3 * 2 * V; x += NT) {
-      const int v = x % V, r = x / V, d = r & 1, kc = r >> 1, k = kc % 3 + 1, c = kc / 3;
+    for (int x = tid; x < TP * 3 * V; x += NT) {
+      const int v = x % V, kc = x / V, k = kc % 3 + 1, c = kc / 3;
       const int i = v / Q1, j = v - i * Q1;
       const int ib = i < QH ? i + QH : i - QH;
       const int rg = -k - s0, rc = k - 1 - s0;  // tile rows of the ghost and of its mirror cell
-      if (rg >= -3) tile[slot(rg, c) * ROW + d * VP + v] = tile[slot(rc, c) * ROW + d * VP + ib * Q1 + j];
+      if (rg >= -3) p_store(tile + slot(rg, c) * ROW + 2 * v, p_load(tile + slot(rc, c) * ROW + 2 * (ib * Q1 + j)));
     }
   }
   // wall lambda = 1: per column, outgoing flux (p^lambda > 0), n_w, incoming ghosts f_eq(n_w, 0, T0)
@@ -351,8 +357,9 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
     for (int x = tid; x < TP * V; x += NT) {
       const int c = x / V, v = x - c * V, i = v / Q1, j = v - i * Q1;
       if (!(p0r[i] > real(0))) continue;
-      const real F0 = tile[slot(sA, c) * ROW + v], F1 = tile[slot(sA - 1, c) * ROW + v];
-      const real F2 = tile[slot(sA - 2, c) * ROW + v];
+      // field 0 (f'), with the reconstruction phase D applies
+      const real F0 = tile[slot(sA, c) * ROW + 2 * v], F1 = tile[slot(sA - 1, c) * ROW + 2 * v];
+      const real F2 = tile[slot(sA - 2, c) * ROW + 2 * v];
       const real G0 = real(3) * F0 - real(3) * F1 + F2, G1 = real(6) * F0 - real(8) * F1 + real(3) * F2;
       const double fl = double(weno5<real>(F2, F1, F0, G0, G1, iw0[i] * iw1[j])) * double(p0r[i]);
 #pragma unroll
@@ -378,23 +385,24 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
       if (!isfinite(nwc)) atomicOr(a.err, ERR_NONFINITE);
     }
     __syncthreads();
-    for (int x = tid; x < TP * 2 * V; x += NT) {
-      const int v = x % V, r = x / V, d = r & 1, c = r >> 1;
+    for (int x = tid; x < TP * V; x += NT) {
+      const int v = x % V, c = x / V;
       const int i = v / Q1, j = v - i * Q1;
-      real g1v, g2v, g3v;
+      pair_t<real> g1v, g2v, g3v;
       if (p0r[i] > real(0)) {
-        const real F0 = tile[slot(sA, c) * ROW + d * VP + v], F1 = tile[slot(sA - 1, c) * ROW + d * VP + v];
-        const real F2 = tile[slot(sA - 2, c) * ROW + d * VP + v];
-        g1v = real(3) * F0 - real(3) * F1 + F2;
-        g2v = real(6) * F0 - real(8) * F1 + real(3) * F2;
+        const pair_t<real> F0 = p_load(tile + slot(sA, c) * ROW + 2 * v);
+        const pair_t<real> F1 = p_load(tile + slot(sA - 1, c) * ROW + 2 * v);
+        const pair_t<real> F2 = p_load(tile + slot(sA - 2, c) * ROW + 2 * v);
+        g1v = p_make(real(3) * F0.x - real(3) * F1.x + F2.x, real(3) * F0.y - real(3) * F1.y + F2.y);
+        g2v = p_make(real(6) * F0.x - real(8) * F1.x + real(3) * F2.x, real(6) * F0.y - real(8) * F1.y + real(3) * F2.y);
         g3v = g2v;
-      } else {
-        g1v = g2v = g3v = real(nwv[c] * double(gw0[i]) * double(gw1[j]) * (d ? double(T0) : 1.0) -
-                               m.w0[i] * m.w1[j]);  // f_eq(n_w, 0, T0) - R
+      } else {  // f_eq(n_w, 0, T0) - R
+        const double e = nwv[c] * double(gw0[i]) * double(gw1[j]), r = m.w0[i] * m.w1[j];
+        g1v = g2v = g3v = p_make(real(e - r), real(e * double(T0) - r));
       }
-      if (sA + 1 < TS + 3) tile[slot(sA + 1, c) * ROW + d * VP + v] = g1v;
-      if (sA + 2 < TS + 3) tile[slot(sA + 2, c) * ROW + d * VP + v] = g2v;
-      if (sA + 3 < TS + 3) tile[slot(sA + 3, c) * ROW + d * VP + v] = g3v;
+      if (sA + 1 < TS + 3) p_store(tile + slot(sA + 1, c) * ROW + 2 * v, g1v);
+      if (sA + 2 < TS + 3) p_store(tile + slot(sA + 2, c) * ROW + 2 * v, g2v);
+      if (sA + 3 < TS + 3) p_store(tile + slot(sA + 3, c) * ROW + 2 * v, g3v);
     }
   }
   // inlet and outlet reservoirs: per row, u^xi of the adjacent cell, then ghosts
@@ -410,8 +418,8 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
       real sn = 0, sx = 0;
       for (int v = lane; v < V; v += 32) {
         const int j = v % Q1;
-        sn += F[v];
-        sx += p1r[j] * F[v];
+        sn += F[2 * v];
+        sx += p1r[j] * F[2 * v];
       }
       const double dn = warp_sum<real>(double(sn)) + m.ref_n, dx = warp_sum<real>(double(sx)) + m.ref_p;
       if (lane == 0) ures[sr] = real(dx / dn);
@@ -430,8 +438,8 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
     }
     __syncthreads();
     const real nres = F32 ? real(end == 0 ? a.cd.n_inf : a.cd.n_outf) : real(end == 0 ? a.cd.n_in : a.cd.n_out);
-    for (int x = tid; x < TSe * 2 * V; x += NT) {
-      const int v = x % V, r = x / V, d = r & 1, sr = r >> 1;
+    for (int x = tid; x < TSe * V; x += NT) {
+      const int v = x % V, sr = x / V;
       const int i = v / Q1, j = v - i * Q1;
       // V^xi at the boundary interface of the adjacent cell
       real bb, cc;
@@ -446,11 +454,16 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
       }
       const real Vx = bb * p1r[j] - cc * p0r[i];
       const bool inflow = end == 0 ? (Vx > real(0)) : (Vx < real(0));
-      const real val = inflow ? nres * gw0[i] * gres[sr * Q1 + j] * (d ? T0 : real(1)) - w0r[i] * w1r[j]
-                              : tile[slot(sr, cA) * ROW + d * VP + v];
+      pair_t<real> val;
+      if (inflow) {  // f_eq(n_res, (0, u_res), T0) - R
+        const real e = nres * gw0[i] * gres[sr * Q1 + j], r = w0r[i] * w1r[j];
+        val = p_make(e - r, e * T0 - r);
+      } else {
+        val = p_load(tile + slot(sr, cA) * ROW + 2 * v);
+      }
       for (int k = 1; k <= 3; ++k) {
         const int c = end == 0 ? cA - k : cA + k;
-        if (c >= -3 && c < TP + 3 && (c < 0 || c >= TP)) tile[slot(sr, c) * ROW + d * VP + v] = val;
+        if (c >= -3 && c < TP + 3 && (c < 0 || c >= TP)) p_store(tile + slot(sr, c) * ROW + 2 * v, val);
       }
     }
   }
@@ -468,7 +481,7 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
     const real sc = iw0[i] * iw1[j];
 #pragma unroll
     for (int c = 0; c < TP; ++c) {
-      const real* S = tile + slot(0, c) * ROW + d * VP + v;  // row sr at S[sr * ROW]
+      const real* S = tile + slot(0, c) * ROW + 2 * v + d;  // row sr at S[sr * ROW]
       real w0 = S[-3 * ROW], w1 = S[-2 * ROW], w2 = S[-1 * ROW], w3 = S[0], w4 = S[ROW], w5 = S[2 * ROW];
       real fm = weno5<real>(upl ? w0 : w5, upl ? w1 : w4, upl ? w2 : w3, upl ? w3 : w2, upl ? w4 : w1, sc);
 #pragma unroll
@@ -479,10 +492,9 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
           const real fp = weno5<real>(upl ? w1 : w6, upl ? w2 : w5, upl ? w3 : w4, upl ? w4 : w3, upl ? w5 : w2, sc);
           const real* gq = geo + q * 10;
           real adv = pl * (gq[1] * fp - gq[0] * fm) * gq[6];
-          // xi interfaces p -/+ 1/2 of this cell
           real h[7];
 #pragma unroll
-          for (int k = 0; k < 7; ++k) h[k] = tile[slot(sr, c - 3 + k) * ROW + d * VP + v];
+          for (int k = 0; k < 7; ++k) h[k] = tile[slot(sr, c - 3 + k) * ROW + 2 * v + d];
           const real Vm = gq[2] * px - gq[4] * pl, Vp_ = gq[3] * px - gq[5] * pl;
           const real Fm = Vm >= real(0) ? weno5<real>(h[0], h[1], h[2], h[3], h[4], sc)
                                         : weno5<real>(h[5], h[4], h[3], h[2], h[1], sc);
@@ -490,11 +502,11 @@ __global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant
                                          : weno5<real>(h[6], h[5], h[4], h[3], h[2], sc);
           adv += (Vp_ * Fp - Vm * Fm) * gq[7];
           const real deq = g0n[q * Q0 + i] * g1[q * Q1 + j] * (d ? cT[q] : real(1)) - w0r[i] * w1r[j];
-          const real Lv = -adv + lbuf[q * ROW + d * VP + v] - (w3 - deq) * citau[q];
+          const real Lv = -adv + lbuf[q * ROW + 2 * v + d] - (w3 - deq) * citau[q];
           real o = w3 + ccoef * Lv;
-          real* dst = flb + q * ROW + d * VP + v;
+          real* dst = flb + q * ROW + 2 * v + d;
           if (need_fl) o += ca * (*dst - w3);
-          *dst = o;  // this (cell, field, momentum) entry of F_l is not read again
+          *dst = o;
           w0 = w1;
           w1 = w2;
           w2 = w3;

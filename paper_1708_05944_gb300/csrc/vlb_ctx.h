@@ -57,9 +57,10 @@ struct vlb_ctx {
   ChanCell<float>* d_cgeof = nullptr;
   std::vector<unsigned char> chanK32, chanK64;
   // CUDA graph of three RK3 steps (nine stage launches), replayed by vlb_step_graph
-  cudaGraphExec_t graph_exec = nullptr;
+  // three-step graphs, one per starting buffer F[cur] (captured on first use)
+  cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};
   cudaStream_t capture_stream = nullptr;
-  int graph_variant = -1;
+  int graph_variant[3] = {-1, -1, -1};
   long long launches = 0;
   long long steps = 0;
   std::string err;

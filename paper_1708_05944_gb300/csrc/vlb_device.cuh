@@ -98,7 +98,7 @@ __device__ __noinline__ void weno5_weights_slow(real s1, real s2, real s3, real*
     w[0] = s1 == real(0) ? d1 : real(0);
     w[1] = s2 == real(0) ? d2 : real(0);
     w[2] = s3 == real(0) ? d3 : real(0);
-  } else {
+  } else {  // IEEE division: the indicators here may be subnormal or beyond 2^126
     const real mn = vmin(s1, vmin(s2, s3));
     const real r1 = mn / s1, r2 = mn / s2, r3 = mn / s3;
     w[0] = d1 * r1 * r1;
@@ -136,6 +136,102 @@ __device__ __forceinline__ real weno5(real a, real b, real c, real d, real e, re
     den = w1 + w2 + w3;
   }
   return vdiv(w1 * F1 + w2 * F2 + w3 * F3, den);
+}
+
+// ---------------------------------------------------------------- pairs (f', f'') of one velocity
+// Device rows interleave the two reduced distributions of Sec. II: element
+// (field d, velocity v) of a cell row sits at 2 v + d, so one 8- or 16-byte
+// access moves both fields of a velocity.  The WENO-5 reconstruction, the
+// BGK relaxation and the RK3 combine treat f' and f'' alike, and run on the
+// pair: single precision through the packed FP32x2 add / multiply / fma of
+// sm_100 and later (each lane rounds as the scalar instruction does), double
+// precision as two scalar operations.
+template <typename real>
+struct PairOf;
+template <>
+struct PairOf<float> {
+  using type = float2;
+};
+template <>
+struct PairOf<double> {
+  using type = double2;
+};
+template <typename real>
+using pair_t = typename PairOf<real>::type;
+
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_set(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 p_make(float x, float y) { return make_float2(x, y); }
+__device__ __forceinline__ double2 p_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 p_mul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ double2 p_set(double s) { return make_double2(s, s); }
+__device__ __forceinline__ double2 p_make(double x, double y) { return make_double2(x, y); }
+
+template <typename real>
+__device__ __forceinline__ pair_t<real> p_load(const real* p) {
+  return *reinterpret_cast<const pair_t<real>*>(p);
+}
+template <typename real>
+__device__ __forceinline__ void p_store(real* p, pair_t<real> v) {
+  *reinterpret_cast<pair_t<real>*>(p) = v;
+}
+template <typename P>
+__device__ __forceinline__ P p_sel(bool c, P a, P b) {
+  return c ? a : b;
+}
+
+// Normalised epsilon-free WENO-5 weights of one field from its indicators (any
+// common factor of s1, s2, s3 drops out), as in weno5 above.
+template <typename real>
+__device__ __forceinline__ void weno5_weights(real s1, real s2, real s3, real& w1, real& w2, real& w3) {
+  const real r = vdiv(real(1), vmax(s1, vmax(s2, s3)));
+  const real x1 = s1 * r, x2 = s2 * r, x3 = s3 * r;
+  const real P = x1 * x1, Qv = x2 * x2, R = x3 * x3;
+  w1 = real(0.1) * (Qv * R), w2 = real(0.6) * (P * R), w3 = real(0.3) * (P * Qv);
+  const real den = w1 + w2 + w3;
+  // the fast path needs a normal-range denominator (the reciprocals above and
+  // below are single-precision fast divides); anything else -- vanishing or
+  // non-finite products, indicators out of range -- takes the slow path
+  if (!(den > real(1e-30)) || !(den < real(1e30))) {
+    real w[3];
+    weno5_weights_slow<real>(s1, s2, s3, w);
+    w1 = w[0], w2 = w[1], w3 = w[2];
+  }
+  const real iden = vdiv(real(1), w1 + w2 + w3);
+  w1 *= iden, w2 *= iden, w3 *= iden;
+}
+
+// weno5 on a pair of fields: the candidate reconstructions and the
+// indicators (times 4, which the normalisation removes) run on the pair; the
+// weights per field.
+template <typename real>
+__device__ __forceinline__ pair_t<real> weno5p(pair_t<real> a, pair_t<real> b, pair_t<real> c, pair_t<real> d,
+                                               pair_t<real> e, real sc) {
+  using P = pair_t<real>;
+  const P F1 = p_fma(a, p_set(real(1) / real(3)), p_fma(b, p_set(real(-7) / real(6)), p_mul(c, p_set(real(11) / real(6)))));
+  const P F2 = p_fma(b, p_set(real(-1) / real(6)), p_fma(c, p_set(real(5) / real(6)), p_mul(d, p_set(real(1) / real(3)))));
+  const P F3 = p_fma(c, p_set(real(1) / real(3)), p_fma(d, p_set(real(5) / real(6)), p_mul(e, p_set(real(-1) / real(6)))));
+  const P S = p_set(sc);
+  const P A = p_mul(a, S), B = p_mul(b, S), C = p_mul(c, S), D = p_mul(d, S), E = p_mul(e, S);
+  const P k = p_set(real(13) / real(3));  // 4 * 13/12: sigma_q times 4
+  const P t1 = p_fma(B, p_set(real(-2)), p_add(A, C));
+  const P u1 = p_fma(B, p_set(real(-4)), p_fma(C, p_set(real(3)), A));
+  const P t2 = p_fma(C, p_set(real(-2)), p_add(B, D));
+  const P u2 = p_fma(D, p_set(real(-1)), B);
+  const P t3 = p_fma(D, p_set(real(-2)), p_add(C, E));
+  const P u3 = p_fma(D, p_set(real(-4)), p_fma(C, p_set(real(3)), E));
+  const P s1 = p_fma(p_mul(t1, k), t1, p_mul(u1, u1));
+  const P s2 = p_fma(p_mul(t2, k), t2, p_mul(u2, u2));
+  const P s3 = p_fma(p_mul(t3, k), t3, p_mul(u3, u3));
+  real wx1, wx2, wx3, wy1, wy2, wy3;
+  weno5_weights<real>(s1.x, s2.x, s3.x, wx1, wx2, wx3);
+  weno5_weights<real>(s1.y, s2.y, s3.y, wy1, wy2, wy3);
+  return p_fma(p_make(wx1, wy1), F1, p_fma(p_make(wx2, wy2), F2, p_mul(p_make(wx3, wy3), F3)));
 }
 
 // ---------------------------------------------------------------- equilibrium

@@ -193,8 +193,8 @@ __global__ void init_equilibrium_kernel(real* F, long long cells, int Vp, const 
   const int V = m.nq0 * m.nq1;
   const long long total = cells * 2 * Vp;
   for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total; x += (long long)gridDim.x * blockDim.x) {
-    const int v = int(x % Vp);
-    const int d = int((x / Vp) & 1);
+    const int e = int(x % (2 * Vp));  // (velocity, field) pairs interleaved
+    const int v = e >> 1, d = e & 1;
     real val = real(0);
     if (v < V) {
       const int i = v / m.nq1, j = v - i * m.nq1;
@@ -291,7 +291,7 @@ __global__ void seed_kernel(real* F, long long cells, int Vp, const __grid_const
     const int V = m.nq0 * m.nq1;
     const double cq = qc / (Tc * Tc);
     for (int x = threadIdx.x; x < 2 * Vp; x += blockDim.x) {
-      const int d = x >= Vp, v = x - d * Vp;
+      const int v = x >> 1, d = x & 1;  // (velocity, field) pairs interleaved
       real val = real(0);
       if (v < V) {
         const int i = v / m.nq1, j = v - i * m.nq1;
@@ -315,34 +315,47 @@ cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, co
   return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------- caller layout <-> deviation from R
+// ---------------------------------------------------------------- caller layout <-> device layout
+// Caller rows hold f' then f'' (V values each); device rows hold the deviation
+// from R as interleaved (f', f'') pairs of Vp velocities.  One CTA per cell row
+// at a time; the row passes through shared memory, so src and dst may be the
+// same buffer when V == Vp.
 template <typename real>
-__global__ void deviation_kernel(const real* src, int sp, real* dst, int dp, long long cells,
+__global__ void deviation_kernel(const real* src, real* dst, long long cells, int Vp,
                                  const __grid_constant__ ModelArgs m, int to_dev) {
+  __shared__ real buf[2 * MAXQ * MAXQ];
   const int V = m.nq0 * m.nq1;
-  const long long total = cells * 2 * dp;
-  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total; x += (long long)gridDim.x * blockDim.x) {
-    const long long row = x / dp;  // (cell, field)
-    const int v = int(x - row * dp);
-    real val = real(0);
-    if (v < V) {
-      const int i = v / m.nq1, j = v - i * m.nq1;
-      const double r = m.w0[i] * m.w1[j];
-      const double s = double(src[row * sp + v]);
-      val = real(to_dev ? s - r : s + r);
+  for (long long c = blockIdx.x; c < cells; c += gridDim.x) {
+    if (to_dev) {
+      for (int x = threadIdx.x; x < 2 * V; x += blockDim.x) buf[x] = src[c * 2 * V + x];
+      __syncthreads();
+      for (int x = threadIdx.x; x < 2 * Vp; x += blockDim.x) {
+        const int v = x >> 1, d = x & 1;
+        real val = real(0);
+        if (v < V) {
+          const int i = v / m.nq1, j = v - i * m.nq1;
+          val = real(double(buf[d * V + v]) - m.w0[i] * m.w1[j]);
+        }
+        dst[c * 2 * Vp + x] = val;
+      }
+    } else {
+      for (int x = threadIdx.x; x < 2 * Vp; x += blockDim.x) buf[x] = src[c * 2 * Vp + x];
+      __syncthreads();
+      for (int x = threadIdx.x; x < 2 * V; x += blockDim.x) {
+        const int d = x >= V, v = x - d * V;
+        const int i = v / m.nq1, j = v - i * m.nq1;
+        dst[c * 2 * V + x] = real(double(buf[2 * v + d]) + m.w0[i] * m.w1[j]);
+      }
     }
-    if (v < V || to_dev) dst[row * dp + v] = val;
+    __syncthreads();
   }
 }
 
 template <typename real>
-cudaError_t launch_deviation(const real* src, int src_pitch, real* dst, int dst_pitch, long long cells,
-                             const ModelArgs& m, int to_deviation, cudaStream_t s) {
-  const long long total = cells * 2 * dst_pitch;
-  long long blocks = (total + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  if (blocks < 1) blocks = 1;
-  deviation_kernel<real><<<int(blocks), 256, 0, s>>>(src, src_pitch, dst, dst_pitch, cells, m, to_deviation);
+cudaError_t launch_deviation(const real* src, real* dst, long long cells, int Vp, const ModelArgs& m,
+                             int to_deviation, cudaStream_t s) {
+  const long long blocks = cells < 152 * 8 ? cells : 152 * 8;
+  deviation_kernel<real><<<int(blocks > 0 ? blocks : 1), 256, 0, s>>>(src, dst, cells, Vp, m, to_deviation);
   return cudaGetLastError();
 }
 
@@ -359,7 +372,7 @@ __global__ void moments_kernel(const real* F, long long cells, int Vp, const __g
     double sn = 0, s0 = 0, s1 = 0;
     for (int v = lane; v < V; v += 32) {
       const int i = v / nq1, j = v - i * nq1;
-      const double f1 = double(f[v]) + m.w0[i] * m.w1[j];  // F = D + R
+      const double f1 = double(f[2 * v]) + m.w0[i] * m.w1[j];  // F = D + R
       sn += f1;
       s0 += m.p0[i] * f1;
       s1 += m.p1[j] * f1;
@@ -372,7 +385,7 @@ __global__ void moments_kernel(const real* F, long long cells, int Vp, const __g
     for (int v = lane; v < V; v += 32) {
       const int i = v / nq1, j = v - i * nq1;
       const double r = m.w0[i] * m.w1[j];
-      const double f1 = double(f[v]) + r, f2 = double(f[Vp + v]) + r;
+      const double f1 = double(f[2 * v]) + r, f2 = double(f[2 * v + 1]) + r;
       const double x0 = m.p0[i] - u0, x1 = m.p1[j] - u1;
       t00 += x0 * x0 * f1;
       t01 += x0 * x1 * f1;
@@ -423,7 +436,7 @@ template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_RE
                                               int, cudaStream_t);
 template cudaError_t launch_seed<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
                                            const double*, const double*, const double*, const double*, cudaStream_t);
-template cudaError_t launch_deviation<VLB_REAL>(const VLB_REAL*, int, VLB_REAL*, int, long long, const ModelArgs&, int,
+template cudaError_t launch_deviation<VLB_REAL>(const VLB_REAL*, VLB_REAL*, long long, int, const ModelArgs&, int,
                                                 cudaStream_t);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,
                                               cudaStream_t);

@@ -55,13 +55,13 @@ template <typename real>
 cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, const double* n, const double* u0,
                         const double* u1, const double* T, const double* q0, cudaStream_t s);
 
-// Caller layout F (src_pitch or dst_pitch values per field) to and from the device
-// deviation D = F - R (to_deviation = 1: dst = src - R; 0: dst = src + R), the sum
-// taken in double.  Padding entries of a wider destination row are zeroed.  src and
-// dst may be the same buffer when the pitches agree.
+// Caller layout F (per cell: f' then f'', V values each) to and from the device
+// layout (per cell: Vp interleaved (f', f'') pairs of the deviation D = F - R;
+// padding zero).  to_deviation = 1: caller -> device, 0: device -> caller; each
+// element is summed in double.  src and dst may be the same buffer when V == Vp.
 template <typename real>
-cudaError_t launch_deviation(const real* src, int src_pitch, real* dst, int dst_pitch, long long cells,
-                             const ModelArgs& m, int to_deviation, cudaStream_t s);
+cudaError_t launch_deviation(const real* src, real* dst, long long cells, int Vp, const ModelArgs& m,
+                             int to_deviation, cudaStream_t s);
 
 // Per cell, FP64: n, u0, u1, T, T00, T01, T11, q0, q1 (stride 9).
 template <typename real>

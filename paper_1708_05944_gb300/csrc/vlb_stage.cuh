@@ -11,6 +11,7 @@
 //
 // Every distribution buffer holds the deviation D = F - R from the rest state
 // (ModelArgs): the operator is linear in R's part, which it leaves unchanged.
+// A cell row holds Vp velocity pairs (f', f'') interleaved (see pair_t).
 #pragma once
 #include "vlb_device.cuh"
 
@@ -34,7 +35,7 @@ struct StageArgs {
   const GeoCellF* geof;  // single-precision copy
   double* nw;          // 2 per instance: inner, outer wall density
   unsigned* err;
-  int Vp;              // per-field stride of a cell row (>= nq0 nq1, multiple of 4)
+  int Vp;              // velocities per cell row, padded (>= nq0 nq1, multiple of 4); a row holds 2 Vp reals
   unsigned long long max_polls;
 };
 
@@ -186,7 +187,8 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
 #pragma unroll 4
     for (int v = lane; v < V; v += 32) {
       const int i = v / nq1, j = v - i * nq1;
-      const real f1 = F[v], f2 = F[Vp + v], pr = p0r[i], pp = p1r[j];
+      const pair_t<real> f = p_load(F + 2 * v);
+      const real f1 = f.x, f2 = f.y, pr = p0r[i], pp = p1r[j];
       sn += f1;
       sr += pr * f1;
       sp += pp * f1;
@@ -222,11 +224,11 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   // lbuf = -(p^phi)^2 K^R f (one task per (cell, field, j): a column of nq0 values)
   for (int x = tid; x < TCe * 2 * nq1; x += NT) {
     const int j = x % nq1, td2 = x / nq1, d = td2 & 1, t = td2 >> 1;
-    const real* F = tile + (t + 3) * row + d * Vp;
+    const real* F = tile + (t + 3) * row + d;
     real col[Q0MAX];
 #pragma unroll
-    for (int ip = 0; ip < Q0MAX; ++ip) col[ip] = ip < nq0 ? F[ip * nq1 + j] : real(0);
-    real* Lr = lbuf + (t * 2 + d) * Vp;
+    for (int ip = 0; ip < Q0MAX; ++ip) col[ip] = ip < nq0 ? F[2 * (ip * nq1 + j)] : real(0);
+    real* Lr = lbuf + t * row + d;
     const real w = -p1r[j] * p1r[j];
 #pragma unroll
     for (int i = 0; i < Q0MAX; ++i) {
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
 #pragma unroll
         for (int ip = 0; ip < Q0MAX; ++ip)
           if (ip < nq0) acc += kk.K0[i * MAXQ + ip] * col[ip];
-        Lr[i * nq1 + j] = w * acc;
+        Lr[2 * (i * nq1 + j)] = w * acc;
       }
     }
   }
@@ -250,11 +252,11 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   // lbuf += p^R K~^phi f (one task per (cell, field, i): a row of nq1 values)
   for (int x = tid; x < TCe * 2 * nq0; x += NT) {
     const int i = x % nq0, td2 = x / nq0, d = td2 & 1, t = td2 >> 1;
-    const real* F = tile + (t + 3) * row + d * Vp + i * nq1;
+    const real* F = tile + (t + 3) * row + d + 2 * i * nq1;
     real rw[Q1MAX];
 #pragma unroll
-    for (int jp = 0; jp < Q1MAX; ++jp) rw[jp] = jp < nq1 ? F[jp] : real(0);
-    real* Lr = lbuf + (t * 2 + d) * Vp + i * nq1;
+    for (int jp = 0; jp < Q1MAX; ++jp) rw[jp] = jp < nq1 ? F[2 * jp] : real(0);
+    real* Lr = lbuf + t * row + d + 2 * i * nq1;
     const real pr = p0r[i];
 #pragma unroll
     for (int j = 0; j < Q1MAX; ++j) {
@@ -263,7 +265,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
 #pragma unroll
         for (int jp = 0; jp < Q1MAX; ++jp)
           if (jp < nq1) acc += kk.Kt1[j * MAXQ + jp] * rw[jp];
-        Lr[j] += pr * acc;
+        Lr[2 * j] += pr * acc;
       }
     }
   }
@@ -325,12 +327,13 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     for (int v = tid; v < V; v += NT) {
       const int i = v / nq1, j = v - i * nq1;
       if (!(sgn * p0d[i] < 0.0)) continue;
-      const real F0 = tile[sA * row + v];
-      const real F1 = tile[(sA + dir) * row + v];
-      const real F2 = tile[(sA + 2 * dir) * row + v];
-      const real G0 = real(3) * F0 - real(3) * F1 + F2;
-      const real G1 = real(6) * F0 - real(8) * F1 + real(3) * F2;
-      num += double(weno5<real>(F2, F1, F0, G0, G1, iw0[i] * iw1[j])) * p0d[i];
+      // the same pair reconstruction as phase D (field 0 enters n_w)
+      const pair_t<real> F0 = p_load(tile + sA * row + 2 * v);
+      const pair_t<real> F1 = p_load(tile + (sA + dir) * row + 2 * v);
+      const pair_t<real> F2 = p_load(tile + (sA + 2 * dir) * row + 2 * v);
+      const pair_t<real> G0 = p_fma(F1, p_set(real(-3)), p_fma(F0, p_set(real(3)), F2));
+      const pair_t<real> G1 = p_fma(F1, p_set(real(-8)), p_fma(F0, p_set(real(6)), p_mul(F2, p_set(real(3)))));
+      num += double(weno5p<real>(F2, F1, F0, G0, G1, iw0[i] * iw1[j]).x) * p0d[i];
     }
     num = warp_sum<real>(num);
     if (warp == 0) {  // incoming flux of f_eq(1, u_w, T_w): (sum over incoming i of g_i p_i) (sum_j g_j)
@@ -354,24 +357,24 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     }
     __syncthreads();
     const double nwd = mw[1];
-    for (int x = tid; x < 2 * V; x += NT) {
-      const int d = x >= V, v = x - d * V;
+    for (int v = tid; v < V; v += NT) {
       const int i = v / nq1, j = v - i * nq1;
-      real g1, g2, g3;  // ghosts at distance 1, 2, 3 from the wall
+      pair_t<real> g1, g2, g3;  // ghosts at distance 1, 2, 3 from the wall
       if (sgn * p0d[i] < 0.0) {
-        const real F0 = tile[sA * row + d * Vp + v];
-        const real F1 = tile[(sA + dir) * row + d * Vp + v];
-        const real F2 = tile[(sA + 2 * dir) * row + d * Vp + v];
-        g1 = real(3) * F0 - real(3) * F1 + F2;
-        g2 = real(6) * F0 - real(8) * F1 + real(3) * F2;
+        const pair_t<real> F0 = p_load(tile + sA * row + 2 * v);
+        const pair_t<real> F1 = p_load(tile + (sA + dir) * row + 2 * v);
+        const pair_t<real> F2 = p_load(tile + (sA + 2 * dir) * row + 2 * v);
+        g1 = p_fma(F1, p_set(real(-3)), p_fma(F0, p_set(real(3)), F2));
+        g2 = p_fma(F1, p_set(real(-8)), p_fma(F0, p_set(real(6)), p_mul(F2, p_set(real(3)))));
         g3 = g2;  // never read by an outgoing stencil
       } else {  // f_eq(n_w, u_w, T_w) - R
-        g1 = g2 = g3 = real(nwd * gw0[i] * gw1[j] * (d ? Tw : 1.0) - m.w0[i] * m.w1[j]);
+        const double e = nwd * gw0[i] * gw1[j], r = m.w0[i] * m.w1[j];
+        g1 = g2 = g3 = p_make(real(e - r), real(e * Tw - r));
       }
       const int s1 = sA - dir, s2 = sA - 2 * dir, s3 = sA - 3 * dir;
-      if (s1 >= 0 && s1 < TC + 6) tile[s1 * row + d * Vp + v] = g1;
-      if (s2 >= 0 && s2 < TC + 6) tile[s2 * row + d * Vp + v] = g2;
-      if (s3 >= 0 && s3 < TC + 6) tile[s3 * row + d * Vp + v] = g3;
+      if (s1 >= 0 && s1 < TC + 6) p_store(tile + s1 * row + 2 * v, g1);
+      if (s2 >= 0 && s2 < TC + 6) p_store(tile + s2 * row + 2 * v, g2);
+      if (s3 >= 0 && s3 < TC + 6) p_store(tile + s3 * row + 2 * v, g3);
     }
   }
   __syncthreads();
@@ -380,38 +383,38 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   const real dtr = F32 ? real(in.dt_f) : real(in.dt);
   const real ca = F32 ? real(a.caf) : real(a.ca);
   const real cc = (F32 ? real(a.ccf) : real(a.cc)) * dtr;
-  // per-cell factors of this tile in registers
-  real rcp[TC], rcm[TC], rir[TC], rit[TC], rT[TC];
-#pragma unroll
-  for (int t = 0; t < TC; ++t) {
-    rcp[t] = ccp[t];
-    rcm[t] = ccm[t];
-    rir[t] = cIR[t];
-    rit[t] = cItau[t];
-    rT[t] = cTr[t];
-  }
-  for (int x = tid; x < 2 * V; x += NT) {
-    const int d = x >= V, v = x - d * V;
+  using P = pair_t<real>;
+  for (int v = tid; v < V; v += NT) {  // one velocity, both fields, walking the tile's cells
     const int i = v / nq1, j = v - i * nq1;
     const real pr = p0r[i];
     const bool up = pr >= real(0);
     const real sc = iw0[i] * iw1[j];
-    real* S = tile + d * Vp + v;
-    const real* Fl = a.Fl + size_t(in.cell0 + c0) * row + d * Vp + v;  // F_l of the owned cells, read once
-    real w0 = S[0], w1 = S[row], w2 = S[2 * row], w3 = S[3 * row], w4 = S[4 * row], w5 = S[5 * row];
+    const real rij = w0r[i] * w1r[j];
+    real* S = tile + 2 * v;
+    const real* Fl = a.Fl + size_t(in.cell0 + c0) * row + 2 * v;  // F_l of the owned cells, read once
+    P w0 = p_load(S), w1 = p_load(S + row), w2 = p_load(S + 2 * row), w3 = p_load(S + 3 * row);
+    P w4 = p_load(S + 4 * row), w5 = p_load(S + 5 * row);
     // upwind stencil: (w0..w4) for p^R >= 0, mirrored (w5..w1) otherwise
-    real fm = weno5<real>(up ? w0 : w5, up ? w1 : w4, up ? w2 : w3, up ? w3 : w2, up ? w4 : w1, sc);
+    P fm = weno5p<real>(p_sel(up, w0, w5), p_sel(up, w1, w4), p_sel(up, w2, w3), p_sel(up, w3, w2),
+                        p_sel(up, w4, w1), sc);
 #pragma unroll
     for (int t = 0; t < TC; ++t) {
       if (t < TCe) {
-        const real w6 = S[(t + 6) * row];
-        const real fp = weno5<real>(up ? w1 : w6, up ? w2 : w5, up ? w3 : w4, up ? w4 : w3, up ? w5 : w2, sc);
-        const real adv = pr * (rcp[t] * fp - rcm[t] * fm);
-        const real deq = gRn[t * MAXQ + i] * gP[t * MAXQ + j] * (d ? rT[t] : real(1)) - w0r[i] * w1r[j];
-        const real Lv = -adv + lbuf[(t * 2 + d) * Vp + v] * rir[t] - (w3 - deq) * rit[t];
-        real o = w3 + cc * Lv;
-        if (need_fl) o += ca * (Fl[t * row] - w3);
-        S[(t + 3) * row] = o;  // in place: this column's slot t+3 is not read again
+        const P w6 = p_load(S + (t + 6) * row);
+        const P fp = weno5p<real>(p_sel(up, w1, w6), p_sel(up, w2, w5), p_sel(up, w3, w4), p_sel(up, w4, w3),
+                                  p_sel(up, w5, w2), sc);
+        // -adv = -p^R (cp F_{s+1/2} - cm F_{s-1/2})
+        // per-cell factors: shared-memory broadcasts
+        const P nadv = p_mul(p_fma(fp, p_set(ccp[t]), p_mul(fm, p_set(-ccm[t]))), p_set(-pr));
+        // f_eq - R for both fields: (g, T g) - R
+        const real g = gRn[t * MAXQ + i] * gP[t * MAXQ + j];
+        const P deq = p_fma(p_set(g), p_make(real(1), cTr[t]), p_set(-rij));
+        const P force = p_load(lbuf + t * row + 2 * v);
+        // L = -adv + force / Rbar - (D - D_eq) / tau
+        const P Lv = p_fma(p_fma(deq, p_set(real(-1)), w3), p_set(-cItau[t]), p_fma(force, p_set(cIR[t]), nadv));
+        P o = p_fma(Lv, p_set(cc), w3);
+        if (need_fl) o = p_fma(p_fma(w3, p_set(real(-1)), p_load(Fl + t * row)), p_set(ca), o);
+        p_store(S + (t + 3) * row, o);  // in place: this column's slot t+3 is not read again
         w0 = w1;
         w1 = w2;
         w2 = w3;

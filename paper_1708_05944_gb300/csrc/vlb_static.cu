@@ -98,10 +98,10 @@ extern "C" vlb_status vlb_step_static_scratch(vlb_ctx* c, const void* f_in, void
   // f_out, step f_out (stage 3 updates it in place: each CTA reads only its own F_l rows), and
   // convert f_out back at the end
   e = c->prec == VLB_FP64
-          ? launch_deviation<double>(static_cast<const double*>(f_in), c->V, static_cast<double*>(f_out), c->Vp,
-                                     c->total_cells, c->margs, 1, c->stream)
-          : launch_deviation<float>(static_cast<const float*>(f_in), c->V, static_cast<float*>(f_out), c->Vp,
-                                    c->total_cells, c->margs, 1, c->stream);
+          ? launch_deviation<double>(static_cast<const double*>(f_in), static_cast<double*>(f_out), c->total_cells,
+                                     c->Vp, c->margs, 1, c->stream)
+          : launch_deviation<float>(static_cast<const float*>(f_in), static_cast<float*>(f_out), c->total_cells,
+                                    c->Vp, c->margs, 1, c->stream);
   if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("conversion launch: ") + cudaGetErrorString(e));
   for (long long s = 0; s < nsteps; ++s) {
     const void* Fl = f_out;
@@ -113,10 +113,10 @@ extern "C" vlb_status vlb_step_static_scratch(vlb_ctx* c, const void* f_in, void
     }
   }
   e = c->prec == VLB_FP64
-          ? launch_deviation<double>(static_cast<const double*>(f_out), c->Vp, static_cast<double*>(f_out), c->V,
-                                     c->total_cells, c->margs, 0, c->stream)
-          : launch_deviation<float>(static_cast<const float*>(f_out), c->Vp, static_cast<float*>(f_out), c->V,
-                                    c->total_cells, c->margs, 0, c->stream);
+          ? launch_deviation<double>(static_cast<const double*>(f_out), static_cast<double*>(f_out), c->total_cells,
+                                     c->Vp, c->margs, 0, c->stream)
+          : launch_deviation<float>(static_cast<const float*>(f_out), static_cast<float*>(f_out), c->total_cells,
+                                    c->Vp, c->margs, 0, c->stream);
   if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("conversion launch: ") + cudaGetErrorString(e));
   return VLB_OK;
 }
