@@ -85,12 +85,32 @@ void couette_geometry(const vlb_couette_grid& g, GeoCell* out) {
   }
 }
 
-// tiles of the current variant's size over every instance
+// Tiles over every instance for the current launch shape.  One-CTA-per-tile
+// launches take tiles of the shape's full size TC.  A persistent launch walks
+// the tile list in rounds of `slots` CTAs, so the tile size s <= TC is chosen to
+// minimise rounds x (s + 3): the makespan in cell-times with the three halo
+// cells as the fixed cost of a tile (for 5 x 1024 cells on 456 CTAs: 6-cell
+// tiles in two rounds instead of 8-cell tiles in two).
 void build_tiles(vlb_ctx* c) {
-  const int TC = c->variants[c->variant].tc;
+  const StageVariant& v = c->variants[c->variant];
+  int s = v.tc;
+  if (v.persist) {
+    const int slots = c->prec == VLB_FP64 ? stage_slots<double>(v, c->margs, c->Vp)
+                                          : stage_slots<float>(v, c->margs, c->Vp);
+    if (slots > 0) {
+      long long best = -1;
+      for (int cand = v.tc; cand >= std::max(3, (v.tc + 1) / 2); --cand) {
+        long long count = 0;
+        for (int i = 0; i < c->n_inst; ++i) count += (c->inst[i].n_cells + cand - 1) / cand;
+        const long long cost = ((count + slots - 1) / slots) * (cand + 3);
+        if (best < 0 || cost < best) best = cost, s = cand;
+      }
+    }
+  }
   c->tiles.clear();
   for (int i = 0; i < c->n_inst; ++i)
-    for (int c0 = 0; c0 < c->inst[i].n_cells; c0 += TC) c->tiles.push_back(TileDesc{i, c0});
+    for (int c0 = 0; c0 < c->inst[i].n_cells; c0 += s)
+      c->tiles.push_back(TileDesc{i, c0, std::min(s, c->inst[i].n_cells - c0)});
 }
 
 template <typename real>
@@ -442,17 +462,9 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     VLB_CUDA(cp, cudaMemsetAsync(c->F[b], 0, fbytes, c->stream));
   }
   VLB_CUDA(cp, cudaMalloc(&c->d_inst, sizeof(InstDesc) * n_inst));
-  // room for the tile list of the smallest tile size among the variants
-  {
-    size_t most = 0;
-    for (int v = 0; v < c->n_variants; ++v) {
-      size_t cnt = 0;
-      for (int i = 0; i < n_inst; ++i) cnt += (grids[i].n_cells + c->variants[v].tc - 1) / c->variants[v].tc;
-      most = cnt > most ? cnt : most;
-    }
-    c->tile_cap = most;
-    VLB_CUDA(cp, cudaMalloc(&c->d_tiles, sizeof(TileDesc) * most));
-  }
+  // room for the tile list of any tile size (at most one tile per cell)
+  c->tile_cap = size_t(c->total_cells);
+  VLB_CUDA(cp, cudaMalloc(&c->d_tiles, sizeof(TileDesc) * c->tile_cap));
   VLB_CUDA(cp, cudaMalloc(&c->d_geo, sizeof(GeoCell) * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_geof, sizeof(GeoCellF) * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_nw, sizeof(double) * 2 * n_inst));

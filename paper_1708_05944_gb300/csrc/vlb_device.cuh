@@ -24,6 +24,7 @@ struct InstDesc {
 struct TileDesc {
   int inst;
   int c0;  // first cell (within the instance) owned by the tile
+  int nc;  // cells owned (1 .. the kernel's TC)
 };
 
 // Per-cell chi-formulation factors (Eqs. flux_kom_R, flux_kom_eta):
@@ -185,15 +186,23 @@ __device__ __forceinline__ P p_sel(bool c, P a, P b) {
   return c ? a : b;
 }
 
+// Rounded multiply and add that the compiler may not fuse: the weights below are
+// inlined at every cell position of an unrolled loop, and a cell must get the
+// same bits whichever position (tile shape) it falls at.
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+
 // Normalised epsilon-free WENO-5 weights of one field from its indicators (any
 // common factor of s1, s2, s3 drops out), as in weno5 above.
 template <typename real>
 __device__ __forceinline__ void weno5_weights(real s1, real s2, real s3, real& w1, real& w2, real& w3) {
   const real r = vdiv(real(1), vmax(s1, vmax(s2, s3)));
-  const real x1 = s1 * r, x2 = s2 * r, x3 = s3 * r;
-  const real P = x1 * x1, Qv = x2 * x2, R = x3 * x3;
-  w1 = real(0.1) * (Qv * R), w2 = real(0.6) * (P * R), w3 = real(0.3) * (P * Qv);
-  const real den = w1 + w2 + w3;
+  const real x1 = rmul(s1, r), x2 = rmul(s2, r), x3 = rmul(s3, r);
+  const real P = rmul(x1, x1), Qv = rmul(x2, x2), R = rmul(x3, x3);
+  w1 = rmul(real(0.1), rmul(Qv, R)), w2 = rmul(real(0.6), rmul(P, R)), w3 = rmul(real(0.3), rmul(P, Qv));
+  const real den = radd(radd(w1, w2), w3);
   // the fast path needs a normal-range denominator (the reciprocals above and
   // below are single-precision fast divides); anything else -- vanishing or
   // non-finite products, indicators out of range -- takes the slow path
@@ -202,8 +211,8 @@ __device__ __forceinline__ void weno5_weights(real s1, real s2, real s3, real& w
     weno5_weights_slow<real>(s1, s2, s3, w);
     w1 = w[0], w2 = w[1], w3 = w[2];
   }
-  const real iden = vdiv(real(1), w1 + w2 + w3);
-  w1 *= iden, w2 *= iden, w3 *= iden;
+  const real iden = vdiv(real(1), radd(radd(w1, w2), w3));
+  w1 = rmul(w1, iden), w2 = rmul(w2, iden), w3 = rmul(w3, iden);
 }
 
 // weno5 on a pair of fields: the candidate reconstructions and the

@@ -118,6 +118,46 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
   return cudaErrorInvalidValue;
 }
 
+// CTAs of one launch shape that are resident on the device at once (occupancy x SMs)
+template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
+static int slots_of(int Vp) {
+  auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
+  const size_t smem = StageSmem<real, TC, NT>::bytes(Vp);
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) return 0;
+  return per_sm * sms;
+}
+
+template <typename real>
+int stage_slots(StageVariant v, const ModelArgs& m, int Vp) {
+  const int sh = shape_of(m.nq0, m.nq1);
+#define VLB_CASE(SH, TC_, NT_, q0, q1, ex) \
+  if (sh == SH && v.tc == TC_ && v.nt == NT_) return slots_of<real, TC_, NT_, q0, q1, ex>(Vp);
+  if constexpr (sizeof(real) == 4) {
+    VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
+    VLB_CASE(SH_16x20, 4, 320, 16, 20, true) VLB_CASE(SH_16x20, 8, 320, 16, 20, true)
+    VLB_CASE(SH_16x20, 16, 320, 16, 20, true)
+    VLB_CASE(SH_16x12, 16, 256, 16, 12, true) VLB_CASE(SH_16x12, 8, 256, 16, 12, true)
+    VLB_CASE(SH_16x12, 16, 384, 16, 12, true)
+    VLB_CASE(SH_8x4, 16, 64, 8, 4, true) VLB_CASE(SH_8x4, 8, 64, 8, 4, true)
+    VLB_CASE(SH_SMALL, 16, 64, MAXQ, MAXQ, false)
+    VLB_CASE(SH_GENERIC, 16, 256, MAXQ, MAXQ, false)
+  } else {
+    VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
+    VLB_CASE(SH_16x20, 4, 128, 16, 20, true) VLB_CASE(SH_16x20, 8, 128, 16, 20, true)
+    VLB_CASE(SH_16x12, 8, 256, 16, 12, true) VLB_CASE(SH_16x12, 4, 256, 16, 12, true)
+    VLB_CASE(SH_16x12, 8, 384, 16, 12, true)
+    VLB_CASE(SH_8x4, 8, 64, 8, 4, true) VLB_CASE(SH_8x4, 16, 64, 8, 4, true)
+    VLB_CASE(SH_SMALL, 8, 64, MAXQ, MAXQ, false)
+    VLB_CASE(SH_GENERIC, 8, 256, MAXQ, MAXQ, false)
+  }
+#undef VLB_CASE
+  return 0;
+}
+
 // ---------------------------------------------------------------- channel dispatch
 template <typename real, int TS, int TP, int Q0, int Q1, int NT>
 static cudaError_t go_channel(const ChanArgs<real>& a, const ModelArgs& m, const void* kbytes, cudaStream_t s) {
@@ -436,6 +476,7 @@ template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_RE
                                               int, cudaStream_t);
 template cudaError_t launch_seed<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
                                            const double*, const double*, const double*, const double*, cudaStream_t);
+template int stage_slots<VLB_REAL>(StageVariant, const ModelArgs&, int);
 template cudaError_t launch_deviation<VLB_REAL>(const VLB_REAL*, VLB_REAL*, long long, int, const ModelArgs&, int,
                                                 cudaStream_t);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,

@@ -24,6 +24,10 @@ template <typename real>
 size_t stage_smem_bytes(StageVariant v, int Vp);
 
 // Launch one RK3 stage over a.n_tiles tiles of v.tc cells.
+// CTAs of a launch shape resident on the device at once (0 if unknown).
+template <typename real>
+int stage_slots(StageVariant v, const ModelArgs& m, int Vp);
+
 template <typename real>
 cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k,
                          cudaStream_t s);

@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   const TileDesc td = a.tiles[tix];
   const InstDesc in = a.inst[td.inst];
   const int n = in.n_cells, c0 = td.c0;
-  const int TCe = min(TC, n - c0);
-  const int lo = max(c0 - 3, 0), hi = min(c0 + TC + 3, n);
+  const int TCe = td.nc;  // the host sizes tiles (1 <= nc <= TC) to fill the launch in whole rounds
+  const int lo = max(c0 - 3, 0), hi = min(c0 + TCe + 3, n);
 
   // ---- stage the tile (cells lo..hi-1 at slots lo-c0+3 ...) and F_l with bulk copies
   if (warp == 0) {
@@ -180,7 +180,9 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   }
   parity ^= 1u;
 
-  // ==== phase A: moment sums per cell (one warp per cell) and the K^R part of the force
+  // ==== phase A: per cell, one warp with no CTA barrier: moments (Eq. macro_red), tau, the
+  // equilibrium moment vectors and factors (Sec. IV.D) and their mass normalisation; the
+  // remaining threads start on the K^R part of the force
   for (int t = warp; t < TCe; t += NW) {
     const real* F = tile + (t + 3) * row;
     real sn = 0, sr = 0, sp = 0, se = 0;  // per-lane partial sums over a tenth of the velocities
@@ -205,21 +207,42 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     kq += __shfl_xor_sync(0xffffffffu, kq, 4);
     kq += __shfl_xor_sync(0xffffffffu, kq, 2);
     kq += __shfl_xor_sync(0xffffffffu, kq, 1);
-    // lanes 0, 8, 16, 24 hold n, rho u^0, rho u^1, energy sum
+    // lanes 0, 8, 16, 24 hold the sums of n, rho u^0, rho u^1 and the energy: to every lane
+    const double dn = __shfl_sync(0xffffffffu, kq, 0);
     const double dr = __shfl_sync(0xffffffffu, kq, 8);
     const double dpp = __shfl_sync(0xffffffffu, kq, 16);
     const double de = __shfl_sync(0xffffffffu, kq, 24);
-    if (lane == 0) {  // sums of D (FP64) plus those of R; the derived fields are formed in the bulk type
-      const real nn = real(kq + m.ref_n), u0 = real(dr + m.ref_r) / nn, u1 = real(dpp + m.ref_p) / nn;
-      const real T = (real(de + m.ref_e) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
-      cn[t] = nn;
-      // target of sum_i gRn_i sum_j gP_j: the f_eq - R of phase D must sum to sum D
-      cnd[t] = kq + (F32 ? m.ref_sum_f : m.ref_n);
-      cu0[t] = u0;
-      cu1[t] = u1;
+    // sums of D (FP64) plus those of R; the derived fields are formed in the bulk type
+    const real nn = real(dn + m.ref_n), u0 = real(dr + m.ref_r) / nn, u1 = real(dpp + m.ref_p) / nn;
+    const real T = (real(de + m.ref_e) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
+    if (lane == 0) {
       cTr[t] = T;
       cItau[t] = real(1) / relaxation_time<real>(in.tau_mode, F32 ? real(in.kn_f) : real(in.kn), nn, T);
     }
+    real* mt = mv + t * 4 * MAXN;  // moment vectors [axis * 2 + side][s]
+    if (lane < 4) {
+      const int ax = lane >> 1, side = lane & 1;
+      const real u = (ax ? u1 : u0) * (side ? real(-1) : real(1));
+      eq_moment_vector<real>(ax ? m.kind1 : m.kind0, ax ? m.N1 : m.N0, u, T, mt + lane * MAXN);
+    }
+    __syncwarp();
+    // equilibrium factors: lane k takes g_R[k] and g_phi[k]
+    real gr = 0, gp = 0;
+    if (lane < nq0) {
+      const real* mm = mt + ((m.kind0 == 1 && p0r[lane] < real(0)) ? 1 : 0) * MAXN;
+      for (int s = 0; s <= m.N0; ++s) gr += tabr0[lane * MAXN + s] * mm[s];
+      gr *= nn;
+    }
+    if (lane < nq1) {
+      const real* mm = mt + (2 + ((m.kind1 == 1 && p1r[lane] < real(0)) ? 1 : 0)) * MAXN;
+      for (int s = 0; s <= m.N1; ++s) gp += tabr1[lane * MAXN + s] * mm[s];
+    }
+    // rescale g_R so that sum_i g_R sum_j g_phi is exactly the target sum D + sum R (f_eq - R
+    // of phase D then carries the cell's mass; see normalise_equilibrium)
+    const double a0 = warp_sum<real>(double(gr)), a1 = warp_sum<real>(double(gp));
+    const real scale = real((dn + (F32 ? m.ref_sum_f : m.ref_n)) / (a0 * a1));
+    if (lane < nq0) gRn[t * MAXQ + lane] = gr * scale;
+    if (lane < nq1) gP[t * MAXQ + lane] = gp;
   }
   // lbuf = -(p^phi)^2 K^R f (one task per (cell, field, j): a column of nq0 values)
   for (int x = tid; x < TCe * 2 * nq1; x += NT) {
@@ -243,13 +266,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   }
   __syncthreads();
 
-  // ==== phase B: equilibrium moment vectors per cell and the K~^phi part of the force
-  for (int x = tid; x < TCe * 4; x += NT) {
-    const int t = x >> 2, ax = (x >> 1) & 1, side = x & 1;
-    const real u = (ax ? cu1[t] : cu0[t]) * (side ? real(-1) : real(1));
-    eq_moment_vector<real>(ax ? m.kind1 : m.kind0, ax ? m.N1 : m.N0, u, cTr[t], mv + (t * 4 + ax * 2 + side) * MAXN);
-  }
-  // lbuf += p^R K~^phi f (one task per (cell, field, i): a row of nq1 values)
+  // ==== phase B: the K~^phi part of the force (adds to the K^R part), and the walls
   for (int x = tid; x < TCe * 2 * nq0; x += NT) {
     const int i = x % nq0, td2 = x / nq0, d = td2 & 1, t = td2 >> 1;
     const real* F = tile + (t + 3) * row + d + 2 * i * nq1;
@@ -269,31 +286,9 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       }
     }
   }
-  __syncthreads();
-
-  // ==== phase C: equilibrium factors per cell, and the walls
-  for (int x = tid; x < TCe * (nq0 + nq1); x += NT) {
-    const int t = x / (nq0 + nq1);
-    int k = x - t * (nq0 + nq1);
-    if (k < nq0) {
-      const int side = (m.kind0 == 1 && p0r[k] < real(0)) ? 1 : 0;
-      const real* mm = mv + (t * 4 + side) * MAXN;
-      real g = 0;
-      for (int s = 0; s <= m.N0; ++s) g += tabr0[k * MAXN + s] * mm[s];
-      gRn[t * MAXQ + k] = cn[t] * g;
-    } else {
-      k -= nq0;
-      const int side = (m.kind1 == 1 && p1r[k] < real(0)) ? 1 : 0;
-      const real* mm = mv + (t * 4 + 2 + side) * MAXN;
-      real g = 0;
-      for (int s = 0; s <= m.N1; ++s) g += tabr1[k * MAXN + s] * mm[s];
-      gP[t * MAXQ + k] = g;
-    }
-  }
-  __syncthreads();
-  if (tid < TCe) normalise_equilibrium<real>(gRn + tid * MAXQ, gP + tid * MAXQ, nq0, nq1, cnd[tid]);
   for (int wall = 0; wall < 2; ++wall) {
-    const bool active = wall == 0 ? (c0 == 0) : (c0 + TC + 3 > n);
+    // every tile whose stencils reach a ghost cell fills the ghosts itself
+    const bool active = wall == 0 ? (c0 < 3) : (c0 + TCe + 3 > n);
     if (!active) continue;  // uniform across the CTA
     const double uw = wall == 0 ? in.u_in : in.u_out;
     const double Tw = wall == 0 ? in.T_in : in.T_out;
@@ -321,7 +316,7 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     }
     __syncthreads();
     // outgoing wall flux of f' (field 0) and the incoming equilibrium flux, FP64 sums
-    const int sA = wall == 0 ? 3 : (n - 1 - c0 + 3);  // slot of the wall-adjacent cell
+    const int sA = wall == 0 ? 3 - c0 : (n - 1 - c0 + 3);  // slot of the wall-adjacent cell
     const int dir = wall == 0 ? 1 : -1;                // towards the interior
     double num = 0;
     for (int v = tid; v < V; v += NT) {
