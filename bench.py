@@ -52,6 +52,22 @@ def dist_env():
     return rank, world, local
 
 
+def whole_job_rate(local_ms, units_per_rank, steps, world):
+    """(whole-job rate, the slowest rank's milliseconds).  Every rank timed
+    `steps` steps of `units_per_rank` cell-velocities in `local_ms`; the job
+    takes as long as its slowest rank (all-reduce MAX over the process group
+    when world > 1), and the rate counts the units of all ranks."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return units_per_rank * world * steps / (total_ms * 1e-3), total_ms
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -263,6 +279,70 @@ def bench_channel(args, torch, stream, vlb):
             "density_finite": bool(np.all(np.isfinite(n)))}
 
 
+def time_to_steady(args, torch):
+    """The second metric: steps and seconds until a batch of held-out Couette
+    instances stays within 1e-3 of its steady profile, started from the rest
+    state (the paper's start) and from the learned warm start.  The network is
+    trained here first, on steady states the solver computes (its cost is
+    reported).  Seconds per step of the same batch are measured for the FP32
+    and the FP64 solver; the FP64 time to steady is its seconds per step times
+    the cold FP32 run's step count (the two paths converge to the same profile
+    within the tolerance).  Reduced scale: see the workload string."""
+    from paper_1708_05944_gb300 import vlb, warmstart as W
+    from paper_1708_05944_gb300.inputs import HELDOUT_SEED, TRAIN_SEED, couette_instances
+    kn_range = (-1.0, 1.0)
+    t0 = time.perf_counter()
+    train = couette_instances(192, seed=TRAIN_SEED, n_min=64, n_max=64, log10_kn=kn_range)
+    c = W.make_context(train)
+    c.init_equilibrium()
+    c.step_graph(0.0, 80_000)
+    targets = np.stack(W.profiles(c, train))
+    c.close()
+    t_data = time.perf_counter() - t0
+    ws = W.WarmStart()
+    ws.init_params(0)
+    t1 = time.perf_counter()
+    hist = ws.fit(W.conditions(train), targets, steps=1500, batch=64, lr=2e-3)
+    t_train = time.perf_counter() - t1
+    held = couette_instances(48, seed=HELDOUT_SEED, n_min=64, n_max=96, log10_kn=kn_range)
+    chunk, n_chunks, tol = 400, 200, 1e-3
+    cold, warm, e0, _ = W.compare(held, ws, chunk=chunk, n_chunks=n_chunks, tol=tol)
+    t2 = time.perf_counter()
+    seeds = W.seed_fields(held, ws.predict_instances(held))
+    t_seed = time.perf_counter() - t2
+    ws.close()
+    per_step = {}
+    for name, prec, n in (("fp32", vlb.VLB_FP32_BULK, 2001), ("fp64", vlb.VLB_FP64, 201)):
+        ctx = W.make_context(held, precision=prec)
+        ctx.init_equilibrium()
+        ctx.step_graph(0.0, 30)
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        ctx.step_graph(0.0, n)
+        ctx.read_moments()
+        per_step[name] = (time.perf_counter() - a) / n
+        ctx.close()
+    horizon = chunk * n_chunks
+    cc = np.where(cold < 0, horizon, cold)
+    wc = np.where(warm < 0, horizon, warm)
+    cells = sum(i["n_cells"] for i in held)
+    return {
+        "workload": f"{len(held)} held-out Couette instances, {cells} cells in total (64..96 each), HH(4;8)xH(4;20), "
+                    "log10 Kn ~ U[-1, 1], inner wall speed ~ U[0.01, 0.5], R_out/R_in ~ U[1.5, 4]; network trained on "
+                    "192 solver steady states on 64 cells",
+        "criterion": f"first step after which max(n, u^phi / u_w, T) RMS deviation from the steady profile stays < {tol}",
+        "steps_cold": {"mean": float(cc.mean()), "max": int(cc.max()), "never": int((cold < 0).sum())},
+        "steps_warm": {"mean": float(wc.mean()), "max": int(wc.max()), "never": int((warm < 0).sum())},
+        "seed_error_median": float(np.median(e0)),
+        "seconds_per_step": per_step,
+        "seconds_to_steady": {"cold_fp64": per_step["fp64"] * float(cc.max()),
+                              "cold_fp32": per_step["fp32"] * float(cc.max()),
+                              "warm_fp32": per_step["fp32"] * float(wc.max()) + t_seed},
+        "warm_start_cost_s": {"training_data": t_data, "training": t_train, "seed": t_seed,
+                              "final_loss": float(hist[-50:].mean())},
+    }
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_env()
@@ -290,14 +370,9 @@ def run_gpu(args):
     step_ms, stage_ms = time_device(ctx, torch, stream, args.steps, args.warmup, flush)
     clocks = sampler.stop()
     torch.cuda.synchronize()
-    total_ms = float(step_ms.sum())
+    value, total_ms = whole_job_rate(float(step_ms.sum()), units, args.steps, world)
     if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    value = units * world * args.steps / (total_ms * 1e-3)
+        torch.distributed.barrier()
     launches = 3 * args.steps
 
     # roofline of the stage kernel: algorithmic bytes per launch / mean launch time
@@ -313,7 +388,7 @@ def run_gpu(args):
     host_out = torch.empty_like(host_in).pin_memory()
     e2e_steps = max(3, min(args.steps, 50))
     e2e_s = time_e2e(ctx, torch, stream, host_in, host_out, e2e_steps)
-    e2e_value = units * world * e2e_steps / e2e_s
+    e2e_value, _ = whole_job_rate(e2e_s * 1e3, units, e2e_steps, world)
     ctx.close()
 
     # FP64 path on the same batch
@@ -322,10 +397,11 @@ def run_gpu(args):
     tuned64, _ = ctx64.autotune(DT, reps=5)
     shape64 = ctx64.variants()[tuned64]
     s64, _ = time_device(ctx64, torch, stream, max(3, min(args.steps, 20)), 2, flush)
-    fp64_value = units * world * len(s64) / (float(s64.sum()) * 1e-3)
+    fp64_value, _ = whole_job_rate(float(s64.sum()), units, len(s64), world)
     ctx64.close()
 
     channel = bench_channel(args, torch, stream, vlb) if args.workload in ("all", "channel") else None
+    steady = time_to_steady(args, torch) if args.time_to_steady and rank == 0 else None
 
     if rank != 0:
         return
@@ -358,6 +434,8 @@ def run_gpu(args):
                  "launch_shape": {"cells_per_cta": shape64[0], "threads": shape64[1]}},
         "channel": channel,
     }
+    if steady is not None:
+        line["time_to_steady"] = steady
     print(json.dumps(line), flush=True)
 
 
@@ -374,6 +452,8 @@ def main():
     ap.add_argument("--channel-cells", default="512x2048", help="lambda x xi cells of the channel measurement")
     ap.add_argument("--channel-steps", type=int, default=5)
     ap.add_argument("--channel-warmup", type=int, default=3)
+    ap.add_argument("--time-to-steady", action="store_true",
+                    help="add the time-to-steady measurement (cold and warm-started runs; about a minute)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

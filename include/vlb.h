@@ -152,6 +152,22 @@ vlb_status vlb_sizes(const vlb_ctx* ctx, long long* total_cells, int* nvel, long
 /* Overwrite the walls (host arrays of n_inst entries). */
 vlb_status vlb_set_walls(vlb_ctx* ctx, const vlb_wall* inner, const vlb_wall* outer);
 
+/* Set the Knudsen number and the relaxation-time convention of every instance
+ * (Couette: tau = Kn/(n T), Aoki's sqrt(pi/8) Kn/n or Kn/n, vlb_tau_mode; the
+ * paper uses the first for the Navier-Stokes comparisons, Sec. VI, and the
+ * second for its Kn scans).  The channel relaxes with tau = Kn/(n T) (Sec. VII.C);
+ * another mode there gives VLB_ERR_UNSUPPORTED.  Kn must be finite and > 0
+ * (VLB_ERR_INVALID).  Takes effect from the next stage; synchronises the stream. */
+vlb_status vlb_set_knudsen(vlb_ctx* ctx, double kn, int tau_mode);
+
+/* Channel contexts only: densities of the inlet and outlet particle reservoirs
+ * and their temperature T0, which is also the wall temperature.  The paper's
+ * channel prescribes flow rates instead; the reservoirs read its "pressure
+ * ratio" (see vlb_create_channel).  All three must be finite and > 0
+ * (VLB_ERR_INVALID); a Couette context gives VLB_ERR_UNSUPPORTED.  Takes effect
+ * from the next stage. */
+vlb_status vlb_set_channel_reservoirs(vlb_ctx* ctx, double n_in, double n_out, double T0);
+
 /* Set every cell of every instance to f_eq(n0, (u0, u1), T0) (Eq. feq_red). */
 vlb_status vlb_init_equilibrium(vlb_ctx* ctx, double n0, double u0, double u1, double T0);
 

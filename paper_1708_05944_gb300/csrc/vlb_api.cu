@@ -657,6 +657,56 @@ vlb_status vlb_set_walls(vlb_ctx* c, const vlb_wall* inner, const vlb_wall* oute
   return VLB_OK;
 }
 
+// Channel launches take their descriptor (dt, Kn, reservoirs) by value, so a
+// captured three-step graph holds the values of its capture: drop the graphs
+// whenever one of them changes (Couette instances read theirs from device
+// memory and keep their graphs).
+static vlb_status drop_channel_graphs(vlb_ctx* c) {
+  if (c->kind != 1) return VLB_OK;
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int b = 0; b < 3; ++b) {
+    if (c->graph_exec[b]) cudaGraphExecDestroy(c->graph_exec[b]);
+    c->graph_exec[b] = nullptr;
+    c->graph_variant[b] = -1;
+  }
+  return VLB_OK;
+}
+
+vlb_status vlb_set_knudsen(vlb_ctx* c, double kn, int tau_mode) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (!(kn > 0.0) || !std::isfinite(kn)) return fail(c, VLB_ERR_INVALID, "Kn must be finite and > 0");
+  if (tau_mode < VLB_TAU_KN_OVER_NT || tau_mode > VLB_TAU_KN_OVER_N)
+    return fail(c, VLB_ERR_INVALID, "unknown relaxation-time convention");
+  if (c->kind == 1) {
+    if (tau_mode != VLB_TAU_KN_OVER_NT)
+      return fail(c, VLB_ERR_UNSUPPORTED, "the channel relaxes with tau = Kn / (n T)");
+    c->cdesc.kn = kn;
+    c->cdesc.knf = float(kn);
+    return drop_channel_graphs(c);
+  }
+  for (int i = 0; i < c->n_inst; ++i) {
+    c->inst[i].kn = kn;
+    c->inst[i].kn_f = float(kn);
+    c->inst[i].tau_mode = tau_mode;
+  }
+  VLB_CUDA(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice,
+                              c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_set_channel_reservoirs(vlb_ctx* c, double n_in, double n_out, double T0) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (c->kind != 1) return fail(c, VLB_ERR_UNSUPPORTED, "reservoirs belong to channel contexts");
+  if (!(n_in > 0.0) || !(n_out > 0.0) || !(T0 > 0.0) || !std::isfinite(n_in) || !std::isfinite(n_out) ||
+      !std::isfinite(T0))
+    return fail(c, VLB_ERR_INVALID, "reservoir densities and temperature must be finite and > 0");
+  c->cdesc.n_in = n_in, c->cdesc.n_inf = float(n_in);
+  c->cdesc.n_out = n_out, c->cdesc.n_outf = float(n_out);
+  c->cdesc.T0 = T0, c->cdesc.T0f = float(T0);
+  return drop_channel_graphs(c);
+}
+
 vlb_status vlb_init_equilibrium(vlb_ctx* c, double n0, double u0, double u1, double T0) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
   if (!(n0 > 0.0) || !(T0 > 0.0)) return fail(c, VLB_ERR_INVALID, "need n0 > 0 and T0 > 0");
@@ -747,7 +797,7 @@ vlb_status vlb_set_dt(vlb_ctx* c, const double* dt) {
   VLB_CUDA(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice,
                               c->stream));
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
-  return VLB_OK;
+  return drop_channel_graphs(c);
 }
 
 static vlb_status apply_dt(vlb_ctx* c, double dt) {

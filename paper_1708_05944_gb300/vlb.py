@@ -62,6 +62,8 @@ EXPORTS = {
     "vlb_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "vlb_set_walls": (C.c_int, [C.c_void_p, C.POINTER(vlb_wall), C.POINTER(vlb_wall)]),
     "vlb_init_equilibrium": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "vlb_set_knudsen": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
+    "vlb_set_channel_reservoirs": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
     "vlb_set_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_read_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_stage": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
@@ -220,6 +222,9 @@ class _Context:
         _check(_lib.vlb_read_moments(self.h, _ptr(n), _ptr(u0), _ptr(u1), _ptr(T), _ptr(Tab), _ptr(q), 0), self.h)
         return (n, u0, u1, T, Tab, q) if full else (n, u0, u1, T)
 
+    def set_knudsen(self, kn, tau_mode=VLB_TAU_KN_OVER_NT):
+        _check(_lib.vlb_set_knudsen(self.h, kn, tau_mode), self.h)
+
     def init_from_moments(self, n, u0, u1, T, q0=None):
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (n, u0, u1, T)]
         q = None if q0 is None else np.ascontiguousarray(q0, dtype=np.float64)
@@ -321,6 +326,9 @@ class Channel(_Context):
         self.n_inst = 1
         self.n_lambda, self.n_xi = n_lambda, n_xi
         self._sizes()
+
+    def set_reservoirs(self, n_in, n_out, T0=1.0):
+        _check(_lib.vlb_set_channel_reservoirs(self.h, n_in, n_out, T0), self.h)
 
     def channel_variants(self):
         ts, tp, nt = (np.zeros(8, dtype=np.int32) for _ in range(3))

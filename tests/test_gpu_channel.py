@@ -118,3 +118,46 @@ def test_full_size_rest_state_is_exact(prec):
     assert float((f1 - f0).abs().max() / scale) < tol
     np.testing.assert_allclose(c.wall_density(), 1.0, rtol=0, atol=1e-5 if prec else 1e-12)
     c.close()
+
+
+def test_reservoirs_and_knudsen_set_after_creation():
+    # a context created with one Kn and one pair of reservoirs, then changed, steps as the
+    # oracle built with the new values
+    nl, nx = 9, 12
+    _, F0 = case(MODEL, nl, nx, kn=0.2, n_in=1.5, n_out=0.8)
+    o2 = ChannelOracle(MODEL, ChannelGrid(nl, nx), 0.2, n_in=1.5, n_out=0.8, T0=1.1)
+    c = vlb.Channel(MODEL, vlb.VLB_FP64, nl, nx, 0.05)
+    c.set_knudsen(0.2)
+    c.set_reservoirs(1.5, 0.8, 1.1)
+    c.set_f(to_lib(F0))
+    dt = 2e-3
+    F1 = o2.stage(1, dt, F0, F0)
+    c.stage(dt, 1)
+    assert rel_err(to_oracle(c.read_f(), nl, nx), F1) < 1e-12
+    with pytest.raises(vlb.VlbError):
+        c.set_knudsen(0.2, vlb.VLB_TAU_AOKI)
+    with pytest.raises(vlb.VlbError):
+        c.set_reservoirs(-1.0, 1.0)
+    c.close()
+
+
+def test_channel_graph_follows_changed_parameters():
+    # a captured graph holds the launch parameters of its capture: after a change of dt or
+    # Kn the graph path must still be the plain path, bit for bit
+    nl, nx = 8, 8
+    _, F0 = case(MODEL, nl, nx, seed=9)
+    a = vlb.Channel(MODEL, vlb.VLB_FP32_BULK, nl, nx, 0.05)
+    b = vlb.Channel(MODEL, vlb.VLB_FP32_BULK, nl, nx, 0.05)
+    for c in (a, b):
+        c.set_f(to_lib(F0).astype(np.float32))
+    a.step_graph(1e-3, 3)
+    b.step(1e-3, 3)
+    a.step_graph(5e-4, 3)
+    b.step(5e-4, 3)
+    for c in (a, b):
+        c.set_knudsen(0.3)
+    a.step_graph(5e-4, 3)
+    b.step(5e-4, 3)
+    assert np.array_equal(a.read_f(), b.read_f())
+    a.close()
+    b.close()

@@ -185,3 +185,19 @@ def test_every_launch_shape_matches_oracle(prec):
     best, ms = c.autotune(1e-4, reps=5)
     assert 0 <= best < len(shapes) and ms > 0
     c.close()
+
+
+def test_knudsen_set_after_creation():
+    o, F0, grid = make_case("HH(3;4)xH(3;4)", 24, kn=2.0, tau_mode=vlb.VLB_TAU_KN_OVER_NT)
+    c = vlb.Couette("HH(3;4)xH(3;4)", vlb.VLB_FP64, [grid], [(0.1, 1.0)], [(0.0, 1.0)], [0.1], [vlb.VLB_TAU_AOKI])
+    c.set_knudsen(2.0, vlb.VLB_TAU_KN_OVER_NT)
+    c.set_f(to_lib(F0))
+    dt = 1e-3
+    c.stage(dt, 1)
+    F1 = o.stage(1, dt, F0, F0)
+    assert rel_err(to_oracle(c.read_f()), F1) < 1e-13
+    with pytest.raises(vlb.VlbError):
+        c.set_knudsen(0.0)
+    with pytest.raises(vlb.VlbError):
+        vlb._check(vlb._lib.vlb_set_channel_reservoirs(c.h, 2.0, 1.0, 1.0), c.h)
+    c.close()

@@ -65,3 +65,8 @@ def test_invalid_arguments_rejected_without_gpu():
             vlb.Couette(b.get("model", "HH(3;4)xH(3;4)"), vlb.VLB_FP64, b.get("grids", [dict(n_cells=8)]),
                         [(0.1, 1.0)], [(0.0, 1.0)], b.get("kn", [0.1]), b.get("tau", [1]))
         assert e.value.status in (vlb.VLB_ERR_INVALID, vlb.VLB_ERR_UNSUPPORTED)
+
+
+def test_setters_reject_a_null_context_without_gpu():
+    assert vlb._lib.vlb_set_knudsen(None, 0.1, vlb.VLB_TAU_AOKI) == vlb.VLB_ERR_INVALID
+    assert vlb._lib.vlb_set_channel_reservoirs(None, 2.0, 1.0, 1.0) == vlb.VLB_ERR_INVALID
