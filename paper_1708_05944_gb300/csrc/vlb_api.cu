@@ -133,6 +133,7 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   a.n_tiles = int(c->tiles.size());
   a.geo = c->d_geo;
   a.nw = c->d_nw;
+  a.wall = c->d_wall;
   a.err = c->d_err;
   a.Vp = c->Vp;
   a.max_polls = 1ull << 26;
@@ -240,6 +241,71 @@ void fill_reference(ModelArgs& m) {
   m.ref_sum_f = sf0 * sf1;
   m.ref_flux_pos = pos * s1;
   m.ref_flux_neg = neg * s1;
+  m.ref_nf[0] = float(m.ref_n);
+  m.ref_nf[1] = float(m.ref_n - double(m.ref_nf[0]));
+  m.ref_sumf[0] = float(m.ref_sum_f);
+  m.ref_sumf[1] = float(m.ref_sum_f - double(m.ref_sumf[0]));
+  m.ref_rf = float(m.ref_r);
+  m.ref_pf = float(m.ref_p);
+  m.ref_ef = float(m.ref_e);
+}
+
+// Moment vector of the truncated equilibrium on one axis (the same recurrences as
+// eq_moment_vector in the kernels), on the host in double.
+void host_moment_vector(int kind, int N, double u, double T, double* m) {
+  if (kind == 0) {
+    m[0] = 1.0;
+    if (N >= 1) m[1] = u;
+    for (int l = 2; l <= N; ++l) m[l] = (u * m[l - 1] + (T - 1.0) * m[l - 2]) / double(l);
+    return;
+  }
+  const double pi = 3.14159265358979323846;
+  const double g0 = std::exp(-u * u / (2.0 * T)) / std::sqrt(2.0 * pi * T);
+  m[0] = 0.5 * (1.0 + std::erf(u / std::sqrt(2.0 * T)));
+  if (N >= 1) m[1] = u * m[0] + T * g0;
+  for (int s = 2; s <= N; ++s) m[s] = u * m[s - 1] + double(s - 1) * T * m[s - 2];
+}
+
+// Wall equilibria f_eq(1, (0, u_w), T_w) of every Couette instance (inner, outer):
+// factors per axis and incoming flux, into c->walls (host) for upload to d_wall.
+void fill_walls(vlb_ctx* c, std::vector<WallEq>& out) {
+  const ModelArgs& m = c->margs;
+  out.assign(size_t(2) * c->n_inst, WallEq{});
+  for (int i = 0; i < c->n_inst; ++i)
+    for (int w = 0; w < 2; ++w) {
+      WallEq& e = out[size_t(2) * i + w];
+      const double uw = w == 0 ? c->inst[i].u_in : c->inst[i].u_out;
+      const double Tw = w == 0 ? c->inst[i].T_in : c->inst[i].T_out;
+      double mp[MAXN], mm[MAXN];
+      host_moment_vector(m.kind0, m.N0, 0.0, Tw, mp);
+      for (int k = 0; k < m.nq0; ++k) {
+        double g = 0;
+        for (int s = 0; s <= m.N0; ++s) g += m.tab0[k * MAXN + s] * mp[s];  // u = 0: both sides alike
+        e.g0[k] = g;
+      }
+      host_moment_vector(m.kind1, m.N1, uw, Tw, mp);
+      host_moment_vector(m.kind1, m.N1, -uw, Tw, mm);
+      for (int k = 0; k < m.nq1; ++k) {
+        const double* v = (m.kind1 == 1 && m.p1[k] < 0.0) ? mm : mp;
+        double g = 0;
+        for (int s = 0; s <= m.N1; ++s) g += m.tab1[k * MAXN + s] * v[s];
+        e.g1[k] = g;
+      }
+      const double sgn = w == 0 ? 1.0 : -1.0;  // incoming half: p^R > 0 at the inner wall
+      double s0 = 0, s1 = 0;
+      for (int k = 0; k < m.nq0; ++k)
+        if (sgn * m.p0[k] > 0.0) s0 += e.g0[k] * m.p0[k];
+      for (int k = 0; k < m.nq1; ++k) s1 += e.g1[k];
+      e.in_flux = s0 * s1;
+    }
+}
+
+vlb_status upload_walls(vlb_ctx* c) {
+  std::vector<WallEq> w;
+  fill_walls(c, w);
+  VLB_CUDA(c, cudaMemcpyAsync(c->d_wall, w.data(), sizeof(WallEq) * w.size(), cudaMemcpyHostToDevice, c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VLB_OK;
 }
 
 // The buffer that holds neither F_l nor the last result: free between calls.
@@ -468,11 +534,16 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   VLB_CUDA(cp, cudaMalloc(&c->d_geo, sizeof(GeoCell) * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_geof, sizeof(GeoCellF) * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_nw, sizeof(double) * 2 * n_inst));
+  VLB_CUDA(cp, cudaMalloc(&c->d_wall, sizeof(WallEq) * 2 * n_inst));
   VLB_CUDA(cp, cudaMalloc(&c->d_err, sizeof(unsigned)));
   VLB_CUDA(cp, cudaMalloc(&c->d_mom, sizeof(double) * 9 * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_prev, sizeof(double) * 9 * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_res, sizeof(double) * 3 * n_inst));
   VLB_CUDA(cp, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * n_inst, cudaMemcpyHostToDevice, c->stream));
+  {
+    vlb_status ws = upload_walls(cp);
+    if (ws != VLB_OK) return ws;
+  }
   VLB_CUDA(cp, cudaMemcpyAsync(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * c->tiles.size(),
                                cudaMemcpyHostToDevice, c->stream));
   VLB_CUDA(cp, cudaMemcpyAsync(c->d_geo, c->geo.data(), sizeof(GeoCell) * c->total_cells, cudaMemcpyHostToDevice,
@@ -654,7 +725,7 @@ vlb_status vlb_set_walls(vlb_ctx* c, const vlb_wall* inner, const vlb_wall* oute
   VLB_CUDA(c, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice,
                               c->stream));
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
-  return VLB_OK;
+  return upload_walls(c);
 }
 
 // Channel launches take their descriptor (dt, Kn, reservoirs) by value, so a
@@ -1175,6 +1246,7 @@ void vlb_destroy(vlb_ctx* c) {
     if (c->graph_exec[b]) cudaGraphExecDestroy(c->graph_exec[b]);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
   cudaFree(c->d_nw);
+  cudaFree(c->d_wall);
   cudaFree(c->d_err);
   cudaFree(c->d_mom);
   cudaFree(c->d_prev);

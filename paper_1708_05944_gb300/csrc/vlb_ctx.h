@@ -43,6 +43,7 @@ struct vlb_ctx {
   GeoCell* d_geo = nullptr;
   GeoCellF* d_geof = nullptr;
   double* d_nw = nullptr;
+  WallEq* d_wall = nullptr;  // Couette: 2 per instance (inner, outer)
   unsigned* d_err = nullptr;
   double* d_mom = nullptr;
   double* d_prev = nullptr;

@@ -21,6 +21,16 @@ struct InstDesc {
   float kn_f, dt_f;                 // single-precision copies
 };
 
+// Diffuse-wall equilibrium f_eq(1, (0, u_w), T_w) of one wall (Eq. weno_populate):
+// its factors per axis and its incoming particle flux, sum over the incoming
+// half of g0_i p_i times sum_j g1_j.  They depend on the wall only, so the host
+// computes them when the walls are set.
+struct WallEq {
+  double g0[MAXQ], g1[MAXQ];
+  double in_flux;
+  double pad;
+};
+
 struct TileDesc {
   int inst;
   int c0;  // first cell (within the instance) owned by the tile
@@ -59,6 +69,9 @@ struct ModelArgs {
   double ref_n, ref_r, ref_p, ref_e;  // sum R, sum p0 R, sum p1 R, sum (p0^2 + p1^2) R + sum R
   double ref_sum_f;                   // sum of the single-precision products float(w0_i) float(w1_j)
   double ref_flux_pos, ref_flux_neg;  // sum over p0 > 0 (p0 < 0) of p0 R
+  // single-precision copies: ref_n and ref_sum_f as (hi, lo) float pairs, the others rounded
+  float ref_nf[2], ref_sumf[2];
+  float ref_rf, ref_pf, ref_ef;
 };
 
 template <typename real>
@@ -348,6 +361,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsign
     if (done) return true;
   }
   return false;
+}
+
+// Compensated butterfly sum over the warp in single precision.  Each step adds
+// the partner's value with Knuth's TwoSum, which yields the rounding error of the
+// addition exactly; the errors accumulate in e.  On return every lane holds the
+// same (s, e), whose sum s + e carries about twice the float precision, so a
+// reduction that would otherwise need the 1/64-rate FP64 pipe stays on FP32.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ void warp_sum_comp(float& s, float& e) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o), e2 = __shfl_xor_sync(0xffffffffu, e, o);
+    const float t = __fadd_rn(s, s2);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
+    s = t;
+    e = __fadd_rn(__fadd_rn(e, e2), err);
+  }
 }
 
 template <typename real>

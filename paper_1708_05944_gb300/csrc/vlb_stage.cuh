@@ -34,6 +34,7 @@ struct StageArgs {
   const GeoCell* geo;    // per global cell
   const GeoCellF* geof;  // single-precision copy
   double* nw;          // 2 per instance: inner, outer wall density
+  const WallEq* wall;  // 2 per instance: inner, outer wall equilibrium
   unsigned* err;
   int Vp;              // velocities per cell row, padded (>= nq0 nq1, multiple of 4); a row holds 2 Vp reals
   unsigned long long max_polls;
@@ -49,13 +50,12 @@ struct StageSmem {
     size_t o = lbuf_off(Vp) + size_t(TC) * 2 * Vp * sizeof(real);
     return (o + 15) & ~size_t(15);
   }
-  // doubles: p0, p1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each, wall equilibria), reduction (NW*4),
-  // wall scratch: equilibrium factors (2*MAXQ), moment vectors (4*MAXN), scalars (16), cell n (TC)
-  static constexpr size_t n_dbl = 2 * MAXQ + 2 * MAXQ * MAXN + NW * 4 + 2 * MAXQ + 4 * MAXN + 16 + TC;
+  // doubles: p0, p1 (MAXQ each), reduction (NW*4), wall equilibrium factors (2*MAXQ), scalars (16)
+  static constexpr size_t n_dbl = 2 * MAXQ + NW * 4 + 2 * MAXQ + 16;
   __host__ __device__ static size_t real_off(int Vp) { return dbl_off(Vp) + n_dbl * sizeof(double); }
   // reals: p0, p1, 1/w0, 1/w1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each), n g_R and g_phi (TC*MAXQ each),
-  // cell n, T, u0, u1, 1/tau, cp, cm, 1/Rbar (TC each), moment vectors (TC*4*MAXN), w0, w1 (MAXQ each)
-  static constexpr size_t n_real = 4 * MAXQ + 2 * MAXQ * MAXN + 2 * TC * MAXQ + 8 * TC + TC * 4 * MAXN + 2 * MAXQ;
+  // cell T, 1/tau, cp, cm, 1/Rbar (TC each), moment vectors (TC*4*MAXN), w0, w1 (MAXQ each)
+  static constexpr size_t n_real = 4 * MAXQ + 2 * MAXQ * MAXN + 2 * TC * MAXQ + 5 * TC + TC * 4 * MAXN + 2 * MAXQ;
   __host__ __device__ static size_t bytes(int Vp) { return real_off(Vp) + n_real * sizeof(real); }
 };
 
@@ -80,14 +80,10 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   real* lbuf = reinterpret_cast<real*>(smem + L::lbuf_off(Vp));
   double* p0d = reinterpret_cast<double*>(smem + L::dbl_off(Vp));
   double* p1d = p0d + MAXQ;
-  double* tab0 = p1d + MAXQ;
-  double* tab1 = tab0 + MAXQ * MAXN;
-  double* red = tab1 + MAXQ * MAXN;
+  double* red = p1d + MAXQ;
   double* gw0 = red + NW * 4;  // wall equilibrium factors
   double* gw1 = gw0 + MAXQ;
-  double* wmv = gw1 + MAXQ;    // wall moment vectors [axis*2 + side][s]
-  double* mw = wmv + 4 * MAXN;  // [0] incoming equilibrium flux, [1] n_w
-  double* cnd = mw + 16;       // [t] cell density as summed (FP64)
+  double* mw = gw1 + MAXQ;     // [0] incoming equilibrium flux, [1] n_w
   real* p0r = reinterpret_cast<real*>(smem + L::real_off(Vp));
   real* p1r = p0r + MAXQ;
   real* iw0 = p1r + MAXQ;  // 1 / w_i
@@ -96,11 +92,8 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   real* tabr1 = tabr0 + MAXQ * MAXN;
   real* gRn = tabr1 + MAXQ * MAXN;  // [t][i] n_t g_{R,i}
   real* gP = gRn + TC * MAXQ;       // [t][j] g_{phi,j}
-  real* cn = gP + TC * MAXQ;
-  real* cTr = cn + TC;
-  real* cu0 = cTr + TC;
-  real* cu1 = cu0 + TC;
-  real* cItau = cu1 + TC;
+  real* cTr = gP + TC * MAXQ;
+  real* cItau = cTr + TC;
   real* ccp = cItau + TC;
   real* ccm = ccp + TC;
   real* cIR = ccm + TC;
@@ -133,8 +126,6 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     }
   }
   for (int x = tid; x < MAXQ * MAXN; x += NT) {
-    tab0[x] = m.tab0[x];
-    tab1[x] = m.tab1[x];
     tabr0[x] = sizeof(real) == 4 ? real(m.tab0f[x]) : real(m.tab0[x]);
     tabr1[x] = sizeof(real) == 4 ? real(m.tab1f[x]) : real(m.tab1[x]);
   }
@@ -196,25 +187,46 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       sp += pp * f1;
       se += (pr * pr + pp * pp) * f1 + f2;
     }
-    // FP64 cross-lane reduction of the four sums: transpose-and-add, six DADDs per lane
-    const bool h16 = lane & 16, h8 = lane & 8;
-    double k0 = h16 ? double(sp) : double(sn), k1 = h16 ? double(se) : double(sr);
-    const double s0 = h16 ? double(sn) : double(sp), s1 = h16 ? double(sr) : double(se);
-    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-    double kq = h8 ? k1 : k0;
-    kq += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
-    kq += __shfl_xor_sync(0xffffffffu, kq, 4);
-    kq += __shfl_xor_sync(0xffffffffu, kq, 2);
-    kq += __shfl_xor_sync(0xffffffffu, kq, 1);
-    // lanes 0, 8, 16, 24 hold the sums of n, rho u^0, rho u^1 and the energy: to every lane
-    const double dn = __shfl_sync(0xffffffffu, kq, 0);
-    const double dr = __shfl_sync(0xffffffffu, kq, 8);
-    const double dpp = __shfl_sync(0xffffffffu, kq, 16);
-    const double de = __shfl_sync(0xffffffffu, kq, 24);
-    // sums of D (FP64) plus those of R; the derived fields are formed in the bulk type
-    const real nn = real(dn + m.ref_n), u0 = real(dr + m.ref_r) / nn, u1 = real(dpp + m.ref_p) / nn;
-    const real T = (real(de + m.ref_e) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
+    // cross-lane sums; then the sums of D plus those of R (in FP64) and the derived fields
+    real nn, u0, u1, T;
+    double dn = 0.0;  // sum of D (n - sum R); meaningful on lane 0 of the FP32 path, on every lane of FP64
+    float en = 0.f;  // FP32 path: rounding error of the mass sum sn (float-float sn + en)
+    if constexpr (F32) {
+      // compensated FP32 butterflies leave the same sums on every lane; n in float-float,
+      // the other fields in FP32 through one reciprocal: no FP64 and no broadcast on the
+      // warp's dependency chain
+      float er = 0.f, ep = 0.f, ee = 0.f;
+      warp_sum_comp(sn, en);
+      warp_sum_comp(sr, er);
+      warp_sum_comp(sp, ep);
+      warp_sum_comp(se, ee);
+      float nh, nl;
+      two_sum(sn, m.ref_nf[0], nh, nl);
+      nn = nh + (nl + (en + m.ref_nf[1]));
+      const float inv = 1.0f / nn;
+      u0 = (sr + (er + m.ref_rf)) * inv;
+      u1 = (sp + (ep + m.ref_pf)) * inv;
+      T = ((se + (ee + m.ref_ef)) * inv - (u0 * u0 + u1 * u1)) * (1.0f / 3.0f);
+    } else {
+      // FP64 transpose-and-add reduction of the four sums (six DADDs per lane)
+      const bool h16 = lane & 16, h8 = lane & 8;
+      double k0 = h16 ? double(sp) : double(sn), k1 = h16 ? double(se) : double(sr);
+      const double s0 = h16 ? double(sn) : double(sp), s1 = h16 ? double(sr) : double(se);
+      k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+      k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+      double kq = h8 ? k1 : k0;
+      kq += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+      kq += __shfl_xor_sync(0xffffffffu, kq, 4);
+      kq += __shfl_xor_sync(0xffffffffu, kq, 2);
+      kq += __shfl_xor_sync(0xffffffffu, kq, 1);
+      // lanes 0, 8, 16, 24 hold the sums of n, rho u^0, rho u^1 and the energy: to every lane
+      dn = __shfl_sync(0xffffffffu, kq, 0);
+      const double dr = __shfl_sync(0xffffffffu, kq, 8);
+      const double dpp = __shfl_sync(0xffffffffu, kq, 16);
+      const double de = __shfl_sync(0xffffffffu, kq, 24);
+      nn = real(dn + m.ref_n), u0 = real(dr + m.ref_r) / nn, u1 = real(dpp + m.ref_p) / nn;
+      T = (real(de + m.ref_e) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
+    }
     if (lane == 0) {
       cTr[t] = T;
       cItau[t] = real(1) / relaxation_time<real>(in.tau_mode, F32 ? real(in.kn_f) : real(in.kn), nn, T);
@@ -238,10 +250,25 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       for (int s = 0; s <= m.N1; ++s) gp += tabr1[lane * MAXN + s] * mm[s];
     }
     // rescale g_R so that sum_i g_R sum_j g_phi is exactly the target sum D + sum R (f_eq - R
-    // of phase D then carries the cell's mass; see normalise_equilibrium)
-    const double a0 = warp_sum<real>(double(gr)), a1 = warp_sum<real>(double(gp));
-    const real scale = real((dn + (F32 ? m.ref_sum_f : m.ref_n)) / (a0 * a1));
-    if (lane < nq0) gRn[t * MAXQ + lane] = gr * scale;
+    // of phase D then carries the cell's mass; see normalise_equilibrium): g_R <- g_R (1 - delta)
+    if constexpr (F32) {
+      // A = sum g_R sum g_phi and the target sum D + sum R, both in float-float;
+      // delta = (A - target) / A, where A_hi - target_hi is exact (the two are close)
+      float a0 = gr, a0e = 0.f, a1 = gp, a1e = 0.f;
+      warp_sum_comp(a0, a0e);
+      warp_sum_comp(a1, a1e);
+      const float Ah = a0 * a1;
+      const float Al = fmaf(a0, a1e, fmaf(a0e, a1, fmaf(a0, a1, -Ah)));
+      float th, tl;
+      two_sum(sn, m.ref_sumf[0], th, tl);
+      tl = tl + (en + m.ref_sumf[1]);
+      const float delta = (__fsub_rn(Ah, th) + (Al - tl)) / Ah;
+      if (lane < nq0) gRn[t * MAXQ + lane] = fmaf(-gr, delta, gr);
+    } else {
+      const double a0 = warp_sum<real>(double(gr)), a1 = warp_sum<real>(double(gp));
+      const real scale = real((dn + m.ref_n) / (a0 * a1));
+      if (lane < nq0) gRn[t * MAXQ + lane] = gr * scale;
+    }
     if (lane < nq1) gP[t * MAXQ + lane] = gp;
   }
   // lbuf = -(p^phi)^2 K^R f (one task per (cell, field, j): a column of nq0 values)
@@ -290,29 +317,16 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
     // every tile whose stencils reach a ghost cell fills the ghosts itself
     const bool active = wall == 0 ? (c0 < 3) : (c0 + TCe + 3 > n);
     if (!active) continue;  // uniform across the CTA
-    const double uw = wall == 0 ? in.u_in : in.u_out;
     const double Tw = wall == 0 ? in.T_in : in.T_out;
     const double sgn = wall == 0 ? 1.0 : -1.0;  // incoming half: p^R > 0 at the inner wall
     __syncthreads();
-    if (tid < 4) {  // wall equilibrium f_eq(1, (0, u_w), T_w): moment vectors per (axis, side)
-      const int ax = tid >> 1, side = tid & 1;
-      const double u = (ax ? uw : 0.0) * (side ? -1.0 : 1.0);
-      eq_moment_vector<double>(ax ? m.kind1 : m.kind0, ax ? m.N1 : m.N0, u, Tw, wmv + tid * MAXN);
-    }
-    __syncthreads();
-    for (int k = tid; k < nq0 + nq1; k += NT) {
-      if (k < nq0) {
-        const double* mm = wmv + ((m.kind0 == 1 && p0d[k] < 0.0) ? 1 : 0) * MAXN;
-        double g = 0;
-        for (int s = 0; s <= m.N0; ++s) g += tab0[k * MAXN + s] * mm[s];
-        gw0[k] = g;
-      } else {
-        const int kk1 = k - nq0;
-        const double* mm = wmv + (2 + ((m.kind1 == 1 && p1d[kk1] < 0.0) ? 1 : 0)) * MAXN;
-        double g = 0;
-        for (int s = 0; s <= m.N1; ++s) g += tab1[kk1 * MAXN + s] * mm[s];
-        gw1[kk1] = g;
+    {  // the wall's equilibrium factors and incoming flux, computed by the host
+      const WallEq& we = a.wall[td.inst * 2 + wall];
+      for (int k = tid; k < nq0 + nq1; k += NT) {
+        if (k < nq0) gw0[k] = we.g0[k];
+        else gw1[k - nq0] = we.g1[k - nq0];
       }
+      if (tid == 0) mw[0] = we.in_flux;
     }
     __syncthreads();
     // outgoing wall flux of f' (field 0) and the incoming equilibrium flux, FP64 sums
@@ -331,15 +345,6 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       num += double(weno5p<real>(F2, F1, F0, G0, G1, iw0[i] * iw1[j]).x) * p0d[i];
     }
     num = warp_sum<real>(num);
-    if (warp == 0) {  // incoming flux of f_eq(1, u_w, T_w): (sum over incoming i of g_i p_i) (sum_j g_j)
-      double s0 = 0, s1 = 0;
-      for (int k = lane; k < nq0; k += 32)
-        if (sgn * p0d[k] > 0.0) s0 += gw0[k] * p0d[k];
-      for (int k = lane; k < nq1; k += 32) s1 += gw1[k];
-      s0 = warp_sum<real>(s0);
-      s1 = warp_sum<real>(s1);
-      if (lane == 0) mw[0] = s0 * s1;
-    }
     if (lane == 0) red[warp] = num;
     __syncthreads();
     if (tid == 0) {

@@ -46,6 +46,7 @@ cudaError_t launch_one(vlb_ctx* c, int k, const void* prev, const void* fl, void
   a.geo = c->d_geo;
   a.geof = c->d_geof;
   a.nw = c->d_nw;
+  a.wall = c->d_wall;
   a.err = c->d_err;
   a.Vp = c->Vp;
   a.max_polls = 1ull << 26;
