@@ -85,6 +85,49 @@ void couette_geometry(const vlb_couette_grid& g, GeoCell* out) {
   }
 }
 
+// K J = sgn J K for the reflection J of an axis (KArgs), to rounding, and the
+// nodes mirror each other: the fixed-shape kernels rely on both.
+bool force_reflection_symmetric(const std::vector<double>& p, const std::vector<double>& K, int kind, int nq,
+                                double sgn) {
+  double kmax = 0.0, pmax = 0.0;
+  for (double x : K) kmax = std::max(kmax, std::fabs(x));
+  for (double x : p) pmax = std::max(pmax, std::fabs(x));
+  for (int a = 0; a < nq; ++a) {
+    if (std::fabs(p[refl(kind, nq, a)] + p[a]) > 1e-13 * pmax) return false;
+    for (int b = 0; b < nq; ++b)
+      if (std::fabs(K[refl(kind, nq, a) * nq + refl(kind, nq, b)] - sgn * K[a * nq + b]) > 1e-12 * kmax) return false;
+  }
+  return true;
+}
+
+// The force kernels in the form the stage kernels of this shape read (KArgs):
+// full matrices, or the half-size blocks P, M of their even and odd parts.
+template <typename real>
+void fill_force_tables(KArgs<real>& k, const std::vector<double>& K0, const std::vector<double>& Kt1, int kind0,
+                       int kind1, int nq0, int nq1, bool split) {
+  memset(&k, 0, sizeof(k));
+  if (!split) {
+    for (int i = 0; i < nq0; ++i)
+      for (int ip = 0; ip < nq0; ++ip) k.full.K0[i * MAXQ + ip] = real(K0[i * nq0 + ip]);
+    for (int j = 0; j < nq1; ++j)
+      for (int jp = 0; jp < nq1; ++jp) k.full.Kt1[j * MAXQ + jp] = real(Kt1[j * nq1 + jp]);
+    return;
+  }
+  constexpr int HQ = KArgs<real>::HQ;
+  for (int i = 0; i < nq0 / 2; ++i)
+    for (int c = 0; c < nq0 / 2; ++c) {
+      const double a = K0[i * nq0 + c], b = K0[i * nq0 + refl(kind0, nq0, c)];
+      k.split.P0[i * HQ + c] = real(0.5 * (a + b));
+      k.split.M0[i * HQ + c] = real(0.5 * (a - b));
+    }
+  for (int j = 0; j < nq1 / 2; ++j)
+    for (int c = 0; c < nq1 / 2; ++c) {
+      const double a = Kt1[j * nq1 + c], b = Kt1[j * nq1 + refl(kind1, nq1, c)];
+      k.split.P1[j * HQ + c] = real(0.5 * (a + b));
+      k.split.M1[j * HQ + c] = real(0.5 * (a - b));
+    }
+}
+
 // Tiles over every instance for the current launch shape.  One-CTA-per-tile
 // launches take tiles of the shape's full size TC.  A persistent launch walks
 // the tile list in rounds of `slots` CTAs, so the tile size s <= TC is chosen to
@@ -485,18 +528,12 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   fill_reference(m);
   c->k32.reset(new KArgs<float>());
   c->k64.reset(new KArgs<double>());
-  memset(c->k32.get(), 0, sizeof(KArgs<float>));
-  memset(c->k64.get(), 0, sizeof(KArgs<double>));
-  for (int i = 0; i < nq0; ++i)
-    for (int ip = 0; ip < nq0; ++ip) {
-      c->k64->K0[i * MAXQ + ip] = c->ax[0].K[i * nq0 + ip];
-      c->k32->K0[i * MAXQ + ip] = float(c->ax[0].K[i * nq0 + ip]);
-    }
-  for (int j = 0; j < nq1; ++j)
-    for (int jp = 0; jp < nq1; ++jp) {
-      c->k64->Kt1[j * MAXQ + jp] = c->ax[1].Kt[j * nq1 + jp];
-      c->k32->Kt1[j * MAXQ + jp] = float(c->ax[1].Kt[j * nq1 + jp]);
-    }
+  const bool split = prec == VLB_FP64 ? stage_split_tables<double>(nq0, nq1) : stage_split_tables<float>(nq0, nq1);
+  if (split && !(force_reflection_symmetric(c->ax[0].p, c->ax[0].K, m.kind0, nq0, -1.0) &&
+                 force_reflection_symmetric(c->ax[1].p, c->ax[1].Kt, m.kind1, nq1, 1.0)))
+    return fail(nullptr, VLB_ERR_UNSUPPORTED, "force kernels are not reflection-symmetric");
+  fill_force_tables(*c->k64, c->ax[0].K, c->ax[1].Kt, m.kind0, m.kind1, nq0, nq1, split);
+  fill_force_tables(*c->k32, c->ax[0].K, c->ax[1].Kt, m.kind0, m.kind1, nq0, nq1, split);
 
   long long cell0 = 0;
   for (int i = 0; i < n_inst; ++i) {

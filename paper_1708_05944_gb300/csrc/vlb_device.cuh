@@ -74,11 +74,39 @@ struct ModelArgs {
   float ref_rf, ref_pf, ref_ef;
 };
 
+// Momentum-space kernels of the inertial force (Eq. boltz_couette_kom): K0 =
+// d/dp^0 on axis 0 and Kt1 = d/dp^1 (p^1 .) on axis 1.  The generic kernels read
+// the full matrices.  The fixed-shape kernels use that each commutes with the
+// reflection of its axis, up to sign: with J the node permutation p_k -> -p_k
+// (see refl), K0 J = -J K0 and Kt1 J = J Kt1.  Each then splits into two
+// half-size blocks acting on the even and odd parts e_k = f_k + f_Jk,
+// o_k = f_k - f_Jk (k over the first half of the nodes):
+//   P[i][k] = (K[i][k] + K[i][Jk]) / 2,   M[i][k] = (K[i][k] - K[i][Jk]) / 2,
+//   axis 0: (K0 f)_i = P e + M o,  (K0 f)_Ji = M o - P e;
+//   axis 1: (Kt1 f)_j = P e + M o, (Kt1 f)_Jj = P e - M o.
 template <typename real>
 struct KArgs {
-  real K0[MAXQ * MAXQ];   // d/dp^0 kernel on axis 0, [i][i'] stride MAXQ
-  real Kt1[MAXQ * MAXQ];  // d/dp^1 (p^1 .) kernel on axis 1, [j][j'] stride MAXQ
+  static constexpr int HQ = MAXQ / 2;
+  struct Full {
+    real K0[MAXQ * MAXQ];   // [i][i'] stride MAXQ
+    real Kt1[MAXQ * MAXQ];  // [j][j'] stride MAXQ
+  };
+  struct Split {
+    real P0[HQ * HQ], M0[HQ * HQ];  // [i][k] stride HQ
+    real P1[HQ * HQ], M1[HQ * HQ];  // [j][k] stride HQ
+  };
+  union {
+    Full full;
+    Split split;
+  };
 };
+
+// Index of the node at -p_k on an axis of nq nodes: half-range axes list the
+// positive nodes first and their mirror images after them (kind 1); full-range
+// axes are symmetric about their middle (kind 0).
+__host__ __device__ __forceinline__ int refl(int kind, int nq, int k) {
+  return kind == 1 ? (k < nq / 2 ? k + nq / 2 : k - nq / 2) : nq - 1 - k;
+}
 
 // Type-exact helpers: float arguments must not be promoted to double (the
 // FP64 pipe of GB300 runs at a small fraction of the FP32 rate).
@@ -159,7 +187,9 @@ __device__ __forceinline__ real weno5(real a, real b, real c, real d, real e, re
 // BGK relaxation and the RK3 combine treat f' and f'' alike, and run on the
 // pair: single precision through the packed FP32x2 add / multiply / fma of
 // sm_100 and later (each lane rounds as the scalar instruction does), double
-// precision as two scalar operations.
+// precision as two scalar operations.  p_add and p_mul are never contracted
+// into an fma (the packed intrinsics round per lane like __fadd_rn and
+// __fmul_rn), so an expression of them rounds the same wherever it is inlined.
 template <typename real>
 struct PairOf;
 template <>
@@ -178,8 +208,12 @@ __device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(
 __device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 p_set(float s) { return make_float2(s, s); }
 __device__ __forceinline__ float2 p_make(float x, float y) { return make_float2(x, y); }
-__device__ __forceinline__ double2 p_add(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 p_mul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 p_add(double2 a, double2 b) {
+  return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y));
+}
+__device__ __forceinline__ double2 p_mul(double2 a, double2 b) {
+  return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y));
+}
 __device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
   return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
 }
@@ -207,30 +241,20 @@ __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a,
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
 
-// Normalised epsilon-free WENO-5 weights of one field from its indicators (any
-// common factor of s1, s2, s3 drops out), as in weno5 above.
+// weno5 on a pair of fields: the candidate reconstructions, the indicators
+// (times 4, which the normalisation removes) and the weights run on the pair;
+// only the maxima, the reciprocals and the test for the slow path are per
+// field.  The weighted sum is normalised once at the end.  The weights are
+// products and sums of p_mul / p_add, so a cell gets the same bits at every
+// position of an unrolled walk and the result does not depend on the tile shape.
 template <typename real>
-__device__ __forceinline__ void weno5_weights(real s1, real s2, real s3, real& w1, real& w2, real& w3) {
-  const real r = vdiv(real(1), vmax(s1, vmax(s2, s3)));
-  const real x1 = rmul(s1, r), x2 = rmul(s2, r), x3 = rmul(s3, r);
-  const real P = rmul(x1, x1), Qv = rmul(x2, x2), R = rmul(x3, x3);
-  w1 = rmul(real(0.1), rmul(Qv, R)), w2 = rmul(real(0.6), rmul(P, R)), w3 = rmul(real(0.3), rmul(P, Qv));
-  const real den = radd(radd(w1, w2), w3);
-  // the fast path needs a normal-range denominator (the reciprocals above and
-  // below are single-precision fast divides); anything else -- vanishing or
-  // non-finite products, indicators out of range -- takes the slow path
-  if (!(den > real(1e-30)) || !(den < real(1e30))) {
-    real w[3];
-    weno5_weights_slow<real>(s1, s2, s3, w);
-    w1 = w[0], w2 = w[1], w3 = w[2];
-  }
-  const real iden = vdiv(real(1), radd(radd(w1, w2), w3));
-  w1 = rmul(w1, iden), w2 = rmul(w2, iden), w3 = rmul(w3, iden);
+__device__ __forceinline__ void weno5_pair_slow(real s1, real s2, real s3, real& w1, real& w2, real& w3, real& den) {
+  real w[3];
+  weno5_weights_slow<real>(s1, s2, s3, w);
+  w1 = w[0], w2 = w[1], w3 = w[2];
+  den = radd(radd(w1, w2), w3);
 }
 
-// weno5 on a pair of fields: the candidate reconstructions and the
-// indicators (times 4, which the normalisation removes) run on the pair; the
-// weights per field.
 template <typename real>
 __device__ __forceinline__ pair_t<real> weno5p(pair_t<real> a, pair_t<real> b, pair_t<real> c, pair_t<real> d,
                                                pair_t<real> e, real sc) {
@@ -250,10 +274,21 @@ __device__ __forceinline__ pair_t<real> weno5p(pair_t<real> a, pair_t<real> b, p
   const P s1 = p_fma(p_mul(t1, k), t1, p_mul(u1, u1));
   const P s2 = p_fma(p_mul(t2, k), t2, p_mul(u2, u2));
   const P s3 = p_fma(p_mul(t3, k), t3, p_mul(u3, u3));
-  real wx1, wx2, wx3, wy1, wy2, wy3;
-  weno5_weights<real>(s1.x, s2.x, s3.x, wx1, wx2, wx3);
-  weno5_weights<real>(s1.y, s2.y, s3.y, wy1, wy2, wy3);
-  return p_fma(p_make(wx1, wy1), F1, p_fma(p_make(wx2, wy2), F2, p_mul(p_make(wx3, wy3), F3)));
+  // delta_q prod_{r != q} x_r^2 with x = sigma / max sigma (exact for one vanishing indicator)
+  const P r = p_make(vdiv(real(1), vmax(s1.x, vmax(s2.x, s3.x))), vdiv(real(1), vmax(s1.y, vmax(s2.y, s3.y))));
+  const P x1 = p_mul(s1, r), x2 = p_mul(s2, r), x3 = p_mul(s3, r);
+  const P q1 = p_mul(x1, x1), q2 = p_mul(x2, x2), q3 = p_mul(x3, x3);
+  P w1 = p_mul(p_set(real(0.1)), p_mul(q2, q3));
+  P w2 = p_mul(p_set(real(0.6)), p_mul(q1, q3));
+  P w3 = p_mul(p_set(real(0.3)), p_mul(q1, q2));
+  P den = p_add(p_add(w1, w2), w3);
+  // the fast path needs a normal-range denominator (the reciprocals are
+  // single-precision fast divides); anything else -- vanishing or non-finite
+  // products, indicators out of range -- takes the slow path of Table IV
+  if (!(den.x > real(1e-30)) || !(den.x < real(1e30))) weno5_pair_slow<real>(s1.x, s2.x, s3.x, w1.x, w2.x, w3.x, den.x);
+  if (!(den.y > real(1e-30)) || !(den.y < real(1e30))) weno5_pair_slow<real>(s1.y, s2.y, s3.y, w1.y, w2.y, w3.y, den.y);
+  const P iden = p_make(vdiv(real(1), den.x), vdiv(real(1), den.y));
+  return p_mul(p_fma(w1, F1, p_fma(w2, F2, p_mul(w3, F3))), iden);
 }
 
 // ---------------------------------------------------------------- equilibrium
@@ -363,20 +398,21 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsign
   return false;
 }
 
-// Compensated butterfly sum over the warp in single precision.  Each step adds
-// the partner's value with Knuth's TwoSum, which yields the rounding error of the
-// addition exactly; the errors accumulate in e.  On return every lane holds the
-// same (s, e), whose sum s + e carries about twice the float precision, so a
-// reduction that would otherwise need the 1/64-rate FP64 pipe stays on FP32.
+// Knuth's TwoSum: s = fl(a + b) and the exact rounding error err = a + b - s.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
   s = __fadd_rn(a, b);
   const float bp = __fsub_rn(s, a);
   err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
 }
 
-__device__ __forceinline__ void warp_sum_comp(float& s, float& e) {
+// Compensated butterfly sum over each half-warp (lanes 0-15 and 16-31
+// separately) in single precision.  Each step adds the partner's value with
+// TwoSum, and the errors accumulate in e.  On return every lane of a half holds
+// the same (s, e), whose sum s + e carries about twice the float precision, so a
+// reduction that would otherwise need the 1/64-rate FP64 pipe stays on FP32.
+__device__ __forceinline__ void half_sum_comp(float& s, float& e) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = 8; o > 0; o >>= 1) {
     const float s2 = __shfl_xor_sync(0xffffffffu, s, o), e2 = __shfl_xor_sync(0xffffffffu, e, o);
     const float t = __fadd_rn(s, s2);
     const float bp = __fsub_rn(t, s);
@@ -384,6 +420,13 @@ __device__ __forceinline__ void warp_sum_comp(float& s, float& e) {
     s = t;
     e = __fadd_rn(__fadd_rn(e, e2), err);
   }
+}
+
+// Plain double sum over each half-warp.
+__device__ __forceinline__ double half_sum(double v) {
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 template <typename real>

@@ -79,6 +79,12 @@ int stage_variants(int nq0, int nq1, StageVariant* out) {
 }
 
 template <typename real>
+bool stage_split_tables(int nq0, int nq1) {
+  const int sh = shape_of(nq0, nq1);
+  return sh == SH_16x20 || sh == SH_16x12 || sh == SH_8x4;
+}
+
+template <typename real>
 size_t stage_smem_bytes(StageVariant v, int Vp) {
 #define VLB_SMEM_CASE(TC_, NT_) \
   if (v.tc == TC_ && v.nt == NT_) return StageSmem<real, TC_, NT_>::bytes(Vp);
@@ -467,6 +473,7 @@ cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelAr
 
 template int stage_variants<VLB_REAL>(int, int, StageVariant*);
 template size_t stage_smem_bytes<VLB_REAL>(StageVariant, int);
+template bool stage_split_tables<VLB_REAL>(int, int);
 template cudaError_t launch_stage<VLB_REAL>(StageVariant, const StageArgs<VLB_REAL>&, const ModelArgs&,
                                             const KArgs<VLB_REAL>&, cudaStream_t);
 template cudaError_t launch_init_equilibrium<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, double, double,

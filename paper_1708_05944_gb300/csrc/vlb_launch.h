@@ -23,6 +23,11 @@ int stage_variants(int nq0, int nq1, StageVariant* out);
 template <typename real>
 size_t stage_smem_bytes(StageVariant v, int Vp);
 
+// Whether the stage kernels of a model shape are the fixed-shape ones, which read
+// the force kernels in split form (KArgs::split); the others read them whole.
+template <typename real>
+bool stage_split_tables(int nq0, int nq1);
+
 // Launch one RK3 stage over a.n_tiles tiles of v.tc cells.
 // CTAs of a launch shape resident on the device at once (0 if unknown).
 template <typename real>

@@ -59,8 +59,17 @@ struct StageSmem {
   __host__ __device__ static size_t bytes(int Vp) { return real_off(Vp) + n_real * sizeof(real); }
 };
 
+// CTAs per SM the register allocation is sized for, where shared memory would
+// allow them but the compiler, left alone, takes too many registers a thread.  A
+// single-precision CTA of 256 to 384 threads needs at most about 64 KB of shared
+// memory for tiles up to 8 cells (three fit on an SM) and about 100 KB for 16
+// (two fit) with the model shapes that have fixed node counts.
+constexpr int stage_min_ctas(int real_bytes, int tc, int nt) {
+  return (real_bytes == 4 && nt >= 256 && nt <= 384) ? (tc <= 8 ? 3 : 2) : 1;
+}
+
 template <typename real, int TC, int Q0MAX, int Q1MAX, int NT, bool EXACT>
-__global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant__ StageArgs<real> a,
+__global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT)) couette_stage_kernel(const __grid_constant__ StageArgs<real> a,
                                                            const __grid_constant__ ModelArgs m,
                                                            const __grid_constant__ KArgs<real> kk) {
   using L = StageSmem<real, TC, NT>;
@@ -171,14 +180,20 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
   }
   parity ^= 1u;
 
-  // ==== phase A: per cell, one warp with no CTA barrier: moments (Eq. macro_red), tau, the
-  // equilibrium moment vectors and factors (Sec. IV.D) and their mass normalisation; the
-  // remaining threads start on the K^R part of the force
-  for (int t = warp; t < TCe; t += NW) {
+  // ==== phase A: per cell, one half-warp (16 lanes) with no CTA barrier: moments (Eq.
+  // macro_red), tau, the equilibrium moment vectors and factors (Sec. IV.D) and their mass
+  // normalisation.  A warp takes two cells, so each shuffle level and each per-cell scalar
+  // step serves both; warps without a cell go on to the force contractions below.
+  const int NA = (TCe + 1) >> 1;  // warps with cells
+  for (int wa = warp; wa < NA; wa += NW) {
+    const int hl = lane & 15;
+    const int tc = 2 * wa + (lane >> 4);
+    const bool has = tc < TCe;         // the upper half of the last warp of an odd tile has no cell:
+    const int t = has ? tc : TCe - 1;  // it repeats the lower half's and writes nothing
     const real* F = tile + (t + 3) * row;
-    real sn = 0, sr = 0, sp = 0, se = 0;  // per-lane partial sums over a tenth of the velocities
+    real sn = 0, sr = 0, sp = 0, se = 0;  // per-lane partial sums over a sixteenth of the velocities
 #pragma unroll 4
-    for (int v = lane; v < V; v += 32) {
+    for (int v = hl; v < V; v += 16) {
       const int i = v / nq1, j = v - i * nq1;
       const pair_t<real> f = p_load(F + 2 * v);
       const real f1 = f.x, f2 = f.y, pr = p0r[i], pp = p1r[j];
@@ -187,19 +202,19 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       sp += pp * f1;
       se += (pr * pr + pp * pp) * f1 + f2;
     }
-    // cross-lane sums; then the sums of D plus those of R (in FP64) and the derived fields
+    // sums over the half-warp; then the sums of D plus those of R and the derived fields
     real nn, u0, u1, T;
-    double dn = 0.0;  // sum of D (n - sum R); meaningful on lane 0 of the FP32 path, on every lane of FP64
-    float en = 0.f;  // FP32 path: rounding error of the mass sum sn (float-float sn + en)
+    double dn = 0.0;  // FP64 path: sum of D (n - sum R)
+    float en = 0.f;   // FP32 path: rounding error of the mass sum sn (float-float sn + en)
     if constexpr (F32) {
-      // compensated FP32 butterflies leave the same sums on every lane; n in float-float,
-      // the other fields in FP32 through one reciprocal: no FP64 and no broadcast on the
-      // warp's dependency chain
+      // compensated FP32 butterflies leave the same sums on every lane of the half; n in
+      // float-float, the other fields in FP32 through one reciprocal: no FP64 and no
+      // broadcast on the dependency chain
       float er = 0.f, ep = 0.f, ee = 0.f;
-      warp_sum_comp(sn, en);
-      warp_sum_comp(sr, er);
-      warp_sum_comp(sp, ep);
-      warp_sum_comp(se, ee);
+      half_sum_comp(sn, en);
+      half_sum_comp(sr, er);
+      half_sum_comp(sp, ep);
+      half_sum_comp(se, ee);
       float nh, nl;
       two_sum(sn, m.ref_nf[0], nh, nl);
       nn = nh + (nl + (en + m.ref_nf[1]));
@@ -208,111 +223,173 @@ __global__ void __launch_bounds__(NT) couette_stage_kernel(const __grid_constant
       u1 = (sp + (ep + m.ref_pf)) * inv;
       T = ((se + (ee + m.ref_ef)) * inv - (u0 * u0 + u1 * u1)) * (1.0f / 3.0f);
     } else {
-      // FP64 transpose-and-add reduction of the four sums (six DADDs per lane)
-      const bool h16 = lane & 16, h8 = lane & 8;
-      double k0 = h16 ? double(sp) : double(sn), k1 = h16 ? double(se) : double(sr);
-      const double s0 = h16 ? double(sn) : double(sp), s1 = h16 ? double(sr) : double(se);
-      k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
-      k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
-      double kq = h8 ? k1 : k0;
-      kq += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
-      kq += __shfl_xor_sync(0xffffffffu, kq, 4);
-      kq += __shfl_xor_sync(0xffffffffu, kq, 2);
-      kq += __shfl_xor_sync(0xffffffffu, kq, 1);
-      // lanes 0, 8, 16, 24 hold the sums of n, rho u^0, rho u^1 and the energy: to every lane
-      dn = __shfl_sync(0xffffffffu, kq, 0);
-      const double dr = __shfl_sync(0xffffffffu, kq, 8);
-      const double dpp = __shfl_sync(0xffffffffu, kq, 16);
-      const double de = __shfl_sync(0xffffffffu, kq, 24);
+      dn = half_sum(double(sn));
+      const double dr = half_sum(double(sr)), dpp = half_sum(double(sp)), de = half_sum(double(se));
       nn = real(dn + m.ref_n), u0 = real(dr + m.ref_r) / nn, u1 = real(dpp + m.ref_p) / nn;
       T = (real(de + m.ref_e) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
     }
-    if (lane == 0) {
+    if (hl == 0 && has) {
       cTr[t] = T;
       cItau[t] = real(1) / relaxation_time<real>(in.tau_mode, F32 ? real(in.kn_f) : real(in.kn), nn, T);
     }
     real* mt = mv + t * 4 * MAXN;  // moment vectors [axis * 2 + side][s]
-    if (lane < 4) {
-      const int ax = lane >> 1, side = lane & 1;
+    if (hl < 4 && has) {
+      const int ax = hl >> 1, side = hl & 1;
       const real u = (ax ? u1 : u0) * (side ? real(-1) : real(1));
-      eq_moment_vector<real>(ax ? m.kind1 : m.kind0, ax ? m.N1 : m.N0, u, T, mt + lane * MAXN);
+      eq_moment_vector<real>(ax ? m.kind1 : m.kind0, ax ? m.N1 : m.N0, u, T, mt + hl * MAXN);
     }
     __syncwarp();
-    // equilibrium factors: lane k takes g_R[k] and g_phi[k]
-    real gr = 0, gp = 0;
-    if (lane < nq0) {
-      const real* mm = mt + ((m.kind0 == 1 && p0r[lane] < real(0)) ? 1 : 0) * MAXN;
-      for (int s = 0; s <= m.N0; ++s) gr += tabr0[lane * MAXN + s] * mm[s];
-      gr *= nn;
-    }
-    if (lane < nq1) {
-      const real* mm = mt + (2 + ((m.kind1 == 1 && p1r[lane] < real(0)) ? 1 : 0)) * MAXN;
-      for (int s = 0; s <= m.N1; ++s) gp += tabr1[lane * MAXN + s] * mm[s];
+    // equilibrium factors: lane hl takes g_R[k] and g_phi[k] for k = hl and hl + 16
+    real gr[2] = {real(0), real(0)}, gp[2] = {real(0), real(0)};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int k = hl + 16 * q;
+      if (16 * q < Q0MAX && k < nq0) {
+        const real* mm = mt + ((m.kind0 == 1 && p0r[k] < real(0)) ? 1 : 0) * MAXN;
+        for (int s2 = 0; s2 <= m.N0; ++s2) gr[q] += tabr0[k * MAXN + s2] * mm[s2];
+        gr[q] *= nn;
+      }
+      if (16 * q < Q1MAX && k < nq1) {
+        const real* mm = mt + (2 + ((m.kind1 == 1 && p1r[k] < real(0)) ? 1 : 0)) * MAXN;
+        for (int s2 = 0; s2 <= m.N1; ++s2) gp[q] += tabr1[k * MAXN + s2] * mm[s2];
+      }
     }
     // rescale g_R so that sum_i g_R sum_j g_phi is exactly the target sum D + sum R (f_eq - R
     // of phase D then carries the cell's mass; see normalise_equilibrium): g_R <- g_R (1 - delta)
+    real scale0;  // FP64 path: the factor of g_R
+    float delta = 0.f;
     if constexpr (F32) {
       // A = sum g_R sum g_phi and the target sum D + sum R, both in float-float;
       // delta = (A - target) / A, where A_hi - target_hi is exact (the two are close)
-      float a0 = gr, a0e = 0.f, a1 = gp, a1e = 0.f;
-      warp_sum_comp(a0, a0e);
-      warp_sum_comp(a1, a1e);
+      float a0, a0e, a1, a1e;
+      two_sum(gr[0], gr[1], a0, a0e);
+      two_sum(gp[0], gp[1], a1, a1e);
+      half_sum_comp(a0, a0e);
+      half_sum_comp(a1, a1e);
       const float Ah = a0 * a1;
       const float Al = fmaf(a0, a1e, fmaf(a0e, a1, fmaf(a0, a1, -Ah)));
       float th, tl;
       two_sum(sn, m.ref_sumf[0], th, tl);
       tl = tl + (en + m.ref_sumf[1]);
-      const float delta = (__fsub_rn(Ah, th) + (Al - tl)) / Ah;
-      if (lane < nq0) gRn[t * MAXQ + lane] = fmaf(-gr, delta, gr);
+      delta = (__fsub_rn(Ah, th) + (Al - tl)) / Ah;
+      scale0 = real(0);
     } else {
-      const double a0 = warp_sum<real>(double(gr)), a1 = warp_sum<real>(double(gp));
-      const real scale = real((dn + m.ref_n) / (a0 * a1));
-      if (lane < nq0) gRn[t * MAXQ + lane] = gr * scale;
+      const double a0 = half_sum(double(gr[0]) + double(gr[1])), a1 = half_sum(double(gp[0]) + double(gp[1]));
+      scale0 = real((dn + m.ref_n) / (a0 * a1));
     }
-    if (lane < nq1) gP[t * MAXQ + lane] = gp;
+    if (has) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int k = hl + 16 * q;
+        if (16 * q < Q0MAX && k < nq0) gRn[t * MAXQ + k] = F32 ? real(fmaf(-float(gr[q]), delta, float(gr[q])))
+                                                                 : gr[q] * scale0;
+        if (16 * q < Q1MAX && k < nq1) gP[t * MAXQ + k] = gp[q];
+      }
+    }
   }
   // lbuf = -(p^phi)^2 K^R f (one task per (cell, field, j): a column of nq0 values)
-  for (int x = tid; x < TCe * 2 * nq1; x += NT) {
+  auto force_R = [&](int x) {
     const int j = x % nq1, td2 = x / nq1, d = td2 & 1, t = td2 >> 1;
     const real* F = tile + (t + 3) * row + d;
-    real col[Q0MAX];
-#pragma unroll
-    for (int ip = 0; ip < Q0MAX; ++ip) col[ip] = ip < nq0 ? F[2 * (ip * nq1 + j)] : real(0);
     real* Lr = lbuf + t * row + d;
     const real w = -p1r[j] * p1r[j];
+    if constexpr (EXACT) {  // even and odd parts under the reflection of axis 0 (KArgs)
+      constexpr int H = Q0MAX / 2;
+      real e[H], o[H];
 #pragma unroll
-    for (int i = 0; i < Q0MAX; ++i) {
-      if (i < nq0) {
-        real acc = 0;
+      for (int k = 0; k < H; ++k) {
+        const real fk = F[2 * (k * nq1 + j)], fr = F[2 * (refl(m.kind0, Q0MAX, k) * nq1 + j)];
+        e[k] = fk + fr;
+        o[k] = fk - fr;
+      }
 #pragma unroll
-        for (int ip = 0; ip < Q0MAX; ++ip)
-          if (ip < nq0) acc += kk.K0[i * MAXQ + ip] * col[ip];
-        Lr[2 * (i * nq1 + j)] = w * acc;
+      for (int i = 0; i < H; ++i) {
+        real pe = 0, mo = 0;
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          pe += kk.split.P0[i * KArgs<real>::HQ + k] * e[k];
+          mo += kk.split.M0[i * KArgs<real>::HQ + k] * o[k];
+        }
+        Lr[2 * (i * nq1 + j)] = w * (mo + pe);
+        Lr[2 * (refl(m.kind0, Q0MAX, i) * nq1 + j)] = w * (mo - pe);
+      }
+    } else {
+      real col[Q0MAX];
+#pragma unroll
+      for (int ip = 0; ip < Q0MAX; ++ip) col[ip] = ip < nq0 ? F[2 * (ip * nq1 + j)] : real(0);
+#pragma unroll
+      for (int i = 0; i < Q0MAX; ++i) {
+        if (i < nq0) {
+          real acc = 0;
+#pragma unroll
+          for (int ip = 0; ip < Q0MAX; ++ip)
+            if (ip < nq0) acc += kk.full.K0[i * MAXQ + ip] * col[ip];
+          Lr[2 * (i * nq1 + j)] = w * acc;
+        }
       }
     }
-  }
-  __syncthreads();
-
-  // ==== phase B: the K~^phi part of the force (adds to the K^R part), and the walls
-  for (int x = tid; x < TCe * 2 * nq0; x += NT) {
+  };
+  // lbuf += p^R K~^phi f (one task per (cell, field, i): a row of nq1 values)
+  auto force_phi = [&](int x) {
     const int i = x % nq0, td2 = x / nq0, d = td2 & 1, t = td2 >> 1;
     const real* F = tile + (t + 3) * row + d + 2 * i * nq1;
-    real rw[Q1MAX];
-#pragma unroll
-    for (int jp = 0; jp < Q1MAX; ++jp) rw[jp] = jp < nq1 ? F[2 * jp] : real(0);
     real* Lr = lbuf + t * row + d + 2 * i * nq1;
     const real pr = p0r[i];
+    if constexpr (EXACT) {  // even and odd parts under the reflection of axis 1 (KArgs)
+      constexpr int H = Q1MAX / 2;
+      real e[H], o[H];
 #pragma unroll
-    for (int j = 0; j < Q1MAX; ++j) {
-      if (j < nq1) {
-        real acc = 0;
+      for (int k = 0; k < H; ++k) {
+        const real fk = F[2 * k], fr = F[2 * refl(m.kind1, Q1MAX, k)];
+        e[k] = fk + fr;
+        o[k] = fk - fr;
+      }
 #pragma unroll
-        for (int jp = 0; jp < Q1MAX; ++jp)
-          if (jp < nq1) acc += kk.Kt1[j * MAXQ + jp] * rw[jp];
-        Lr[2 * j] += pr * acc;
+      for (int j = 0; j < H; ++j) {
+        real pe = 0, mo = 0;
+#pragma unroll
+        for (int k = 0; k < H; ++k) {
+          pe += kk.split.P1[j * KArgs<real>::HQ + k] * e[k];
+          mo += kk.split.M1[j * KArgs<real>::HQ + k] * o[k];
+        }
+        Lr[2 * j] += pr * (pe + mo);
+        Lr[2 * refl(m.kind1, Q1MAX, j)] += pr * (pe - mo);
+      }
+    } else {
+      real rw[Q1MAX];
+#pragma unroll
+      for (int jp = 0; jp < Q1MAX; ++jp) rw[jp] = jp < nq1 ? F[2 * jp] : real(0);
+#pragma unroll
+      for (int j = 0; j < Q1MAX; ++j) {
+        if (j < nq1) {
+          real acc = 0;
+#pragma unroll
+          for (int jp = 0; jp < Q1MAX; ++jp)
+            if (jp < nq1) acc += kk.full.Kt1[j * MAXQ + jp] * rw[jp];
+          Lr[2 * j] += pr * acc;
+        }
       }
     }
-  }
+  };
+  // Both contractions read only the owned cells, which phase A does not change.  When
+  // some warps have no cell and the tasks come to at most six per idle thread, those
+  // warps run all of them during phase A (the K~^phi tasks after a barrier among those
+  // warps only); otherwise every thread takes K^R tasks after phase A and K~^phi tasks
+  // after a CTA barrier.
+  const int nR = TCe * 2 * nq1, nP = TCe * 2 * nq0;
+  const int nfree = NA < NW ? NT - 32 * NA : 0;
+  const bool early = nR + nP <= 6 * nfree;  // uniform across the CTA
+  const bool runs = !early || warp >= NA;
+  const int f0 = early ? tid - 32 * NA : tid, fs = early ? nfree : NT;
+  if (runs)
+    for (int x = f0; x < nR; x += fs) force_R(x);
+  if (!early) __syncthreads();
+  else if (runs) asm volatile("bar.sync 1, %0;" ::"r"(nfree) : "memory");
+  if (runs)
+    for (int x = f0; x < nP; x += fs) force_phi(x);
+  __syncthreads();
+
+  // ==== phase B: the walls
   for (int wall = 0; wall < 2; ++wall) {
     // every tile whose stencils reach a ghost cell fills the ghosts itself
     const bool active = wall == 0 ? (c0 < 3) : (c0 + TCe + 3 > n);
