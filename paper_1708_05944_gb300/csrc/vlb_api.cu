@@ -114,17 +114,29 @@ void fill_force_tables(KArgs<real>& k, const std::vector<double>& K0, const std:
     return;
   }
   constexpr int HQ = KArgs<real>::HQ;
+  // single precision: every coefficient duplicated (KArgs::SplitPairs)
+  const bool paired = sizeof(real) == 4;
   for (int i = 0; i < nq0 / 2; ++i)
     for (int c = 0; c < nq0 / 2; ++c) {
       const double a = K0[i * nq0 + c], b = K0[i * nq0 + refl(kind0, nq0, c)];
-      k.split.P0[i * HQ + c] = real(0.5 * (a + b));
-      k.split.M0[i * HQ + c] = real(0.5 * (a - b));
+      if (paired) {
+        k.pairs.P0[i * HQ + c].x = k.pairs.P0[i * HQ + c].y = real(0.5 * (a + b));
+        k.pairs.M0[i * HQ + c].x = k.pairs.M0[i * HQ + c].y = real(0.5 * (a - b));
+      } else {
+        k.split.P0[i * HQ + c] = real(0.5 * (a + b));
+        k.split.M0[i * HQ + c] = real(0.5 * (a - b));
+      }
     }
   for (int j = 0; j < nq1 / 2; ++j)
     for (int c = 0; c < nq1 / 2; ++c) {
       const double a = Kt1[j * nq1 + c], b = Kt1[j * nq1 + refl(kind1, nq1, c)];
-      k.split.P1[j * HQ + c] = real(0.5 * (a + b));
-      k.split.M1[j * HQ + c] = real(0.5 * (a - b));
+      if (paired) {
+        k.pairs.P1[j * HQ + c].x = k.pairs.P1[j * HQ + c].y = real(0.5 * (a + b));
+        k.pairs.M1[j * HQ + c].x = k.pairs.M1[j * HQ + c].y = real(0.5 * (a - b));
+      } else {
+        k.split.P1[j * HQ + c] = real(0.5 * (a + b));
+        k.split.M1[j * HQ + c] = real(0.5 * (a - b));
+      }
     }
 }
 

@@ -37,6 +37,20 @@ struct TileDesc {
   int nc;  // cells owned (1 .. the kernel's TC)
 };
 
+// (f', f'') pair of one velocity in the bulk type (see the pair operations below).
+template <typename real>
+struct PairOf;
+template <>
+struct PairOf<float> {
+  using type = float2;
+};
+template <>
+struct PairOf<double> {
+  using type = double2;
+};
+template <typename real>
+using pair_t = typename PairOf<real>::type;
+
 // Per-cell chi-formulation factors (Eqs. flux_kom_R, flux_kom_eta):
 //   advection = p^R (cp * Flux_{s+1/2} - cm * Flux_{s-1/2}),
 //   cp = 2 R_{s+1/2} / (R_{s+1/2}^2 - R_{s-1/2}^2), cm = 2 R_{s-1/2} / (...),
@@ -76,7 +90,8 @@ struct ModelArgs {
 
 // Momentum-space kernels of the inertial force (Eq. boltz_couette_kom): K0 =
 // d/dp^0 on axis 0 and Kt1 = d/dp^1 (p^1 .) on axis 1.  The generic kernels read
-// the full matrices.  The fixed-shape kernels use that each commutes with the
+// the full matrices; the fixed-shape kernels read the split blocks below (as
+// duplicated pairs in single precision).  The split uses that each commutes with the
 // reflection of its axis, up to sign: with J the node permutation p_k -> -p_k
 // (see refl), K0 J = -J K0 and Kt1 J = J Kt1.  Each then splits into two
 // half-size blocks acting on the even and odd parts e_k = f_k + f_Jk,
@@ -95,9 +110,14 @@ struct KArgs {
     real P0[HQ * HQ], M0[HQ * HQ];  // [i][k] stride HQ
     real P1[HQ * HQ], M1[HQ * HQ];  // [j][k] stride HQ
   };
+  struct SplitPairs {  // the same blocks with every coefficient duplicated, for packed
+    pair_t<real> P0[HQ * HQ], M0[HQ * HQ];  // contraction of both fields of a velocity
+    pair_t<real> P1[HQ * HQ], M1[HQ * HQ];
+  };
   union {
     Full full;
     Split split;
+    SplitPairs pairs;
   };
 };
 
@@ -190,18 +210,6 @@ __device__ __forceinline__ real weno5(real a, real b, real c, real d, real e, re
 // precision as two scalar operations.  p_add and p_mul are never contracted
 // into an fma (the packed intrinsics round per lane like __fadd_rn and
 // __fmul_rn), so an expression of them rounds the same wherever it is inlined.
-template <typename real>
-struct PairOf;
-template <>
-struct PairOf<float> {
-  using type = float2;
-};
-template <>
-struct PairOf<double> {
-  using type = double2;
-};
-template <typename real>
-using pair_t = typename PairOf<real>::type;
 
 __device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
@@ -219,6 +227,18 @@ __device__ __forceinline__ double2 p_fma(double2 a, double2 b, double2 c) {
 }
 __device__ __forceinline__ double2 p_set(double s) { return make_double2(s, s); }
 __device__ __forceinline__ double2 p_make(double x, double y) { return make_double2(x, y); }
+
+// a - b on the pair (packed FP32x2 subtract; rounded, never contracted)
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(r)
+      : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+  return *reinterpret_cast<float2*>(&r);
+}
+__device__ __forceinline__ double2 p_sub(double2 a, double2 b) {
+  return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y));
+}
 
 template <typename real>
 __device__ __forceinline__ pair_t<real> p_load(const real* p) {

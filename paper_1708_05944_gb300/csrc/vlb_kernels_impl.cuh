@@ -47,7 +47,8 @@ template <typename real>
 struct VariantTable;
 template <>
 struct VariantTable<float> {
-  static constexpr StageVariant v16x20[] = {{4, 256, 0}, {8, 256, 0}, {4, 320, 0}, {8, 320, 0}, {16, 320, 0}};
+  static constexpr StageVariant v16x20[] = {{4, 256, 0},  {8, 256, 0},  {4, 320, 0},
+                                            {8, 320, 0},  {16, 320, 0}, {10, 320, 0}};
   static constexpr StageVariant v16x12[] = {{16, 256, 0}, {8, 256, 0}, {16, 384, 0}};
   static constexpr StageVariant v8x4[] = {{16, 64, 0}, {8, 64, 0}};
   static constexpr StageVariant vsmall[] = {{16, 64, 0}};
@@ -91,7 +92,7 @@ size_t stage_smem_bytes(StageVariant v, int Vp) {
   VLB_SMEM_CASE(16, 256) VLB_SMEM_CASE(8, 256) VLB_SMEM_CASE(16, 512) VLB_SMEM_CASE(8, 128)
   VLB_SMEM_CASE(16, 384) VLB_SMEM_CASE(16, 64) VLB_SMEM_CASE(8, 64) VLB_SMEM_CASE(4, 256)
   VLB_SMEM_CASE(4, 128) VLB_SMEM_CASE(8, 384) VLB_SMEM_CASE(4, 320) VLB_SMEM_CASE(8, 320)
-  VLB_SMEM_CASE(16, 320)
+  VLB_SMEM_CASE(16, 320) VLB_SMEM_CASE(10, 320)
 #undef VLB_SMEM_CASE
   return 0;
 }
@@ -105,7 +106,7 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
   if constexpr (sizeof(real) == 4) {
     VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
     VLB_CASE(SH_16x20, 4, 320, 16, 20, true) VLB_CASE(SH_16x20, 8, 320, 16, 20, true)
-    VLB_CASE(SH_16x20, 16, 320, 16, 20, true)
+    VLB_CASE(SH_16x20, 16, 320, 16, 20, true) VLB_CASE(SH_16x20, 10, 320, 16, 20, true)
     VLB_CASE(SH_16x12, 16, 256, 16, 12, true) VLB_CASE(SH_16x12, 8, 256, 16, 12, true)
     VLB_CASE(SH_16x12, 16, 384, 16, 12, true)
     VLB_CASE(SH_8x4, 16, 64, 8, 4, true) VLB_CASE(SH_8x4, 8, 64, 8, 4, true)
@@ -145,7 +146,7 @@ int stage_slots(StageVariant v, const ModelArgs& m, int Vp) {
   if constexpr (sizeof(real) == 4) {
     VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
     VLB_CASE(SH_16x20, 4, 320, 16, 20, true) VLB_CASE(SH_16x20, 8, 320, 16, 20, true)
-    VLB_CASE(SH_16x20, 16, 320, 16, 20, true)
+    VLB_CASE(SH_16x20, 16, 320, 16, 20, true) VLB_CASE(SH_16x20, 10, 320, 16, 20, true)
     VLB_CASE(SH_16x12, 16, 256, 16, 12, true) VLB_CASE(SH_16x12, 8, 256, 16, 12, true)
     VLB_CASE(SH_16x12, 16, 384, 16, 12, true)
     VLB_CASE(SH_8x4, 16, 64, 8, 4, true) VLB_CASE(SH_8x4, 8, 64, 8, 4, true)

@@ -53,9 +53,10 @@ struct StageSmem {
   // doubles: p0, p1 (MAXQ each), reduction (NW*4), wall equilibrium factors (2*MAXQ), scalars (16)
   static constexpr size_t n_dbl = 2 * MAXQ + NW * 4 + 2 * MAXQ + 16;
   __host__ __device__ static size_t real_off(int Vp) { return dbl_off(Vp) + n_dbl * sizeof(double); }
-  // reals: p0, p1, 1/w0, 1/w1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each), n g_R and g_phi (TC*MAXQ each),
-  // cell T, 1/tau, cp, cm, 1/Rbar (TC each), moment vectors (TC*4*MAXN), w0, w1 (MAXQ each)
-  static constexpr size_t n_real = 4 * MAXQ + 2 * MAXQ * MAXN + 2 * TC * MAXQ + 5 * TC + TC * 4 * MAXN + 2 * MAXQ;
+  // reals: p0, p1, 1/w0, 1/w1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each), then pairs: n g_R and g_phi
+  // (TC*MAXQ each), (1, T), -1/tau, cp, -cm, 1/Rbar (TC each); then moment vectors (TC*4*MAXN),
+  // w0, w1 (MAXQ each)
+  static constexpr size_t n_real = 4 * MAXQ + 2 * MAXQ * MAXN + 4 * TC * MAXQ + 10 * TC + TC * 4 * MAXN + 2 * MAXQ;
   __host__ __device__ static size_t bytes(int Vp) { return real_off(Vp) + n_real * sizeof(real); }
 };
 
@@ -99,14 +100,16 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
   real* iw1 = iw0 + MAXQ;  // 1 / w_j
   real* tabr0 = iw1 + MAXQ;  // equilibrium tables in the bulk type
   real* tabr1 = tabr0 + MAXQ * MAXN;
-  real* gRn = tabr1 + MAXQ * MAXN;  // [t][i] n_t g_{R,i}
-  real* gP = gRn + TC * MAXQ;       // [t][j] g_{phi,j}
-  real* cTr = gP + TC * MAXQ;
-  real* cItau = cTr + TC;
-  real* ccp = cItau + TC;
-  real* ccm = ccp + TC;
-  real* cIR = ccm + TC;
-  real* mv = cIR + TC;  // [t][axis*2 + side][s]
+  // per-cell values of phase D as ready pairs (both lanes of a packed operand)
+  using P2 = pair_t<real>;
+  P2* gRn = reinterpret_cast<P2*>(tabr1 + MAXQ * MAXN);  // [t][i] n_t g_{R,i} twice
+  P2* gP = gRn + TC * MAXQ;                              // [t][j] g_{phi,j} twice
+  P2* cT1 = gP + TC * MAXQ;                              // (1, T)
+  P2* cNtau = cT1 + TC;                                  // -1/tau twice
+  P2* ccp = cNtau + TC;                                  // cp twice
+  P2* cNcm = ccp + TC;                                   // -cm twice
+  P2* cIR = cNcm + TC;                                   // 1/Rbar twice
+  real* mv = reinterpret_cast<real*>(cIR + TC);          // [t][axis*2 + side][s]
   real* w0r = mv + TC * 4 * MAXN;  // weights: R_ij = w0_i w1_j in the bulk type
   real* w1r = w0r + MAXQ;
 
@@ -161,14 +164,14 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
   for (int t = tid; t < TCe; t += NT) {
     if constexpr (F32) {
       const GeoCellF g = a.geof[in.cell0 + c0 + t];
-      ccp[t] = g.cp;
-      ccm[t] = g.cm;
-      cIR[t] = g.inv_rbar;
+      ccp[t] = p_set(g.cp);
+      cNcm[t] = p_set(-g.cm);
+      cIR[t] = p_set(g.inv_rbar);
     } else {
       const GeoCell g = a.geo[in.cell0 + c0 + t];
-      ccp[t] = g.cp;
-      ccm[t] = g.cm;
-      cIR[t] = g.inv_rbar;
+      ccp[t] = p_set(g.cp);
+      cNcm[t] = p_set(-g.cm);
+      cIR[t] = p_set(g.inv_rbar);
     }
   }
   bool ok = mbar_wait(bar, parity, a.max_polls);
@@ -229,8 +232,8 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
       T = (real(de + m.ref_e) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
     }
     if (hl == 0 && has) {
-      cTr[t] = T;
-      cItau[t] = real(1) / relaxation_time<real>(in.tau_mode, F32 ? real(in.kn_f) : real(in.kn), nn, T);
+      cT1[t] = p_make(real(1), T);
+      cNtau[t] = p_set(-(real(1) / relaxation_time<real>(in.tau_mode, F32 ? real(in.kn_f) : real(in.kn), nn, T)));
     }
     real* mt = mv + t * 4 * MAXN;  // moment vectors [axis * 2 + side][s]
     if (hl < 4 && has) {
@@ -281,92 +284,159 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const int k = hl + 16 * q;
-        if (16 * q < Q0MAX && k < nq0) gRn[t * MAXQ + k] = F32 ? real(fmaf(-float(gr[q]), delta, float(gr[q])))
-                                                                 : gr[q] * scale0;
-        if (16 * q < Q1MAX && k < nq1) gP[t * MAXQ + k] = gp[q];
+        if (16 * q < Q0MAX && k < nq0)
+          gRn[t * MAXQ + k] = p_set(F32 ? real(fmaf(-float(gr[q]), delta, float(gr[q]))) : gr[q] * scale0);
+        if (16 * q < Q1MAX && k < nq1) gP[t * MAXQ + k] = p_set(gp[q]);
       }
     }
   }
-  // lbuf = -(p^phi)^2 K^R f (one task per (cell, field, j): a column of nq0 values)
+  // Single-precision fixed-shape kernels contract both fields of a velocity in one task
+  // (packed FP32x2 against duplicated coefficients); the others one field per task.
+  constexpr bool PAIRED = F32 && EXACT;
+  constexpr int TPF = PAIRED ? 1 : 2;  // tasks per (cell, column) and per (cell, row)
+  constexpr int HQ = KArgs<real>::HQ;
+  // lbuf = -(p^phi)^2 K^R f (one task per (cell, [field,] j): a column of nq0 values)
   auto force_R = [&](int x) {
-    const int j = x % nq1, td2 = x / nq1, d = td2 & 1, t = td2 >> 1;
-    const real* F = tile + (t + 3) * row + d;
-    real* Lr = lbuf + t * row + d;
-    const real w = -p1r[j] * p1r[j];
-    if constexpr (EXACT) {  // even and odd parts under the reflection of axis 0 (KArgs)
+    if constexpr (PAIRED) {  // even and odd parts under the reflection of axis 0 (KArgs)
       constexpr int H = Q0MAX / 2;
-      real e[H], o[H];
+      const int j = x % Q1MAX, t = x / Q1MAX;
+      const real* F = tile + (t + 3) * row;
+      real* Lr = lbuf + t * row;
+      // node k of the first half and its mirror refl(k) = k + H (half range) or Q - 1 - k
+      // (full range): the mirror's pair sits at r0 + k rs
+      const int rs = m.kind0 == 1 ? 2 * Q1MAX : -2 * Q1MAX;
+      const int r0 = 2 * refl(m.kind0, Q0MAX, 0) * Q1MAX + 2 * j;
+      pair_t<real> e[H], o[H];
 #pragma unroll
       for (int k = 0; k < H; ++k) {
-        const real fk = F[2 * (k * nq1 + j)], fr = F[2 * (refl(m.kind0, Q0MAX, k) * nq1 + j)];
-        e[k] = fk + fr;
-        o[k] = fk - fr;
+        const pair_t<real> fk = p_load(F + 2 * j + 2 * k * Q1MAX), fr = p_load(F + r0 + k * rs);
+        e[k] = p_add(fk, fr);
+        o[k] = p_sub(fk, fr);
       }
+      const pair_t<real> w = p_set(-p1r[j] * p1r[j]);
 #pragma unroll
       for (int i = 0; i < H; ++i) {
-        real pe = 0, mo = 0;
+        pair_t<real> pe = p_set(real(0)), mo = p_set(real(0));
 #pragma unroll
         for (int k = 0; k < H; ++k) {
-          pe += kk.split.P0[i * KArgs<real>::HQ + k] * e[k];
-          mo += kk.split.M0[i * KArgs<real>::HQ + k] * o[k];
+          pe = p_fma(kk.pairs.P0[i * HQ + k], e[k], pe);
+          mo = p_fma(kk.pairs.M0[i * HQ + k], o[k], mo);
         }
-        Lr[2 * (i * nq1 + j)] = w * (mo + pe);
-        Lr[2 * (refl(m.kind0, Q0MAX, i) * nq1 + j)] = w * (mo - pe);
+        p_store(Lr + 2 * j + 2 * i * Q1MAX, p_mul(w, p_add(mo, pe)));
+        p_store(Lr + r0 + i * rs, p_mul(w, p_sub(mo, pe)));
       }
     } else {
-      real col[Q0MAX];
+      const int j = x % nq1, td2 = x / nq1, d = td2 & 1, t = td2 >> 1;
+      const real* F = tile + (t + 3) * row + d;
+      real* Lr = lbuf + t * row + d;
+      const real w = -p1r[j] * p1r[j];
+      if constexpr (EXACT) {  // as above, one field
+        constexpr int H = Q0MAX / 2;
+        const int rs = m.kind0 == 1 ? 2 * Q1MAX : -2 * Q1MAX;
+        const int r0 = 2 * refl(m.kind0, Q0MAX, 0) * Q1MAX + 2 * j;
+        real e[H], o[H];
 #pragma unroll
-      for (int ip = 0; ip < Q0MAX; ++ip) col[ip] = ip < nq0 ? F[2 * (ip * nq1 + j)] : real(0);
+        for (int k = 0; k < H; ++k) {
+          const real fk = F[2 * j + 2 * k * Q1MAX], fr = F[r0 + k * rs];
+          e[k] = fk + fr;
+          o[k] = fk - fr;
+        }
 #pragma unroll
-      for (int i = 0; i < Q0MAX; ++i) {
-        if (i < nq0) {
-          real acc = 0;
+        for (int i = 0; i < H; ++i) {
+          real pe = 0, mo = 0;
 #pragma unroll
-          for (int ip = 0; ip < Q0MAX; ++ip)
-            if (ip < nq0) acc += kk.full.K0[i * MAXQ + ip] * col[ip];
-          Lr[2 * (i * nq1 + j)] = w * acc;
+          for (int k = 0; k < H; ++k) {
+            pe += kk.split.P0[i * HQ + k] * e[k];
+            mo += kk.split.M0[i * HQ + k] * o[k];
+          }
+          Lr[2 * j + 2 * i * Q1MAX] = w * (mo + pe);
+          Lr[r0 + i * rs] = w * (mo - pe);
+        }
+      } else {
+        real col[Q0MAX];
+#pragma unroll
+        for (int ip = 0; ip < Q0MAX; ++ip) col[ip] = ip < nq0 ? F[2 * (ip * nq1 + j)] : real(0);
+#pragma unroll
+        for (int i = 0; i < Q0MAX; ++i) {
+          if (i < nq0) {
+            real acc = 0;
+#pragma unroll
+            for (int ip = 0; ip < Q0MAX; ++ip)
+              if (ip < nq0) acc += kk.full.K0[i * MAXQ + ip] * col[ip];
+            Lr[2 * (i * nq1 + j)] = w * acc;
+          }
         }
       }
     }
   };
-  // lbuf += p^R K~^phi f (one task per (cell, field, i): a row of nq1 values)
+  // lbuf += p^R K~^phi f (one task per (cell, [field,] i): a row of nq1 values)
   auto force_phi = [&](int x) {
-    const int i = x % nq0, td2 = x / nq0, d = td2 & 1, t = td2 >> 1;
-    const real* F = tile + (t + 3) * row + d + 2 * i * nq1;
-    real* Lr = lbuf + t * row + d + 2 * i * nq1;
-    const real pr = p0r[i];
-    if constexpr (EXACT) {  // even and odd parts under the reflection of axis 1 (KArgs)
+    if constexpr (PAIRED) {  // even and odd parts under the reflection of axis 1 (KArgs)
       constexpr int H = Q1MAX / 2;
-      real e[H], o[H];
+      const int i = x % Q0MAX, t = x / Q0MAX;
+      const real* F = tile + (t + 3) * row + 2 * i * Q1MAX;
+      real* Lr = lbuf + t * row + 2 * i * Q1MAX;
+      const int rs = m.kind1 == 1 ? 2 : -2;  // the mirror of node k sits at r0 + k rs
+      const int r0 = 2 * refl(m.kind1, Q1MAX, 0);
+      pair_t<real> e[H], o[H];
 #pragma unroll
       for (int k = 0; k < H; ++k) {
-        const real fk = F[2 * k], fr = F[2 * refl(m.kind1, Q1MAX, k)];
-        e[k] = fk + fr;
-        o[k] = fk - fr;
+        const pair_t<real> fk = p_load(F + 2 * k), fr = p_load(F + r0 + k * rs);
+        e[k] = p_add(fk, fr);
+        o[k] = p_sub(fk, fr);
       }
+      const pair_t<real> pr = p_set(p0r[i]);
 #pragma unroll
       for (int j = 0; j < H; ++j) {
-        real pe = 0, mo = 0;
+        pair_t<real> pe = p_set(real(0)), mo = p_set(real(0));
 #pragma unroll
         for (int k = 0; k < H; ++k) {
-          pe += kk.split.P1[j * KArgs<real>::HQ + k] * e[k];
-          mo += kk.split.M1[j * KArgs<real>::HQ + k] * o[k];
+          pe = p_fma(kk.pairs.P1[j * HQ + k], e[k], pe);
+          mo = p_fma(kk.pairs.M1[j * HQ + k], o[k], mo);
         }
-        Lr[2 * j] += pr * (pe + mo);
-        Lr[2 * refl(m.kind1, Q1MAX, j)] += pr * (pe - mo);
+        p_store(Lr + 2 * j, p_fma(pr, p_add(pe, mo), p_load(Lr + 2 * j)));
+        p_store(Lr + r0 + j * rs, p_fma(pr, p_sub(pe, mo), p_load(Lr + r0 + j * rs)));
       }
     } else {
-      real rw[Q1MAX];
+      const int i = x % nq0, td2 = x / nq0, d = td2 & 1, t = td2 >> 1;
+      const real* F = tile + (t + 3) * row + d + 2 * i * nq1;
+      real* Lr = lbuf + t * row + d + 2 * i * nq1;
+      const real pr = p0r[i];
+      if constexpr (EXACT) {  // as above, one field
+        constexpr int H = Q1MAX / 2;
+        const int rs = m.kind1 == 1 ? 2 : -2;
+        const int r0 = 2 * refl(m.kind1, Q1MAX, 0);
+        real e[H], o[H];
 #pragma unroll
-      for (int jp = 0; jp < Q1MAX; ++jp) rw[jp] = jp < nq1 ? F[2 * jp] : real(0);
+        for (int k = 0; k < H; ++k) {
+          const real fk = F[2 * k], fr = F[r0 + k * rs];
+          e[k] = fk + fr;
+          o[k] = fk - fr;
+        }
 #pragma unroll
-      for (int j = 0; j < Q1MAX; ++j) {
-        if (j < nq1) {
-          real acc = 0;
+        for (int j = 0; j < H; ++j) {
+          real pe = 0, mo = 0;
 #pragma unroll
-          for (int jp = 0; jp < Q1MAX; ++jp)
-            if (jp < nq1) acc += kk.full.Kt1[j * MAXQ + jp] * rw[jp];
-          Lr[2 * j] += pr * acc;
+          for (int k = 0; k < H; ++k) {
+            pe += kk.split.P1[j * HQ + k] * e[k];
+            mo += kk.split.M1[j * HQ + k] * o[k];
+          }
+          Lr[2 * j] += pr * (pe + mo);
+          Lr[r0 + j * rs] += pr * (pe - mo);
+        }
+      } else {
+        real rw[Q1MAX];
+#pragma unroll
+        for (int jp = 0; jp < Q1MAX; ++jp) rw[jp] = jp < nq1 ? F[2 * jp] : real(0);
+#pragma unroll
+        for (int j = 0; j < Q1MAX; ++j) {
+          if (j < nq1) {
+            real acc = 0;
+#pragma unroll
+            for (int jp = 0; jp < Q1MAX; ++jp)
+              if (jp < nq1) acc += kk.full.Kt1[j * MAXQ + jp] * rw[jp];
+            Lr[2 * j] += pr * acc;
+          }
         }
       }
     }
@@ -376,7 +446,7 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
   // warps run all of them during phase A (the K~^phi tasks after a barrier among those
   // warps only); otherwise every thread takes K^R tasks after phase A and K~^phi tasks
   // after a CTA barrier.
-  const int nR = TCe * 2 * nq1, nP = TCe * 2 * nq0;
+  const int nR = TCe * TPF * nq1, nP = TCe * TPF * nq0;
   const int nfree = NA < NW ? NT - 32 * NA : 0;
   const bool early = nR + nP <= 6 * nfree;  // uniform across the CTA
   const bool runs = !early || warp >= NA;
@@ -466,7 +536,8 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
     const real pr = p0r[i];
     const bool up = pr >= real(0);
     const real sc = iw0[i] * iw1[j];
-    const real rij = w0r[i] * w1r[j];
+    const P nrij = p_set(-(w0r[i] * w1r[j]));
+    const P npr = p_set(-pr);
     real* S = tile + 2 * v;
     const real* Fl = a.Fl + size_t(in.cell0 + c0) * row + 2 * v;  // F_l of the owned cells, read once
     P w0 = p_load(S), w1 = p_load(S + row), w2 = p_load(S + 2 * row), w3 = p_load(S + 3 * row);
@@ -480,15 +551,13 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
         const P w6 = p_load(S + (t + 6) * row);
         const P fp = weno5p<real>(p_sel(up, w1, w6), p_sel(up, w2, w5), p_sel(up, w3, w4), p_sel(up, w4, w3),
                                   p_sel(up, w5, w2), sc);
-        // -adv = -p^R (cp F_{s+1/2} - cm F_{s-1/2})
-        // per-cell factors: shared-memory broadcasts
-        const P nadv = p_mul(p_fma(fp, p_set(ccp[t]), p_mul(fm, p_set(-ccm[t]))), p_set(-pr));
+        // -adv = -p^R (cp F_{s+1/2} - cm F_{s-1/2}); per-cell factors: shared-memory broadcasts
+        const P nadv = p_mul(p_fma(fp, ccp[t], p_mul(fm, cNcm[t])), npr);
         // f_eq - R for both fields: (g, T g) - R
-        const real g = gRn[t * MAXQ + i] * gP[t * MAXQ + j];
-        const P deq = p_fma(p_set(g), p_make(real(1), cTr[t]), p_set(-rij));
+        const P deq = p_fma(p_mul(gRn[t * MAXQ + i], gP[t * MAXQ + j]), cT1[t], nrij);
         const P force = p_load(lbuf + t * row + 2 * v);
         // L = -adv + force / Rbar - (D - D_eq) / tau
-        const P Lv = p_fma(p_fma(deq, p_set(real(-1)), w3), p_set(-cItau[t]), p_fma(force, p_set(cIR[t]), nadv));
+        const P Lv = p_fma(p_sub(w3, deq), cNtau[t], p_fma(force, cIR[t], nadv));
         P o = p_fma(Lv, p_set(cc), w3);
         if (need_fl) o = p_fma(p_fma(w3, p_set(real(-1)), p_load(Fl + t * row)), p_set(ca), o);
         p_store(S + (t + 3) * row, o);  // in place: this column's slot t+3 is not read again
