@@ -145,13 +145,17 @@ void fill_force_tables(KArgs<real>& k, const std::vector<double>& K0, const std:
 // the tile list in rounds of `slots` CTAs, so the tile size s <= TC is chosen to
 // minimise rounds x (s + 3): the makespan in cell-times with the three halo
 // cells as the fixed cost of a tile (for 5 x 1024 cells on 456 CTAs: 6-cell
-// tiles in two rounds instead of 8-cell tiles in two).
+// tiles in two rounds instead of 8-cell tiles in two).  CTA b takes the tiles
+// b, b + slots, ...; when the last round is not full, the tiles that reach a
+// wall (and so also fill its ghost cells, several times the work of an interior
+// tile's phase in between) are placed in the first round of the CTAs that have
+// no tile in the last round.
 void build_tiles(vlb_ctx* c) {
   const StageVariant& v = c->variants[c->variant];
   int s = v.tc;
+  int slots = 0;
   if (v.persist) {
-    const int slots = c->prec == VLB_FP64 ? stage_slots<double>(v, c->margs, c->Vp)
-                                          : stage_slots<float>(v, c->margs, c->Vp);
+    slots = c->prec == VLB_FP64 ? stage_slots<double>(v, c->margs, c->Vp) : stage_slots<float>(v, c->margs, c->Vp);
     if (slots > 0) {
       long long best = -1;
       for (int cand = v.tc; cand >= std::max(3, (v.tc + 1) / 2); --cand) {
@@ -166,6 +170,21 @@ void build_tiles(vlb_ctx* c) {
   for (int i = 0; i < c->n_inst; ++i)
     for (int c0 = 0; c0 < c->inst[i].n_cells; c0 += s)
       c->tiles.push_back(TileDesc{i, c0, std::min(s, c->inst[i].n_cells - c0)});
+  const int T = int(c->tiles.size());
+  if (slots <= 0 || T <= slots || T % slots == 0) return;
+  const int full = T - (T - 1) / slots * slots;  // CTAs 0 .. full-1 take a tile in the last round
+  std::vector<TileDesc> wall, rest;
+  for (const TileDesc& t : c->tiles) {
+    const int n = c->inst[t.inst].n_cells;
+    (t.c0 < 3 || t.c0 + t.nc + 3 > n ? wall : rest).push_back(t);
+  }
+  std::vector<TileDesc> out(T);
+  std::vector<char> used(T, 0);
+  size_t w = 0, r = 0;
+  for (int b = full; b < slots && w < wall.size(); ++b) out[b] = wall[w++], used[b] = 1;
+  for (int p = 0; p < T; ++p)
+    if (!used[p]) out[p] = w < wall.size() ? wall[w++] : rest[r++];
+  c->tiles.swap(out);
 }
 
 template <typename real>

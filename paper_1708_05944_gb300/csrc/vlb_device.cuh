@@ -260,6 +260,8 @@ __device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b)
 __device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // weno5 on a pair of fields: the candidate reconstructions, the indicators
 // (times 4, which the normalisation removes) and the weights run on the pair;
@@ -267,12 +269,25 @@ __device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a,
 // field.  The weighted sum is normalised once at the end.  The weights are
 // products and sums of p_mul / p_add, so a cell gets the same bits at every
 // position of an unrolled walk and the result does not depend on the tile shape.
+// The reconstruction of both fields from their indicators and candidates, as the
+// fast path of weno5p computes it, with the Table IV weights of weno5_weights_slow
+// for each field whose fast-path denominator den is out of range (fast holds the
+// fast-path result, kept for the other field).
 template <typename real>
-__device__ __forceinline__ void weno5_pair_slow(real s1, real s2, real s3, real& w1, real& w2, real& w3, real& den) {
-  real w[3];
-  weno5_weights_slow<real>(s1, s2, s3, w);
-  w1 = w[0], w2 = w[1], w3 = w[2];
-  den = radd(radd(w1, w2), w3);
+__device__ __noinline__ pair_t<real> weno5p_slow(pair_t<real> s1, pair_t<real> s2, pair_t<real> s3, pair_t<real> F1,
+                                                 pair_t<real> F2, pair_t<real> F3, pair_t<real> den,
+                                                 pair_t<real> fast) {
+  real r[2] = {fast.x, fast.y};
+  const real S1[2] = {s1.x, s1.y}, S2[2] = {s2.x, s2.y}, S3[2] = {s3.x, s3.y};
+  const real G1[2] = {F1.x, F1.y}, G2[2] = {F2.x, F2.y}, G3[2] = {F3.x, F3.y}, Dn[2] = {den.x, den.y};
+  for (int c = 0; c < 2; ++c) {
+    if (Dn[c] > real(1e-30) && Dn[c] < real(1e30)) continue;
+    real w[3];
+    weno5_weights_slow<real>(S1[c], S2[c], S3[c], w);
+    const real iden = vdiv(real(1), radd(radd(w[0], w[1]), w[2]));
+    r[c] = rmul(rfma(w[0], G1[c], rfma(w[1], G2[c], rmul(w[2], G3[c]))), iden);
+  }
+  return p_make(r[0], r[1]);
 }
 
 template <typename real>
@@ -301,14 +316,16 @@ __device__ __forceinline__ pair_t<real> weno5p(pair_t<real> a, pair_t<real> b, p
   P w1 = p_mul(p_set(real(0.1)), p_mul(q2, q3));
   P w2 = p_mul(p_set(real(0.6)), p_mul(q1, q3));
   P w3 = p_mul(p_set(real(0.3)), p_mul(q1, q2));
-  P den = p_add(p_add(w1, w2), w3);
+  const P den = p_add(p_add(w1, w2), w3);
+  const P iden = p_make(vdiv(real(1), den.x), vdiv(real(1), den.y));
+  const P res = p_mul(p_fma(w1, F1, p_fma(w2, F2, p_mul(w3, F3))), iden);
   // the fast path needs a normal-range denominator (the reciprocals are
   // single-precision fast divides); anything else -- vanishing or non-finite
-  // products, indicators out of range -- takes the slow path of Table IV
-  if (!(den.x > real(1e-30)) || !(den.x < real(1e30))) weno5_pair_slow<real>(s1.x, s2.x, s3.x, w1.x, w2.x, w3.x, den.x);
-  if (!(den.y > real(1e-30)) || !(den.y < real(1e30))) weno5_pair_slow<real>(s1.y, s2.y, s3.y, w1.y, w2.y, w3.y, den.y);
-  const P iden = p_make(vdiv(real(1), den.x), vdiv(real(1), den.y));
-  return p_mul(p_fma(w1, F1, p_fma(w2, F2, p_mul(w3, F3))), iden);
+  // products, indicators out of range -- takes the slow path of Table IV for
+  // that field: one test for both fields and one rarely taken branch
+  const bool ok = (den.x > real(1e-30)) & (den.x < real(1e30)) & (den.y > real(1e-30)) & (den.y < real(1e30));
+  if (__builtin_expect(!ok, 0)) return weno5p_slow<real>(s1, s2, s3, F1, F2, F3, den, res);
+  return res;
 }
 
 // ---------------------------------------------------------------- equilibrium
@@ -403,6 +420,13 @@ __device__ __forceinline__ void bulk_commit_and_wait_read() {
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
   asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
 }
+
+// The same in parts: commit the issued bulk stores as a group; wait until every
+// committed group of this thread has read its shared-memory source; wait until
+// every committed group has completed.
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Bounded wait for the phase with the given parity; false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity, unsigned long long max_polls) {

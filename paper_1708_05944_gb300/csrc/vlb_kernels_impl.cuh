@@ -12,23 +12,44 @@ namespace vlb {
 // per CTA NT.  Exact instantiations exist for the node counts of the
 // configured models; anything else takes the generic kernel.  The autotuner
 // (vlb_autotune) times the variants of a context's shape and keeps the best.
+// Tile buffers and resident CTAs per SM of a launch shape: one buffer for a launch
+// with one CTA per tile; a persistent launch takes two (staging its next tile while
+// it computes one) when that leaves as many CTAs resident as one buffer does.
+template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
+static cudaError_t stage_buffers(int Vp, int persist, int* nbuf, int* per_sm) {
+  using L = StageSmem<real, TC, NT>;
+  auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
+  const size_t limit = 227 * 1024;
+  const int top = persist && L::bytes(Vp, 2) <= limit ? 2 : 1;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::bytes(Vp, top)));
+  if (e != cudaSuccess) return e;
+  *nbuf = 1, *per_sm = 0;
+  for (int nb = 1; nb <= top; ++nb) {
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, L::bytes(Vp, nb))) != cudaSuccess) return e;
+    if (nb == 1 || (occ > 0 && occ >= *per_sm)) *nbuf = nb, *per_sm = occ;
+  }
+  return cudaSuccess;
+}
+
 template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
 static cudaError_t go_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int persist,
                             cudaStream_t s) {
   auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
-  const size_t smem = StageSmem<real, TC, NT>::bytes(a.Vp);
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  StageArgs<real> args = a;
+  int per_sm = 0;
+  cudaError_t e = stage_buffers<real, TC, NT, Q0, Q1, EXACT>(a.Vp, persist, &args.nbuf, &per_sm);
   if (e != cudaSuccess) return e;
+  const size_t smem = StageSmem<real, TC, NT>::bytes(a.Vp, args.nbuf);
   int grid = a.n_tiles;
   if (persist) {  // persistent: as many CTAs as fit on the device at once, each walking the tile list
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem)) != cudaSuccess) return e;
     const int cap = per_sm * sms;
     if (cap > 0 && cap < grid) grid = cap;
   }
-  kern<<<grid, NT, smem, s>>>(a, m, k);
+  kern<<<grid, NT, smem, s>>>(args, m, k);
   return cudaGetLastError();
 }
 
@@ -47,8 +68,8 @@ template <typename real>
 struct VariantTable;
 template <>
 struct VariantTable<float> {
-  static constexpr StageVariant v16x20[] = {{4, 256, 0},  {8, 256, 0},  {4, 320, 0},
-                                            {8, 320, 0},  {16, 320, 0}, {10, 320, 0}};
+  static constexpr StageVariant v16x20[] = {{4, 256, 0},  {8, 256, 0},  {4, 320, 0}, {8, 320, 0},
+                                            {16, 320, 0}, {10, 320, 0}, {9, 320, 0}};
   static constexpr StageVariant v16x12[] = {{16, 256, 0}, {8, 256, 0}, {16, 384, 0}};
   static constexpr StageVariant v8x4[] = {{16, 64, 0}, {8, 64, 0}};
   static constexpr StageVariant vsmall[] = {{16, 64, 0}};
@@ -88,11 +109,11 @@ bool stage_split_tables(int nq0, int nq1) {
 template <typename real>
 size_t stage_smem_bytes(StageVariant v, int Vp) {
 #define VLB_SMEM_CASE(TC_, NT_) \
-  if (v.tc == TC_ && v.nt == NT_) return StageSmem<real, TC_, NT_>::bytes(Vp);
+  if (v.tc == TC_ && v.nt == NT_) return StageSmem<real, TC_, NT_>::bytes(Vp, 1);
   VLB_SMEM_CASE(16, 256) VLB_SMEM_CASE(8, 256) VLB_SMEM_CASE(16, 512) VLB_SMEM_CASE(8, 128)
   VLB_SMEM_CASE(16, 384) VLB_SMEM_CASE(16, 64) VLB_SMEM_CASE(8, 64) VLB_SMEM_CASE(4, 256)
   VLB_SMEM_CASE(4, 128) VLB_SMEM_CASE(8, 384) VLB_SMEM_CASE(4, 320) VLB_SMEM_CASE(8, 320)
-  VLB_SMEM_CASE(16, 320) VLB_SMEM_CASE(10, 320)
+  VLB_SMEM_CASE(16, 320) VLB_SMEM_CASE(10, 320) VLB_SMEM_CASE(9, 320)
 #undef VLB_SMEM_CASE
   return 0;
 }
@@ -107,6 +128,7 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
     VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
     VLB_CASE(SH_16x20, 4, 320, 16, 20, true) VLB_CASE(SH_16x20, 8, 320, 16, 20, true)
     VLB_CASE(SH_16x20, 16, 320, 16, 20, true) VLB_CASE(SH_16x20, 10, 320, 16, 20, true)
+    VLB_CASE(SH_16x20, 9, 320, 16, 20, true)
     VLB_CASE(SH_16x12, 16, 256, 16, 12, true) VLB_CASE(SH_16x12, 8, 256, 16, 12, true)
     VLB_CASE(SH_16x12, 16, 384, 16, 12, true)
     VLB_CASE(SH_8x4, 16, 64, 8, 4, true) VLB_CASE(SH_8x4, 8, 64, 8, 4, true)
@@ -128,13 +150,10 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
 // CTAs of one launch shape that are resident on the device at once (occupancy x SMs)
 template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
 static int slots_of(int Vp) {
-  auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
-  const size_t smem = StageSmem<real, TC, NT>::bytes(Vp);
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) != cudaSuccess) return 0;
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0, nbuf = 1, per_sm = 0;
+  if (stage_buffers<real, TC, NT, Q0, Q1, EXACT>(Vp, 1, &nbuf, &per_sm) != cudaSuccess) return 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem) != cudaSuccess) return 0;
   return per_sm * sms;
 }
 
@@ -147,6 +166,7 @@ int stage_slots(StageVariant v, const ModelArgs& m, int Vp) {
     VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
     VLB_CASE(SH_16x20, 4, 320, 16, 20, true) VLB_CASE(SH_16x20, 8, 320, 16, 20, true)
     VLB_CASE(SH_16x20, 16, 320, 16, 20, true) VLB_CASE(SH_16x20, 10, 320, 16, 20, true)
+    VLB_CASE(SH_16x20, 9, 320, 16, 20, true)
     VLB_CASE(SH_16x12, 16, 256, 16, 12, true) VLB_CASE(SH_16x12, 8, 256, 16, 12, true)
     VLB_CASE(SH_16x12, 16, 384, 16, 12, true)
     VLB_CASE(SH_8x4, 16, 64, 8, 4, true) VLB_CASE(SH_8x4, 8, 64, 8, 4, true)

@@ -13,6 +13,8 @@
 // (ModelArgs): the operator is linear in R's part, which it leaves unchanged.
 // A cell row holds Vp velocity pairs (f', f'') interleaved (see pair_t).
 #pragma once
+#include <type_traits>
+
 #include "vlb_device.cuh"
 
 namespace vlb {
@@ -37,27 +39,33 @@ struct StageArgs {
   const WallEq* wall;  // 2 per instance: inner, outer wall equilibrium
   unsigned* err;
   int Vp;              // velocities per cell row, padded (>= nq0 nq1, multiple of 4); a row holds 2 Vp reals
+  int nbuf;            // tile buffers: 1, or 2 when a persistent CTA stages its next tile during this one
   unsigned long long max_polls;
 };
 
-// Shared-memory carve-up, identical on host and device.
+// Shared-memory carve-up, identical on host and device: two mbarriers, nbuf tile
+// buffers (the TC + 6 rows of a tile with its halo, then the geometry of its TC
+// cells), the force buffer (TC rows), then doubles and reals.
 template <typename real, int TC, int NT>
 struct StageSmem {
   static constexpr int NW = NT / 32;
+  using Geo = typename std::conditional<sizeof(real) == 4, GeoCellF, GeoCell>::type;
   __host__ __device__ static size_t tile_off() { return 16; }
-  __host__ __device__ static size_t lbuf_off(int Vp) { return tile_off() + size_t(TC + 6) * 2 * Vp * sizeof(real); }
-  __host__ __device__ static size_t dbl_off(int Vp) {
-    size_t o = lbuf_off(Vp) + size_t(TC) * 2 * Vp * sizeof(real);
+  __host__ __device__ static size_t geo_off(int Vp) { return size_t(TC + 6) * 2 * Vp * sizeof(real); }
+  __host__ __device__ static size_t buf_bytes(int Vp) { return geo_off(Vp) + size_t(TC) * sizeof(Geo); }
+  __host__ __device__ static size_t lbuf_off(int Vp, int nbuf) { return tile_off() + size_t(nbuf) * buf_bytes(Vp); }
+  __host__ __device__ static size_t dbl_off(int Vp, int nbuf) {
+    size_t o = lbuf_off(Vp, nbuf) + size_t(TC) * 2 * Vp * sizeof(real);
     return (o + 15) & ~size_t(15);
   }
   // doubles: p0, p1 (MAXQ each), reduction (NW*4), wall equilibrium factors (2*MAXQ), scalars (16)
   static constexpr size_t n_dbl = 2 * MAXQ + NW * 4 + 2 * MAXQ + 16;
-  __host__ __device__ static size_t real_off(int Vp) { return dbl_off(Vp) + n_dbl * sizeof(double); }
+  __host__ __device__ static size_t real_off(int Vp, int nbuf) { return dbl_off(Vp, nbuf) + n_dbl * sizeof(double); }
   // reals: p0, p1, 1/w0, 1/w1 (MAXQ each), tab0, tab1 (MAXQ*MAXN each), then pairs: n g_R and g_phi
   // (TC*MAXQ each), (1, T), -1/tau, cp, -cm, 1/Rbar (TC each); then moment vectors (TC*4*MAXN),
   // w0, w1 (MAXQ each)
   static constexpr size_t n_real = 4 * MAXQ + 2 * MAXQ * MAXN + 4 * TC * MAXQ + 10 * TC + TC * 4 * MAXN + 2 * MAXQ;
-  __host__ __device__ static size_t bytes(int Vp) { return real_off(Vp) + n_real * sizeof(real); }
+  __host__ __device__ static size_t bytes(int Vp, int nbuf) { return real_off(Vp, nbuf) + n_real * sizeof(real); }
 };
 
 // CTAs per SM the register allocation is sized for, where shared memory would
@@ -85,16 +93,18 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
   const int Vp = EXACT ? VPC : a.Vp;
   const int row = 2 * Vp;
 
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  real* tile = reinterpret_cast<real*>(smem + L::tile_off());
-  real* lbuf = reinterpret_cast<real*>(smem + L::lbuf_off(Vp));
-  double* p0d = reinterpret_cast<double*>(smem + L::dbl_off(Vp));
+  const int nbuf = a.nbuf;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);  // one mbarrier per tile buffer
+  real* tile0 = reinterpret_cast<real*>(smem + L::tile_off());
+  const size_t bstride = L::buf_bytes(Vp) / sizeof(real);  // reals per tile buffer
+  real* lbuf = reinterpret_cast<real*>(smem + L::lbuf_off(Vp, nbuf));
+  double* p0d = reinterpret_cast<double*>(smem + L::dbl_off(Vp, nbuf));
   double* p1d = p0d + MAXQ;
   double* red = p1d + MAXQ;
   double* gw0 = red + NW * 4;  // wall equilibrium factors
   double* gw1 = gw0 + MAXQ;
   double* mw = gw1 + MAXQ;     // [0] incoming equilibrium flux, [1] n_w
-  real* p0r = reinterpret_cast<real*>(smem + L::real_off(Vp));
+  real* p0r = reinterpret_cast<real*>(smem + L::real_off(Vp, nbuf));
   real* p1r = p0r + MAXQ;
   real* iw0 = p1r + MAXQ;  // 1 / w_i
   real* iw1 = iw0 + MAXQ;  // 1 / w_j
@@ -115,6 +125,7 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
 
   if (tid == 0) {
     mbar_init(bar, 1);
+    mbar_init(bar + 1, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   constexpr bool F32 = sizeof(real) == 4;
@@ -143,45 +154,52 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
   }
   __syncthreads();
   const bool need_fl = a.caf != 0.0f;
-  unsigned parity = 0;
+  using Geo = typename L::Geo;
+  const Geo* geo_src = reinterpret_cast<const Geo*>(F32 ? static_cast<const void*>(a.geof) : static_cast<const void*>(a.geo));
+  // warp 0 stages tile tx (cells lo..hi-1 at slots lo-c0+3 ..., then its cells' geometry) into
+  // buffer b with bulk copies that complete on the buffer's mbarrier
+  auto stage_tile = [&](int tx, int b) {
+    const TileDesc t = a.tiles[tx];
+    const InstDesc i = a.inst[t.inst];
+    const int lo = max(t.c0 - 3, 0), hi = min(t.c0 + t.nc + 3, i.n_cells);
+    real* dst = tile0 + b * bstride;
+    const unsigned rbytes = unsigned(row * sizeof(real)), gbytes = unsigned(t.nc * sizeof(Geo));
+    if (lane == 0) mbar_expect_tx(bar + b, rbytes * unsigned(hi - lo) + gbytes);
+    __syncwarp();
+    for (int c = lo + lane; c < hi; c += 32)
+      bulk_g2s(dst + (c - t.c0 + 3) * row, a.Fprev + size_t(i.cell0 + c) * row, rbytes, bar + b);
+    if (lane == 0) bulk_g2s(dst + L::geo_off(Vp) / sizeof(real), geo_src + i.cell0 + t.c0, gbytes, bar + b);
+  };
+  unsigned phase = 0;  // bit b: parity of buffer b's next completion
+  if (nbuf == 2 && warp == 0 && blockIdx.x < a.n_tiles) stage_tile(blockIdx.x, 0);
   // one tile per iteration: a launch with one CTA per tile runs the body once, a persistent
-  // launch (grid sized by occupancy) walks the tile list
-  for (int tix = blockIdx.x; tix < a.n_tiles; tix += gridDim.x) {
+  // launch (grid sized by occupancy) walks the tile list, with two buffers staging the next
+  // tile while this one is computed
+  for (int tix = blockIdx.x, it = 0; tix < a.n_tiles; tix += gridDim.x, ++it) {
+  const int b = nbuf == 2 ? (it & 1) : 0;
+  real* tile = tile0 + b * bstride;
   const TileDesc td = a.tiles[tix];
   const InstDesc in = a.inst[td.inst];
   const int n = in.n_cells, c0 = td.c0;
   const int TCe = td.nc;  // the host sizes tiles (1 <= nc <= TC) to fill the launch in whole rounds
-  const int lo = max(c0 - 3, 0), hi = min(c0 + TCe + 3, n);
-
-  // ---- stage the tile (cells lo..hi-1 at slots lo-c0+3 ...) and F_l with bulk copies
-  if (warp == 0) {
-    const unsigned rbytes = unsigned(row * sizeof(real));
-    if (lane == 0) mbar_expect_tx(bar, rbytes * unsigned(hi - lo));
-    __syncwarp();
-    for (int c = lo + lane; c < hi; c += 32)
-      bulk_g2s(tile + (c - c0 + 3) * row, a.Fprev + size_t(in.cell0 + c) * row, rbytes, bar);
-  }
-  for (int t = tid; t < TCe; t += NT) {
-    if constexpr (F32) {
-      const GeoCellF g = a.geof[in.cell0 + c0 + t];
-      ccp[t] = p_set(g.cp);
-      cNcm[t] = p_set(-g.cm);
-      cIR[t] = p_set(g.inv_rbar);
-    } else {
-      const GeoCell g = a.geo[in.cell0 + c0 + t];
-      ccp[t] = p_set(g.cp);
-      cNcm[t] = p_set(-g.cm);
-      cIR[t] = p_set(g.inv_rbar);
-    }
-  }
-  bool ok = mbar_wait(bar, parity, a.max_polls);
+  if (nbuf == 1 && warp == 0) stage_tile(tix, 0);
+  bool ok = mbar_wait(bar + b, (phase >> b) & 1u, a.max_polls);
   ok = __syncthreads_and(ok);
   if (!ok) {
     if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
-    mbar_wait(bar, parity, a.max_polls);  // let the copies land before the CTA exits
+    mbar_wait(bar + b, (phase >> b) & 1u, a.max_polls);  // let the copies land before the CTA exits
+    if (tid == 0) bulk_wait_all();                        // and the stores read their source
     return;
   }
-  parity ^= 1u;
+  phase ^= 1u << b;
+  {  // the cells' geometry as pairs for phase D
+    const Geo* g = reinterpret_cast<const Geo*>(tile + L::geo_off(Vp) / sizeof(real));
+    for (int t = tid; t < TCe; t += NT) {
+      ccp[t] = p_set(real(g[t].cp));
+      cNcm[t] = p_set(real(-g[t].cm));
+      cIR[t] = p_set(real(g[t].inv_rbar));
+    }
+  }
 
   // ==== phase A: per cell, one half-warp (16 lanes) with no CTA barrier: moments (Eq.
   // macro_red), tau, the equilibrium moment vectors and factors (Sec. IV.D) and their mass
@@ -459,6 +477,13 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
     for (int x = f0; x < nP; x += fs) force_phi(x);
   __syncthreads();
 
+  // stage the next tile into the other buffer, the source of the previous tile's store
+  if (nbuf == 2 && warp == 0 && tix + int(gridDim.x) < a.n_tiles) {
+    if (lane == 0) bulk_wait_read_all();
+    __syncwarp();
+    stage_tile(tix + gridDim.x, b ^ 1);
+  }
+
   // ==== phase B: the walls
   for (int wall = 0; wall < 2; ++wall) {
     // every tile whose stencils reach a ghost cell fills the ghosts itself
@@ -576,10 +601,12 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
   __syncthreads();
   if (tid == 0) {
     bulk_s2g(a.Fout + size_t(in.cell0 + c0) * row, tile + 3 * row, unsigned(TCe * row * sizeof(real)));
-    bulk_commit_and_wait_read();
+    bulk_commit();
+    if (nbuf == 1) bulk_wait_read_all();
   }
-  __syncthreads();  // shared memory is reused by the next tile
+  if (nbuf == 1) __syncthreads();  // the next tile is staged into this buffer
   }
+  if (tid == 0) bulk_wait_all();  // the stores have read their source before the CTA exits
 }
 
 }  // namespace vlb
