@@ -11,8 +11,10 @@ equilibrium, synthetic.
 
 Metric: cell-velocity updates per second (cells x velocities advanced by one
 RK3 step / wall time).  The working set (13 MB) fits in L2, so L2 is flushed
-(a 512 MB write) between timed steps; each step is timed alone with CUDA
-events on the launching stream.
+between timed steps: a 512 MB buffer is written, then read back, so that the
+timed step starts from an L2 holding none of its data and no dirty lines of
+the flush to write back; each step is timed alone with CUDA events on the
+launching stream.
 
 --impl reference times the fp64 CPU oracle on the host cores on a bounded
 sample of the same workload.
@@ -146,26 +148,36 @@ def make_ctx(prec, stream_ptr):
                        [vlb.VLB_TAU_AOKI] * n, stream=stream_ptr)
 
 
+def evict_l2(flush, sink):
+    """Write the flush buffer (larger than L2), then read it back into sink, so that
+    the dirty lines the write leaves are written back before the next timed region."""
+    flush.fill_(1.0)
+    sink.copy_(flush.sum())
+
+
 def time_device(ctx, torch, stream, steps, warmup, flush):
-    """Per-step and per-stage-launch device times with CUDA events on the launching stream."""
+    """Per-step device times with CUDA events on the launching stream around one
+    vlb_step call (its three stage launches, queued by the library back to back),
+    and the mean stage-launch time, a third of each step (it carries the gaps
+    between the launches too).  Events between the stages would put the host's
+    work between them into the timed region."""
     ev = lambda: torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
+        sink = torch.zeros((), dtype=flush.dtype, device=flush.device)
         for _ in range(warmup):
             ctx.step(DT, 1)
         stream.synchronize()
-        step_ms, stage_ms = [], []
+        step_ms = []
         for _ in range(steps):
-            flush.fill_(1.0)  # evict L2 between timed steps (outside the events)
-            marks = [ev() for _ in range(4)]
-            marks[0].record(stream)
-            for k in (1, 2, 3):
-                ctx.stage(DT, k)
-                marks[k].record(stream)
+            evict_l2(flush, sink)  # outside the events
+            t0, t1 = ev(), ev()
+            t0.record(stream)
+            ctx.step(DT, 1)
+            t1.record(stream)
             stream.synchronize()
-            t = [marks[0].elapsed_time(marks[k]) for k in (1, 2, 3)]
-            step_ms.append(t[2])
-            stage_ms += [t[0], t[1] - t[0], t[2] - t[1]]
-    return np.array(step_ms), np.array(stage_ms)
+            step_ms.append(t0.elapsed_time(t1))
+    step_ms = np.array(step_ms)
+    return step_ms, step_ms / 3.0
 
 
 def time_e2e(ctx, torch, stream, host_in, host_out, steps):
@@ -417,7 +429,7 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "model": MODEL, "cells": N_CELLS, "velocities": 320,
                    "instances_per_gpu": len(KNS), "kn": KNS, "precision": "fp32-bulk (fp64 reductions)",
-                   "dt": DT, "l2": "flushed (512 MB write) between timed steps",
+                   "dt": DT, "l2": "flushed between timed steps (512 MB written, then read back)",
                    "launch_shape": {"cells_per_cta": shape32[0], "threads": shape32[1], "persistent": bool(shape32[2]),
                                     "autotuned": True}},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",

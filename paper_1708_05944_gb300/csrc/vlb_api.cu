@@ -140,6 +140,32 @@ void fill_force_tables(KArgs<real>& k, const std::vector<double>& K0, const std:
     }
 }
 
+}  // namespace
+
+cudaError_t stage_launch_config(vlb_ctx* c, int n_tiles, int* nbuf, int* grid) {
+  const int v = c->variant;
+  if (c->cfg_nbuf[v] == 0) {  // first use of this launch shape
+    cudaError_t e;
+    if (c->sms == 0) {
+      int dev = 0;
+      if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+      if ((e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    }
+    int nb = 1, per_sm = 0;
+    e = c->prec == VLB_FP64 ? stage_config<double>(c->variants[v], c->margs, c->Vp, &nb, &per_sm)
+                            : stage_config<float>(c->variants[v], c->margs, c->Vp, &nb, &per_sm);
+    if (e != cudaSuccess) return e;
+    c->cfg_nbuf[v] = nb;
+    c->cfg_per_sm[v] = per_sm;
+  }
+  *nbuf = c->cfg_nbuf[v];
+  const int cap = c->cfg_per_sm[v] * c->sms;  // persistent: as many CTAs as are resident at once
+  *grid = c->variants[v].persist && cap > 0 && cap < n_tiles ? cap : n_tiles;
+  return cudaSuccess;
+}
+
+namespace {
+
 // Tiles over every instance for the current launch shape.  One-CTA-per-tile
 // launches take tiles of the shape's full size TC.  A persistent launch walks
 // the tile list in rounds of `slots` CTAs, so the tile size s <= TC is chosen to
@@ -155,7 +181,8 @@ void build_tiles(vlb_ctx* c) {
   int s = v.tc;
   int slots = 0;
   if (v.persist) {
-    slots = c->prec == VLB_FP64 ? stage_slots<double>(v, c->margs, c->Vp) : stage_slots<float>(v, c->margs, c->Vp);
+    int nbuf = 1;
+    if (stage_launch_config(c, 1 << 30, &nbuf, &slots) != cudaSuccess) slots = 0;
     if (slots > 0) {
       long long best = -1;
       for (int cand = v.tc; cand >= std::max(3, (v.tc + 1) / 2); --cand) {
@@ -213,7 +240,9 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   a.max_polls = 1ull << 26;
   const KArgs<real>* kk;
   if constexpr (sizeof(real) == 4) kk = c->k32.get(); else kk = c->k64.get();
-  cudaError_t e = launch_stage<real>(c->variants[c->variant], a, c->margs, *kk, c->stream);
+  int grid = 0;
+  cudaError_t e = stage_launch_config(c, a.n_tiles, &a.nbuf, &grid);
+  if (e == cudaSuccess) e = launch_stage<real>(c->variants[c->variant], a, c->margs, *kk, grid, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
   c->launches += 1;
   return VLB_OK;

@@ -14,6 +14,11 @@
 
 using namespace vlb;
 
+struct vlb_ctx;
+// Tile buffers and grid of a stage launch with the context's current launch shape
+// over n_tiles tiles (the shape's configuration is computed once and kept).
+cudaError_t stage_launch_config(vlb_ctx* c, int n_tiles, int* nbuf, int* grid);
+
 struct vlb_ctx {
   int kind = 0;  // 0 circular Couette instances, 1 gradually expanding channel
   vlb_model model{};
@@ -35,6 +40,10 @@ struct vlb_ctx {
   StageVariant variants[16];
   int n_variants = 0;
   int variant = 0;
+  // launch configuration per launch shape, computed on its first use (stage_launch_config)
+  int cfg_nbuf[16] = {};
+  int cfg_per_sm[16] = {};
+  int sms = 0;  // SMs of the context's device
   int cur = 0;   // buffer holding F_l
   int last = 0;  // buffer written by the most recent stage
   int stage_done = 0;

@@ -21,8 +21,15 @@ static cudaError_t stage_buffers(int Vp, int persist, int* nbuf, int* per_sm) {
   auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
   const size_t limit = 227 * 1024;
   const int top = persist && L::bytes(Vp, 2) <= limit ? 2 : 1;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::bytes(Vp, top)));
+  // the kernel's shared-memory limit is process-wide and shared by contexts of other row
+  // lengths (the generic kernels), so it is only ever raised
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
   if (e != cudaSuccess) return e;
+  if (size_t(fa.maxDynamicSharedSizeBytes) < L::bytes(Vp, top)) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::bytes(Vp, top)));
+    if (e != cudaSuccess) return e;
+  }
   *nbuf = 1, *per_sm = 0;
   for (int nb = 1; nb <= top; ++nb) {
     int occ = 0;
@@ -33,23 +40,10 @@ static cudaError_t stage_buffers(int Vp, int persist, int* nbuf, int* per_sm) {
 }
 
 template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
-static cudaError_t go_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int persist,
+static cudaError_t go_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int grid,
                             cudaStream_t s) {
-  auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
-  StageArgs<real> args = a;
-  int per_sm = 0;
-  cudaError_t e = stage_buffers<real, TC, NT, Q0, Q1, EXACT>(a.Vp, persist, &args.nbuf, &per_sm);
-  if (e != cudaSuccess) return e;
-  const size_t smem = StageSmem<real, TC, NT>::bytes(a.Vp, args.nbuf);
-  int grid = a.n_tiles;
-  if (persist) {  // persistent: as many CTAs as fit on the device at once, each walking the tile list
-    int dev = 0, sms = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int cap = per_sm * sms;
-    if (cap > 0 && cap < grid) grid = cap;
-  }
-  kern<<<grid, NT, smem, s>>>(args, m, k);
+  couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>
+      <<<grid, NT, StageSmem<real, TC, NT>::bytes(a.Vp, a.nbuf), s>>>(a, m, k);
   return cudaGetLastError();
 }
 
@@ -119,11 +113,11 @@ size_t stage_smem_bytes(StageVariant v, int Vp) {
 }
 
 template <typename real>
-cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k,
+cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int grid,
                          cudaStream_t s) {
   const int sh = shape_of(m.nq0, m.nq1);
 #define VLB_CASE(SH, TC_, NT_, q0, q1, ex) \
-  if (sh == SH && v.tc == TC_ && v.nt == NT_) return go_stage<real, TC_, NT_, q0, q1, ex>(a, m, k, v.persist, s);
+  if (sh == SH && v.tc == TC_ && v.nt == NT_) return go_stage<real, TC_, NT_, q0, q1, ex>(a, m, k, grid, s);
   if constexpr (sizeof(real) == 4) {
     VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
     VLB_CASE(SH_16x20, 4, 320, 16, 20, true) VLB_CASE(SH_16x20, 8, 320, 16, 20, true)
@@ -147,21 +141,12 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
   return cudaErrorInvalidValue;
 }
 
-// CTAs of one launch shape that are resident on the device at once (occupancy x SMs)
-template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
-static int slots_of(int Vp) {
-  int dev = 0, sms = 0, nbuf = 1, per_sm = 0;
-  if (stage_buffers<real, TC, NT, Q0, Q1, EXACT>(Vp, 1, &nbuf, &per_sm) != cudaSuccess) return 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  return per_sm * sms;
-}
-
 template <typename real>
-int stage_slots(StageVariant v, const ModelArgs& m, int Vp) {
+cudaError_t stage_config(StageVariant v, const ModelArgs& m, int Vp, int* nbuf, int* per_sm) {
   const int sh = shape_of(m.nq0, m.nq1);
 #define VLB_CASE(SH, TC_, NT_, q0, q1, ex) \
-  if (sh == SH && v.tc == TC_ && v.nt == NT_) return slots_of<real, TC_, NT_, q0, q1, ex>(Vp);
+  if (sh == SH && v.tc == TC_ && v.nt == NT_)      \
+    return stage_buffers<real, TC_, NT_, q0, q1, ex>(Vp, v.persist, nbuf, per_sm);
   if constexpr (sizeof(real) == 4) {
     VLB_CASE(SH_16x20, 4, 256, 16, 20, true) VLB_CASE(SH_16x20, 8, 256, 16, 20, true)
     VLB_CASE(SH_16x20, 4, 320, 16, 20, true) VLB_CASE(SH_16x20, 8, 320, 16, 20, true)
@@ -182,7 +167,8 @@ int stage_slots(StageVariant v, const ModelArgs& m, int Vp) {
     VLB_CASE(SH_GENERIC, 8, 256, MAXQ, MAXQ, false)
   }
 #undef VLB_CASE
-  return 0;
+  *nbuf = 1, *per_sm = 0;
+  return cudaErrorInvalidValue;
 }
 
 // ---------------------------------------------------------------- channel dispatch
@@ -496,7 +482,7 @@ template int stage_variants<VLB_REAL>(int, int, StageVariant*);
 template size_t stage_smem_bytes<VLB_REAL>(StageVariant, int);
 template bool stage_split_tables<VLB_REAL>(int, int);
 template cudaError_t launch_stage<VLB_REAL>(StageVariant, const StageArgs<VLB_REAL>&, const ModelArgs&,
-                                            const KArgs<VLB_REAL>&, cudaStream_t);
+                                            const KArgs<VLB_REAL>&, int, cudaStream_t);
 template cudaError_t launch_init_equilibrium<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, double, double,
                                                        double, double, cudaStream_t);
 template size_t channel_smem_bytes<VLB_REAL>(ChanVariant, int, int);
@@ -504,7 +490,7 @@ template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_RE
                                               int, cudaStream_t);
 template cudaError_t launch_seed<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
                                            const double*, const double*, const double*, const double*, cudaStream_t);
-template int stage_slots<VLB_REAL>(StageVariant, const ModelArgs&, int);
+template cudaError_t stage_config<VLB_REAL>(StageVariant, const ModelArgs&, int, int*, int*);
 template cudaError_t launch_deviation<VLB_REAL>(const VLB_REAL*, VLB_REAL*, long long, int, const ModelArgs&, int,
                                                 cudaStream_t);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,

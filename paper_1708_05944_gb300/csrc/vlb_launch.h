@@ -28,13 +28,17 @@ size_t stage_smem_bytes(StageVariant v, int Vp);
 template <typename real>
 bool stage_split_tables(int nq0, int nq1);
 
-// Launch one RK3 stage over a.n_tiles tiles of v.tc cells.
-// CTAs of a launch shape resident on the device at once (0 if unknown).
+// Launch configuration of a stage launch shape on the current device: tile
+// buffers (StageArgs::nbuf) and resident CTAs per SM (0 if none fit).  Also
+// raises the kernel's dynamic shared-memory limit to what the configuration
+// needs, which its launches rely on; a context computes it once per shape.
 template <typename real>
-int stage_slots(StageVariant v, const ModelArgs& m, int Vp);
+cudaError_t stage_config(StageVariant v, const ModelArgs& m, int Vp, int* nbuf, int* per_sm);
 
+// Launch one RK3 stage over a.n_tiles tiles of at most v.tc cells on `grid` CTAs
+// (a.nbuf as stage_config gave it).
 template <typename real>
-cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k,
+cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int grid,
                          cudaStream_t s);
 
 // Launch shapes of the channel stage kernel: cells per tile in lambda (ts) and xi (tp), threads.

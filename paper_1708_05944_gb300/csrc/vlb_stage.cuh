@@ -158,8 +158,7 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
   const Geo* geo_src = reinterpret_cast<const Geo*>(F32 ? static_cast<const void*>(a.geof) : static_cast<const void*>(a.geo));
   // warp 0 stages tile tx (cells lo..hi-1 at slots lo-c0+3 ..., then its cells' geometry) into
   // buffer b with bulk copies that complete on the buffer's mbarrier
-  auto stage_tile = [&](int tx, int b) {
-    const TileDesc t = a.tiles[tx];
+  auto stage_tile = [&](const TileDesc& t, int b) {
     const InstDesc i = a.inst[t.inst];
     const int lo = max(t.c0 - 3, 0), hi = min(t.c0 + t.nc + 3, i.n_cells);
     real* dst = tile0 + b * bstride;
@@ -171,18 +170,20 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
     if (lane == 0) bulk_g2s(dst + L::geo_off(Vp) / sizeof(real), geo_src + i.cell0 + t.c0, gbytes, bar + b);
   };
   unsigned phase = 0;  // bit b: parity of buffer b's next completion
-  if (nbuf == 2 && warp == 0 && blockIdx.x < a.n_tiles) stage_tile(blockIdx.x, 0);
+  // the next tile's descriptor is read during the current tile (its load latency hidden)
+  TileDesc td_next = blockIdx.x < a.n_tiles ? a.tiles[blockIdx.x] : TileDesc{0, 0, 0};
+  if (nbuf == 2 && warp == 0 && blockIdx.x < a.n_tiles) stage_tile(td_next, 0);
   // one tile per iteration: a launch with one CTA per tile runs the body once, a persistent
   // launch (grid sized by occupancy) walks the tile list, with two buffers staging the next
   // tile while this one is computed
   for (int tix = blockIdx.x, it = 0; tix < a.n_tiles; tix += gridDim.x, ++it) {
   const int b = nbuf == 2 ? (it & 1) : 0;
   real* tile = tile0 + b * bstride;
-  const TileDesc td = a.tiles[tix];
+  const TileDesc td = td_next;
   const InstDesc in = a.inst[td.inst];
   const int n = in.n_cells, c0 = td.c0;
   const int TCe = td.nc;  // the host sizes tiles (1 <= nc <= TC) to fill the launch in whole rounds
-  if (nbuf == 1 && warp == 0) stage_tile(tix, 0);
+  if (nbuf == 1 && warp == 0) stage_tile(td, 0);
   bool ok = mbar_wait(bar + b, (phase >> b) & 1u, a.max_polls);
   ok = __syncthreads_and(ok);
   if (!ok) {
@@ -477,11 +478,13 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
     for (int x = f0; x < nP; x += fs) force_phi(x);
   __syncthreads();
 
+  if (tix + int(gridDim.x) < a.n_tiles) td_next = a.tiles[tix + gridDim.x];
+
   // stage the next tile into the other buffer, the source of the previous tile's store
   if (nbuf == 2 && warp == 0 && tix + int(gridDim.x) < a.n_tiles) {
     if (lane == 0) bulk_wait_read_all();
     __syncwarp();
-    stage_tile(tix + gridDim.x, b ^ 1);
+    stage_tile(td_next, b ^ 1);
   }
 
   // ==== phase B: the walls
@@ -570,9 +573,13 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
     // upwind stencil: (w0..w4) for p^R >= 0, mirrored (w5..w1) otherwise
     P fm = weno5p<real>(p_sel(up, w0, w5), p_sel(up, w1, w4), p_sel(up, w2, w3), p_sel(up, w3, w2),
                         p_sel(up, w4, w1), sc);
+    // F_l of the next cell is loaded one cell ahead (a global load, the only one of the walk)
+    P fl_next = need_fl ? p_load(Fl) : p_set(real(0));
 #pragma unroll
     for (int t = 0; t < TC; ++t) {
       if (t < TCe) {
+        const P fl = fl_next;
+        if (need_fl && t + 1 < TCe) fl_next = p_load(Fl + (t + 1) * row);
         const P w6 = p_load(S + (t + 6) * row);
         const P fp = weno5p<real>(p_sel(up, w1, w6), p_sel(up, w2, w5), p_sel(up, w3, w4), p_sel(up, w4, w3),
                                   p_sel(up, w5, w2), sc);
@@ -584,7 +591,7 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
         // L = -adv + force / Rbar - (D - D_eq) / tau
         const P Lv = p_fma(p_sub(w3, deq), cNtau[t], p_fma(force, cIR[t], nadv));
         P o = p_fma(Lv, p_set(cc), w3);
-        if (need_fl) o = p_fma(p_fma(w3, p_set(real(-1)), p_load(Fl + t * row)), p_set(ca), o);
+        if (need_fl) o = p_fma(p_sub(fl, w3), p_set(ca), o);
         p_store(S + (t + 3) * row, o);  // in place: this column's slot t+3 is not read again
         w0 = w1;
         w1 = w2;

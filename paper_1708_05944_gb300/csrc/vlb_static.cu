@@ -52,7 +52,10 @@ cudaError_t launch_one(vlb_ctx* c, int k, const void* prev, const void* fl, void
   a.max_polls = 1ull << 26;
   const KArgs<real>* kk;
   if constexpr (sizeof(real) == 4) kk = c->k32.get(); else kk = c->k64.get();
-  return launch_stage<real>(c->variants[c->variant], a, c->margs, *kk, c->stream);
+  int grid = 0;
+  cudaError_t e = stage_launch_config(c, a.n_tiles, &a.nbuf, &grid);
+  if (e != cudaSuccess) return e;
+  return launch_stage<real>(c->variants[c->variant], a, c->margs, *kk, grid, c->stream);
 }
 
 }  // namespace
