@@ -552,7 +552,9 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
       if (s3 >= 0 && s3 < TC + 6) p_store(tile + s3 * row + 2 * v, g3);
     }
   }
-  __syncthreads();
+  // phase D reads the ghost rows the walls wrote; an interior tile wrote nothing since the
+  // barrier after phase A (warp 0's staging goes to the other buffer)
+  if (c0 < 3 || c0 + TCe + 3 > n) __syncthreads();  // uniform across the CTA
 
   // ==== phase D: WENO-5 fluxes along the cells, flux difference, BGK, RK3 combine (in place)
   const real dtr = F32 ? real(in.dt_f) : real(in.dt);
