@@ -52,6 +52,21 @@ def test_tables_equal_oracle(spec):
         np.testing.assert_allclose(Kt, om.Kt[a], rtol=0, atol=1e-13 * np.abs(om.Kt[a]).max())
 
 
+@pytest.mark.parametrize("spec", ["HH(4;8)xH(4;20)", "HH(4;8)xH(4;12)", "HH(3;4)xH(3;4)", "H(4;16)xHH(4;10)"])
+def test_node_reflection_used_by_the_split_contractions(spec):
+    """The stage kernels of the fixed shapes mirror node k of an axis to k + Q/2 on
+    half-range axes (positive nodes first) and to nq - 1 - k on full-range axes,
+    and rely on K J = -J K, Kt J = J Kt for that permutation."""
+    m = vlb.vlb_parse_model(spec)
+    for a in (0, 1):
+        p, _, K, Kt = vlb.vlb_axis_tables(m, a)
+        n = len(p)
+        J = np.array([(k + n // 2) % n if m.kind[a] == vlb.VLB_HALF else n - 1 - k for k in range(n)])
+        np.testing.assert_allclose(p[J], -p, rtol=0, atol=1e-14 * np.abs(p).max())
+        np.testing.assert_allclose(K[np.ix_(J, J)], -K, rtol=0, atol=1e-12 * np.abs(K).max())
+        np.testing.assert_allclose(Kt[np.ix_(J, J)], Kt, rtol=0, atol=1e-12 * np.abs(Kt).max())
+
+
 def test_invalid_arguments_rejected_without_gpu():
     bad = [
         dict(grids=[dict(n_cells=2)]),

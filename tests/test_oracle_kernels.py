@@ -122,3 +122,16 @@ def test_half_range_K_exact_on_continuous_gaussian_polynomial():
     f = w * P(p)
     exact = w * (P.deriv()(p) - p * P(p))
     np.testing.assert_allclose(K @ f, exact, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind,Q", [("H", 4), ("H", 5), ("H", 12), ("H", 20), ("HH", 2), ("HH", 4), ("HH", 8)])
+def test_kernels_commute_with_the_reflection(kind, Q):
+    """d/dp anticommutes and d/dp (p .) commutes with f(p) -> f(-p); the printed
+    kernels keep this exactly on the symmetric node sets (the stage kernels of the
+    library split both contractions into even and odd parts on that basis)."""
+    m = lb.Model(f"{kind}({min(Q - 1, 4)};{Q})x{kind}({min(Q - 1, 4)};{Q})")
+    p, K, Kt = m.p[0], m.K[0], m.Kt[0]
+    J = np.array([int(np.argmin(np.abs(p + pk))) for pk in p])
+    np.testing.assert_allclose(p[J], -p, rtol=0, atol=1e-14 * np.abs(p).max())
+    np.testing.assert_allclose(K[np.ix_(J, J)], -K, rtol=0, atol=1e-13 * np.abs(K).max())
+    np.testing.assert_allclose(Kt[np.ix_(J, J)], Kt, rtol=0, atol=1e-13 * np.abs(Kt).max())
