@@ -5,9 +5,11 @@ one batch): the circular Couette scale-up case -- 1024 equidistant cells between
 R_in = 1 and R_out = 2, model HH(4;8)xH(4;20) (16 x 20 = 320 velocities), inner
 wall speed 0.1, outer wall at rest, T_w = 1, one instance for each
 Kn in {1e-3, 1e-2, 0.1, 1, 10} (Aoki relaxation time), FP32-bulk storage and
-stencil arithmetic with FP64 moment and wall-flux reductions.  The FP64 path is
-timed on the same batch and reported beside it.  Input: seeded perturbed
-equilibrium, synthetic.
+stencil arithmetic, compensated (float-float) moment sums and an FP64 wall-flux
+balance.  The FP64 path is timed on the same batch and reported beside it, and
+two HBM-scale workloads beside that: the batched Couette case (256 instances,
+~360 MB per distribution copy) and the gradually expanding channel.  Input:
+seeded perturbed equilibrium, synthetic.
 
 Metric: cell-velocity updates per second (cells x velocities advanced by one
 RK3 step / wall time).  The working set (13 MB) fits in L2, so L2 is flushed
@@ -41,6 +43,8 @@ KNS = [1e-3, 1e-2, 0.1, 1.0, 10.0]
 U_WALL = 0.1
 DT = 5e-5  # CFL 0.4 with max |p^R| = 5.21 and dR = 1/1024, and below tau_min
 METRIC = "cell-velocity updates/s"
+BATCH_N = 256  # instances of the batched Couette measurement
+BATCH_F_SEED = 4  # seed of its perturbed initial populations
 CH_MODEL = "HH(4;8)xH(4;12)"
 CH_KN, CH_NIN, CH_NOUT = 0.05, 2.0, 1.0
 CH_DT = 2e-5  # CFL 0.4 on the wall-adjacent cell of the stretched lambda grid (d lambda = 3.7e-4)
@@ -155,7 +159,7 @@ def evict_l2(flush, sink):
     sink.copy_(flush.sum())
 
 
-def time_device(ctx, torch, stream, steps, warmup, flush):
+def time_device(ctx, torch, stream, steps, warmup, flush, dt=DT):
     """Per-step device times with CUDA events on the launching stream around one
     vlb_step call (its three stage launches, queued by the library back to back),
     and the mean stage-launch time, a third of each step (it carries the gaps
@@ -165,14 +169,14 @@ def time_device(ctx, torch, stream, steps, warmup, flush):
     with torch.cuda.stream(stream):
         sink = torch.zeros((), dtype=flush.dtype, device=flush.device)
         for _ in range(warmup):
-            ctx.step(DT, 1)
+            ctx.step(dt, 1)
         stream.synchronize()
         step_ms = []
         for _ in range(steps):
             evict_l2(flush, sink)  # outside the events
             t0, t1 = ev(), ev()
             t0.record(stream)
-            ctx.step(DT, 1)
+            ctx.step(dt, 1)
             t1.record(stream)
             stream.synchronize()
             step_ms.append(t0.elapsed_time(t1))
@@ -245,6 +249,51 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def bench_batched(args, torch, stream, vlb, flush):
+    """The batched Couette workload: BATCH_N instances from the seeded sampler (cells
+    U{64..1024}, log10 Kn U[-3, 1], inner wall speed U[0.01, 0.5], R_out/R_in U[1.5, 4]),
+    HH(4;8)xH(4;20), FP32 bulk, each instance with its own stable time step, one
+    launch per stage over all of them.  One distribution copy (~360 MB) is larger
+    than L2: the Couette case measured against HBM."""
+    from paper_1708_05944_gb300 import warmstart as W
+    from paper_1708_05944_gb300.inputs import couette_instances, perturbation
+    insts = couette_instances(BATCH_N)
+    n = len(insts)
+    grids = [dict(n_cells=i["n_cells"], r_in=i["r_in"], r_out=i["r_out"]) for i in insts]
+    ctx = vlb.Couette(MODEL, vlb.VLB_FP32_BULK, grids, [(i["u_wall"], 1.0) for i in insts], [(0.0, 1.0)] * n,
+                      [i["kn"] for i in insts], [vlb.VLB_TAU_AOKI] * n, stream=stream.cuda_stream)
+    pm, rho = W.p_max(MODEL), W.force_radius(MODEL)
+    ctx.set_dt([W.stable_dt(i, pm, rho) for i in insts])
+    m = vlb.vlb_parse_model(MODEL)
+    _, w0 = vlb.vlb_quadrature(m, 0)
+    _, w1 = vlb.vlb_quadrature(m, 1)
+    cells = sum(i["n_cells"] for i in insts)
+    F = np.broadcast_to(np.outer(w0, w1), (cells, 2, 16, 20)) * perturbation((cells, 2, 16, 20), seed=BATCH_F_SEED)
+    ctx.set_f(np.ascontiguousarray(F.astype(np.float32)))
+    del F
+    tuned, _ = ctx.autotune(0.0, reps=5)
+    shape = ctx.variants()[tuned]
+    step_ms, stage_ms = time_device(ctx, torch, stream, args.batch_steps, 3, flush, dt=0.0)
+    nmom = ctx.read_moments()[0]
+    ctx.close()
+    units = cells * 320
+    bytes_per_launch = units * 2 * 4 * (2 + 3 + 3) / 3.0
+    launch_ms = float(stage_ms.mean())
+    hbm, kind = peaks()
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
+    return {"workload": f"batched circular Couette: {n} instances, {cells} cells in total (64..1024 each), "
+                        f"{MODEL} (320 velocities), log10 Kn in [-3, 1], FP32 bulk, per-instance dt",
+            "value": units / (float(step_ms.mean()) * 1e-3), "unit": "cell-velocity updates/s",
+            "ms_per_step": float(step_ms.mean()), "steps": len(step_ms),
+            "launch_shape": {"cells_per_cta": shape[0], "threads": shape[1], "persistent": bool(shape[2]),
+                             "autotuned": True},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": None, "kernel": f"couette_stage_kernel<float, TC={shape[0]}, NT={shape[1]}>",
+                         "peak_source": f"{kind} hbm_gbs", "algorithmic_bytes_per_launch": bytes_per_launch,
+                         "launch_ms": launch_ms},
+            "density_finite": bool(np.all(np.isfinite(nmom)))}
 
 
 def bench_channel(args, torch, stream, vlb):
@@ -412,6 +461,7 @@ def run_gpu(args):
     fp64_value, _ = whole_job_rate(float(s64.sum()), units, len(s64), world)
     ctx64.close()
 
+    batched = bench_batched(args, torch, stream, vlb, flush) if args.workload in ("all", "batched") else None
     channel = bench_channel(args, torch, stream, vlb) if args.workload in ("all", "channel") else None
     steady = time_to_steady(args, torch) if args.time_to_steady and rank == 0 else None
 
@@ -428,7 +478,7 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "model": MODEL, "cells": N_CELLS, "velocities": 320,
-                   "instances_per_gpu": len(KNS), "kn": KNS, "precision": "fp32-bulk (fp64 reductions)",
+                   "instances_per_gpu": len(KNS), "kn": KNS, "precision": "fp32-bulk (compensated moment sums, fp64 wall flux)",
                    "dt": DT, "l2": "flushed between timed steps (512 MB written, then read back)",
                    "launch_shape": {"cells_per_cta": shape32[0], "threads": shape32[1], "persistent": bool(shape32[2]),
                                     "autotuned": True}},
@@ -444,6 +494,7 @@ def run_gpu(args):
         "clocks": clocks,
         "fp64": {"value": fp64_value, "unit": "cell-velocity updates/s", "ms_per_step": float(s64.mean()),
                  "launch_shape": {"cells_per_cta": shape64[0], "threads": shape64[1]}},
+        "batched": batched,
         "channel": channel,
     }
     if steady is not None:
@@ -459,8 +510,10 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="all", choices=["all", "couette"],
-                    help="all: the Couette scale-up line plus the channel measurement")
+    ap.add_argument("--workload", default="all", choices=["all", "couette", "batched", "channel"],
+                    help="all: the Couette scale-up line plus the batched Couette and channel measurements; "
+                         "batched / channel: the line plus that one")
+    ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batched Couette measurement")
     ap.add_argument("--channel-cells", default="512x2048", help="lambda x xi cells of the channel measurement")
     ap.add_argument("--channel-steps", type=int, default=5)
     ap.add_argument("--channel-warmup", type=int, default=3)
