@@ -1,11 +1,12 @@
 // One TVD-RK3 stage of the chi-formulation circular Couette update, fused into
-// one kernel per tile of TC cells of one instance (all momenta of those cells):
+// one kernel per tile of up to TC cells of one instance (all momenta of those cells):
 //
-//   bulk-copy the tile and its three-cell halo to shared memory
-//   -> moments per cell (Eq. macro_red)          -> truncated equilibrium and tau
+//   bulk-copy the tile, its three-cell halo and its cells' geometry to shared memory
+//   -> moments per cell (Eq. macro_red), truncated equilibrium and tau; meanwhile,
+//      on the warps without a cell, the inertial force
+//      (1/R)[(p^phi)^2 K^R f - p^R K~^phi f] (Eq. boltz_couette_kom)
 //   -> walls: extrapolated outgoing ghosts (Eq. extrapol), wall flux, n_w
 //      (Eq. nw), incoming ghosts f_eq(n_w, u_w, T_w) (Eq. weno_populate)
-//   -> inertial force (1/R)[(p^phi)^2 K^R f - p^R K~^phi f] (Eq. boltz_couette_kom)
 //   -> WENO-5 fluxes along the cells, chi flux difference, BGK, RK3 combine
 //      (Eqs. weno5_flux, flux_kom_R / flux_kom_eta, BGK, rk3) -> global.
 //
@@ -78,9 +79,9 @@ constexpr int stage_min_ctas(int real_bytes, int tc, int nt) {
 }
 
 template <typename real, int TC, int Q0MAX, int Q1MAX, int NT, bool EXACT>
-__global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT)) couette_stage_kernel(const __grid_constant__ StageArgs<real> a,
-                                                           const __grid_constant__ ModelArgs m,
-                                                           const __grid_constant__ KArgs<real> kk) {
+__global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
+    couette_stage_kernel(const __grid_constant__ StageArgs<real> a, const __grid_constant__ ModelArgs m,
+                         const __grid_constant__ KArgs<real> kk) {
   using L = StageSmem<real, TC, NT>;
   constexpr int NW = L::NW;
   constexpr int VPC = (Q0MAX * Q1MAX + 3) / 4 * 4;
@@ -155,7 +156,8 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
   __syncthreads();
   const bool need_fl = a.caf != 0.0f;
   using Geo = typename L::Geo;
-  const Geo* geo_src = reinterpret_cast<const Geo*>(F32 ? static_cast<const void*>(a.geof) : static_cast<const void*>(a.geo));
+  const Geo* geo_src =
+      reinterpret_cast<const Geo*>(F32 ? static_cast<const void*>(a.geof) : static_cast<const void*>(a.geo));
   // warp 0 stages tile tx (cells lo..hi-1 at slots lo-c0+3 ..., then its cells' geometry) into
   // buffer b with bulk copies that complete on the buffer's mbarrier
   auto stage_tile = [&](const TileDesc& t, int b) {
