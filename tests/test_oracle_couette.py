@@ -83,3 +83,27 @@ def test_rigid_density_normalisation():
     n = an.rigid_density(R, Om, 1.0, ri, ro)
     total = 2 * math.pi * np.trapezoid(n * R, R)
     assert total == pytest.approx(math.pi * (ro ** 2 - ri ** 2), rel=1e-8)
+
+
+def test_steady_state_near_the_navier_stokes_limit():
+    """Sec. VI.D.1 at Kn = 0.02 (tau = Kn / (n T), so mu = Kn), 32 cells, steady
+    after about 30 time units (viscous time 1 / (pi^2 Kn)):
+    * the azimuthal velocity is the no-slip Navier-Stokes profile A R + B / R
+      (Eq. NS_U) up to the velocity slip at the walls, first order in Kn
+      (6 % of u_w here; 3 % at Kn = 0.01);
+    * the angular-momentum flux R^2 T^{R phi} is the same at every radius (Eq.
+      TRph), and equals the Navier-Stokes torque (Eq. NS_TRph) reduced by the slip
+      (0.92 of it here).
+    The flux pins the force term: with its sign flipped the spread is 130 % and
+    the mean half the torque, while the velocity profile alone hardly changes."""
+    o = CouetteOracle("HH(3;4)xH(3;4)", CouetteGrid(32), Wall(0.1), Wall(0.0), 0.02, TAU_KN_OVER_NT)
+    F = o.initial_equilibrium()
+    for _ in range(7500):
+        F = o.step(F, 4e-3)
+    R = o.g.Rc
+    mom = o.m.full_moments(F)
+    assert np.abs(mom["u1"] - an.ns_u_phi(R, 0.1, 1.0, 2.0)).max() / 0.1 < 0.08
+    flux = R ** 2 * mom["T01"]
+    assert (flux.max() - flux.min()) / abs(flux.mean()) < 0.10
+    torque = float((R ** 2 * an.ns_T_Rphi(R, 0.02, 0.1, 1.0, 2.0)).mean())
+    assert abs(flux.mean() / torque - 1.0) < 0.15
