@@ -93,9 +93,14 @@ def test_steady_state_near_the_navier_stokes_limit():
       (6 % of u_w here; 3 % at Kn = 0.01);
     * the angular-momentum flux R^2 T^{R phi} is the same at every radius (Eq.
       TRph), and equals the Navier-Stokes torque (Eq. NS_TRph) reduced by the slip
-      (0.92 of it here).
-    The flux pins the force term: with its sign flipped the spread is 130 % and
-    the mean half the torque, while the velocity profile alone hardly changes."""
+      (0.92 of it here);
+    * the energy flux R (q^R + u^phi T^{R phi}) is the same at every radius (Eq.
+      Q_def) and 0.92 of its Navier-Stokes value (Eq. NS_Q); the viscous heating
+      raises T as Eq. (NS_T) with mu / kappa = 2/5 (peak within 2 %), with the
+      maximum one cell from Eq. (NS_Rmax).
+    The fluxes pin the force term: with its sign flipped their spreads are 130 % and
+    3400 % and the peak temperature rise a fifth of the NS one, while the velocity
+    profile alone hardly changes."""
     o = CouetteOracle("HH(3;4)xH(3;4)", CouetteGrid(32), Wall(0.1), Wall(0.0), 0.02, TAU_KN_OVER_NT)
     F = o.initial_equilibrium()
     for _ in range(7500):
@@ -107,3 +112,9 @@ def test_steady_state_near_the_navier_stokes_limit():
     assert (flux.max() - flux.min()) / abs(flux.mean()) < 0.10
     torque = float((R ** 2 * an.ns_T_Rphi(R, 0.02, 0.1, 1.0, 2.0)).mean())
     assert abs(flux.mean() / torque - 1.0) < 0.15
+    energy = R * (mom["q0"] + mom["u1"] * mom["T01"])
+    assert (energy.max() - energy.min()) / abs(energy.mean()) < 0.10
+    assert abs(energy.mean() / an.ns_Q(0.02, 0.1, 1.0, 2.0) - 1.0) < 0.15
+    rise, rise_ns = mom["T"] - 1.0, an.ns_T(R, 0.4, 0.1, 1.0, 1.0, 2.0) - 1.0
+    assert abs(rise.max() / rise_ns.max() - 1.0) < 0.10
+    assert abs(R[np.argmax(rise)] - an.ns_R_Tmax(1.0, 2.0)) < 2.0 / 32
