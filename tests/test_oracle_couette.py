@@ -118,3 +118,30 @@ def test_steady_state_near_the_navier_stokes_limit():
     rise, rise_ns = mom["T"] - 1.0, an.ns_T(R, 0.4, 0.1, 1.0, 1.0, 2.0) - 1.0
     assert abs(rise.max() / rise_ns.max() - 1.0) < 0.10
     assert abs(R[np.argmax(rise)] - an.ns_R_Tmax(1.0, 2.0)) < 2.0 / 32
+
+
+def test_steady_state_in_the_free_molecular_limit():
+    """Sec. VI.D.2 (no collisions: Kn = 1000), 32 cells, HH(3;4) x H(3;4), steady
+    after about 12 time units.  Exactly, the angular-momentum and energy fluxes
+    are the same at every radius, R^2 T^{R phi} = n_w T_w Om R_in^2 / sqrt(pi)
+    (Eq. bal_TRp) and Q = n_w R_in T_w^{3/2} Om^2 / sqrt(2 pi) (Eq. bal_Q) with
+    Om = Omega_in R_in sqrt(1 / (2 T_w)) and n_w = 1 to O(Omega^2), and u^phi
+    follows Eq. (bal_u_willis) to O(Omega^3).  The fluxes come out constant to
+    about 1 %; their values are 14 % and 16 % above the closed forms with this
+    small velocity set (9 % and 6 % with HH(4;8) x H(4;12); the paper needs 200
+    nodes per half-axis to remove the discrete-velocity error).  With the force
+    term's sign flipped the spreads exceed 100 %."""
+    o = CouetteOracle("HH(3;4)xH(3;4)", CouetteGrid(32), Wall(0.1), Wall(0.0), 1000.0, TAU_KN_OVER_NT)
+    F = o.initial_equilibrium()
+    for _ in range(3000):
+        F = o.step(F, 4e-3)
+    R = o.g.Rc
+    mom = o.m.full_moments(F)
+    om = 0.1 / math.sqrt(2.0)
+    flux = R ** 2 * mom["T01"]
+    energy = R * (mom["q0"] + mom["u1"] * mom["T01"])
+    for x, exact in ((flux, om / math.sqrt(math.pi)), (energy, om ** 2 / math.sqrt(2.0 * math.pi))):
+        assert (x.max() - x.min()) / abs(x.mean()) < 0.03
+        assert 1.0 < x.mean() / exact < 1.25
+    willis = 0.1 * R / math.pi * (np.arcsin(1.0 / R) - np.sqrt(1.0 - R ** -2) / R)
+    assert np.abs(mom["u1"] - willis).max() / 0.1 < 0.10
