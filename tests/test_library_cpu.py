@@ -67,6 +67,31 @@ def test_node_reflection_used_by_the_split_contractions(spec):
         np.testing.assert_allclose(Kt[np.ix_(J, J)], Kt, rtol=0, atol=1e-12 * np.abs(Kt).max())
 
 
+@pytest.mark.parametrize("spec", ["HH(4;8)xH(4;20)", "HH(4;8)xH(4;12)", "HH(3;4)xH(3;4)"])
+def test_split_contraction_reproduces_the_full_one(spec):
+    """The recombination the fixed-shape stage kernels use, on the library's tables:
+    with e = f_k + f_Jk, o = f_k - f_Jk (k in the first half), P = (K[:, k] + K[:, Jk]) / 2
+    and M = (K[:, k] - K[:, Jk]) / 2 over the first-half rows,
+    axis 0 (K0 J = -J K0): (K0 f)_i = P e + M o, (K0 f)_Ji = M o - P e;
+    axis 1 (Kt1 J = J Kt1): (Kt1 f)_j = P e + M o, (Kt1 f)_Jj = P e - M o."""
+    m = vlb.vlb_parse_model(spec)
+    rng = np.random.default_rng(7)
+    for a, mat, anti in ((0, 2, True), (1, 3, False)):
+        tabs = vlb.vlb_axis_tables(m, a)
+        K, n = tabs[mat], len(tabs[0])
+        h = n // 2
+        J = np.array([(k + h) % n if m.kind[a] == vlb.VLB_HALF else n - 1 - k for k in range(n)])
+        P = 0.5 * (K[:h, :h] + K[:h][:, J[:h]])
+        M = 0.5 * (K[:h, :h] - K[:h][:, J[:h]])
+        f = rng.standard_normal(n)
+        e, o = f[:h] + f[J[:h]], f[:h] - f[J[:h]]
+        full = K @ f
+        scale = np.abs(full).max()
+        np.testing.assert_allclose(P @ e + M @ o, full[:h], rtol=0, atol=1e-12 * scale)
+        mirror = M @ o - P @ e if anti else P @ e - M @ o
+        np.testing.assert_allclose(mirror, full[J[:h]], rtol=0, atol=1e-12 * scale)
+
+
 def test_invalid_arguments_rejected_without_gpu():
     bad = [
         dict(grids=[dict(n_cells=2)]),
