@@ -136,14 +136,19 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
  * see the adjacent cell (zeroth-order extrapolation).  Cell (s, p) is cell
  * index p * n_lambda + s of the distribution layout.  Axis 0 must be half
  * range; kernels exist for 16 x 12 and 8 x 4 nodes (VLB_ERR_UNSUPPORTED
- * otherwise); n_lambda >= 3, n_xi >= 4.  Starts at f_eq(1, 0, T0). */
+ * otherwise); n_lambda >= 3, n_xi >= 4 and a multiple of 4.  Starts at f_eq(1, 0, T0). */
 vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const vlb_channel_grid* grid, double kn,
                               double n_in, double n_out, double T0, void* cuda_stream, vlb_ctx** out);
 
-/* Launch shapes of a channel context's stage kernel: cells per tile along
- * lambda (ts) and xi (tp) and threads per CTA; returns their number (0 for
- * Couette contexts, negative on error). */
+/* Launch shapes of a channel context's stage kernel, each CTA marching up
+ * ts lambda rows of a strip of tp xi-columns with nt threads; returns their
+ * number (0 for Couette contexts, negative on error).  Arrays may be NULL. */
 int vlb_channel_variants(const vlb_ctx* ctx, int* ts, int* tp, int* nt, int max);
+
+/* Force contraction of channel launch shape v: 1 on the tensor cores (single
+ * precision, TF32 with hi/lo operand splits), 0 on the CUDA cores (packed
+ * FP32x2, or FP64 in double precision); negative on error. */
+int vlb_channel_variant_tensor_cores(const vlb_ctx* ctx, int v);
 
 /* Total number of cells over all instances, nodes per cell (nq0 * nq1), and
  * the size in bytes of one distribution copy in the layout documented above. */
@@ -256,25 +261,30 @@ vlb_status vlb_set_variant(vlb_ctx* ctx, int variant);
  * (either pointer may be NULL). */
 vlb_status vlb_autotune(vlb_ctx* ctx, double dt, int reps, int* chosen, double* best_ms);
 
-/* nsteps (>= 1) TVD-RK3 steps of the context's instances from the caller's
- * device buffer f_in into the caller's device buffer f_out (distinct, both in
- * the documented layout and the context's real type; f_in is only read),
- * with time step dt > 0 for every instance.  The paper has no counterpart:
- * this entry point is for callers that cannot allocate device memory when
- * they step (their memory belongs to another allocator or to a full pool, or
- * the step runs where cudaMalloc is not allowed).  It allocates nothing: the
- * two intermediate stage buffers F^(1), F^(2) live in one static device array
- * of 64 MiB compiled into the library (every GPU that loads the library holds
- * it until the process exits), so 2 x total_cells x 2 x nvel x sizeof(real)
- * must not exceed 64 MiB, else VLB_ERR_UNSUPPORTED; nvel must be a multiple
- * of 4, else VLB_ERR_UNSUPPORTED.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls share the array and it keeps the last
- * call's contents (nothing in it needs to start at zero): calls that overlap
- * on the GPU -- two streams, two contexts, or a context's own vlb_step
- * running concurrently -- race on it.  Asynchronous on the context stream;
- * it also updates the context's per-instance time step to dt and its wall
- * densities (vlb_wall_density). */
+/* nsteps (>= 1) TVD-RK3 steps of the instances of a circular Couette context
+ * from the caller's device buffer f_in into the caller's device buffer f_out
+ * (distinct, both in the documented layout and the context's real type; f_in
+ * is only read), with a finite time step dt > 0 for every instance.  The paper
+ * has no counterpart: this entry point is for callers that cannot allocate
+ * device memory when they step (their memory belongs to another allocator or
+ * to a full pool, or the step runs where cudaMalloc is not allowed).  It
+ * allocates nothing: the two intermediate stage buffers F^(1), F^(2) live in
+ * one static device array of 64 MiB compiled into the library (every GPU that
+ * loads the library holds it until the process exits), so
+ * 2 x total_cells x 2 x nvel x sizeof(real) must not exceed 64 MiB, else
+ * VLB_ERR_UNSUPPORTED; nvel must be a multiple of 4, else VLB_ERR_UNSUPPORTED;
+ * a channel context gets VLB_ERR_UNSUPPORTED and nothing is launched.  The
+ * context's device must be the current device (else VLB_ERR_INVALID).  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), and a call whose dt differs from the context's
+ * current time step copies the instance descriptors and synchronises the
+ * stream (as vlb_set_dt does): make the first call, and any call that changes
+ * dt, outside stream capture.  All calls share the array and it keeps the
+ * last call's contents (nothing in it needs to start at zero): calls that
+ * overlap on the GPU -- two streams, two contexts, or a context's own
+ * vlb_step running concurrently -- race on it.  Asynchronous on the context
+ * stream otherwise; it also updates the context's per-instance time step to
+ * dt and its wall densities (vlb_wall_density). */
 vlb_status vlb_step_static_scratch(vlb_ctx* ctx, const void* f_in, void* f_out, double dt, long long nsteps);
 
 /* Number of kernels the last vlb_step / vlb_stage call launched. */

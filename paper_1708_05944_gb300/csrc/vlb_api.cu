@@ -248,27 +248,80 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   return VLB_OK;
 }
 
+// Rows per lambda segment and segments of a channel launch shape.  A fixed ts
+// is used as given (at least 3 rows per segment, the last one included); ts = 0
+// picks the segment count that minimises waves x (rows + 6) over the SMs of the
+// device, one resident CTA each: the 6 rows are the warm-up of a segment (window
+// rows below it and the equilibria of its first three rows).
+void channel_segments(const vlb_ctx* c, const ChanVariant& v, int* seglen, int* nseg) {
+  const int nl = c->cdesc.nl, nstrips = c->cdesc.nx / v.tp;
+  auto count = [&](int L) {  // segments of L rows, 0 if the last would be shorter than 3
+    const int n = (nl + L - 1) / L;
+    return nl - (n - 1) * L >= 3 ? n : 0;
+  };
+  if (v.ts > 0) {
+    int L = std::max(3, std::min(v.ts, nl));
+    int n = count(L);
+    if (n == 0) L = nl, n = 1;
+    *seglen = L, *nseg = n;
+    return;
+  }
+  const int sms = c->sms > 0 ? c->sms : 1;
+  long long best = -1;
+  *seglen = nl, *nseg = 1;
+  for (int want = 1; want <= nl / 3; ++want) {
+    const int L = (nl + want - 1) / want;
+    const int n = count(L);
+    if (n == 0) continue;
+    const long long waves = (static_cast<long long>(nstrips) * n + sms - 1) / sms;
+    const long long cost = waves * (L + 6);
+    if (best < 0 || cost < best) best = cost, *seglen = L, *nseg = n;
+  }
+}
+
 template <typename real>
 vlb_status do_chan_stage(vlb_ctx* c, int k, int prev, int out) {
   ChanArgs<real> a{};
   a.Fprev = static_cast<const real*>(c->F[prev]);
   a.Fl = static_cast<const real*>(c->F[c->cur]);
   a.Fout = static_cast<real*>(c->F[out]);
-  const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0}, cc[3] = {1.0, 0.25, 2.0 / 3.0};
-  a.ca = ca[k - 1], a.cb = cb[k - 1], a.cc = cc[k - 1];
-  a.caf = float(a.ca), a.cbf = float(a.cb), a.ccf = float(a.cc);
-  a.cd = c->cdesc;
-  a.cd.dt = c->inst[0].dt;
-  a.cd.dtf = float(a.cd.dt);
-  a.geo = c->d_cgeo;
-  a.geof = c->d_cgeof;
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cc[3] = {1.0, 0.25, 2.0 / 3.0};
+  a.ca = real(ca[k - 1]);
+  a.ccdt = real(cc[k - 1] * c->inst[0].dt);
+  a.tables = c->d_ctab;
+  if constexpr (sizeof(real) == 8) a.geo = c->d_cgeo; else a.geo = c->d_cgeof;
   a.nw = c->d_nw;
   a.err = c->d_err;
+  a.nl = c->cdesc.nl;
+  a.nx = c->cdesc.nx;
+  a.ikn = real(1.0 / c->cdesc.kn);
+  a.n_in = real(c->cdesc.n_in);
+  a.n_out = real(c->cdesc.n_out);
+  a.T0 = real(c->cdesc.T0);
   a.max_polls = 1ull << 26;
-  const void* kb = sizeof(real) == 4 ? (const void*)c->chanK32.data() : (const void*)c->chanK64.data();
-  cudaError_t e = launch_channel<real>(c->cvariants[c->variant], a, c->margs, kb, c->nq0, c->nq1, c->stream);
+  const ChanVariant& v = c->cvariants[c->variant];
+  channel_segments(c, v, &a.seglen, &a.nseg);
+  const int grid = (a.nx / v.tp) * a.nseg;
+  cudaError_t e = launch_channel<real>(v, a, c->chan_kp.data(), c->nq0, c->nq1, grid, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "channel stage kernel launch");
   c->launches += 1;
+  return VLB_OK;
+}
+
+// Rebuild the channel's table block (it carries f_eq(1, 0, T0)) and upload it
+// on the context stream.
+vlb_status upload_channel_tables(vlb_ctx* c) {
+  std::vector<unsigned char> tb;
+  const bool ok = c->prec == VLB_FP64 ? channel_tables<double>(c->nq0, c->nq1, c->ax, c->margs, c->cdesc.T0, &tb)
+                                      : channel_tables<float>(c->nq0, c->nq1, c->ax, c->margs, c->cdesc.T0, &tb);
+  if (!ok) return fail(c, VLB_ERR_UNSUPPORTED, "no channel kernel for this velocity set");
+  if (!c->d_ctab) {
+    VLB_CUDA(c, cudaMalloc(&c->d_ctab, tb.size()));
+    c->ctab_bytes = tb.size();
+  }
+  if (tb.size() != c->ctab_bytes) return fail(c, VLB_ERR_STATE, "channel table size changed");
+  VLB_CUDA(c, cudaMemcpyAsync(c->d_ctab, tb.data(), tb.size(), cudaMemcpyHostToDevice, c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   return VLB_OK;
 }
 
@@ -310,9 +363,9 @@ vlb_status check_err(vlb_ctx* c) {
 vlb_status compute_moments(vlb_ctx* c, double* dst) {
   cudaError_t e = c->prec == VLB_FP64
                       ? launch_moments<double>(static_cast<const double*>(c->F[c->last]), c->total_cells, c->Vp,
-                                               c->margs, dst, c->stream)
+                                               c->margs, dst, c->stream, c->cmap)
                       : launch_moments<float>(static_cast<const float*>(c->F[c->last]), c->total_cells, c->Vp,
-                                              c->margs, dst, c->stream);
+                                              c->margs, dst, c->stream, c->cmap);
   if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel launch");
   return VLB_OK;
 }
@@ -422,9 +475,9 @@ int spare_buffer(const vlb_ctx* c) {
 vlb_status convert(vlb_ctx* c, const void* src, void* dst, int to_deviation) {
   cudaError_t e = c->prec == VLB_FP64
                       ? launch_deviation<double>(static_cast<const double*>(src), static_cast<double*>(dst),
-                                                 c->total_cells, c->Vp, c->margs, to_deviation, c->stream)
+                                                 c->total_cells, c->Vp, c->margs, to_deviation, c->stream, c->cmap)
                       : launch_deviation<float>(static_cast<const float*>(src), static_cast<float*>(dst),
-                                                c->total_cells, c->Vp, c->margs, to_deviation, c->stream);
+                                                c->total_cells, c->Vp, c->margs, to_deviation, c->stream, c->cmap);
   if (e != cudaSuccess) return cuda_fail(c, e, "conversion kernel launch");
   return VLB_OK;
 }
@@ -530,6 +583,7 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     return fail(nullptr, VLB_ERR_UNSUPPORTED, "expansion order above 7");
 
   std::unique_ptr<vlb_ctx> c(new vlb_ctx);
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(nullptr, VLB_ERR_CUDA, "cudaGetDevice failed");
   c->model = *model;
   c->prec = prec;
   c->n_inst = n_inst;
@@ -676,21 +730,16 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
     return fail(nullptr, VLB_ERR_INVALID, "need Kn, reservoir densities and T0 positive");
   const int nq0 = axis_nodes(model, 0), nq1 = axis_nodes(model, 1);
   std::unique_ptr<vlb_ctx> c(new vlb_ctx);
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(nullptr, VLB_ERR_CUDA, "cudaGetDevice failed");
   c->kind = 1;
   c->model = *model;
   c->prec = prec;
   c->n_inst = 1;
   c->stream = static_cast<cudaStream_t>(cuda_stream);
   {
-    ChanVariant all[8];
-    const int n = channel_variants(nq0, nq1, all);
-    for (int i = 0; i < n; ++i) {
-      const size_t sm = prec == VLB_FP64 ? channel_smem_bytes<double>(all[i], nq0, nq1)
-                                         : channel_smem_bytes<float>(all[i], nq0, nq1);
-      if (sm > 0 && sm <= 227 * 1024 && nx % all[i].tp == 0) c->cvariants[c->n_cvariants++] = all[i];
-    }
-    if (c->n_cvariants == 0)
-      return fail(nullptr, VLB_ERR_UNSUPPORTED, "no channel kernel for this velocity set and n_xi (16x12 or 8x4 nodes)");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return fail(nullptr, VLB_ERR_CUDA, "cannot query the device");
   }
   for (int a = 0; a < 2; ++a)
     if (!build_axis(model->kind[a] == VLB_HALF ? 1 : 0, model->N[a], model->Q[a], &c->ax[a], &why))
@@ -700,6 +749,26 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
   c->V = nq0 * nq1;
   c->Vp = (c->V + 3) / 4 * 4;
   c->esize = prec == VLB_FP64 ? 8 : 4;
+  {
+    // launch shapes: shared memory within an SM's, whole strips of columns; the
+    // single-precision CUDA-core force needs the split force block, the double-precision
+    // kernel contracts on its own (its shapes are the tc = 0 ones)
+    const bool kp_ok = channel_force_pairs(nq0, nq1, c->ax, &c->chan_kp);
+    if (!kp_ok) c->chan_kp.assign(16384, 0);
+    ChanVariant all[8];
+    const int n = channel_variants(nq0, nq1, all);
+    for (int i = 0; i < n; ++i) {
+      const size_t sm = prec == VLB_FP64 ? channel_smem_bytes<double>(all[i], nq0, nq1)
+                                         : channel_smem_bytes<float>(all[i], nq0, nq1);
+      if (!(sm > 0 && sm <= 227 * 1024 && nx % all[i].tp == 0)) continue;
+      if (prec == VLB_FP64 && all[i].tc) continue;
+      if (prec == VLB_FP32_BULK && !all[i].tc && !kp_ok) continue;
+      c->cvariants[c->n_cvariants++] = all[i];
+    }
+    if (c->n_cvariants == 0)
+      return fail(nullptr, VLB_ERR_UNSUPPORTED,
+                  "no channel kernel for this velocity set and n_xi (16x12 or 8x4 nodes, n_xi a multiple of 4)");
+  }
   ModelArgs& m = c->margs;
   m.nq0 = nq0, m.nq1 = nq1, m.N0 = model->N[0], m.N1 = model->N[1];
   m.kind0 = 1, m.kind1 = model->kind[1] == VLB_HALF ? 1 : 0;
@@ -719,16 +788,6 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
     }
   }
   fill_reference(m);
-  {
-    std::vector<double> kd;
-    for (const std::vector<double>* v : {&c->ax[0].K, &c->ax[0].Kt, &c->ax[1].K, &c->ax[1].Kt})
-      kd.insert(kd.end(), v->begin(), v->end());
-    c->chanK64.resize(kd.size() * sizeof(double));
-    memcpy(c->chanK64.data(), kd.data(), c->chanK64.size());
-    std::vector<float> kf(kd.begin(), kd.end());
-    c->chanK32.resize(kf.size() * sizeof(float));
-    memcpy(c->chanK32.data(), kf.data(), c->chanK32.size());
-  }
   // geometry (Sec. VII.A-B): lambda(eta) = tanh(eta) / A, eta equidistant; xi equidistant; H/2 = 1
   const double A = grid->stretch_A, ea = atanh(A), re = grid->re_c;
   auto phi = [&](double x) { return 0.5 * (tanh(2.0) - tanh(2.0 - 30.0 * x / re)); };
@@ -761,12 +820,14 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
       g.idx = 1.0 / dchi;
       g.glxl = (g.bp - g.bm) / dchi;
       g.glxx = -(g.ap - g.am) / dl + (g.cp - g.cm) / dchi;
-      gd[size_t(p) * nl + s] = g;
+      gd[size_t(s) * nx + p] = g;  // device cell order: s * n_xi + p
       const double* src = &g.am;
-      float* dst = &gf[size_t(p) * nl + s].am;
+      float* dst = &gf[size_t(s) * nx + p].am;
       for (int k = 0; k < 12; ++k) dst[k] = float(src[k]);
     }
   }
+  c->cmap.nl = nl;
+  c->cmap.nx = nx;
   ChanDesc& cd = c->cdesc;
   cd.nl = nl, cd.nx = nx, cd.kn = kn, cd.n_in = n_in, cd.n_out = n_out, cd.T0 = T0, cd.dt = 0.0;
   cd.knf = float(kn), cd.n_inf = float(n_in), cd.n_outf = float(n_out), cd.T0f = float(T0), cd.dtf = 0.0f;
@@ -795,6 +856,10 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
   VLB_CUDA(cp, cudaMemsetAsync(c->d_nw, 0, sizeof(double) * nx, c->stream));
   VLB_CUDA(cp, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
   VLB_CUDA(cp, cudaStreamSynchronize(c->stream));
+  {
+    vlb_status ts = upload_channel_tables(cp);
+    if (ts != VLB_OK) return ts;
+  }
   vlb_status st = vlb_init_equilibrium(cp, 1.0, 0.0, 0.0, T0);
   if (st != VLB_OK) return st;
   *out = c.release();
@@ -872,7 +937,9 @@ vlb_status vlb_set_channel_reservoirs(vlb_ctx* c, double n_in, double n_out, dou
   c->cdesc.n_in = n_in, c->cdesc.n_inf = float(n_in);
   c->cdesc.n_out = n_out, c->cdesc.n_outf = float(n_out);
   c->cdesc.T0 = T0, c->cdesc.T0f = float(T0);
-  return drop_channel_graphs(c);
+  vlb_status st = drop_channel_graphs(c);
+  if (st != VLB_OK) return st;
+  return upload_channel_tables(c);
 }
 
 vlb_status vlb_init_equilibrium(vlb_ctx* c, double n0, double u0, double u1, double T0) {
@@ -910,9 +977,9 @@ vlb_status vlb_init_from_moments(vlb_ctx* c, const double* n, const double* u0, 
   const double* dq = q0 ? dev + 4 * N : nullptr;
   cudaError_t e = c->prec == VLB_FP64
                       ? launch_seed<double>(static_cast<double*>(c->F[c->cur]), c->total_cells, c->Vp, c->margs, dev,
-                                            dev + N, dev + 2 * N, dev + 3 * N, dq, c->stream)
+                                            dev + N, dev + 2 * N, dev + 3 * N, dq, c->stream, c->cmap)
                       : launch_seed<float>(static_cast<float*>(c->F[c->cur]), c->total_cells, c->Vp, c->margs, dev,
-                                           dev + N, dev + 2 * N, dev + 3 * N, dq, c->stream);
+                                           dev + N, dev + 2 * N, dev + 3 * N, dq, c->stream, c->cmap);
   if (e != cudaSuccess) return cuda_fail(c, e, "seed kernel launch");
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->last = c->cur;
@@ -957,7 +1024,7 @@ vlb_status vlb_read_f(vlb_ctx* c, void* f, int on_device) {
 vlb_status vlb_set_dt(vlb_ctx* c, const double* dt) {
   if (!c || !dt) return fail(c, VLB_ERR_INVALID, "null argument");
   for (int i = 0; i < c->n_inst; ++i)
-    if (!(dt[i] > 0.0)) return fail(c, VLB_ERR_INVALID, "time steps must be positive");
+    if (!(dt[i] > 0.0) || !std::isfinite(dt[i])) return fail(c, VLB_ERR_INVALID, "time steps must be finite and positive");
   for (int i = 0; i < c->n_inst; ++i) {
     c->inst[i].dt = dt[i];
     c->inst[i].dt_f = float(dt[i]);
@@ -969,7 +1036,7 @@ vlb_status vlb_set_dt(vlb_ctx* c, const double* dt) {
 }
 
 static vlb_status apply_dt(vlb_ctx* c, double dt) {
-  if (dt < 0.0 || std::isnan(dt)) return fail(c, VLB_ERR_INVALID, "dt must be >= 0");
+  if (dt < 0.0 || !std::isfinite(dt)) return fail(c, VLB_ERR_INVALID, "dt must be finite and >= 0");
   if (dt > 0.0) {
     bool change = false;
     for (int i = 0; i < c->n_inst; ++i) change |= c->inst[i].dt != dt;
@@ -1155,18 +1222,27 @@ int vlb_channel_variants(const vlb_ctx* c, int* ts, int* tp, int* nt, int max) {
   if (!c) return VLB_ERR_INVALID;
   if (c->kind != 1) return 0;
   for (int v = 0; v < c->n_cvariants && v < max; ++v) {
-    if (ts) ts[v] = c->cvariants[v].ts;
+    int L = 0, n = 0;
+    channel_segments(c, c->cvariants[v], &L, &n);
+    if (ts) ts[v] = L;
     if (tp) tp[v] = c->cvariants[v].tp;
     if (nt) nt[v] = c->cvariants[v].nt;
   }
   return c->n_cvariants;
 }
 
+int vlb_channel_variant_tensor_cores(const vlb_ctx* c, int v) {
+  if (!c || c->kind != 1 || v < 0 || v >= c->n_cvariants) return VLB_ERR_INVALID;
+  return c->cvariants[v].tc;
+}
+
 int vlb_variants(const vlb_ctx* c, int* tc, int* nt, int* persistent, int max) {
   if (!c) return VLB_ERR_INVALID;
   if (c->kind == 1) {
     for (int v = 0; v < c->n_cvariants && v < max; ++v) {
-      if (tc) tc[v] = c->cvariants[v].ts * c->cvariants[v].tp;
+      int L = 0, n = 0;
+      channel_segments(c, c->cvariants[v], &L, &n);
+      if (tc) tc[v] = L * c->cvariants[v].tp;
       if (nt) nt[v] = c->cvariants[v].nt;
       if (persistent) persistent[v] = 0;
     }
@@ -1339,6 +1415,7 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_geof);
   cudaFree(c->d_cgeo);
   cudaFree(c->d_cgeof);
+  cudaFree(c->d_ctab);
   for (int b = 0; b < 3; ++b)
     if (c->graph_exec[b]) cudaGraphExecDestroy(c->graph_exec[b]);
   if (c->capture_stream) cudaStreamDestroy(c->capture_stream);

@@ -1,24 +1,31 @@
 // One TVD-RK3 stage of the gradually expanding channel in the vielbein frame
-// (Sec. VII.A-C, Eq. canalie_boltz), fused into one kernel per tile of
-// TS (wall-normal, lambda) x TP (streamwise, xi) cells with all momenta:
+// (Sec. VII.A-C, Eq. canalie_boltz), as a marching kernel: each CTA owns a
+// strip of TP adjacent xi-columns and walks up a segment of lambda rows
+// (wall-normal, the contiguous direction of the cell index p * n_lambda + s).
+// For every row s it
 //
-//   bulk-copy the tile's columns with a 3-cell lambda halo and 3 xi-halo
-//   columns -> moments and the lambda-axis force contractions
-//   -> equilibrium moment vectors and the xi-axis force contractions
-//   -> equilibrium factors; centreline mirror; wall n_w per column; inlet and
-//      outlet reservoir ghosts
-//   -> WENO-5 in lambda (walking the column) and in xi, chi flux differences,
-//      BGK, RK3 combine -> bulk store.
+//   - pushes row s+3 into a per-thread six-row register window (f', f'') of
+//     its (column, velocity), so the lambda-WENO-5 interface value s+1/2
+//     comes from registers and every lambda interface is reconstructed once;
+//   - reduces the moments of row s+3 and builds its truncated equilibrium
+//     (Sec. IV.D) three rows ahead of use;
+//   - reconstructs the xi interfaces of row s from a shared-memory ring that
+//     bulk copies (cp.async.bulk, mbarrier completion) fill one row ahead;
+//   - contracts the momentum-space force matrices of Eq. (canalie_boltz)
+//     over the row's cells on the tensor cores (single precision:
+//     mma.sync m16n8k8 TF32 with a hi/lo split of both operands, three
+//     products per tile) or in FP64 on the CUDA cores (double precision);
+//   - combines advection, force, BGK relaxation and the RK3 weights and
+//     stores the cell's updated populations straight to global memory.
+//
+// Boundaries: the centreline mirror (Sec. VII.C.3) fills the window at the
+// bottom of the march, the diffuse wall (Sec. VII.C.4) at its top with n_w per
+// column from the zero-mass-flux balance, and the inlet/outlet reservoirs fill
+// the xi-halo cells of the first and last strip.
 //
 // Distribution buffers hold the deviation D = F - R from the rest state
-// (ModelArgs), as in the Couette kernel, with (f', f'') interleaved per
-// velocity (pair_t).  The arithmetic here is scalar per field: a pair-wise
-// phase D (as in the Couette kernel) gave wrong boundary ghosts for the
-// 2 x 4-cell tile shape of the 16 x 12 velocity set while every other shape
-// matched the oracle; the cause was not found, and the scalar form matches
-// the oracle for every shape.
-//
-// Cell (s, p) of the grid has global index p * n_lambda + s (lambda fastest).
+// (ModelArgs), with (f', f'') interleaved per velocity: a cell row is
+// 2 Q0 Q1 reals, element (i, j, d) at 2 (i Q1 + j) + d.
 #pragma once
 #include "vlb_device.cuh"
 
@@ -35,7 +42,49 @@ struct ChanCell {
   T glxl, glxx;      // Gamma_{l x l}, Gamma_{l x x}
   T pad0, pad1;
 };
+static_assert(sizeof(ChanCell<float>) == 48 && sizeof(ChanCell<double>) == 96, "bulk-copied geometry rows");
 
+// Tile counts of the force contractions of one cell on m16n8k8 tensor-core tiles.
+// lambda: D = [K0; Kt0] F, rows of the A operand interleaved per m-tile t as
+//   (K0 rows 8t..8t+7, Kt0 rows 8t..8t+7), F as the B operand [i'][2 j + d];
+// xi: D = F [K1^T | Kt1^T], F as the A operand with rows (i, d) of m-tile t =
+//   (8t + r/2, r & 1), the B operand [j'][2 j + e] (e = 0: K1, e = 1: Kt1), j' >= Q1 zero.
+template <int Q0, int Q1>
+struct ChanShape {
+  static constexpr int V = Q0 * Q1;
+  static constexpr int ROW = 2 * V;         // reals per cell row
+  static constexpr int NWC = V / 32;        // warps per column (one velocity per thread)
+  static constexpr int MT = Q0 / 8;         // m-tiles (both contractions)
+  static constexpr int KKL = Q0 / 8;        // k-steps of the lambda contraction
+  static constexpr int NN = Q1 / 4;         // n-tiles (both contractions)
+  static constexpr int KKX = (Q1 + 7) / 8;  // k-steps of the xi contraction
+  static constexpr int S = 2 * NN;          // force subtasks per cell (one n-tile each)
+  static constexpr int EQW = Q0 + Q1 + 4;   // per-cell equilibrium record: n g0, g1, T, 1/tau, u^xi, pad
+  static_assert(V % 32 == 0 && Q0 % 8 == 0 && Q1 % 4 == 0, "velocity set shape of the channel kernel");
+  static_assert(Q0 + Q1 <= 32, "one lane per equilibrium factor");
+};
+
+// Model tables of a channel context, in device memory, bulk-copied into each
+// CTA's shared memory.  gw0/gw1 are the factors of f_eq(1, 0, T0), the wall and
+// reservoir equilibrium at rest (they change with T0).
+template <typename real, int Q0, int Q1>
+struct alignas(16) ChanTables {
+  using S = ChanShape<Q0, Q1>;
+  uint32_t fl[S::MT][S::KKL][2][32][4];  // lambda A fragments, [hi|lo] TF32 bit patterns
+  uint32_t fx[S::KKX][S::NN][2][32][2];  // xi B fragments, [hi|lo]
+  real K0[Q0 * Q0], Kt0[Q0 * Q0];        // d/dp^lambda, d/dp^lambda (p^lambda .)
+  real K1[Q1 * Q1], Kt1[Q1 * Q1];        // d/dp^xi, d/dp^xi (p^xi .)
+  real p0[Q0], p1[Q1], iw0[Q0], iw1[Q1], w0[Q0], w1[Q1];
+  real tab0[Q0 * MAXN], tab1[Q1 * MAXN];  // equilibrium tables [k][s]
+  real gw0[Q0], gw1[Q1];
+  double wall_den;  // sum over p^lambda < 0 of gw0 p^lambda times sum of gw1: incoming flux of f_eq(1, 0, T0)
+  double ref_flux_pos;  // sum over p^lambda > 0 of p^lambda R (ModelArgs)
+  // sums of R (ModelArgs: n, rho u0, rho u1, energy) as (hi, lo) in the bulk type (lo = 0 in double)
+  real ref_hi[4], ref_lo[4];
+  int N0, N1, kind0, kind1;
+};
+
+// Host-side description of a channel context: grid size, Kn, time step, reservoirs.
 struct ChanDesc {
   int nl, nx;
   double kn, dt, n_in, n_out, T0;
@@ -44,485 +93,764 @@ struct ChanDesc {
 
 template <typename real>
 struct ChanArgs {
-  const real* Fprev;
-  const real* Fl;
+  const real* Fprev;  // distribution L acts on
+  const real* Fl;     // F_l of the step (read when ca != 0)
   real* Fout;
-  double ca, cb, cc;
-  float caf, cbf, ccf;
-  ChanDesc cd;
-  const ChanCell<double>* geo;
-  const ChanCell<float>* geof;
+  const void* tables;  // ChanTables of the context's shape
+  const ChanCell<real>* geo;
   double* nw;  // per column
   unsigned* err;
+  int nl, nx;
+  int seglen;  // rows per lambda segment (the last one may be shorter, >= 3 rows)
+  int nseg;
+  // Fout = F_prev + ca (F_l - F_prev) + ccdt L[F_prev] (see StageArgs)
+  real ca, ccdt;
+  real ikn, n_in, n_out, T0;  // 1/Kn, reservoir densities, wall and reservoir temperature
   unsigned long long max_polls;
 };
 
-template <typename real, int Q0, int Q1>
-struct ChanK {
-  real K0[Q0 * Q0], Kt0[Q0 * Q0];  // d/dp^lambda, d/dp^lambda (p^lambda .)
-  real K1[Q1 * Q1], Kt1[Q1 * Q1];  // d/dp^xi, d/dp^xi (p^xi .)
-};
-
-template <typename real, int TS, int TP, int Q0, int Q1, int NT>
+// Shared-memory carve-up of a CTA, identical on host and device.  The ring holds
+// rows s .. s+3+PD of the strip, each with its xi-halo (TP + 6 cells): row s for
+// the xi reconstruction and the force, s+1 for the reservoir ghosts, s+3 for the
+// window, and PD rows in flight (bulk copies issued PD steps ahead).
+template <typename real, int Q0, int Q1, int TP>
 struct ChanSmem {
-  static constexpr int NW = NT / 32;
-  static constexpr int V = Q0 * Q1;
-  static constexpr int VP = (V + 3) / 4 * 4;
-  static constexpr int ROW = 2 * VP;
-  static constexpr int NCS = TP * (TS + 6) + 6 * TS;  // cell slots in shared memory
-  static constexpr int NC = TS * TP;                  // owned cells
-  static constexpr size_t tile_off = 16;
-  static constexpr size_t lbuf_off = tile_off + size_t(NCS) * ROW * sizeof(real);
-  static constexpr size_t fl_off = lbuf_off + size_t(NC) * ROW * sizeof(real);
-  static constexpr size_t dbl_off = (fl_off + size_t(NC) * ROW * sizeof(real) + 15) & ~size_t(15);
-  // doubles: reduction (NW*4 + TP*NW), wall n_w (TP), scalars (16), equilibrium sum targets (NC)
-  static constexpr size_t n_dbl = NW * 4 + TP * NW + TP + 16 + NC;
-  static constexpr size_t real_off = dbl_off + n_dbl * sizeof(double);
-  // reals: p0, p1, 1/w0, 1/w1 (Q each), tables (Q*MAXN each), per cell: 10 geometry + n, T, u0, u1, 1/tau,
-  // g0 (Q0), g1 (Q1), moment vectors (4*MAXN); boundary: wall factors (Q0 + Q1), inlet/outlet factors (TS*Q1 each),
-  // weights (Q0 + Q1)
-  static constexpr size_t n_real = 2 * Q0 + 2 * Q1 + (Q0 + Q1) * MAXN + size_t(NC) * (15 + Q0 + Q1 + 4 * MAXN) +
-                                   (Q0 + Q1) + 2 * size_t(TS) * Q1 + Q0 + Q1 + 2 * TS + 8;
-  static constexpr size_t bytes = real_off + n_real * sizeof(real);
+  using S = ChanShape<Q0, Q1>;
+  using Tab = ChanTables<real, Q0, Q1>;
+  static constexpr bool F32 = sizeof(real) == 4;
+  static constexpr int NT = (TP + 1) * S::V;  // TP column groups and one extra group
+  static constexpr int PD = F32 ? 2 : 1;      // prefetch distance in rows
+  static constexpr int NRING = 4 + PD;        // ring rows
+  static constexpr int NB = PD + 1;           // mbarriers of the step groups (one more for the prologue)
+  static constexpr int NEQ = 4;               // equilibrium records of rows s .. s+3
+  static constexpr int RC = TP + 6;           // cells of a ring row
+  static constexpr size_t al(size_t x) { return (x + 15) & ~size_t(15); }
+  static constexpr size_t rowb = size_t(S::ROW) * sizeof(real);
+  static constexpr size_t bar_off = 0;
+  static constexpr size_t tab_off = 32;
+  static constexpr size_t ring_off = al(tab_off + sizeof(Tab));
+  static constexpr size_t geo_off = ring_off + size_t(NRING) * RC * rowb;
+  static constexpr size_t xif_off = al(geo_off + size_t(NRING) * TP * sizeof(ChanCell<real>));
+  static constexpr size_t lbl_off = xif_off + size_t(TP + 1) * S::V * 2 * sizeof(real);
+  static constexpr size_t lbuf_rows = F32 ? TP : 0;  // tensor-core force results (single precision only)
+  static constexpr size_t lbx_off = lbl_off + lbuf_rows * rowb;
+  static constexpr size_t eq_off = lbx_off + lbuf_rows * rowb;
+  static constexpr size_t res_off = al(eq_off + size_t(NEQ) * TP * S::EQW * sizeof(real));
+  static constexpr size_t mvs_off = al(res_off + size_t(NEQ) * 2 * Q1 * sizeof(real));
+  static constexpr size_t red_off = al(mvs_off + size_t(TP + 2) * 4 * MAXN * sizeof(real));
+  static constexpr size_t wred_off = al(red_off + size_t(2) * TP * S::NWC * 4 * sizeof(real));
+  static constexpr size_t nwv_off = al(wred_off + size_t(TP) * S::NWC * sizeof(real));
+  static constexpr size_t bytes = al(nwv_off + size_t(TP) * sizeof(double));
+  static_assert(sizeof(Tab) % 16 == 0, "tables are one bulk copy");
+  static_assert(rowb % 16 == 0 && (TP * sizeof(ChanCell<real>)) % 16 == 0, "rows are bulk copies");
+  static_assert(ring_off % 16 == 0 && geo_off % 16 == 0, "bulk destinations are 16-byte aligned");
+  static_assert(xif_off % 16 == 0 && lbl_off % 16 == 0 && lbx_off % 16 == 0, "pair arrays are aligned");
+  static_assert(bar_off + (NB + 1) * sizeof(uint64_t) <= tab_off, "mbarriers fit before the tables");
+  static_assert(TP >= 3, "the inlet/outlet ghosts of a strip come from its own first/last column");
+  static_assert(NT <= 1024, "one thread per (column, velocity) and an extra group");
 };
 
-template <typename real, int TS, int TP, int Q0, int Q1, int NT>
-__global__ void __launch_bounds__(NT) channel_stage_kernel(const __grid_constant__ ChanArgs<real> a,
-                                                           const __grid_constant__ ModelArgs m,
-                                                           const __grid_constant__ ChanK<real, Q0, Q1> kk) {
-  using L = ChanSmem<real, TS, TP, Q0, Q1, NT>;
-  constexpr int NW = L::NW, V = L::V, VP = L::VP, ROW = L::ROW, NC = L::NC;
-  constexpr bool F32 = sizeof(real) == 4;
+// Moment vector of the truncated equilibrium on one axis (the recurrences of
+// eq_moment_vector) with the loop unrolled to MAXN terms, the 1/l factors as
+// constants and one reciprocal of T: no division on the per-cell path.
+template <typename R>
+__device__ __forceinline__ void eq_moments_fast(int kind, int N, R u, R T, R* m) {
+  if (kind == 0) {
+    R a = R(1), b = u;
+    m[0] = a;
+    m[1] = b;
+#pragma unroll
+    for (int l = 2; l < MAXN; ++l) {
+      const R x = (u * b + (T - R(1)) * a) * R(1.0 / l);
+      if (l <= N) m[l] = x;
+      a = b;
+      b = x;
+    }
+  } else {
+    const R iT = rcp_rn(T);
+    const R is2T = rsqrt_t(R(2) * T);
+    const R g0 = exp_t(-R(0.5) * u * u * iT) * is2T * R(0.56418958354775628695);  // N(0; u, T) = e^.. / sqrt(2 pi T)
+    R a = R(0.5) * (R(1) + erf_t<R>(u * is2T));
+    R b = u * a + T * g0;
+    m[0] = a;
+    m[1] = b;
+#pragma unroll
+    for (int l = 2; l < MAXN; ++l) {
+      const R x = u * b + R(l - 1) * T * a;
+      if (l <= N) m[l] = x;
+      a = b;
+      b = x;
+    }
+  }
+}
+
+// Force matrices of the channel split by the reflection of each axis (see
+// KArgs): with J the node permutation p -> -p, K0 J = -J K0 and K1 J = -J K1
+// (derivatives), Kt0 J = J Kt0 and Kt1 J = J Kt1 (derivatives of p f).  On the
+// even and odd parts e_k = f_k + f_Jk, o_k = f_k - f_Jk (k over the first half):
+//   P[i][k] = (K[i][k] + K[i][Jk]) / 2,  M[i][k] = (K[i][k] - K[i][Jk]) / 2,
+//   odd K:  (K f)_i = P e + M o,  (K f)_Ji = M o - P e;
+//   even K: (K f)_i = P e + M o,  (K f)_Ji = P e - M o.
+// Every coefficient is duplicated into a pair, the operand of a packed fma over
+// (f', f''); the block travels as a kernel parameter, so the coefficients are
+// uniform constant-bank operands.
+template <int Q0, int Q1>
+struct ChanKP {
+  static constexpr int H0 = Q0 / 2, H1 = Q1 / 2;
+  float2 P0[H0 * H0], M0[H0 * H0], Pt0[H0 * H0], Mt0[H0 * H0];  // K0, Kt0: [i][k]
+  float2 P1[H1 * H1], M1[H1 * H1], Pt1[H1 * H1], Mt1[H1 * H1];  // K1, Kt1: [j][k]
+};
+
+// lambda force task of column j of one cell on the CUDA cores: out[(i, j)] =
+// G_lxx (p^xi_j)^2 (K0 f)_i + G_lxl p^xi_j (Kt0 f)_i for both fields.
+template <int Q0, int Q1>
+__device__ __forceinline__ void force_lambda_cc(const ChanKP<Q0, Q1>& kp, const float* F, int j, float wa, float wb,
+                                                float* out) {
+  constexpr int H = Q0 / 2;
+  float2 e[H], o[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float2 f = p_load(F + 2 * (k * Q1 + j)), g = p_load(F + 2 * ((k + H) * Q1 + j));
+    e[k] = p_add(f, g);
+    o[k] = p_sub(f, g);
+  }
+  const float2 WA = p_set(wa), WB = p_set(wb);
+#pragma unroll
+  for (int i = 0; i < H; ++i) {
+    float2 A = p_mul(kp.P0[i * H], e[0]), B = p_mul(kp.M0[i * H], o[0]);
+    float2 C = p_mul(kp.Pt0[i * H], e[0]), D = p_mul(kp.Mt0[i * H], o[0]);
+#pragma unroll
+    for (int k = 1; k < H; ++k) {
+      A = p_fma(kp.P0[i * H + k], e[k], A);
+      B = p_fma(kp.M0[i * H + k], o[k], B);
+      C = p_fma(kp.Pt0[i * H + k], e[k], C);
+      D = p_fma(kp.Mt0[i * H + k], o[k], D);
+    }
+    // row i: wa (A + B) + wb (C + D); row Ji: wa (B - A) + wb (C - D)
+    p_store(out + 2 * (i * Q1 + j), p_fma(WA, p_add(A, B), p_mul(WB, p_add(C, D))));
+    p_store(out + 2 * ((i + H) * Q1 + j), p_fma(WA, p_sub(B, A), p_mul(WB, p_sub(C, D))));
+  }
+}
+
+// xi force task of row i of one cell on the CUDA cores: out[(i, j)] =
+// -G_lxx p^lambda_i (Kt1 f)_j - G_lxl (p^lambda_i)^2 (K1 f)_j for both fields
+// (wa = -G_lxx p^lambda_i, wb = -G_lxl (p^lambda_i)^2).
+template <int Q0, int Q1>
+__device__ __forceinline__ void force_xi_cc(const ChanKP<Q0, Q1>& kp, const float* F, int i, float wa, float wb,
+                                            float* out) {
+  constexpr int H = Q1 / 2;
+  float2 e[H], o[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float2 f = p_load(F + 2 * (i * Q1 + k)), g = p_load(F + 2 * (i * Q1 + Q1 - 1 - k));
+    e[k] = p_add(f, g);
+    o[k] = p_sub(f, g);
+  }
+  const float2 WA = p_set(wa), WB = p_set(wb);
+#pragma unroll
+  for (int j = 0; j < H; ++j) {
+    float2 A = p_mul(kp.P1[j * H], e[0]), B = p_mul(kp.M1[j * H], o[0]);
+    float2 C = p_mul(kp.Pt1[j * H], e[0]), D = p_mul(kp.Mt1[j * H], o[0]);
+#pragma unroll
+    for (int k = 1; k < H; ++k) {
+      A = p_fma(kp.P1[j * H + k], e[k], A);
+      B = p_fma(kp.M1[j * H + k], o[k], B);
+      C = p_fma(kp.Pt1[j * H + k], e[k], C);
+      D = p_fma(kp.Mt1[j * H + k], o[k], D);
+    }
+    // K1 odd: (K1 f)_j = A + B, (K1 f)_Jj = B - A; Kt1 even: (Kt1 f)_j = C + D, (Kt1 f)_Jj = C - D
+    p_store(out + 2 * (i * Q1 + j), p_fma(WA, p_add(C, D), p_mul(WB, p_add(A, B))));
+    p_store(out + 2 * (i * Q1 + Q1 - 1 - j), p_fma(WA, p_sub(C, D), p_mul(WB, p_sub(B, A))));
+  }
+}
+
+// ------------------------------------------------------------------ tensor-core helpers
+__device__ __forceinline__ uint32_t tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+// x = hi + lo with hi, lo TF32 (hi carries the top 11 significand bits, lo the next 11)
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = tf32_rna(x);
+  lo = tf32_rna(__fsub_rn(x, __uint_as_float(hi)));
+}
+__device__ __forceinline__ void mma_tf32(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Force subtask of one cell on the tensor cores (single precision): n-tile nn of
+// the lambda contraction (k < NN) or of the xi contraction (k >= NN), written to
+// fl_out (lambda part, pairs) or fx_out (xi part, scalars):
+//   lambda: G_lxx (p^xi)^2 K0 f + G_lxl p^xi Kt0 f,
+//   xi:    -G_lxx p^lambda Kt1 f - G_lxl (p^lambda)^2 K1 f    (Eq. canalie_boltz).
+template <int Q0, int Q1>
+__device__ __forceinline__ void force_subtask_tc(const ChanTables<float, Q0, Q1>& tb, const float* F, float glxx,
+                                                 float glxl, int k, int lane, float* fl_out, float* fx_out) {
+  using S = ChanShape<Q0, Q1>;
+  const int g = lane >> 2, tq = lane & 3;
+  float acc[S::MT][4];
+#pragma unroll
+  for (int t = 0; t < S::MT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.0f;
+  if (k < S::NN) {
+    const int nn = k;
+#pragma unroll
+    for (int kk = 0; kk < S::KKL; ++kk) {
+      uint32_t bh0, bl0, bh1, bl1;
+      tf32_split(F[(8 * kk + tq) * (2 * Q1) + 8 * nn + g], bh0, bl0);
+      tf32_split(F[(8 * kk + tq + 4) * (2 * Q1) + 8 * nn + g], bh1, bl1);
+#pragma unroll
+      for (int t = 0; t < S::MT; ++t) {
+        const uint4 h4 = *reinterpret_cast<const uint4*>(tb.fl[t][kk][0][lane]);
+        const uint4 l4 = *reinterpret_cast<const uint4*>(tb.fl[t][kk][1][lane]);
+        const uint32_t ah[4] = {h4.x, h4.y, h4.z, h4.w}, alo[4] = {l4.x, l4.y, l4.z, l4.w};
+        mma_tf32(acc[t], alo, bh0, bh1);
+        mma_tf32(acc[t], ah, bl0, bl1);
+        mma_tf32(acc[t], ah, bh0, bh1);
+      }
+    }
+    const int j = 4 * nn + tq;
+    const float px = tb.p1[j];
+    const float wa = glxx * px * px, wb = glxl * px;
+#pragma unroll
+    for (int t = 0; t < S::MT; ++t) {
+      const int i = 8 * t + g;
+      float2 o;
+      o.x = fmaf(wa, acc[t][0], wb * acc[t][2]);
+      o.y = fmaf(wa, acc[t][1], wb * acc[t][3]);
+      *reinterpret_cast<float2*>(fl_out + 2 * (i * Q1 + j)) = o;
+    }
+  } else {
+    const int nn = k - S::NN;
+    const int d = g & 1;
+#pragma unroll
+    for (int kk = 0; kk < S::KKX; ++kk) {
+      const uint2 bh = *reinterpret_cast<const uint2*>(tb.fx[kk][nn][0][lane]);
+      const uint2 bl = *reinterpret_cast<const uint2*>(tb.fx[kk][nn][1][lane]);
+      const int ja = 8 * kk + tq, jb = ja + 4;
+#pragma unroll
+      for (int t = 0; t < S::MT; ++t) {
+        const int ia = 8 * t + (g >> 1), ib = ia + 4;
+        const float x0 = ja < Q1 ? F[ia * (2 * Q1) + 2 * ja + d] : 0.0f;
+        const float x1 = ja < Q1 ? F[ib * (2 * Q1) + 2 * ja + d] : 0.0f;
+        const float x2 = jb < Q1 ? F[ia * (2 * Q1) + 2 * jb + d] : 0.0f;
+        const float x3 = jb < Q1 ? F[ib * (2 * Q1) + 2 * jb + d] : 0.0f;
+        uint32_t ah[4], alo[4];
+        tf32_split(x0, ah[0], alo[0]);
+        tf32_split(x1, ah[1], alo[1]);
+        tf32_split(x2, ah[2], alo[2]);
+        tf32_split(x3, ah[3], alo[3]);
+        mma_tf32(acc[t], alo, bh.x, bh.y);
+        mma_tf32(acc[t], ah, bl.x, bl.y);
+        mma_tf32(acc[t], ah, bh.x, bh.y);
+      }
+    }
+    const int j = 4 * nn + tq;
+#pragma unroll
+    for (int t = 0; t < S::MT; ++t) {
+      const int ia = 8 * t + (g >> 1), ib = ia + 4;
+      const float pa = tb.p0[ia], pb = tb.p0[ib];
+      fx_out[2 * (ia * Q1 + j) + d] = -fmaf(glxx * pa, acc[t][1], glxl * pa * pa * acc[t][0]);
+      fx_out[2 * (ib * Q1 + j) + d] = -fmaf(glxx * pb, acc[t][3], glxl * pb * pb * acc[t][2]);
+    }
+  }
+}
+
+// Geometry of one cell into registers with vector loads (12 reals).
+template <typename real>
+__device__ __forceinline__ void load_geo(const ChanCell<real>* g, real* o) {
+  if constexpr (sizeof(real) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(g);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float4 x = q[k];
+      o[4 * k] = x.x, o[4 * k + 1] = x.y, o[4 * k + 2] = x.z, o[4 * k + 3] = x.w;
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(g);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const double2 x = q[k];
+      o[2 * k] = x.x, o[2 * k + 1] = x.y;
+    }
+  }
+}
+enum { G_AM = 0, G_AP, G_BM, G_BP, G_CM, G_CP, G_IDL, G_IDX, G_GLXL, G_GLXX };
+
+// ------------------------------------------------------------------ the stage kernel
+// Device cell (s, p) of the channel is s * n_xi + p (xi fastest), so the cells of a
+// strip's row and its xi-halo are one contiguous bulk copy.
+//
+// TC selects the single-precision force contraction: true, the tensor cores
+// (mma.sync TF32, three products per tile) on the column-group warps; false,
+// packed FP32x2 fmas with the split matrices of kp on the extra warps.  The
+// double-precision kernel contracts in FP64 on the column-group threads.
+template <typename real, int Q0, int Q1, int TP, bool TC>
+__global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
+    channel_stage_kernel(const __grid_constant__ ChanArgs<real> a, const __grid_constant__ ChanKP<Q0, Q1> kp) {
+  using S = ChanShape<Q0, Q1>;
+  using L = ChanSmem<real, Q0, Q1, TP>;
+  using Tab = ChanTables<real, Q0, Q1>;
+  using P = pair_t<real>;
+  constexpr int V = S::V, ROW = S::ROW, NWC = S::NWC, EQW = S::EQW;
+  constexpr int NMAIN = TP * V;    // threads of the column groups
+  constexpr int NMW = NMAIN / 32;  // their warps
+  constexpr int PD = L::PD, NRING = L::NRING, NB = L::NB, RC = L::RC;
+  constexpr bool F32 = L::F32;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nl = a.cd.nl, nx = a.cd.nx;
 
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  real* tile = reinterpret_cast<real*>(smem + L::tile_off);
-  real* lbuf = reinterpret_cast<real*>(smem + L::lbuf_off);
-  real* flb = reinterpret_cast<real*>(smem + L::fl_off);
-  double* red = reinterpret_cast<double*>(smem + L::dbl_off);  // NW*4 + TP*NW
-  double* nwv = red + NW * 4 + TP * NW;                           // TP
-  double* dsc = nwv + TP;                                         // 16 scalars
-  double* cnd = dsc + 16;                                         // [q] target of sum g0n * sum g1
-  real* rp = reinterpret_cast<real*>(smem + L::real_off);
-  real* p0r = rp;
-  real* p1r = p0r + Q0;
-  real* iw0 = p1r + Q1;
-  real* iw1 = iw0 + Q0;
-  real* tb0 = iw1 + Q1;
-  real* tb1 = tb0 + Q0 * MAXN;
-  real* geo = tb1 + Q1 * MAXN;        // [q][10]
-  real* cn = geo + NC * 10;           // [q]
-  real* cT = cn + NC;
-  real* cu0 = cT + NC;
-  real* cu1 = cu0 + NC;
-  real* citau = cu1 + NC;
-  real* g0n = citau + NC;             // [q][Q0] n g_lambda
-  real* g1 = g0n + NC * Q0;           // [q][Q1]
-  real* mv = g1 + NC * Q1;            // [q][4][MAXN]
-  real* gw0 = mv + NC * 4 * MAXN;     // wall / reservoir lambda factor g_lambda(0, T0)
-  real* gw1 = gw0 + Q0;               // wall xi factor g_xi(0, T0)
-  real* gin = gw1 + Q1;               // [TS][Q1] inlet xi factor per row
-  real* gout = gin + TS * Q1;         // [TS][Q1]
-  real* w0r = gout + TS * Q1;         // [Q0] weights: R_ij = w0_i w1_j in the bulk type
-  real* w1r = w0r + Q0;               // [Q1]
-  real* uin = w1r + Q1;               // [TS] inlet / outlet u^xi of the adjacent cell
-  real* uout = uin + TS;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const bool is_main = tid < NMAIN;
+  const int c = is_main ? tid / V : TP;  // column of a main thread; TP marks the extra group
+  const int v = is_main ? tid - c * V : tid - NMAIN;
+  const int i = v / Q1, j = v - i * Q1;
+  const int wc = v >> 5;                             // warp within the group
+  const int mw = is_main ? tid >> 5 : -1;            // main warp index
+  const int ew = is_main ? -1 : (tid - NMAIN) >> 5;  // extra warp index
 
-  const int nts = (nl + TS - 1) / TS;
-  const int s0 = (blockIdx.x % nts) * TS, p0 = (blockIdx.x / nts) * TP;
-  const int TSe = min(TS, nl - s0);
-  auto slot = [&](int sr, int c) -> int {
-    if (c >= 0 && c < TP) return c * (TS + 6) + sr + 3;
-    const int h = c < 0 ? c + 3 : c - TP + 3;
-    return TP * (TS + 6) + h * TS + sr;
+  const int nl = a.nl, nx = a.nx;
+  const int nstrips = nx / TP;
+  const int strip = blockIdx.x % nstrips, seg = blockIdx.x / nstrips;
+  const int p0 = strip * TP;
+  const int sA = seg * a.seglen, sB = min(sA + a.seglen, nl);
+  const bool inlet = p0 == 0, outlet = p0 + TP == nx;
+  const bool top = sB == nl;
+  const bool need_fl = a.ca != real(0);
+  const int rlast = min(sB + 2, nl - 1);  // last row a segment reads
+  const int pa = max(p0 - 3, 0), pb = min(p0 + TP + 3, nx);  // xi cells of a ring row in memory
+
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off);  // NB step groups, then the prologue
+  const Tab& tb = *reinterpret_cast<const Tab*>(smem + L::tab_off);
+  real* ring = reinterpret_cast<real*>(smem + L::ring_off);                      // [NRING][RC][ROW]
+  ChanCell<real>* gring = reinterpret_cast<ChanCell<real>*>(smem + L::geo_off);  // [NRING][TP]
+  P* xif = reinterpret_cast<P*>(smem + L::xif_off);                              // [TP+1][V]
+  real* lbl = reinterpret_cast<real*>(smem + L::lbl_off);                        // [TP][ROW] (single precision)
+  real* lbx = reinterpret_cast<real*>(smem + L::lbx_off);                        // [TP][ROW]
+  real* eqr = reinterpret_cast<real*>(smem + L::eq_off);                         // [4][TP][EQW]
+  real* resr = reinterpret_cast<real*>(smem + L::res_off);                       // [4][2][Q1]
+  real* mvs = reinterpret_cast<real*>(smem + L::mvs_off);                        // [TP+2][4][MAXN]
+  real* red = reinterpret_cast<real*>(smem + L::red_off);                        // [2][TP][NWC][4]
+  real* wred = reinterpret_cast<real*>(smem + L::wred_off);                      // [TP][NWC]
+  double* nwv = reinterpret_cast<double*>(smem + L::nwv_off);                    // [TP]
+
+  auto dcell = [&](int s, int p) -> size_t { return size_t(s) * nx + p; };
+  // cell cc in [-3, TP + 3) of the ring row in slot k
+  auto krow = [&](int k, int cc) -> real* { return ring + size_t(k * RC + cc + 3) * ROW; };
+  auto row_bytes = [&]() -> unsigned { return unsigned((pb - pa) * L::rowb + TP * sizeof(ChanCell<real>)); };
+  auto row_issue = [&](int r, uint64_t* b) {  // row r with its halo, and its geometry
+    const int k = r % NRING;
+    bulk_g2s(krow(k, pa - p0), a.Fprev + dcell(r, pa) * ROW, unsigned((pb - pa) * L::rowb), b);
+    bulk_g2s(gring + k * TP, a.geo + dcell(r, p0), unsigned(TP * sizeof(ChanCell<real>)), b);
   };
-  auto gcell = [&](int s, int p) -> size_t { return size_t(p) * nl + s; };
 
-  // ---- bulk copies: tile columns with lambda halo, xi-halo columns, F_l of the owned cells
+  // ---- prologue: tables and rows sA .. sA+2+PD
   if (tid == 0) {
-    mbar_init(bar, 1);
+    for (int b = 0; b <= NB; ++b) mbar_init(bar + b, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  const bool need_fl = a.caf != 0.0f;
-  if (warp == 0) {
-    const unsigned rb = unsigned(ROW * sizeof(real));
-    const int slo = max(s0 - 3, 0), shi = min(s0 + TS + 3, nl);
-    unsigned total = 0;
-    for (int c = -3; c < TP + 3; ++c) {
-      const int p = p0 + c;
-      if (p < 0 || p >= nx) continue;
-      total += (c >= 0 && c < TP) ? unsigned(shi - slo) * rb : unsigned(TSe) * rb;
-    }
-    if (need_fl) total += unsigned(TP * TSe) * rb;
-    if (lane == 0) mbar_expect_tx(bar, total);
-    __syncwarp();
-    if (lane < TP + 6) {
-      const int c = lane - 3, p = p0 + c;
-      if (p >= 0 && p < nx) {
-        if (c >= 0 && c < TP)
-          bulk_g2s(tile + slot(slo - s0, c) * ROW, a.Fprev + gcell(slo, p) * ROW, unsigned(shi - slo) * rb, bar);
-        else
-          bulk_g2s(tile + slot(0, c) * ROW, a.Fprev + gcell(s0, p) * ROW, unsigned(TSe) * rb, bar);
+  const int rtop = min(sA + 2 + PD, rlast);
+  if (tid == NMAIN) {  // one arrival with every byte of the prologue, then the copies
+    const unsigned total = unsigned(sizeof(Tab)) + unsigned(rtop - sA + 1) * row_bytes();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar + NB, total);
+    bulk_g2s(smem + L::tab_off, a.tables, unsigned(sizeof(Tab)), bar + NB);
+    for (int r = sA; r <= rtop; ++r) row_issue(r, bar + NB);
+  }
+  P W0, W1, W2, W3, W4, W5;  // F(s-3 .. s+2) before the push of step s
+  W0 = W1 = W2 = p_set(real(0));
+  if (is_main && sA > 0) {  // window rows below the segment (each thread its own populations)
+    const real* base = a.Fprev + 2 * v;
+    W0 = p_load(base + dcell(sA - 3, p0 + c) * ROW);
+    W1 = p_load(base + dcell(sA - 2, p0 + c) * ROW);
+    W2 = p_load(base + dcell(sA - 1, p0 + c) * ROW);
+  }
+  P flr = p_set(real(0));  // F_l of the cell being finished, prefetched one row ahead
+  if (is_main && need_fl) flr = p_load(a.Fl + dcell(sA, p0 + c) * ROW + 2 * v);
+  {
+    bool ok = true;
+    if (tid == 0) ok = mbar_wait(bar + NB, 0, a.max_polls);
+    ok = __syncthreads_and(ok);
+    if (!ok) {
+      if (tid == 0) {
+        atomicOr(a.err, ERR_TIMEOUT);
+        mbar_wait(bar + NB, 0, a.max_polls);
       }
-    } else if (need_fl && lane >= 16 && lane < 16 + TP) {
-      const int c = lane - 16;
-      bulk_g2s(flb + c * TS * ROW, a.Fl + gcell(s0, p0 + c) * ROW, unsigned(TSe) * rb, bar);
+      __syncthreads();
+      return;
     }
   }
-  for (int x = tid; x < Q0; x += NT) {
-    p0r[x] = F32 ? real(m.p0f[x]) : real(m.p0[x]);
-    iw0[x] = F32 ? real(m.iw0f[x]) : real(m.iw0[x]);
-    w0r[x] = F32 ? real(m.w0f[x]) : real(m.w0[x]);
-  }
-  for (int x = tid; x < Q1; x += NT) {
-    p1r[x] = F32 ? real(m.p1f[x]) : real(m.p1[x]);
-    iw1[x] = F32 ? real(m.iw1f[x]) : real(m.iw1[x]);
-    w1r[x] = F32 ? real(m.w1f[x]) : real(m.w1[x]);
-  }
-  for (int x = tid; x < Q0 * MAXN; x += NT) tb0[x] = F32 ? real(m.tab0f[x]) : real(m.tab0[x]);
-  for (int x = tid; x < Q1 * MAXN; x += NT) tb1[x] = F32 ? real(m.tab1f[x]) : real(m.tab1[x]);
-  for (int x = tid; x < NC * 10; x += NT) {
-    const int q = x / 10, k = x - q * 10, c = q / TS, sr = q - c * TS;
-    real v = 0;
-    if (sr < TSe) {
-      if constexpr (F32) v = (&a.geof[gcell(s0 + sr, p0 + c)].am)[k];
-      else v = (&a.geo[gcell(s0 + sr, p0 + c)].am)[k];
-    }
-    geo[x] = v;
-  }
-  bool ok = mbar_wait(bar, 0, a.max_polls);
-  ok = __syncthreads_and(ok);
-  if (!ok) {
-    if (tid == 0) atomicOr(a.err, ERR_TIMEOUT);
-    mbar_wait(bar, 0, a.max_polls);
-    return;
-  }
-  const real T0 = F32 ? real(a.cd.T0f) : real(a.cd.T0);
+  // per-thread constants
+  const real pl = tb.p0[i], px = tb.p1[j];
+  const real sc = tb.iw0[i] * tb.iw1[j];
+  const real Rij = tb.w0[i] * tb.w1[j];
+  const bool lpos = pl >= real(0);
+  const real T0 = a.T0;
 
-  // ==== phase A: moments per owned cell (warp per cell) and the lambda-axis contractions
-  for (int q = warp; q < NC; q += NW) {
-    const int c = q / TS, sr = q - c * TS;
-    if (sr >= TSe) continue;
-    const real* F = tile + slot(sr, c) * ROW;
-    real sn = 0, sr0 = 0, sp1 = 0, se = 0;
-    for (int v = lane; v < V; v += 32) {
-      const int i = v / Q1, j = v - i * Q1;
-      const pair_t<real> f = p_load(F + 2 * v);
-      const real f1 = f.x, f2 = f.y, pl = p0r[i], px = p1r[j];
-      sn += f1;
-      sr0 += pl * f1;
-      sp1 += px * f1;
-      se += (pl * pl + px * px) * f1 + f2;
-    }
+  // moments of row r (main threads): per-warp partial sums of the deviation
+  auto moment_partials = [&](P f, int r) {
+    const real f1 = f.x, f2 = f.y;
+    const real sn = f1, srr = pl * f1, spp = px * f1, se = (pl * pl + px * px) * f1 + f2;
     const bool h16 = lane & 16, h8 = lane & 8;
-    double k0 = h16 ? double(sp1) : double(sn), k1 = h16 ? double(se) : double(sr0);
-    const double t0 = h16 ? double(sn) : double(sp1), t1 = h16 ? double(sr0) : double(se);
+    real k0 = h16 ? spp : sn, k1 = h16 ? se : srr;
+    const real t0 = h16 ? sn : spp, t1 = h16 ? srr : se;
     k0 += __shfl_xor_sync(0xffffffffu, t0, 16);
     k1 += __shfl_xor_sync(0xffffffffu, t1, 16);
-    double kq = h8 ? k1 : k0;
+    real kq = h8 ? k1 : k0;
     kq += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
     kq += __shfl_xor_sync(0xffffffffu, kq, 4);
     kq += __shfl_xor_sync(0xffffffffu, kq, 2);
     kq += __shfl_xor_sync(0xffffffffu, kq, 1);
-    const double d0 = __shfl_sync(0xffffffffu, kq, 8), d1 = __shfl_sync(0xffffffffu, kq, 16);
-    const double de = __shfl_sync(0xffffffffu, kq, 24);
-    if (lane == 0) {  // sums of D plus those of R
-      const real nn = real(kq + m.ref_n), u0 = real(d0 + m.ref_r) / nn, u1 = real(d1 + m.ref_p) / nn;
-      const real T = (real(de + m.ref_e) - nn * (u0 * u0 + u1 * u1)) / (real(3) * nn);
-      cn[q] = nn;
-      cnd[q] = kq + (F32 ? m.ref_sum_f : m.ref_n);
-      cu0[q] = u0;
-      cu1[q] = u1;
-      cT[q] = T;
-      citau[q] = nn * T / (F32 ? real(a.cd.knf) : real(a.cd.kn));  // tau = Kn / (n T), Eq. (canalie_tau)
-    }
-  }
-  // lbuf = G_lxx (p^xi)^2 K^l f + G_lxl p^xi K~^l f (task: owned cell, field, column j)
-  for (int x = tid; x < NC * 2 * Q1; x += NT) {
-    const int j = x % Q1, qd = x / Q1, d = qd & 1, q = qd >> 1;
-    const int c = q / TS, sr = q - c * TS;
-    if (sr >= TSe) continue;
-    const real* F = tile + slot(sr, c) * ROW + d;
-    real col[Q0];
-#pragma unroll
-    for (int ip = 0; ip < Q0; ++ip) col[ip] = F[2 * (ip * Q1 + j)];
-    const real px = p1r[j];
-    const real wa = geo[q * 10 + 9] * px * px, wb = geo[q * 10 + 8] * px;
-    real* Lr = lbuf + q * ROW + d;
-#pragma unroll
-    for (int i = 0; i < Q0; ++i) {
-      real s1 = 0, s2 = 0;
-#pragma unroll
-      for (int ip = 0; ip < Q0; ++ip) {
-        s1 += kk.K0[i * Q0 + ip] * col[ip];
-        s2 += kk.Kt0[i * Q0 + ip] * col[ip];
-      }
-      Lr[2 * (i * Q1 + j)] = wa * s1 + wb * s2;
-    }
-  }
-  __syncthreads();
+    // lanes 0, 8, 16, 24: n, rho u0, rho u1, energy
+    if ((lane & 7) == 0) red[(((r & 1) * TP + c) * NWC + wc) * 4 + (lane >> 3)] = kq;
+  };
 
-  // ==== phase B: equilibrium moment vectors and the xi-axis contractions
-  for (int x = tid; x < NC * 4; x += NT) {
-    const int q = x >> 2, ax = (x >> 1) & 1, side = x & 1;
-    const int c = q / TS, sr = q - c * TS;
-    if (sr >= TSe) continue;
-    const real u = (ax ? cu1[q] : cu0[q]) * (side ? real(-1) : real(1));
-    eq_moment_vector<real>(ax ? m.kind1 : m.kind0, ax ? m.N1 : m.N0, u, cT[q], mv + (q * 4 + ax * 2 + side) * MAXN);
-  }
-  // lbuf -= G_lxx p^l K~^xi f + G_lxl (p^l)^2 K^xi f (task: owned cell, field, row i)
-  for (int x = tid; x < NC * 2 * Q0; x += NT) {
-    const int i = x % Q0, qd = x / Q0, d = qd & 1, q = qd >> 1;
-    const int c = q / TS, sr = q - c * TS;
-    if (sr >= TSe) continue;
-    const real* F = tile + slot(sr, c) * ROW + d + 2 * i * Q1;
-    real rw[Q1];
+  // equilibrium record of cell cc of row r (one extra warp): n, u, T, tau and the
+  // factors n g0_i, g1_j normalised so that sum_ij n g0_i g1_j = n (reading 18)
+  auto eq_job = [&](int r, int cc) {
+    real* mv = mvs + cc * 4 * MAXN;
+    const real* rp = red + ((r & 1) * TP + cc) * NWC * 4;
+    // cross-warp sums of the partials plus the sums of R; n compensated (float-float)
+    // on the single-precision path
+    real q[4], nlo = real(0);
+    {
+      real sn = real(0), e = real(0);
 #pragma unroll
-    for (int jp = 0; jp < Q1; ++jp) rw[jp] = F[2 * jp];
-    const real pl = p0r[i];
-    const real wa = geo[q * 10 + 9] * pl, wb = geo[q * 10 + 8] * pl * pl;
-    real* Lr = lbuf + q * ROW + d + 2 * i * Q1;
-#pragma unroll
-    for (int j = 0; j < Q1; ++j) {
-      real s1 = 0, s2 = 0;
-#pragma unroll
-      for (int jp = 0; jp < Q1; ++jp) {
-        s1 += kk.Kt1[j * Q1 + jp] * rw[jp];
-        s2 += kk.K1[j * Q1 + jp] * rw[jp];
-      }
-      Lr[2 * j] -= wa * s1 + wb * s2;
-    }
-  }
-  // equilibrium factors of the walls and reservoirs: g_lambda(0, T0), g_xi(0, T0)
-  if (tid == 0) {
-    real ml[MAXN], mx[MAXN];
-    eq_moment_vector<real>(m.kind0, m.N0, real(0), T0, ml);
-    eq_moment_vector<real>(m.kind1, m.N1, real(0), T0, mx);
-    for (int k = 0; k < Q0; ++k) {
-      real g = 0;
-      for (int s = 0; s <= m.N0; ++s) g += tb0[k * MAXN + s] * ml[s];
-      gw0[k] = g;
-    }
-    for (int k = 0; k < Q1; ++k) {
-      real g = 0;
-      for (int s = 0; s <= m.N1; ++s) g += tb1[k * MAXN + s] * mx[s];
-      gw1[k] = g;
-    }
-  }
-  __syncthreads();
-
-  // ==== phase C: equilibrium factors per cell and the boundaries
-  for (int x = tid; x < NC * (Q0 + Q1); x += NT) {
-    const int q = x / (Q0 + Q1);
-    int k = x - q * (Q0 + Q1);
-    const int c = q / TS, sr = q - c * TS;
-    if (sr >= TSe) continue;
-    if (k < Q0) {
-      const int side = (m.kind0 == 1 && p0r[k] < real(0)) ? 1 : 0;
-      const real* mm = mv + (q * 4 + side) * MAXN;
-      real g = 0;
-      for (int s = 0; s <= m.N0; ++s) g += tb0[k * MAXN + s] * mm[s];
-      g0n[q * Q0 + k] = cn[q] * g;
-    } else {
-      k -= Q0;
-      const int side = (m.kind1 == 1 && p1r[k] < real(0)) ? 1 : 0;
-      const real* mm = mv + (q * 4 + 2 + side) * MAXN;
-      real g = 0;
-      for (int s = 0; s <= m.N1; ++s) g += tb1[k * MAXN + s] * mm[s];
-      g1[q * Q1 + k] = g;
-    }
-  }
-  __syncthreads();
-  if (tid < NC && tid % TS < TSe) normalise_equilibrium<real>(g0n + tid * Q0, g1 + tid * Q1, Q0, Q1, cnd[tid]);
-  // centreline lambda = 0: specular reflection, ghost 1-k mirrors cell k (p^lambda -> -p^lambda)
-  if (s0 < 3) {  // the lambda halo reaches the ghost cells s = -1, -2, -3 (s = -k mirrors cell k - 1)
-    constexpr int QH = Q0 / 2;
-    for (int x = tid; x < TP * 3 * V; x += NT) {
-      const int v = x % V, kc = x / V, k = kc % 3 + 1, c = kc / 3;
-      const int i = v / Q1, j = v - i * Q1;
-      const int ib = i < QH ? i + QH : i - QH;
-      const int rg = -k - s0, rc = k - 1 - s0;  // tile rows of the ghost and of its mirror cell
-      if (rg >= -3) p_store(tile + slot(rg, c) * ROW + 2 * v, p_load(tile + slot(rc, c) * ROW + 2 * (ib * Q1 + j)));
-    }
-  }
-  // wall lambda = 1: per column, outgoing flux (p^lambda > 0), n_w, incoming ghosts f_eq(n_w, 0, T0)
-  if (s0 + TS + 3 > nl) {
-    const int sA = nl - 1 - s0;  // row of the wall-adjacent cell, relative to s0
-    double part[TP];
-#pragma unroll
-    for (int c = 0; c < TP; ++c) part[c] = 0;
-    for (int x = tid; x < TP * V; x += NT) {
-      const int c = x / V, v = x - c * V, i = v / Q1, j = v - i * Q1;
-      if (!(p0r[i] > real(0))) continue;
-      // field 0 (f'), with the reconstruction phase D applies
-      const real F0 = tile[slot(sA, c) * ROW + 2 * v], F1 = tile[slot(sA - 1, c) * ROW + 2 * v];
-      const real F2 = tile[slot(sA - 2, c) * ROW + 2 * v];
-      const real G0 = real(3) * F0 - real(3) * F1 + F2, G1 = real(6) * F0 - real(8) * F1 + real(3) * F2;
-      const double fl = double(weno5<real>(F2, F1, F0, G0, G1, iw0[i] * iw1[j])) * double(p0r[i]);
-#pragma unroll
-      for (int cc = 0; cc < TP; ++cc)
-        if (cc == c) part[cc] += fl;
-    }
-#pragma unroll
-    for (int c = 0; c < TP; ++c) {
-      const double s = warp_sum<real>(part[c]);
-      if (lane == 0) red[NW * 4 + c * NW + warp] = s;
-    }
-    __syncthreads();
-    if (tid < TP) {
-      double s = m.ref_flux_pos;  // the outgoing flux of R
-      for (int w = 0; w < NW; ++w) s += red[NW * 4 + tid * NW + w];
-      double den0 = 0, den1 = 0;  // incoming flux of f_eq(1, 0, T0): sum_{p^l<0} g p^l * sum_j g
-      for (int k = 0; k < Q0; ++k)
-        if (p0r[k] < real(0)) den0 += double(gw0[k]) * double(p0r[k]);
-      for (int k = 0; k < Q1; ++k) den1 += double(gw1[k]);
-      const double nwc = -s / (den0 * den1);
-      nwv[tid] = nwc;
-      a.nw[p0 + tid] = nwc;
-      if (!isfinite(nwc)) atomicOr(a.err, ERR_NONFINITE);
-    }
-    __syncthreads();
-    for (int x = tid; x < TP * V; x += NT) {
-      const int v = x % V, c = x / V;
-      const int i = v / Q1, j = v - i * Q1;
-      pair_t<real> g1v, g2v, g3v;
-      if (p0r[i] > real(0)) {
-        const pair_t<real> F0 = p_load(tile + slot(sA, c) * ROW + 2 * v);
-        const pair_t<real> F1 = p_load(tile + slot(sA - 1, c) * ROW + 2 * v);
-        const pair_t<real> F2 = p_load(tile + slot(sA - 2, c) * ROW + 2 * v);
-        g1v = p_make(real(3) * F0.x - real(3) * F1.x + F2.x, real(3) * F0.y - real(3) * F1.y + F2.y);
-        g2v = p_make(real(6) * F0.x - real(8) * F1.x + real(3) * F2.x, real(6) * F0.y - real(8) * F1.y + real(3) * F2.y);
-        g3v = g2v;
-      } else {  // f_eq(n_w, 0, T0) - R
-        const double e = nwv[c] * double(gw0[i]) * double(gw1[j]), r = m.w0[i] * m.w1[j];
-        g1v = g2v = g3v = p_make(real(e - r), real(e * double(T0) - r));
-      }
-      if (sA + 1 < TS + 3) p_store(tile + slot(sA + 1, c) * ROW + 2 * v, g1v);
-      if (sA + 2 < TS + 3) p_store(tile + slot(sA + 2, c) * ROW + 2 * v, g2v);
-      if (sA + 3 < TS + 3) p_store(tile + slot(sA + 3, c) * ROW + 2 * v, g3v);
-    }
-  }
-  // inlet and outlet reservoirs: per row, u^xi of the adjacent cell, then ghosts
-  for (int end = 0; end < 2; ++end) {
-    const bool active = end == 0 ? (p0 < 3) : (p0 + TP + 3 > nx);
-    if (!active) continue;
-    const int cA = end == 0 ? -p0 : nx - 1 - p0;  // tile column of the adjacent cell
-    real* gres = end == 0 ? gin : gout;
-    real* ures = end == 0 ? uin : uout;
-    __syncthreads();
-    for (int sr = warp; sr < TSe; sr += NW) {
-      const real* F = tile + slot(sr, cA) * ROW;
-      real sn = 0, sx = 0;
-      for (int v = lane; v < V; v += 32) {
-        const int j = v % Q1;
-        sn += F[2 * v];
-        sx += p1r[j] * F[2 * v];
-      }
-      const double dn = warp_sum<real>(double(sn)) + m.ref_n, dx = warp_sum<real>(double(sx)) + m.ref_p;
-      if (lane == 0) ures[sr] = real(dx / dn);
-    }
-    __syncthreads();
-    for (int sr = tid; sr < TSe; sr += NT) {
-      real mx[MAXN], mxm[MAXN];
-      eq_moment_vector<real>(m.kind1, m.N1, ures[sr], T0, mx);
-      eq_moment_vector<real>(m.kind1, m.N1, -ures[sr], T0, mxm);
-      for (int k = 0; k < Q1; ++k) {
-        const real* mm = (m.kind1 == 1 && p1r[k] < real(0)) ? mxm : mx;
-        real g = 0;
-        for (int s = 0; s <= m.N1; ++s) g += tb1[k * MAXN + s] * mm[s];
-        gres[sr * Q1 + k] = g;
-      }
-    }
-    __syncthreads();
-    const real nres = F32 ? real(end == 0 ? a.cd.n_inf : a.cd.n_outf) : real(end == 0 ? a.cd.n_in : a.cd.n_out);
-    for (int x = tid; x < TSe * V; x += NT) {
-      const int v = x % V, sr = x / V;
-      const int i = v / Q1, j = v - i * Q1;
-      // V^xi at the boundary interface of the adjacent cell
-      real bb, cc;
-      if constexpr (F32) {
-        const ChanCell<float>& gc = a.geof[gcell(s0 + sr, p0 + cA)];
-        bb = end == 0 ? gc.bm : gc.bp;
-        cc = end == 0 ? gc.cm : gc.cp;
-      } else {
-        const ChanCell<double>& gc = a.geo[gcell(s0 + sr, p0 + cA)];
-        bb = end == 0 ? gc.bm : gc.bp;
-        cc = end == 0 ? gc.cm : gc.cp;
-      }
-      const real Vx = bb * p1r[j] - cc * p0r[i];
-      const bool inflow = end == 0 ? (Vx > real(0)) : (Vx < real(0));
-      pair_t<real> val;
-      if (inflow) {  // f_eq(n_res, (0, u_res), T0) - R
-        const real e = nres * gw0[i] * gres[sr * Q1 + j], r = w0r[i] * w1r[j];
-        val = p_make(e - r, e * T0 - r);
-      } else {
-        val = p_load(tile + slot(sr, cA) * ROW + 2 * v);
-      }
-      for (int k = 1; k <= 3; ++k) {
-        const int c = end == 0 ? cA - k : cA + k;
-        if (c >= -3 && c < TP + 3 && (c < 0 || c >= TP)) p_store(tile + slot(sr, c) * ROW + 2 * v, val);
-      }
-    }
-  }
-  __syncthreads();
-
-  // ==== phase D: WENO-5 in lambda (walking each column) and in xi, flux differences, BGK, RK3
-  const real dtr = F32 ? real(a.cd.dtf) : real(a.cd.dt);
-  const real ca = F32 ? real(a.caf) : real(a.ca);  // cb = 1 - ca: see StageArgs
-  const real ccoef = (F32 ? real(a.ccf) : real(a.cc)) * dtr;
-  for (int x = tid; x < 2 * V; x += NT) {
-    const int d = x >= V, v = x - d * V;
-    const int i = v / Q1, j = v - i * Q1;
-    const real pl = p0r[i], px = p1r[j];
-    const bool upl = pl >= real(0);
-    const real sc = iw0[i] * iw1[j];
-#pragma unroll
-    for (int c = 0; c < TP; ++c) {
-      const real* S = tile + slot(0, c) * ROW + 2 * v + d;  // row sr at S[sr * ROW]
-      real w0 = S[-3 * ROW], w1 = S[-2 * ROW], w2 = S[-1 * ROW], w3 = S[0], w4 = S[ROW], w5 = S[2 * ROW];
-      real fm = weno5<real>(upl ? w0 : w5, upl ? w1 : w4, upl ? w2 : w3, upl ? w3 : w2, upl ? w4 : w1, sc);
-#pragma unroll
-      for (int sr = 0; sr < TS; ++sr) {
-        if (sr < TSe) {
-          const int q = c * TS + sr;
-          const real w6 = S[(sr + 3) * ROW];
-          const real fp = weno5<real>(upl ? w1 : w6, upl ? w2 : w5, upl ? w3 : w4, upl ? w4 : w3, upl ? w5 : w2, sc);
-          const real* gq = geo + q * 10;
-          real adv = pl * (gq[1] * fp - gq[0] * fm) * gq[6];
-          real h[7];
-#pragma unroll
-          for (int k = 0; k < 7; ++k) h[k] = tile[slot(sr, c - 3 + k) * ROW + 2 * v + d];
-          const real Vm = gq[2] * px - gq[4] * pl, Vp_ = gq[3] * px - gq[5] * pl;
-          const real Fm = Vm >= real(0) ? weno5<real>(h[0], h[1], h[2], h[3], h[4], sc)
-                                        : weno5<real>(h[5], h[4], h[3], h[2], h[1], sc);
-          const real Fp = Vp_ >= real(0) ? weno5<real>(h[1], h[2], h[3], h[4], h[5], sc)
-                                         : weno5<real>(h[6], h[5], h[4], h[3], h[2], sc);
-          adv += (Vp_ * Fp - Vm * Fm) * gq[7];
-          const real deq = g0n[q * Q0 + i] * g1[q * Q1 + j] * (d ? cT[q] : real(1)) - w0r[i] * w1r[j];
-          const real Lv = -adv + lbuf[q * ROW + 2 * v + d] - (w3 - deq) * citau[q];
-          real o = w3 + ccoef * Lv;
-          real* dst = flb + q * ROW + 2 * v + d;
-          if (need_fl) o += ca * (*dst - w3);
-          *dst = o;
-          w0 = w1;
-          w1 = w2;
-          w2 = w3;
-          w3 = w4;
-          w4 = w5;
-          w5 = w6;
-          fm = fp;
+      for (int w = 0; w < NWC; ++w) {
+        const real x = rp[w * 4];
+        if constexpr (F32) {
+          float t, er;
+          two_sum(sn, x, t, er);
+          sn = t;
+          e += er;
+        } else {
+          sn += x;
         }
       }
+      if constexpr (F32) {
+        float t, er;
+        two_sum(sn, tb.ref_hi[0], t, er);
+        q[0] = t;
+        nlo = er + e + tb.ref_lo[0];
+      } else {
+        q[0] = sn + tb.ref_hi[0];
+      }
     }
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      real sk = real(0);
+#pragma unroll
+      for (int w = 0; w < NWC; ++w) sk += rp[w * 4 + k];
+      q[k] = sk + (tb.ref_hi[k] + tb.ref_lo[k]);
+    }
+    const real nn = q[0] + nlo;
+    const real inn = rcp_rn(nn);
+    const real u0 = q[1] * inn, u1 = q[2] * inn;
+    const real T = (q[3] * inn - (u0 * u0 + u1 * u1)) * (real(1) / real(3));
+    if (lane < 4) {
+      const int ax = lane >> 1, side = lane & 1;
+      const real u = (ax ? u1 : u0) * (side ? real(-1) : real(1));
+      eq_moments_fast<real>(ax ? tb.kind1 : tb.kind0, ax ? tb.N1 : tb.N0, u, T, mv + lane * MAXN);
+    }
+    __syncwarp();
+    real g = real(0);
+    if (lane < Q0) {
+      const real* m = mv + ((tb.kind0 == 1 && tb.p0[lane] < real(0)) ? 1 : 0) * MAXN;
+      for (int s = 0; s <= tb.N0; ++s) g += tb.tab0[lane * MAXN + s] * m[s];
+      g *= nn;
+    } else if (lane < Q0 + Q1) {
+      const int jj = lane - Q0;
+      const real* m = mv + (2 + ((tb.kind1 == 1 && tb.p1[jj] < real(0)) ? 1 : 0)) * MAXN;
+      for (int s = 0; s <= tb.N1; ++s) g += tb.tab1[jj * MAXN + s] * m[s];
+    }
+    real s0 = lane < Q0 ? g : real(0), s1 = (lane >= Q0 && lane < Q0 + Q1) ? g : real(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    // scale = n / (s0 s1), n in float-float on the single-precision path
+    const real iden = rcp_rn(s0 * s1);
+    const real scl = q[0] * iden + nlo * iden;
+    real val = g;
+    if (lane < Q0) val = g * scl;
+    else if (lane == Q0 + Q1) val = T;
+    else if (lane == Q0 + Q1 + 1) val = nn * T * a.ikn;  // 1/tau, tau = Kn / (n T) (Eq. canalie_tau)
+    else if (lane == Q0 + Q1 + 2) val = u1;
+    if (lane < EQW) eqr[((r & 3) * TP + cc) * EQW + lane] = val;
+    __syncwarp();
+  };
+
+  // reservoir factors g_xi(u^xi, T0) of row r at one end, u^xi of the adjacent cell
+  // from its moment partials
+  auto res_job = [&](int r, int end) {
+    const int cc = end == 0 ? 0 : TP - 1;
+    const real* rp = red + ((r & 1) * TP + cc) * NWC * 4;
+    real sn = real(0), sp = real(0);
+#pragma unroll
+    for (int w = 0; w < NWC; ++w) sn += rp[w * 4], sp += rp[w * 4 + 2];
+    const real ures = (sp + (tb.ref_hi[2] + tb.ref_lo[2])) * rcp_rn(sn + (tb.ref_hi[0] + tb.ref_lo[0]));
+    real* mv = mvs + (TP + end) * 4 * MAXN;
+    if (lane < 2) eq_moments_fast<real>(tb.kind1, tb.N1, lane ? -ures : ures, T0, mv + lane * MAXN);
+    __syncwarp();
+    if (lane < Q1) {
+      const real* m = mv + ((tb.kind1 == 1 && tb.p1[lane] < real(0)) ? 1 : 0) * MAXN;
+      real g = real(0);
+      for (int s = 0; s <= tb.N1; ++s) g += tb.tab1[lane * MAXN + s] * m[s];
+      resr[((r & 3) * 2 + end) * Q1 + lane] = g;
+    }
+    __syncwarp();
+  };
+  auto res_jobs = [&](int r) {  // extra warps: both ends where the strip has one
+    for (int end = 0; end < 2; ++end)
+      if ((end == 0 ? inlet : outlet) && ew == (TP + end) % NWC) res_job(r, end);
+  };
+
+  // inlet / outlet ghosts of row r (main threads of the first / last column): the
+  // populations entering the domain see f_eq(n_res, (0, u^xi), T0) - R, the others
+  // the adjacent cell (zeroth order); written into the row's halo cells, which the
+  // bulk copy leaves out at the ends
+  auto reservoir_ghosts = [&](int r) {
+    if (!is_main) return;
+    for (int end = 0; end < 2; ++end) {
+      const bool act = end == 0 ? (inlet && c == 0) : (outlet && c == TP - 1);
+      if (!act) continue;
+      const int k = r % NRING;
+      real gm[12];
+      load_geo(gring + k * TP + c, gm);
+      const real Vx = end == 0 ? gm[G_BM] * px - gm[G_CM] * pl : gm[G_BP] * px - gm[G_CP] * pl;
+      const bool inflow = end == 0 ? (Vx > real(0)) : (Vx < real(0));
+      P val;
+      if (inflow) {
+        const real e = (end == 0 ? a.n_in : a.n_out) * tb.gw0[i] * resr[((r & 3) * 2 + end) * Q1 + j];
+        val = p_make(e - Rij, e * T0 - Rij);
+      } else {
+        val = p_load(krow(k, c) + 2 * v);
+      }
+      for (int q = 1; q <= 3; ++q) p_store(krow(k, end == 0 ? -q : TP - 1 + q) + 2 * v, val);
+    }
+  };
+
+  // xi interface TP - 1/2 of row s (the right edge of the strip) for the 32 velocities of chunk ch
+  auto edge_weno = [&](int k, int ch) {
+    const int vv = 32 * ch + lane, ii = vv / Q1, jj = vv - ii * Q1;
+    const real pli = tb.p0[ii], pxj = tb.p1[jj];
+    real gm[12];
+    load_geo(gring + k * TP + TP - 1, gm);
+    const bool up = gm[G_BP] * pxj - gm[G_CP] * pli >= real(0);
+    P h[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) h[q] = p_load(krow(k, TP - 3 + q) + 2 * vv);
+    xif[TP * V + vv] = weno5p<real>(p_sel(up, h[0], h[5]), p_sel(up, h[1], h[4]), p_sel(up, h[2], h[3]),
+                                    p_sel(up, h[3], h[2]), p_sel(up, h[4], h[1]), tb.iw0[ii] * tb.iw1[jj]);
+  };
+
+  // window rows from the ring (the centreline mirror below row 0: ghost 1-k of
+  // cell k, p^lambda -> -p^lambda, Sec. VII.C.3)
+  if (is_main) {
+    if (sA == 0) {
+      const int ib = refl(1, Q0, i);
+      W0 = p_load(krow(2 % NRING, c) + 2 * (ib * Q1 + j));
+      W1 = p_load(krow(1 % NRING, c) + 2 * (ib * Q1 + j));
+      W2 = p_load(krow(0, c) + 2 * (ib * Q1 + j));
+    }
+    W3 = p_load(krow(sA % NRING, c) + 2 * v);
+    W4 = p_load(krow((sA + 1) % NRING, c) + 2 * v);
+    W5 = p_load(krow((sA + 2) % NRING, c) + 2 * v);
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  // moments of rows sA .. sA+2, equilibria and reservoir factors of rows sA, sA+1
+  // (row sA+2's come in the first step)
+  for (int r = sA; r < min(sA + 3, sB); ++r) {
+    if (is_main) moment_partials(p_load(krow(r % NRING, c) + 2 * v), r);
+    __syncthreads();
+    if (!is_main && r < sA + 2) {
+      for (int job = ew; job < TP; job += NWC) eq_job(r, job);
+      res_jobs(r);
+    }
+    __syncthreads();
+  }
+  reservoir_ghosts(sA);
+  // lambda interface sA - 1/2
+  P fm = p_set(real(0));
+  if (is_main) fm = lpos ? weno5p<real>(W0, W1, W2, W3, W4, sc) : weno5p<real>(W5, W4, W3, W2, W1, sc);
+  P gh0 = p_set(real(0)), gh1 = p_set(real(0));  // wall ghosts of rows nl, nl+1 (and nl+2)
+  unsigned phase_bits = 0;                        // thread 0: parity of the next wait, per step mbarrier
   __syncthreads();
-  if (tid < TP) {
-    bulk_s2g(a.Fout + gcell(s0, p0 + tid) * ROW, flb + tid * TS * ROW, unsigned(TSe * ROW * sizeof(real)));
-    bulk_commit_and_wait_read();
+
+  // ---- the march
+  for (int s = sA; s < sB; ++s) {
+    const int k0 = s % NRING, k3 = (k0 + 3) % NRING;
+    if (s - PD >= sA && s + 3 <= rlast) {  // the group issued PD steps ago brought row s+3
+      bool ok = true;
+      if (tid == 0) {
+        const int b = (s - PD) % NB;
+        ok = mbar_wait(bar + b, (phase_bits >> b) & 1u, a.max_polls);
+        phase_bits ^= 1u << b;
+      }
+      ok = __syncthreads_and(ok);
+      if (!ok) {  // wait (bounded) for every group still in flight, then leave
+        if (tid == 0) {
+          atomicOr(a.err, ERR_TIMEOUT);
+          for (int g = s - PD; g < s; ++g)
+            if (g + 3 + PD <= rlast) {
+              const int b = g % NB;
+              mbar_wait(bar + b, g == s - PD ? ((phase_bits >> b) & 1u) ^ 1u : (phase_bits >> b) & 1u, a.max_polls);
+            }
+        }
+        __syncthreads();
+        return;
+      }
+    }
+    if (tid == NMAIN && s + 3 + PD <= rlast) {  // row s+3+PD into the slot row s-1 left
+      uint64_t* b = bar + s % NB;
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(b, row_bytes());
+      row_issue(s + 3 + PD, b);
+    }
+    // the wall (Sec. VII.C.4): at the first row whose window reaches it, n_w per
+    // column from the zero-mass-flux balance and the ghosts of rows nl .. nl+2
+    if (top && s == nl - 3) {
+      if (is_main) {
+        // W3 .. W5 = F(nl-3 .. nl-1); outgoing populations: quadratic extrapolation (Eq. extrapol)
+        const P G0 = p_add(p_sub(p_mul(p_set(real(3)), W5), p_mul(p_set(real(3)), W4)), W3);
+        const P G1 = p_add(p_sub(p_mul(p_set(real(6)), W5), p_mul(p_set(real(8)), W4)), p_mul(p_set(real(3)), W3));
+        real fl = real(0);
+        if (pl > real(0)) fl = weno5p<real>(W3, W4, W5, G0, G1, sc).x * pl;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) fl += __shfl_xor_sync(0xffffffffu, fl, o);
+        if (lane == 0) wred[c * NWC + wc] = fl;
+        gh0 = G0;
+        gh1 = G1;
+      }
+      __syncthreads();
+      if (!is_main && lane == 0)
+        for (int cc = ew; cc < TP; cc += NWC) {
+          double num = tb.ref_flux_pos;  // outgoing flux of R
+          for (int w = 0; w < NWC; ++w) num += double(wred[cc * NWC + w]);
+          const double nwc = -num / tb.wall_den;  // Eq. (nw)
+          nwv[cc] = nwc;
+          a.nw[p0 + cc] = nwc;
+          if (!isfinite(nwc)) atomicOr(a.err, ERR_NONFINITE);
+        }
+      __syncthreads();
+      if (is_main && !(pl > real(0))) {  // incoming: f_eq(n_w, 0, T0) - R (Eq. weno_populate)
+        const real e = real(nwv[c]) * tb.gw0[i] * tb.gw1[j];
+        gh0 = gh1 = p_make(e - Rij, e * T0 - Rij);
+      }
+    }
+
+    // ==== phase A
+    P FL = p_set(real(0));   // xi interface c - 1/2 of row s
+    P frc = p_set(real(0));  // force (double precision path)
+    if (is_main) {
+      const int rn = s + 3;
+      const P fnew = rn < nl ? p_load(krow(k3, c) + 2 * v) : (rn == nl ? gh0 : gh1);
+      if (rn < min(nl, sB)) moment_partials(fnew, rn);
+      W0 = W1, W1 = W2, W2 = W3, W3 = W4, W4 = W5, W5 = fnew;  // W = F(s-2 .. s+3)
+      real gm[12];
+      load_geo(gring + k0 * TP + c, gm);
+      // xi interface c - 1/2: upwind by V^xi = b p^xi - c p^lambda (Eq. canalie_V)
+      const bool up = gm[G_BM] * px - gm[G_CM] * pl >= real(0);
+      P h[6];
+#pragma unroll
+      for (int q = 0; q < 6; ++q) h[q] = p_load(krow(k0, c - 3 + q) + 2 * v);
+      FL = weno5p<real>(p_sel(up, h[0], h[5]), p_sel(up, h[1], h[4]), p_sel(up, h[2], h[3]), p_sel(up, h[3], h[2]),
+                        p_sel(up, h[4], h[1]), sc);
+      xif[c * V + v] = FL;
+      if constexpr (F32 && TC) {
+        // force subtasks of the row's cells on the tensor cores (mma.sync needs the
+        // warp converged after the data-dependent WENO branches)
+        __syncwarp();
+        for (int t = mw; t < TP * S::S; t += NMW) {
+          const int cc = t / S::S, kt = t - cc * S::S;
+          const ChanCell<real>& gk = gring[k0 * TP + cc];
+          force_subtask_tc<Q0, Q1>(tb, krow(k0, cc), gk.glxx, gk.glxl, kt, lane, lbl + cc * ROW, lbx + cc * ROW);
+        }
+      } else if constexpr (!F32) {
+        const real* F = krow(k0, c);
+        P s0 = p_set(real(0)), s1 = p_set(real(0)), s2 = p_set(real(0)), s3 = p_set(real(0));
+        for (int ip = 0; ip < Q0; ++ip) {
+          const P f = p_load(F + 2 * (ip * Q1 + j));
+          s0 = p_fma(p_set(tb.K0[i * Q0 + ip]), f, s0);
+          s1 = p_fma(p_set(tb.Kt0[i * Q0 + ip]), f, s1);
+        }
+        for (int jp = 0; jp < Q1; ++jp) {
+          const P f = p_load(F + 2 * (i * Q1 + jp));
+          s2 = p_fma(p_set(tb.K1[j * Q1 + jp]), f, s2);
+          s3 = p_fma(p_set(tb.Kt1[j * Q1 + jp]), f, s3);
+        }
+        // G_lxx [(p^xi)^2 K0 f - p^lambda Kt1 f] - G_lxl [(p^lambda)^2 K1 f - p^xi Kt0 f]
+        const P A = p_fma(p_set(px * px), s0, p_mul(p_set(-pl), s3));
+        const P B = p_fma(p_set(pl * pl), s2, p_mul(p_set(-px), s1));
+        frc = p_fma(p_set(gm[G_GLXX]), A, p_mul(p_set(-gm[G_GLXL]), B));
+      }
+    } else if constexpr (F32 && !TC) {
+      // force tasks of the row's cells on the CUDA cores (lambda: one per (cell, column
+      // j); xi: one per (cell, row i)) and the strip's right-edge xi interface, over the
+      // extra warps in units of one warp
+      constexpr int NWL = (TP * Q1 + 31) / 32, NWX = (TP * Q0 + 31) / 32;
+      for (int u = ew; u < NWL + NWX + NWC; u += NWC) {
+        if (u < NWL) {
+          const int t = 32 * u + lane;
+          if (t < TP * Q1) {
+            const int cc = t / Q1, jj = t - cc * Q1;
+            const ChanCell<real>& gk = gring[k0 * TP + cc];
+            const float pxj = tb.p1[jj];
+            force_lambda_cc<Q0, Q1>(kp, krow(k0, cc), jj, gk.glxx * pxj * pxj, gk.glxl * pxj, lbl + cc * ROW);
+          }
+        } else if (u < NWL + NWX) {
+          const int t = 32 * (u - NWL) + lane;
+          if (t < TP * Q0) {
+            const int cc = t / Q0, ii = t - cc * Q0;
+            const ChanCell<real>& gk = gring[k0 * TP + cc];
+            const float pli = tb.p0[ii];
+            force_xi_cc<Q0, Q1>(kp, krow(k0, cc), ii, -gk.glxx * pli, -gk.glxl * pli * pli, lbx + cc * ROW);
+          }
+        } else {
+          edge_weno(k0, u - NWL - NWX);
+        }
+      }
+    } else {
+      // the strip's right-edge xi interface of row s, 32 velocities per extra warp
+      for (int ch = ew; ch < NWC; ch += NWC) edge_weno(k0, ch);
+    }
+    __syncthreads();
+
+    // ==== phase C
+    if (is_main) {
+      // lambda interface s + 1/2, upwind by p^lambda (a > 0)
+      const P fp = lpos ? weno5p<real>(W0, W1, W2, W3, W4, sc) : weno5p<real>(W5, W4, W3, W2, W1, sc);
+      real gm[12];
+      load_geo(gring + k0 * TP + c, gm);
+      const P FR = xif[(c + 1) * V + v];
+      const real Vm = gm[G_BM] * px - gm[G_CM] * pl, Vp = gm[G_BP] * px - gm[G_CP] * pl;
+      // chi flux differences (Sec. VII.B)
+      P adv = p_mul(p_set(pl * gm[G_IDL]), p_sub(p_mul(p_set(gm[G_AP]), fp), p_mul(p_set(gm[G_AM]), fm)));
+      adv = p_fma(p_set(gm[G_IDX]), p_sub(p_mul(p_set(Vp), FR), p_mul(p_set(Vm), FL)), adv);
+      if constexpr (F32) frc = p_add(p_load(lbl + c * ROW + 2 * v), p_load(lbx + c * ROW + 2 * v));
+      const real* rec = eqr + ((s & 3) * TP + c) * EQW;
+      const real geq = rec[i] * rec[Q0 + j];
+      const P deq = p_make(geq - Rij, geq * rec[Q0 + Q1] - Rij);
+      const real itau = rec[Q0 + Q1 + 1];
+      const P F = W2;  // F(s)
+      // L = -advection + force - (F - f_eq) / tau
+      const P Lv = p_sub(p_sub(frc, adv), p_mul(p_set(itau), p_sub(F, deq)));
+      P o = p_fma(p_set(a.ccdt), Lv, F);
+      if (need_fl) o = p_fma(p_set(a.ca), p_sub(flr, F), o);
+      p_store(a.Fout + dcell(s, p0 + c) * ROW + 2 * v, o);
+      if (need_fl && s + 1 < sB) flr = p_load(a.Fl + dcell(s + 1, p0 + c) * ROW + 2 * v);
+      fm = fp;
+    } else if (s + 2 < min(nl, sB)) {
+      // the equilibria and reservoir factors of row s+2 (moment partials of the previous step)
+      for (int job = ew; job < TP; job += NWC) eq_job(s + 2, job);
+      res_jobs(s + 2);
+    }
+    if (s + 1 < sB) reservoir_ghosts(s + 1);
+    __syncthreads();
   }
 }
 

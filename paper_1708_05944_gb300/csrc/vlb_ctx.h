@@ -44,6 +44,7 @@ struct vlb_ctx {
   int cfg_nbuf[16] = {};
   int cfg_per_sm[16] = {};
   int sms = 0;  // SMs of the context's device
+  int device = -1;  // CUDA device current when the context was created
   int cur = 0;   // buffer holding F_l
   int last = 0;  // buffer written by the most recent stage
   int stage_done = 0;
@@ -65,7 +66,10 @@ struct vlb_ctx {
   int n_cvariants = 0;
   ChanCell<double>* d_cgeo = nullptr;
   ChanCell<float>* d_cgeof = nullptr;
-  std::vector<unsigned char> chanK32, chanK64;
+  CellMap cmap;  // device cell order against the caller's (identity for Couette)
+  std::vector<unsigned char> chan_kp;  // ChanKP block (split force matrices), a kernel parameter
+  void* d_ctab = nullptr;  // ChanTables of the model shape in the context's real type
+  size_t ctab_bytes = 0;
   // CUDA graph of three RK3 steps (nine stage launches), replayed by vlb_step_graph
   // three-step graphs, one per starting buffer F[cur] (captured on first use)
   cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};

@@ -134,6 +134,9 @@ __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double vmax(double a, double b) { return fmax(a, b); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double vmin(double a, double b) { return fmin(a, b); }
+// 1 / x correctly rounded (single precision: the reciprocal intrinsic, cheaper than a division).
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_rn(double x) { return 1.0 / x; }
 // x / y; single precision uses the fast divide (2 ulp), valid for |y| < 2^126.
 __device__ __forceinline__ float vdiv(float x, float y) { return __fdividef(x, y); }
 __device__ __forceinline__ double vdiv(double x, double y) { return x / y; }

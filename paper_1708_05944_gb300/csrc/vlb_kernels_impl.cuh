@@ -1,6 +1,9 @@
 // Kernels and launchers instantiated once per precision by vlb_f32.cu / vlb_f64.cu.
 #pragma once
+#include <algorithm>
+#include <cmath>
 #include <cstring>
+#include <vector>
 #include "vlb_launch.h"
 #include "vlb_stage.cuh"
 #include "vlb_channel.cuh"
@@ -172,53 +175,204 @@ cudaError_t stage_config(StageVariant v, const ModelArgs& m, int Vp, int* nbuf, 
 }
 
 // ---------------------------------------------------------------- channel dispatch
-template <typename real, int TS, int TP, int Q0, int Q1, int NT>
-static cudaError_t go_channel(const ChanArgs<real>& a, const ModelArgs& m, const void* kbytes, cudaStream_t s) {
-  using L = ChanSmem<real, TS, TP, Q0, Q1, NT>;
-  auto kern = channel_stage_kernel<real, TS, TP, Q0, Q1, NT>;
+template <typename real, int Q0, int Q1, int TP, bool TC>
+static cudaError_t go_channel(const ChanArgs<real>& a, const void* kpb, int grid, cudaStream_t s) {
+  using L = ChanSmem<real, Q0, Q1, TP>;
+  auto kern = channel_stage_kernel<real, Q0, Q1, TP, TC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::bytes));
   if (e != cudaSuccess) return e;
-  ChanK<real, Q0, Q1> k;
-  memcpy(&k, kbytes, sizeof(k));
-  const int nts = (a.cd.nl + TS - 1) / TS;
-  const int blocks = nts * (a.cd.nx / TP);
-  kern<<<blocks, NT, L::bytes, s>>>(a, m, k);
+  ChanKP<Q0, Q1> kp;
+  memcpy(&kp, kpb, sizeof(kp));
+  kern<<<grid, L::NT, L::bytes, s>>>(a, kp);
   return cudaGetLastError();
 }
 
 #ifdef VLB_DEFINE_SHARED
-static const ChanVariant kChanVariants[] = {{4, 2, 192}, {2, 4, 192}, {4, 4, 192}, {8, 2, 192}, {4, 2, 384}};
+// {rows per segment (0: host's choice, 1 << 20: one segment), columns per strip, threads, tensor-core force}
+static const ChanVariant kChan16x12[] = {{0, 4, 960, 0}, {0, 4, 960, 1}, {1 << 20, 4, 960, 0}, {64, 4, 960, 0}};
+static const ChanVariant kChan8x4[] = {{0, 4, 160, 0}, {0, 8, 288, 0}, {0, 4, 160, 1}, {1 << 20, 4, 160, 0}};
 
 int channel_variants(int nq0, int nq1, ChanVariant* out) {
-  if (!((nq0 == 16 && nq1 == 12) || (nq0 == 8 && nq1 == 4))) return 0;
-  const int n = int(sizeof(kChanVariants) / sizeof(ChanVariant));
-  for (int i = 0; i < n; ++i) out[i] = kChanVariants[i];
+  const ChanVariant* v = nullptr;
+  int n = 0;
+  if (nq0 == 16 && nq1 == 12) v = kChan16x12, n = int(sizeof(kChan16x12) / sizeof(ChanVariant));
+  if (nq0 == 8 && nq1 == 4) v = kChan8x4, n = int(sizeof(kChan8x4) / sizeof(ChanVariant));
+  for (int i = 0; i < n; ++i) out[i] = v[i];
   return n;
+}
+
+template <int Q0, int Q1>
+static bool fill_force_pairs(const AxisTables* ax, std::vector<unsigned char>* out) {
+  using KP = ChanKP<Q0, Q1>;
+  out->assign(sizeof(KP), 0);
+  KP& kp = *reinterpret_cast<KP*>(out->data());
+  // each axis: nodes mirror each other under J, K J = -J K and Kt J = J Kt, to rounding
+  for (int a = 0; a < 2; ++a) {
+    const AxisTables& t = ax[a];
+    const int nq = t.nq;
+    double kmax = 0.0, tmax = 0.0, pmax = 0.0;
+    for (int k = 0; k < nq * nq; ++k) kmax = std::max(kmax, std::fabs(t.K[k])), tmax = std::max(tmax, std::fabs(t.Kt[k]));
+    for (int k = 0; k < nq; ++k) pmax = std::max(pmax, std::fabs(t.p[k]));
+    for (int r = 0; r < nq; ++r) {
+      if (std::fabs(t.p[refl(t.kind, nq, r)] + t.p[r]) > 1e-13 * pmax) return false;
+      for (int q = 0; q < nq; ++q) {
+        const int rr = refl(t.kind, nq, r), qq = refl(t.kind, nq, q);
+        if (std::fabs(t.K[rr * nq + qq] + t.K[r * nq + q]) > 1e-12 * kmax) return false;
+        if (std::fabs(t.Kt[rr * nq + qq] - t.Kt[r * nq + q]) > 1e-12 * tmax) return false;
+      }
+    }
+  }
+  // the kernels take the mirror of k as k + H on the half-range lambda axis and Q1 - 1 - k
+  // on the full-range xi axis
+  if (ax[0].kind != 1 || ax[1].kind != 0) return false;
+  auto put = [](float2* P, float2* M, const std::vector<double>& K, int nq, int kind) {
+    const int H = nq / 2;
+    for (int r = 0; r < H; ++r)
+      for (int q = 0; q < H; ++q) {
+        const double x = K[r * nq + q], y = K[r * nq + refl(kind, nq, q)];
+        const float pv = float(0.5 * (x + y)), mv = float(0.5 * (x - y));
+        P[r * H + q] = make_float2(pv, pv);
+        M[r * H + q] = make_float2(mv, mv);
+      }
+  };
+  put(kp.P0, kp.M0, ax[0].K, Q0, 1);
+  put(kp.Pt0, kp.Mt0, ax[0].Kt, Q0, 1);
+  put(kp.P1, kp.M1, ax[1].K, Q1, 0);
+  put(kp.Pt1, kp.Mt1, ax[1].Kt, Q1, 0);
+  return true;
+}
+
+bool channel_force_pairs(int nq0, int nq1, const AxisTables* ax, std::vector<unsigned char>* out) {
+  if (nq0 == 16 && nq1 == 12) return fill_force_pairs<16, 12>(ax, out);
+  if (nq0 == 8 && nq1 == 4) return fill_force_pairs<8, 4>(ax, out);
+  return false;
 }
 #endif
 
 template <typename real>
 size_t channel_smem_bytes(ChanVariant v, int nq0, int nq1) {
-#define VLB_CSM(TS_, TP_, NT_)                                                       \
-  if (v.ts == TS_ && v.tp == TP_ && v.nt == NT_) {                                   \
-    if (nq0 == 16 && nq1 == 12) return ChanSmem<real, TS_, TP_, 16, 12, NT_>::bytes; \
-    if (nq0 == 8 && nq1 == 4) return ChanSmem<real, TS_, TP_, 8, 4, NT_>::bytes;     \
-  }
-  VLB_CSM(4, 2, 192) VLB_CSM(2, 4, 192) VLB_CSM(4, 4, 192) VLB_CSM(8, 2, 192) VLB_CSM(4, 2, 384)
-#undef VLB_CSM
+  if (nq0 == 16 && nq1 == 12 && v.tp == 4) return ChanSmem<real, 16, 12, 4>::bytes;
+  if (nq0 == 8 && nq1 == 4 && v.tp == 4) return ChanSmem<real, 8, 4, 4>::bytes;
+  if (nq0 == 8 && nq1 == 4 && v.tp == 8) return ChanSmem<real, 8, 4, 8>::bytes;
   return 0;
 }
 
-template <typename real>
-cudaError_t launch_channel(ChanVariant v, const ChanArgs<real>& a, const ModelArgs& m, const void* kbytes, int nq0,
-                           int nq1, cudaStream_t s) {
-#define VLB_CL(TS_, TP_, NT_)                                                                   \
-  if (v.ts == TS_ && v.tp == TP_ && v.nt == NT_) {                                              \
-    if (nq0 == 16 && nq1 == 12) return go_channel<real, TS_, TP_, 16, 12, NT_>(a, m, kbytes, s); \
-    if (nq0 == 8 && nq1 == 4) return go_channel<real, TS_, TP_, 8, 4, NT_>(a, m, kbytes, s);     \
+// TF32 part of x rounded to nearest, ties away from zero (the rounding of
+// cvt.rna.tf32.f32): the low 13 significand bits cleared.
+static inline uint32_t host_tf32(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return u;
+  return (u + 0x1000u) & 0xffffe000u;
+}
+static inline void host_tf32_split(double x, uint32_t* hi, uint32_t* lo) {
+  const float f = float(x);
+  *hi = host_tf32(f);
+  float h;
+  memcpy(&h, hi, 4);
+  *lo = host_tf32(f - h);
+}
+
+// Axis moment vector of the truncated equilibrium at rest (u = 0), in double.
+static void rest_moment_vector(int kind, int N, double T, double* m) {
+  if (kind == 0) {
+    m[0] = 1.0;
+    if (N >= 1) m[1] = 0.0;
+    for (int l = 2; l <= N; ++l) m[l] = (T - 1.0) * m[l - 2] / double(l);
+    return;
   }
-  VLB_CL(4, 2, 192) VLB_CL(2, 4, 192) VLB_CL(4, 4, 192) VLB_CL(8, 2, 192) VLB_CL(4, 2, 384)
-#undef VLB_CL
+  m[0] = 0.5;
+  if (N >= 1) m[1] = T / std::sqrt(2.0 * 3.14159265358979323846 * T);
+  for (int s = 2; s <= N; ++s) m[s] = double(s - 1) * T * m[s - 2];
+}
+
+template <typename real, int Q0, int Q1>
+static void fill_chan_tables(const AxisTables* ax, const ModelArgs& m, double T0, std::vector<unsigned char>* out) {
+  using Tab = ChanTables<real, Q0, Q1>;
+  using S = ChanShape<Q0, Q1>;
+  out->assign(sizeof(Tab), 0);
+  Tab& t = *reinterpret_cast<Tab*>(out->data());
+  const std::vector<double>&K0 = ax[0].K, &Kt0 = ax[0].Kt, &K1 = ax[1].K, &Kt1 = ax[1].Kt;
+  for (int k = 0; k < Q0 * Q0; ++k) t.K0[k] = real(K0[k]), t.Kt0[k] = real(Kt0[k]);
+  for (int k = 0; k < Q1 * Q1; ++k) t.K1[k] = real(K1[k]), t.Kt1[k] = real(Kt1[k]);
+  // lambda A fragments: a0 = K0[8t+g][8kk+tq], a1 = Kt0[..][8kk+tq], a2 = K0[..][8kk+tq+4], a3 = Kt0[..][8kk+tq+4]
+  for (int mt = 0; mt < S::MT; ++mt)
+    for (int kk = 0; kk < S::KKL; ++kk)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, tq = lane & 3, r = 8 * mt + g;
+        const double v4[4] = {K0[r * Q0 + 8 * kk + tq], Kt0[r * Q0 + 8 * kk + tq], K0[r * Q0 + 8 * kk + tq + 4],
+                              Kt0[r * Q0 + 8 * kk + tq + 4]};
+        for (int q = 0; q < 4; ++q) host_tf32_split(v4[q], &t.fl[mt][kk][0][lane][q], &t.fl[mt][kk][1][lane][q]);
+      }
+  // xi B fragments: b0 = B[8kk+tq][8nn+g], b1 = B[8kk+tq+4][8nn+g], B[j'][2j+e] = (e ? Kt1 : K1)[j][j']
+  for (int kk = 0; kk < S::KKX; ++kk)
+    for (int nn = 0; nn < S::NN; ++nn)
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, tq = lane & 3;
+        const int jj = 4 * nn + (g >> 1), e = g & 1;
+        const std::vector<double>& M = e ? Kt1 : K1;
+        for (int q = 0; q < 2; ++q) {
+          const int jp = 8 * kk + tq + 4 * q;
+          const double x = jp < Q1 ? M[jj * Q1 + jp] : 0.0;
+          host_tf32_split(x, &t.fx[kk][nn][0][lane][q], &t.fx[kk][nn][1][lane][q]);
+        }
+      }
+  for (int k = 0; k < Q0; ++k) {
+    t.p0[k] = real(m.p0[k]);
+    t.iw0[k] = real(m.iw0[k]);
+    t.w0[k] = real(m.w0[k]);
+    for (int s = 0; s < MAXN; ++s) t.tab0[k * MAXN + s] = real(m.tab0[k * MAXN + s]);
+  }
+  for (int k = 0; k < Q1; ++k) {
+    t.p1[k] = real(m.p1[k]);
+    t.iw1[k] = real(m.iw1[k]);
+    t.w1[k] = real(m.w1[k]);
+    for (int s = 0; s < MAXN; ++s) t.tab1[k * MAXN + s] = real(m.tab1[k * MAXN + s]);
+  }
+  // f_eq(1, 0, T0): factors and the incoming wall flux (the denominator of Eq. nw)
+  double mv0[MAXN], mv1[MAXN], g0[Q0], g1[Q1];
+  rest_moment_vector(m.kind0, m.N0, T0, mv0);
+  rest_moment_vector(m.kind1, m.N1, T0, mv1);
+  double den0 = 0.0, den1 = 0.0;
+  for (int k = 0; k < Q0; ++k) {
+    g0[k] = 0.0;
+    for (int s = 0; s <= m.N0; ++s) g0[k] += m.tab0[k * MAXN + s] * mv0[s];
+    t.gw0[k] = real(g0[k]);
+    if (m.p0[k] < 0.0) den0 += g0[k] * m.p0[k];
+  }
+  for (int k = 0; k < Q1; ++k) {
+    g1[k] = 0.0;
+    for (int s = 0; s <= m.N1; ++s) g1[k] += m.tab1[k * MAXN + s] * mv1[s];
+    t.gw1[k] = real(g1[k]);
+    den1 += g1[k];
+  }
+  t.wall_den = den0 * den1;
+  t.ref_flux_pos = m.ref_flux_pos;
+  const double refs[4] = {m.ref_n, m.ref_r, m.ref_p, m.ref_e};
+  for (int k = 0; k < 4; ++k) {
+    t.ref_hi[k] = real(refs[k]);
+    t.ref_lo[k] = real(refs[k] - double(t.ref_hi[k]));
+  }
+  t.N0 = m.N0, t.N1 = m.N1, t.kind0 = m.kind0, t.kind1 = m.kind1;
+}
+
+template <typename real>
+bool channel_tables(int nq0, int nq1, const AxisTables* ax, const ModelArgs& m, double T0,
+                    std::vector<unsigned char>* out) {
+  if (nq0 == 16 && nq1 == 12) return fill_chan_tables<real, 16, 12>(ax, m, T0, out), true;
+  if (nq0 == 8 && nq1 == 4) return fill_chan_tables<real, 8, 4>(ax, m, T0, out), true;
+  return false;
+}
+
+template <typename real>
+cudaError_t launch_channel(ChanVariant v, const ChanArgs<real>& a, const void* kp, int nq0, int nq1, int grid,
+                           cudaStream_t s) {
+#define VLB_CH(q0, q1, TP_)                                                                  \
+  if (nq0 == q0 && nq1 == q1 && v.tp == TP_)                                                 \
+    return (sizeof(real) == 4 && v.tc) ? go_channel<real, q0, q1, TP_, sizeof(real) == 4>(a, kp, grid, s) \
+                                       : go_channel<real, q0, q1, TP_, false>(a, kp, grid, s);
+  VLB_CH(16, 12, 4) VLB_CH(8, 4, 4) VLB_CH(8, 4, 8)
+#undef VLB_CH
   return cudaErrorInvalidValue;
 }
 
@@ -327,17 +481,18 @@ __device__ inline void xi_power_populations(int kind, int N, int nq, const doubl
 // integrated out, projected on the model basis axis by axis.
 template <typename real>
 __global__ void seed_kernel(real* F, long long cells, int Vp, const __grid_constant__ ModelArgs m, const double* n,
-                            const double* u0, const double* u1, const double* T, const double* q0) {
+                            const double* u0, const double* u1, const double* T, const double* q0, CellMap map) {
   __shared__ double A[3][MAXQ], B[2][MAXQ];  // axis 0: xi^0, xi^1, xi^3; axis 1: xi^0, xi^2
   for (long long c = blockIdx.x; c < cells; c += gridDim.x) {
-    const double Tc = T[c], qc = q0 ? q0[c] : 0.0;
+    const long long cc = caller_cell(map, c);  // the fields are in the caller's cell order
+    const double Tc = T[cc], qc = q0 ? q0[cc] : 0.0;
     if (threadIdx.x < 5) {
       const int t = threadIdx.x;
       if (t < 3) {
         const int k = t == 2 ? 3 : t;
-        xi_power_populations(m.kind0, m.N0, m.nq0, m.p0, m.tab0, u0[c], Tc, k, A[t]);
+        xi_power_populations(m.kind0, m.N0, m.nq0, m.p0, m.tab0, u0[cc], Tc, k, A[t]);
       } else {
-        xi_power_populations(m.kind1, m.N1, m.nq1, m.p1, m.tab1, u1[c], Tc, 2 * (t - 3), B[t - 3]);
+        xi_power_populations(m.kind1, m.N1, m.nq1, m.p1, m.tab1, u1[cc], Tc, 2 * (t - 3), B[t - 3]);
       }
     }
     __syncthreads();
@@ -348,7 +503,7 @@ __global__ void seed_kernel(real* F, long long cells, int Vp, const __grid_const
       real val = real(0);
       if (v < V) {
         const int i = v / m.nq1, j = v - i * m.nq1;
-        const double base = n[c] * A[0][i] * B[0][j];
+        const double base = n[cc] * A[0][i] * B[0][j];
         const double t3 = A[2][i] * B[0][j] + A[1][i] * B[1][j];
         const double t1 = A[1][i] * B[0][j];
         const double full = d ? Tc * base + cq * (0.2 * t3 - 0.4 * Tc * t1) : base + cq * (t3 / (5.0 * Tc) - 0.8 * t1);
@@ -362,9 +517,9 @@ __global__ void seed_kernel(real* F, long long cells, int Vp, const __grid_const
 
 template <typename real>
 cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, const double* n, const double* u0,
-                        const double* u1, const double* T, const double* q0, cudaStream_t s) {
+                        const double* u1, const double* T, const double* q0, cudaStream_t s, CellMap map) {
   const long long blocks = cells < 152 * 16 ? cells : 152 * 16;
-  seed_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(F, cells, Vp, m, n, u0, u1, T, q0);
+  seed_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(F, cells, Vp, m, n, u0, u1, T, q0, map);
   return cudaGetLastError();
 }
 
@@ -375,12 +530,13 @@ cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, co
 // same buffer when V == Vp.
 template <typename real>
 __global__ void deviation_kernel(const real* src, real* dst, long long cells, int Vp,
-                                 const __grid_constant__ ModelArgs m, int to_dev) {
+                                 const __grid_constant__ ModelArgs m, int to_dev, CellMap map) {
   __shared__ real buf[2 * MAXQ * MAXQ];
   const int V = m.nq0 * m.nq1;
   for (long long c = blockIdx.x; c < cells; c += gridDim.x) {
+    const long long cc = caller_cell(map, c);  // device cell c is the caller's cell cc
     if (to_dev) {
-      for (int x = threadIdx.x; x < 2 * V; x += blockDim.x) buf[x] = src[c * 2 * V + x];
+      for (int x = threadIdx.x; x < 2 * V; x += blockDim.x) buf[x] = src[cc * 2 * V + x];
       __syncthreads();
       for (int x = threadIdx.x; x < 2 * Vp; x += blockDim.x) {
         const int v = x >> 1, d = x & 1;
@@ -397,7 +553,7 @@ __global__ void deviation_kernel(const real* src, real* dst, long long cells, in
       for (int x = threadIdx.x; x < 2 * V; x += blockDim.x) {
         const int d = x >= V, v = x - d * V;
         const int i = v / m.nq1, j = v - i * m.nq1;
-        dst[c * 2 * V + x] = real(double(buf[2 * v + d]) + m.w0[i] * m.w1[j]);
+        dst[cc * 2 * V + x] = real(double(buf[2 * v + d]) + m.w0[i] * m.w1[j]);
       }
     }
     __syncthreads();
@@ -406,16 +562,16 @@ __global__ void deviation_kernel(const real* src, real* dst, long long cells, in
 
 template <typename real>
 cudaError_t launch_deviation(const real* src, real* dst, long long cells, int Vp, const ModelArgs& m,
-                             int to_deviation, cudaStream_t s) {
+                             int to_deviation, cudaStream_t s, CellMap map) {
   const long long blocks = cells < 152 * 8 ? cells : 152 * 8;
-  deviation_kernel<real><<<int(blocks > 0 ? blocks : 1), 256, 0, s>>>(src, dst, cells, Vp, m, to_deviation);
+  deviation_kernel<real><<<int(blocks > 0 ? blocks : 1), 256, 0, s>>>(src, dst, cells, Vp, m, to_deviation, map);
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- moments (FP64), one warp per cell
 template <typename real>
 __global__ void moments_kernel(const real* F, long long cells, int Vp, const __grid_constant__ ModelArgs m,
-                               double* out) {
+                               double* out, CellMap map) {
   const int lane = threadIdx.x & 31;
   const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -455,7 +611,7 @@ __global__ void moments_kernel(const real* F, long long cells, int Vp, const __g
     q0 = warp_sum<real>(q0);
     q1 = warp_sum<real>(q1);
     if (lane == 0) {
-      double* o = out + c * 9;
+      double* o = out + caller_cell(map, c) * 9;  // in the caller's cell order
       o[0] = n;
       o[1] = u0;
       o[2] = u1;
@@ -470,11 +626,12 @@ __global__ void moments_kernel(const real* F, long long cells, int Vp, const __g
 }
 
 template <typename real>
-cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelArgs& m, double* out, cudaStream_t s) {
+cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelArgs& m, double* out, cudaStream_t s,
+                           CellMap map) {
   long long blocks = (cells * 32 + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
-  moments_kernel<real><<<int(blocks), 256, 0, s>>>(F, cells, Vp, m, out);
+  moments_kernel<real><<<int(blocks), 256, 0, s>>>(F, cells, Vp, m, out, map);
   return cudaGetLastError();
 }
 
@@ -486,14 +643,17 @@ template cudaError_t launch_stage<VLB_REAL>(StageVariant, const StageArgs<VLB_RE
 template cudaError_t launch_init_equilibrium<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, double, double,
                                                        double, double, cudaStream_t);
 template size_t channel_smem_bytes<VLB_REAL>(ChanVariant, int, int);
-template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_REAL>&, const ModelArgs&, const void*, int,
-                                              int, cudaStream_t);
+template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_REAL>&, const void*, int, int, int,
+                                              cudaStream_t);
+template bool channel_tables<VLB_REAL>(int, int, const AxisTables*, const ModelArgs&, double,
+                                       std::vector<unsigned char>*);
 template cudaError_t launch_seed<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
-                                           const double*, const double*, const double*, const double*, cudaStream_t);
+                                           const double*, const double*, const double*, const double*, cudaStream_t,
+                                           CellMap);
 template cudaError_t stage_config<VLB_REAL>(StageVariant, const ModelArgs&, int, int*, int*);
 template cudaError_t launch_deviation<VLB_REAL>(const VLB_REAL*, VLB_REAL*, long long, int, const ModelArgs&, int,
-                                                cudaStream_t);
+                                                cudaStream_t, CellMap);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,
-                                              cudaStream_t);
+                                              cudaStream_t, CellMap);
 
 }  // namespace vlb

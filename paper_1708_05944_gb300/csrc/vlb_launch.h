@@ -2,7 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "vlb_device.cuh"
+#include "vlb_tables.h"
 
 namespace vlb {
 
@@ -41,9 +44,12 @@ template <typename real>
 cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int grid,
                          cudaStream_t s);
 
-// Launch shapes of the channel stage kernel: cells per tile in lambda (ts) and xi (tp), threads.
+// Launch shapes of the channel stage kernel: ts lambda rows per segment of a
+// CTA's march (0: chosen by the host from the SM count; at least n_lambda: one
+// segment), tp xi-columns per strip, nt threads ((tp + 1) x velocities).
 struct ChanVariant {
   int ts, tp, nt;
+  int tc;  // single precision: force contraction on the tensor cores (1) or the CUDA cores (0)
 };
 template <typename real>
 struct ChanArgs;
@@ -52,10 +58,33 @@ struct ChanArgs;
 int channel_variants(int nq0, int nq1, ChanVariant* out);
 template <typename real>
 size_t channel_smem_bytes(ChanVariant v, int nq0, int nq1);
-// kbytes points to the packed K0, Kt0 (nq0 x nq0) and K1, Kt1 (nq1 x nq1) tables in the bulk type.
+// The ChanTables block of a model shape (bytes, bulk-copied by every CTA) for the
+// axis tables, the model arguments and the reservoir / wall temperature T0; false
+// if the shape has no channel kernel.
 template <typename real>
-cudaError_t launch_channel(ChanVariant v, const ChanArgs<real>& a, const ModelArgs& m, const void* kbytes, int nq0,
-                           int nq1, cudaStream_t s);
+bool channel_tables(int nq0, int nq1, const AxisTables* ax, const ModelArgs& m, double T0,
+                    std::vector<unsigned char>* out);
+// One channel stage on `grid` CTAs (a.nx / v.tp strips x a.nseg segments).
+// The split force block (ChanKP) of a model shape from the full matrices of the two
+// axes; false if the shape has no channel kernel or a matrix lacks the reflection
+// symmetry the split relies on.
+bool channel_force_pairs(int nq0, int nq1, const AxisTables* ax, std::vector<unsigned char>* out);
+template <typename real>
+cudaError_t launch_channel(ChanVariant v, const ChanArgs<real>& a, const void* kp, int nq0, int nq1, int grid,
+                           cudaStream_t s);
+
+// Order of a context's cells in device buffers against the caller's order.
+// Couette contexts keep the caller's order (nx = 0).  Channel contexts store cell
+// (s, p) at s * nx + p (xi fastest, one lambda row of the channel after another)
+// and callers see it at p * nl + s (one xi column after another).
+struct CellMap {
+  int nl = 0, nx = 0;
+};
+__host__ __device__ __forceinline__ long long caller_cell(const CellMap& m, long long q) {
+  if (m.nx == 0) return q;
+  const long long s = q / m.nx, p = q - s * m.nx;
+  return p * m.nl + s;
+}
 
 // f_eq(n0, (u0, u1), T0) in every cell.
 template <typename real>
@@ -66,19 +95,21 @@ cudaError_t launch_init_equilibrium(real* F, long long cells, int Vp, const Mode
 // flux, the truncated equilibrium) projected on the model, per cell from device arrays.
 template <typename real>
 cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, const double* n, const double* u0,
-                        const double* u1, const double* T, const double* q0, cudaStream_t s);
+                        const double* u1, const double* T, const double* q0, cudaStream_t s, CellMap map = CellMap{});
 
 // Caller layout F (per cell: f' then f'', V values each) to and from the device
 // layout (per cell: Vp interleaved (f', f'') pairs of the deviation D = F - R;
 // padding zero).  to_deviation = 1: caller -> device, 0: device -> caller; each
-// element is summed in double.  src and dst may be the same buffer when V == Vp.
+// element is summed in double.  src and dst may be the same buffer when V == Vp and
+// the cell map is the identity.
 template <typename real>
 cudaError_t launch_deviation(const real* src, real* dst, long long cells, int Vp, const ModelArgs& m,
-                             int to_deviation, cudaStream_t s);
+                             int to_deviation, cudaStream_t s, CellMap map = CellMap{});
 
 // Per cell, FP64: n, u0, u1, T, T00, T01, T11, q0, q1 (stride 9).
 template <typename real>
-cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelArgs& m, double* out, cudaStream_t s);
+cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelArgs& m, double* out, cudaStream_t s,
+                           CellMap map = CellMap{});
 
 // Per instance L2 norms of Eq. (msites_steady) between mom and prev (stride 9 per cell), into res (3 per instance).
 cudaError_t launch_residual(const double* mom, const double* prev, const InstDesc* inst, const GeoCell* geo,

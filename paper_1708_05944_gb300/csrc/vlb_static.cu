@@ -8,8 +8,10 @@
 // call this entry point, which uses g_step_scratch below for F^(1) and F^(2).
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include "vlb_ctx.h"
 
@@ -19,8 +21,11 @@ namespace {
 constexpr size_t kScratchBytes = size_t(64) << 20;
 static __device__ __align__(256) unsigned char g_step_scratch[kScratchBytes];
 
+// Device address of g_step_scratch per device, looked up on the first call
+// made on that device (host threads may race to fill an entry; they store the
+// same address).
 constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {nullptr};
+std::atomic<void*> g_scratch_ptr[kMaxDevices];
 
 vlb_status static_fail(vlb_ctx* c, vlb_status s, const std::string& msg) {
   c->err = msg;
@@ -63,40 +68,43 @@ cudaError_t launch_one(vlb_ctx* c, int k, const void* prev, const void* fl, void
 extern "C" vlb_status vlb_step_static_scratch(vlb_ctx* c, const void* f_in, void* f_out, double dt,
                                               long long nsteps) {
   if (!c) return VLB_ERR_INVALID;
+  // Couette contexts only: the channel stage has its own kernel and buffers, and this
+  // entry point launches nothing for it
+  if (c->kind != 0) return static_fail(c, VLB_ERR_UNSUPPORTED, "static-scratch stepping covers Couette contexts only");
   if (!f_in || !f_out || f_in == f_out) return static_fail(c, VLB_ERR_INVALID, "need distinct input and output buffers");
-  if (nsteps < 1 || !(dt > 0.0)) return static_fail(c, VLB_ERR_INVALID, "need dt > 0 and nsteps >= 1");
+  if (nsteps < 1 || !(dt > 0.0) || !std::isfinite(dt))
+    return static_fail(c, VLB_ERR_INVALID, "need a finite dt > 0 and nsteps >= 1");
   if (c->Vp != c->V)
     return static_fail(c, VLB_ERR_UNSUPPORTED, "velocity count must be a multiple of 4 for caller-owned buffers");
   const size_t fbytes = size_t(c->total_cells) * 2 * c->Vp * c->esize;
   if (2 * fbytes > kScratchBytes)
     return static_fail(c, VLB_ERR_UNSUPPORTED,
                        "two stage buffers of " + std::to_string(fbytes) + " bytes exceed the 64 MiB static scratch");
+  // the array's address is per device: the context's device must be the current one
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != c->device)
+    return static_fail(c, VLB_ERR_INVALID, "the context's device must be the current device");
   if (dev < 0 || dev >= kMaxDevices) return static_fail(c, VLB_ERR_UNSUPPORTED, "device index out of range");
-  if (!g_scratch_ptr[dev]) {  // first call on this device: device address of the static array
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_step_scratch);
+  void* addr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!addr) {  // first call on this device: device address of the static array
+    e = cudaGetSymbolAddress(&addr, g_step_scratch);
     if (e != cudaSuccess)
       return static_fail(c, VLB_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_ptr[dev] = p;
+    g_scratch_ptr[dev].store(addr, std::memory_order_release);
   }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_ptr[dev]);
+  unsigned char* base = static_cast<unsigned char*>(addr);
   void* s1 = base;
   void* s2 = base + fbytes;
-  // time step for every instance (the context's descriptor copy on the device)
+  // time step for every instance: the same update as vlb_set_dt (a synchronising copy of the
+  // instance descriptors), made only when dt differs from the context's current one
   bool change = false;
   for (int i = 0; i < c->n_inst; ++i) change |= c->inst[i].dt != dt;
   if (change) {
-    for (int i = 0; i < c->n_inst; ++i) {
-      c->inst[i].dt = dt;
-      c->inst[i].dt_f = float(dt);
-    }
-    e = cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * c->n_inst, cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("descriptor copy: ") + cudaGetErrorString(e));
-    e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return static_fail(c, VLB_ERR_CUDA, std::string("descriptor copy: ") + cudaGetErrorString(e));
+    std::vector<double> v(c->n_inst, dt);
+    const vlb_status st = vlb_set_dt(c, v.data());
+    if (st != VLB_OK) return st;
   }
   // the stage kernels work on the deviation D = F - R from the rest state: convert f_in into
   // f_out, step f_out (stage 3 updates it in place: each CTA reads only its own F_l rows), and

@@ -59,6 +59,7 @@ EXPORTS = {
     "vlb_create_channel": (C.c_int, [C.POINTER(vlb_model), C.c_int, C.POINTER(vlb_channel_grid), C.c_double,
                                      C.c_double, C.c_double, C.c_double, C.c_void_p, C.POINTER(C.c_void_p)]),
     "vlb_channel_variants": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "vlb_channel_variant_tensor_cores": (C.c_int, [C.c_void_p, C.c_int]),
     "vlb_sizes": (C.c_int, [C.c_void_p, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
     "vlb_set_walls": (C.c_int, [C.c_void_p, C.POINTER(vlb_wall), C.POINTER(vlb_wall)]),
     "vlb_init_equilibrium": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]),
@@ -336,6 +337,13 @@ class Channel(_Context):
         if n < 0:
             _check(n, self.h)
         return [(int(ts[i]), int(tp[i]), int(nt[i])) for i in range(n)]
+
+    def channel_variant_tensor_cores(self, v):
+        """vlb_channel_variant_tensor_cores: whether launch shape v contracts the force on the tensor cores."""
+        r = _lib.vlb_channel_variant_tensor_cores(self.h, v)
+        if r < 0:
+            _check(r, self.h)
+        return bool(r)
 
     def wall_density(self):
         nw = np.empty(self.n_xi)

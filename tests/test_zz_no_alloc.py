@@ -58,3 +58,31 @@ def test_static_scratch_rejects_oversize_and_aliasing():
         c.step_static_scratch(f, f, 1e-4, 1)
     assert e.value.status == vlb.VLB_ERR_INVALID
     c.close()
+
+
+def test_static_scratch_rejects_channel_contexts():
+    """The entry point steps Couette contexts only: a channel context (small
+    enough for the scratch) gets VLB_ERR_UNSUPPORTED before anything runs, and
+    its own state is untouched."""
+    ch = vlb.Channel("HH(4;8)xH(4;12)", vlb.VLB_FP32_BULK, n_lambda=8, n_xi=16, kn=0.05)
+    before = ch.read_f()
+    f = torch.zeros((8 * 16, 2, 16, 12), dtype=torch.float32, device="cuda")
+    g = torch.zeros_like(f)
+    with pytest.raises(vlb.VlbError) as e:
+        ch.step_static_scratch(f, g, 1e-4, 1)
+    assert e.value.status == vlb.VLB_ERR_UNSUPPORTED
+    assert torch.count_nonzero(g).item() == 0
+    assert np.array_equal(ch.read_f(), before)
+    ch.close()
+
+
+def test_static_scratch_rejects_non_finite_dt():
+    spec = "HH(3;4)xH(3;4)"
+    c = vlb.Couette(spec, vlb.VLB_FP64, [dict(n_cells=16)], [(0.1, 1.0)], [(0.0, 1.0)], [0.1], [1])
+    f = torch.zeros((16, 2, 8, 4), dtype=torch.float64, device="cuda")
+    g = torch.zeros_like(f)
+    for dt in (float("inf"), float("nan"), 0.0, -1e-4):
+        with pytest.raises(vlb.VlbError) as e:
+            c.step_static_scratch(f, g, dt, 1)
+        assert e.value.status == vlb.VLB_ERR_INVALID
+    c.close()
