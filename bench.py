@@ -1,22 +1,19 @@
-"""Benchmark of the chi-formulation circular Couette TVD-RK3 step on GB300.
+"""Benchmark of the vielbein lattice Boltzmann TVD-RK3 step on GB300.
 
-Workload (one "step" = one full TVD-RK3 step, three fused stage kernels, over
-one batch): the circular Couette scale-up case -- 1024 equidistant cells between
-R_in = 1 and R_out = 2, model HH(4;8)xH(4;20) (16 x 20 = 320 velocities), inner
-wall speed 0.1, outer wall at rest, T_w = 1, one instance for each
-Kn in {1e-3, 1e-2, 0.1, 1, 10} (Aoki relaxation time), FP32-bulk storage and
-stencil arithmetic, compensated (float-float) moment sums and an FP64 wall-flux
-balance.  The FP64 path is timed on the same batch and reported beside it, and
-two HBM-scale workloads beside that: the batched Couette case (256 instances,
-~360 MB per distribution copy) and the gradually expanding channel.  Input:
-seeded perturbed equilibrium, synthetic.
+Headline workload (one "step" = one full TVD-RK3 step, three stage launches):
+the gradually expanding channel on its body-fitted grid, 2048 (xi) x 512
+(lambda, tanh-stretched) cells, model HH(4;8)xH(4;12) (16 x 12 = 192
+velocities), Kn = 0.05, particle reservoirs n_in / n_out = 2 / 1 at T0 = 1,
+FP32-bulk storage and stencil arithmetic, compensated density sums and an FP64
+wall-flux balance.  Input: seeded perturbed equilibrium, synthetic.  One
+distribution copy is 1.6 GB, larger than L2, so no flush is needed.
 
-Metric: cell-velocity updates per second (cells x velocities advanced by one
-RK3 step / wall time).  The working set (13 MB) fits in L2, so L2 is flushed
-between timed steps: a 512 MB buffer is written, then read back, so that the
-timed step starts from an L2 holding none of its data and no dirty lines of
-the flush to write back; each step is timed alone with CUDA events on the
-launching stream.
+Metric: cell-velocity updates per second (cells x velocities advanced by one RK3
+step / time), each stage timed with CUDA events on the launching stream.  Beside
+it: the end-to-end rate through the C ABI with pinned host buffers, the stage
+kernel's roofline, the circular Couette scale-up batch (the L2-resident case,
+FP32 and FP64), the batched Couette case (HBM-scale), a bounded time-to-steady
+measurement, the measured FP64 FMA peak and the oracle on the host cores.
 
 --impl reference times the fp64 CPU oracle on the host cores on a bounded
 sample of the same workload.
@@ -43,12 +40,26 @@ KNS = [1e-3, 1e-2, 0.1, 1.0, 10.0]
 U_WALL = 0.1
 DT = 5e-5  # CFL 0.4 with max |p^R| = 5.21 and dR = 1/1024, and below tau_min
 METRIC = "cell-velocity updates/s"
+# floating-point operations of one stage per cell-velocity (both fields) of the Couette
+# scale-up model, counted from the equations: WENO-5 2 x 60, force 2 x 2 (2 Q_R + Q_phi) = 144,
+# moments 10, equilibrium + BGK + RK3 combine 16 (the per-cell equilibrium factors are O(cells))
+FLOP_PER_CELL_VELOCITY_STAGE = 290
 BATCH_N = 256  # instances of the batched Couette measurement
 BATCH_F_SEED = 4  # seed of its perturbed initial populations
 CH_MODEL = "HH(4;8)xH(4;12)"
 CH_KN, CH_NIN, CH_NOUT = 0.05, 2.0, 1.0
 CH_DT = 2e-5  # CFL 0.4 on the wall-adjacent cell of the stretched lambda grid (d lambda = 3.7e-4)
-WORKLOAD = "circular Couette scale-up: 1024 cells x HH(4;8)xH(4;20) (320 velocities), Kn in {1e-3,1e-2,0.1,1,10}"
+COUETTE_WORKLOAD = ("circular Couette scale-up: 1024 cells x HH(4;8)xH(4;20) (320 velocities), "
+                    "Kn in {1e-3,1e-2,0.1,1,10}")
+CH_NL, CH_NX = 512, 2048
+CH_VEL = 192
+CH_SEED = 12  # seed of the channel's perturbed initial populations
+WORKLOAD = (f"gradually expanding channel: {CH_NX} (xi) x {CH_NL} (lambda) cells x {CH_MODEL} ({CH_VEL} velocities), "
+            f"Kn={CH_KN}, reservoirs n_in/n_out = {CH_NIN}/{CH_NOUT}, FP32 bulk")
+# DRAM bytes (read + write) per launch of the channel stage kernel from one ncu capture, keyed by
+# the SHA-256 of the kernel's source at the time of the capture (a changed kernel reports null):
+# see profiles/ for the command and the scaling to the full grid
+CH_TRAFFIC = {}
 
 
 def dist_env():
@@ -130,6 +141,56 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def channel_inputs(vlb):
+    """Perturbed equilibrium f_eq(1, 0, 1) * (1 + 0.01 U(-1, 1)) of the headline channel in the
+    library's caller layout (cell p * n_lambda + s, then f', f'', then the 16 x 12 nodes),
+    float32; the weights come from the library's own quadrature."""
+    from paper_1708_05944_gb300.inputs import perturbation32
+    m = vlb.vlb_parse_model(CH_MODEL)
+    _, w0 = vlb.vlb_quadrature(m, 0)
+    _, w1 = vlb.vlb_quadrature(m, 1)
+    F = perturbation32((CH_NL * CH_NX, 2, 16, 12), seed=CH_SEED)
+    F *= np.outer(w0, w1).astype(np.float32)
+    return F
+
+
+def kernel_source_sha():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1708_05944_gb300", "csrc", "vlb_channel.cuh")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def stage_bytes(units, esize):
+    """Algorithmic bytes of one stage launch, averaged over the three stages: stage 1
+    reads F and writes F^(1) (4 values per cell-velocity: two fields), stages 2 and 3
+    also read F_l (6 values)."""
+    return units * esize * (4 + 6 + 6) / 3.0
+
+
+def channel_oracle_sample(seconds_target=12.0, nx_sample=8):
+    """The fp64 CPU oracle, as it stands, on a bounded sample of the headline workload: a
+    channel of the same model and lambda grid with nx_sample xi-columns (the whole lambda
+    extent, walls and reservoirs included), whole RK3 steps until the target time."""
+    from oracle.channel import ChannelGrid, ChannelOracle
+    from paper_1708_05944_gb300.inputs import perturbation
+    o = ChannelOracle(CH_MODEL, ChannelGrid(CH_NL, nx_sample), CH_KN, n_in=CH_NIN, n_out=CH_NOUT)
+    F = o.initial_state()
+    F = F * perturbation(F.shape, seed=CH_SEED)
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < seconds_target or steps == 0:
+        F = o.step(F, CH_DT)
+        steps += 1
+    dt = time.perf_counter() - t0
+    units = CH_NL * nx_sample * CH_VEL * steps
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count()
+    return units / dt, steps, dt, cores
+
+
 def make_inputs(dtype):
     """Perturbed equilibrium f_eq(1, 0, 1) * (1 + 0.01 U(-1, 1)) in the library layout.
     f_eq(1, 0, 1) has weighted populations w_i w_j (f'') and w_i w_j (f'); the
@@ -184,68 +245,35 @@ def time_device(ctx, torch, stream, steps, warmup, flush, dt=DT):
     return step_ms, step_ms / 3.0
 
 
-def time_e2e(ctx, torch, stream, host_in, host_out, steps):
-    """Same metric through the C ABI with host buffers: H2D of the step's input,
-    one RK3 step, D2H of the result, all inside the timed region."""
-    with torch.cuda.stream(stream):
-        stream.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(steps):
-            ctx.set_f(host_in)
-            ctx.step(DT, 1)
-            ctx.read_f(host_out)
-        stream.synchronize()
-        return time.perf_counter() - t0
-
-
-def oracle_sample(seconds_target=15.0):
-    """The fp64 CPU oracle, as it stands, on a bounded sample: one Kn = 0.1 instance
-    of the workload (1024 cells x 320 velocities), whole RK3 steps until the
-    target time is reached."""
-    from oracle.couette import TAU_AOKI, CouetteGrid, CouetteOracle, Wall
-    from paper_1708_05944_gb300.inputs import perturbation
-    o = CouetteOracle(MODEL, CouetteGrid(N_CELLS), Wall(U_WALL), Wall(0.0), 0.1, TAU_AOKI)
-    F = o.initial_equilibrium()
-    F = F * perturbation(F.shape)
-    t0 = time.perf_counter()
-    steps = 0
-    while time.perf_counter() - t0 < seconds_target or steps == 0:
-        F = o.step(F, DT)
-        steps += 1
-    dt = time.perf_counter() - t0
-    units = N_CELLS * 320 * steps
-    try:
-        cores = len(os.sched_getaffinity(0))
-    except Exception:
-        cores = os.cpu_count()
-    return units / dt, steps, dt, cores
-
-
 def threads_used():
     # numpy element-wise work and einsum without BLAS run on one thread
     return 1
 
 
 def run_reference(args):
+    """The reference arm: the oracle, as it stands, timed on the host cores on bounded
+    samples of the headline workload; rank 0 alone."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    per = []
     for _ in range(args.warmup):
-        oracle_sample(seconds_target=0.0)
-    for _ in range(args.steps):  # each step: one RK3 step of one instance (about 0.5 s)
-        v, steps, dt, _ = oracle_sample(seconds_target=0.0)
+        channel_oracle_sample(seconds_target=0.0, nx_sample=4)
+    per = []
+    for _ in range(args.steps):  # each step: one RK3 step of the 512 x 8 sample (about 3 s)
+        v, steps, dt, _ = channel_oracle_sample(seconds_target=0.0)
         per.append((v, steps, dt))
     value = float(np.mean([p[0] for p in per]))
-    units = N_CELLS * 320
+    units = CH_NL * CH_NX * CH_VEL
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cell-velocity updates/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * units / value, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "one Kn=0.1 instance, whole RK3 steps", "model": MODEL},
+            "config": {"workload": WORKLOAD, "sample": f"{CH_NL} x 8 cells (all lambda rows, 8 xi-columns), "
+                                                      "whole RK3 steps", "model": CH_MODEL},
             "cpu_baseline": {"value": value, "unit": "cell-velocity updates/s", "cores": threads_used(),
                              "kind": "oracle",
-                             "sample": f"{sum(p[1] for p in per)} RK3 steps of one 1024-cell Kn=0.1 instance"},
+                             "sample": f"{sum(p[1] for p in per)} RK3 steps of a {CH_NL} x 8-cell sample of the "
+                                       "channel"},
             "e2e": {"value": value, "unit": "cell-velocity updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -279,7 +307,7 @@ def bench_batched(args, torch, stream, vlb, flush):
     nmom = ctx.read_moments()[0]
     ctx.close()
     units = cells * 320
-    bytes_per_launch = units * 2 * 4 * (2 + 3 + 3) / 3.0
+    bytes_per_launch = stage_bytes(units, 4)
     launch_ms = float(stage_ms.mean())
     hbm, kind = peaks()
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
@@ -296,48 +324,125 @@ def bench_batched(args, torch, stream, vlb, flush):
             "density_finite": bool(np.all(np.isfinite(nmom)))}
 
 
-def bench_channel(args, torch, stream, vlb):
-    """Gradually expanding channel, 512 (lambda) x 2048 (xi) cells x 192 velocities, FP32 bulk.
-    One distribution copy is 1.6 GB, larger than L2, so no flush is needed."""
-    nl, nx = (int(x) for x in args.channel_cells.split("x"))
-    ctx = vlb.Channel(CH_MODEL, vlb.VLB_FP32_BULK, nl, nx, CH_KN, n_in=CH_NIN, n_out=CH_NOUT,
+def bench_channel(args, torch, stream, vlb, world):
+    """The headline: the gradually expanding channel, FP32 bulk, one RK3 step per timed
+    step, each stage launch bracketed by CUDA events on the launching stream (the
+    launches are milliseconds long, so the host's enqueueing between them is hidden).
+    Then the same metric end to end through the C ABI from pinned host buffers."""
+    ctx = vlb.Channel(CH_MODEL, vlb.VLB_FP32_BULK, CH_NL, CH_NX, CH_KN, n_in=CH_NIN, n_out=CH_NOUT,
                       stream=stream.cuda_stream)
-    ctx.init_equilibrium(1.5, 0.0, 0.0, 1.0)
+    host_in = torch.from_numpy(channel_inputs(vlb)).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    ctx.set_f(host_in)
     tuned, _ = ctx.autotune(CH_DT, reps=3)
     shape = ctx.channel_variants()[tuned]
+    tensor_cores = ctx.channel_variant_tensor_cores(tuned)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
-        for _ in range(args.channel_warmup):
+        for _ in range(args.warmup):
             ctx.step(CH_DT, 1)
         stream.synchronize()
-        step_ms, stage_ms = [], []
-        for _ in range(args.channel_steps):
-            marks = [ev() for _ in range(4)]
-            marks[0].record(stream)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        marks = []
+        for _ in range(args.steps):
+            m = [ev() for _ in range(4)]
+            m[0].record(stream)
             for k in (1, 2, 3):
                 ctx.stage(CH_DT, k)
-                marks[k].record(stream)
-            stream.synchronize()
-            t = [marks[0].elapsed_time(marks[k]) for k in (1, 2, 3)]
-            step_ms.append(t[2])
-            stage_ms += [t[0], t[1] - t[0], t[2] - t[1]]
-    n = ctx.read_moments()[0]
+                m[k].record(stream)
+            marks.append(m)
+        stream.synchronize()
+        clocks = sampler.stop()
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        step_ms = np.array([m[0].elapsed_time(m[3]) for m in marks])
+        stage_ms = np.array([m[k - 1].elapsed_time(m[k]) for m in marks for k in (1, 2, 3)])
+        # end to end: H2D of the step's input, one RK3 step, D2H of the result
+        e2e_steps = args.e2e_steps
+        stream.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ctx.set_f(host_in)
+            ctx.step(CH_DT, 1)
+            ctx.read_f(host_out)
+        stream.synchronize()
+        e2e_s = time.perf_counter() - t0
+    nmom = ctx.read_moments()[0]
     ctx.close()
-    units = nl * nx * 192
-    total = float(np.sum(step_ms))
-    bytes_per_launch = units * 2 * 4 * (2 + 3 + 3) / 3.0
-    launch_ms = float(np.mean(stage_ms))
+    units = CH_NL * CH_NX * CH_VEL
+    value, total_ms = whole_job_rate(float(step_ms.sum()), units, args.steps, world)
+    e2e_value, _ = whole_job_rate(e2e_s * 1e3, units, e2e_steps, world)
+    bytes_per_launch = stage_bytes(units, 4)
+    launch_ms = float(stage_ms.mean())
     hbm, kind = peaks()
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
-    return {"workload": f"gradually expanding channel {nx} (xi) x {nl} (lambda) x {CH_MODEL} (192 velocities), "
-                        f"Kn={CH_KN}, reservoirs n_in/n_out = {CH_NIN}/{CH_NOUT}, FP32 bulk",
-            "value": units * len(step_ms) / (total * 1e-3), "unit": "cell-velocity updates/s",
-            "ms_per_step": total / len(step_ms), "steps": len(step_ms),
-            "launch_shape": {"cells_lambda": shape[0], "cells_xi": shape[1], "threads": shape[2], "autotuned": True},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                         "traffic": None, "kernel": "channel_stage_kernel<float>", "peak_source": f"{kind} hbm_gbs",
-                         "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms},
-            "density_finite": bool(np.all(np.isfinite(n)))}
+    sha = kernel_source_sha()
+    traffic = CH_TRAFFIC.get(sha)
+    return {
+        "value": value, "ms_per_step": total_ms / args.steps, "units": units, "clocks": clocks,
+        "launches": 3 * args.steps,
+        "launch_shape": {"rows_per_segment": shape[0], "columns_per_strip": shape[1], "threads": shape[2],
+                         "force": "tensor cores (mma.sync TF32, hi/lo split)" if tensor_cores
+                                  else "CUDA cores (packed FP32x2, reflection-split matrices)",
+                         "autotuned": True},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                     "traffic": traffic, "kernel": f"channel_stage_kernel<float, 16, 12, {shape[1]}, "
+                                                   f"{'true' if tensor_cores else 'false'}>",
+                     "kernel_source_sha": sha, "peak_source": f"{kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
+                     "launch_ms_by_stage": [float(stage_ms[k::3].mean()) for k in range(3)]},
+        "e2e": {"value": e2e_value, "unit": "cell-velocity updates/s", "steps": e2e_steps,
+                "h2d_bytes_per_step": int(host_in.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4)},
+        "density_finite": bool(np.all(np.isfinite(nmom))),
+    }
+
+
+def bench_couette(args, torch, stream, vlb, flush):
+    """The circular Couette scale-up batch (5 x 1024 cells x 320 velocities, one instance
+    per Kn), FP32 bulk and FP64.  Its 13 MB copies fit in L2, so L2 is flushed before
+    each timed step; it is reported as a rate, the L2-resident case."""
+    units = N_CELLS * len(KNS) * 320
+    ctx = make_ctx(vlb.VLB_FP32_BULK, stream.cuda_stream)
+    ctx.set_f(make_inputs(np.float32))
+    tuned32, _ = ctx.autotune(DT, reps=20)
+    shape32 = ctx.variants()[tuned32]
+    step_ms, stage_ms = time_device(ctx, torch, stream, args.couette_steps, 3, flush)
+    ctx.close()
+    ctx64 = make_ctx(vlb.VLB_FP64, stream.cuda_stream)
+    ctx64.set_f(make_inputs(np.float64))
+    tuned64, _ = ctx64.autotune(DT, reps=5)
+    shape64 = ctx64.variants()[tuned64]
+    s64, st64 = time_device(ctx64, torch, stream, max(3, min(args.couette_steps, 20)), 2, flush)
+    ctx64.close()
+    launch_ms = float(stage_ms.mean())
+    b32 = stage_bytes(units, 4)
+    try:
+        fp64_tflops = vlb.vlb_peak_fp64()
+    except Exception:
+        fp64_tflops = None
+    flops_per_launch = units * FLOP_PER_CELL_VELOCITY_STAGE
+    launch64 = float(st64.mean())
+    fp64_achieved = flops_per_launch / (launch64 * 1e-3) / 1e12
+    return {
+        "workload": COUETTE_WORKLOAD + ", FP32 bulk; L2 flushed before each timed step (512 MB written, then read)",
+        "value": units / (float(step_ms.mean()) * 1e-3), "unit": "cell-velocity updates/s",
+        "ms_per_step": float(step_ms.mean()), "steps": len(step_ms), "launch_ms": launch_ms,
+        "achieved_GBps_algorithmic": b32 / (launch_ms * 1e-3) / 1e9,
+        "launch_shape": {"cells_per_cta": shape32[0], "threads": shape32[1], "persistent": bool(shape32[2])},
+        "fp64": {"value": units / (float(s64.mean()) * 1e-3), "unit": "cell-velocity updates/s",
+                 "ms_per_step": float(s64.mean()), "launch_shape": {"cells_per_cta": shape64[0], "threads": shape64[1]},
+                 "roofline": {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
+                              "frac": (fp64_achieved / fp64_tflops) if fp64_tflops else None,
+                              "peak_source": "measured FP64 fma throughput (vlb_peak_fp64, this run)",
+                              "flops_per_cell_velocity_stage": FLOP_PER_CELL_VELOCITY_STAGE,
+                              "kernel": f"couette_stage_kernel<double, TC={shape64[0]}, NT={shape64[1]}>",
+                              "launch_ms": launch64}},
+    }
 
 
 def time_to_steady(args, torch):
@@ -414,88 +519,38 @@ def run_gpu(args):
     from paper_1708_05944_gb300 import vlb
 
     stream = torch.cuda.Stream()
-    sptr = stream.cuda_stream
+    head = bench_channel(args, torch, stream, vlb, world)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    units = N_CELLS * len(KNS) * 320  # cell-velocities of one batch
-
-    # FP32-bulk (headline); the autotuner picks the launch shape on this workload
-    ctx = make_ctx(vlb.VLB_FP32_BULK, sptr)
-    ctx.set_f(make_inputs(np.float32))
-    tuned32, _ = ctx.autotune(DT, reps=20)
-    shape32 = ctx.variants()[tuned32]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    step_ms, stage_ms = time_device(ctx, torch, stream, args.steps, args.warmup, flush)
-    clocks = sampler.stop()
-    torch.cuda.synchronize()
-    value, total_ms = whole_job_rate(float(step_ms.sum()), units, args.steps, world)
-    if world > 1:
-        torch.distributed.barrier()
-    launches = 3 * args.steps
-
-    # roofline of the stage kernel: algorithmic bytes per launch / mean launch time
-    esize = 4
-    bytes_per_step = units * 2 * esize * (2 + 3 + 3)  # stage 1: r+w; stages 2, 3: 2 reads + w
-    bytes_per_launch = bytes_per_step / 3.0
-    launch_ms = float(stage_ms.mean())
-    hbm, peak_kind = peaks()
-    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
-
-    # end to end through the C ABI with pinned host buffers
-    host_in = torch.from_numpy(make_inputs(np.float32)).pin_memory()
-    host_out = torch.empty_like(host_in).pin_memory()
-    e2e_steps = max(3, min(args.steps, 50))
-    e2e_s = time_e2e(ctx, torch, stream, host_in, host_out, e2e_steps)
-    e2e_value, _ = whole_job_rate(e2e_s * 1e3, units, e2e_steps, world)
-    ctx.close()
-
-    # FP64 path on the same batch
-    ctx64 = make_ctx(vlb.VLB_FP64, sptr)
-    ctx64.set_f(make_inputs(np.float64))
-    tuned64, _ = ctx64.autotune(DT, reps=5)
-    shape64 = ctx64.variants()[tuned64]
-    s64, _ = time_device(ctx64, torch, stream, max(3, min(args.steps, 20)), 2, flush)
-    fp64_value, _ = whole_job_rate(float(s64.sum()), units, len(s64), world)
-    ctx64.close()
-
+    couette = bench_couette(args, torch, stream, vlb, flush) if args.workload in ("all", "couette") else None
     batched = bench_batched(args, torch, stream, vlb, flush) if args.workload in ("all", "batched") else None
-    channel = bench_channel(args, torch, stream, vlb) if args.workload in ("all", "channel") else None
-    steady = time_to_steady(args, torch) if args.time_to_steady and rank == 0 else None
+    del flush
+    steady = time_to_steady(args, torch) if (not args.no_time_to_steady and rank == 0) else None
 
     if rank != 0:
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        v, steps, dt, cores = oracle_sample(seconds_target=args.cpu_seconds)
+        v, steps, dt, cores = channel_oracle_sample(seconds_target=args.cpu_seconds)
         cpu = {"value": v, "unit": "cell-velocity updates/s", "cores": threads_used(), "kind": "oracle",
-               "sample": f"{steps} RK3 steps of one 1024-cell Kn=0.1 instance in {dt:.1f} s "
-                         f"({cores} host cores visible, numpy single-threaded)"}
+               "sample": f"{steps} RK3 steps of a {CH_NL} x 8-cell sample of the channel (all lambda rows, 8 "
+                         f"xi-columns) in {dt:.1f} s ({cores} host cores visible, numpy single-threaded)"}
     line = {
-        "metric": METRIC, "value": value, "unit": "cell-velocity updates/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "metric": METRIC, "value": head["value"], "unit": "cell-velocity updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "model": MODEL, "cells": N_CELLS, "velocities": 320,
-                   "instances_per_gpu": len(KNS), "kn": KNS, "precision": "fp32-bulk (compensated moment sums, fp64 wall flux)",
-                   "dt": DT, "l2": "flushed between timed steps (512 MB written, then read back)",
-                   "launch_shape": {"cells_per_cta": shape32[0], "threads": shape32[1], "persistent": bool(shape32[2]),
-                                    "autotuned": True}},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "traffic": None,
-                     "kernel": f"couette_stage_kernel<float, TC={shape32[0]}, 16x20 nodes, NT={shape32[1]}>",
-                     "peak_source": f"{peak_kind} hbm_gbs",
-                     "algorithmic_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms},
+        "config": {"workload": WORKLOAD, "model": CH_MODEL, "cells": [CH_NX, CH_NL], "velocities": CH_VEL,
+                   "grid": "xi in [-10, 40] equidistant, lambda tanh-stretched (A = 0.95), Re_c = 100, H/2 = 1",
+                   "kn": CH_KN, "reservoirs": {"n_in": CH_NIN, "n_out": CH_NOUT, "T0": 1.0}, "dt": CH_DT,
+                   "precision": "fp32-bulk (compensated density sums, fp64 wall flux)",
+                   "l2": "inputs larger than L2 (1.6 GB per distribution copy); no flush",
+                   "launch_shape": head["launch_shape"], "replicas_per_gpu": 1},
+        "roofline": head["roofline"],
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": "cell-velocity updates/s",
-                "h2d_bytes_per_step": int(host_in.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4)},
-        "gpu_launches": launches,
-        "clocks": clocks,
-        "fp64": {"value": fp64_value, "unit": "cell-velocity updates/s", "ms_per_step": float(s64.mean()),
-                 "launch_shape": {"cells_per_cta": shape64[0], "threads": shape64[1]}},
+        "e2e": head["e2e"],
+        "gpu_launches": head["launches"],
+        "clocks": head["clocks"],
+        "couette_scaleup": couette,
         "batched": batched,
-        "channel": channel,
     }
     if steady is not None:
         line["time_to_steady"] = steady
@@ -505,20 +560,17 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20, help="timed RK3 steps of the headline channel")
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="all", choices=["all", "couette", "batched", "channel"],
-                    help="all: the Couette scale-up line plus the batched Couette and channel measurements; "
-                         "batched / channel: the line plus that one")
+    ap.add_argument("--workload", default="all", choices=["all", "channel", "couette", "batched"],
+                    help="all: the channel line with the Couette scale-up and batched measurements beside it")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps (host buffers) of the headline")
+    ap.add_argument("--couette-steps", type=int, default=100, help="timed steps of the Couette scale-up batch")
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batched Couette measurement")
-    ap.add_argument("--channel-cells", default="512x2048", help="lambda x xi cells of the channel measurement")
-    ap.add_argument("--channel-steps", type=int, default=5)
-    ap.add_argument("--channel-warmup", type=int, default=3)
-    ap.add_argument("--time-to-steady", action="store_true",
-                    help="add the time-to-steady measurement (cold and warm-started runs; about a minute)")
+    ap.add_argument("--no-time-to-steady", action="store_true", help="leave out the time-to-steady measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -287,6 +287,12 @@ vlb_status vlb_autotune(vlb_ctx* ctx, double dt, int reps, int* chosen, double* 
  * dt and its wall densities (vlb_wall_density). */
 vlb_status vlb_step_static_scratch(vlb_ctx* ctx, const void* f_in, void* f_out, double dt, long long nsteps);
 
+/* Measured double-precision FMA throughput of the current device in TFLOP/s
+ * (2 flops per fma): the denominator of the roofline of the FP64 stage
+ * kernels.  No counterpart in the paper.  Launches a timing kernel on the
+ * default stream and allocates 8 bytes of device memory; about 0.1 s. */
+vlb_status vlb_peak_fp64(double* tflops);
+
 /* Number of kernels the last vlb_step / vlb_stage call launched. */
 long long vlb_kernel_launches(const vlb_ctx* ctx);
 

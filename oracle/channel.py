@@ -44,7 +44,7 @@ import math
 import numpy as np
 
 from .lbmodel import Model
-from .weno import weno5
+from .weno import upwind_interfaces, weno5
 
 
 def phi(xi, re_c=100.0):
@@ -152,10 +152,8 @@ class ChannelOracle:
         for k, e in ((1, e1), (2, e2), (3, e2)):
             inc = nw[None, :, None, None] * weq[:, None]  # (2, nx, nq0, nq1)
             Gl[:, nl + 2 + k] = np.where(pos[None, None, :, None], e, inc)
-        jl = np.arange(2, nl + 3)  # interfaces s+1/2, s = 0..nl, between Gl[j] and Gl[j+1]
-        upl = weno5(Gl[:, jl - 2], Gl[:, jl - 1], Gl[:, jl], Gl[:, jl + 1], Gl[:, jl + 2])
-        dnl = weno5(Gl[:, jl + 3], Gl[:, jl + 2], Gl[:, jl + 1], Gl[:, jl], Gl[:, jl - 1])
-        Fl_ = np.where((pl >= 0)[None, None, None, :, None], upl, dnl)  # (2, nl+1, nx, nq0, nq1)
+        # interfaces s+1/2, s = 0..nl, between Gl[:, s+2] and Gl[:, s+3]
+        Fl_ = upwind_interfaces(Gl, (pl >= 0)[None, None, None, :, None], axis=1)  # (2, nl+1, nx, nq0, nq1)
         fluxl = g.a[None, :, :, None, None] * PL[None, None, None] * Fl_
         adv = (fluxl[:, 1:] - fluxl[:, :-1]) / g.dl[None, :, None, None, None]
 
@@ -170,10 +168,7 @@ class ChannelOracle:
         for k in (0, 1, 2):
             Hx[:, :, k] = np.where(into_in[None], f_in, F[:, :, 0])
             Hx[:, :, nx + 3 + k] = np.where(into_out[None], f_out, F[:, :, nx - 1])
-        jx = np.arange(2, nx + 3)
-        upx = weno5(Hx[:, :, jx - 2], Hx[:, :, jx - 1], Hx[:, :, jx], Hx[:, :, jx + 1], Hx[:, :, jx + 2])
-        dnx = weno5(Hx[:, :, jx + 3], Hx[:, :, jx + 2], Hx[:, :, jx + 1], Hx[:, :, jx], Hx[:, :, jx - 1])
-        Fx = np.where((Vx >= 0)[None], upx, dnx)  # (2, nl, nx+1, nq0, nq1)
+        Fx = upwind_interfaces(Hx, (Vx >= 0)[None], axis=2)  # (2, nl, nx+1, nq0, nq1)
         fluxx = Vx[None] * Fx
         adv = adv + (fluxx[:, :, 1:] - fluxx[:, :, :-1]) / g.dchi[None, None, :, None, None]
 

@@ -37,7 +37,7 @@ from dataclasses import dataclass
 import numpy as np
 
 from .lbmodel import Model
-from .weno import weno5
+from .weno import upwind_interfaces, weno5
 
 TAU_KN_OVER_NT, TAU_AOKI, TAU_KN_OVER_N = 0, 1, 2
 
@@ -148,14 +148,8 @@ class CouetteOracle:
             G[:, k][:, neg] = ghost[:, neg]
         self.last_nw = (nw_in, nw_out)
 
-        # 4: interface values for interfaces s + 1/2, s = 0..N (between G[j] and G[j+1], j = s + 2)
-        j = np.arange(2, N + 3)
-        up = weno5(G[:, j - 2], G[:, j - 1], G[:, j], G[:, j + 1], G[:, j + 2])
-        dn = weno5(G[:, j + 3], G[:, j + 2], G[:, j + 1], G[:, j], G[:, j - 1])
-        sel = (p0 >= 0)[None, None, :, None]
-        Fl = np.where(sel, up, dn)  # (2, N+1, nq0, nq1)
-        RF = g.Rf[None, :, None, None] * Fl
-        adv = p0[None, None, :, None] * (RF[:, 1:] - RF[:, :-1]) / g.dchi[None, :, None, None]
+        # 4: advection
+        adv = self.advection(G)
 
         # 5: inertial force, (1/R)[(p^phi)^2 K^R f - p^R K~^phi f]
         dfdpR = np.einsum("ik,dskj->dsij", m.K[0], F)
@@ -165,6 +159,16 @@ class CouetteOracle:
         # 6: BGK
         coll = -(F - Feq) / tau[None, :, None, None]
         return -adv - force + coll
+
+    def advection(self, G):
+        """chi-form flux difference p^R (R_{s+1/2} F_{s+1/2} - R_{s-1/2} F_{s-1/2}) / d chi_s
+        (Eqs. flux_kom_R, flux_kom_eta; d chi = R dR) of the ghosted populations G, shape
+        (2, N + 6, nq0, nq1) with G[:, s + 2] holding cell s (s = -2 .. N + 3), from the
+        WENO-5 interface values of the upwind side of each velocity."""
+        p0 = self.m.p[0]
+        Fl = upwind_interfaces(G, (p0 >= 0)[None, None, :, None], axis=1)  # (2, N+1, nq0, nq1)
+        RF = self.g.Rf[None, :, None, None] * Fl
+        return p0[None, None, :, None] * (RF[:, 1:] - RF[:, :-1]) / self.g.dchi[None, :, None, None]
 
     def stage(self, k: int, dt: float, F_l, F_prev):
         """One TVD-RK3 stage, Eq. (rk3): k = 1, 2, 3 with F_prev = F_l, F^(1), F^(2)."""

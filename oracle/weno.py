@@ -58,3 +58,17 @@ def weno5_weights(a, b, c, d, e):
         t = [D[q] / s[q] ** 2 for q in range(3)]
     tot = sum(t)
     return [x / tot for x in t]
+
+
+def upwind_interfaces(G, positive, axis=1):
+    """Interface values between G[j] and G[j + 1] along `axis`, j = 2 .. len - 4 (the
+    interfaces s + 1/2 of data with three ghost layers on each side): the stencil
+    (G[j-2], ..., G[j+2]) where `positive` holds (advection velocity >= 0), the
+    mirror stencil (G[j+3], G[j+2], G[j+1], G[j], G[j-1]) elsewhere.  `positive`
+    broadcasts against the result."""
+    n = G.shape[axis]
+    j = np.arange(2, n - 3)
+    at = lambda k: np.take(G, j + k, axis=axis)
+    up = weno5(at(-2), at(-1), at(0), at(1), at(2))
+    dn = weno5(at(3), at(2), at(1), at(0), at(-1))
+    return np.where(positive, up, dn)

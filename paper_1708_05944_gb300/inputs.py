@@ -20,6 +20,16 @@ def perturbation(shape, seed: int = PARITY_SEED, amplitude: float = 0.01) -> np.
     return 1.0 + amplitude * rng.uniform(-1.0, 1.0, size=shape)
 
 
+def perturbation32(shape, seed: int = PARITY_SEED, amplitude: float = 0.01) -> np.ndarray:
+    """Multiplicative factors 1 + amplitude * U(-1, 1) drawn in float32 (for inputs of
+    gigabytes, where a float64 draw would double the host memory)."""
+    rng = np.random.default_rng(seed)
+    out = rng.random(size=shape, dtype=np.float32)
+    out *= np.float32(2.0 * amplitude)
+    out += np.float32(1.0 - amplitude)
+    return out
+
+
 def couette_instances(n_inst: int, seed: int = BATCH_SEED, n_min: int = 64, n_max: int = 1024,
                       log10_kn=(-3.0, 1.0)):
     """Circular Couette instances: cells ~ U{n_min..n_max}, log10 Kn ~ U[log10_kn],

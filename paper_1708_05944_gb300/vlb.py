@@ -96,6 +96,7 @@ EXPORTS = {
     "vlb_no_last_error": (C.c_char_p, [C.c_void_p]),
     "vlb_no_destroy": (None, [C.c_void_p]),
     "vlb_kernel_launches": (C.c_longlong, [C.c_void_p]),
+    "vlb_peak_fp64": (C.c_int, [C.POINTER(C.c_double)]),
     "vlb_last_error": (C.c_char_p, [C.c_void_p]),
     "vlb_destroy": (None, [C.c_void_p]),
 }
@@ -411,3 +412,10 @@ class NeuralOperator:
         loss = C.c_double()
         self._chk(_lib.vlb_no_train_step(self.h, _ptr(c), _ptr(t), c.shape[0], lr, C.byref(loss)))
         return loss.value
+
+
+def vlb_peak_fp64():
+    """vlb_peak_fp64: measured FP64 fma throughput of the current device, TFLOP/s."""
+    t = C.c_double()
+    _check(_lib.vlb_peak_fp64(C.byref(t)))
+    return t.value

@@ -161,3 +161,28 @@ def test_channel_graph_follows_changed_parameters():
     assert np.array_equal(a.read_f(), b.read_f())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", [vlb.VLB_FP64, vlb.VLB_FP32_BULK])
+def test_table_iv_rows(prec):
+    # populations piecewise constant in runs of four cells along both lambda and xi: every
+    # five-point stencil holds at most one jump, so the indicators vanish in each combination
+    # of Table IV (one, two, three), in either precision, on every launch shape
+    nl, nx = 12, 16
+    o = ChannelOracle(MODEL, ChannelGrid(nl, nx), 0.05)
+    F = o.initial_state()
+    a = np.sign(perturbation(F.shape[3:], seed=41, amplitude=1.0) - 1.0)
+    ks = ((np.arange(nl) // 4) % 3 - 1).astype(np.float64)
+    kp = ((np.arange(nx) // 4) % 3 - 1).astype(np.float64)
+    F0 = F * (1.0 + 0.01 * a[None, None, None] * (ks[:, None] + kp[None, :])[None, :, :, None, None])
+    dt = 1e-3
+    ref = o.step(F0, dt)
+    c = vlb.Channel(MODEL, prec, nl, nx, 0.05)
+    dtype = np.float64 if prec == vlb.VLB_FP64 else np.float32
+    for v in range(len(c.channel_variants())):
+        c.set_variant(v)
+        c.set_f(to_lib(F0).astype(dtype))
+        c.step(dt, 1)
+        got = to_oracle(c.read_f(), nl, nx)
+        assert rel_err(got, ref) < (1e-12 if prec == vlb.VLB_FP64 else 1e-6), v
+    c.close()

@@ -14,6 +14,7 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
 from paper_1708_05944_gb300 import vlb  # noqa: E402
+from paper_1708_05944_gb300.inputs import perturbation  # noqa: E402
 from tests.helpers import make_case, rel_err, to_lib, to_oracle  # noqa: E402
 
 CONFIG1 = "HH(3;4)xH(3;4)"
@@ -200,4 +201,117 @@ def test_knudsen_set_after_creation():
         c.set_knudsen(0.0)
     with pytest.raises(vlb.VlbError):
         vlb._check(vlb._lib.vlb_set_channel_reservoirs(c.h, 2.0, 1.0, 1.0), c.h)
+    c.close()
+
+
+def _golden(name):
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        return json.load(f)
+
+
+def test_fp64_config1_ten_thousand_steps():
+    # the whole configured run: 32 cells, HH(3;4)xH(3;4), Kn = 0.1, dt = 1e-3, 10^4 steps, against
+    # the oracle's run (tests/golden/make_oracle_references.py); 1e-10 relative
+    ref = _golden("couette_config1_10000_steps.json")
+    o, F0, grid = make_case(CONFIG1, 32)
+    c = ctx_for(CONFIG1, vlb.VLB_FP64, [grid], [(0.1, 1.0)], [(0.0, 1.0)], [0.1], [1])
+    c.set_f(to_lib(F0))
+    c.step_graph(1e-3, 10000)
+    assert rel_err(to_oracle(c.read_f()), np.asarray(ref["F"])) < 1e-10
+    n, u0, u1, T = c.read_moments()
+    assert np.abs(n / np.asarray(ref["n"]) - 1).max() < 1e-10
+    assert np.abs(T / np.asarray(ref["T"]) - 1).max() < 1e-10
+    assert np.abs(u1 - np.asarray(ref["u1"])).max() < 1e-10 * 0.1
+    c.close()
+
+
+@pytest.mark.parametrize("kn", [1e-3, 0.1, 10.0])
+def test_fp32_bulk_one_stage_and_hundred_steps(kn):
+    # FP32-bulk storage and stencil arithmetic against the FP64 oracle: moments within 1e-5
+    # after a single stage and after 100 steps (64 cells of the scale-up model)
+    o, F0, grid = make_case(CONFIG2, 64, kn=kn, tau_mode=1, u_in=0.2)
+    dt = 5e-4 if kn > 1e-2 else 1e-4
+    c = ctx_for(CONFIG2, vlb.VLB_FP32_BULK, [grid], [(0.2, 1.0)], [(0.0, 1.0)], [kn], [1])
+    c.set_f(to_lib(F0).astype(np.float32))
+    F1 = o.stage(1, dt, F0, F0)
+    c.stage(dt, 1)
+
+    def check(F):
+        n, u0, u1, T = c.read_moments()
+        on, ou0, ou1, oT = o.m.moments(F)
+        assert np.abs(n / on - 1).max() < 1e-5
+        assert np.abs(T / oT - 1).max() < 1e-5
+        assert np.abs(u0 - ou0).max() < 1e-5 and np.abs(u1 - ou1).max() < 1e-5
+
+    check(F1)
+    c.stage(dt, 2)
+    c.stage(dt, 3)
+    F = o.step(F0, dt)
+    for _ in range(99):
+        F = o.step(F, dt)
+    c.step(dt, 99)
+    check(F)
+    c.close()
+
+
+def test_fp32_bulk_steady_state():
+    # the steady state of a small instance of the scale-up model, FP32 bulk against the
+    # oracle's (tests/golden/make_oracle_references.py): moments within 1e-5
+    ref = _golden("couette_steady_16x320.json")
+    grid = dict(n_cells=16, r_in=1.0, r_out=2.0, stretch_A=0.0, stretch_delta=0.5)
+    c = ctx_for(CONFIG2, vlb.VLB_FP32_BULK, [grid], [(0.2, 1.0)], [(0.0, 1.0)], [0.1], [1])
+    c.init_equilibrium()
+    c.step_graph(ref["dt"], ref["steps"])
+    n, u0, u1, T = c.read_moments()
+    assert np.abs(n / np.asarray(ref["n"]) - 1).max() < 1e-5
+    assert np.abs(T / np.asarray(ref["T"]) - 1).max() < 1e-5
+    assert np.abs(u1 - np.asarray(ref["u1"])).max() < 1e-5
+    assert np.abs(u0 - np.asarray(ref["u0"])).max() < 1e-5
+    c.close()
+
+
+def plateau_input(o, seed, run=4, amplitude=0.02):
+    """Equilibrium populations times 1 + amplitude * a_ij * k(s), with a_ij = +-1 drawn from the
+    seeded generator and k(s) piecewise constant in runs of `run` cells: every five-point stencil
+    holds at most one jump, so its indicators vanish in every combination of Table IV (one, two
+    or all three), in either precision."""
+    F = o.initial_equilibrium()
+    a = np.sign(perturbation(F.shape[2:], seed=seed, amplitude=1.0) - 1.0)
+    k = ((np.arange(F.shape[1]) // run) % 3 - 1).astype(np.float64)
+    return F * (1.0 + amplitude * a[None, None] * k[None, :, None, None])
+
+
+@pytest.mark.parametrize("prec", [vlb.VLB_FP64, vlb.VLB_FP32_BULK])
+def test_table_iv_rows(prec):
+    spec, n = CONFIG2, 40
+    o, _, grid = make_case(spec, n, kn=0.3, tau_mode=1, u_in=0.15)
+    F0 = plateau_input(o, seed=77)
+    c = ctx_for(spec, prec, [grid], [(0.15, 1.0)], [(0.0, 1.0)], [0.3], [1])
+    dtype = np.float64 if prec == vlb.VLB_FP64 else np.float32
+    c.set_f(to_lib(F0).astype(dtype))
+    dt = 4e-4
+    F = o.step(F0, dt)
+    c.step(dt, 1)
+    got = to_oracle(c.read_f())
+    if prec == vlb.VLB_FP64:
+        assert rel_err(got, F) < 1e-13
+    else:
+        assert rel_err(got, F) < 1e-6
+        n_, u0, u1, T = c.read_moments()
+        on, ou0, ou1, oT = o.m.moments(F)
+        assert np.abs(n_ / on - 1).max() < 1e-6 and np.abs(T / oT - 1).max() < 1e-6
+    c.close()
+
+
+def test_kn_over_n_relaxation_time():
+    # tau = Kn / n (vlb_tau_mode 2), three stages against the oracle
+    o, F0, grid = make_case(CONFIG1, 20, kn=0.05, tau_mode=2, u_in=0.1)
+    c = ctx_for(CONFIG1, vlb.VLB_FP64, [grid], [(0.1, 1.0)], [(0.0, 1.0)], [0.05], [2])
+    c.set_f(to_lib(F0))
+    dt = 1e-3
+    F = o.step(F0, dt)
+    c.step(dt, 1)
+    assert rel_err(to_oracle(c.read_f()), F) < 1e-13
     c.close()

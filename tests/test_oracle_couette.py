@@ -145,3 +145,78 @@ def test_steady_state_in_the_free_molecular_limit():
         assert 1.0 < x.mean() / exact < 1.25
     willis = 0.1 * R / math.pi * (np.arcsin(1.0 / R) - np.sqrt(1.0 - R ** -2) / R)
     assert np.abs(mom["u1"] - willis).max() / 0.1 < 0.10
+
+
+def _ghosted_centres(N, A, delta=0.5, r_in=1.0, r_out=2.0):
+    """Cell centres s = -3 .. N+2 of the grid continued past both walls (equidistant in R,
+    or in eta on the tanh-stretched grid), for exact ghost values of a smooth profile."""
+    s = np.arange(-3, N + 3) + 0.5
+    if A == 0.0:
+        return r_in + (r_out - r_in) * s / N
+    A0 = max(delta, 1.0 - delta)
+    e_in, e_out = -math.atanh(A * delta / A0), math.atanh(A * (1.0 - delta) / A0)
+    return r_in + (r_out - r_in) * (delta + A0 / A * np.tanh(e_in + s * (e_out - e_in) / N))
+
+
+@pytest.mark.parametrize("A", [0.0, 0.9])
+def test_chi_advection_is_second_order(A):
+    """The chi-form flux difference p^R (R F)|_{s-1/2}^{s+1/2} / d chi of WENO-5 interface
+    values approximates (p^R / R) d(R f)/dR at second order when V = p^R R varies across
+    the cell (Sec. III.D), on the equidistant and on the tanh-stretched grid, for both
+    signs of p^R (the mirror stencil on the negative side).  Exact ghosts, smooth profile."""
+    f = lambda R: np.exp(-(R - 1.4) ** 2) * (1.0 + 0.2 * R)
+    df = lambda R: np.exp(-(R - 1.4) ** 2) * (0.2 - 2.0 * (R - 1.4) * (1.0 + 0.2 * R))
+    errs = []
+    for N in (32, 64, 128):
+        g = CouetteGrid(N, A=A)
+        o = CouetteOracle("HH(2;3)xH(2;3)", g, Wall(0.0), Wall(0.0), 1.0, TAU_KN_OVER_N)
+        p0 = o.m.p[0]
+        Rg = _ghosted_centres(N, A)
+        G = np.broadcast_to(f(Rg)[None, :, None, None], (2, N + 6) + tuple(o.m.nq)).copy()
+        adv = o.advection(G)
+        R = g.Rc
+        exact = p0[None, None, :, None] * (f(R) / R + df(R))[None, :, None, None]
+        errs.append(np.abs(adv - exact).max())
+    order = np.log2(errs[0] / errs[1]), np.log2(errs[1] / errs[2])
+    assert 1.9 < min(order) and max(order) < 2.2, (errs, order)
+
+
+def test_residual_norms_on_the_equidistant_grid():
+    """Eq. (msites_steady) with the rectangle rule of Sec. VI.E: on the equidistant grid the
+    weights R_s dR are the midpoint rule of int R dR, exact for a constant integrand, so
+    constant relative changes a of n and b of T and a uniform change c u_w of u^phi give the
+    norms |a|, |b|, |c| times sqrt((R_out^2 - R_in^2) / 2).  The density and temperature
+    enter as ratios (n varies across the gap here), the velocity scaled by u_w."""
+    r_in, r_out, u_w = 1.0, 2.5, 0.37
+    g = CouetteGrid(40, r_in, r_out)
+    o = CouetteOracle("HH(2;3)xH(2;3)", g, Wall(u_w), Wall(0.0), 1.0, TAU_KN_OVER_N)
+    R = g.Rc
+    n0, T0, u0 = 2.0 + 0.3 * np.sin(3 * R), 1.0 + 0.1 * R, 0.2 / R
+    a, b, c = 3e-3, -7e-4, 2e-3
+    l2u, l2n, l2T = o.residual((n0 * (1 + a), 0 * R, u0 + c * u_w, T0 * (1 + b)), (n0, 0 * R, u0, T0), u_w)
+    S = math.sqrt((r_out ** 2 - r_in ** 2) / 2.0)
+    assert l2n == pytest.approx(abs(a) * S, rel=1e-12)
+    assert l2T == pytest.approx(abs(b) * S, rel=1e-12)
+    assert l2u == pytest.approx(abs(c) * S, rel=1e-12)
+
+
+@pytest.mark.parametrize("A", [0.5, 0.95])
+def test_residual_norms_on_the_stretched_grid(A):
+    """On the stretched grid the rule is the rectangle rule in eta with the Jacobian
+    (A0/A)(R_out - R_in) / cosh^2(eta) (Sec. VI.E): for the relative change a(R) = (R - R_in)^2
+    the squared norm tends to int R (R - R_in)^4 dR = L^6/6 + R_in L^5/5 (L = R_out - R_in) at
+    second order in the cell size."""
+    r_in, r_out = 1.0, 2.0
+    L = r_out - r_in
+    exact = L ** 6 / 6.0 + r_in * L ** 5 / 5.0
+    errs = []
+    for N in (50, 100, 200):
+        g = CouetteGrid(N, r_in, r_out, A=A)
+        o = CouetteOracle("HH(2;3)xH(2;3)", g, Wall(0.1), Wall(0.0), 1.0, TAU_KN_OVER_N)
+        R = g.Rc
+        one = np.ones(N)
+        _, l2n, _ = o.residual((one * (1 + (R - r_in) ** 2), 0 * R, 0 * R, one), (one, 0 * R, 0 * R, one), 0.1)
+        errs.append(abs(l2n ** 2 - exact) / exact)
+    order = np.log2(errs[0] / errs[1]), np.log2(errs[1] / errs[2])
+    assert 1.8 < min(order) and max(order) < 2.2, (errs, order)
+    assert errs[-1] < 2e-3
