@@ -446,14 +446,15 @@ def bench_couette(args, torch, stream, vlb, flush):
 
 
 def time_to_steady(args, torch):
-    """The second metric: steps and seconds until a batch of held-out Couette
-    instances stays within 1e-3 of its steady profile, started from the rest
-    state (the paper's start) and from the learned warm start.  The network is
-    trained here first, on steady states the solver computes (its cost is
-    reported).  Seconds per step of the same batch are measured for the FP32
-    and the FP64 solver; the FP64 time to steady is its seconds per step times
-    the cold FP32 run's step count (the two paths converge to the same profile
-    within the tolerance).  Reduced scale: see the workload string."""
+    """The second metric: how long a batch of held-out Couette instances takes to reach a
+    steady state, judged as the paper does by the L2 norms of Eq. (msites_steady) between
+    checks (here every 500 steps, about one time unit at these time steps) falling below a
+    threshold (1e-6, the metric's).  Three solvers run the same batch to the same criterion,
+    each timed as a whole: the plain FP64 GPU solver from rest (the paper's start), the
+    FP32-bulk batched solver from rest, and the FP32-bulk solver seeded by the learned warm
+    start.  The network is trained first on steady states the solver computes (its cost is
+    reported apart).  With the epsilon-free weights some instances never get below ~1e-5
+    (the oracle shows the same floor); they count as not converged within the horizon."""
     from paper_1708_05944_gb300 import vlb, warmstart as W
     from paper_1708_05944_gb300.inputs import HELDOUT_SEED, TRAIN_SEED, couette_instances
     kn_range = (-1.0, 1.0)
@@ -470,40 +471,51 @@ def time_to_steady(args, torch):
     t1 = time.perf_counter()
     hist = ws.fit(W.conditions(train), targets, steps=1500, batch=64, lr=2e-3)
     t_train = time.perf_counter() - t1
-    held = couette_instances(48, seed=HELDOUT_SEED, n_min=64, n_max=96, log10_kn=kn_range)
-    chunk, n_chunks, tol = 400, 200, 1e-3
-    cold, warm, e0, _ = W.compare(held, ws, chunk=chunk, n_chunks=n_chunks, tol=tol)
+    held = couette_instances(args.tts_instances, seed=HELDOUT_SEED, n_min=64, n_max=96, log10_kn=kn_range)
     t2 = time.perf_counter()
     seeds = W.seed_fields(held, ws.predict_instances(held))
     t_seed = time.perf_counter() - t2
     ws.close()
-    per_step = {}
-    for name, prec, n in (("fp32", vlb.VLB_FP32_BULK, 2001), ("fp64", vlb.VLB_FP64, 201)):
+    check, threshold, horizon = 500, args.tts_threshold, args.tts_steps
+    runs, convs = {}, {}
+    for name, prec, warm in (("plain_fp64", vlb.VLB_FP64, False), ("batched_fp32", vlb.VLB_FP32_BULK, False),
+                             ("warm_fp32", vlb.VLB_FP32_BULK, True)):
         ctx = W.make_context(held, precision=prec)
-        ctx.init_equilibrium()
-        ctx.step_graph(0.0, 30)
+        if warm:
+            ctx.init_from_moments(*seeds)
+        else:
+            ctx.init_equilibrium()
         torch.cuda.synchronize()
         a = time.perf_counter()
-        ctx.step_graph(0.0, n)
-        ctx.read_moments()
-        per_step[name] = (time.perf_counter() - a) / n
+        taken, res, conv = ctx.run_to_steady(0.0, check, threshold, horizon)
+        secs = time.perf_counter() - a
         ctx.close()
-    horizon = chunk * n_chunks
-    cc = np.where(cold < 0, horizon, cold)
-    wc = np.where(warm < 0, horizon, warm)
+        ok = conv > 0
+        convs[name] = conv
+        runs[name] = {"seconds": secs + (t_seed if warm else 0.0), "steps_taken": int(taken),
+                      "seconds_per_step": secs / max(taken, 1), "converged": int(ok.sum()),
+                      "steps_mean_converged": float(conv[ok].mean()) if ok.any() else None,
+                      "steps_max_converged": int(conv[ok].max()) if ok.any() else None,
+                      "residual_median_at_end": float(np.median(res))}
     cells = sum(i["n_cells"] for i in held)
+    # the instances every run brought below the threshold: each solver's time to converge
+    # all of them (its last converged check times its seconds per step, plus the seed)
+    common = np.all([convs[k] > 0 for k in convs], axis=0)
+    to_common = {}
+    for k in runs:
+        if common.any():
+            to_common[k] = float(convs[k][common].max()) * runs[k]["seconds_per_step"] + (
+                t_seed if k == "warm_fp32" else 0.0)
     return {
         "workload": f"{len(held)} held-out Couette instances, {cells} cells in total (64..96 each), HH(4;8)xH(4;20), "
                     "log10 Kn ~ U[-1, 1], inner wall speed ~ U[0.01, 0.5], R_out/R_in ~ U[1.5, 4]; network trained on "
                     "192 solver steady states on 64 cells",
-        "criterion": f"first step after which max(n, u^phi / u_w, T) RMS deviation from the steady profile stays < {tol}",
-        "steps_cold": {"mean": float(cc.mean()), "max": int(cc.max()), "never": int((cold < 0).sum())},
-        "steps_warm": {"mean": float(wc.mean()), "max": int(wc.max()), "never": int((warm < 0).sum())},
-        "seed_error_median": float(np.median(e0)),
-        "seconds_per_step": per_step,
-        "seconds_to_steady": {"cold_fp64": per_step["fp64"] * float(cc.max()),
-                              "cold_fp32": per_step["fp32"] * float(cc.max()),
-                              "warm_fp32": per_step["fp32"] * float(wc.max()) + t_seed},
+        "criterion": f"max(L2_u, L2_n, L2_T) of Eq. (msites_steady) between checks {check} steps apart < {threshold:g}; "
+                     f"horizon {horizon} steps",
+        "runs": runs,
+        "instances_converged_by_all": int(common.sum()),
+        "seconds_to_steady_common": to_common,
+        "speedup_vs_plain_fp64": {k: to_common["plain_fp64"] / to_common[k] for k in to_common},
         "warm_start_cost_s": {"training_data": t_data, "training": t_train, "seed": t_seed,
                               "final_loss": float(hist[-50:].mean())},
     }
@@ -571,6 +583,9 @@ def main():
     ap.add_argument("--couette-steps", type=int, default=100, help="timed steps of the Couette scale-up batch")
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batched Couette measurement")
     ap.add_argument("--no-time-to-steady", action="store_true", help="leave out the time-to-steady measurement")
+    ap.add_argument("--tts-instances", type=int, default=24, help="held-out instances of the time-to-steady batch")
+    ap.add_argument("--tts-threshold", type=float, default=1e-6, help="residual threshold of the time to steady")
+    ap.add_argument("--tts-steps", type=int, default=20000, help="step horizon of the time-to-steady runs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

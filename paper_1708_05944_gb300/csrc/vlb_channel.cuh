@@ -118,7 +118,9 @@ struct ChanSmem {
   using S = ChanShape<Q0, Q1>;
   using Tab = ChanTables<real, Q0, Q1>;
   static constexpr bool F32 = sizeof(real) == 4;
-  static constexpr int NT = (TP + 1) * S::V;  // TP column groups and one extra group
+  static constexpr int NSYNC = (TP + 1) * S::V;  // TP column groups and one extra group, in step
+  static constexpr int NT = NSYNC + 64;          // and two equilibrium warps running ahead of them
+  static constexpr int NPR = 4;                  // moment-partial ring (rows r .. r+3)
   static constexpr int PD = F32 ? 2 : 1;      // prefetch distance in rows
   static constexpr int NRING = 4 + PD;        // ring rows
   static constexpr int NB = PD + 1;           // mbarriers of the step groups (one more for the prologue)
@@ -126,8 +128,10 @@ struct ChanSmem {
   static constexpr int RC = TP + 6;           // cells of a ring row
   static constexpr size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   static constexpr size_t rowb = size_t(S::ROW) * sizeof(real);
+  // mbarriers: NB step groups, the prologue, NPR partials-ready, NEQ equilibrium-ready
   static constexpr size_t bar_off = 0;
-  static constexpr size_t tab_off = 32;
+  static constexpr int NBAR = NB + 1 + NPR + NEQ;
+  static constexpr size_t tab_off = 128;
   static constexpr size_t ring_off = al(tab_off + sizeof(Tab));
   static constexpr size_t geo_off = ring_off + size_t(NRING) * RC * rowb;
   static constexpr size_t xif_off = al(geo_off + size_t(NRING) * TP * sizeof(ChanCell<real>));
@@ -138,14 +142,14 @@ struct ChanSmem {
   static constexpr size_t res_off = al(eq_off + size_t(NEQ) * TP * S::EQW * sizeof(real));
   static constexpr size_t mvs_off = al(res_off + size_t(NEQ) * 2 * Q1 * sizeof(real));
   static constexpr size_t red_off = al(mvs_off + size_t(TP + 2) * 4 * MAXN * sizeof(real));
-  static constexpr size_t wred_off = al(red_off + size_t(2) * TP * S::NWC * 4 * sizeof(real));
+  static constexpr size_t wred_off = al(red_off + size_t(NPR) * TP * S::NWC * 4 * sizeof(real));
   static constexpr size_t nwv_off = al(wred_off + size_t(TP) * S::NWC * sizeof(real));
   static constexpr size_t bytes = al(nwv_off + size_t(TP) * sizeof(double));
   static_assert(sizeof(Tab) % 16 == 0, "tables are one bulk copy");
   static_assert(rowb % 16 == 0 && (TP * sizeof(ChanCell<real>)) % 16 == 0, "rows are bulk copies");
   static_assert(ring_off % 16 == 0 && geo_off % 16 == 0, "bulk destinations are 16-byte aligned");
   static_assert(xif_off % 16 == 0 && lbl_off % 16 == 0 && lbx_off % 16 == 0, "pair arrays are aligned");
-  static_assert(bar_off + (NB + 1) * sizeof(uint64_t) <= tab_off, "mbarriers fit before the tables");
+  static_assert(bar_off + NBAR * sizeof(uint64_t) <= tab_off, "mbarriers fit before the tables");
   static_assert(TP >= 3, "the inlet/outlet ghosts of a strip come from its own first/last column");
   static_assert(NT <= 1024, "one thread per (column, velocity) and an extra group");
 };
@@ -403,10 +407,13 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   constexpr bool F32 = L::F32;
   extern __shared__ __align__(128) unsigned char smem[];
 
+  constexpr int NSYNC = L::NSYNC;  // threads of the named barrier the step phases use
   const int tid = threadIdx.x, lane = tid & 31;
   const bool is_main = tid < NMAIN;
+  const bool is_eqw = tid >= NSYNC;       // the two equilibrium warps
+  const int qw = is_eqw ? (tid - NSYNC) >> 5 : -1;
   const int c = is_main ? tid / V : TP;  // column of a main thread; TP marks the extra group
-  const int v = is_main ? tid - c * V : tid - NMAIN;
+  const int v = is_main ? tid - c * V : (is_eqw ? lane : tid - NMAIN);
   const int i = v / Q1, j = v - i * Q1;
   const int wc = v >> 5;                             // warp within the group
   const int mw = is_main ? tid >> 5 : -1;            // main warp index
@@ -424,6 +431,8 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   const int pa = max(p0 - 3, 0), pb = min(p0 + TP + 3, nx);  // xi cells of a ring row in memory
 
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off);  // NB step groups, then the prologue
+  uint64_t* pready = bar + NB + 1;     // [NPR] moment partials of row r in slot r % NPR written
+  uint64_t* eready = pready + L::NPR;  // [NEQ] equilibrium record of row r in slot r % NEQ written
   const Tab& tb = *reinterpret_cast<const Tab*>(smem + L::tab_off);
   real* ring = reinterpret_cast<real*>(smem + L::ring_off);                      // [NRING][RC][ROW]
   ChanCell<real>* gring = reinterpret_cast<ChanCell<real>*>(smem + L::geo_off);  // [NRING][TP]
@@ -433,7 +442,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   real* eqr = reinterpret_cast<real*>(smem + L::eq_off);                         // [4][TP][EQW]
   real* resr = reinterpret_cast<real*>(smem + L::res_off);                       // [4][2][Q1]
   real* mvs = reinterpret_cast<real*>(smem + L::mvs_off);                        // [TP+2][4][MAXN]
-  real* red = reinterpret_cast<real*>(smem + L::red_off);                        // [2][TP][NWC][4]
+  real* red = reinterpret_cast<real*>(smem + L::red_off);                        // [NPR][TP][NWC][4]
   real* wred = reinterpret_cast<real*>(smem + L::wred_off);                      // [TP][NWC]
   double* nwv = reinterpret_cast<double*>(smem + L::nwv_off);                    // [TP]
 
@@ -450,6 +459,8 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   // ---- prologue: tables and rows sA .. sA+2+PD
   if (tid == 0) {
     for (int b = 0; b <= NB; ++b) mbar_init(bar + b, 1);
+    for (int k = 0; k < L::NPR; ++k) mbar_init(pready + k, NMW);
+    for (int k = 0; k < L::NEQ; ++k) mbar_init(eready + k, 2);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -506,14 +517,14 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
     kq += __shfl_xor_sync(0xffffffffu, kq, 2);
     kq += __shfl_xor_sync(0xffffffffu, kq, 1);
     // lanes 0, 8, 16, 24: n, rho u0, rho u1, energy
-    if ((lane & 7) == 0) red[(((r & 1) * TP + c) * NWC + wc) * 4 + (lane >> 3)] = kq;
+    if ((lane & 7) == 0) red[(((r % L::NPR) * TP + c) * NWC + wc) * 4 + (lane >> 3)] = kq;
   };
 
   // equilibrium record of cell cc of row r (one extra warp): n, u, T, tau and the
   // factors n g0_i, g1_j normalised so that sum_ij n g0_i g1_j = n (reading 18)
   auto eq_job = [&](int r, int cc) {
     real* mv = mvs + cc * 4 * MAXN;
-    const real* rp = red + ((r & 1) * TP + cc) * NWC * 4;
+    const real* rp = red + ((r % L::NPR) * TP + cc) * NWC * 4;
     // cross-warp sums of the partials plus the sums of R; n compensated (float-float)
     // on the single-precision path
     real q[4], nlo = real(0);
@@ -589,7 +600,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   // from its moment partials
   auto res_job = [&](int r, int end) {
     const int cc = end == 0 ? 0 : TP - 1;
-    const real* rp = red + ((r & 1) * TP + cc) * NWC * 4;
+    const real* rp = red + ((r % L::NPR) * TP + cc) * NWC * 4;
     real sn = real(0), sp = real(0);
 #pragma unroll
     for (int w = 0; w < NWC; ++w) sn += rp[w * 4], sp += rp[w * 4 + 2];
@@ -605,9 +616,9 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
     }
     __syncwarp();
   };
-  auto res_jobs = [&](int r) {  // extra warps: both ends where the strip has one
+  auto res_jobs = [&](int r) {  // equilibrium warps: both ends where the strip has one
     for (int end = 0; end < 2; ++end)
-      if ((end == 0 ? inlet : outlet) && ew == (TP + end) % NWC) res_job(r, end);
+      if ((end == 0 ? inlet : outlet) && qw == end) res_job(r, end);
   };
 
   // inlet / outlet ghosts of row r (main threads of the first / last column): the
@@ -642,11 +653,10 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
     real gm[12];
     load_geo(gring + k * TP + TP - 1, gm);
     const bool up = gm[G_BP] * pxj - gm[G_CP] * pli >= real(0);
-    P h[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) h[q] = p_load(krow(k, TP - 3 + q) + 2 * vv);
-    xif[TP * V + vv] = weno5p<real>(p_sel(up, h[0], h[5]), p_sel(up, h[1], h[4]), p_sel(up, h[2], h[3]),
-                                    p_sel(up, h[3], h[2]), p_sel(up, h[4], h[1]), tb.iw0[ii] * tb.iw1[jj]);
+    const real* st = krow(k, up ? TP - 3 : TP + 2) + 2 * vv;  // upwind-ordered stencil of TP - 1/2
+    const int sd = up ? ROW : -ROW;
+    xif[TP * V + vv] = weno5p<real>(p_load(st), p_load(st + sd), p_load(st + 2 * sd), p_load(st + 3 * sd),
+                                    p_load(st + 4 * sd), tb.iw0[ii] * tb.iw1[jj]);
   };
 
   // window rows from the ring (the centreline mirror below row 0: ghost 1-k of
@@ -667,12 +677,14 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   for (int r = sA; r < min(sA + 3, sB); ++r) {
     if (is_main) moment_partials(p_load(krow(r % NRING, c) + 2 * v), r);
     __syncthreads();
-    if (!is_main && r < sA + 2) {
-      for (int job = ew; job < TP; job += NWC) eq_job(r, job);
+    if (is_eqw && r < sA + 2) {
+      for (int job = qw; job < TP; job += 2) eq_job(r, job);
       res_jobs(r);
     }
     __syncthreads();
   }
+  // row sA+2's partials are the first the equilibrium warps take from the ring
+  if (is_main && sA + 2 < min(nl, sB) && lane == 0) mbar_arrive(pready + (sA + 2) % L::NPR);
   reservoir_ghosts(sA);
   // lambda interface sA - 1/2
   P fm = p_set(real(0));
@@ -680,6 +692,35 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   P gh0 = p_set(real(0)), gh1 = p_set(real(0));  // wall ghosts of rows nl, nl+1 (and nl+2)
   unsigned phase_bits = 0;                        // thread 0: parity of the next wait, per step mbarrier
   __syncthreads();
+
+  // ---- the equilibrium warps: rows sA+2 .. in order, each as soon as the column warps have
+  // reduced its moments, two or three rows ahead of the step that uses it; they take part in
+  // no step barrier (the step phases synchronise on named barrier 1 of the other NSYNC threads)
+  if (is_eqw) {
+    unsigned pph = 0;
+    const int rend = min(nl, sB);
+    for (int r = sA + 2; r < rend; ++r) {
+      const int k = r % L::NPR;
+      bool ok = true;
+      if (lane == 0) ok = mbar_wait(pready + k, (pph >> k) & 1u, a.max_polls);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      pph ^= 1u << k;
+      if (!ok) {  // the column warps stopped (their own wait ran out): leave
+        if (lane == 0) atomicOr(a.err, ERR_TIMEOUT);
+        return;
+      }
+      __syncwarp();
+      for (int job = qw; job < TP; job += 2) eq_job(r, job);
+      res_jobs(r);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(eready + r % L::NEQ);
+    }
+    return;
+  }
+  unsigned eph = 0;        // thread 0: parity of the next wait, per equilibrium-ready slot
+  int eq_waited = sA + 1;  // rows up to this one have their records (the prologue made sA, sA+1)
+  auto sync_all = [&]() { named_bar(1, NSYNC); };
+  auto sync_and = [&](bool v) { return named_bar_and(1, NSYNC, v); };
 
   // ---- the march
   for (int s = sA; s < sB; ++s) {
@@ -691,7 +732,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
         ok = mbar_wait(bar + b, (phase_bits >> b) & 1u, a.max_polls);
         phase_bits ^= 1u << b;
       }
-      ok = __syncthreads_and(ok);
+      ok = sync_and(ok);
       if (!ok) {  // wait (bounded) for every group still in flight, then leave
         if (tid == 0) {
           atomicOr(a.err, ERR_TIMEOUT);
@@ -701,7 +742,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
               mbar_wait(bar + b, g == s - PD ? ((phase_bits >> b) & 1u) ^ 1u : (phase_bits >> b) & 1u, a.max_polls);
             }
         }
-        __syncthreads();
+        sync_all();
         return;
       }
     }
@@ -726,7 +767,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
         gh0 = G0;
         gh1 = G1;
       }
-      __syncthreads();
+      sync_all();
       if (!is_main && lane == 0)
         for (int cc = ew; cc < TP; cc += NWC) {
           double num = tb.ref_flux_pos;  // outgoing flux of R
@@ -736,7 +777,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
           a.nw[p0 + cc] = nwc;
           if (!isfinite(nwc)) atomicOr(a.err, ERR_NONFINITE);
         }
-      __syncthreads();
+      sync_all();
       if (is_main && !(pl > real(0))) {  // incoming: f_eq(n_w, 0, T0) - R (Eq. weno_populate)
         const real e = real(nwv[c]) * tb.gw0[i] * tb.gw1[j];
         gh0 = gh1 = p_make(e - Rij, e * T0 - Rij);
@@ -745,21 +786,28 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
 
     // ==== phase A
     P FL = p_set(real(0));   // xi interface c - 1/2 of row s
+    P fp = p_set(real(0));   // lambda interface s + 1/2
     P frc = p_set(real(0));  // force (double precision path)
     if (is_main) {
       const int rn = s + 3;
       const P fnew = rn < nl ? p_load(krow(k3, c) + 2 * v) : (rn == nl ? gh0 : gh1);
-      if (rn < min(nl, sB)) moment_partials(fnew, rn);
+      if (rn < min(nl, sB)) {
+        moment_partials(fnew, rn);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(pready + rn % L::NPR);  // the equilibrium warps take row rn from here
+      }
       W0 = W1, W1 = W2, W2 = W3, W3 = W4, W4 = W5, W5 = fnew;  // W = F(s-2 .. s+3)
       real gm[12];
       load_geo(gring + k0 * TP + c, gm);
       // xi interface c - 1/2: upwind by V^xi = b p^xi - c p^lambda (Eq. canalie_V)
       const bool up = gm[G_BM] * px - gm[G_CM] * pl >= real(0);
-      P h[6];
-#pragma unroll
-      for (int q = 0; q < 6; ++q) h[q] = p_load(krow(k0, c - 3 + q) + 2 * v);
-      FL = weno5p<real>(p_sel(up, h[0], h[5]), p_sel(up, h[1], h[4]), p_sel(up, h[2], h[3]), p_sel(up, h[3], h[2]),
-                        p_sel(up, h[4], h[1]), sc);
+      // the upwind-ordered stencil of interface c - 1/2: cells c-3 .. c+1 or c+2 .. c-2
+      const real* st = krow(k0, up ? c - 3 : c + 2) + 2 * v;
+      const int sd = up ? ROW : -ROW;
+      FL = weno5p<real>(p_load(st), p_load(st + sd), p_load(st + 2 * sd), p_load(st + 3 * sd), p_load(st + 4 * sd), sc);
+      // lambda interface s + 1/2 from the window, upwind by p^lambda (a > 0): independent of
+      // the xi one, so the two interleave
+      fp = lpos ? weno5p<real>(W0, W1, W2, W3, W4, sc) : weno5p<real>(W5, W4, W3, W2, W1, sc);
       xif[c * V + v] = FL;
       if constexpr (F32 && TC) {
         // force subtasks of the row's cells on the tensor cores (mma.sync needs the
@@ -792,11 +840,14 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       // force tasks of the row's cells on the CUDA cores (lambda: one per (cell, column
       // j); xi: one per (cell, row i)) and the strip's right-edge xi interface, over the
       // extra warps in units of one warp
-      constexpr int NWL = (TP * Q1 + 31) / 32, NWX = (TP * Q0 + 31) / 32;
+      // tasks: (cell, column j) for lambda, (cell, row i) for xi, in units of 32 (one warp);
+      // then the edge chunks
+      constexpr int NTL = TP * Q1, NTX = TP * Q0;
+      constexpr int NWL = (NTL + 31) / 32, NWX = (NTX + 31) / 32;
       for (int u = ew; u < NWL + NWX + NWC; u += NWC) {
         if (u < NWL) {
           const int t = 32 * u + lane;
-          if (t < TP * Q1) {
+          if (t < NTL) {
             const int cc = t / Q1, jj = t - cc * Q1;
             const ChanCell<real>& gk = gring[k0 * TP + cc];
             const float pxj = tb.p1[jj];
@@ -804,7 +855,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
           }
         } else if (u < NWL + NWX) {
           const int t = 32 * (u - NWL) + lane;
-          if (t < TP * Q0) {
+          if (t < NTX) {
             const int cc = t / Q0, ii = t - cc * Q0;
             const ChanCell<real>& gk = gring[k0 * TP + cc];
             const float pli = tb.p0[ii];
@@ -818,12 +869,29 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       // the strip's right-edge xi interface of row s, 32 velocities per extra warp
       for (int ch = ew; ch < NWC; ch += NWC) edge_weno(k0, ch);
     }
-    __syncthreads();
+    {  // the records of rows s (the combine) and s+1 (the reservoir ghosts) must be written
+      bool ok = true;
+      const int want = min(s + 1, min(nl, sB) - 1);
+      if (tid == 0)
+        while (eq_waited < want) {
+          const int r = ++eq_waited, k = r % L::NEQ;
+          ok = ok && mbar_wait(eready + k, (eph >> k) & 1u, a.max_polls);
+          eph ^= 1u << k;
+        }
+      ok = sync_and(ok);
+      if (!ok) {  // an equilibrium warp stopped: wait (bounded) for the bulk copies in flight, then leave
+        if (tid == 0) {
+          atomicOr(a.err, ERR_TIMEOUT);
+          for (int g = s - PD + 1; g <= s; ++g)
+            if (g >= sA && g + 3 + PD <= rlast) mbar_wait(bar + g % NB, (phase_bits >> (g % NB)) & 1u, a.max_polls);
+        }
+        sync_all();
+        return;
+      }
+    }
 
     // ==== phase C
     if (is_main) {
-      // lambda interface s + 1/2, upwind by p^lambda (a > 0)
-      const P fp = lpos ? weno5p<real>(W0, W1, W2, W3, W4, sc) : weno5p<real>(W5, W4, W3, W2, W1, sc);
       real gm[12];
       load_geo(gring + k0 * TP + c, gm);
       const P FR = xif[(c + 1) * V + v];
@@ -844,13 +912,9 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       p_store(a.Fout + dcell(s, p0 + c) * ROW + 2 * v, o);
       if (need_fl && s + 1 < sB) flr = p_load(a.Fl + dcell(s + 1, p0 + c) * ROW + 2 * v);
       fm = fp;
-    } else if (s + 2 < min(nl, sB)) {
-      // the equilibria and reservoir factors of row s+2 (moment partials of the previous step)
-      for (int job = ew; job < TP; job += NWC) eq_job(s + 2, job);
-      res_jobs(s + 2);
     }
     if (s + 1 < sB) reservoir_ghosts(s + 1);
-    __syncthreads();
+    sync_all();
   }
 }
 

@@ -189,8 +189,8 @@ static cudaError_t go_channel(const ChanArgs<real>& a, const void* kpb, int grid
 
 #ifdef VLB_DEFINE_SHARED
 // {rows per segment (0: host's choice, 1 << 20: one segment), columns per strip, threads, tensor-core force}
-static const ChanVariant kChan16x12[] = {{0, 4, 960, 0}, {0, 4, 960, 1}, {1 << 20, 4, 960, 0}, {64, 4, 960, 0}};
-static const ChanVariant kChan8x4[] = {{0, 4, 160, 0}, {0, 8, 288, 0}, {0, 4, 160, 1}, {1 << 20, 4, 160, 0}};
+static const ChanVariant kChan16x12[] = {{0, 4, 1024, 0}, {0, 4, 1024, 1}, {1 << 20, 4, 1024, 0}, {64, 4, 1024, 0}};
+static const ChanVariant kChan8x4[] = {{0, 4, 224, 0}, {0, 8, 352, 0}, {0, 4, 224, 1}, {1 << 20, 4, 224, 0}};
 
 int channel_variants(int nq0, int nq1, ChanVariant* out) {
   const ChanVariant* v = nullptr;

@@ -13,6 +13,15 @@ root:  python tests/golden/make_oracle_references.py
   wall speed 0.2, Kn = 0.1 (Aoki tau), from f_eq(1, 0, 1) for 13340 steps of
   dt = 1.5e-3 (20 time units of 667 steps; the residual of Eq. msites_steady between the last
   two time units is recorded): the steady moments.
+* couette_residual_floor.json -- the norms of Eq. (msites_steady) between
+  checks 300 steps apart over 120 checks for two instances of HH(4;8)xH(4;20)
+  started from f_eq(1, 0, 1): 24 cells, R in [1, 1.5], Kn = 5, inner wall speed
+  0.1; and 32 cells, R in [1, 2], Kn = 2, inner wall speed 0.3 (Aoki tau, dt =
+  min(CFL 0.4 on the radial spacing, half the relaxation time at n = 1.2)).
+  With the epsilon-free weights the norms stop falling near 1e-5 and wander
+  there (the weights switch between the stencils from one check to the next).
+
+Usage: python tests/golden/make_oracle_references.py [name ...] (all by default).
 """
 import json
 import os
@@ -56,8 +65,37 @@ def steady():
             "dt": dt, "last_residual": res}
 
 
+FLOOR_INSTANCES = [dict(n_cells=24, kn=5.0, u_wall=0.1, r_in=1.0, r_out=1.5),
+                   dict(n_cells=32, kn=2.0, u_wall=0.3, r_in=1.0, r_out=2.0)]
+PMAX = 5.2128  # largest |p^R| of the half-range rule of order 8
+
+
+def residual_floor(checks=120, every=300):
+    out = []
+    for inst in FLOOR_INSTANCES:
+        dr = (inst["r_out"] - inst["r_in"]) / inst["n_cells"]
+        dt = min(0.4 * dr / PMAX, 0.5 * np.sqrt(np.pi / 8) * inst["kn"] / 1.2)
+        o = CouetteOracle("HH(4;8)xH(4;20)", CouetteGrid(inst["n_cells"], inst["r_in"], inst["r_out"]),
+                          Wall(inst["u_wall"]), Wall(0.0), inst["kn"], TAU_AOKI)
+        F = o.initial_equilibrium()
+        prev = o.m.moments(F)
+        hist = []
+        for _ in range(checks):
+            for _ in range(every):
+                F = o.step(F, dt)
+            mom = o.m.moments(F)
+            hist.append(list(o.residual(mom, prev, inst["u_wall"])))
+            prev = mom
+        out.append({"instance": inst, "dt": dt, "every": every, "norms": hist})
+    return out
+
+
+ALL = {"couette_config1_10000_steps.json": config1, "couette_steady_16x320.json": steady,
+       "couette_residual_floor.json": residual_floor}
+
 if __name__ == "__main__":
-    for name, fn in (("couette_config1_10000_steps.json", config1), ("couette_steady_16x320.json", steady)):
+    names = sys.argv[1:] or list(ALL)
+    for name, fn in ((n, ALL[n]) for n in names):
         t0 = time.time()
         out = fn()
         with open(os.path.join(HERE, name), "w") as f:
