@@ -40,6 +40,7 @@ KNS = [1e-3, 1e-2, 0.1, 1.0, 10.0]
 U_WALL = 0.1
 DT = 5e-5  # CFL 0.4 with max |p^R| = 5.21 and dR = 1/1024, and below tau_min
 METRIC = "cell-velocity updates/s"
+L2_BYTES = 129 * 1024 * 1024  # GB300 L2
 # floating-point operations of one stage per cell-velocity (both fields) of the Couette
 # scale-up model, counted from the equations: WENO-5 2 x 60, force 2 x 2 (2 Q_R + Q_phi) = 144,
 # moments 10, equilibrium + BGK + RK3 combine 16 (the per-cell equilibrium factors are O(cells))
@@ -59,7 +60,7 @@ WORKLOAD = (f"gradually expanding channel: {CH_NX} (xi) x {CH_NL} (lambda) cells
 # DRAM bytes (read + write) per launch of the channel stage kernel from one ncu capture, keyed by
 # the SHA-256 of the kernel's source at the time of the capture (a changed kernel reports null):
 # see profiles/ for the command and the scaling to the full grid
-CH_TRAFFIC = {}
+CH_TRAFFIC = {"507cbccd163ebdb1": 4.449e9}
 
 
 def dist_env():
@@ -141,7 +142,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def channel_inputs(vlb):
+def channel_inputs(vlb, nl=CH_NL, nx=CH_NX):
     """Perturbed equilibrium f_eq(1, 0, 1) * (1 + 0.01 U(-1, 1)) of the headline channel in the
     library's caller layout (cell p * n_lambda + s, then f', f'', then the 16 x 12 nodes),
     float32; the weights come from the library's own quadrature."""
@@ -149,7 +150,7 @@ def channel_inputs(vlb):
     m = vlb.vlb_parse_model(CH_MODEL)
     _, w0 = vlb.vlb_quadrature(m, 0)
     _, w1 = vlb.vlb_quadrature(m, 1)
-    F = perturbation32((CH_NL * CH_NX, 2, 16, 12), seed=CH_SEED)
+    F = perturbation32((nl * nx, 2, 16, 12), seed=CH_SEED)
     F *= np.outer(w0, w1).astype(np.float32)
     return F
 
@@ -329,12 +330,17 @@ def bench_channel(args, torch, stream, vlb, world):
     step, each stage launch bracketed by CUDA events on the launching stream (the
     launches are milliseconds long, so the host's enqueueing between them is hidden).
     Then the same metric end to end through the C ABI from pinned host buffers."""
-    ctx = vlb.Channel(CH_MODEL, vlb.VLB_FP32_BULK, CH_NL, CH_NX, CH_KN, n_in=CH_NIN, n_out=CH_NOUT,
+    nl, nx = (int(x) for x in args.channel_cells.split("x"))
+    ctx = vlb.Channel(CH_MODEL, vlb.VLB_FP32_BULK, nl, nx, CH_KN, n_in=CH_NIN, n_out=CH_NOUT,
                       stream=stream.cuda_stream)
-    host_in = torch.from_numpy(channel_inputs(vlb)).pin_memory()
+    host_in = torch.from_numpy(channel_inputs(vlb, nl, nx)).pin_memory()
     host_out = torch.empty_like(host_in).pin_memory()
     ctx.set_f(host_in)
-    tuned, _ = ctx.autotune(CH_DT, reps=3)
+    if args.channel_shape is None:
+        tuned, _ = ctx.autotune(CH_DT, reps=3)
+    else:
+        tuned = args.channel_shape
+        ctx.set_variant(tuned)
     shape = ctx.channel_variants()[tuned]
     tensor_cores = ctx.channel_variant_tensor_cores(tuned)
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -374,15 +380,16 @@ def bench_channel(args, torch, stream, vlb, world):
         e2e_s = time.perf_counter() - t0
     nmom = ctx.read_moments()[0]
     ctx.close()
-    units = CH_NL * CH_NX * CH_VEL
+    units = nl * nx * CH_VEL
     value, total_ms = whole_job_rate(float(step_ms.sum()), units, args.steps, world)
-    e2e_value, _ = whole_job_rate(e2e_s * 1e3, units, e2e_steps, world)
+    e2e_value, _ = whole_job_rate(e2e_s * 1e3, units, max(e2e_steps, 1), world)
     bytes_per_launch = stage_bytes(units, 4)
     launch_ms = float(stage_ms.mean())
     hbm, kind = peaks()
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     sha = kernel_source_sha()
-    traffic = CH_TRAFFIC.get(sha)
+    # the recorded traffic is for the full grid and the autotuned shape
+    traffic = CH_TRAFFIC.get(sha) if (nl, nx) == (CH_NL, CH_NX) and args.channel_shape is None else None
     return {
         "value": value, "ms_per_step": total_ms / args.steps, "units": units, "clocks": clocks,
         "launches": 3 * args.steps,
@@ -400,6 +407,14 @@ def bench_channel(args, torch, stream, vlb, world):
                 "h2d_bytes_per_step": int(host_in.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4)},
         "density_finite": bool(np.all(np.isfinite(nmom))),
     }
+
+
+def l2_note(copy_bytes):
+    """How the headline treats L2: a distribution copy larger than L2 needs no flush."""
+    gb = copy_bytes / 1e9
+    if copy_bytes > L2_BYTES:
+        return f"inputs larger than L2 ({gb:.2f} GB per distribution copy); no flush"
+    return f"inputs smaller than L2 ({gb:.3f} GB per distribution copy), not flushed: a profiling size only"
 
 
 def bench_couette(args, torch, stream, vlb, flush):
@@ -550,11 +565,15 @@ def run_gpu(args):
         "metric": METRIC, "value": head["value"], "unit": "cell-velocity updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "model": CH_MODEL, "cells": [CH_NX, CH_NL], "velocities": CH_VEL,
+        "config": {"workload": WORKLOAD if args.channel_cells == f"{CH_NL}x{CH_NX}" else
+                   WORKLOAD.replace(f"{CH_NX} (xi) x {CH_NL} (lambda)", "{1} (xi) x {0} (lambda)".format(
+                       *args.channel_cells.split("x"))),
+                   "model": CH_MODEL, "cells": [int(x) for x in args.channel_cells.split("x")[::-1]],
+                   "velocities": CH_VEL,
                    "grid": "xi in [-10, 40] equidistant, lambda tanh-stretched (A = 0.95), Re_c = 100, H/2 = 1",
                    "kn": CH_KN, "reservoirs": {"n_in": CH_NIN, "n_out": CH_NOUT, "T0": 1.0}, "dt": CH_DT,
                    "precision": "fp32-bulk (compensated density sums, fp64 wall flux)",
-                   "l2": "inputs larger than L2 (1.6 GB per distribution copy); no flush",
+                   "l2": l2_note(head["units"] * 4),
                    "launch_shape": head["launch_shape"], "replicas_per_gpu": 1},
         "roofline": head["roofline"],
         "cpu_baseline": cpu,
@@ -580,6 +599,10 @@ def main():
     ap.add_argument("--workload", default="all", choices=["all", "channel", "couette", "batched"],
                     help="all: the channel line with the Couette scale-up and batched measurements beside it")
     ap.add_argument("--e2e-steps", type=int, default=3, help="end-to-end steps (host buffers) of the headline")
+    ap.add_argument("--channel-cells", default=f"{CH_NL}x{CH_NX}",
+                    help="lambda x xi cells of the channel (another size than the headline's is for profiling)")
+    ap.add_argument("--channel-shape", type=int, default=None,
+                    help="channel launch shape index instead of the autotuner's choice (for profiling)")
     ap.add_argument("--couette-steps", type=int, default=100, help="timed steps of the Couette scale-up batch")
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batched Couette measurement")
     ap.add_argument("--no-time-to-steady", action="store_true", help="leave out the time-to-steady measurement")
