@@ -7,14 +7,17 @@
 //   - pushes row s+3 into a per-thread six-row register window (f', f'') of
 //     its (column, velocity), so the lambda-WENO-5 interface value s+1/2
 //     comes from registers and every lambda interface is reconstructed once;
-//   - reduces the moments of row s+3 and builds its truncated equilibrium
-//     (Sec. IV.D) three rows ahead of use;
+//   - reduces the moments of row s+3; two dedicated equilibrium warps turn
+//     them into the row's truncated equilibrium (Sec. IV.D) asynchronously,
+//     handing rows over through mbarrier rings, two or three rows ahead of use;
 //   - reconstructs the xi interfaces of row s from a shared-memory ring that
-//     bulk copies (cp.async.bulk, mbarrier completion) fill one row ahead;
+//     bulk copies (cp.async.bulk, mbarrier completion) fill PD rows ahead;
 //   - contracts the momentum-space force matrices of Eq. (canalie_boltz)
-//     over the row's cells on the tensor cores (single precision:
-//     mma.sync m16n8k8 TF32 with a hi/lo split of both operands, three
-//     products per tile) or in FP64 on the CUDA cores (double precision);
+//     over the row's cells: in single precision either on the CUDA cores
+//     (packed FP32x2 fmas on the reflection-split matrices, run by two extra
+//     warps) or on the tensor cores (mma.sync m16n8k8 TF32 with a hi/lo split
+//     of both operands, three products per tile), one template instance each,
+//     chosen per context by timing; in double precision on the CUDA cores;
 //   - combines advection, force, BGK relaxation and the RK3 weights and
 //     stores the cell's updated populations straight to global memory.
 //
