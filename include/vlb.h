@@ -71,11 +71,21 @@ typedef struct {
 
 /* Circular Couette grid (Sec. VI.A.1): n_cells cells between r_in < r_out,
  * equidistant when stretch_A == 0, else tanh-stretched per Eq. (eta_def) with
- * amplitude 0 < stretch_A < 1 and centre 0 <= stretch_delta <= 1. */
+ * amplitude 0 < stretch_A < 1 and centre 0 <= stretch_delta <= 1.
+ *
+ * Slab: an instance may hold only the cells [cell_begin, cell_end) of that
+ * grid (both 0: all n_cells cells; otherwise 0 <= cell_begin, cell_end <=
+ * n_cells, at least 3 cells), with the geometry of the full grid.  An end of
+ * the slab that is not r_in or r_out is a halo end: no wall there, its three
+ * ghost cells are the neighbouring slab's cells, written with vlb_write_halo
+ * before every stage (the WENO-5 stencils of Sec. III.C reach three cells
+ * across an interface).  This is the domain decomposition of the radial
+ * direction: each slab steps as the whole grid would, cell for cell. */
 typedef struct {
   int n_cells;
   double r_in, r_out;
   double stretch_A, stretch_delta;
+  int cell_begin, cell_end;
 } vlb_couette_grid;
 
 /* Gradually expanding channel grid (Sec. VII.A-B, H/2 = 1): n_lambda cells in
@@ -227,13 +237,44 @@ vlb_status vlb_read_moments(vlb_ctx* ctx, double* n, double* u0, double* u1, dou
                             double* Tab, double* q, int on_device);
 
 /* Wall densities n_w (Eq. nw) of the last stage: 2 per instance (inner, outer)
- * for Couette contexts, one per xi column for the channel. */
+ * for Couette contexts (0 at a halo end of a slab), one per xi column for the
+ * channel. */
 vlb_status vlb_wall_density(vlb_ctx* ctx, double* nw);
 
 /* Steady-state norms of Eq. (msites_steady) between the current moments and
  * those of the previous call (the first call only stores them and returns
  * zeros): per instance L2_u, L2_n, L2_T (host arrays of n_inst, NULL allowed). */
 vlb_status vlb_residual(vlb_ctx* ctx, double* l2_u, double* l2_n, double* l2_T);
+
+/* The squared norms of vlb_residual before the square root, per instance:
+ * sum_s w_s (du_s / u_w)^2, sum_s w_s (n_s / n_prev,s - 1)^2 and the same for T,
+ * over the instance's own cells.  Slabs of one grid add theirs (one
+ * all-reduce of three numbers per instance) and take the square root.  Same
+ * state rules as vlb_residual (the first call stores the moments). */
+vlb_status vlb_residual_sums(vlb_ctx* ctx, double* s_u, double* s_n, double* s_T);
+
+/* Slab halos (Couette contexts whose instances have halo ends, see
+ * vlb_couette_grid).  A halo block is three cell rows in the library's
+ * device form (the deviation from the rest state, fields interleaved per
+ * velocity, rows padded): vlb_halo_bytes bytes, meaningful only to a context
+ * of the same model and precision.
+ *
+ * vlb_read_edge copies the three cells at end `end` (0: the r_in side, cells
+ * 0, 1, 2 of the instance; 1: the r_out side, its last three cells, in
+ * increasing radius) of the distribution the next stage reads (the one
+ * vlb_stage(ctx, dt, k) with k = the next stage number takes as F_prev) into
+ * rows.  vlb_write_halo copies rows into the ghost cells of end `end` (0: the
+ * three cells below the slab, in increasing radius; 1: the three above it).
+ * Between the two, the caller moves the block to the neighbouring slab
+ * (a device copy, or host or NCCL messages between processes).  A context
+ * with a halo end steps with vlb_stage only: vlb_step, vlb_step_graph,
+ * vlb_run_to_steady and vlb_step_static_scratch return VLB_ERR_STATE.
+ * rows is host or device memory (on_device); the copy is complete when the
+ * call returns.  Errors: VLB_ERR_INVALID (bad instance or end, null rows),
+ * VLB_ERR_STATE (vlb_write_halo on an end that is a wall). */
+long long vlb_halo_bytes(const vlb_ctx* ctx);
+vlb_status vlb_read_edge(vlb_ctx* ctx, int inst, int end, void* rows, int on_device);
+vlb_status vlb_write_halo(vlb_ctx* ctx, int inst, int end, const void* rows, int on_device);
 
 /* Write / restore the distribution and step counter to / from a file
  * (little-endian; a header records model, precision and sizes, checked on load).

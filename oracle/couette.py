@@ -28,6 +28,11 @@ state of Sec. VI.C.2 stays exact (on the equidistant grid it is R_s itself).
 
 Array layout: F has shape (2, N_R, nq0, nq1): field (f', f''), cell, radial
 momentum index i, azimuthal momentum index j.
+
+Radial slabs (domain decomposition): a grid made by CouetteGrid.slab holds a
+contiguous range of the cells; at an end that is not a wall, step 3 takes the
+three ghost cells from the neighbouring slab (set_halo) and the rest of the
+stage is unchanged, so every cell gets what the whole grid gives it.
 """
 from __future__ import annotations
 
@@ -76,6 +81,29 @@ class CouetteGrid:
             self.wres = A0 / A * (r_out - r_in) * self.Rc * deta / np.cosh(eta_c) ** 2
         self.dchi = 0.5 * (self.Rf[1:] ** 2 - self.Rf[:-1] ** 2)
         self.Rbar = 0.5 * (self.Rf[1:] + self.Rf[:-1])
+        self.n_total, self.cell_begin = n, 0  # a whole grid: both ends are walls
+
+    def slab(self, begin: int, end: int) -> "CouetteGrid":
+        """Cells [begin, end) of this grid with their own geometry: a radial slab of a
+        domain decomposition.  An end inside the grid has no wall; the oracle takes its
+        three ghost cells from the neighbouring slab (CouetteOracle.set_halo)."""
+        if not (0 <= begin and end <= self.n and end - begin >= 3):
+            raise ValueError("a slab needs at least three cells of the grid")
+        g = object.__new__(CouetteGrid)
+        g.n, g.r_in, g.r_out, g.A, g.delta = end - begin, self.r_in, self.r_out, self.A, self.delta
+        g.Rf = self.Rf[begin:end + 1].copy()
+        for name in ("Rc", "wres", "dchi", "Rbar"):
+            setattr(g, name, getattr(self, name)[begin:end].copy())
+        g.n_total, g.cell_begin = self.n, begin
+        return g
+
+    @property
+    def inner_is_wall(self) -> bool:
+        return self.cell_begin == 0
+
+    @property
+    def outer_is_wall(self) -> bool:
+        return self.cell_begin + self.n == self.n_total
 
 
 def relaxation_time(kn, n, T, mode):
@@ -95,6 +123,14 @@ class CouetteOracle:
         self.inner, self.outer = inner, outer
         self.kn, self.tau_mode = kn, tau_mode
         self.last_nw = (float("nan"), float("nan"))
+        self.halo = [None, None]  # ghost cells of slab ends (set_halo)
+
+    def set_halo(self, lo=None, hi=None):
+        """Ghost cells of the ends of a slab grid that are not walls, shape (2, 3, nq0, nq1)
+        each, in increasing radius: the three cells below the slab (lo) and above it (hi),
+        taken from the neighbouring slabs' current stage input."""
+        self.halo = [None if lo is None else np.asarray(lo, dtype=np.float64),
+                     None if hi is None else np.asarray(hi, dtype=np.float64)]
 
     # -- equilibrium of a wall, shape (2, nq0, nq1)
     def _wall_feq(self, n, wall: Wall):
@@ -111,7 +147,6 @@ class CouetteOracle:
         N = g.n
         p0 = m.p[0]
         p1 = m.p[1]
-        pos, neg = p0 > 0, p0 < 0
 
         # 1-2: moments, equilibrium, relaxation time
         n, u0, u1, T = m.moments(F)
@@ -122,30 +157,15 @@ class CouetteOracle:
         # 3: ghosts; G[:, s + 2] holds cell s (s = -2 .. N + 3)
         G = np.zeros((2, N + 6) + F.shape[2:])
         G[:, 3:N + 3] = F
-        # inner wall: outgoing (p^R < 0) ghosts by quadratic extrapolation
-        F1, F2, F3 = F[:, 0], F[:, 1], F[:, 2]
-        G[:, 2][:, neg] = (3 * F1 - 3 * F2 + F3)[:, neg]
-        G[:, 1][:, neg] = (6 * F1 - 8 * F2 + 3 * F3)[:, neg]
-        flux_in = weno5(G[:, 5], G[:, 4], G[:, 3], G[:, 2], G[:, 1])  # mirror stencil at s = 1/2
-        feq1 = self._wall_feq(1.0, self.inner)
-        num = -(flux_in[0][neg] * p0[neg, None]).sum()
-        den = (feq1[0][pos] * p0[pos, None]).sum()
-        nw_in = num / den
-        ghost = nw_in * feq1
-        for k in (0, 1, 2):
-            G[:, k][:, pos] = ghost[:, pos]
-        # outer wall: outgoing (p^R > 0) ghosts, mirrored
-        FN, FN1, FN2 = F[:, N - 1], F[:, N - 2], F[:, N - 3]
-        G[:, N + 3][:, pos] = (3 * FN - 3 * FN1 + FN2)[:, pos]
-        G[:, N + 4][:, pos] = (6 * FN - 8 * FN1 + 3 * FN2)[:, pos]
-        flux_out = weno5(G[:, N], G[:, N + 1], G[:, N + 2], G[:, N + 3], G[:, N + 4])
-        feq1o = self._wall_feq(1.0, self.outer)
-        num = -(flux_out[0][pos] * p0[pos, None]).sum()
-        den = (feq1o[0][neg] * p0[neg, None]).sum()
-        nw_out = num / den
-        ghost = nw_out * feq1o
-        for k in (N + 3, N + 4, N + 5):
-            G[:, k][:, neg] = ghost[:, neg]
+        nw_in = nw_out = 0.0
+        if g.inner_is_wall:
+            nw_in = self._inner_wall(F, G)
+        else:  # a slab end inside the grid: the neighbour's cells
+            G[:, 0:3] = self.halo[0]
+        if g.outer_is_wall:
+            nw_out = self._outer_wall(F, G)
+        else:
+            G[:, N + 3:N + 6] = self.halo[1]
         self.last_nw = (nw_in, nw_out)
 
         # 4: advection
@@ -159,6 +179,43 @@ class CouetteOracle:
         # 6: BGK
         coll = -(F - Feq) / tau[None, :, None, None]
         return -adv - force + coll
+
+    def _inner_wall(self, F, G):
+        """Ghost cells -3 .. -1 of the inner wall (step 3) written into G; returns n_w."""
+        p0 = self.m.p[0]
+        pos, neg = p0 > 0, p0 < 0
+        # inner wall: outgoing (p^R < 0) ghosts by quadratic extrapolation
+        F1, F2, F3 = F[:, 0], F[:, 1], F[:, 2]
+        G[:, 2][:, neg] = (3 * F1 - 3 * F2 + F3)[:, neg]
+        G[:, 1][:, neg] = (6 * F1 - 8 * F2 + 3 * F3)[:, neg]
+        flux_in = weno5(G[:, 5], G[:, 4], G[:, 3], G[:, 2], G[:, 1])  # mirror stencil at s = 1/2
+        feq1 = self._wall_feq(1.0, self.inner)
+        num = -(flux_in[0][neg] * p0[neg, None]).sum()
+        den = (feq1[0][pos] * p0[pos, None]).sum()
+        nw_in = num / den
+        ghost = nw_in * feq1
+        for k in (0, 1, 2):
+            G[:, k][:, pos] = ghost[:, pos]
+        return nw_in
+
+    def _outer_wall(self, F, G):
+        """Ghost cells N .. N+2 of the outer wall (step 3) written into G; returns n_w."""
+        p0 = self.m.p[0]
+        pos, neg = p0 > 0, p0 < 0
+        N = F.shape[1]
+        # outer wall: outgoing (p^R > 0) ghosts, mirrored
+        FN, FN1, FN2 = F[:, N - 1], F[:, N - 2], F[:, N - 3]
+        G[:, N + 3][:, pos] = (3 * FN - 3 * FN1 + FN2)[:, pos]
+        G[:, N + 4][:, pos] = (6 * FN - 8 * FN1 + 3 * FN2)[:, pos]
+        flux_out = weno5(G[:, N], G[:, N + 1], G[:, N + 2], G[:, N + 3], G[:, N + 4])
+        feq1o = self._wall_feq(1.0, self.outer)
+        num = -(flux_out[0][pos] * p0[pos, None]).sum()
+        den = (feq1o[0][neg] * p0[neg, None]).sum()
+        nw_out = num / den
+        ghost = nw_out * feq1o
+        for k in (N + 3, N + 4, N + 5):
+            G[:, k][:, neg] = ghost[:, neg]
+        return nw_out
 
     def advection(self, G):
         """chi-form flux difference p^R (R_{s+1/2} F_{s+1/2} - R_{s-1/2} F_{s-1/2}) / d chi_s

@@ -235,6 +235,7 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   a.geo = c->d_geo;
   a.nw = c->d_nw;
   a.wall = c->d_wall;
+  a.halo = static_cast<const real*>(c->d_halo);
   a.err = c->d_err;
   a.Vp = c->Vp;
   a.max_polls = 1ull << 26;
@@ -570,6 +571,9 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   for (int i = 0; i < n_inst; ++i) {
     const vlb_couette_grid& g = grids[i];
     if (g.n_cells < 3) return fail(nullptr, VLB_ERR_INVALID, "a Couette instance needs at least 3 cells");
+    if (!(g.cell_begin == 0 && g.cell_end == 0) &&
+        !(g.cell_begin >= 0 && g.cell_end <= g.n_cells && g.cell_end - g.cell_begin >= 3))
+      return fail(nullptr, VLB_ERR_INVALID, "a slab needs 0 <= cell_begin, cell_end <= n_cells and at least 3 cells");
     if (!(g.r_in > 0.0) || !(g.r_out > g.r_in)) return fail(nullptr, VLB_ERR_INVALID, "need 0 < r_in < r_out");
     if (!(g.stretch_A >= 0.0 && g.stretch_A < 1.0) || !(g.stretch_delta >= 0.0 && g.stretch_delta <= 1.0))
       return fail(nullptr, VLB_ERR_INVALID, "stretching needs 0 <= A < 1, 0 <= delta <= 1");
@@ -652,8 +656,13 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   long long cell0 = 0;
   for (int i = 0; i < n_inst; ++i) {
     InstDesc d{};
+    const vlb_couette_grid& g = grids[i];
+    const bool slab = !(g.cell_begin == 0 && g.cell_end == 0);
+    const int cb = slab ? g.cell_begin : 0, ce = slab ? g.cell_end : g.n_cells;
     d.cell0 = cell0;
-    d.n_cells = grids[i].n_cells;
+    d.n_cells = ce - cb;
+    d.halo = (cb > 0 ? 1 : 0) | (ce < g.n_cells ? 2 : 0);
+    c->has_halo |= d.halo != 0;
     d.tau_mode = tau_mode[i];
     d.kn = kn[i];
     d.dt = 0.0;
@@ -670,7 +679,12 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   c->total_cells = cell0;
   build_tiles(c.get());
   c->geo.resize(cell0);
-  for (int i = 0; i < n_inst; ++i) couette_geometry(grids[i], c->geo.data() + c->inst[i].cell0);
+  for (int i = 0; i < n_inst; ++i) {  // a slab takes its cells' geometry from the whole grid
+    std::vector<GeoCell> full(grids[i].n_cells);
+    couette_geometry(grids[i], full.data());
+    const int cb = grids[i].cell_begin == 0 && grids[i].cell_end == 0 ? 0 : grids[i].cell_begin;
+    std::copy(full.begin() + cb, full.begin() + cb + c->inst[i].n_cells, c->geo.begin() + c->inst[i].cell0);
+  }
 
   vlb_ctx* cp = c.get();
   const size_t fbytes = size_t(c->total_cells) * 2 * c->Vp * c->esize;
@@ -690,6 +704,8 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   VLB_CUDA(cp, cudaMalloc(&c->d_mom, sizeof(double) * 9 * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_prev, sizeof(double) * 9 * c->total_cells));
   VLB_CUDA(cp, cudaMalloc(&c->d_res, sizeof(double) * 3 * n_inst));
+  VLB_CUDA(cp, cudaMalloc(&c->d_halo, size_t(n_inst) * 6 * 2 * c->Vp * c->esize));
+  VLB_CUDA(cp, cudaMemsetAsync(c->d_halo, 0, size_t(n_inst) * 6 * 2 * c->Vp * c->esize, c->stream));
   VLB_CUDA(cp, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * n_inst, cudaMemcpyHostToDevice, c->stream));
   {
     vlb_status ws = upload_walls(cp);
@@ -1063,6 +1079,7 @@ vlb_status vlb_stage(vlb_ctx* c, double dt, int k) {
 
 vlb_status vlb_step(vlb_ctx* c, double dt, long long nsteps) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (c->has_halo) return fail(c, VLB_ERR_STATE, "a slab steps one stage at a time (vlb_stage), halos written before each");
   if (nsteps < 0) return fail(c, VLB_ERR_INVALID, "nsteps must be >= 0");
   if (c->stage_done % 3 != 0) return fail(c, VLB_ERR_STATE, "a partial RK3 step is pending");
   vlb_status st = apply_dt(c, dt);
@@ -1129,12 +1146,12 @@ vlb_status vlb_wall_density(vlb_ctx* c, double* nw) {
   return check_err(c);
 }
 
-vlb_status vlb_residual(vlb_ctx* c, double* l2u, double* l2n, double* l2T) {
-  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+// the weighted sums of squares of Eq. (msites_steady) per instance (zeros on the first call)
+static vlb_status residual_sums(vlb_ctx* c, std::vector<double>& res) {
   if (c->kind != 0) return fail(c, VLB_ERR_UNSUPPORTED, "steady-state norms are defined for Couette contexts");
   vlb_status st = compute_moments(c, c->d_mom);
   if (st != VLB_OK) return st;
-  std::vector<double> res(3 * size_t(c->n_inst), 0.0);
+  res.assign(3 * size_t(c->n_inst), 0.0);
   if (c->have_prev) {
     cudaError_t e = launch_residual(c->d_mom, c->d_prev, c->d_inst, c->d_geo, c->n_inst, c->d_res, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "residual kernel launch");
@@ -1145,11 +1162,70 @@ vlb_status vlb_residual(vlb_ctx* c, double* l2u, double* l2n, double* l2T) {
   st = check_err(c);
   if (st != VLB_OK) return st;
   c->have_prev = true;
+  return VLB_OK;
+}
+
+vlb_status vlb_residual(vlb_ctx* c, double* l2u, double* l2n, double* l2T) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  std::vector<double> res;
+  vlb_status st = residual_sums(c, res);
+  if (st != VLB_OK) return st;
   for (int i = 0; i < c->n_inst; ++i) {
-    if (l2u) l2u[i] = res[3 * i];
-    if (l2n) l2n[i] = res[3 * i + 1];
-    if (l2T) l2T[i] = res[3 * i + 2];
+    if (l2u) l2u[i] = std::sqrt(res[3 * i]);
+    if (l2n) l2n[i] = std::sqrt(res[3 * i + 1]);
+    if (l2T) l2T[i] = std::sqrt(res[3 * i + 2]);
   }
+  return VLB_OK;
+}
+
+vlb_status vlb_residual_sums(vlb_ctx* c, double* su, double* sn, double* sT) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  std::vector<double> res;
+  vlb_status st = residual_sums(c, res);
+  if (st != VLB_OK) return st;
+  for (int i = 0; i < c->n_inst; ++i) {
+    if (su) su[i] = res[3 * i];
+    if (sn) sn[i] = res[3 * i + 1];
+    if (sT) sT[i] = res[3 * i + 2];
+  }
+  return VLB_OK;
+}
+
+long long vlb_halo_bytes(const vlb_ctx* c) {
+  if (!c) return VLB_ERR_INVALID;
+  return 3ll * 2 * c->Vp * (long long)c->esize;
+}
+
+// the buffer the next stage reads as F_prev (see run_stage)
+static int next_stage_input(const vlb_ctx* c) {
+  const int k = c->stage_done % 3 + 1;
+  return k == 1 ? c->cur : (k == 2 ? (c->cur + 1) % 3 : (c->cur + 2) % 3);
+}
+
+vlb_status vlb_read_edge(vlb_ctx* c, int inst, int end, void* rows, int on_device) {
+  if (!c || !rows) return fail(c, VLB_ERR_INVALID, "null argument");
+  if (c->kind != 0) return fail(c, VLB_ERR_UNSUPPORTED, "slabs are Couette instances");
+  if (inst < 0 || inst >= c->n_inst || (end != 0 && end != 1)) return fail(c, VLB_ERR_INVALID, "bad instance or end");
+  const InstDesc& d = c->inst[inst];
+  const size_t rowb = size_t(2) * c->Vp * c->esize;
+  const long long first = d.cell0 + (end == 0 ? 0 : d.n_cells - 3);
+  const char* src = static_cast<const char*>(c->F[next_stage_input(c)]) + size_t(first) * rowb;
+  VLB_CUDA(c, cudaMemcpyAsync(rows, src, 3 * rowb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                              c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  return VLB_OK;
+}
+
+vlb_status vlb_write_halo(vlb_ctx* c, int inst, int end, const void* rows, int on_device) {
+  if (!c || !rows) return fail(c, VLB_ERR_INVALID, "null argument");
+  if (c->kind != 0) return fail(c, VLB_ERR_UNSUPPORTED, "slabs are Couette instances");
+  if (inst < 0 || inst >= c->n_inst || (end != 0 && end != 1)) return fail(c, VLB_ERR_INVALID, "bad instance or end");
+  if (!(c->inst[inst].halo & (1 << end))) return fail(c, VLB_ERR_STATE, "that end is a wall, not a slab halo");
+  const size_t rowb = size_t(2) * c->Vp * c->esize;
+  char* dst = static_cast<char*>(c->d_halo) + (size_t(inst) * 2 + end) * 3 * rowb;
+  VLB_CUDA(c, cudaMemcpyAsync(dst, rows, 3 * rowb, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                              c->stream));
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   return VLB_OK;
 }
 
@@ -1310,6 +1386,7 @@ vlb_status vlb_autotune(vlb_ctx* c, double dt, int reps, int* chosen, double* be
 
 vlb_status vlb_step_graph(vlb_ctx* c, double dt, long long nsteps) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (c->has_halo) return fail(c, VLB_ERR_STATE, "a slab steps one stage at a time (vlb_stage), halos written before each");
   if (nsteps < 0) return fail(c, VLB_ERR_INVALID, "nsteps must be >= 0");
   if (c->stage_done % 3 != 0) return fail(c, VLB_ERR_STATE, "a partial RK3 step is pending");
   vlb_status st = apply_dt(c, dt);
@@ -1370,6 +1447,7 @@ vlb_status vlb_run_to_steady(vlb_ctx* c, double dt, long long check_steps, doubl
                              long long* steps_taken, double* residual, long long* converged_step) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
   if (c->kind != 0) return fail(c, VLB_ERR_UNSUPPORTED, "steady-state norms are defined for Couette contexts");
+  if (c->has_halo) return fail(c, VLB_ERR_STATE, "a slab steps one stage at a time (vlb_stage), halos written before each");
   if (check_steps < 1 || !(threshold > 0.0) || max_steps < check_steps)
     return fail(c, VLB_ERR_INVALID, "need check_steps >= 1, threshold > 0, max_steps >= check_steps");
   const int ni = c->n_inst;
@@ -1425,6 +1503,7 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_mom);
   cudaFree(c->d_prev);
   cudaFree(c->d_res);
+  cudaFree(c->d_halo);
   delete c;
 }
 
@@ -1433,7 +1512,7 @@ void vlb_destroy(vlb_ctx* c) {
 // ---------------------------------------------------------------- residual kernel
 namespace vlb {
 
-// One block per instance: L2 norms of Eq. (msites_steady) with the weights R dR
+// One block per instance: squared L2 norms of Eq. (msites_steady) with the weights R dR
 // (equidistant grid) or the rectangle rule in eta (stretched grid).
 __global__ void residual_kernel(const double* mom, const double* prev, const InstDesc* inst, const GeoCell* geo,
                                 double* res) {
@@ -1457,10 +1536,10 @@ __global__ void residual_kernel(const double* mom, const double* prev, const Ins
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) red[0][warp] = su, red[1][warp] = sn, red[2][warp] = sT;
   __syncthreads();
-  if (threadIdx.x < 3) {
+  if (threadIdx.x < 3) {  // the sums of squares; the host takes the square root
     double t = 0;
     for (int w = 0; w < int(blockDim.x >> 5); ++w) t += red[threadIdx.x][w];
-    res[3 * blockIdx.x + threadIdx.x] = sqrt(t);
+    res[3 * blockIdx.x + threadIdx.x] = t;
   }
 }
 

@@ -58,6 +58,8 @@ struct vlb_ctx {
   double* d_mom = nullptr;
   double* d_prev = nullptr;
   double* d_res = nullptr;
+  void* d_halo = nullptr;  // Couette: 2 x 3 ghost rows per instance for slab halo ends
+  bool has_halo = false;   // some instance has a halo end (vlb_stage only)
   bool have_prev = false;
   size_t tile_cap = 0;
   // channel

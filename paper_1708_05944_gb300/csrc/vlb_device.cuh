@@ -19,6 +19,8 @@ struct InstDesc {
   double kn, dt;
   double u_in, T_in, u_out, T_out;  // walls: tangential speed, temperature
   float kn_f, dt_f;                 // single-precision copies
+  int halo;                         // bit e set: end e (0 inner, 1 outer) is a slab halo, not a wall
+  int pad;
 };
 
 // Diffuse-wall equilibrium f_eq(1, (0, u_w), T_w) of one wall (Eq. weno_populate):

@@ -38,6 +38,7 @@ struct StageArgs {
   const GeoCellF* geof;  // single-precision copy
   double* nw;          // 2 per instance: inner, outer wall density
   const WallEq* wall;  // 2 per instance: inner, outer wall equilibrium
+  const real* halo;    // 2 x 3 rows per instance: ghost cells of slab halo ends (InstDesc::halo)
   unsigned* err;
   int Vp;              // velocities per cell row, padded (>= nq0 nq1, multiple of 4); a row holds 2 Vp reals
   int nbuf;            // tile buffers: 1, or 2 when a persistent CTA stages its next tile during this one
@@ -494,6 +495,18 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
     // every tile whose stencils reach a ghost cell fills the ghosts itself
     const bool active = wall == 0 ? (c0 < 3) : (c0 + TCe + 3 > n);
     if (!active) continue;  // uniform across the CTA
+    if (in.halo & (1 << wall)) {
+      // a slab end: the three ghost cells are the neighbouring slab's, in increasing
+      // radius (below the slab at the inner end, above it at the outer end)
+      const real* hb = a.halo + (size_t(td.inst) * 2 + wall) * 3 * row;
+      const int sA = wall == 0 ? 3 - c0 : (n - 1 - c0 + 3);  // slot of the edge cell
+      for (int x = tid; x < 3 * V; x += NT) {
+        const int q = x / V, v = x - q * V;  // ghost q (increasing radius), velocity v
+        const int slot = wall == 0 ? sA - 3 + q : sA + 1 + q;
+        if (slot >= 0 && slot < TC + 6) p_store(tile + slot * row + 2 * v, p_load(hb + q * row + 2 * v));
+      }
+      continue;
+    }
     const double Tw = wall == 0 ? in.T_in : in.T_out;
     const double sgn = wall == 0 ? 1.0 : -1.0;  // incoming half: p^R > 0 at the inner wall
     __syncthreads();

@@ -36,7 +36,8 @@ class vlb_model(C.Structure):
 
 class vlb_couette_grid(C.Structure):
     _fields_ = [("n_cells", C.c_int), ("r_in", C.c_double), ("r_out", C.c_double),
-                ("stretch_A", C.c_double), ("stretch_delta", C.c_double)]
+                ("stretch_A", C.c_double), ("stretch_delta", C.c_double),
+                ("cell_begin", C.c_int), ("cell_end", C.c_int)]
 
 
 class vlb_channel_grid(C.Structure):
@@ -73,6 +74,10 @@ EXPORTS = {
     "vlb_read_moments": (C.c_int, [C.c_void_p] + [C.c_void_p] * 6 + [C.c_int]),
     "vlb_wall_density": (C.c_int, [C.c_void_p, C.c_void_p]),
     "vlb_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vlb_residual_sums": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "vlb_halo_bytes": (C.c_longlong, [C.c_void_p]),
+    "vlb_read_edge": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
+    "vlb_write_halo": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int]),
     "vlb_save": (C.c_int, [C.c_void_p, C.c_char_p]),
     "vlb_load": (C.c_int, [C.c_void_p, C.c_char_p]),
     "vlb_variants": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
@@ -272,7 +277,8 @@ class Couette(_Context):
         self.precision = precision
         n = len(grids)
         G = (vlb_couette_grid * n)(*[vlb_couette_grid(g["n_cells"], g.get("r_in", 1.0), g.get("r_out", 2.0),
-                                                      g.get("stretch_A", 0.0), g.get("stretch_delta", 0.5))
+                                                      g.get("stretch_A", 0.0), g.get("stretch_delta", 0.5),
+                                                      g.get("cell_begin", 0), g.get("cell_end", 0))
                                      for g in grids])
         Wi = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in inner])
         Wo = (vlb_wall * n)(*[vlb_wall(w[0], w[1]) for w in outer])
@@ -310,6 +316,28 @@ class Couette(_Context):
         a, b, c = (np.empty(self.n_inst) for _ in range(3))
         _check(_lib.vlb_residual(self.h, _ptr(a), _ptr(b), _ptr(c)), self.h)
         return a, b, c
+
+    def residual_sums(self):
+        """vlb_residual_sums: the squared norms (u, n, T) per instance, before the root."""
+        a, b, c = (np.empty(self.n_inst) for _ in range(3))
+        _check(_lib.vlb_residual_sums(self.h, _ptr(a), _ptr(b), _ptr(c)), self.h)
+        return a, b, c
+
+    def halo_bytes(self):
+        n = _lib.vlb_halo_bytes(self.h)
+        if n < 0:
+            _check(int(n), self.h)
+        return int(n)
+
+    def read_edge(self, inst, end, out=None):
+        """vlb_read_edge into out (a host uint8 array or a device tensor of halo_bytes bytes)."""
+        if out is None:
+            out = np.empty(self.halo_bytes(), dtype=np.uint8)
+        _check(_lib.vlb_read_edge(self.h, inst, end, _ptr(out), _on_device(out)), self.h)
+        return out
+
+    def write_halo(self, inst, end, rows):
+        _check(_lib.vlb_write_halo(self.h, inst, end, _ptr(rows), _on_device(rows)), self.h)
 
 
 class Channel(_Context):
