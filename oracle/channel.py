@@ -27,13 +27,21 @@ Boundaries:
 * wall lambda = 1: diffuse reflection at rest and T_0, per-column n_w from the
   zero-mass-flux balance, outgoing ghosts by quadratic extrapolation
   (Sec. VII.C.4, Eqs. extrapol, weno_populate);
-* inlet and outlet: the paper prescribes parabolic flow-rate profiles
-  (Sec. VII.C.1-2); the pressure-ratio workload is read here as two particle
-  reservoirs.  Per (row, momentum), the populations entering the domain
-  (V^xi > 0 at the inlet, V^xi < 0 at the outlet) see ghosts
-  f_eq(n_res, (0, u_x), T_0), with u_x the u^xi of the adjacent cell; those
-  leaving see ghosts equal to the adjacent cell (zeroth-order extrapolation,
-  as the paper does for its inlet).
+* inlet and outlet, two kinds:
+  - particle reservoirs (the pressure-ratio workload): per (row, momentum),
+    the populations entering the domain (V^xi > 0 at the inlet, V^xi < 0 at
+    the outlet) see ghosts f_eq(n_res, (0, u_x), T_0), with u_x the u^xi of
+    the adjacent cell; those leaving see ghosts equal to the adjacent cell
+    (zeroth-order extrapolation, as the paper does for its inlet);
+  - the paper's flow-rate profiles (Sec. VII.C.1-2, Eqs. canalie_inlet,
+    canalie_outlet): the leaving populations as above; the entering ones see
+    f_eq(n_s, (0, Q_s), T_0) with Q_s = 3 Q_0 (1 - lambda_s^2) / (H (1 + phi))
+    at the end's xi (H = 2) and n_s fixed per row by the flux balance of
+    Eq. (canalie_inlet_s): the particle flux through the end interface,
+    entering part n_s f_eq(1, (0, Q_s), T_0) and leaving part the adjacent
+    cell, equals Q_s.  The balance is taken with the chi-form velocity
+    V^xi = (1 + phi) p^y of the interface, so the target is (1 + phi) Q_s
+    (the same equation times 1 + phi).
 
 Array layout: F has shape (2, N_lambda, N_xi, nq0, nq1).
 """
@@ -91,10 +99,12 @@ class ChannelGrid:
 
 
 class ChannelOracle:
-    def __init__(self, model, grid: ChannelGrid, kn, n_in=2.0, n_out=1.0, T0=1.0):
+    def __init__(self, model, grid: ChannelGrid, kn, n_in=2.0, n_out=1.0, T0=1.0, q0=None):
         self.m = model if isinstance(model, Model) else Model(model)
         self.g = grid
         self.kn, self.n_in, self.n_out, self.T0 = kn, n_in, n_out, T0
+        self.q0 = q0  # None: reservoirs; else the half-channel flow rate Q_0 of the flow-rate profiles
+        self.last_inflow_density = None
         Q = self.m.spec[0][2]
         nq0 = self.m.nq[0]
         self.ibar = np.where(np.arange(nq0) < Q, np.arange(nq0) + Q, np.arange(nq0) - Q)
@@ -115,6 +125,17 @@ class ChannelOracle:
         n = np.broadcast_to(n_profile[None, :], (g.nl, g.nx))
         z = np.zeros((g.nl, g.nx))
         return self.feq_cells(n, z, z, np.full((g.nl, g.nx), T0))
+
+    def flow_profile(self, end):
+        """(Q_s, (1 + phi) Q_s) per row at the inlet (end 0) or outlet (end 1):
+        Q_s = 3 Q_0 (1 - 4 lambda_s^2 / H^2) / (H (1 + phi(xi_end))), H = 2 (Eqs. canalie_inlet,
+        canalie_outlet), lambda_s the row's cell centre, xi_end the end interface."""
+        g = self.g
+        xe = g.xf[0] if end == 0 else g.xf[-1]
+        ph = float(phi(xe, g.re_c))
+        H = 2.0
+        q = 3.0 * self.q0 * (1.0 - 4.0 * g.lc ** 2 / H ** 2) / (H * (1.0 + ph))
+        return q, (1.0 + ph) * q
 
     def moments(self, F):
         nl, nx = F.shape[1], F.shape[2]
@@ -161,10 +182,25 @@ class ChannelOracle:
         Vx = g.b[:, :, None, None] * PX[None, None] - g.c[:, :, None, None] * PL[None, None]  # (nl, nx+1, nq0, nq1)
         Hx = np.zeros((2, nl, nx + 6) + F.shape[3:])
         Hx[:, :, 3:nx + 3] = F
-        f_in = self.feq_cells(np.full(nl, self.n_in), np.zeros(nl), ux[:, 0], np.full(nl, self.T0))  # (2, nl, nq0, nq1)
-        f_out = self.feq_cells(np.full(nl, self.n_out), np.zeros(nl), ux[:, -1], np.full(nl, self.T0))
         into_in = Vx[:, 0] > 0  # (nl, nq0, nq1)
         into_out = Vx[:, nx] < 0
+        if self.q0 is None:
+            f_in = self.feq_cells(np.full(nl, self.n_in), np.zeros(nl), ux[:, 0], np.full(nl, self.T0))  # (2, nl, nq0, nq1)
+            f_out = self.feq_cells(np.full(nl, self.n_out), np.zeros(nl), ux[:, -1], np.full(nl, self.T0))
+        else:
+            ns = []
+            fe = []
+            for end, into, Fadj, V in ((0, into_in, F[0, :, 0], Vx[:, 0]), (1, into_out, F[0, :, nx - 1], Vx[:, nx])):
+                q, target = self.flow_profile(end)
+                e1 = self.feq_cells(np.ones(nl), np.zeros(nl), q, np.full(nl, self.T0))  # f_eq(1, (0, Q_s), T0)
+                # Eq. (canalie_inlet_s): n_s sum_in V f'_eq(1) + sum_out V f'_adjacent = (1 + phi) Q_s
+                leaving = np.where(into, 0.0, V * Fadj).sum(axis=(1, 2))
+                entering = np.where(into, V * e1[0], 0.0).sum(axis=(1, 2))
+                n_s = (target - leaving) / entering
+                ns.append(n_s)
+                fe.append(n_s[None, :, None, None] * e1)
+            f_in, f_out = fe
+            self.last_inflow_density = tuple(ns)
         for k in (0, 1, 2):
             Hx[:, :, k] = np.where(into_in[None], f_in, F[:, :, 0])
             Hx[:, :, nx + 3 + k] = np.where(into_out[None], f_out, F[:, :, nx - 1])
@@ -187,7 +223,8 @@ class ChannelOracle:
         coll = -(F - Feq) / tau[None, :, :, None, None]
         self.last_boundary_flux = dict(
             inlet=(g.dl[:, None, None] * fluxx[0, :, 0]).sum(), outlet=(g.dl[:, None, None] * fluxx[0, :, nx]).sum(),
-            wall=(g.dchi[:, None, None] * fluxl[0, nl]).sum(), centre=(g.dchi[:, None, None] * fluxl[0, 0]).sum())
+            wall=(g.dchi[:, None, None] * fluxl[0, nl]).sum(), centre=(g.dchi[:, None, None] * fluxl[0, 0]).sum(),
+            inlet_rows=fluxx[0, :, 0].sum(axis=(1, 2)), outlet_rows=fluxx[0, :, nx].sum(axis=(1, 2)))
         return -adv + force + coll
 
     def stage(self, k, dt, F_l, F_prev):

@@ -62,3 +62,48 @@ def test_specular_centreline_keeps_mirror_symmetry_of_rest():
     F = o.initial_state()
     o.L(F)
     assert abs(o.last_boundary_flux["centre"]) < 1e-15
+
+
+def test_flow_rate_ends_impose_the_profile():
+    """Eq. (canalie_inlet_s) is the definition of the flow-rate boundary: after the ghosts
+    are set, the particle flux through each end interface of row s equals (1 + phi) Q_s,
+    Q_s the parabolic profile of Eqs. (canalie_inlet, canalie_outlet), on a perturbed
+    state (the interface values of the entering and leaving halves come from three equal
+    ghost or stencil cells, where WENO-5 returns that value: Table IV)."""
+    g = ChannelGrid(10, 12)
+    o = ChannelOracle(MODEL, g, 0.05, q0=0.1)
+    F = o.initial_state(n_profile=np.ones(12)) * perturbation((2, 10, 12) + tuple(o.m.nq), seed=17)
+    o.L(F)
+    for end, key in ((0, "inlet_rows"), (1, "outlet_rows")):
+        q, target = o.flow_profile(end)
+        assert np.abs(o.last_boundary_flux[key] / target - 1).max() < 1e-12
+        # the profile: 3 Q_0 / (H (1 + phi)) (1 - lambda^2) (H = 2), zero flux at the wall
+        assert np.allclose(target, 1.5 * 0.1 * (1.0 - g.lc ** 2), rtol=1e-14)
+        assert np.all(o.last_inflow_density[end] > 0)
+    # the inflow densities are near 1 for a state near f_eq(1, 0, 1) with small Q_0
+    assert np.abs(o.last_inflow_density[0] - 1).max() < 0.2
+
+
+def test_flow_rate_rest_state_is_exact():
+    """With Q_0 = 0 the rest state f_eq(1, 0, T0) has zero flux through each end on its own
+    (sum of V^xi w_i w_j = 0), so n_s = 1 and L vanishes."""
+    o = ChannelOracle(MODEL, ChannelGrid(8, 8), 0.05, q0=0.0)
+    F = o.initial_state(n_profile=np.ones(8))
+    L = o.L(F)
+    assert np.abs(L).max() / np.abs(F).max() < 1e-13
+    for ns in o.last_inflow_density:
+        assert np.abs(ns - 1).max() < 1e-13
+
+
+def test_flow_rate_ends_conserve_particles():
+    """In = out row by row ((1 + phi) Q_s is the same at both ends), the wall and the
+    centreline carry no flux: the particle number is constant while the flow develops."""
+    o = ChannelOracle(MODEL, ChannelGrid(8, 12), 0.05, q0=0.1)
+    F = o.initial_state(n_profile=np.ones(12))
+    n0 = o.n_tot(F)
+    for _ in range(5):
+        F = o.step(F, 1e-3)
+    assert abs(o.n_tot(F) / n0 - 1) < 1e-13
+    # and the flow is established at the inlet: u^xi of the first column follows the profile's shape
+    n, ul, ux, T = o.moments(F)
+    assert ux[0, 0] > ux[-1, 0] > 0
