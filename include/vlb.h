@@ -143,7 +143,8 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
  * with a zero-mass-flux density n_w per column (Eq. nw), and particle
  * reservoirs at both ends: populations entering the domain see
  * f_eq(n_in or n_out, (0, u^xi of the adjacent cell), T0), those leaving
- * see the adjacent cell (zeroth-order extrapolation).  Cell (s, p) is cell
+ * see the adjacent cell (zeroth-order extrapolation); vlb_set_channel_flow_rate
+ * replaces the reservoirs by the paper's flow-rate ends.  Cell (s, p) is cell
  * index p * n_lambda + s of the distribution layout.  Axis 0 must be half
  * range; kernels exist for 16 x 12 and 8 x 4 nodes (VLB_ERR_UNSUPPORTED
  * otherwise); n_lambda >= 3, n_xi >= 4 and a multiple of 4.  Starts at f_eq(1, 0, T0). */
@@ -176,12 +177,26 @@ vlb_status vlb_set_walls(vlb_ctx* ctx, const vlb_wall* inner, const vlb_wall* ou
 vlb_status vlb_set_knudsen(vlb_ctx* ctx, double kn, int tau_mode);
 
 /* Channel contexts only: densities of the inlet and outlet particle reservoirs
- * and their temperature T0, which is also the wall temperature.  The paper's
- * channel prescribes flow rates instead; the reservoirs read its "pressure
- * ratio" (see vlb_create_channel).  All three must be finite and > 0
+ * and their temperature T0, which is also the wall temperature.  The reservoirs
+ * read the "pressure ratio" of the benchmark workload (see vlb_create_channel);
+ * the paper's own flow-rate ends are vlb_set_channel_flow_rate.  Calling this
+ * switches the ends (back) to reservoirs.  All three must be finite and > 0
  * (VLB_ERR_INVALID); a Couette context gives VLB_ERR_UNSUPPORTED.  Takes effect
  * from the next stage. */
 vlb_status vlb_set_channel_reservoirs(vlb_ctx* ctx, double n_in, double n_out, double T0);
+
+/* Replace the channel's reservoirs by the paper's flow-rate ends (Sec. VII.C.1-2,
+ * Eqs. canalie_inlet, canalie_outlet, canalie_inlet_s), half-channel particle flow
+ * rate q0 >= 0 at both ends: per row s (lambda_s the row centre, H = 2) the
+ * populations entering the domain see f_eq(n_s, (0, Q_s), T0) with
+ * Q_s = 3 q0 (1 - lambda_s^2) / (H (1 + phi(xi_end))) and n_s fixed by the
+ * particle flux through the end interface (entering part plus the leaving
+ * populations of the adjacent cell) being (1 + phi) Q_s, i.e. Q_s in the
+ * Cartesian frame; the leaving populations see the adjacent cell (zeroth
+ * order).  T0 is the one of vlb_set_channel_reservoirs (default 1);
+ * vlb_set_channel_reservoirs switches back.  Errors: VLB_ERR_INVALID (q0 < 0
+ * or not finite), VLB_ERR_UNSUPPORTED (not a channel context). */
+vlb_status vlb_set_channel_flow_rate(vlb_ctx* ctx, double q0);
 
 /* Set every cell of every instance to f_eq(n0, (u0, u1), T0) (Eq. feq_red). */
 vlb_status vlb_init_equilibrium(vlb_ctx* ctx, double n0, double u0, double u1, double T0);

@@ -300,6 +300,8 @@ vlb_status do_chan_stage(vlb_ctx* c, int k, int prev, int out) {
   a.n_out = real(c->cdesc.n_out);
   a.T0 = real(c->cdesc.T0);
   a.max_polls = 1ull << 26;
+  a.flow = c->cdesc.flow;
+  a.qflow = static_cast<const real*>(c->d_qflow);
   const ChanVariant& v = c->cvariants[c->variant];
   channel_segments(c, v, &a.seglen, &a.nseg);
   const int grid = (a.nx / v.tp) * a.nseg;
@@ -844,6 +846,9 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
   }
   c->cmap.nl = nl;
   c->cmap.nx = nx;
+  c->chan_lc = lc;
+  c->chan_phi_end[0] = phi(xf[0]);
+  c->chan_phi_end[1] = phi(xf[nx]);
   ChanDesc& cd = c->cdesc;
   cd.nl = nl, cd.nx = nx, cd.kn = kn, cd.n_in = n_in, cd.n_out = n_out, cd.T0 = T0, cd.dt = 0.0;
   cd.knf = float(kn), cd.n_inf = float(n_in), cd.n_outf = float(n_out), cd.T0f = float(T0), cd.dtf = 0.0f;
@@ -953,9 +958,39 @@ vlb_status vlb_set_channel_reservoirs(vlb_ctx* c, double n_in, double n_out, dou
   c->cdesc.n_in = n_in, c->cdesc.n_inf = float(n_in);
   c->cdesc.n_out = n_out, c->cdesc.n_outf = float(n_out);
   c->cdesc.T0 = T0, c->cdesc.T0f = float(T0);
+  c->cdesc.flow = 0;
   vlb_status st = drop_channel_graphs(c);
   if (st != VLB_OK) return st;
   return upload_channel_tables(c);
+}
+
+vlb_status vlb_set_channel_flow_rate(vlb_ctx* c, double q0) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (c->kind != 1) return fail(c, VLB_ERR_UNSUPPORTED, "flow-rate ends belong to channel contexts");
+  if (!(q0 >= 0.0) || !std::isfinite(q0)) return fail(c, VLB_ERR_INVALID, "the flow rate must be finite and >= 0");
+  const int nl = c->cdesc.nl;
+  // Eqs. (canalie_inlet, canalie_outlet), H = 2: Q_s = 3 Q0 (1 - 4 lambda_s^2 / H^2) / (H (1 + phi))
+  std::vector<double> q(size_t(4) * nl);
+  const double H = 2.0;
+  for (int e = 0; e < 2; ++e) {
+    const double ph = c->chan_phi_end[e];
+    for (int r = 0; r < nl; ++r) {
+      const double lam = c->chan_lc[r];
+      const double Qs = 3.0 * q0 * (1.0 - 4.0 * lam * lam / (H * H)) / (H * (1.0 + ph));
+      q[size_t(2 * e) * nl + r] = Qs;
+      q[size_t(2 * e + 1) * nl + r] = (1.0 + ph) * Qs;
+    }
+  }
+  if (!c->d_qflow) VLB_CUDA(c, cudaMalloc(&c->d_qflow, size_t(4) * nl * c->esize));
+  if (c->prec == VLB_FP64) {
+    VLB_CUDA(c, cudaMemcpy(c->d_qflow, q.data(), q.size() * sizeof(double), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> qf(q.begin(), q.end());
+    VLB_CUDA(c, cudaMemcpy(c->d_qflow, qf.data(), qf.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  c->cdesc.flow = 1;
+  c->cdesc.q0 = q0;
+  return drop_channel_graphs(c);
 }
 
 vlb_status vlb_init_equilibrium(vlb_ctx* c, double n0, double u0, double u1, double T0) {
@@ -1504,6 +1539,7 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_prev);
   cudaFree(c->d_res);
   cudaFree(c->d_halo);
+  cudaFree(c->d_qflow);
   delete c;
 }
 

@@ -87,11 +87,14 @@ struct alignas(16) ChanTables {
   int N0, N1, kind0, kind1;
 };
 
-// Host-side description of a channel context: grid size, Kn, time step, reservoirs.
+// Host-side description of a channel context: grid size, Kn, time step, reservoirs,
+// and the flow-rate ends (flow = 1: the parabolic profiles of Q0 replace the reservoirs).
 struct ChanDesc {
   int nl, nx;
   double kn, dt, n_in, n_out, T0;
   float knf, dtf, n_inf, n_outf, T0f;
+  int flow;
+  double q0;
 };
 
 template <typename real>
@@ -110,6 +113,11 @@ struct ChanArgs {
   real ca, ccdt;
   real ikn, n_in, n_out, T0;  // 1/Kn, reservoir densities, wall and reservoir temperature
   unsigned long long max_polls;
+  // flow-rate ends (Sec. VII.C.1-2), when flow != 0: per end e and row s,
+  // qflow[(2 e) nl + s] = Q_s (the inflow equilibrium's u^xi) and
+  // qflow[(2 e + 1) nl + s] = (1 + phi) Q_s (the particle flux through the end interface)
+  const real* qflow;
+  int flow;
 };
 
 // Shared-memory carve-up of a CTA, identical on host and device.  The ring holds
@@ -143,7 +151,8 @@ struct ChanSmem {
   static constexpr size_t lbx_off = lbl_off + lbuf_rows * rowb;
   static constexpr size_t eq_off = lbx_off + lbuf_rows * rowb;
   static constexpr size_t res_off = al(eq_off + size_t(NEQ) * TP * S::EQW * sizeof(real));
-  static constexpr size_t mvs_off = al(res_off + size_t(NEQ) * 2 * Q1 * sizeof(real));
+  static constexpr size_t resn_off = al(res_off + size_t(NEQ) * 2 * Q1 * sizeof(real));
+  static constexpr size_t mvs_off = al(resn_off + size_t(NEQ) * 2 * sizeof(real));
   static constexpr size_t red_off = al(mvs_off + size_t(TP + 2) * 4 * MAXN * sizeof(real));
   static constexpr size_t wred_off = al(red_off + size_t(NPR) * TP * S::NWC * 4 * sizeof(real));
   static constexpr size_t nwv_off = al(wred_off + size_t(TP) * S::NWC * sizeof(real));
@@ -444,6 +453,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   real* lbx = reinterpret_cast<real*>(smem + L::lbx_off);                        // [TP][ROW]
   real* eqr = reinterpret_cast<real*>(smem + L::eq_off);                         // [4][TP][EQW]
   real* resr = reinterpret_cast<real*>(smem + L::res_off);                       // [4][2][Q1]
+  real* resn = reinterpret_cast<real*>(smem + L::resn_off);                      // [4][2] inflow densities
   real* mvs = reinterpret_cast<real*>(smem + L::mvs_off);                        // [TP+2][4][MAXN]
   real* red = reinterpret_cast<real*>(smem + L::red_off);                        // [NPR][TP][NWC][4]
   real* wred = reinterpret_cast<real*>(smem + L::wred_off);                      // [TP][NWC]
@@ -599,15 +609,21 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
     __syncwarp();
   };
 
-  // reservoir factors g_xi(u^xi, T0) of row r at one end, u^xi of the adjacent cell
-  // from its moment partials
+  // inflow factors g_xi(u^xi, T0) of row r at one end: reservoirs, u^xi of the adjacent
+  // cell from its moment partials; flow-rate ends, u^xi = Q_s and the density n_s of
+  // Eq. (canalie_inlet_s)
   auto res_job = [&](int r, int end) {
     const int cc = end == 0 ? 0 : TP - 1;
-    const real* rp = red + ((r % L::NPR) * TP + cc) * NWC * 4;
-    real sn = real(0), sp = real(0);
+    real ures;
+    if (a.flow) {
+      ures = a.qflow[(2 * end) * nl + r];
+    } else {
+      const real* rp = red + ((r % L::NPR) * TP + cc) * NWC * 4;
+      real sn = real(0), sp = real(0);
 #pragma unroll
-    for (int w = 0; w < NWC; ++w) sn += rp[w * 4], sp += rp[w * 4 + 2];
-    const real ures = (sp + (tb.ref_hi[2] + tb.ref_lo[2])) * rcp_rn(sn + (tb.ref_hi[0] + tb.ref_lo[0]));
+      for (int w = 0; w < NWC; ++w) sn += rp[w * 4], sp += rp[w * 4 + 2];
+      ures = (sp + (tb.ref_hi[2] + tb.ref_lo[2])) * rcp_rn(sn + (tb.ref_hi[0] + tb.ref_lo[0]));
+    }
     real* mv = mvs + (TP + end) * 4 * MAXN;
     if (lane < 2) eq_moments_fast<real>(tb.kind1, tb.N1, lane ? -ures : ures, T0, mv + lane * MAXN);
     __syncwarp();
@@ -618,6 +634,32 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       resr[((r & 3) * 2 + end) * Q1 + lane] = g;
     }
     __syncwarp();
+    if (a.flow) {
+      // n_s sum_{entering} V f'_eq(1, (0, Q_s), T0) + sum_{leaving} V f'_adjacent = (1 + phi) Q_s,
+      // V = b p^xi - c p^lambda of the end interface (the decision of reservoir_ghosts);
+      // the adjacent cell is row r of the ring (its slot is refilled only after this row's
+      // record is waited for), FP64 sums as for n_w
+      const int k = r % NRING;
+      const ChanCell<real>& gk = gring[k * TP + cc];
+      const real bb = end == 0 ? gk.bm : gk.bp, cq = end == 0 ? gk.cm : gk.cp;
+      const real* Fa = krow(k, cc);
+      const real* gr = resr + ((r & 3) * 2 + end) * Q1;
+      double lv = 0.0, en = 0.0;
+      for (int vv = lane; vv < V; vv += 32) {
+        const int ii = vv / Q1, jj = vv - ii * Q1;
+        const real Vx = bb * tb.p1[jj] - cq * tb.p0[ii];
+        const bool into = end == 0 ? (Vx > real(0)) : (Vx < real(0));
+        if (into) en += double(Vx) * double(tb.gw0[ii] * gr[jj]);
+        else lv += double(Vx) * (double(Fa[2 * vv]) + double(tb.w0[ii]) * double(tb.w1[jj]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        lv += __shfl_xor_sync(0xffffffffu, lv, o);
+        en += __shfl_xor_sync(0xffffffffu, en, o);
+      }
+      if (lane == 0) resn[(r & 3) * 2 + end] = real((double(a.qflow[(2 * end + 1) * nl + r]) - lv) / en);
+      __syncwarp();
+    }
   };
   auto res_jobs = [&](int r) {  // equilibrium warps: both ends where the strip has one
     for (int end = 0; end < 2; ++end)
@@ -640,7 +682,8 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       const bool inflow = end == 0 ? (Vx > real(0)) : (Vx < real(0));
       P val;
       if (inflow) {
-        const real e = (end == 0 ? a.n_in : a.n_out) * tb.gw0[i] * resr[((r & 3) * 2 + end) * Q1 + j];
+        const real nres = a.flow ? resn[(r & 3) * 2 + end] : (end == 0 ? a.n_in : a.n_out);
+        const real e = nres * tb.gw0[i] * resr[((r & 3) * 2 + end) * Q1 + j];
         val = p_make(e - Rij, e * T0 - Rij);
       } else {
         val = p_load(krow(k, c) + 2 * v);

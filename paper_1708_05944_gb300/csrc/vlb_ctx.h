@@ -72,6 +72,9 @@ struct vlb_ctx {
   std::vector<unsigned char> chan_kp;  // ChanKP block (split force matrices), a kernel parameter
   void* d_ctab = nullptr;  // ChanTables of the model shape in the context's real type
   size_t ctab_bytes = 0;
+  std::vector<double> chan_lc;    // lambda of the row centres
+  double chan_phi_end[2] = {0, 0};  // phi at the inlet and outlet interfaces
+  void* d_qflow = nullptr;        // flow-rate ends: 4 n_lambda reals (ChanArgs::qflow)
   // CUDA graph of three RK3 steps (nine stage launches), replayed by vlb_step_graph
   // three-step graphs, one per starting buffer F[cur] (captured on first use)
   cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};

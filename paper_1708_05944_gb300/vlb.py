@@ -66,6 +66,7 @@ EXPORTS = {
     "vlb_init_equilibrium": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]),
     "vlb_set_knudsen": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "vlb_set_channel_reservoirs": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
+    "vlb_set_channel_flow_rate": (C.c_int, [C.c_void_p, C.c_double]),
     "vlb_set_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_read_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_stage": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
@@ -359,6 +360,10 @@ class Channel(_Context):
 
     def set_reservoirs(self, n_in, n_out, T0=1.0):
         _check(_lib.vlb_set_channel_reservoirs(self.h, n_in, n_out, T0), self.h)
+
+    def set_flow_rate(self, q0):
+        """vlb_set_channel_flow_rate: the paper's parabolic flow-rate ends with half-channel rate q0."""
+        _check(_lib.vlb_set_channel_flow_rate(self.h, q0), self.h)
 
     def channel_variants(self):
         ts, tp, nt = (np.zeros(8, dtype=np.int32) for _ in range(3))

@@ -186,3 +186,93 @@ def test_table_iv_rows(prec):
         got = to_oracle(c.read_f(), nl, nx)
         assert rel_err(got, ref) < (1e-12 if prec == vlb.VLB_FP64 else 1e-6), v
     c.close()
+
+
+@pytest.mark.parametrize("prec", [vlb.VLB_FP64, vlb.VLB_FP32_BULK])
+def test_flow_rate_ends_match_oracle(prec):
+    """The paper's flow-rate inlet and outlet (vlb_set_channel_flow_rate) against the oracle's,
+    three stages on every launch shape: FP64 within 1e-12, FP32 within 1e-6."""
+    nl, nx = 10, 16
+    o = ChannelOracle(MODEL, ChannelGrid(nl, nx), 0.05, q0=0.12)
+    F0 = o.initial_state(n_profile=np.ones(nx))
+    F0 = F0 * perturbation(F0.shape, seed=23, amplitude=0.02)
+    dt = 2e-3
+    F1 = o.stage(1, dt, F0, F0)
+    F2 = o.stage(2, dt, F0, F1)
+    F3 = o.stage(3, dt, F0, F2)
+    c = vlb.Channel(MODEL, prec, nl, nx, 0.05)
+    c.set_flow_rate(0.12)
+    dtype = np.float64 if prec == vlb.VLB_FP64 else np.float32
+    tol = 1e-12 if prec == vlb.VLB_FP64 else 1e-6
+    for v in range(len(c.channel_variants())):
+        c.set_variant(v)
+        c.set_f(to_lib(F0).astype(dtype))
+        for k, ref in ((1, F1), (2, F2), (3, F3)):
+            c.stage(dt, k)
+            assert rel_err(to_oracle(c.read_f(), nl, nx), ref) < tol, (v, k)
+    c.close()
+
+
+def test_flow_rate_and_reservoirs_switch():
+    nl, nx = 8, 12
+    o_res, F0 = case(MODEL, nl, nx, n_in=1.3, n_out=0.9)
+    o_flow = ChannelOracle(MODEL, ChannelGrid(nl, nx), 0.05, n_in=1.3, n_out=0.9, q0=0.05)
+    c = vlb.Channel(MODEL, vlb.VLB_FP64, nl, nx, 0.05, n_in=1.3, n_out=0.9)
+    dt = 2e-3
+    c.set_flow_rate(0.05)
+    c.set_f(to_lib(F0))
+    c.step_graph(dt, 3)
+    F = F0
+    for _ in range(3):
+        F = o_flow.step(F, dt)
+    assert rel_err(to_oracle(c.read_f(), nl, nx), F) < 1e-12
+    c.set_reservoirs(1.3, 0.9)
+    c.step(dt, 1)
+    assert rel_err(to_oracle(c.read_f(), nl, nx), o_res.step(F, dt)) < 1e-12
+    with pytest.raises(vlb.VlbError):
+        c.set_flow_rate(-0.1)
+    c.close()
+
+
+def test_flow_rate_channel_reaches_the_poiseuille_gradients():
+    """Validation of the flow-rate channel (Sec. VII.D): far upstream and far downstream of
+    the expansion the steady pressure falls linearly with y = xi at the hydrodynamic rate of
+    Eq. (canalie_pois), dP/dy = -3 Q_0 Kn / (n (1 + phi)^3).  At Kn = 0.01 on 16 rows the
+    measured gradients are 0.967 (upstream) and 1.019 (downstream) of it: the kinetic wall
+    slip lowers it by a few per cent, the 16-row resolution of the twice wider downstream
+    channel adds about as much.  A wrong force sign or flow rate is off by far more.
+    Seeded with the local parabolic profile, run until the two fitted gradients settle."""
+    from oracle.channel import phi
+    nl, nx, kn, q0, dt = 16, 128, 0.01, 0.1, 1.5e-3
+    c = vlb.Channel(SMALL, vlb.VLB_FP32_BULK, nl, nx, kn)
+    c.set_flow_rate(q0)
+    g = ChannelGrid(nl, nx)
+    lam = np.tile(g.lc, nx)                   # caller cell order p * n_lambda + s
+    xi = np.repeat(g.xc, nl)
+    u_xi = 3.0 * q0 * (1.0 - lam ** 2) / (2.0 * (1.0 + phi(xi)))
+    ones = np.ones(nl * nx)
+    c.init_from_moments(ones, 0.0 * ones, u_xi, ones)
+    up = (g.xc > -8.0) & (g.xc < -2.0)
+    down = (g.xc > 24.0) & (g.xc < 38.0)
+
+    def gradients():
+        n, ul, ux, T = (x.reshape(nx, nl) for x in c.read_moments())
+        P = (n * T).mean(axis=1)  # across the channel
+        nbar = n.mean(axis=1)
+        out = []
+        for sel in (up, down):
+            slope = np.polyfit(g.xc[sel], P[sel], 1)[0]
+            ph = float(np.mean(phi(g.xc[sel])))
+            out.append((slope, -3.0 * q0 * kn / (float(nbar[sel].mean()) * (1.0 + ph) ** 3)))
+        return out
+
+    prev = None
+    for chunk in range(12):
+        c.step_graph(dt, 15000)
+        got = gradients()
+        if prev is not None and all(abs(a[0] / b[0] - 1) < 3e-3 for a, b in zip(got, prev)):
+            break
+        prev = got
+    (su, hu), (sd, hd) = got
+    assert abs(su / hu - 1) < 0.06 and abs(sd / hd - 1) < 0.06, got
+    c.close()
