@@ -242,3 +242,65 @@ class ChannelOracle:
 
     def n_tot(self, F):
         return float((self.g.vol * F[0].sum(axis=(2, 3))).sum())
+
+
+def lambda_derivative(f, lam):
+    """d f / d lambda on the non-equidistant row centres lam (axis 0 of f) with the paper's
+    three-point formulas of Sec. VII.F: the bulk formula for 1 < s < N_lambda, the one-sided
+    forward formula at the first node and the backward one at the last."""
+    f = np.asarray(f, dtype=np.float64)
+    d = np.empty_like(f)
+    L = lam
+    for s in range(1, len(L) - 1):
+        lm, l0, lp = L[s - 1], L[s], L[s + 1]
+        d[s] = ((l0 - lm) * f[s + 1] / ((lp - l0) * (lp - lm))
+                + (lp - 2 * l0 + lm) * f[s] / ((lp - l0) * (l0 - lm))
+                - (lp - l0) * f[s - 1] / ((lp - lm) * (l0 - lm)))
+    l1, l2, l3 = L[0], L[1], L[2]
+    d[0] = (-(l2 + l3 - 2 * l1) * f[0] / ((l2 - l1) * (l3 - l1))
+            + (l3 - l1) * f[1] / ((l2 - l1) * (l3 - l2))
+            - (l2 - l1) * f[2] / ((l3 - l1) * (l3 - l2)))
+    lN, lN1, lN2 = L[-1], L[-2], L[-3]
+    d[-1] = ((2 * lN - lN1 - lN2) * f[-1] / ((lN - lN1) * (lN - lN2))
+             - (lN - lN2) * f[-2] / ((lN - lN1) * (lN1 - lN2))
+             + (lN - lN1) * f[-3] / ((lN - lN2) * (lN1 - lN2)))
+    return d
+
+
+def xi_derivative(f, dxi):
+    """d f / d xi on the equidistant columns (axis 1 of f): centred differences, the
+    second-order forward formula at the inlet column and the backward one at the outlet."""
+    f = np.asarray(f, dtype=np.float64)
+    d = np.empty_like(f)
+    d[:, 1:-1] = (f[:, 2:] - f[:, :-2]) / (2.0 * dxi)
+    d[:, 0] = (-3.0 * f[:, 0] + 4.0 * f[:, 1] - f[:, 2]) / (2.0 * dxi)
+    d[:, -1] = (3.0 * f[:, -1] - 4.0 * f[:, -2] + f[:, -3]) / (2.0 * dxi)
+    return d
+
+
+def postprocess(oracle: ChannelOracle, F):
+    """Macroscopic fields of Sec. VII.D-F from the populations F (2, N_lambda, N_xi, nq0, nq1):
+    * u^x, u^y, the Cartesian velocity of Eq. (canalie_u) from the triad components;
+    * psi at the row interfaces lambda_{s+1/2} (N_lambda + 1 per column), Eq.
+      (canalie_psi_sol): psi = 0 on the centreline, psi_{s+1/2} = psi_{s-1/2} -
+      rho u^y (x_{s+1/2} - x_{s-1/2}) along each column, x = lambda (1 + phi(xi_p));
+    * omega of Eq. (canalie_vorti) with the derivative formulas above;
+    * P_w, the wall pressure per column: P = n T extrapolated linearly in x from the
+      last two rows to the wall (Sec. VII.D; the ratio of x differences within a column
+      is that of the lambda differences)."""
+    g = oracle.g
+    n, ul, ux_hat, T = oracle.moments(F)
+    ph, dp = phi(g.xc, g.re_c)[None, :], dphi(g.xc, g.re_c)[None, :]
+    lam = g.lc[:, None]
+    root = np.sqrt(1.0 + lam ** 2 * dp ** 2)
+    ux = (ul + lam * dp * ux_hat) / root
+    uy = (ux_hat - lam * dp * ul) / root
+    psi = np.zeros((g.nl + 1, g.nx))
+    for s in range(g.nl):
+        psi[s + 1] = psi[s] - n[s] * uy[s] * (g.lf[s + 1] - g.lf[s]) * (1.0 + ph[0])
+    dxi = g.xc[1] - g.xc[0]
+    omega = -xi_derivative(ux, dxi) + (lambda_derivative(uy, g.lc) + lam * dp * lambda_derivative(ux, g.lc)) / (1.0 + ph)
+    P = n * T
+    lw, l1, l2 = g.lf[-1], g.lc[-1], g.lc[-2]
+    pw = ((lw - l2) * P[-1] - (lw - l1) * P[-2]) / (l1 - l2)
+    return dict(ux=ux, uy=uy, psi=psi, omega=omega, pw=pw)

@@ -107,3 +107,67 @@ def test_flow_rate_ends_conserve_particles():
     # and the flow is established at the inlet: u^xi of the first column follows the profile's shape
     n, ul, ux, T = o.moments(F)
     assert ux[0, 0] > ux[-1, 0] > 0
+
+
+def test_post_derivative_formulas_are_exact_on_quadratics():
+    """The three-point lambda formulas (bulk, first and last node) on the stretched rows and
+    the xi formulas (centred, one-sided second order) differentiate quadratics exactly."""
+    from oracle.channel import lambda_derivative, xi_derivative
+    g = ChannelGrid(11, 9)
+    f = (0.3 - 1.7 * g.lc + 2.2 * g.lc ** 2)[:, None] * np.ones((1, 4))
+    np.testing.assert_allclose(lambda_derivative(f, g.lc)[:, 0], -1.7 + 4.4 * g.lc, rtol=1e-11, atol=1e-11)
+    x = np.linspace(-3.0, 5.0, 9)
+    h = np.ones((3, 1)) * (1.0 + 0.5 * x - 0.25 * x ** 2)[None, :]
+    np.testing.assert_allclose(xi_derivative(h, x[1] - x[0])[0], 0.5 - 0.5 * x, rtol=1e-12, atol=1e-12)
+    # a wrong sign in the last-node formula would not pass
+    assert abs(lambda_derivative(g.lc[:, None] ** 2, g.lc)[-1, 0] - 2 * g.lc[-1]) < 1e-11
+
+
+def test_post_fields_of_a_poiseuille_state():
+    """A state with u^xi-hat = U (1 - lambda^2), u^lambda-hat = 0, n = 1 + 0.1 lambda, T = 1:
+    the rotation to (u^x, u^y) keeps |u|; where phi' vanishes (far downstream) the vorticity
+    is that of the parabola, -2 U lambda / (1 + phi) (the Poiseuille form -3 u_0 x / x_top^2);
+    P = n T is linear in lambda, so its extrapolation to the wall is exact; psi telescopes."""
+    from oracle.channel import postprocess
+    g = ChannelGrid(12, 16, xi_in=20.0, xi_out=40.0)
+    o = ChannelOracle(MODEL, g, 0.05)
+    U = 0.15
+    lam = g.lc[:, None] * np.ones((1, g.nx))
+    n = 1.0 + 0.1 * lam
+    F = o.feq_cells(n, 0.0 * lam, U * (1.0 - lam ** 2), np.ones_like(lam))
+    p = postprocess(o, F)
+    nn, ul, uxh, T = o.moments(F)
+    np.testing.assert_allclose(p["ux"] ** 2 + p["uy"] ** 2, ul ** 2 + uxh ** 2, rtol=1e-12, atol=1e-15)
+    ph = phi(g.xc)[None, :]
+    far = g.xc > 30.0  # phi' < 1e-6 there
+    np.testing.assert_allclose(p["omega"][:, far], (-2.0 * U * lam / (1.0 + ph))[:, far], rtol=1e-5)
+    np.testing.assert_allclose(p["pw"], 1.1, rtol=1e-12)
+    # psi at the wall: minus the row sum of rho u^y times the x width of each row
+    wall = -(nn * p["uy"] * g.dl[:, None]).sum(axis=0) * (1.0 + phi(g.xc))
+    np.testing.assert_allclose(p["psi"][-1], wall, rtol=1e-12)
+    assert np.all(p["psi"][0] == 0.0) and np.all(np.diff(p["psi"], axis=0) < 0)
+
+
+def test_post_rotation_and_vorticity_in_the_expansion():
+    """Where phi' is large (the expanding part, xi in [0, 12]): a Cartesian field given as
+    triad components through the inverse rotation comes back unchanged (a sign slip in
+    Eq. canalie_u would not), and the two geometric terms of Eq. (canalie_vorti) are exact
+    for u^x = W lambda^2, u^y = 0 (omega = 2 W lambda^2 phi' / (1 + phi)) and for
+    u^x = W (xi - 5)^2, u^y = 0 (omega = -2 W (xi - 5))."""
+    from oracle.channel import postprocess
+    g = ChannelGrid(10, 24, xi_in=0.0, xi_out=12.0)
+    o = ChannelOracle(MODEL, g, 0.05)
+    lam = g.lc[:, None] * np.ones((1, g.nx))
+    xi = np.ones((g.nl, 1)) * g.xc[None, :]
+    a = lam * dphi(g.xc)[None, :]
+    root = np.sqrt(1.0 + a ** 2)
+    ph = phi(g.xc)[None, :]
+    W = 0.05
+    for ux_c, om in ((W * lam ** 2, 2.0 * W * lam ** 2 * dphi(g.xc)[None, :] / (1.0 + ph)),
+                     (W * (xi - 5.0) ** 2, -2.0 * W * (xi - 5.0))):
+        uy_c = 0.02 + 0.0 * lam
+        F = o.feq_cells(np.ones_like(lam), (ux_c - a * uy_c) / root, (a * ux_c + uy_c) / root, np.ones_like(lam))
+        p = postprocess(o, F)
+        np.testing.assert_allclose(p["ux"], ux_c, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(p["uy"], uy_c, rtol=1e-12)
+        np.testing.assert_allclose(p["omega"], om, rtol=1e-9, atol=1e-13)
