@@ -198,6 +198,22 @@ vlb_status vlb_set_channel_reservoirs(vlb_ctx* ctx, double n_in, double n_out, d
  * or not finite), VLB_ERR_UNSUPPORTED (not a channel context). */
 vlb_status vlb_set_channel_flow_rate(vlb_ctx* ctx, double q0);
 
+/* Channel post-processing (Sec. VII.D-F) of the current state, in FP64 on the device:
+ * ux, uy  -- the Cartesian velocity of Eq. (canalie_u) per cell (n_lambda n_xi, the
+ *            cell order p * n_lambda + s of the distribution layout);
+ * omega   -- the vorticity of Eq. (canalie_vorti) per cell, d/d xi by centred
+ *            differences (second-order one-sided at the first and last column),
+ *            d/d lambda by the paper's three-point formulas on the stretched rows;
+ * psi     -- the stream function of Eq. (canalie_psi_sol) at the row interfaces,
+ *            (n_lambda + 1) per column, index p * (n_lambda + 1) + s for
+ *            lambda_{s}, zero on the centreline, x = lambda (1 + phi) spacing;
+ * pw      -- the wall pressure per column: n T extrapolated linearly from the last
+ *            two rows to the wall.
+ * Host arrays; any may be NULL.  The normalised wall pressure of Eq.
+ * (canalie_wall_pressure) is (pw - pw at the reference column) / (rho0 u0^2).
+ * Errors: VLB_ERR_UNSUPPORTED (not a channel context), VLB_ERR_CUDA. */
+vlb_status vlb_channel_postprocess(vlb_ctx* ctx, double* ux, double* uy, double* psi, double* omega, double* pw);
+
 /* Set every cell of every instance to f_eq(n0, (u0, u1), T0) (Eq. feq_red). */
 vlb_status vlb_init_equilibrium(vlb_ctx* ctx, double n0, double u0, double u1, double T0);
 

@@ -876,6 +876,16 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
   VLB_CUDA(cp, cudaMemcpy(c->d_cgeof, gf.data(), sizeof(ChanCell<float>) * gf.size(), cudaMemcpyHostToDevice));
   VLB_CUDA(cp, cudaMemsetAsync(c->d_nw, 0, sizeof(double) * nx, c->stream));
   VLB_CUDA(cp, cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream));
+  {  // geometry of the post-processing (vlb_channel_postprocess)
+    std::vector<double> pg;
+    pg.insert(pg.end(), lc.begin(), lc.end());
+    pg.insert(pg.end(), lf.begin(), lf.end());
+    for (int p = 0; p < nx; ++p) pg.push_back(phi(xc[p]));
+    for (int p = 0; p < nx; ++p) pg.push_back(dphi(xc[p]));
+    c->chan_dxi = L / nx;
+    VLB_CUDA(cp, cudaMalloc(&c->d_cpost, pg.size() * sizeof(double)));
+    VLB_CUDA(cp, cudaMemcpy(c->d_cpost, pg.data(), pg.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
   VLB_CUDA(cp, cudaStreamSynchronize(c->stream));
   {
     vlb_status ts = upload_channel_tables(cp);
@@ -991,6 +1001,28 @@ vlb_status vlb_set_channel_flow_rate(vlb_ctx* c, double q0) {
   c->cdesc.flow = 1;
   c->cdesc.q0 = q0;
   return drop_channel_graphs(c);
+}
+
+vlb_status vlb_channel_postprocess(vlb_ctx* c, double* ux, double* uy, double* psi, double* omega, double* pw) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (c->kind != 1) return fail(c, VLB_ERR_UNSUPPORTED, "post-processing belongs to channel contexts");
+  const int nl = c->cdesc.nl, nx = c->cdesc.nx;
+  const size_t cells = size_t(nl) * nx, npsi = size_t(nl + 1) * nx;
+  const size_t total = 3 * cells + npsi + nx;
+  if (!c->d_post) VLB_CUDA(c, cudaMalloc(&c->d_post, total * sizeof(double)));
+  vlb_status st = compute_moments(c, c->d_mom);
+  if (st != VLB_OK) return st;
+  double* d = c->d_post;
+  cudaError_t e = launch_channel_post(c->d_mom, c->d_cpost, nl, nx, c->chan_dxi, d, d + cells, d + 2 * cells,
+                                      d + 3 * cells, d + 3 * cells + npsi, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "post-processing kernel launch");
+  double* dst[5] = {ux, uy, omega, psi, pw};
+  const size_t off[5] = {0, cells, 2 * cells, 3 * cells, 3 * cells + npsi};
+  const size_t cnt[5] = {cells, cells, cells, npsi, size_t(nx)};
+  for (int k = 0; k < 5; ++k)
+    if (dst[k])
+      VLB_CUDA(c, cudaMemcpyAsync(dst[k], d + off[k], cnt[k] * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return check_err(c);
 }
 
 vlb_status vlb_init_equilibrium(vlb_ctx* c, double n0, double u0, double u1, double T0) {
@@ -1540,6 +1572,8 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_res);
   cudaFree(c->d_halo);
   cudaFree(c->d_qflow);
+  cudaFree(c->d_cpost);
+  cudaFree(c->d_post);
   delete c;
 }
 
@@ -1582,6 +1616,80 @@ __global__ void residual_kernel(const double* mom, const double* prev, const Ins
 cudaError_t launch_residual(const double* mom, const double* prev, const InstDesc* inst, const GeoCell* geo,
                             int n_inst, double* res, cudaStream_t s) {
   residual_kernel<<<n_inst, 256, 0, s>>>(mom, prev, inst, geo, res);
+  return cudaGetLastError();
+}
+
+// Channel post-processing (Sec. VII.D-F), one thread per xi column p, moments mom in the
+// caller's cell order p * nl + s (n, u^lambda-hat, u^xi-hat, T first):
+//  - Cartesian velocity (Eq. canalie_u): u^x = (u^l + a u^x-hat) / r, u^y = (u^x-hat - a u^l) / r,
+//    a = lambda_s phi'(xi_p), r = sqrt(1 + a^2);
+//  - stream function at the row interfaces (Eq. canalie_psi_sol), zero on the centreline:
+//    psi_{s+1/2} = psi_{s-1/2} - n u^y (lambda_{s+1/2} - lambda_{s-1/2}) (1 + phi_p);
+//  - vorticity (Eq. canalie_vorti): -d u^x / d xi + [d u^y / d lambda + a d u^x / d lambda] / (1 + phi),
+//    xi derivatives centred (second-order one-sided at the first and last column), lambda
+//    derivatives by the three-point formulas on the non-equidistant rows (bulk, first, last node);
+//  - wall pressure: P = n T extrapolated linearly from the last two rows to lambda = 1.
+// tab: lambda_c (nl), lambda_f (nl + 1), phi (nx), phi' (nx) of the column centres.
+__global__ void channel_post_kernel(const double* mom, const double* tab, int nl, int nx, double dxi, double* ux,
+                                    double* uy, double* omega, double* psi, double* pw) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nx) return;
+  const double* lc = tab;
+  const double* lf = lc + nl;
+  const double* ph = lf + nl + 1;
+  const double* dph = ph + nx;
+  auto cart = [&](int q, int s, double& x, double& y) {
+    const double* m = mom + 9 * (size_t(q) * nl + s);
+    const double a = lc[s] * dph[q], r = sqrt(1.0 + a * a);
+    x = (m[1] + a * m[2]) / r;
+    y = (m[2] - a * m[1]) / r;
+  };
+  auto cx = [&](int q, int s) { double x, y; cart(q, s, x, y); return x; };
+  auto cy = [&](int q, int s) { double x, y; cart(q, s, x, y); return y; };
+  // three-point d/d lambda of g(row) at row s
+  auto dl = [&](auto g, int s) {
+    if (s == 0) {
+      const double l1 = lc[0], l2 = lc[1], l3 = lc[2];
+      return -(l2 + l3 - 2 * l1) * g(0) / ((l2 - l1) * (l3 - l1)) + (l3 - l1) * g(1) / ((l2 - l1) * (l3 - l2)) -
+             (l2 - l1) * g(2) / ((l3 - l1) * (l3 - l2));
+    }
+    if (s == nl - 1) {
+      const double lN = lc[nl - 1], lN1 = lc[nl - 2], lN2 = lc[nl - 3];
+      return (2 * lN - lN1 - lN2) * g(nl - 1) / ((lN - lN1) * (lN - lN2)) -
+             (lN - lN2) * g(nl - 2) / ((lN - lN1) * (lN1 - lN2)) + (lN - lN1) * g(nl - 3) / ((lN - lN2) * (lN1 - lN2));
+    }
+    const double lm = lc[s - 1], l0 = lc[s], lp = lc[s + 1];
+    return (l0 - lm) * g(s + 1) / ((lp - l0) * (lp - lm)) + (lp - 2 * l0 + lm) * g(s) / ((lp - l0) * (l0 - lm)) -
+           (lp - l0) * g(s - 1) / ((lp - lm) * (l0 - lm));
+  };
+  double ps = 0.0;
+  psi[size_t(p) * (nl + 1)] = 0.0;
+  for (int s = 0; s < nl; ++s) {
+    double x, y;
+    cart(p, s, x, y);
+    const size_t k = size_t(p) * nl + s;
+    ux[k] = x;
+    uy[k] = y;
+    ps = ps - mom[9 * k] * y * (lf[s + 1] - lf[s]) * (1.0 + ph[p]);
+    psi[size_t(p) * (nl + 1) + s + 1] = ps;
+    double dxux;
+    if (p == 0) dxux = (-3.0 * x + 4.0 * cx(1, s) - cx(2, s)) / (2.0 * dxi);
+    else if (p == nx - 1) dxux = (3.0 * x - 4.0 * cx(nx - 2, s) + cx(nx - 3, s)) / (2.0 * dxi);
+    else dxux = (cx(p + 1, s) - cx(p - 1, s)) / (2.0 * dxi);
+    const double dly = dl([&](int r) { return cy(p, r); }, s);
+    const double dlx = dl([&](int r) { return cx(p, r); }, s);
+    omega[k] = -dxux + (dly + lc[s] * dph[p] * dlx) / (1.0 + ph[p]);
+  }
+  const double* mN = mom + 9 * (size_t(p) * nl + nl - 1);
+  const double* mN1 = mom + 9 * (size_t(p) * nl + nl - 2);
+  const double PN = mN[0] * mN[3], PN1 = mN1[0] * mN1[3];
+  const double lw = lf[nl], l1 = lc[nl - 1], l2 = lc[nl - 2];
+  pw[p] = ((lw - l2) * PN - (lw - l1) * PN1) / (l1 - l2);
+}
+
+cudaError_t launch_channel_post(const double* mom, const double* tab, int nl, int nx, double dxi, double* ux,
+                                double* uy, double* omega, double* psi, double* pw, cudaStream_t s) {
+  channel_post_kernel<<<(nx + 127) / 128, 128, 0, s>>>(mom, tab, nl, nx, dxi, ux, uy, omega, psi, pw);
   return cudaGetLastError();
 }
 

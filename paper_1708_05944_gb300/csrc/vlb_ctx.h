@@ -75,6 +75,9 @@ struct vlb_ctx {
   std::vector<double> chan_lc;    // lambda of the row centres
   double chan_phi_end[2] = {0, 0};  // phi at the inlet and outlet interfaces
   void* d_qflow = nullptr;        // flow-rate ends: 4 n_lambda reals (ChanArgs::qflow)
+  double* d_cpost = nullptr;      // post-processing geometry: lambda_c, lambda_f, phi_c, phi'_c
+  double* d_post = nullptr;       // post-processing outputs (allocated on first use)
+  double chan_dxi = 0.0;
   // CUDA graph of three RK3 steps (nine stage launches), replayed by vlb_step_graph
   // three-step graphs, one per starting buffer F[cur] (captured on first use)
   cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};

@@ -114,5 +114,7 @@ cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelAr
 // Per instance L2 norms of Eq. (msites_steady) between mom and prev (stride 9 per cell), into res (3 per instance).
 cudaError_t launch_residual(const double* mom, const double* prev, const InstDesc* inst, const GeoCell* geo,
                             int n_inst, double* res, cudaStream_t s);
+cudaError_t launch_channel_post(const double* mom, const double* tab, int nl, int nx, double dxi, double* ux,
+                                double* uy, double* omega, double* psi, double* pw, cudaStream_t s);
 
 }  // namespace vlb

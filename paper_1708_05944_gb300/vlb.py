@@ -67,6 +67,7 @@ EXPORTS = {
     "vlb_set_knudsen": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "vlb_set_channel_reservoirs": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
     "vlb_set_channel_flow_rate": (C.c_int, [C.c_void_p, C.c_double]),
+    "vlb_channel_postprocess": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
     "vlb_set_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_read_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_stage": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
@@ -364,6 +365,16 @@ class Channel(_Context):
     def set_flow_rate(self, q0):
         """vlb_set_channel_flow_rate: the paper's parabolic flow-rate ends with half-channel rate q0."""
         _check(_lib.vlb_set_channel_flow_rate(self.h, q0), self.h)
+
+    def postprocess(self):
+        """vlb_channel_postprocess: dict of ux, uy, omega (n_lambda, n_xi), psi (n_lambda + 1, n_xi)
+        and pw (n_xi,), rearranged from the library's column-major order."""
+        nl, nx = self.n_lambda, self.n_xi
+        ux, uy, om = (np.empty(nl * nx) for _ in range(3))
+        psi, pw = np.empty((nl + 1) * nx), np.empty(nx)
+        _check(_lib.vlb_channel_postprocess(self.h, _ptr(ux), _ptr(uy), _ptr(psi), _ptr(om), _ptr(pw)), self.h)
+        col = lambda a, rows: a.reshape(nx, rows).T.copy()
+        return dict(ux=col(ux, nl), uy=col(uy, nl), omega=col(om, nl), psi=col(psi, nl + 1), pw=pw)
 
     def channel_variants(self):
         ts, tp, nt = (np.zeros(8, dtype=np.int32) for _ in range(3))

@@ -276,3 +276,27 @@ def test_flow_rate_channel_reaches_the_poiseuille_gradients():
     (su, hu), (sd, hd) = got
     assert abs(su / hu - 1) < 0.06 and abs(sd / hd - 1) < 0.06, got
     c.close()
+
+
+@pytest.mark.parametrize("prec", [vlb.VLB_FP64, vlb.VLB_FP32_BULK])
+def test_postprocess_matches_oracle(prec):
+    """vlb_channel_postprocess against the oracle's post-processing of the same populations
+    (the library's state read back), after a few flow-rate steps, relative to each field's
+    scale: 1e-12 in FP64; in FP32 1e-5, since the library takes the moments of D + R in FP64
+    while the state it hands back, F in FP32, has lost the low bits of D."""
+    from oracle.channel import postprocess
+    nl, nx = 12, 24
+    o = ChannelOracle(MODEL, ChannelGrid(nl, nx, xi_in=-2.0, xi_out=14.0), 0.05, q0=0.1)
+    F0 = o.initial_state(n_profile=np.ones(nx))
+    F0 = F0 * perturbation(F0.shape, seed=29, amplitude=0.02)
+    c = vlb.Channel(MODEL, prec, nl, nx, 0.05, xi_in=-2.0, xi_out=14.0)
+    c.set_flow_rate(0.1)
+    c.set_f(to_lib(F0).astype(np.float64 if prec == vlb.VLB_FP64 else np.float32))
+    c.step(1e-3, 3)
+    got = c.postprocess()
+    ref = postprocess(o, to_oracle(c.read_f(), nl, nx))
+    tol = 1e-12 if prec == vlb.VLB_FP64 else 1e-5
+    for k in ("ux", "uy", "omega", "psi", "pw"):
+        scale = np.abs(ref[k]).max()
+        assert np.abs(got[k] - ref[k]).max() <= tol * scale, k
+    c.close()
