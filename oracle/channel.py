@@ -99,11 +99,12 @@ class ChannelGrid:
 
 
 class ChannelOracle:
-    def __init__(self, model, grid: ChannelGrid, kn, n_in=2.0, n_out=1.0, T0=1.0, q0=None):
+    def __init__(self, model, grid: ChannelGrid, kn, n_in=2.0, n_out=1.0, T0=1.0, q0=None, prandtl=None):
         self.m = model if isinstance(model, Model) else Model(model)
         self.g = grid
         self.kn, self.n_in, self.n_out, self.T0 = kn, n_in, n_out, T0
         self.q0 = q0  # None: reservoirs; else the half-channel flow rate Q_0 of the flow-rate profiles
+        self.prandtl = prandtl  # None: BGK; else the Shakhov collision with this Pr
         self.last_inflow_density = None
         Q = self.m.spec[0][2]
         nq0 = self.m.nq[0]
@@ -221,6 +222,11 @@ class ChannelOracle:
         force = Glxx * (PXb ** 2 * dl_f - PLb * dxp_f) - Glxl * (PLb ** 2 * dx_f - PXb * dlp_f)
 
         coll = -(F - Feq) / tau[None, :, :, None, None]
+        if self.prandtl is not None:  # Shakhov: the target gains (1 - Pr) times the heat-flux term
+            from .couette import shakhov_term
+            flat = F.reshape((2, nl * nx) + F.shape[3:])
+            G = shakhov_term(m, flat).reshape(F.shape)
+            coll = coll + (1.0 - self.prandtl) * G / tau[None, :, :, None, None]
         self.last_boundary_flux = dict(
             inlet=(g.dl[:, None, None] * fluxx[0, :, 0]).sum(), outlet=(g.dl[:, None, None] * fluxx[0, :, nx]).sum(),
             wall=(g.dchi[:, None, None] * fluxl[0, nl]).sum(), centre=(g.dchi[:, None, None] * fluxl[0, 0]).sum(),

@@ -16,7 +16,10 @@ stretched form, Eq. boltz_couette_str_kom), followed step by step:
    (R_{s+1/2}^2 - R_{s-1/2}^2) (Eqs. flux_kom_R, flux_kom_eta);
 5. the inertial force (1/R)[(p^phi)^2 d_{p^R} f - p^R d_{p^phi}(p^phi f)],
    with the momentum derivatives as K and K~ contractions (Sec. IV.C);
-6. BGK relaxation -(F - F_eq)/tau (Eq. BGK).
+6. BGK relaxation -(F - F_eq)/tau (Eq. BGK), or, with a Prandtl number given, the
+   Shakhov collision the paper names as the extension of BGK (Sec. II.C):
+   -(F - F_eq - (1 - Pr) G)/tau, G the heat-flux part of Grad's form for the
+   cell's own q, projected on the model basis (oracle.seeding).
 
 L = -(advection) - (force) - (F - F_eq)/tau; TVD-RK3 per Eq. (rk3).
 
@@ -106,6 +109,15 @@ class CouetteGrid:
         return self.cell_begin + self.n == self.n_total
 
 
+def shakhov_term(model: Model, F):
+    """The heat-flux term G[F] of the Shakhov target f_eq + (1 - Pr) G (oracle.seeding.heat_flux_term)
+    for the moments n, u, T, q of F, shape (2, S, nq0, nq1) like F."""
+    from .seeding import heat_flux_term
+    mom = model.full_moments(F)
+    g1, g2 = heat_flux_term(model, mom["n"], mom["u0"], mom["u1"], mom["T"], mom["q0"], mom["q1"])
+    return np.stack([g1, g2])
+
+
 def relaxation_time(kn, n, T, mode):
     if mode == TAU_KN_OVER_NT:
         return kn / (n * T)
@@ -117,11 +129,13 @@ def relaxation_time(kn, n, T, mode):
 
 
 class CouetteOracle:
-    def __init__(self, model, grid: CouetteGrid, inner: Wall, outer: Wall, kn: float, tau_mode: int = TAU_AOKI):
+    def __init__(self, model, grid: CouetteGrid, inner: Wall, outer: Wall, kn: float, tau_mode: int = TAU_AOKI,
+                 prandtl=None):
         self.m = model if isinstance(model, Model) else Model(model)
         self.g = grid
         self.inner, self.outer = inner, outer
         self.kn, self.tau_mode = kn, tau_mode
+        self.prandtl = prandtl  # None: BGK (Eq. BGK); else the Shakhov collision with this Pr
         self.last_nw = (float("nan"), float("nan"))
         self.halo = [None, None]  # ghost cells of slab ends (set_halo)
 
@@ -176,8 +190,10 @@ class CouetteOracle:
         dpfdpphi = np.einsum("jk,dsik->dsij", m.Kt[1], F)
         force = (p1[None, None, None, :] ** 2 * dfdpR - p0[None, None, :, None] * dpfdpphi) / g.Rbar[None, :, None, None]
 
-        # 6: BGK
+        # 6: BGK, or Shakhov: the target gains (1 - Pr) times the heat-flux term of the cell's q
         coll = -(F - Feq) / tau[None, :, None, None]
+        if self.prandtl is not None:
+            coll = coll + (1.0 - self.prandtl) * shakhov_term(m, F) / tau[None, :, None, None]
         return -adv - force + coll
 
     def _inner_wall(self, F, G):

@@ -1,8 +1,8 @@
 """Seeding a distribution from macroscopic fields (oracle; test infrastructure only).
 
 The paper has no warm start; this is the reference for the seeding kernel that
-turns predicted fields (n, u^0, u^1, T and the axis-0 heat flux q^0) into the
-populations of a model.  The continuous distribution is Grad's 13-moment form
+turns predicted fields (n, u^0, u^1, T and the heat flux q) into the populations
+of a model, and for the heat-flux term of the Shakhov collision.  The continuous distribution is Grad's 13-moment form
 with only the heat-flux part kept, in three momentum dimensions (p^z is
 integrated out as in Sec. II, which gives the reduced pair f', f''):
 
@@ -106,20 +106,35 @@ def _gauss_power(k, u, T):
     return lambda p: (p - u) ** k * norm * math.exp(-(p - u) ** 2 / (2.0 * T))
 
 
-def seed(model: Model, n, u0, u1, T, q0=None):
-    """(f', f'') of shape (S, nq0, nq1) for fields per cell; q0 = None means q^0 = 0."""
+def seed(model: Model, n, u0, u1, T, q0=None, q1=None):
+    """(f', f'') of shape (S, nq0, nq1) for fields per cell; q0 / q1 = None mean a zero
+    heat flux along that axis.  The axis-1 part is the mirror of the axis-0 part:
+    q^1/T^2 g_0 g_1 xi_1 [(xi_0^2 + xi_1^2)/(5T) - 4/5] in f' (and /5, 2T/5 in f'')."""
     n, u0, u1, T = (np.atleast_1d(np.asarray(x, dtype=np.float64)) for x in (n, u0, u1, T))
     q0 = np.zeros_like(n) if q0 is None else np.atleast_1d(np.asarray(q0, dtype=np.float64))
+    q1 = np.zeros_like(n) if q1 is None else np.atleast_1d(np.asarray(q1, dtype=np.float64))
     S = len(n)
     f1 = np.empty((S, model.nq[0], model.nq[1]))
     f2 = np.empty_like(f1)
     for c in range(S):
-        A = {k: project_axis(model, 0, _gauss_power(k, u0[c], T[c]), u0[c], T[c]) for k in (0, 1, 3)}
-        Bv = {k: project_axis(model, 1, _gauss_power(k, u1[c], T[c]), u1[c], T[c]) for k in (0, 2)}
+        A = {k: project_axis(model, 0, _gauss_power(k, u0[c], T[c]), u0[c], T[c]) for k in (0, 1, 2, 3)}
+        Bv = {k: project_axis(model, 1, _gauss_power(k, u1[c], T[c]), u1[c], T[c]) for k in (0, 1, 2, 3)}
         base = np.outer(A[0], Bv[0])
         t3 = np.outer(A[3], Bv[0]) + np.outer(A[1], Bv[2])  # xi_0 (xi_0^2 + xi_1^2) g_0 g_1
         t1 = np.outer(A[1], Bv[0])                           # xi_0 g_0 g_1
-        Tc, qc = T[c], q0[c]
-        f1[c] = n[c] * base + qc / Tc ** 2 * (t3 / (5.0 * Tc) - 0.8 * t1)
-        f2[c] = Tc * n[c] * base + qc / Tc ** 2 * (t3 / 5.0 - 0.4 * Tc * t1)
+        s3 = np.outer(A[2], Bv[1]) + np.outer(A[0], Bv[3])  # xi_1 (xi_0^2 + xi_1^2) g_0 g_1
+        s1 = np.outer(A[0], Bv[1])                           # xi_1 g_0 g_1
+        Tc, a0, a1 = T[c], q0[c], q1[c]
+        f1[c] = n[c] * base + (a0 * (t3 / (5.0 * Tc) - 0.8 * t1) + a1 * (s3 / (5.0 * Tc) - 0.8 * s1)) / Tc ** 2
+        f2[c] = Tc * n[c] * base + (a0 * (t3 / 5.0 - 0.4 * Tc * t1) + a1 * (s3 / 5.0 - 0.4 * Tc * s1)) / Tc ** 2
     return f1, f2
+
+
+def heat_flux_term(model: Model, n, u0, u1, T, q0, q1):
+    """G = seed(n, u, T, q) - seed(n, u, T, 0): the heat-flux part of Grad's form on the model
+    basis, (G', G'') of shape (S, nq0, nq1).  The Shakhov collision term, the extension of
+    BGK the paper names in Sec. II.C, relaxes towards f_eq + (1 - Pr) G with G built from
+    the current q, so that q relaxes at the rate Pr / tau."""
+    f1, f2 = seed(model, n, u0, u1, T, q0, q1)
+    b1, b2 = seed(model, n, u0, u1, T)
+    return f1 - b1, f2 - b2
