@@ -54,6 +54,7 @@ typedef enum {
 
 typedef enum { VLB_FULL = 0, VLB_HALF = 1 } vlb_quad_kind;           /* H(N;Q) or HH(N;Q) */
 typedef enum { VLB_FP64 = 0, VLB_FP32_BULK = 1 } vlb_precision;
+typedef enum { VLB_BGK = 0, VLB_SHAKHOV = 1 } vlb_collision;
 typedef enum {
   VLB_TAU_KN_OVER_NT = 0, /* tau = Kn / (n T), Eq. (hydro_tau) and Eq. (canalie_tau) */
   VLB_TAU_AOKI = 1,       /* tau = sqrt(pi/8) Kn / n, Eq. (tau_aoki) */
@@ -184,6 +185,16 @@ vlb_status vlb_set_knudsen(vlb_ctx* ctx, double kn, int tau_mode);
  * (VLB_ERR_INVALID); a Couette context gives VLB_ERR_UNSUPPORTED.  Takes effect
  * from the next stage. */
 vlb_status vlb_set_channel_reservoirs(vlb_ctx* ctx, double n_in, double n_out, double T0);
+
+/* Collision term of every stage: VLB_BGK (Eq. BGK, the default) or VLB_SHAKHOV, the
+ * extension the paper names in Sec. II.C: relaxation towards f_eq + (1 - Pr) G, G the
+ * heat-flux part of Grad's 13-moment form for the cell's own heat flux q (both components;
+ * p^z integrated out as in Sec. II; projected on the model basis axis by axis), so that q
+ * relaxes at Pr / tau while n, u, T relax as with BGK; prandtl > 0 (2/3 for hard spheres).
+ * Each stage then adds a second pass (moments of F_prev, then cc dt (1 - Pr) G / tau onto
+ * the stage's output).  Needs expansion orders >= 3 on both axes (VLB_ERR_UNSUPPORTED);
+ * Couette and channel contexts; not with vlb_step_static_scratch. */
+vlb_status vlb_set_collision(vlb_ctx* ctx, int collision, double prandtl);
 
 /* Replace the channel's reservoirs by the paper's flow-rate ends (Sec. VII.C.1-2,
  * Eqs. canalie_inlet, canalie_outlet, canalie_inlet_s), half-channel particle flow

@@ -345,6 +345,26 @@ vlb_status run_stage(vlb_ctx* c, int k) {
   else
     st = c->prec == VLB_FP64 ? do_stage<double>(c, k, prev, out) : do_stage<float>(c, k, prev, out);
   if (st != VLB_OK) return st;
+  if (c->collision == 1) {  // Shakhov: the heat-flux term of F_prev, added to the BGK stage's output
+    const double ccw[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double knf = c->kind == 1 ? c->cdesc.kn : -1.0;
+    cudaError_t e;
+    if (c->prec == VLB_FP64) {
+      e = launch_moments<double>(static_cast<const double*>(c->F[prev]), c->total_cells, c->Vp, c->margs, c->d_mom,
+                                 c->stream, c->cmap);
+      if (e == cudaSuccess)
+        e = launch_shakhov<double>(static_cast<double*>(c->F[out]), c->total_cells, c->Vp, c->margs, c->d_mom,
+                                   c->d_inst, c->n_inst, ccw[k - 1], 1.0 - c->prandtl, knf, c->stream, c->cmap);
+    } else {
+      e = launch_moments<float>(static_cast<const float*>(c->F[prev]), c->total_cells, c->Vp, c->margs, c->d_mom,
+                                c->stream, c->cmap);
+      if (e == cudaSuccess)
+        e = launch_shakhov<float>(static_cast<float*>(c->F[out]), c->total_cells, c->Vp, c->margs, c->d_mom,
+                                  c->d_inst, c->n_inst, ccw[k - 1], 1.0 - c->prandtl, knf, c->stream, c->cmap);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "Shakhov correction launch");
+    c->launches += 2;
+  }
   c->last = out;
   c->stage_done = k;
   if (k == 3) {
@@ -972,6 +992,24 @@ vlb_status vlb_set_channel_reservoirs(vlb_ctx* c, double n_in, double n_out, dou
   vlb_status st = drop_channel_graphs(c);
   if (st != VLB_OK) return st;
   return upload_channel_tables(c);
+}
+
+vlb_status vlb_set_collision(vlb_ctx* c, int collision, double prandtl) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (collision != 0 && collision != 1) return fail(c, VLB_ERR_INVALID, "collision must be VLB_BGK or VLB_SHAKHOV");
+  if (collision == 1 && (!(prandtl > 0.0) || !std::isfinite(prandtl)))
+    return fail(c, VLB_ERR_INVALID, "the Prandtl number must be finite and > 0");
+  if (collision == 1 && (c->margs.N0 < 3 || c->margs.N1 < 3))
+    return fail(c, VLB_ERR_UNSUPPORTED, "the Shakhov term needs expansion orders >= 3 on both axes");
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int b = 0; b < 3; ++b) {  // captured graphs hold the old launch sequence
+    if (c->graph_exec[b]) cudaGraphExecDestroy(c->graph_exec[b]);
+    c->graph_exec[b] = nullptr;
+    c->graph_variant[b] = -1;
+  }
+  c->collision = collision;
+  c->prandtl = collision == 1 ? prandtl : 1.0;
+  return VLB_OK;
 }
 
 vlb_status vlb_set_channel_flow_rate(vlb_ctx* c, double q0) {

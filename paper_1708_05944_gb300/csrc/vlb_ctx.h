@@ -60,6 +60,8 @@ struct vlb_ctx {
   double* d_res = nullptr;
   void* d_halo = nullptr;  // Couette: 2 x 3 ghost rows per instance for slab halo ends
   bool has_halo = false;   // some instance has a halo end (vlb_stage only)
+  int collision = 0;       // vlb_collision: 0 BGK, 1 Shakhov
+  double prandtl = 1.0;
   bool have_prev = false;
   size_t tile_cap = 0;
   // channel

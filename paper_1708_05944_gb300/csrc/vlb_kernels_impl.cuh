@@ -523,6 +523,64 @@ cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, co
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- Shakhov collision
+// The Shakhov collision relaxes towards f_eq + (1 - Pr) G, G the heat-flux part of Grad's
+// form for the cell's own q (the seed kernel's term, with both axes):
+//   G'  = [q0 (t3_0 / (5T) - 4/5 t1_0) + q1 (t3_1 / (5T) - 4/5 t1_1)] / T^2,
+//   G'' = [q0 (t3_0 / 5 - 2T/5 t1_0) + q1 (t3_1 / 5 - 2T/5 t1_1)] / T^2,
+//   t3_0 = A3 B0 + A1 B2, t1_0 = A1 B0, t3_1 = A2 B1 + A0 B3, t1_1 = A0 B1,
+// A_k, B_k the projections of xi^k g on axes 0 and 1.  Against the BGK stage that the stage
+// kernel has written, a stage of weight cc adds cc dt (1 - Pr) G[F_prev] / tau to F_out;
+// mom holds the moments of F_prev (launch_moments, caller cell order).  One CTA per cell.
+template <typename real>
+__global__ void shakhov_kernel(real* Fout, long long cells, int Vp, const __grid_constant__ ModelArgs m,
+                               const double* mom, const InstDesc* inst, int n_inst, double cc, double omp,
+                               double kn_fixed, CellMap map) {
+  __shared__ double A[4][MAXQ], B[4][MAXQ];
+  for (long long c = blockIdx.x; c < cells; c += gridDim.x) {
+    const double* o = mom + 9 * caller_cell(map, c);
+    const double n = o[0], u0 = o[1], u1 = o[2], T = o[3], q0 = o[7], q1 = o[8];
+    if (threadIdx.x < 8) {
+      const int t = threadIdx.x;
+      if (t < 4) xi_power_populations(m.kind0, m.N0, m.nq0, m.p0, m.tab0, u0, T, t, A[t]);
+      else xi_power_populations(m.kind1, m.N1, m.nq1, m.p1, m.tab1, u1, T, t - 4, B[t - 4]);
+    }
+    // the instance of the cell (its Kn, tau convention and dt): cells run over the instances in order
+    int lo = 0, hi = n_inst - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (inst[mid].cell0 <= c) lo = mid; else hi = mid - 1;
+    }
+    const InstDesc& d = inst[lo];
+    const double tau = kn_fixed > 0.0 ? kn_fixed / (n * T) : relaxation_time<double>(d.tau_mode, d.kn, n, T);
+    const double coef = cc * d.dt * omp / tau;
+    const double a0 = q0 / (T * T), a1 = q1 / (T * T);
+    __syncthreads();
+    const int V = m.nq0 * m.nq1;
+    for (int x = threadIdx.x; x < 2 * V; x += blockDim.x) {
+      const int v = x >> 1, f = x & 1;
+      const int i = v / m.nq1, j = v - i * m.nq1;
+      const double t3a = A[3][i] * B[0][j] + A[1][i] * B[2][j], t1a = A[1][i] * B[0][j];
+      const double t3b = A[2][i] * B[1][j] + A[0][i] * B[3][j], t1b = A[0][i] * B[1][j];
+      const double G = f ? a0 * (0.2 * t3a - 0.4 * T * t1a) + a1 * (0.2 * t3b - 0.4 * T * t1b)
+                         : a0 * (t3a / (5.0 * T) - 0.8 * t1a) + a1 * (t3b / (5.0 * T) - 0.8 * t1b);
+      real* y = Fout + c * 2 * Vp + x;
+      *y = real(double(*y) + coef * G);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename real>
+cudaError_t launch_shakhov(real* Fout, long long cells, int Vp, const ModelArgs& m, const double* mom,
+                           const InstDesc* inst, int n_inst, double cc, double one_minus_pr, double kn_fixed,
+                           cudaStream_t s, CellMap map) {
+  const long long blocks = cells < 152 * 16 ? cells : 152 * 16;
+  shakhov_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(Fout, cells, Vp, m, mom, inst, n_inst, cc,
+                                                                    one_minus_pr, kn_fixed, map);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- caller layout <-> device layout
 // Caller rows hold f' then f'' (V values each); device rows hold the deviation
 // from R as interleaved (f', f'') pairs of Vp velocities.  One CTA per cell row
@@ -655,5 +713,7 @@ template cudaError_t launch_deviation<VLB_REAL>(const VLB_REAL*, VLB_REAL*, long
                                                 cudaStream_t, CellMap);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,
                                               cudaStream_t, CellMap);
+template cudaError_t launch_shakhov<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
+                                              const InstDesc*, int, double, double, double, cudaStream_t, CellMap);
 
 }  // namespace vlb

@@ -106,6 +106,14 @@ template <typename real>
 cudaError_t launch_deviation(const real* src, real* dst, long long cells, int Vp, const ModelArgs& m,
                              int to_deviation, cudaStream_t s, CellMap map = CellMap{});
 
+// Shakhov correction of a stage (see shakhov_kernel): F_out += cc dt (1 - Pr) G[F_prev] / tau per
+// cell, mom the moments of F_prev (launch_moments); kn_fixed > 0: tau = kn_fixed / (n T) for
+// every cell, else each cell's instance (Kn, tau convention); dt from the instance.
+template <typename real>
+cudaError_t launch_shakhov(real* Fout, long long cells, int Vp, const ModelArgs& m, const double* mom,
+                           const InstDesc* inst, int n_inst, double cc, double one_minus_pr, double kn_fixed,
+                           cudaStream_t s, CellMap map = CellMap{});
+
 // Per cell, FP64: n, u0, u1, T, T00, T01, T11, q0, q1 (stride 9).
 template <typename real>
 cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelArgs& m, double* out, cudaStream_t s,

@@ -18,6 +18,7 @@ VLB_OK, VLB_ERR_INVALID, VLB_ERR_UNSUPPORTED, VLB_ERR_CUDA, VLB_ERR_NONFINITE, V
     0, -1, -2, -3, -4, -5, -6)
 VLB_FULL, VLB_HALF = 0, 1
 VLB_FP64, VLB_FP32_BULK = 0, 1
+VLB_BGK, VLB_SHAKHOV = 0, 1
 VLB_TAU_KN_OVER_NT, VLB_TAU_AOKI, VLB_TAU_KN_OVER_N = 0, 1, 2
 
 _STATUS = {VLB_ERR_INVALID: "INVALID", VLB_ERR_UNSUPPORTED: "UNSUPPORTED", VLB_ERR_CUDA: "CUDA",
@@ -67,6 +68,7 @@ EXPORTS = {
     "vlb_set_knudsen": (C.c_int, [C.c_void_p, C.c_double, C.c_int]),
     "vlb_set_channel_reservoirs": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
     "vlb_set_channel_flow_rate": (C.c_int, [C.c_void_p, C.c_double]),
+    "vlb_set_collision": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
     "vlb_channel_postprocess": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
     "vlb_set_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_read_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -230,6 +232,10 @@ class _Context:
         q = np.empty((N, 2)) if full else None
         _check(_lib.vlb_read_moments(self.h, _ptr(n), _ptr(u0), _ptr(u1), _ptr(T), _ptr(Tab), _ptr(q), 0), self.h)
         return (n, u0, u1, T, Tab, q) if full else (n, u0, u1, T)
+
+    def set_collision(self, collision, prandtl=1.0):
+        """vlb_set_collision: VLB_BGK, or VLB_SHAKHOV with the given Prandtl number."""
+        _check(_lib.vlb_set_collision(self.h, collision, prandtl), self.h)
 
     def set_knudsen(self, kn, tau_mode=VLB_TAU_KN_OVER_NT):
         _check(_lib.vlb_set_knudsen(self.h, kn, tau_mode), self.h)
