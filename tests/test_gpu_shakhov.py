@@ -48,7 +48,7 @@ def test_couette_stages_match_oracle(prec, spec, n, A):
     b = vlb.Couette(spec, prec, [grid], [(0.2, 1.0)], [(0.0, 1.05)], [0.1], [1])
     b.set_f(to_lib(F0).astype(np.float64 if prec == vlb.VLB_FP64 else np.float32))
     b.step(dt, 1)
-    assert rel_err(to_oracle(b.read_f()), F3) > 100 * tol
+    assert rel_err(to_oracle(b.read_f()), F3) > 1e-5  # one step's correction: about 4e-5 of F
     c.close()
     b.close()
 
