@@ -432,6 +432,9 @@ def bench_couette(args, torch, stream, vlb, flush):
     tuned32, _ = ctx.autotune(DT, reps=20)
     shape32 = ctx.variants()[tuned32]
     step_ms, stage_ms = time_device(ctx, torch, stream, args.couette_steps, 3, flush)
+    # the same batch with the Shakhov collision (Pr = 2/3): the BGK stage plus its correction pass
+    ctx.set_collision(vlb.VLB_SHAKHOV, 2.0 / 3.0)
+    shk_ms, _ = time_device(ctx, torch, stream, max(3, min(args.couette_steps, 20)), 2, flush)
     ctx.close()
     ctx64 = make_ctx(vlb.VLB_FP64, stream.cuda_stream)
     ctx64.set_f(make_inputs(np.float64))
@@ -454,6 +457,10 @@ def bench_couette(args, torch, stream, vlb, flush):
         "ms_per_step": float(step_ms.mean()), "steps": len(step_ms), "launch_ms": launch_ms,
         "achieved_GBps_algorithmic": b32 / (launch_ms * 1e-3) / 1e9,
         "launch_shape": {"cells_per_cta": shape32[0], "threads": shape32[1], "persistent": bool(shape32[2])},
+        "shakhov": {"value": units / (float(shk_ms.mean()) * 1e-3), "unit": "cell-velocity updates/s",
+                    "ms_per_step": float(shk_ms.mean()), "prandtl": 2.0 / 3.0,
+                    "note": "FP32 bulk; each stage is the BGK stage kernel, a moments pass over F_prev and the "
+                            "Shakhov correction kernel"},
         "fp64": {"value": units / (float(s64.mean()) * 1e-3), "unit": "cell-velocity updates/s",
                  "ms_per_step": float(s64.mean()), "launch_shape": {"cells_per_cta": shape64[0], "threads": shape64[1]},
                  "roofline": {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
