@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libvlb.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["vlb_api.cu", "vlb_f32.cu", "vlb_f64.cu", "vlb_tables.cpp", "vlb_static.cu", "vlb_no.cu", "vlb_peak.cu"]
+SOURCES = ["vlb_api.cu", "vlb_f32.cu", "vlb_f64.cu", "vlb_tables.cpp", "vlb_static.cu", "vlb_no.cu", "vlb_peak.cu",
+           "vlb_large.cu"]
 
 
 def nvcc() -> str:

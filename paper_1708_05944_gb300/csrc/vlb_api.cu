@@ -249,6 +249,71 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   return VLB_OK;
 }
 
+template <typename real>
+vlb_status do_large_stage(vlb_ctx* c, int k, int prev, int out) {
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cc[3] = {1.0, 0.25, 2.0 / 3.0};
+  cudaError_t e = lm_stage<real>(c->lm, static_cast<const real*>(c->F[prev]), static_cast<const real*>(c->F[c->cur]),
+                                 static_cast<real*>(c->F[out]), c->total_cells, c->d_inst, c->n_inst, c->d_geo,
+                                 c->d_lwall, c->d_nw, static_cast<real*>(c->d_lrec), static_cast<real*>(c->d_lforce),
+                                 c->d_lpart, ca[k - 1], cc[k - 1], c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "large-set stage launch");
+  c->launches += 5;
+  return VLB_OK;
+}
+
+// Model tables of a large velocity set in device memory (LargeModel), from the axis tables.
+vlb_status setup_large(vlb_ctx* c) {
+  const AxisTables &a0 = c->ax[0], &a1 = c->ax[1];
+  const int nq0 = c->nq0, nq1 = c->nq1;
+  std::vector<double> d;
+  auto put = [&](const std::vector<double>& v) { size_t o = d.size(); d.insert(d.end(), v.begin(), v.end()); return o; };
+  std::vector<double> iw0(nq0), iw1(nq1), t0(size_t(nq0) * MAXN, 0.0), t1(size_t(nq1) * MAXN, 0.0);
+  for (int k = 0; k < nq0; ++k) iw0[k] = 1.0 / a0.w[k];
+  for (int k = 0; k < nq1; ++k) iw1[k] = 1.0 / a1.w[k];
+  for (int k = 0; k < nq0; ++k)
+    for (int s2 = 0; s2 <= a0.N; ++s2) t0[size_t(k) * MAXN + s2] = a0.eqtab[size_t(k) * (a0.N + 1) + s2];
+  for (int k = 0; k < nq1; ++k)
+    for (int s2 = 0; s2 <= a1.N; ++s2) t1[size_t(k) * MAXN + s2] = a1.eqtab[size_t(k) * (a1.N + 1) + s2];
+  const size_t op0 = put(a0.p), op1 = put(a1.p), ow0 = put(a0.w), ow1 = put(a1.w), oi0 = put(iw0), oi1 = put(iw1);
+  const size_t ot0 = put(t0), ot1 = put(t1), oK = put(a0.K), oKt = put(a1.Kt);
+  // single precision: sqrt(w_k' / w_k) K and the scale vectors (see LargeModel)
+  std::vector<float> f;
+  for (int k = 0; k < nq0; ++k)
+    for (int kp = 0; kp < nq0; ++kp) f.push_back(float(a0.K[size_t(k) * nq0 + kp] * std::sqrt(a0.w[kp] / a0.w[k])));
+  const size_t ofKt = f.size();
+  for (int k = 0; k < nq1; ++k)
+    for (int kp = 0; kp < nq1; ++kp) f.push_back(float(a1.Kt[size_t(k) * nq1 + kp] * std::sqrt(a1.w[kp] / a1.w[k])));
+  const size_t os0 = f.size();
+  for (int k = 0; k < nq0; ++k) f.push_back(float(std::sqrt(a0.w[k])));
+  const size_t ois0 = f.size();
+  for (int k = 0; k < nq0; ++k) f.push_back(float(std::min(1.0 / std::sqrt(a0.w[k]), 1e30)));
+  const size_t os1 = f.size();
+  for (int k = 0; k < nq1; ++k) f.push_back(float(std::sqrt(a1.w[k])));
+  const size_t ois1 = f.size();
+  for (int k = 0; k < nq1; ++k) f.push_back(float(std::min(1.0 / std::sqrt(a1.w[k]), 1e30)));
+  const size_t dbytes = d.size() * sizeof(double);
+  VLB_CUDA(c, cudaMalloc(&c->d_lm, dbytes + f.size() * sizeof(float)));
+  VLB_CUDA(c, cudaMemcpy(c->d_lm, d.data(), dbytes, cudaMemcpyHostToDevice));
+  VLB_CUDA(c, cudaMemcpy(static_cast<char*>(c->d_lm) + dbytes, f.data(), f.size() * sizeof(float),
+                         cudaMemcpyHostToDevice));
+  const double* D = static_cast<const double*>(c->d_lm);
+  const float* Fp = reinterpret_cast<const float*>(static_cast<const char*>(c->d_lm) + dbytes);
+  LargeModel& m = c->lm;
+  m.nq0 = nq0, m.nq1 = nq1, m.V = c->V, m.Vp = c->Vp, m.N0 = a0.N, m.N1 = a1.N, m.kind0 = a0.kind, m.kind1 = a1.kind;
+  m.p0 = D + op0, m.p1 = D + op1, m.w0 = D + ow0, m.w1 = D + ow1, m.iw0 = D + oi0, m.iw1 = D + oi1;
+  m.tab0 = D + ot0, m.tab1 = D + ot1, m.K0 = D + oK, m.Kt1 = D + oKt, m.K0f = Fp, m.Kt1f = Fp + ofKt;
+  m.s0f = Fp + os0, m.is0f = Fp + ois0, m.s1f = Fp + os1, m.is1f = Fp + ois1;
+  double sw1 = 0, pos = 0, neg = 0;
+  for (int k = 0; k < nq1; ++k) sw1 += a1.w[k];
+  for (int k = 0; k < nq0; ++k) {
+    if (a0.p[k] > 0.0) pos += a0.p[k] * a0.w[k];
+    if (a0.p[k] < 0.0) neg += a0.p[k] * a0.w[k];
+  }
+  m.ref_flux_pos = pos * sw1;
+  m.ref_flux_neg = neg * sw1;
+  return VLB_OK;
+}
+
 // Rows per lambda segment and segments of a channel launch shape.  A fixed ts
 // is used as given (at least 3 rows per segment, the last one included); ts = 0
 // picks the segment count that minimises waves x (rows + 6) over the SMs of the
@@ -342,6 +407,8 @@ vlb_status run_stage(vlb_ctx* c, int k) {
   vlb_status st;
   if (c->kind == 1)
     st = c->prec == VLB_FP64 ? do_chan_stage<double>(c, k, prev, out) : do_chan_stage<float>(c, k, prev, out);
+  else if (c->large)
+    st = c->prec == VLB_FP64 ? do_large_stage<double>(c, k, prev, out) : do_large_stage<float>(c, k, prev, out);
   else
     st = c->prec == VLB_FP64 ? do_stage<double>(c, k, prev, out) : do_stage<float>(c, k, prev, out);
   if (st != VLB_OK) return st;
@@ -384,6 +451,15 @@ vlb_status check_err(vlb_ctx* c) {
 }
 
 vlb_status compute_moments(vlb_ctx* c, double* dst) {
+  if (c->large) {
+    cudaError_t e = c->prec == VLB_FP64
+                        ? lm_moments<double>(c->lm, static_cast<const double*>(c->F[c->last]), c->total_cells, dst,
+                                             c->stream)
+                        : lm_moments<float>(c->lm, static_cast<const float*>(c->F[c->last]), c->total_cells, dst,
+                                            c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "moments kernel launch");
+    return VLB_OK;
+  }
   cudaError_t e = c->prec == VLB_FP64
                       ? launch_moments<double>(static_cast<const double*>(c->F[c->last]), c->total_cells, c->Vp,
                                                c->margs, dst, c->stream, c->cmap)
@@ -480,6 +556,42 @@ void fill_walls(vlb_ctx* c, std::vector<WallEq>& out) {
 }
 
 vlb_status upload_walls(vlb_ctx* c) {
+  if (c->large) {  // per (instance, wall): g0, g1, in_flux, T_w from the axis tables
+    const int nq0 = c->nq0, nq1 = c->nq1, st = nq0 + nq1 + 2;
+    const AxisTables &a0 = c->ax[0], &a1 = c->ax[1];
+    std::vector<double> w(size_t(c->n_inst) * 2 * st);
+    for (int i = 0; i < c->n_inst; ++i)
+      for (int wl = 0; wl < 2; ++wl) {
+        double* e = &w[(size_t(i) * 2 + wl) * st];
+        const double uw = wl == 0 ? c->inst[i].u_in : c->inst[i].u_out;
+        const double Tw = wl == 0 ? c->inst[i].T_in : c->inst[i].T_out;
+        double mp[MAXN], mm[MAXN];
+        host_moment_vector(a0.kind, a0.N, 0.0, Tw, mp);
+        for (int k = 0; k < nq0; ++k) {
+          double g = 0;
+          for (int s2 = 0; s2 <= a0.N; ++s2) g += a0.eqtab[size_t(k) * (a0.N + 1) + s2] * mp[s2];
+          e[k] = g;
+        }
+        host_moment_vector(a1.kind, a1.N, uw, Tw, mp);
+        host_moment_vector(a1.kind, a1.N, -uw, Tw, mm);
+        for (int k = 0; k < nq1; ++k) {
+          const double* v = (a1.kind == 1 && a1.p[k] < 0.0) ? mm : mp;
+          double g = 0;
+          for (int s2 = 0; s2 <= a1.N; ++s2) g += a1.eqtab[size_t(k) * (a1.N + 1) + s2] * v[s2];
+          e[nq0 + k] = g;
+        }
+        const double sgn = wl == 0 ? 1.0 : -1.0;
+        double s0 = 0, s1 = 0;
+        for (int k = 0; k < nq0; ++k)
+          if (sgn * a0.p[k] > 0.0) s0 += e[k] * a0.p[k];
+        for (int k = 0; k < nq1; ++k) s1 += e[nq0 + k];
+        e[nq0 + nq1] = s0 * s1;
+        e[nq0 + nq1 + 1] = Tw;
+      }
+    VLB_CUDA(c, cudaMemcpyAsync(c->d_lwall, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+    return VLB_OK;
+  }
   std::vector<WallEq> w;
   fill_walls(c, w);
   VLB_CUDA(c, cudaMemcpyAsync(c->d_wall, w.data(), sizeof(WallEq) * w.size(), cudaMemcpyHostToDevice, c->stream));
@@ -496,6 +608,15 @@ int spare_buffer(const vlb_ctx* c) {
 
 // Caller layout F <-> device layout D = F - R (see launch_deviation).
 vlb_status convert(vlb_ctx* c, const void* src, void* dst, int to_deviation) {
+  if (c->large) {
+    cudaError_t e = c->prec == VLB_FP64
+                        ? lm_deviation<double>(c->lm, static_cast<const double*>(src), static_cast<double*>(dst),
+                                               c->total_cells, to_deviation, c->stream)
+                        : lm_deviation<float>(c->lm, static_cast<const float*>(src), static_cast<float*>(dst),
+                                              c->total_cells, to_deviation, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "conversion kernel launch");
+    return VLB_OK;
+  }
   cudaError_t e = c->prec == VLB_FP64
                       ? launch_deviation<double>(static_cast<const double*>(src), static_cast<double*>(dst),
                                                  c->total_cells, c->Vp, c->margs, to_deviation, c->stream, c->cmap)
@@ -604,7 +725,13 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     if (!(inner[i].T > 0.0) || !(outer[i].T > 0.0)) return fail(nullptr, VLB_ERR_INVALID, "wall temperature must be > 0");
   }
   const int nq0 = axis_nodes(model, 0), nq1 = axis_nodes(model, 1);
-  if (nq0 > MAXQ || nq1 > MAXQ) return fail(nullptr, VLB_ERR_UNSUPPORTED, "more than 32 nodes on an axis");
+  const bool large = nq0 > MAXQ || nq1 > MAXQ;  // beyond the fused kernels: the multi-kernel path
+  if (large && (long long)nq0 * nq1 > 65536) return fail(nullptr, VLB_ERR_UNSUPPORTED, "more than 65536 velocities");
+  if (large)
+    for (int i = 0; i < n_inst; ++i)
+      if (!(grids[i].cell_begin == 0 && grids[i].cell_end == 0) &&
+          !(grids[i].cell_begin == 0 && grids[i].cell_end == grids[i].n_cells))
+        return fail(nullptr, VLB_ERR_UNSUPPORTED, "slabs of large velocity sets are not built");
   if (model->N[0] + 1 > MAXN || model->N[1] + 1 > MAXN)
     return fail(nullptr, VLB_ERR_UNSUPPORTED, "expansion order above 7");
 
@@ -622,7 +749,13 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   c->V = nq0 * nq1;
   c->Vp = (c->V + 3) / 4 * 4;
   c->esize = prec == VLB_FP64 ? 8 : 4;
-  {
+  c->large = large;
+  if (large) {
+    c->variants[0] = StageVariant{1, 256, 0};  // one launch shape: the four kernels of vlb_large.cu
+    c->n_variants = 1;
+    vlb_status ls = setup_large(c.get());
+    if (ls != VLB_OK) return ls;
+  } else {
     StageVariant all[8];
     const int n = prec == VLB_FP64 ? stage_variants<double>(nq0, nq1, all) : stage_variants<float>(nq0, nq1, all);
     for (int i = 0; i < n; ++i) {
@@ -637,6 +770,7 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   }
 
   ModelArgs& m = c->margs;
+  if (!large) {
   m.nq0 = nq0;
   m.nq1 = nq1;
   m.N0 = model->N[0];
@@ -674,6 +808,11 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     return fail(nullptr, VLB_ERR_UNSUPPORTED, "force kernels are not reflection-symmetric");
   fill_force_tables(*c->k64, c->ax[0].K, c->ax[1].Kt, m.kind0, m.kind1, nq0, nq1, split);
   fill_force_tables(*c->k32, c->ax[0].K, c->ax[1].Kt, m.kind0, m.kind1, nq0, nq1, split);
+  } else {
+    m.nq0 = nq0, m.nq1 = nq1, m.N0 = model->N[0], m.N1 = model->N[1];
+    m.kind0 = model->kind[0] == VLB_HALF ? 1 : 0;
+    m.kind1 = model->kind[1] == VLB_HALF ? 1 : 0;
+  }
 
   long long cell0 = 0;
   for (int i = 0; i < n_inst; ++i) {
@@ -699,7 +838,7 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
     cell0 += d.n_cells;
   }
   c->total_cells = cell0;
-  build_tiles(c.get());
+  if (!large) build_tiles(c.get());
   c->geo.resize(cell0);
   for (int i = 0; i < n_inst; ++i) {  // a slab takes its cells' geometry from the whole grid
     std::vector<GeoCell> full(grids[i].n_cells);
@@ -729,6 +868,14 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
   VLB_CUDA(cp, cudaMalloc(&c->d_halo, size_t(n_inst) * 6 * 2 * c->Vp * c->esize));
   VLB_CUDA(cp, cudaMemsetAsync(c->d_halo, 0, size_t(n_inst) * 6 * 2 * c->Vp * c->esize, c->stream));
   VLB_CUDA(cp, cudaMemcpyAsync(c->d_inst, c->inst.data(), sizeof(InstDesc) * n_inst, cudaMemcpyHostToDevice, c->stream));
+  if (large) {
+    const size_t cells = size_t(c->total_cells), es = c->esize;
+    VLB_CUDA(cp, cudaMalloc(&c->d_lrec, cells * (nq0 + nq1 + 2) * es));
+    VLB_CUDA(cp, cudaMalloc(&c->d_lforce, lm_force_reals(c->lm, c->total_cells) * es));
+    VLB_CUDA(cp, cudaMalloc(&c->d_lpart, lm_part_doubles(c->lm, c->total_cells, n_inst) * sizeof(double)));
+    VLB_CUDA(cp, cudaMalloc(&c->d_lwall, size_t(n_inst) * 2 * (nq0 + nq1 + 2) * sizeof(double)));
+    c->lm.err = c->d_err;
+  }
   {
     vlb_status ws = upload_walls(cp);
     if (ws != VLB_OK) return ws;
@@ -999,6 +1146,7 @@ vlb_status vlb_set_collision(vlb_ctx* c, int collision, double prandtl) {
   if (collision != 0 && collision != 1) return fail(c, VLB_ERR_INVALID, "collision must be VLB_BGK or VLB_SHAKHOV");
   if (collision == 1 && (!(prandtl > 0.0) || !std::isfinite(prandtl)))
     return fail(c, VLB_ERR_INVALID, "the Prandtl number must be finite and > 0");
+  if (collision == 1 && c->large) return fail(c, VLB_ERR_UNSUPPORTED, "the Shakhov pass is built for up to 32 nodes per axis");
   if (collision == 1 && (c->margs.N0 < 3 || c->margs.N1 < 3))
     return fail(c, VLB_ERR_UNSUPPORTED, "the Shakhov term needs expansion orders >= 3 on both axes");
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1066,7 +1214,13 @@ vlb_status vlb_channel_postprocess(vlb_ctx* c, double* ux, double* uy, double* p
 vlb_status vlb_init_equilibrium(vlb_ctx* c, double n0, double u0, double u1, double T0) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
   if (!(n0 > 0.0) || !(T0 > 0.0)) return fail(c, VLB_ERR_INVALID, "need n0 > 0 and T0 > 0");
-  cudaError_t e = c->prec == VLB_FP64
+  cudaError_t e = c->large
+                      ? (c->prec == VLB_FP64
+                             ? lm_init<double>(c->lm, static_cast<double*>(c->F[c->cur]), c->total_cells, n0, u0, u1,
+                                               T0, c->stream)
+                             : lm_init<float>(c->lm, static_cast<float*>(c->F[c->cur]), c->total_cells, n0, u0, u1,
+                                              T0, c->stream))
+                  : c->prec == VLB_FP64
                       ? launch_init_equilibrium<double>(static_cast<double*>(c->F[c->cur]), c->total_cells, c->Vp,
                                                         c->margs, n0, u0, u1, T0, c->stream)
                       : launch_init_equilibrium<float>(static_cast<float*>(c->F[c->cur]), c->total_cells, c->Vp,
@@ -1081,6 +1235,7 @@ vlb_status vlb_init_equilibrium(vlb_ctx* c, double n0, double u0, double u1, dou
 vlb_status vlb_init_from_moments(vlb_ctx* c, const double* n, const double* u0, const double* u1, const double* T,
                                  const double* q0, int on_device) {
   if (!c || !n || !u0 || !u1 || !T) return fail(c, VLB_ERR_INVALID, "null argument");
+  if (c->large) return fail(c, VLB_ERR_UNSUPPORTED, "seeding is built for up to 32 nodes per axis");
   const size_t N = size_t(c->total_cells);
   if (!on_device)
     for (size_t i = 0; i < N; ++i)
@@ -1442,7 +1597,7 @@ vlb_status vlb_set_variant(vlb_ctx* c, int v) {
   if (v < 0 || v >= (c->kind == 1 ? c->n_cvariants : c->n_variants)) return fail(c, VLB_ERR_INVALID, "no such launch shape");
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->variant = v;
-  if (c->kind == 1) return VLB_OK;
+  if (c->kind == 1 || c->large) return VLB_OK;
   build_tiles(c);
   VLB_CUDA(c, cudaMemcpyAsync(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * c->tiles.size(),
                               cudaMemcpyHostToDevice, c->stream));
@@ -1612,6 +1767,11 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_qflow);
   cudaFree(c->d_cpost);
   cudaFree(c->d_post);
+  cudaFree(c->d_lm);
+  cudaFree(c->d_lwall);
+  cudaFree(c->d_lrec);
+  cudaFree(c->d_lforce);
+  cudaFree(c->d_lpart);
   delete c;
 }
 

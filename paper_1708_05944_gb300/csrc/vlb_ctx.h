@@ -61,6 +61,14 @@ struct vlb_ctx {
   void* d_halo = nullptr;  // Couette: 2 x 3 ghost rows per instance for slab halo ends
   bool has_halo = false;   // some instance has a halo end (vlb_stage only)
   int collision = 0;       // vlb_collision: 0 BGK, 1 Shakhov
+  // velocity sets beyond 32 nodes on an axis: the multi-kernel path of vlb_large.cu
+  bool large = false;
+  LargeModel lm{};
+  void* d_lm = nullptr;      // the LargeModel tables (one allocation)
+  double* d_lwall = nullptr;  // per (instance, wall): g0, g1, in_flux, T_w
+  void* d_lrec = nullptr;     // per cell equilibrium record
+  void* d_lforce = nullptr;   // per cell force term
+  double* d_lpart = nullptr;  // per cell and wall chunk sums
   double prandtl = 1.0;
   bool have_prev = false;
   size_t tile_cap = 0;

@@ -114,6 +114,35 @@ cudaError_t launch_shakhov(real* Fout, long long cells, int Vp, const ModelArgs&
                            const InstDesc* inst, int n_inst, double cc, double one_minus_pr, double kn_fixed,
                            cudaStream_t s, CellMap map = CellMap{});
 
+// Model tables of a Couette context beyond the fused kernels' 32 nodes per axis (device
+// pointers; tab rows have stride MAXN; K0 is d/dp on axis 0, Kt1 d/dp (p .) on axis 1).
+struct LargeModel {
+  int nq0, nq1, V, Vp, N0, N1, kind0, kind1;
+  const double *p0, *p1, *w0, *w1, *iw0, *iw1, *tab0, *tab1, *K0, *Kt1;
+  // single precision: the symmetric scaling sqrt(w_k' / w_k) K of both matrices (entries of
+  // order Q^(3/2); K itself reaches 1e117 at Q = 200), with sqrt(w) and 1/sqrt(w) (capped at 1e30)
+  const float *K0f, *Kt1f, *s0f, *is0f, *s1f, *is1f;
+  double ref_flux_neg, ref_flux_pos;  // outgoing particle flux of R at the inner / outer wall
+  unsigned* err;
+};
+
+// One RK3 stage of the large-set Couette path (see vlb_large.cu): walls holds per
+// (instance, wall) g0 (nq0), g1 (nq1) of f_eq(1, (0, u_w), T_w), the incoming flux and T_w;
+// rec (cells x (nq0 + nq1 + 2)), force (lm_force_reals) and part (lm_part_doubles) are scratch.
+template <typename real>
+cudaError_t lm_stage(const LargeModel& m, const real* Fprev, const real* Fl, real* Fout, long long cells,
+                     const InstDesc* inst, int n_inst, const GeoCell* geo, const double* walls, double* nw,
+                     real* rec, real* force, double* part, double ca, double cc, cudaStream_t s);
+size_t lm_part_doubles(const LargeModel& m, long long cells, int n_inst);
+size_t lm_force_reals(const LargeModel& m, long long cells);  // the force scratch, in reals
+template <typename real>
+cudaError_t lm_deviation(const LargeModel& m, const real* src, real* dst, long long cells, int to_dev, cudaStream_t s);
+template <typename real>
+cudaError_t lm_init(const LargeModel& m, real* F, long long cells, double n, double u0, double u1, double T,
+                    cudaStream_t s);
+template <typename real>
+cudaError_t lm_moments(const LargeModel& m, const real* F, long long cells, double* out, cudaStream_t s);
+
 // Per cell, FP64: n, u0, u1, T, T00, T01, T11, q0, q1 (stride 9).
 template <typename real>
 cudaError_t launch_moments(const real* F, long long cells, int Vp, const ModelArgs& m, double* out, cudaStream_t s,

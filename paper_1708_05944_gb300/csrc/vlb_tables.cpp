@@ -5,7 +5,8 @@
 // which the tests compare against):
 //  * the weight omega(x) = exp(-x^2/2)/sqrt(2 pi) on [0, inf) (half range) or
 //    on the real line (full range) is discretised by composite Gauss-Legendre
-//    panels on [0, L] or [-L, L], L = 40;
+//    panels on [0, L] or [-L, L], L = 40 (48 points per panel of width 0.5: the
+//    projections of K below integrate products of degree ~2Q; 24 points lost K at Q = 200);
 //  * the Stieltjes procedure on that discrete measure gives the three-term
 //    recurrence of the orthonormal family psi_l (h_l for the half range, the
 //    normalised Hermite polynomials for the full range);
@@ -58,7 +59,7 @@ struct Measure {
 
 Measure discretise(bool half) {
   const LD L = 40, width = 0.5L;
-  const int per = 24;
+  const int per = 48;  // per panel of width 0.5: resolves the products of the degree-~2Q polynomials up to Q = 200
   std::vector<LD> gx, gw;
   gauss_legendre(per, &gx, &gw);
   Measure m;
@@ -237,23 +238,32 @@ bool build_axis(int kind, int N, int Q, AxisTables* out, std::string* err) {
     out->p[k] = (double)P[k];
     out->w[k] = (double)Wt[k];
   }
+  // the projections of the expanded node function kp on psi_s do not depend on the output
+  // node k: C[s][kp] = sum_l D[s][l] psi_l(|p_kp|) (likewise Ct), and the jump term's
+  // f(0) = sum_l psi_l(0) psi_l(|p_kp|); then K[k][kp] = w_k sum_s psi_s(|p_k|) (...)
+  std::vector<LD> C(size_t(Q) * nq), Ct(size_t(Q) * nq), f0v(nq, 0);
+  for (int kp = 0; kp < nq; ++kp) {
+    for (int l = 0; l < Q; ++l) f0v[kp] += psi_at0[l] * psi[kp][l];
+    for (int s = 0; s < Q; ++s) {
+      LD cs = 0, cts = 0;
+      for (int l = 0; l < Q; ++l) {
+        cs += D[s * Q + l] * psi[kp][l];
+        cts += Dt[s * Q + l] * psi[kp][l];
+      }
+      C[size_t(s) * nq + kp] = cs;
+      Ct[size_t(s) * nq + kp] = cts;
+    }
+  }
   for (int k = 0; k < nq; ++k) {
     for (int kp = 0; kp < nq; ++kp) {
       LD acc = 0, acct = 0;
       for (int s = 0; s < Q; ++s) {
         LD cs = 0, cts = 0;
         if (sig[k] == sig[kp]) {
-          for (int l = 0; l < Q; ++l) {
-            cs += D[s * Q + l] * psi[kp][l];
-            cts += Dt[s * Q + l] * psi[kp][l];
-          }
-          cs *= sig[k];  // d/dp = sigma d/d|p| on each semi-axis
+          cs = C[size_t(s) * nq + kp] * sig[k];  // d/dp = sigma d/d|p| on each semi-axis
+          cts = Ct[size_t(s) * nq + kp];
         }
-        if (half) {  // jump of f at p = 0, half of delta(p) on each semi-axis
-          LD f0 = 0;
-          for (int l = 0; l < Q; ++l) f0 += psi_at0[l] * psi[kp][l];
-          cs += 0.5L * psi_at0[s] * om0 * sig[kp] * f0;
-        }
+        if (half) cs += 0.5L * psi_at0[s] * om0 * sig[kp] * f0v[kp];  // half of delta(p) on each semi-axis
         acc += psi[k][s] * cs;
         acct += psi[k][s] * cts;
       }

@@ -98,7 +98,7 @@ def test_invalid_arguments_rejected_without_gpu():
         dict(grids=[dict(n_cells=8, r_in=2.0, r_out=1.0)]),
         dict(kn=[0.0]),
         dict(tau=[7]),
-        dict(model="HH(4;40)xH(4;20)"),
+        dict(model="HH(4;200)xH(4;200)"),  # beyond 65536 velocities
     ]
     for b in bad:
         with pytest.raises(vlb.VlbError) as e:
@@ -110,3 +110,30 @@ def test_invalid_arguments_rejected_without_gpu():
 def test_setters_reject_a_null_context_without_gpu():
     assert vlb._lib.vlb_set_knudsen(None, 0.1, vlb.VLB_TAU_AOKI) == vlb.VLB_ERR_INVALID
     assert vlb._lib.vlb_set_channel_reservoirs(None, 2.0, 1.0, 1.0) == vlb.VLB_ERR_INVALID
+
+
+def test_high_order_half_range_tables():
+    """The library's tables for the paper's high-order axis HH(4;200) (Sec. VI.D.2): the rule
+    integrates the half-Gaussian moments (checked up to degree 180, where double still holds
+    p^k), and the force kernels act on
+    populations of omega P (P a polynomial; no jump at p = 0) as the derivative does,
+    d/dp (omega P) = omega (P' - p P), d/dp (p omega P) = omega (P + p P' - p^2 P); in the
+    symmetric scaling sqrt(w_k'/w_k) K their entries stay of order Q^(3/2)."""
+    m = vlb.vlb_parse_model("HH(4;200)xHH(4;10)")
+    p, w, K, Kt = vlb.vlb_axis_tables(m, 0)
+    Q = 200
+    half = p > 0
+    Mk = [0.5, 1.0 / np.sqrt(2.0 * np.pi)]
+    for k in range(2, 181):
+        Mk.append((k - 1) * Mk[k - 2])
+    for k in (0, 1, 2, 7, 50, 120, 180):
+        got = (w[half] * p[half] ** k).sum()
+        assert abs(got / Mk[k] - 1) < 1e-12, k
+    P = np.polynomial.polynomial.Polynomial([0.3, -1.0, 0.5, 0.2, -0.05])
+    f = w * P(p)
+    rows = np.abs(p) < 8.0  # where the polynomial's populations are not negligible in double
+    np.testing.assert_allclose(((K @ f) / w)[rows], (P.deriv()(p) - p * P(p))[rows], rtol=1e-8, atol=1e-8)
+    np.testing.assert_allclose(((Kt @ f) / w)[rows], (P(p) + p * P.deriv()(p) - p * p * P(p))[rows],
+                               rtol=1e-8, atol=1e-8)
+    s = np.sqrt(w)
+    assert np.abs(K * s[None, :] / s[:, None]).max() < 3.0 * Q ** 1.5
