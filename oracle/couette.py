@@ -85,6 +85,16 @@ class CouetteGrid:
         self.dchi = 0.5 * (self.Rf[1:] ** 2 - self.Rf[:-1] ** 2)
         self.Rbar = 0.5 * (self.Rf[1:] + self.Rf[:-1])
         self.n_total, self.cell_begin = n, 0  # a whole grid: both ends are walls
+        # the f~ formulation (Eqs. boltz_couette_cons, boltz_couette_str_cons): the advected
+        # F~ = sqrt(g) f, its flux p e F~ differenced over d eta (equidistant: e = 1, d eta = dR)
+        if A == 0.0:
+            self.sqrtg = self.Rc.copy()
+            self.e_f = np.ones(n + 1)
+            self.deta = (r_out - r_in) / n
+        else:
+            self.sqrtg = A0 * (r_out - r_in) * self.Rc / (A * np.cosh(eta_c) ** 2)
+            self.e_f = A * np.cosh(eta_f) ** 2 / (A0 * (r_out - r_in))
+            self.deta = deta
 
     def slab(self, begin: int, end: int) -> "CouetteGrid":
         """Cells [begin, end) of this grid with their own geometry: a radial slab of a
@@ -95,8 +105,9 @@ class CouetteGrid:
         g = object.__new__(CouetteGrid)
         g.n, g.r_in, g.r_out, g.A, g.delta = end - begin, self.r_in, self.r_out, self.A, self.delta
         g.Rf = self.Rf[begin:end + 1].copy()
-        for name in ("Rc", "wres", "dchi", "Rbar"):
+        for name in ("Rc", "wres", "dchi", "Rbar", "sqrtg"):
             setattr(g, name, getattr(self, name)[begin:end].copy())
+        g.e_f, g.deta = self.e_f[begin:end + 1].copy(), self.deta
         g.n_total, g.cell_begin = self.n, begin
         return g
 
@@ -130,12 +141,15 @@ def relaxation_time(kn, n, T, mode):
 
 class CouetteOracle:
     def __init__(self, model, grid: CouetteGrid, inner: Wall, outer: Wall, kn: float, tau_mode: int = TAU_AOKI,
-                 prandtl=None):
+                 prandtl=None, formulation: str = "chi"):
         self.m = model if isinstance(model, Model) else Model(model)
         self.g = grid
         self.inner, self.outer = inner, outer
         self.kn, self.tau_mode = kn, tau_mode
         self.prandtl = prandtl  # None: BGK (Eq. BGK); else the Shakhov collision with this Pr
+        if formulation not in ("chi", "ftilde"):
+            raise ValueError(formulation)
+        self.formulation = formulation  # "chi" (Eq. boltz_couette_kom) or "ftilde" (Eq. boltz_couette_cons)
         self.last_nw = (float("nan"), float("nan"))
         self.halo = [None, None]  # ghost cells of slab ends (set_halo)
 
@@ -168,27 +182,35 @@ class CouetteOracle:
         Feq = np.stack([f1eq, f2eq])
         tau = relaxation_time(self.kn, n, T, self.tau_mode)
 
-        # 3: ghosts; G[:, s + 2] holds cell s (s = -2 .. N + 3)
+        # 3: ghosts; G[:, s + 2] holds cell s (s = -2 .. N + 3).  In the f~ formulation the
+        # advected quantity is F~ = sqrt(g) f and the walls act on it (Sec. III.E: the sqrt(g)
+        # of the incoming half is absorbed into n_w, the outgoing half is extrapolated in F~)
+        ft = self.formulation == "ftilde"
+        A = g.sqrtg[None, :, None, None] * F if ft else F
         G = np.zeros((2, N + 6) + F.shape[2:])
-        G[:, 3:N + 3] = F
+        G[:, 3:N + 3] = A
         nw_in = nw_out = 0.0
         if g.inner_is_wall:
-            nw_in = self._inner_wall(F, G)
+            nw_in = self._inner_wall(A, G)
         else:  # a slab end inside the grid: the neighbour's cells
             G[:, 0:3] = self.halo[0]
         if g.outer_is_wall:
-            nw_out = self._outer_wall(F, G)
+            nw_out = self._outer_wall(A, G)
         else:
             G[:, N + 3:N + 6] = self.halo[1]
         self.last_nw = (nw_in, nw_out)
 
-        # 4: advection
-        adv = self.advection(G)
+        # 4: advection; f~: p (e_{s+1/2} F~_{s+1/2} - e_{s-1/2} F~_{s-1/2}) / d eta (Eqs. flux_cons_R,
+        # flux_cons_eta), divided by sqrt(g_s) to act on f
+        adv = self.advection_tilde(G) if ft else self.advection(G)
 
-        # 5: inertial force, (1/R)[(p^phi)^2 K^R f - p^R K~^phi f]
+        # 5: inertial force, (1/R)[(p^phi)^2 K^R f - p^R K~^phi f]: R = 2 / (R_{s+1/2} + R_{s-1/2})
+        # in the chi formulation (reading that keeps the rest state exact), the cell centre R_s in
+        # the f~ formulation (as printed)
         dfdpR = np.einsum("ik,dskj->dsij", m.K[0], F)
         dpfdpphi = np.einsum("jk,dsik->dsij", m.Kt[1], F)
-        force = (p1[None, None, None, :] ** 2 * dfdpR - p0[None, None, :, None] * dpfdpphi) / g.Rbar[None, :, None, None]
+        Rf = g.Rc if ft else g.Rbar
+        force = (p1[None, None, None, :] ** 2 * dfdpR - p0[None, None, :, None] * dpfdpphi) / Rf[None, :, None, None]
 
         # 6: BGK, or Shakhov: the target gains (1 - Pr) times the heat-flux term of the cell's q
         coll = -(F - Feq) / tau[None, :, None, None]
@@ -243,6 +265,15 @@ class CouetteOracle:
         RF = self.g.Rf[None, :, None, None] * Fl
         return p0[None, None, :, None] * (RF[:, 1:] - RF[:, :-1]) / self.g.dchi[None, :, None, None]
 
+    def advection_tilde(self, G):
+        """f~ formulation: p (e_{s+1/2} F~_{s+1/2} - e_{s-1/2} F~_{s-1/2}) / (d eta sqrt(g_s)) of the
+        ghosted G = F~ (Eqs. flux_cons_R, flux_cons_eta), the WENO-5 interface values of F~ on
+        the upwind side; divided by sqrt(g_s) it is the advection of f."""
+        p0 = self.m.p[0]
+        Fl = upwind_interfaces(G, (p0 >= 0)[None, None, :, None], axis=1)
+        flux = self.g.e_f[None, :, None, None] * Fl
+        return p0[None, None, :, None] * (flux[:, 1:] - flux[:, :-1]) / (self.g.deta * self.g.sqrtg[None, :, None, None])
+
     def stage(self, k: int, dt: float, F_l, F_prev):
         """One TVD-RK3 stage, Eq. (rk3): k = 1, 2, 3 with F_prev = F_l, F^(1), F^(2)."""
         Lp = self.L(F_prev)
@@ -262,6 +293,11 @@ class CouetteOracle:
     def n_tot(self, F):
         """Particle number per unit height divided by 2 pi: sum_s dchi_s sum_ij f'_{s,ij} (Eq. Ntot_def)."""
         return float((self.g.dchi * F[0].sum(axis=(1, 2))).sum())
+
+    def n_tot_ftilde(self, F):
+        """The particle number the f~ scheme conserves: sum_s d eta sqrt(g_s) sum_ij f'_{s,ij}
+        (its flux difference telescopes over d eta)."""
+        return float((self.g.deta * self.g.sqrtg * F[0].sum(axis=(1, 2))).sum())
 
     def residual(self, mom_now, mom_prev, u_w):
         """L2 norms of Eq. (msites_steady) between two successive checks."""
