@@ -55,6 +55,7 @@ typedef enum {
 typedef enum { VLB_FULL = 0, VLB_HALF = 1 } vlb_quad_kind;           /* H(N;Q) or HH(N;Q) */
 typedef enum { VLB_FP64 = 0, VLB_FP32_BULK = 1 } vlb_precision;
 typedef enum { VLB_BGK = 0, VLB_SHAKHOV = 1 } vlb_collision;
+typedef enum { VLB_CHI = 0, VLB_FTILDE = 1 } vlb_formulation;
 typedef enum {
   VLB_TAU_KN_OVER_NT = 0, /* tau = Kn / (n T), Eq. (hydro_tau) and Eq. (canalie_tau) */
   VLB_TAU_AOKI = 1,       /* tau = sqrt(pi/8) Kn / n, Eq. (tau_aoki) */
@@ -195,6 +196,18 @@ vlb_status vlb_set_channel_reservoirs(vlb_ctx* ctx, double n_in, double n_out, d
  * the stage's output).  Needs expansion orders >= 3 on both axes (VLB_ERR_UNSUPPORTED);
  * Couette and channel contexts; not with vlb_step_static_scratch. */
 vlb_status vlb_set_collision(vlb_ctx* ctx, int collision, double prandtl);
+
+/* Formulation of the advection of a Couette context: VLB_CHI (the default; Eq.
+ * boltz_couette_kom and its stretched form) or VLB_FTILDE, the conservative f~ formulation
+ * the paper compares it with (Sec. VI.B, Eqs. boltz_couette_cons, boltz_couette_str_cons,
+ * flux_cons_R, flux_cons_eta): F~ = sqrt(g) f is reconstructed by WENO-5 and differenced as
+ * p (e_{s+1/2} F~_{s+1/2} - e_{s-1/2} F~_{s-1/2}) / d eta (e = 1, d eta = d R on the
+ * equidistant grid), the walls act on F~ (Sec. III.E; n_w then carries sqrt(g)), and the
+ * force term takes 1 / R at the cell centre.  It conserves sum d eta sqrt(g) sum f' exactly
+ * but does not hold f = const at the walls (the paper's point).  The distribution stays f in
+ * every call.  VLB_FTILDE runs on the multi-kernel stage (any velocity set); not with slabs
+ * or vlb_step_static_scratch.  Errors: VLB_ERR_INVALID, VLB_ERR_UNSUPPORTED (channel). */
+vlb_status vlb_set_formulation(vlb_ctx* ctx, int formulation);
 
 /* Replace the channel's reservoirs by the paper's flow-rate ends (Sec. VII.C.1-2,
  * Eqs. canalie_inlet, canalie_outlet, canalie_inlet_s), half-channel particle flow

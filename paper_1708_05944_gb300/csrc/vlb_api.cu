@@ -407,7 +407,7 @@ vlb_status run_stage(vlb_ctx* c, int k) {
   vlb_status st;
   if (c->kind == 1)
     st = c->prec == VLB_FP64 ? do_chan_stage<double>(c, k, prev, out) : do_chan_stage<float>(c, k, prev, out);
-  else if (c->large)
+  else if (c->large || c->ftilde)
     st = c->prec == VLB_FP64 ? do_large_stage<double>(c, k, prev, out) : do_large_stage<float>(c, k, prev, out);
   else
     st = c->prec == VLB_FP64 ? do_stage<double>(c, k, prev, out) : do_stage<float>(c, k, prev, out);
@@ -556,7 +556,7 @@ void fill_walls(vlb_ctx* c, std::vector<WallEq>& out) {
 }
 
 vlb_status upload_walls(vlb_ctx* c) {
-  if (c->large) {  // per (instance, wall): g0, g1, in_flux, T_w from the axis tables
+  if (c->d_lwall) {  // the multi-kernel path: per (instance, wall) g0, g1, in_flux, T_w from the axis tables
     const int nq0 = c->nq0, nq1 = c->nq1, st = nq0 + nq1 + 2;
     const AxisTables &a0 = c->ax[0], &a1 = c->ax[1];
     std::vector<double> w(size_t(c->n_inst) * 2 * st);
@@ -590,7 +590,7 @@ vlb_status upload_walls(vlb_ctx* c) {
       }
     VLB_CUDA(c, cudaMemcpyAsync(c->d_lwall, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     VLB_CUDA(c, cudaStreamSynchronize(c->stream));
-    return VLB_OK;
+    if (c->large) return VLB_OK;
   }
   std::vector<WallEq> w;
   fill_walls(c, w);
@@ -1139,6 +1139,89 @@ vlb_status vlb_set_channel_reservoirs(vlb_ctx* c, double n_in, double n_out, dou
   vlb_status st = drop_channel_graphs(c);
   if (st != VLB_OK) return st;
   return upload_channel_tables(c);
+}
+
+// The resources of the multi-kernel Couette path (vlb_large.cu) for a context created on the
+// fused path (the f~ formulation runs there for any velocity set).
+static vlb_status ensure_multi_path(vlb_ctx* c) {
+  if (!c->d_lm) {
+    vlb_status st = setup_large(c);
+    if (st != VLB_OK) return st;
+  }
+  const size_t cells = size_t(c->total_cells), es = c->esize;
+  if (!c->d_lrec) VLB_CUDA(c, cudaMalloc(&c->d_lrec, cells * (c->nq0 + c->nq1 + 2) * es));
+  if (!c->d_lforce) VLB_CUDA(c, cudaMalloc(&c->d_lforce, lm_force_reals(c->lm, c->total_cells) * es));
+  if (!c->d_lpart) VLB_CUDA(c, cudaMalloc(&c->d_lpart, lm_part_doubles(c->lm, c->total_cells, c->n_inst) * sizeof(double)));
+  if (!c->d_lwall) {
+    VLB_CUDA(c, cudaMalloc(&c->d_lwall, size_t(c->n_inst) * 2 * (c->nq0 + c->nq1 + 2) * sizeof(double)));
+    vlb_status st = upload_walls(c);
+    if (st != VLB_OK) return st;
+  }
+  c->lm.err = c->d_err;
+  return VLB_OK;
+}
+
+vlb_status vlb_set_formulation(vlb_ctx* c, int formulation) {
+  if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (formulation != 0 && formulation != 1) return fail(c, VLB_ERR_INVALID, "formulation must be VLB_CHI or VLB_FTILDE");
+  if (c->kind != 0) return fail(c, VLB_ERR_UNSUPPORTED, "the f~ formulation is built for Couette contexts");
+  if (formulation == 1 && c->has_halo) return fail(c, VLB_ERR_UNSUPPORTED, "slabs run the chi formulation");
+  VLB_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (int b = 0; b < 3; ++b) {  // captured graphs hold the old launch sequence
+    if (c->graph_exec[b]) cudaGraphExecDestroy(c->graph_exec[b]);
+    c->graph_exec[b] = nullptr;
+    c->graph_variant[b] = -1;
+  }
+  if (formulation == 1) {
+    vlb_status st = ensure_multi_path(c);
+    if (st != VLB_OK) return st;
+    if (!c->d_tgeo) {  // per cell: sqrt(g), e_{s+1/2} / (d eta sqrt(g)), e_{s-1/2} / (...), 1 / R_s; per velocity forceR
+      const size_t N = size_t(c->total_cells);
+      std::vector<double> t(4 * N);
+      for (int i = 0; i < c->n_inst; ++i) {
+        const vlb_couette_grid& g = c->grids[i];
+        const int n = g.n_cells;
+        const double L = g.r_out - g.r_in;
+        for (int s2 = 0; s2 < n; ++s2) {
+          double sg, ep, em, R;
+          if (g.stretch_A == 0.0) {
+            R = g.r_in + (s2 + 0.5) / n * L;
+            sg = R, ep = em = 1.0;
+            const double de = L / n;
+            ep /= de * sg, em /= de * sg;
+          } else {
+            const double A = g.stretch_A, dl = g.stretch_delta, A0 = dl > 1.0 - dl ? dl : 1.0 - dl;
+            const double e_in = -atanh(A * dl / A0), e_out = atanh(A * (1.0 - dl) / A0), de = (e_out - e_in) / n;
+            const double ec = e_in + (s2 + 0.5) * de, em_ = e_in + s2 * de, ep_ = e_in + (s2 + 1) * de;
+            R = g.r_in + L * (dl + A0 / A * tanh(ec));
+            sg = A0 * L * R / (A * cosh(ec) * cosh(ec));
+            ep = A * cosh(ep_) * cosh(ep_) / (A0 * L) / (de * sg);
+            em = A * cosh(em_) * cosh(em_) / (A0 * L) / (de * sg);
+          }
+          const size_t k = size_t(c->inst[i].cell0) + s2;
+          t[k] = sg, t[N + k] = ep, t[2 * N + k] = em, t[3 * N + k] = 1.0 / R;
+        }
+      }
+      // the inertial term of the rest state R_ij = w0_i w1_j through the discrete kernels
+      const AxisTables &a0 = c->ax[0], &a1 = c->ax[1];
+      const int nq0 = c->nq0, nq1 = c->nq1;
+      std::vector<double> k0w(nq0, 0.0), k1w(nq1, 0.0);
+      for (int i = 0; i < nq0; ++i)
+        for (int k = 0; k < nq0; ++k) k0w[i] += a0.K[size_t(i) * nq0 + k] * a0.w[k];
+      for (int j = 0; j < nq1; ++j)
+        for (int l = 0; l < nq1; ++l) k1w[j] += a1.Kt[size_t(j) * nq1 + l] * a1.w[l];
+      for (int i = 0; i < nq0; ++i)
+        for (int j = 0; j < nq1; ++j)
+          t.push_back(a1.p[j] * a1.p[j] * k0w[i] * a1.w[j] - a0.p[i] * a0.w[i] * k1w[j]);
+      VLB_CUDA(c, cudaMalloc(&c->d_tgeo, t.size() * sizeof(double)));
+      VLB_CUDA(c, cudaMemcpy(c->d_tgeo, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+      c->lm.sqrtg = c->d_tgeo, c->lm.advp = c->d_tgeo + N, c->lm.advm = c->d_tgeo + 2 * N, c->lm.inv_r = c->d_tgeo + 3 * N;
+      c->lm.forceR = c->d_tgeo + 4 * N;
+    }
+  }
+  c->lm.ftilde = formulation;
+  c->ftilde = formulation == 1;
+  return VLB_OK;
 }
 
 vlb_status vlb_set_collision(vlb_ctx* c, int collision, double prandtl) {
@@ -1772,6 +1855,7 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_lrec);
   cudaFree(c->d_lforce);
   cudaFree(c->d_lpart);
+  cudaFree(c->d_tgeo);
   delete c;
 }
 

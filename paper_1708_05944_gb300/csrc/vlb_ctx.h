@@ -69,6 +69,8 @@ struct vlb_ctx {
   void* d_lrec = nullptr;     // per cell equilibrium record
   void* d_lforce = nullptr;   // per cell force term
   double* d_lpart = nullptr;  // per cell and wall chunk sums
+  bool ftilde = false;        // the f~ formulation (on the multi-kernel path)
+  double* d_tgeo = nullptr;   // its per-cell geometry: sqrt(g), advp, advm, 1/R_s
   double prandtl = 1.0;
   bool have_prev = false;
   size_t tile_cap = 0;

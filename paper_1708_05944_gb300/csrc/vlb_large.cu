@@ -20,6 +20,10 @@
 //             the RK3 combine, both fields as a pair.
 // Every sum is taken in a fixed order, so results do not depend on scheduling.
 //
+// The same kernels run the f~ formulation (LargeModel::ftilde, Sec. VI.B): the stencils and
+// the wall construction act on F~ = sqrt(g) f, whose flux difference e_{s+1/2} F~_{s+1/2} -
+// e_{s-1/2} F~_{s-1/2} over d eta sqrt(g_s) is the advection of f; the force takes 1 / R_s.
+//
 // The arithmetic is that of the fused kernel: deviations D = F - R stored, the same
 // epsilon-free pair WENO, the same wall construction.  In single precision the WENO
 // indicator scale 1 / (w_i w_j) is capped at 1e30: tail populations below ~1e-38 are
@@ -156,7 +160,13 @@ __global__ void __launch_bounds__(256) lm_wallpart_kernel(const LargeModel m, co
     if (v >= m.V) break;
     const int i = v / m.nq1, j = v - i * m.nq1;
     if (!(sgn * m.p0[i] < 0.0)) continue;
-    const P F0 = p_load(F0r + 2 * v), F1 = p_load(F1r + 2 * v), F2 = p_load(F2r + 2 * v);
+    P F0 = p_load(F0r + 2 * v), F1 = p_load(F1r + 2 * v), F2 = p_load(F2r + 2 * v);
+    if (m.ftilde) {  // the walls act on F~ = sqrt(g) (D + R)
+      const real R = real(m.w0[i] * m.w1[j]);
+      F0 = p_mul(p_add(F0, p_set(R)), p_set(real(m.sqrtg[edge])));
+      F1 = p_mul(p_add(F1, p_set(R)), p_set(real(m.sqrtg[edge + dir])));
+      F2 = p_mul(p_add(F2, p_set(R)), p_set(real(m.sqrtg[edge + 2 * dir])));
+    }
     const P G0 = p_fma(F1, p_set(real(-3)), p_fma(F0, p_set(real(3)), F2));
     const P G1 = p_fma(F1, p_set(real(-8)), p_fma(F0, p_set(real(6)), p_mul(F2, p_set(real(3)))));
     num += double(weno5p<real>(F2, F1, F0, G0, G1, weno_scale<real>(m.iw0[i] * m.iw1[j])).x) * m.p0[i];
@@ -252,7 +262,7 @@ __global__ void __launch_bounds__(FT) lm_force_kernel(const LargeModel m, const 
     }
     __syncthreads();
   }
-  const real irb = real(geo[c].inv_rbar);
+  const real irb = real(m.ftilde ? m.inv_r[c] : geo[c].inv_rbar);
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const int i = i0 + ti + 16 * q;
@@ -287,29 +297,35 @@ __global__ void lm_update_kernel(const LargeModel m, const real* Fprev, const re
     const int s = int(c - d.cell0), n = d.n_cells;
     const double Rd = m.w0[i] * m.w1[j];
     auto wall_density = [&](int wall) {  // n_w of Eq. (nw) from the chunk sums, in a fixed order
-      double t = wall == 0 ? m.ref_flux_neg : m.ref_flux_pos;
+      double t = m.ftilde ? 0.0 : (wall == 0 ? m.ref_flux_neg : m.ref_flux_pos);  // f~: no R split
       for (int p = 0; p < NP; ++p) t += wpart[(size_t(ii) * 2 + wall) * NP + p];
       return -t / walls[(size_t(ii) * 2 + wall) * (m.nq0 + m.nq1 + 2) + m.nq0 + m.nq1];
+    };
+    // the advected value of a cell: D (chi), or F~ = sqrt(g) (D + R) (f~)
+    auto cell = [&](long long cc) -> P {
+      const P x = p_load(Fprev + cc * 2 * m.Vp + 2 * v);
+      if (!m.ftilde) return x;
+      return p_mul(p_add(x, p_set(real(Rd))), p_set(real(m.sqrtg[cc])));
     };
     auto ghost = [&](int wall, int dist) -> P {  // ghost at distance 1..3 past a wall (Eq. weno_populate)
       const double sgn = wall == 0 ? 1.0 : -1.0;
       if (sgn * m.p0[i] < 0.0) {  // outgoing: quadratic extrapolation (Eq. extrapol)
         const long long e0 = d.cell0 + (wall == 0 ? 0 : n - 1);
         const int dir = wall == 0 ? 1 : -1;
-        const P F0 = p_load(Fprev + e0 * 2 * m.Vp + 2 * v), F1 = p_load(Fprev + (e0 + dir) * 2 * m.Vp + 2 * v);
-        const P F2 = p_load(Fprev + (e0 + 2 * dir) * 2 * m.Vp + 2 * v);
+        const P F0 = cell(e0), F1 = cell(e0 + dir), F2 = cell(e0 + 2 * dir);
         if (dist == 1) return p_fma(F1, p_set(real(-3)), p_fma(F0, p_set(real(3)), F2));
         return p_fma(F1, p_set(real(-8)), p_fma(F0, p_set(real(6)), p_mul(F2, p_set(real(3)))));
       }
       const double* wt = walls + (size_t(ii) * 2 + wall) * (m.nq0 + m.nq1 + 2);
       const double e = wall_density(wall) * wt[i] * wt[m.nq0 + j];
-      return p_make(real(e - Rd), real(e * wt[m.nq0 + m.nq1 + 1] - Rd));
+      const double r = m.ftilde ? 0.0 : Rd;  // f~ ghosts are F~ itself
+      return p_make(real(e - r), real(e * wt[m.nq0 + m.nq1 + 1] - r));
     };
-    auto at = [&](int k) -> P {  // populations of cell s + k, ghosts past the walls
+    auto at = [&](int k) -> P {  // advected values of cell s + k, ghosts past the walls
       const int t = s + k;
       if (t < 0) return ghost(0, -t);
       if (t >= n) return ghost(1, t - n + 1);
-      return p_load(Fprev + (c + k) * 2 * m.Vp + 2 * v);
+      return cell(c + k);
     };
     if (v == 0 && (s == 0 || s == n - 1))  // the wall densities of the stage, for vlb_wall_density
       for (int wall = 0; wall < 2; ++wall)
@@ -318,20 +334,22 @@ __global__ void lm_update_kernel(const LargeModel m, const real* Fprev, const re
           nw[ii * 2 + wall] = nwv;
           if (!isfinite(nwv)) atomicOr(m.err, ERR_NONFINITE);
         }
-    const P Fm3 = at(-3), Fm2 = at(-2), Fm1 = at(-1), F0 = at(0), Fp1 = at(1), Fp2 = at(2), Fp3 = at(3);
+    const P Fm3 = at(-3), Fm2 = at(-2), Fm1 = at(-1), S0 = at(0), Fp1 = at(1), Fp2 = at(2), Fp3 = at(3);
+    const P F0 = p_load(Fprev + c * 2 * m.Vp + 2 * v);  // the cell's own D
     const real sc = weno_scale<real>(m.iw0[i] * m.iw1[j]);
     const real pr = real(m.p0[i]);
     P fm, fp;
     if (pr >= real(0)) {
-      fm = weno5p<real>(Fm3, Fm2, Fm1, F0, Fp1, sc);
-      fp = weno5p<real>(Fm2, Fm1, F0, Fp1, Fp2, sc);
+      fm = weno5p<real>(Fm3, Fm2, Fm1, S0, Fp1, sc);
+      fp = weno5p<real>(Fm2, Fm1, S0, Fp1, Fp2, sc);
     } else {
-      fm = weno5p<real>(Fp2, Fp1, F0, Fm1, Fm2, sc);
-      fp = weno5p<real>(Fp3, Fp2, Fp1, F0, Fm1, sc);
+      fm = weno5p<real>(Fp2, Fp1, S0, Fm1, Fm2, sc);
+      fp = weno5p<real>(Fp3, Fp2, Fp1, S0, Fm1, sc);
     }
     const GeoCell g = geo[c];
-    // -adv = -p^R (cp F_{s+1/2} - cm F_{s-1/2})
-    const P nadv = p_mul(p_sub(p_mul(fp, p_set(real(g.cp))), p_mul(fm, p_set(real(g.cm)))), p_set(-pr));
+    // -adv = -p^R (cp F_{s+1/2} - cm F_{s-1/2}); f~: the factors e_{s+-1/2} / (d eta sqrt(g_s))
+    const real cp = real(m.ftilde ? m.advp[c] : g.cp), cm = real(m.ftilde ? m.advm[c] : g.cm);
+    const P nadv = p_mul(p_sub(p_mul(fp, p_set(cp)), p_mul(fm, p_set(cm))), p_set(-pr));
     // the azimuthal part of the inertial term, +inv_rbar p0_i sum_l Kt1[j][l] D[c][i][l]
     const real* Drow = Fprev + c * 2 * m.Vp + size_t(i) * 2 * m.nq1;
     P e = p_set(real(0));
@@ -343,7 +361,8 @@ __global__ void lm_update_kernel(const LargeModel m, const real* Fprev, const re
     }
     P fr = p_load(force + c * 2 * m.Vp + 2 * v);
     for (int h = 1; h < KS; ++h) fr = p_add(fr, p_load(force + (size_t(h) * cells + c) * 2 * m.Vp + 2 * v));
-    const P frc = p_fma(e, p_set(real(g.inv_rbar) * pr), fr);
+    P frc = p_fma(e, p_set(real(m.ftilde ? m.inv_r[c] : g.inv_rbar) * pr), fr);
+    if (m.ftilde) frc = p_add(frc, p_set(real(-m.inv_r[c] * m.forceR[v])));  // f~ advects R too
     const real* rc = rec + c * stride;
     const real geq = rc[i] * rc[m.nq0 + j];
     const real R = real(Rd);

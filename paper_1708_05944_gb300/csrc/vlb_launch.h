@@ -124,6 +124,14 @@ struct LargeModel {
   const float *K0f, *Kt1f, *s0f, *is0f, *s1f, *is1f;
   double ref_flux_neg, ref_flux_pos;  // outgoing particle flux of R at the inner / outer wall
   unsigned* err;
+  // the f~ formulation (Eqs. boltz_couette_cons, boltz_couette_str_cons) when ftilde != 0: per
+  // cell sqrt(g), the advection factors e_{s+1/2} / (d eta sqrt(g_s)) and e_{s-1/2} / (...),
+  // and 1 / R_s of the force term
+  int ftilde;
+  const double *sqrtg, *advp, *advm, *inv_r;
+  // per velocity (p1_j^2 (K0 R)_ij - p0_i (Kt1 R)_ij), R_ij = w0_i w1_j: the inertial term of the
+  // rest state, which the chi form drops with the advection of R (they cancel) and f~ must keep
+  const double* forceR;
 };
 
 // One RK3 stage of the large-set Couette path (see vlb_large.cu): walls holds per

@@ -73,7 +73,8 @@ extern "C" vlb_status vlb_step_static_scratch(vlb_ctx* c, const void* f_in, void
   if (c->kind != 0) return static_fail(c, VLB_ERR_UNSUPPORTED, "static-scratch stepping covers Couette contexts only");
   if (c->has_halo) return static_fail(c, VLB_ERR_STATE, "a slab steps one stage at a time (vlb_stage)");
   if (c->collision != 0) return static_fail(c, VLB_ERR_UNSUPPORTED, "static-scratch stepping runs the BGK stage only");
-  if (c->large) return static_fail(c, VLB_ERR_UNSUPPORTED, "static-scratch stepping covers up to 32 nodes per axis");
+  if (c->large || c->ftilde)
+    return static_fail(c, VLB_ERR_UNSUPPORTED, "static-scratch stepping covers the chi formulation up to 32 nodes per axis");
   if (!f_in || !f_out || f_in == f_out) return static_fail(c, VLB_ERR_INVALID, "need distinct input and output buffers");
   if (nsteps < 1 || !(dt > 0.0) || !std::isfinite(dt))
     return static_fail(c, VLB_ERR_INVALID, "need a finite dt > 0 and nsteps >= 1");

@@ -19,6 +19,7 @@ VLB_OK, VLB_ERR_INVALID, VLB_ERR_UNSUPPORTED, VLB_ERR_CUDA, VLB_ERR_NONFINITE, V
 VLB_FULL, VLB_HALF = 0, 1
 VLB_FP64, VLB_FP32_BULK = 0, 1
 VLB_BGK, VLB_SHAKHOV = 0, 1
+VLB_CHI, VLB_FTILDE = 0, 1
 VLB_TAU_KN_OVER_NT, VLB_TAU_AOKI, VLB_TAU_KN_OVER_N = 0, 1, 2
 
 _STATUS = {VLB_ERR_INVALID: "INVALID", VLB_ERR_UNSUPPORTED: "UNSUPPORTED", VLB_ERR_CUDA: "CUDA",
@@ -69,6 +70,7 @@ EXPORTS = {
     "vlb_set_channel_reservoirs": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
     "vlb_set_channel_flow_rate": (C.c_int, [C.c_void_p, C.c_double]),
     "vlb_set_collision": (C.c_int, [C.c_void_p, C.c_int, C.c_double]),
+    "vlb_set_formulation": (C.c_int, [C.c_void_p, C.c_int]),
     "vlb_channel_postprocess": (C.c_int, [C.c_void_p] + [C.c_void_p] * 5),
     "vlb_set_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "vlb_read_f": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
@@ -299,6 +301,10 @@ class Couette(_Context):
         self.h = h
         self.n_inst = n
         self._sizes()
+
+    def set_formulation(self, formulation):
+        """vlb_set_formulation: VLB_CHI or VLB_FTILDE."""
+        _check(_lib.vlb_set_formulation(self.h, formulation), self.h)
 
     def set_walls(self, inner, outer):
         n = self.n_inst
