@@ -310,3 +310,78 @@ def postprocess(oracle: ChannelOracle, F):
     lw, l1, l2 = g.lf[-1], g.lc[-1], g.lc[-2]
     pw = ((lw - l2) * P[-1] - (lw - l1) * P[-2]) / (l1 - l2)
     return dict(ux=ux, uy=uy, psi=psi, omega=omega, pw=pw)
+
+
+class ClbChannelOracle(ChannelOracle):
+    """The Cartesian-split channel of Sec. VII.G (Eq. canalie_coord_beq_cons): momenta are the
+    Cartesian (p^x, p^y) on the model's axes 0 and 1 (both usually half range), there is no
+    force term, and the advection is
+
+      L[f] = -[V^l_{s+1/2} F_{s+1/2} - V^l_{s-1/2} F_{s-1/2}] / d lambda_s
+             -[V^x_{p+1/2} F_{p+1/2} - V^x_{p-1/2} F_{p-1/2}] / d chi^xi_p - (f - f_eq)/tau,
+
+    V^lambda = (p^x - lambda phi' p^y) / (1 + phi) at (lambda_{s+1/2}, xi_p) and
+    V^xi = (1 + phi) p^y at xi_{p+1/2}: each lambda interface of a column upwinds by the sign of
+    a combination of p^x and p^y, so the wall's incoming half-plane V^lambda < 0 depends on
+    the column (Eq. canalie_coord_nw).  Boundaries as in ChannelOracle: the centreline mirrors
+    p^x, the wall is diffuse at rest and T_0 (outgoing half extrapolated, n_w per column),
+    the reservoirs at the ends fill the populations entering (p^y > 0 at the inlet, < 0 at the
+    outlet) with f_eq(n_res, (0, u^y of the adjacent cell), T_0)."""
+
+    def __init__(self, model, grid: ChannelGrid, kn, n_in=2.0, n_out=1.0, T0=1.0):
+        super().__init__(model, grid, kn, n_in=n_in, n_out=n_out, T0=T0)
+        g = grid
+        phc, dpc = phi(g.xc, g.re_c), dphi(g.xc, g.re_c)
+        self.Vl_a = 1.0 / (1.0 + phc)                     # V^l = a (p^x - lambda_f phi' p^y)
+        self.Vl_b = g.lf[:, None] * dpc[None, :]          # lambda_{s+1/2} phi'(xi_p), (nl+1, nx)
+        self.Vx = 1.0 + phi(g.xf, g.re_c)                 # V^xi / p^y at xi_{p+1/2}, (nx+1,)
+
+    def L(self, F):
+        m, g = self.m, self.g
+        nl, nx = g.nl, g.nx
+        px, py = m.p[0], m.p[1]
+        PX, PY = px[:, None], py[None, :]
+        n, ux, uy, T = self.moments(F)
+        Feq = self.feq_cells(n, ux, uy, T)
+        tau = self.kn / (n * T)
+
+        # ---- lambda: V^l (nl+1, nx, nq0, nq1) at the row interfaces of each column
+        Vl = self.Vl_a[None, :, None, None] * (PX[None, None] - self.Vl_b[:, :, None, None] * PY[None, None])
+        Gl = np.zeros((2, nl + 6, nx) + F.shape[3:])
+        Gl[:, 3:nl + 3] = F
+        for k in (1, 2, 3):  # centreline: specular in p^x
+            Gl[:, 3 - k] = F[:, k - 1][:, :, self.ibar, :]
+        out = Vl[nl] > 0  # (nx, nq0, nq1): leaving through the wall
+        FN, FN1, FN2 = F[:, nl - 1], F[:, nl - 2], F[:, nl - 3]
+        e1 = 3 * FN - 3 * FN1 + FN2
+        e2 = 6 * FN - 8 * FN1 + 3 * FN2
+        flux_w = np.where(out[None], weno5(FN2, FN1, FN, e1, e2), 0.0)  # the WENO value of the leaving half
+        weq = self.feq_cells(np.ones(1), np.zeros(1), np.zeros(1), np.full(1, self.T0))[:, 0]  # (2, nq0, nq1)
+        num = (flux_w[0] * Vl[nl]).sum(axis=(1, 2))
+        den = np.where(~out, weq[0][None] * Vl[nl], 0.0).sum(axis=(1, 2))
+        nw = -num / den  # Eq. (canalie_coord_nw), per column
+        self.last_nw = nw
+        for k, e in ((1, e1), (2, e2), (3, e2)):
+            inc = nw[None, :, None, None] * weq[:, None]
+            Gl[:, nl + 2 + k] = np.where(out[None], e, inc)
+        Fl_ = upwind_interfaces(Gl, (Vl >= 0)[None], axis=1)
+        fluxl = Vl[None] * Fl_
+        adv = (fluxl[:, 1:] - fluxl[:, :-1]) / g.dl[None, :, None, None, None]
+
+        # ---- xi: V^xi = (1 + phi) p^y at the column interfaces
+        Vx = self.Vx[None, :, None, None] * PY[None, None] * np.ones((nl, 1, len(px), 1))  # (nl, nx+1, nq0, nq1)
+        Hx = np.zeros((2, nl, nx + 6) + F.shape[3:])
+        Hx[:, :, 3:nx + 3] = F
+        f_in = self.feq_cells(np.full(nl, self.n_in), np.zeros(nl), uy[:, 0], np.full(nl, self.T0))
+        f_out = self.feq_cells(np.full(nl, self.n_out), np.zeros(nl), uy[:, -1], np.full(nl, self.T0))
+        into_in, into_out = Vx[:, 0] > 0, Vx[:, nx] < 0
+        for k in (0, 1, 2):
+            Hx[:, :, k] = np.where(into_in[None], f_in, F[:, :, 0])
+            Hx[:, :, nx + 3 + k] = np.where(into_out[None], f_out, F[:, :, nx - 1])
+        Fx = upwind_interfaces(Hx, (Vx >= 0)[None], axis=2)
+        fluxx = Vx[None] * Fx
+        adv = adv + (fluxx[:, :, 1:] - fluxx[:, :, :-1]) / g.dchi[None, None, :, None, None]
+        self.last_boundary_flux = dict(
+            inlet=(g.dl[:, None, None] * fluxx[0, :, 0]).sum(), outlet=(g.dl[:, None, None] * fluxx[0, :, nx]).sum(),
+            wall=(g.dchi[:, None, None] * fluxl[0, nl]).sum(), centre=(g.dchi[:, None, None] * fluxl[0, 0]).sum())
+        return -adv - (F - Feq) / tau[None, :, :, None, None]
