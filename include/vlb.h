@@ -55,7 +55,7 @@ typedef enum {
 typedef enum { VLB_FULL = 0, VLB_HALF = 1 } vlb_quad_kind;           /* H(N;Q) or HH(N;Q) */
 typedef enum { VLB_FP64 = 0, VLB_FP32_BULK = 1 } vlb_precision;
 typedef enum { VLB_BGK = 0, VLB_SHAKHOV = 1 } vlb_collision;
-typedef enum { VLB_CHI = 0, VLB_FTILDE = 1 } vlb_formulation;
+typedef enum { VLB_CHI = 0, VLB_FTILDE = 1, VLB_CARTESIAN = 2 } vlb_formulation;
 typedef enum {
   VLB_TAU_KN_OVER_NT = 0, /* tau = Kn / (n T), Eq. (hydro_tau) and Eq. (canalie_tau) */
   VLB_TAU_AOKI = 1,       /* tau = sqrt(pi/8) Kn / n, Eq. (tau_aoki) */
@@ -148,8 +148,10 @@ vlb_status vlb_create_couette(const vlb_model* model, vlb_precision prec, int n_
  * see the adjacent cell (zeroth-order extrapolation); vlb_set_channel_flow_rate
  * replaces the reservoirs by the paper's flow-rate ends.  Cell (s, p) is cell
  * index p * n_lambda + s of the distribution layout.  Axis 0 must be half
- * range; kernels exist for 16 x 12 and 8 x 4 nodes (VLB_ERR_UNSUPPORTED
- * otherwise); n_lambda >= 3, n_xi >= 4 and a multiple of 4.  Starts at f_eq(1, 0, T0). */
+ * range; the vielbein stage kernels exist for 16 x 12 and 8 x 4 nodes, other
+ * velocity sets (up to 32 nodes per axis) run only the Cartesian-split
+ * formulation (vlb_set_formulation; stepping before it is VLB_ERR_UNSUPPORTED);
+ * n_lambda >= 3, n_xi >= 4 and a multiple of 4.  Starts at f_eq(1, 0, T0). */
 vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const vlb_channel_grid* grid, double kn,
                               double n_in, double n_out, double T0, void* cuda_stream, vlb_ctx** out);
 
@@ -206,7 +208,16 @@ vlb_status vlb_set_collision(vlb_ctx* ctx, int collision, double prandtl);
  * force term takes 1 / R at the cell centre.  It conserves sum d eta sqrt(g) sum f' exactly
  * but does not hold f = const at the walls (the paper's point).  The distribution stays f in
  * every call.  VLB_FTILDE runs on the multi-kernel stage (any velocity set); not with slabs
- * or vlb_step_static_scratch.  Errors: VLB_ERR_INVALID, VLB_ERR_UNSUPPORTED (channel). */
+ * or vlb_step_static_scratch.
+ * Channel contexts: VLB_CHI (the vielbein stage of vlb_create_channel) or VLB_CARTESIAN, the
+ * Cartesian-split channel the paper compares it with (Sec. VII.G, Eqs. canalie_coord_beq_cons,
+ * canalie_coord_nw): the model's axes are read as the Cartesian momenta (p^x, p^y) (the
+ * distribution and the moments of every call are then in that frame), there is no force
+ * term, V^lambda = (p^x - lambda phi' p^y) / (1 + phi), V^xi = (1 + phi) p^y, the wall's
+ * incoming half-plane V^lambda < 0 is taken per column, and the fluxes are of F itself (the
+ * rest state is not an exact steady state of this scheme); reservoir ends only, no
+ * post-processing (VLB_ERR_STATE).  Errors: VLB_ERR_INVALID, VLB_ERR_UNSUPPORTED (f~ on a
+ * channel, Cartesian on a Couette context), VLB_ERR_STATE. */
 vlb_status vlb_set_formulation(vlb_ctx* ctx, int formulation);
 
 /* Replace the channel's reservoirs by the paper's flow-rate ends (Sec. VII.C.1-2,

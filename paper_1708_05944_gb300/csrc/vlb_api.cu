@@ -250,6 +250,20 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
 }
 
 template <typename real>
+vlb_status do_clb_stage(vlb_ctx* c, int k, int prev, int out) {
+  const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cc[3] = {1.0, 0.25, 2.0 / 3.0};
+  ClbGeom g = c->clbg;
+  g.kn = c->cdesc.kn, g.n_in = c->cdesc.n_in, g.n_out = c->cdesc.n_out, g.T0 = c->cdesc.T0;
+  cudaError_t e = clb_stage<real>(c->lm, g, static_cast<const real*>(c->F[prev]), static_cast<const real*>(c->F[c->cur]),
+                                  static_cast<real*>(c->F[out]), static_cast<real*>(c->d_clbrec),
+                                  static_cast<real*>(c->d_clbres), c->d_nw, c->inst[0].dt, ca[k - 1], cc[k - 1],
+                                  c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "Cartesian-split stage launch");
+  c->launches += 3;
+  return VLB_OK;
+}
+
+template <typename real>
 vlb_status do_large_stage(vlb_ctx* c, int k, int prev, int out) {
   const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cc[3] = {1.0, 0.25, 2.0 / 3.0};
   cudaError_t e = lm_stage<real>(c->lm, static_cast<const real*>(c->F[prev]), static_cast<const real*>(c->F[c->cur]),
@@ -405,7 +419,12 @@ vlb_status run_stage(vlb_ctx* c, int k) {
     prev = b2, out = b1;
   }
   vlb_status st;
-  if (c->kind == 1)
+  if (c->kind == 1 && c->clb)
+    st = c->prec == VLB_FP64 ? do_clb_stage<double>(c, k, prev, out) : do_clb_stage<float>(c, k, prev, out);
+  else if (c->kind == 1 && c->n_cvariants == 0)
+    return fail(c, VLB_ERR_UNSUPPORTED, "no vielbein channel kernel for this velocity set (16x12 or 8x4 nodes): "
+                                        "it runs the Cartesian split (vlb_set_formulation)");
+  else if (c->kind == 1)
     st = c->prec == VLB_FP64 ? do_chan_stage<double>(c, k, prev, out) : do_chan_stage<float>(c, k, prev, out);
   else if (c->large || c->ftilde)
     st = c->prec == VLB_FP64 ? do_large_stage<double>(c, k, prev, out) : do_large_stage<float>(c, k, prev, out);
@@ -950,9 +969,9 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
       if (prec == VLB_FP32_BULK && !all[i].tc && !kp_ok) continue;
       c->cvariants[c->n_cvariants++] = all[i];
     }
-    if (c->n_cvariants == 0)
-      return fail(nullptr, VLB_ERR_UNSUPPORTED,
-                  "no channel kernel for this velocity set and n_xi (16x12 or 8x4 nodes, n_xi a multiple of 4)");
+    // no vielbein kernel for this velocity set: the context can still run the Cartesian split
+    if (c->n_cvariants == 0 && (nq0 > MAXQ || nq1 > MAXQ))
+      return fail(nullptr, VLB_ERR_UNSUPPORTED, "more than 32 nodes on an axis of a channel velocity set");
   }
   ModelArgs& m = c->margs;
   m.nq0 = nq0, m.nq1 = nq1, m.N0 = model->N[0], m.N1 = model->N[1];
@@ -1014,6 +1033,7 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
   c->cmap.nl = nl;
   c->cmap.nx = nx;
   c->chan_lc = lc;
+  c->chan_grid = *grid;
   c->chan_phi_end[0] = phi(xf[0]);
   c->chan_phi_end[1] = phi(xf[nx]);
   ChanDesc& cd = c->cdesc;
@@ -1054,7 +1074,7 @@ vlb_status vlb_create_channel(const vlb_model* model, vlb_precision prec, const 
     VLB_CUDA(cp, cudaMemcpy(c->d_cpost, pg.data(), pg.size() * sizeof(double), cudaMemcpyHostToDevice));
   }
   VLB_CUDA(cp, cudaStreamSynchronize(c->stream));
-  {
+  if (c->n_cvariants > 0) {
     vlb_status ts = upload_channel_tables(cp);
     if (ts != VLB_OK) return ts;
   }
@@ -1126,6 +1146,8 @@ vlb_status vlb_set_knudsen(vlb_ctx* c, double kn, int tau_mode) {
   return VLB_OK;
 }
 
+static vlb_status upload_clb_weq(vlb_ctx* c);
+
 vlb_status vlb_set_channel_reservoirs(vlb_ctx* c, double n_in, double n_out, double T0) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
   if (c->kind != 1) return fail(c, VLB_ERR_UNSUPPORTED, "reservoirs belong to channel contexts");
@@ -1138,7 +1160,11 @@ vlb_status vlb_set_channel_reservoirs(vlb_ctx* c, double n_in, double n_out, dou
   c->cdesc.flow = 0;
   vlb_status st = drop_channel_graphs(c);
   if (st != VLB_OK) return st;
-  return upload_channel_tables(c);
+  if (c->clb) {
+    st = upload_clb_weq(c);
+    if (st != VLB_OK) return st;
+  }
+  return c->n_cvariants > 0 ? upload_channel_tables(c) : VLB_OK;
 }
 
 // The resources of the multi-kernel Couette path (vlb_large.cu) for a context created on the
@@ -1161,10 +1187,95 @@ static vlb_status ensure_multi_path(vlb_ctx* c) {
   return VLB_OK;
 }
 
+// the wall equilibrium factors f_eq(1, 0, T0) of the Cartesian-split channel (host tables)
+static vlb_status upload_clb_weq(vlb_ctx* c) {
+  const AxisTables &a0 = c->ax[0], &a1 = c->ax[1];
+  std::vector<double> w(size_t(c->nq0) + c->nq1);
+  double mp[MAXN];
+  host_moment_vector(a0.kind, a0.N, 0.0, c->cdesc.T0, mp);
+  for (int k = 0; k < c->nq0; ++k) {
+    double g = 0;
+    for (int s2 = 0; s2 <= a0.N; ++s2) g += a0.eqtab[size_t(k) * (a0.N + 1) + s2] * mp[s2];
+    w[k] = g;
+  }
+  host_moment_vector(a1.kind, a1.N, 0.0, c->cdesc.T0, mp);
+  for (int k = 0; k < c->nq1; ++k) {
+    double g = 0;
+    for (int s2 = 0; s2 <= a1.N; ++s2) g += a1.eqtab[size_t(k) * (a1.N + 1) + s2] * mp[s2];
+    w[c->nq0 + k] = g;
+  }
+  VLB_CUDA(c, cudaMemcpy(const_cast<double*>(c->clbg.weq), w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  return VLB_OK;
+}
+
+// Channel contexts: VLB_CHI (the vielbein stage) or VLB_CARTESIAN (Sec. VII.G)
+static vlb_status set_channel_formulation(vlb_ctx* c, int formulation) {
+  if (formulation == 1) return fail(c, VLB_ERR_UNSUPPORTED, "the f~ formulation is built for Couette contexts");
+  if (formulation == 0 && c->n_cvariants == 0)
+    return fail(c, VLB_ERR_UNSUPPORTED, "no vielbein channel kernel for this velocity set (16x12 or 8x4 nodes)");
+  if (formulation == 2 && c->cdesc.flow) return fail(c, VLB_ERR_STATE, "the Cartesian split runs with reservoir ends");
+  vlb_status st = drop_channel_graphs(c);
+  if (st != VLB_OK) return st;
+  if (formulation == 2 && !c->d_clbgeo) {
+    if (!c->d_lm) {
+      st = setup_large(c);
+      if (st != VLB_OK) return st;
+    }
+    c->lm.err = c->d_err;
+    const vlb_channel_grid& gr = c->chan_grid;
+    const int nl = gr.n_lambda, nx = gr.n_xi;
+    const double A = gr.stretch_A, ea = atanh(A), re = gr.re_c, L = gr.xi_out - gr.xi_in;
+    auto phi = [&](double x) { return 0.5 * (tanh(2.0) - tanh(2.0 - 30.0 * x / re)); };
+    auto dphi = [&](double x) { const double ch = cosh(2.0 - 30.0 * x / re); return 0.5 * (30.0 / re) / (ch * ch); };
+    auto chi = [&](double x) { return (1.0 + tanh(2.0) / 2.0) * x + re / 60.0 * log(cosh(2.0 - 30.0 * x / re) / cosh(2.0)); };
+    std::vector<double> d;
+    const size_t o_va = d.size();
+    for (int p = 0; p < nx; ++p) d.push_back(1.0 / (1.0 + phi(gr.xi_in + L * (p + 0.5) / nx)));
+    const size_t o_dph = d.size();
+    for (int p = 0; p < nx; ++p) d.push_back(dphi(gr.xi_in + L * (p + 0.5) / nx));
+    const size_t o_lf = d.size();
+    for (int s2 = 0; s2 <= nl; ++s2) d.push_back(s2 == nl ? 1.0 : tanh(double(s2) / nl * ea) / A);
+    const size_t o_vx = d.size();
+    for (int p = 0; p <= nx; ++p) d.push_back(1.0 + phi(gr.xi_in + L * p / nx));
+    const size_t o_idl = d.size();
+    for (int s2 = 0; s2 < nl; ++s2) {
+      const double lo = tanh(double(s2) / nl * ea) / A, hi = s2 + 1 == nl ? 1.0 : tanh(double(s2 + 1) / nl * ea) / A;
+      d.push_back(1.0 / (hi - lo));
+    }
+    const size_t o_idx = d.size();
+    for (int p = 0; p < nx; ++p) d.push_back(1.0 / (chi(gr.xi_in + L * (p + 1) / nx) - chi(gr.xi_in + L * p / nx)));
+    const size_t o_weq = d.size();
+    d.resize(d.size() + c->nq0 + c->nq1, 0.0);
+    std::vector<int> ib(c->nq0);
+    for (int k = 0; k < c->nq0; ++k) ib[k] = refl(c->margs.kind0, c->nq0, k);
+    const size_t dbytes = d.size() * sizeof(double);
+    VLB_CUDA(c, cudaMalloc(&c->d_clbgeo, dbytes + ib.size() * sizeof(int)));
+    VLB_CUDA(c, cudaMemcpy(c->d_clbgeo, d.data(), dbytes, cudaMemcpyHostToDevice));
+    VLB_CUDA(c, cudaMemcpy(static_cast<char*>(c->d_clbgeo) + dbytes, ib.data(), ib.size() * sizeof(int),
+                           cudaMemcpyHostToDevice));
+    const double* D = static_cast<const double*>(c->d_clbgeo);
+    ClbGeom& g = c->clbg;
+    g.nl = nl, g.nx = nx;
+    g.va = D + o_va, g.dph = D + o_dph, g.lf = D + o_lf, g.vx = D + o_vx, g.idl = D + o_idl, g.idx = D + o_idx;
+    g.weq = D + o_weq;
+    g.ibar = reinterpret_cast<const int*>(static_cast<const char*>(c->d_clbgeo) + dbytes);
+    const size_t cells = size_t(nl) * nx;
+    VLB_CUDA(c, cudaMalloc(&c->d_clbrec, cells * (c->nq0 + c->nq1 + 2) * c->esize));
+    VLB_CUDA(c, cudaMalloc(&c->d_clbres, size_t(nl) * 2 * (c->nq0 + c->nq1) * c->esize));
+  }
+  if (formulation == 2) {
+    st = upload_clb_weq(c);
+    if (st != VLB_OK) return st;
+  }
+  c->clb = formulation == 2;
+  return VLB_OK;
+}
+
 vlb_status vlb_set_formulation(vlb_ctx* c, int formulation) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
-  if (formulation != 0 && formulation != 1) return fail(c, VLB_ERR_INVALID, "formulation must be VLB_CHI or VLB_FTILDE");
-  if (c->kind != 0) return fail(c, VLB_ERR_UNSUPPORTED, "the f~ formulation is built for Couette contexts");
+  if (formulation < 0 || formulation > 2) return fail(c, VLB_ERR_INVALID, "unknown formulation");
+  if (c->kind == 1) return set_channel_formulation(c, formulation);
+  if (formulation == 2) return fail(c, VLB_ERR_UNSUPPORTED, "the Cartesian split is a channel formulation");
   if (formulation == 1 && c->has_halo) return fail(c, VLB_ERR_UNSUPPORTED, "slabs run the chi formulation");
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   for (int b = 0; b < 3; ++b) {  // captured graphs hold the old launch sequence
@@ -1247,6 +1358,7 @@ vlb_status vlb_set_channel_flow_rate(vlb_ctx* c, double q0) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
   if (c->kind != 1) return fail(c, VLB_ERR_UNSUPPORTED, "flow-rate ends belong to channel contexts");
   if (!(q0 >= 0.0) || !std::isfinite(q0)) return fail(c, VLB_ERR_INVALID, "the flow rate must be finite and >= 0");
+  if (c->clb) return fail(c, VLB_ERR_STATE, "the Cartesian split runs with reservoir ends");
   const int nl = c->cdesc.nl;
   // Eqs. (canalie_inlet, canalie_outlet), H = 2: Q_s = 3 Q0 (1 - 4 lambda_s^2 / H^2) / (H (1 + phi))
   std::vector<double> q(size_t(4) * nl);
@@ -1275,6 +1387,7 @@ vlb_status vlb_set_channel_flow_rate(vlb_ctx* c, double q0) {
 vlb_status vlb_channel_postprocess(vlb_ctx* c, double* ux, double* uy, double* psi, double* omega, double* pw) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
   if (c->kind != 1) return fail(c, VLB_ERR_UNSUPPORTED, "post-processing belongs to channel contexts");
+  if (c->clb) return fail(c, VLB_ERR_STATE, "post-processing reads triad components (the vielbein formulation)");
   const int nl = c->cdesc.nl, nx = c->cdesc.nx;
   const size_t cells = size_t(nl) * nx, npsi = size_t(nl + 1) * nx;
   const size_t total = 3 * cells + npsi + nx;
@@ -1677,6 +1790,7 @@ int vlb_variants(const vlb_ctx* c, int* tc, int* nt, int* persistent, int max) {
 
 vlb_status vlb_set_variant(vlb_ctx* c, int v) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
+  if (c->kind == 1 && c->n_cvariants == 0 && v == 0) return VLB_OK;  // a Cartesian-split-only channel
   if (v < 0 || v >= (c->kind == 1 ? c->n_cvariants : c->n_variants)) return fail(c, VLB_ERR_INVALID, "no such launch shape");
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->variant = v;
@@ -1700,7 +1814,7 @@ vlb_status vlb_autotune(vlb_ctx* c, double dt, int reps, int* chosen, double* be
   int best = 0;
   float best_t = 1e30f;
   const int keep_last = c->last;
-  const int nvar = c->kind == 1 ? c->n_cvariants : c->n_variants;
+  const int nvar = c->kind == 1 ? std::max(1, c->n_cvariants) : c->n_variants;
   for (int v = 0; v < nvar; ++v) {
     st = vlb_set_variant(c, v);
     if (st != VLB_OK) break;
@@ -1856,6 +1970,9 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_lforce);
   cudaFree(c->d_lpart);
   cudaFree(c->d_tgeo);
+  cudaFree(c->d_clbgeo);
+  cudaFree(c->d_clbrec);
+  cudaFree(c->d_clbres);
   delete c;
 }
 

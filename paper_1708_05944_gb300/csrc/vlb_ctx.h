@@ -90,6 +90,12 @@ struct vlb_ctx {
   double* d_cpost = nullptr;      // post-processing geometry: lambda_c, lambda_f, phi_c, phi'_c
   double* d_post = nullptr;       // post-processing outputs (allocated on first use)
   double chan_dxi = 0.0;
+  vlb_channel_grid chan_grid{};   // the channel's grid parameters
+  bool clb = false;               // the Cartesian-split formulation (Sec. VII.G) is on
+  ClbGeom clbg{};                 // its geometry (device arrays in d_clbgeo)
+  void* d_clbgeo = nullptr;
+  void* d_clbrec = nullptr;       // per cell equilibrium record
+  void* d_clbres = nullptr;       // per row and end: reservoir factors
   // CUDA graph of three RK3 steps (nine stage launches), replayed by vlb_step_graph
   // three-step graphs, one per starting buffer F[cur] (captured on first use)
   cudaGraphExec_t graph_exec[3] = {nullptr, nullptr, nullptr};

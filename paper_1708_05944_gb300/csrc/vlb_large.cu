@@ -376,6 +376,158 @@ __global__ void lm_update_kernel(const LargeModel m, const real* Fprev, const re
   }
 }
 
+// ---------------------------------------------------------------- Cartesian-split channel (Sec. VII.G)
+// Eq. (canalie_coord_beq_cons): no force term; the lambda flux upwinds by the sign of
+// V^lambda = (p^x - lambda phi' p^y) / (1 + phi), a combination of both momenta that changes
+// along the wall, so the wall's incoming half-plane is per column (Eq. canalie_coord_nw).
+// The fluxes are taken of F = D + R: without a force term the rest state's advection does not
+// cancel discretely, so R is kept.
+
+// per cell: moments, tau = Kn / (n T), the equilibrium record; the end columns also the
+// reservoir factors of f_eq(1, (0, u^y), T0) (u^y of that cell)
+template <typename real>
+__global__ void __launch_bounds__(kCellThreads) clb_cell_kernel(const LargeModel m, const ClbGeom g, const real* F,
+                                                                real* rec, real* res) {
+  extern __shared__ double sh[];
+  double* g0 = sh;
+  double* g1 = g0 + m.nq0;
+  double* mv = g1 + m.nq1;
+  double* red = mv + 4 * MAXN;
+  const int stride = m.nq0 + m.nq1 + 2;
+  const long long cells = (long long)g.nl * g.nx;
+  for (long long c = blockIdx.x; c < cells; c += gridDim.x) {
+    const real* f = F + c * 2 * m.Vp;
+    double sn = 0, s0 = 0, s1 = 0, se = 0;
+    for (int v = threadIdx.x; v < m.V; v += blockDim.x) {
+      const int i = v / m.nq1, j = v - i * m.nq1;
+      const double r = m.w0[i] * m.w1[j];
+      const double f1 = double(f[2 * v]) + r, f2 = double(f[2 * v + 1]) + r;
+      const double a = m.p0[i], b = m.p1[j];
+      sn += f1;
+      s0 += a * f1;
+      s1 += b * f1;
+      se += (a * a + b * b) * f1 + f2;
+    }
+    const double n = block_sum(sn, red), u0 = block_sum(s0, red) / n, u1 = block_sum(s1, red) / n;
+    const double T = (block_sum(se, red) / n - u0 * u0 - u1 * u1) / 3.0;
+    eq_factors(m, n, u0, u1, T, g0, g1, mv, red);
+    real* o = rec + c * stride;
+    for (int k = threadIdx.x; k < m.nq0 + m.nq1; k += blockDim.x) o[k] = real(k < m.nq0 ? g0[k] : g1[k - m.nq0]);
+    if (threadIdx.x == 0) {
+      o[m.nq0 + m.nq1] = real(T);
+      o[m.nq0 + m.nq1 + 1] = real(n * T / g.kn);
+      if (!(n > 0.0) || !(T > 0.0)) atomicOr(m.err, ERR_NONFINITE);
+    }
+    __syncthreads();
+    const int s_ = int(c / g.nx), p = int(c - (long long)s_ * g.nx);
+    for (int end = 0; end < 2; ++end) {  // uniform across the block
+      if (p != (end == 0 ? 0 : g.nx - 1)) continue;
+      eq_factors(m, 1.0, 0.0, u1, g.T0, g0, g1, mv, red);
+      real* q = res + (size_t(s_) * 2 + end) * (m.nq0 + m.nq1);
+      for (int k = threadIdx.x; k < m.nq0 + m.nq1; k += blockDim.x) q[k] = real(k < m.nq0 ? g0[k] : g1[k - m.nq0]);
+      __syncthreads();
+    }
+  }
+}
+
+// per column: n_w of Eq. (canalie_coord_nw) from the leaving half (V^lambda > 0 at the wall)
+template <typename real>
+__global__ void __launch_bounds__(256) clb_wall_kernel(const LargeModel m, const ClbGeom g, const real* F, double* nw) {
+  __shared__ double red[33];
+  using P = pair_t<real>;
+  const int p = blockIdx.x, nl = g.nl, nx = g.nx;
+  const real* FN = F + ((long long)(nl - 1) * nx + p) * 2 * m.Vp;
+  const real* FN1 = F + ((long long)(nl - 2) * nx + p) * 2 * m.Vp;
+  const real* FN2 = F + ((long long)(nl - 3) * nx + p) * 2 * m.Vp;
+  const double lw = g.lf[nl];
+  double num = 0.0, den = 0.0;
+  for (int v = threadIdx.x; v < m.V; v += blockDim.x) {
+    const int i = v / m.nq1, j = v - i * m.nq1;
+    const double V = g.va[p] * (m.p0[i] - lw * g.dph[p] * m.p1[j]);
+    if (V > 0.0) {
+      const P a = p_load(FN2 + 2 * v), b = p_load(FN1 + 2 * v), c0 = p_load(FN + 2 * v);
+      const P e1 = p_fma(b, p_set(real(-3)), p_fma(c0, p_set(real(3)), a));
+      const P e2 = p_fma(b, p_set(real(-8)), p_fma(c0, p_set(real(6)), p_mul(a, p_set(real(3)))));
+      const double fx = double(weno5p<real>(a, b, c0, e1, e2, weno_scale<real>(m.iw0[i] * m.iw1[j])).x);
+      num += (fx + m.w0[i] * m.w1[j]) * V;  // the flux of F = D + R
+    } else {
+      den += g.weq[i] * g.weq[m.nq0 + j] * V;
+    }
+  }
+  num = block_sum(num, red);
+  den = block_sum(den, red);
+  if (threadIdx.x == 0) {
+    const double nwv = -num / den;
+    nw[p] = nwv;
+    if (!isfinite(nwv)) atomicOr(m.err, ERR_NONFINITE);
+  }
+}
+
+template <typename real>
+__global__ void clb_update_kernel(const LargeModel m, const ClbGeom g, const real* Fprev, const real* Fl, real* Fout,
+                                  const real* rec, const real* res, const double* nw, double dt, double ca, double cc) {
+  using P = pair_t<real>;
+  const int nl = g.nl, nx = g.nx;
+  const long long total = (long long)nl * nx * m.V;
+  const int stride = m.nq0 + m.nq1 + 2;
+  for (long long x = blockIdx.x * (long long)blockDim.x + threadIdx.x; x < total; x += (long long)gridDim.x * blockDim.x) {
+    const long long c = x / m.V;
+    const int v = int(x - c * m.V);
+    const int i = v / m.nq1, j = v - i * m.nq1;
+    const int s = int(c / nx), p = int(c - (long long)s * nx);
+    const double Rd = m.w0[i] * m.w1[j];
+    const real R = real(Rd);
+    auto D = [&](int r, int q, int vv) -> P { return p_load(Fprev + ((long long)r * nx + q) * 2 * m.Vp + 2 * vv); };
+    // lambda column p: rows below 0 mirror p^x (specular centreline), rows past nl are wall ghosts
+    const double Vw = g.va[p] * (m.p0[i] - g.lf[nl] * g.dph[p] * m.p1[j]);
+    auto lam = [&](int r) -> P {
+      if (r >= 0 && r < nl) return D(r, p, v);
+      if (r < 0) return D(-r - 1, p, g.ibar[i] * m.nq1 + j);
+      const int dist = r - nl + 1;
+      if (Vw > 0.0) {  // leaving through the wall: quadratic extrapolation (Eq. extrapol)
+        const P a = D(nl - 3, p, v), b = D(nl - 2, p, v), c0 = D(nl - 1, p, v);
+        if (dist == 1) return p_fma(b, p_set(real(-3)), p_fma(c0, p_set(real(3)), a));
+        return p_fma(b, p_set(real(-8)), p_fma(c0, p_set(real(6)), p_mul(a, p_set(real(3)))));
+      }
+      const double e = nw[p] * g.weq[i] * g.weq[m.nq0 + j];
+      return p_make(real(e - Rd), real(e * g.T0 - Rd));
+    };
+    // xi row s: columns past the ends are the reservoirs for the entering populations
+    auto xi = [&](int q) -> P {
+      if (q >= 0 && q < nx) return D(s, q, v);
+      const int end = q < 0 ? 0 : 1;
+      const bool entering = end == 0 ? (m.p1[j] > 0.0) : (m.p1[j] < 0.0);
+      if (!entering) return D(s, end == 0 ? 0 : nx - 1, v);
+      const real* rr = res + (size_t(s) * 2 + end) * (m.nq0 + m.nq1);
+      const double e = (end == 0 ? g.n_in : g.n_out) * double(rr[i]) * double(rr[m.nq0 + j]);
+      return p_make(real(e - Rd), real(e * g.T0 - Rd));
+    };
+    const real sc = weno_scale<real>(m.iw0[i] * m.iw1[j]);
+    const P L3 = lam(s - 3), L2 = lam(s - 2), L1 = lam(s - 1), C0 = lam(s), U1 = lam(s + 1), U2 = lam(s + 2), U3 = lam(s + 3);
+    const double Vm = g.va[p] * (m.p0[i] - g.lf[s] * g.dph[p] * m.p1[j]);
+    const double Vp = g.va[p] * (m.p0[i] - g.lf[s + 1] * g.dph[p] * m.p1[j]);
+    const P fm = Vm >= 0.0 ? weno5p<real>(L3, L2, L1, C0, U1, sc) : weno5p<real>(U2, U1, C0, L1, L2, sc);
+    const P fp = Vp >= 0.0 ? weno5p<real>(L2, L1, C0, U1, U2, sc) : weno5p<real>(U3, U2, U1, C0, L1, sc);
+    const P X3 = xi(p - 3), X2 = xi(p - 2), X1 = xi(p - 1), X4 = xi(p + 1), X5 = xi(p + 2), X6 = xi(p + 3);
+    const bool up = m.p1[j] >= 0.0;
+    const P xm = up ? weno5p<real>(X3, X2, X1, C0, X4, sc) : weno5p<real>(X5, X4, C0, X1, X2, sc);
+    const P xp = up ? weno5p<real>(X2, X1, C0, X4, X5, sc) : weno5p<real>(X6, X5, X4, C0, X1, sc);
+    const P Rp = p_set(R);
+    // -[V F]_{s-1/2}^{s+1/2} / d lambda - [V F]_{p-1/2}^{p+1/2} / d chi, F = D + R
+    P nadv = p_mul(p_sub(p_mul(p_add(fp, Rp), p_set(real(Vp))), p_mul(p_add(fm, Rp), p_set(real(Vm)))),
+                   p_set(real(-g.idl[s])));
+    const real vxm = real(g.vx[p] * m.p1[j]), vxp = real(g.vx[p + 1] * m.p1[j]);
+    nadv = p_fma(p_sub(p_mul(p_add(xp, Rp), p_set(vxp)), p_mul(p_add(xm, Rp), p_set(vxm))), p_set(real(-g.idx[p])), nadv);
+    const real* rc = rec + c * stride;
+    const real geq = rc[i] * rc[m.nq0 + j];
+    const P deq = p_make(geq - R, geq * rc[m.nq0 + m.nq1] - R);
+    const P Lv = p_fma(p_sub(C0, deq), p_set(-rc[m.nq0 + m.nq1 + 1]), nadv);
+    P o = p_fma(Lv, p_set(real(cc * dt)), C0);
+    if (ca != 0.0) o = p_fma(p_sub(p_load(Fl + c * 2 * m.Vp + 2 * v), C0), p_set(real(ca)), o);
+    p_store(Fout + c * 2 * m.Vp + 2 * v, o);
+  }
+}
+
 // ---------------------------------------------------------------- layout, initial state, moments
 template <typename real>
 __global__ void lm_deviation_kernel(const LargeModel m, const real* src, real* dst, long long cells, int to_dev) {
@@ -495,6 +647,17 @@ cudaError_t lm_stage(const LargeModel& m, const real* Fprev, const real* Fl, rea
   return cudaGetLastError();
 }
 
+template <typename real>
+cudaError_t clb_stage(const LargeModel& m, const ClbGeom& g, const real* Fprev, const real* Fl, real* Fout, real* rec,
+                      real* res, double* nw, double dt, double ca, double cc, cudaStream_t s) {
+  const long long cells = (long long)g.nl * g.nx;
+  const int cg = int(cells < 152 * 8 ? cells : 152 * 8);
+  clb_cell_kernel<real><<<cg, kCellThreads, cell_smem(m), s>>>(m, g, Fprev, rec, res);
+  clb_wall_kernel<real><<<g.nx, 256, 0, s>>>(m, g, Fprev, nw);
+  clb_update_kernel<real><<<grid_for(cells * m.V, 256), 256, 0, s>>>(m, g, Fprev, Fl, Fout, rec, res, nw, dt, ca, cc);
+  return cudaGetLastError();
+}
+
 size_t lm_force_reals(const LargeModel& m, long long cells) { return size_t(KS) * cells * 2 * m.Vp; }
 
 size_t lm_part_doubles(const LargeModel& m, long long cells, int n_inst) {
@@ -527,6 +690,8 @@ cudaError_t lm_moments(const LargeModel& m, const real* F, long long cells, doub
                                       const InstDesc*, int, const GeoCell*, const double*, double*, real*, real*,    \
                                       double*, double, double, cudaStream_t);                                        \
   template cudaError_t lm_deviation<real>(const LargeModel&, const real*, real*, long long, int, cudaStream_t);    \
+  template cudaError_t clb_stage<real>(const LargeModel&, const ClbGeom&, const real*, const real*, real*, real*,  \
+                                       real*, double*, double, double, double, cudaStream_t);                        \
   template cudaError_t lm_init<real>(const LargeModel&, real*, long long, double, double, double, double,          \
                                      cudaStream_t);                                                                  \
   template cudaError_t lm_moments<real>(const LargeModel&, const real*, long long, double*, cudaStream_t);

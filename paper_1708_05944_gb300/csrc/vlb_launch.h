@@ -143,6 +143,25 @@ cudaError_t lm_stage(const LargeModel& m, const real* Fprev, const real* Fl, rea
                      real* rec, real* force, double* part, double ca, double cc, cudaStream_t s);
 size_t lm_part_doubles(const LargeModel& m, long long cells, int n_inst);
 size_t lm_force_reals(const LargeModel& m, long long cells);  // the force scratch, in reals
+// The Cartesian-split channel (Sec. VII.G): geometry of the advection velocities
+// V^lambda = va_p (p^x - lambda_{s+1/2} dph_p p^y) and V^xi = vx_{p+1/2} p^y, device arrays.
+struct ClbGeom {
+  int nl, nx;
+  const double *va, *dph;  // [nx] 1 / (1 + phi(xi_p)), phi'(xi_p)
+  const double* lf;        // [nl + 1] lambda_{s+1/2}
+  const double* vx;        // [nx + 1] 1 + phi(xi_{p+1/2})
+  const double *idl, *idx;  // [nl] 1 / d lambda_s, [nx] 1 / d chi_p
+  const double* weq;       // [nq0 + nq1] factors of f_eq(1, 0, T0) (the wall)
+  double kn, n_in, n_out, T0;
+  const int* ibar;         // [nq0] the p^x mirror of each axis-0 node
+};
+
+// One RK3 stage of the Cartesian-split channel: rec (cells x (nq0 + nq1 + 2)) and res
+// (nl x 2 x (nq0 + nq1)) are scratch; nw gets n_w per column.  Device cell s * nx + p.
+template <typename real>
+cudaError_t clb_stage(const LargeModel& m, const ClbGeom& g, const real* Fprev, const real* Fl, real* Fout, real* rec,
+                      real* res, double* nw, double dt, double ca, double cc, cudaStream_t s);
+
 template <typename real>
 cudaError_t lm_deviation(const LargeModel& m, const real* src, real* dst, long long cells, int to_dev, cudaStream_t s);
 template <typename real>

@@ -19,7 +19,7 @@ VLB_OK, VLB_ERR_INVALID, VLB_ERR_UNSUPPORTED, VLB_ERR_CUDA, VLB_ERR_NONFINITE, V
 VLB_FULL, VLB_HALF = 0, 1
 VLB_FP64, VLB_FP32_BULK = 0, 1
 VLB_BGK, VLB_SHAKHOV = 0, 1
-VLB_CHI, VLB_FTILDE = 0, 1
+VLB_CHI, VLB_FTILDE, VLB_CARTESIAN = 0, 1, 2
 VLB_TAU_KN_OVER_NT, VLB_TAU_AOKI, VLB_TAU_KN_OVER_N = 0, 1, 2
 
 _STATUS = {VLB_ERR_INVALID: "INVALID", VLB_ERR_UNSUPPORTED: "UNSUPPORTED", VLB_ERR_CUDA: "CUDA",
@@ -373,6 +373,10 @@ class Channel(_Context):
 
     def set_reservoirs(self, n_in, n_out, T0=1.0):
         _check(_lib.vlb_set_channel_reservoirs(self.h, n_in, n_out, T0), self.h)
+
+    def set_formulation(self, formulation):
+        """vlb_set_formulation: VLB_CHI (vielbein) or VLB_CARTESIAN (the Cartesian-split channel)."""
+        _check(_lib.vlb_set_formulation(self.h, formulation), self.h)
 
     def set_flow_rate(self, q0):
         """vlb_set_channel_flow_rate: the paper's parabolic flow-rate ends with half-channel rate q0."""
