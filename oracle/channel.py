@@ -328,8 +328,8 @@ class ClbChannelOracle(ChannelOracle):
     the reservoirs at the ends fill the populations entering (p^y > 0 at the inlet, < 0 at the
     outlet) with f_eq(n_res, (0, u^y of the adjacent cell), T_0)."""
 
-    def __init__(self, model, grid: ChannelGrid, kn, n_in=2.0, n_out=1.0, T0=1.0):
-        super().__init__(model, grid, kn, n_in=n_in, n_out=n_out, T0=T0)
+    def __init__(self, model, grid: ChannelGrid, kn, n_in=2.0, n_out=1.0, T0=1.0, prandtl=None):
+        super().__init__(model, grid, kn, n_in=n_in, n_out=n_out, T0=T0, prandtl=prandtl)
         g = grid
         phc, dpc = phi(g.xc, g.re_c), dphi(g.xc, g.re_c)
         self.Vl_a = 1.0 / (1.0 + phc)                     # V^l = a (p^x - lambda_f phi' p^y)
@@ -384,4 +384,9 @@ class ClbChannelOracle(ChannelOracle):
         self.last_boundary_flux = dict(
             inlet=(g.dl[:, None, None] * fluxx[0, :, 0]).sum(), outlet=(g.dl[:, None, None] * fluxx[0, :, nx]).sum(),
             wall=(g.dchi[:, None, None] * fluxl[0, nl]).sum(), centre=(g.dchi[:, None, None] * fluxl[0, 0]).sum())
-        return -adv - (F - Feq) / tau[None, :, :, None, None]
+        coll = -(F - Feq) / tau[None, :, :, None, None]
+        if self.prandtl is not None:  # Shakhov, as in the vielbein channel: (1 - Pr) G of the cell's own q
+            from .couette import shakhov_term
+            flat = F.reshape((2, nl * nx) + F.shape[3:])
+            coll = coll + (1.0 - self.prandtl) * shakhov_term(m, flat).reshape(F.shape) / tau[None, :, :, None, None]
+        return -adv + coll

@@ -196,6 +196,35 @@ def test_clb_particle_balance_and_rest_state():
     assert res[-1] > 1e-5 and res[-1] < res[0] and res[1] / res[2] > 2.5, res
 
 
+def test_clb_shakhov_term_relaxes_each_cell_s_heat_flux():
+    """The Shakhov collision on the Cartesian split: what it adds to L at each cell carries no
+    particles, momentum or energy, and its heat-flux moment is (1 - Pr) q / tau with the cell's
+    own q and the channel's tau = Kn / (n T)."""
+    from oracle.channel import ClbChannelOracle
+    spec, g = "HH(3;4)xHH(3;4)", ChannelGrid(6, 8)
+    a = ClbChannelOracle(spec, g, 0.05)
+    b = ClbChannelOracle(spec, g, 0.05, prandtl=2.0 / 3.0)
+    F = a.initial_state()
+    F = F * perturbation(F.shape, seed=8, amplitude=0.05)
+    dL = b.L(F) - a.L(F)
+    m = a.m
+    flat = F.reshape((2, -1) + F.shape[3:])
+    dflat = dL.reshape((2, -1) + F.shape[3:])
+    mom = m.full_moments(flat)
+    tau = 0.05 / (mom["n"] * mom["T"])
+    x0 = m.p[0][None, :, None] - mom["u0"][:, None, None]
+    x1 = m.p[1][None, None, :] - mom["u1"][:, None, None]
+    scale = np.abs(dflat).max()
+    assert scale > 1e-4
+    assert np.abs(dflat[0].sum(axis=(1, 2))).max() < 1e-12 * scale
+    assert np.abs((x0 * dflat[0]).sum(axis=(1, 2))).max() < 1e-12 * scale
+    assert np.abs((x1 * dflat[0]).sum(axis=(1, 2))).max() < 1e-12 * scale
+    e = 0.5 * (x0 ** 2 + x1 ** 2) * dflat[0] + 0.5 * dflat[1]
+    assert np.abs(e.sum(axis=(1, 2))).max() < 1e-11 * scale
+    dq = np.stack([(e * x0).sum(axis=(1, 2)), (e * x1).sum(axis=(1, 2))])
+    np.testing.assert_allclose(dq, (1.0 / 3.0) * np.stack([mom["q0"], mom["q1"]]) / tau, rtol=1e-9, atol=1e-12)
+
+
 def test_clb_equals_the_vielbein_channel_where_the_wall_is_straight():
     """Far downstream (xi in [30, 40], phi' < 1e-6) the triad of Eq. (canalie_phat) is the
     Cartesian one and the connection coefficients vanish, so the Cartesian-split and the
