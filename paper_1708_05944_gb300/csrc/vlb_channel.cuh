@@ -21,10 +21,16 @@
 //   - combines advection, force, BGK relaxation and the RK3 weights and
 //     stores the cell's updated populations straight to global memory.
 //
+// The march is software-pipelined: step s combines row s-1 while it builds row
+// s's interface values and force (double-buffered by row parity), so all warp
+// roles work between the one barrier a step takes, and each column warp waits
+// for its own bulk copies.
+//
 // Boundaries: the centreline mirror (Sec. VII.C.3) fills the window at the
 // bottom of the march, the diffuse wall (Sec. VII.C.4) at its top with n_w per
-// column from the zero-mass-flux balance, and the inlet/outlet reservoirs fill
-// the xi-halo cells of the first and last strip.
+// column from the zero-mass-flux balance, and the inlet/outlet reservoirs give
+// the xi-halo values past the first and last strip, evaluated by each thread
+// whose stencil reaches them.
 //
 // Distribution buffers hold the deviation D = F - R from the rest state
 // (ModelArgs), with (f', f'') interleaved per velocity: a cell row is
@@ -121,9 +127,11 @@ struct ChanArgs {
 };
 
 // Shared-memory carve-up of a CTA, identical on host and device.  The ring holds
-// rows s .. s+3+PD of the strip, each with its xi-halo (TP + 6 cells): row s for
-// the xi reconstruction and the force, s+1 for the reservoir ghosts, s+3 for the
-// window, and PD rows in flight (bulk copies issued PD steps ahead).
+// rows s-1 .. s+3+PD of the strip, each with its xi-halo (TP + 6 cells): row s-1
+// for the geometry of the combine, row s for the xi reconstruction and the force,
+// s+3 for the window, and PD rows in flight (bulk copies issued PD steps ahead).
+// The xi interface values and the force results are double-buffered by row parity:
+// step s writes row s's while it combines row s-1 from the other half.
 template <typename real, int Q0, int Q1, int TP>
 struct ChanSmem {
   using S = ChanShape<Q0, Q1>;
@@ -132,10 +140,12 @@ struct ChanSmem {
   static constexpr int NSYNC = (TP + 1) * S::V;  // TP column groups and one extra group, in step
   static constexpr int NT = NSYNC + 64;          // and two equilibrium warps running ahead of them
   static constexpr int NPR = 4;                  // moment-partial ring (rows r .. r+3)
-  static constexpr int PD = F32 ? 2 : 1;      // prefetch distance in rows
-  static constexpr int NRING = 4 + PD;        // ring rows
+  // prefetch distance in rows: double precision copies each row in the step that needs it,
+  // which keeps its larger ring within an SM's shared memory
+  static constexpr int PD = F32 ? 2 : 0;
+  static constexpr int NRING = 5 + PD;        // ring rows
   static constexpr int NB = PD + 1;           // mbarriers of the step groups (one more for the prologue)
-  static constexpr int NEQ = 4;               // equilibrium records of rows s .. s+3
+  static constexpr int NEQ = 8;               // equilibrium records (rows s-1 .. s+3 in use), a power of 2
   static constexpr int RC = TP + 6;           // cells of a ring row
   static constexpr size_t al(size_t x) { return (x + 15) & ~size_t(15); }
   static constexpr size_t rowb = size_t(S::ROW) * sizeof(real);
@@ -146,8 +156,8 @@ struct ChanSmem {
   static constexpr size_t ring_off = al(tab_off + sizeof(Tab));
   static constexpr size_t geo_off = ring_off + size_t(NRING) * RC * rowb;
   static constexpr size_t xif_off = al(geo_off + size_t(NRING) * TP * sizeof(ChanCell<real>));
-  static constexpr size_t lbl_off = xif_off + size_t(TP + 1) * S::V * 2 * sizeof(real);
-  static constexpr size_t lbuf_rows = F32 ? TP : 0;  // tensor-core force results (single precision only)
+  static constexpr size_t lbl_off = xif_off + size_t(2) * (TP + 1) * S::V * 2 * sizeof(real);
+  static constexpr size_t lbuf_rows = F32 ? 2 * TP : 0;  // force results of two rows (single precision only)
   static constexpr size_t lbx_off = lbl_off + lbuf_rows * rowb;
   static constexpr size_t eq_off = lbx_off + lbuf_rows * rowb;
   static constexpr size_t res_off = al(eq_off + size_t(NEQ) * TP * S::EQW * sizeof(real));
@@ -162,7 +172,8 @@ struct ChanSmem {
   static_assert(ring_off % 16 == 0 && geo_off % 16 == 0, "bulk destinations are 16-byte aligned");
   static_assert(xif_off % 16 == 0 && lbl_off % 16 == 0 && lbx_off % 16 == 0, "pair arrays are aligned");
   static_assert(bar_off + NBAR * sizeof(uint64_t) <= tab_off, "mbarriers fit before the tables");
-  static_assert(TP >= 3, "the inlet/outlet ghosts of a strip come from its own first/last column");
+  static_assert((NEQ & (NEQ - 1)) == 0, "record slots by mask");
+  static_assert(TP >= 3, "only the end strips' stencils reach past the inlet / outlet");
   static_assert(NT <= 1024, "one thread per (column, velocity) and an extra group");
 };
 
@@ -493,8 +504,6 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
     W1 = p_load(base + dcell(sA - 2, p0 + c) * ROW);
     W2 = p_load(base + dcell(sA - 1, p0 + c) * ROW);
   }
-  P flr = p_set(real(0));  // F_l of the cell being finished, prefetched one row ahead
-  if (is_main && need_fl) flr = p_load(a.Fl + dcell(sA, p0 + c) * ROW + 2 * v);
   {
     bool ok = true;
     if (tid == 0) ok = mbar_wait(bar + NB, 0, a.max_polls);
@@ -605,7 +614,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
     else if (lane == Q0 + Q1) val = T;
     else if (lane == Q0 + Q1 + 1) val = nn * T * a.ikn;  // 1/tau, tau = Kn / (n T) (Eq. canalie_tau)
     else if (lane == Q0 + Q1 + 2) val = u1;
-    if (lane < EQW) eqr[((r & 3) * TP + cc) * EQW + lane] = val;
+    if (lane < EQW) eqr[((r & (L::NEQ - 1)) * TP + cc) * EQW + lane] = val;
     __syncwarp();
   };
 
@@ -631,19 +640,19 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       const real* m = mv + ((tb.kind1 == 1 && tb.p1[lane] < real(0)) ? 1 : 0) * MAXN;
       real g = real(0);
       for (int s = 0; s <= tb.N1; ++s) g += tb.tab1[lane * MAXN + s] * m[s];
-      resr[((r & 3) * 2 + end) * Q1 + lane] = g;
+      resr[((r & (L::NEQ - 1)) * 2 + end) * Q1 + lane] = g;
     }
     __syncwarp();
     if (a.flow) {
       // n_s sum_{entering} V f'_eq(1, (0, Q_s), T0) + sum_{leaving} V f'_adjacent = (1 + phi) Q_s,
-      // V = b p^xi - c p^lambda of the end interface (the decision of reservoir_ghosts);
+      // V = b p^xi - c p^lambda of the end interface (the decision of end_ghost);
       // the adjacent cell is row r of the ring (its slot is refilled only after this row's
       // record is waited for), FP64 sums as for n_w
       const int k = r % NRING;
       const ChanCell<real>& gk = gring[k * TP + cc];
       const real bb = end == 0 ? gk.bm : gk.bp, cq = end == 0 ? gk.cm : gk.cp;
       const real* Fa = krow(k, cc);
-      const real* gr = resr + ((r & 3) * 2 + end) * Q1;
+      const real* gr = resr + ((r & (L::NEQ - 1)) * 2 + end) * Q1;
       double lv = 0.0, en = 0.0;
       for (int vv = lane; vv < V; vv += 32) {
         const int ii = vv / Q1, jj = vv - ii * Q1;
@@ -657,7 +666,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
         lv += __shfl_xor_sync(0xffffffffu, lv, o);
         en += __shfl_xor_sync(0xffffffffu, en, o);
       }
-      if (lane == 0) resn[(r & 3) * 2 + end] = real((double(a.qflow[(2 * end + 1) * nl + r]) - lv) / en);
+      if (lane == 0) resn[(r & (L::NEQ - 1)) * 2 + end] = real((double(a.qflow[(2 * end + 1) * nl + r]) - lv) / en);
       __syncwarp();
     }
   };
@@ -666,43 +675,55 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       if ((end == 0 ? inlet : outlet) && qw == end) res_job(r, end);
   };
 
-  // inlet / outlet ghosts of row r (main threads of the first / last column): the
-  // populations entering the domain see f_eq(n_res, (0, u^xi), T0) - R, the others
-  // the adjacent cell (zeroth order); written into the row's halo cells, which the
-  // bulk copy leaves out at the ends
-  auto reservoir_ghosts = [&](int r) {
-    if (!is_main) return;
-    for (int end = 0; end < 2; ++end) {
-      const bool act = end == 0 ? (inlet && c == 0) : (outlet && c == TP - 1);
-      if (!act) continue;
-      const int k = r % NRING;
-      real gm[12];
-      load_geo(gring + k * TP + c, gm);
-      const real Vx = end == 0 ? gm[G_BM] * px - gm[G_CM] * pl : gm[G_BP] * px - gm[G_CP] * pl;
-      const bool inflow = end == 0 ? (Vx > real(0)) : (Vx < real(0));
-      P val;
-      if (inflow) {
-        const real nres = a.flow ? resn[(r & 3) * 2 + end] : (end == 0 ? a.n_in : a.n_out);
-        const real e = nres * tb.gw0[i] * resr[((r & 3) * 2 + end) * Q1 + j];
-        val = p_make(e - Rij, e * T0 - Rij);
-      } else {
-        val = p_load(krow(k, c) + 2 * v);
-      }
-      for (int q = 1; q <= 3; ++q) p_store(krow(k, end == 0 ? -q : TP - 1 + q) + 2 * v, val);
+  // xi-halo value of velocity (ii, jj) of row r beyond strip end `end` (the inlet / outlet
+  // reservoirs): populations entering the domain see f_eq(n_res, (0, u^xi), T0) - R, the
+  // others the adjacent cell (zeroth order).  Every thread whose stencil reaches past an
+  // end evaluates it itself; the bulk copy leaves those cells out.
+  auto end_ghost = [&](int r, int end, int ii, int jj) -> P {
+    const int k = r % NRING, ce = end == 0 ? 0 : TP - 1;
+    real gm[12];
+    load_geo(gring + k * TP + ce, gm);
+    const real pli = tb.p0[ii], pxj = tb.p1[jj];
+    const real Vx = end == 0 ? gm[G_BM] * pxj - gm[G_CM] * pli : gm[G_BP] * pxj - gm[G_CP] * pli;
+    const bool inflow = end == 0 ? (Vx > real(0)) : (Vx < real(0));
+    if (inflow) {
+      const int e8 = (r & (L::NEQ - 1)) * 2 + end;
+      const real nres = a.flow ? resn[e8] : (end == 0 ? a.n_in : a.n_out);
+      const real e = nres * tb.gw0[ii] * resr[e8 * Q1 + jj];
+      const real R = tb.w0[ii] * tb.w1[jj];
+      return p_make(e - R, e * T0 - R);
+    }
+    return p_load(krow(k, ce) + 2 * (ii * Q1 + jj));
+  };
+  // the upwind-ordered five-cell stencil of xi interface cl - 1/2 of ring slot k (cells
+  // cl-3 .. cl+1 when up, cl+2 .. cl-2 otherwise), with the reservoir ghosts at the ends
+  auto xi_stencil = [&](int r, int k, int cl, bool up, int vv, P* h) {
+    const int ii = vv / Q1, jj = vv - ii * Q1;
+    const int c0 = up ? cl - 3 : cl + 2, sd = up ? 1 : -1;
+    if (!((inlet && cl < 3) || (outlet && cl > TP - 3))) {  // no end within reach (warp-uniform)
+#pragma unroll
+      for (int q = 0; q < 5; ++q) h[q] = p_load(krow(k, c0 + q * sd) + 2 * vv);
+      return;
+    }
+    const P gin = inlet ? end_ghost(r, 0, ii, jj) : p_set(real(0));
+    const P gout = outlet ? end_ghost(r, 1, ii, jj) : p_set(real(0));
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const int cc = c0 + q * sd;
+      h[q] = (inlet && cc < 0) ? gin : (outlet && cc >= TP) ? gout : p_load(krow(k, cc) + 2 * vv);
     }
   };
 
   // xi interface TP - 1/2 of row s (the right edge of the strip) for the 32 velocities of chunk ch
-  auto edge_weno = [&](int k, int ch) {
+  auto edge_weno = [&](int r, int k, int ch, P* xo) {
     const int vv = 32 * ch + lane, ii = vv / Q1, jj = vv - ii * Q1;
     const real pli = tb.p0[ii], pxj = tb.p1[jj];
     real gm[12];
     load_geo(gring + k * TP + TP - 1, gm);
     const bool up = gm[G_BP] * pxj - gm[G_CP] * pli >= real(0);
-    const real* st = krow(k, up ? TP - 3 : TP + 2) + 2 * vv;  // upwind-ordered stencil of TP - 1/2
-    const int sd = up ? ROW : -ROW;
-    xif[TP * V + vv] = weno5p<real>(p_load(st), p_load(st + sd), p_load(st + 2 * sd), p_load(st + 3 * sd),
-                                    p_load(st + 4 * sd), tb.iw0[ii] * tb.iw1[jj]);
+    P h[5];
+    xi_stencil(r, k, TP, up, vv, h);
+    xo[TP * V + vv] = weno5p<real>(h[0], h[1], h[2], h[3], h[4], tb.iw0[ii] * tb.iw1[jj]);
   };
 
   // window rows from the ring (the centreline mirror below row 0: ghost 1-k of
@@ -731,20 +752,18 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   }
   // row sA+2's partials are the first the equilibrium warps take from the ring
   if (is_main && sA + 2 < min(nl, sB) && lane == 0) mbar_arrive(pready + (sA + 2) % L::NPR);
-  reservoir_ghosts(sA);
   // lambda interface sA - 1/2
   P fm = p_set(real(0));
   if (is_main) fm = lpos ? weno5p<real>(W0, W1, W2, W3, W4, sc) : weno5p<real>(W5, W4, W3, W2, W1, sc);
   P gh0 = p_set(real(0)), gh1 = p_set(real(0));  // wall ghosts of rows nl, nl+1 (and nl+2)
-  unsigned phase_bits = 0;                        // thread 0: parity of the next wait, per step mbarrier
   __syncthreads();
 
   // ---- the equilibrium warps: rows sA+2 .. in order, each as soon as the column warps have
   // reduced its moments, two or three rows ahead of the step that uses it; they take part in
   // no step barrier (the step phases synchronise on named barrier 1 of the other NSYNC threads)
+  const int rend = min(nl, sB);
   if (is_eqw) {
     unsigned pph = 0;
-    const int rend = min(nl, sB);
     for (int r = sA + 2; r < rend; ++r) {
       const int k = r % L::NPR;
       bool ok = true;
@@ -759,40 +778,63 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       for (int job = qw; job < TP; job += 2) eq_job(r, job);
       res_jobs(r);
       __syncwarp();
-      if (lane == 0) mbar_arrive(eready + r % L::NEQ);
+      if (lane == 0) mbar_arrive(eready + (r & (L::NEQ - 1)));
     }
     return;
   }
-  unsigned eph = 0;        // thread 0: parity of the next wait, per equilibrium-ready slot
-  int eq_waited = sA + 1;  // rows up to this one have their records (the prologue made sA, sA+1)
+  unsigned eph = 0;          // thread 0: parity of the next wait, per equilibrium-ready slot
+  int eq_waited = sA + 1;    // rows up to this one have their records (the prologue made sA, sA+1)
+  unsigned phase_bits = 0;   // main threads: parity of the next wait, per step mbarrier
+  bool good = true;          // every wait of this thread so far ended in time
+  P flr = p_set(real(0));    // F_l of the row being finished, prefetched one step ahead
+  if (is_main && need_fl) flr = p_load(a.Fl + dcell(sA, p0 + c) * ROW + 2 * v);
+  P fp = p_set(real(0));     // lambda interface s + 1/2 of the row whose interfaces were built last
+  P frc = p_set(real(0));    // force of that row (double-precision path)
   auto sync_all = [&]() { named_bar(1, NSYNC); };
   auto sync_and = [&](bool v) { return named_bar_and(1, NSYNC, v); };
 
-  // ---- the march
-  for (int s = sA; s < sB; ++s) {
-    const int k0 = s % NRING, k3 = (k0 + 3) % NRING;
-    if (s - PD >= sA && s + 3 <= rlast) {  // the group issued PD steps ago brought row s+3
-      bool ok = true;
-      if (tid == 0) {
-        const int b = (s - PD) % NB;
-        ok = mbar_wait(bar + b, (phase_bits >> b) & 1u, a.max_polls);
-        phase_bits ^= 1u << b;
-      }
-      ok = sync_and(ok);
-      if (!ok) {  // wait (bounded) for every group still in flight, then leave
-        if (tid == 0) {
-          atomicOr(a.err, ERR_TIMEOUT);
-          for (int g = s - PD; g < s; ++g)
-            if (g + 3 + PD <= rlast) {
-              const int b = g % NB;
-              mbar_wait(bar + b, g == s - PD ? ((phase_bits >> b) & 1u) ^ 1u : (phase_bits >> b) & 1u, a.max_polls);
-            }
-        }
-        sync_all();
-        return;
-      }
+  // combine of cell (r, c) (main threads), once row r's interface values and force are
+  // written (the step barrier after row r's step): F(r) = W2, lambda interfaces r -/+ 1/2 in
+  // fm / fp, xi interfaces and force from the row-parity half of the buffers
+  auto combine = [&](int r) {
+    real gm[12];
+    load_geo(gring + (r % NRING) * TP + c, gm);
+    const P* xb = xif + (r & 1) * (TP + 1) * V;
+    const P FL = xb[c * V + v], FR = xb[(c + 1) * V + v];
+    const real Vm = gm[G_BM] * px - gm[G_CM] * pl, Vp = gm[G_BP] * px - gm[G_CP] * pl;
+    // chi flux differences (Sec. VII.B)
+    P adv = p_mul(p_set(pl * gm[G_IDL]), p_sub(p_mul(p_set(gm[G_AP]), fp), p_mul(p_set(gm[G_AM]), fm)));
+    adv = p_fma(p_set(gm[G_IDX]), p_sub(p_mul(p_set(Vp), FR), p_mul(p_set(Vm), FL)), adv);
+    if constexpr (F32) {
+      const real* lb = lbl + (r & 1) * TP * ROW;
+      const real* lx = lbx + (r & 1) * TP * ROW;
+      frc = p_add(p_load(lb + c * ROW + 2 * v), p_load(lx + c * ROW + 2 * v));
     }
-    if (tid == NMAIN && s + 3 + PD <= rlast) {  // row s+3+PD into the slot row s-1 left
+    const real* rec = eqr + ((r & (L::NEQ - 1)) * TP + c) * EQW;
+    const real geq = rec[i] * rec[Q0 + j];
+    const P deq = p_make(geq - Rij, geq * rec[Q0 + Q1] - Rij);
+    const real itau = rec[Q0 + Q1 + 1];
+    const P F = W2;  // F(r)
+    // L = -advection + force - (F - f_eq) / tau
+    const P Lv = p_sub(p_sub(frc, adv), p_mul(p_set(itau), p_sub(F, deq)));
+    P o = p_fma(p_set(a.ccdt), Lv, F);
+    if (need_fl) o = p_fma(p_set(a.ca), p_sub(flr, F), o);
+    p_store(a.Fout + dcell(r, p0 + c) * ROW + 2 * v, o);
+    if (need_fl && r + 1 < sB) flr = p_load(a.Fl + dcell(r + 1, p0 + c) * ROW + 2 * v);
+  };
+
+  // ---- the march: step s finishes row s-1 (the combine) while it builds row s's interface
+  // values and force; one barrier per step, after which row s's outputs are complete.  The
+  // last pass (s = sB) only finishes row sB-1.
+  for (int s = sA; s <= sB; ++s) {
+    const bool build = s < sB;
+    const int k0 = s % NRING, k3 = (s + 3) % NRING;
+    if (build && is_main && s - PD >= sA && s + 3 <= rlast) {  // the group issued PD steps ago brought row s+3
+      const int b = (s - PD) % NB;
+      good = mbar_wait(bar + b, (phase_bits >> b) & 1u, a.max_polls) && good;
+      phase_bits ^= 1u << b;
+    }
+    if (build && tid == NMAIN && s + 3 + PD <= rlast) {  // row s+3+PD into the slot row s-2 left
       uint64_t* b = bar + s % NB;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_expect_tx(b, row_bytes());
@@ -800,7 +842,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
     }
     // the wall (Sec. VII.C.4): at the first row whose window reaches it, n_w per
     // column from the zero-mass-flux balance and the ghosts of rows nl .. nl+2
-    if (top && s == nl - 3) {
+    if (build && top && s == nl - 3) {
       if (is_main) {
         // W3 .. W5 = F(nl-3 .. nl-1); outgoing populations: quadratic extrapolation (Eq. extrapol)
         const P G0 = p_add(p_sub(p_mul(p_set(real(3)), W5), p_mul(p_set(real(3)), W4)), W3);
@@ -829,15 +871,20 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
         gh0 = gh1 = p_make(e - Rij, e * T0 - Rij);
       }
     }
+    if (is_main && s > sA) {
+      combine(s - 1);
+      fm = fp;
+    }
+    if (!build) break;
 
-    // ==== phase A
-    P FL = p_set(real(0));   // xi interface c - 1/2 of row s
-    P fp = p_set(real(0));   // lambda interface s + 1/2
-    P frc = p_set(real(0));  // force (double precision path)
+    // ==== row s: interface values and force, into the row-parity half of the buffers
+    P* xo = xif + (s & 1) * (TP + 1) * V;
+    real* lo = lbl + (s & 1) * TP * ROW;
+    real* xo2 = lbx + (s & 1) * TP * ROW;
     if (is_main) {
       const int rn = s + 3;
       const P fnew = rn < nl ? p_load(krow(k3, c) + 2 * v) : (rn == nl ? gh0 : gh1);
-      if (rn < min(nl, sB)) {
+      if (rn < rend) {
         moment_partials(fnew, rn);
         __syncwarp();
         if (lane == 0) mbar_arrive(pready + rn % L::NPR);  // the equilibrium warps take row rn from here
@@ -847,14 +894,13 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       load_geo(gring + k0 * TP + c, gm);
       // xi interface c - 1/2: upwind by V^xi = b p^xi - c p^lambda (Eq. canalie_V)
       const bool up = gm[G_BM] * px - gm[G_CM] * pl >= real(0);
-      // the upwind-ordered stencil of interface c - 1/2: cells c-3 .. c+1 or c+2 .. c-2
-      const real* st = krow(k0, up ? c - 3 : c + 2) + 2 * v;
-      const int sd = up ? ROW : -ROW;
-      FL = weno5p<real>(p_load(st), p_load(st + sd), p_load(st + 2 * sd), p_load(st + 3 * sd), p_load(st + 4 * sd), sc);
+      P h[5];
+      xi_stencil(s, k0, c, up, v, h);
+      const P FL = weno5p<real>(h[0], h[1], h[2], h[3], h[4], sc);
       // lambda interface s + 1/2 from the window, upwind by p^lambda (a > 0): independent of
       // the xi one, so the two interleave
       fp = lpos ? weno5p<real>(W0, W1, W2, W3, W4, sc) : weno5p<real>(W5, W4, W3, W2, W1, sc);
-      xif[c * V + v] = FL;
+      xo[c * V + v] = FL;
       if constexpr (F32 && TC) {
         // force subtasks of the row's cells on the tensor cores (mma.sync needs the
         // warp converged after the data-dependent WENO branches)
@@ -862,7 +908,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
         for (int t = mw; t < TP * S::S; t += NMW) {
           const int cc = t / S::S, kt = t - cc * S::S;
           const ChanCell<real>& gk = gring[k0 * TP + cc];
-          force_subtask_tc<Q0, Q1>(tb, krow(k0, cc), gk.glxx, gk.glxl, kt, lane, lbl + cc * ROW, lbx + cc * ROW);
+          force_subtask_tc<Q0, Q1>(tb, krow(k0, cc), gk.glxx, gk.glxl, kt, lane, lo + cc * ROW, xo2 + cc * ROW);
         }
       } else if constexpr (!F32) {
         const real* F = krow(k0, c);
@@ -884,10 +930,8 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       }
     } else if constexpr (F32 && !TC) {
       // force tasks of the row's cells on the CUDA cores (lambda: one per (cell, column
-      // j); xi: one per (cell, row i)) and the strip's right-edge xi interface, over the
-      // extra warps in units of one warp
-      // tasks: (cell, column j) for lambda, (cell, row i) for xi, in units of 32 (one warp);
-      // then the edge chunks
+      // j); xi: one per (cell, row i)) in units of 32 (one warp), then the strip's
+      // right-edge xi interface, over the extra warps
       constexpr int NTL = TP * Q1, NTX = TP * Q0;
       constexpr int NWL = (NTL + 31) / 32, NWX = (NTX + 31) / 32;
       for (int u = ew; u < NWL + NWX + NWC; u += NWC) {
@@ -897,7 +941,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
             const int cc = t / Q1, jj = t - cc * Q1;
             const ChanCell<real>& gk = gring[k0 * TP + cc];
             const float pxj = tb.p1[jj];
-            force_lambda_cc<Q0, Q1>(kp, krow(k0, cc), jj, gk.glxx * pxj * pxj, gk.glxl * pxj, lbl + cc * ROW);
+            force_lambda_cc<Q0, Q1>(kp, krow(k0, cc), jj, gk.glxx * pxj * pxj, gk.glxl * pxj, lo + cc * ROW);
           }
         } else if (u < NWL + NWX) {
           const int t = 32 * (u - NWL) + lane;
@@ -905,62 +949,42 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
             const int cc = t / Q0, ii = t - cc * Q0;
             const ChanCell<real>& gk = gring[k0 * TP + cc];
             const float pli = tb.p0[ii];
-            force_xi_cc<Q0, Q1>(kp, krow(k0, cc), ii, -gk.glxx * pli, -gk.glxl * pli * pli, lbx + cc * ROW);
+            force_xi_cc<Q0, Q1>(kp, krow(k0, cc), ii, -gk.glxx * pli, -gk.glxl * pli * pli, xo2 + cc * ROW);
           }
         } else {
-          edge_weno(k0, u - NWL - NWX);
+          edge_weno(s, k0, u - NWL - NWX, xo);
         }
       }
     } else {
       // the strip's right-edge xi interface of row s, 32 velocities per extra warp
-      for (int ch = ew; ch < NWC; ch += NWC) edge_weno(k0, ch);
+      for (int ch = ew; ch < NWC; ch += NWC) edge_weno(s, k0, ch, xo);
     }
-    {  // the records of rows s (the combine) and s+1 (the reservoir ghosts) must be written
-      bool ok = true;
-      const int want = min(s + 1, min(nl, sB) - 1);
+    // the step barrier; before it, the records of rows s (the next combine) and s+1 (the
+    // reservoir ghosts of the next step) must be written
+    {
+      const int want = min(s + 1, rend - 1);
       if (tid == 0)
         while (eq_waited < want) {
-          const int r = ++eq_waited, k = r % L::NEQ;
-          ok = ok && mbar_wait(eready + k, (eph >> k) & 1u, a.max_polls);
+          const int r = ++eq_waited, k = r & (L::NEQ - 1);
+          good = mbar_wait(eready + k, (eph >> k) & 1u, a.max_polls) && good;
           eph ^= 1u << k;
         }
-      ok = sync_and(ok);
-      if (!ok) {  // an equilibrium warp stopped: wait (bounded) for the bulk copies in flight, then leave
+      if (!sync_and(good)) {
+        // a wait ran out: wait (bounded) for the bulk copies still in flight -- the groups
+        // issued at steps s-PD .. s (the one waited for this step may be the late one) --
+        // then leave together
         if (tid == 0) {
           atomicOr(a.err, ERR_TIMEOUT);
-          for (int g = s - PD + 1; g <= s; ++g)
-            if (g >= sA && g + 3 + PD <= rlast) mbar_wait(bar + g % NB, (phase_bits >> (g % NB)) & 1u, a.max_polls);
+          for (int g = s - PD; g <= s; ++g)
+            if (g >= sA && g + 3 + PD <= rlast) {
+              const int b = g % NB;
+              mbar_wait(bar + b, g == s - PD ? ((phase_bits >> b) & 1u) ^ 1u : (phase_bits >> b) & 1u, a.max_polls);
+            }
         }
         sync_all();
         return;
       }
     }
-
-    // ==== phase C
-    if (is_main) {
-      real gm[12];
-      load_geo(gring + k0 * TP + c, gm);
-      const P FR = xif[(c + 1) * V + v];
-      const real Vm = gm[G_BM] * px - gm[G_CM] * pl, Vp = gm[G_BP] * px - gm[G_CP] * pl;
-      // chi flux differences (Sec. VII.B)
-      P adv = p_mul(p_set(pl * gm[G_IDL]), p_sub(p_mul(p_set(gm[G_AP]), fp), p_mul(p_set(gm[G_AM]), fm)));
-      adv = p_fma(p_set(gm[G_IDX]), p_sub(p_mul(p_set(Vp), FR), p_mul(p_set(Vm), FL)), adv);
-      if constexpr (F32) frc = p_add(p_load(lbl + c * ROW + 2 * v), p_load(lbx + c * ROW + 2 * v));
-      const real* rec = eqr + ((s & 3) * TP + c) * EQW;
-      const real geq = rec[i] * rec[Q0 + j];
-      const P deq = p_make(geq - Rij, geq * rec[Q0 + Q1] - Rij);
-      const real itau = rec[Q0 + Q1 + 1];
-      const P F = W2;  // F(s)
-      // L = -advection + force - (F - f_eq) / tau
-      const P Lv = p_sub(p_sub(frc, adv), p_mul(p_set(itau), p_sub(F, deq)));
-      P o = p_fma(p_set(a.ccdt), Lv, F);
-      if (need_fl) o = p_fma(p_set(a.ca), p_sub(flr, F), o);
-      p_store(a.Fout + dcell(s, p0 + c) * ROW + 2 * v, o);
-      if (need_fl && s + 1 < sB) flr = p_load(a.Fl + dcell(s + 1, p0 + c) * ROW + 2 * v);
-      fm = fp;
-    }
-    if (s + 1 < sB) reservoir_ghosts(s + 1);
-    sync_all();
   }
 }
 
