@@ -60,7 +60,7 @@ WORKLOAD = (f"gradually expanding channel: {CH_NX} (xi) x {CH_NL} (lambda) cells
 # DRAM bytes (read + write) per launch of the channel stage kernel from one ncu capture, keyed by
 # the SHA-256 of the kernel's code at the time of the capture (a changed kernel reports null):
 # see profiles/ for the command and the scaling to the full grid
-CH_TRAFFIC = {"2136950b3e5fe6b7": 4.449e9, "430a6d91e4dc5596": 4.397e9}
+CH_TRAFFIC = {"2136950b3e5fe6b7": 4.449e9, "430a6d91e4dc5596": 4.397e9, "70feb0c42dc71e10": 4.385e9}
 
 
 def dist_env():
@@ -585,7 +585,7 @@ def run_gpu(args):
                    "grid": "xi in [-10, 40] equidistant, lambda tanh-stretched (A = 0.95), Re_c = 100, H/2 = 1",
                    "kn": CH_KN, "reservoirs": {"n_in": CH_NIN, "n_out": CH_NOUT, "T0": 1.0}, "dt": CH_DT,
                    "precision": "fp32-bulk (compensated density sums, fp64 wall flux)",
-                   "l2": l2_note(head["units"] * 4),
+                   "l2": l2_note(head["units"] * 8),  # two fields of four bytes per cell-velocity
                    "launch_shape": head["launch_shape"], "replicas_per_gpu": 1},
         "roofline": head["roofline"],
         "cpu_baseline": cpu,
