@@ -197,6 +197,26 @@ def channel_oracle_sample(seconds_target=12.0, nx_sample=8):
     return units / dt, steps, dt, cores
 
 
+def _oracle_worker(seconds):
+    v, steps, dt, _ = channel_oracle_sample(seconds_target=seconds)
+    return v, steps, dt
+
+
+def oracle_all_cores(seconds):
+    """The same oracle sample run as one single-threaded process per visible host core, at
+    once (processes started with spawn): the summed rate is the all-core CPU figure."""
+    import multiprocessing as mp
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    with mp.get_context("spawn").Pool(n) as pool:
+        res = pool.map(_oracle_worker, [seconds] * n)
+    return float(sum(r[0] for r in res)), n, int(sum(r[1] for r in res)), float(max(r[2] for r in res))
+
+
 def make_inputs(dtype):
     """Perturbed equilibrium f_eq(1, 0, 1) * (1 + 0.01 U(-1, 1)) in the library layout.
     f_eq(1, 0, 1) has weighted populations w_i w_j (f'') and w_i w_j (f'); the
@@ -411,7 +431,90 @@ def bench_channel(args, torch, stream, vlb, world):
         "e2e": {"value": e2e_value, "unit": "cell-velocity updates/s", "steps": e2e_steps,
                 "h2d_bytes_per_step": int(host_in.numel() * 4), "d2h_bytes_per_step": int(host_out.numel() * 4)},
         "density_finite": bool(np.all(np.isfinite(nmom))),
+        "variant": tuned,
     }
+
+
+def time_steps(ctx, torch, stream, steps, warmup, dt, flush=None):
+    """Per-step device times (CUDA events on the launching stream around each vlb_step), after
+    warmup untimed steps; L2 written over before each step when flush is given."""
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    out = []
+    with torch.cuda.stream(stream):
+        sink = torch.zeros((), dtype=torch.float32, device="cuda")
+        for _ in range(warmup):
+            ctx.step(dt, 1)
+        stream.synchronize()
+        for _ in range(steps):
+            if flush is not None:
+                evict_l2(flush, sink)
+            t0, t1 = ev(), ev()
+            t0.record(stream)
+            ctx.step(dt, 1)
+            t1.record(stream)
+            stream.synchronize()
+            out.append(t0.elapsed_time(t1))
+    return np.array(out)
+
+
+def bench_next(args, torch, stream, vlb, flush, head):
+    """The extensions beyond the vielbein BGK stage, each timed on its own workload: the
+    channel with the paper's flow-rate ends and the Cartesian-split channel (both on the
+    headline grid), the Couette scale-up batch in the f~ formulation, and the ballistic
+    Couette case with 8000 velocities (the multi-kernel large-set path)."""
+    hbm, kind = peaks()
+    out = {}
+    nl, nx = (int(x) for x in args.channel_cells.split("x"))
+    units = nl * nx * CH_VEL
+    for name, setup in (("channel_flow_rate", lambda c: (c.set_variant(head["variant"]), c.set_flow_rate(0.1))),
+                        ("cartesian_split_channel", lambda c: c.set_formulation(vlb.VLB_CARTESIAN))):
+        ctx = vlb.Channel(CH_MODEL, vlb.VLB_FP32_BULK, nl, nx, CH_KN, n_in=CH_NIN, n_out=CH_NOUT,
+                          stream=stream.cuda_stream)
+        ctx.set_f(channel_inputs(vlb, nl, nx))
+        setup(ctx)
+        ms = time_steps(ctx, torch, stream, 3, 1, CH_DT)
+        ctx.close()
+        launch = float(ms.mean()) / 3.0
+        achieved = stage_bytes(units, 4) / (launch * 1e-3) / 1e9
+        out[name] = {"value": units / (float(ms.mean()) * 1e-3), "unit": "cell-velocity updates/s",
+                     "ms_per_step": float(ms.mean()), "steps": len(ms),
+                     "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                                  "frac": achieved / hbm, "peak_source": f"{kind} hbm_gbs",
+                                  "algorithmic_bytes_per_stage": stage_bytes(units, 4),
+                                  "stage_ms": launch}}
+    out["channel_flow_rate"]["workload"] = (f"the headline channel with the flow-rate ends of Sec. VII.C.1-2 "
+                                            f"(Q0 = 0.1), the same stage kernel and launch shape")
+    out["cartesian_split_channel"]["workload"] = ("the headline channel in the Cartesian split of Sec. VII.G: "
+                                                  "per stage a cell pass (moments, equilibrium), a wall pass "
+                                                  "(n_w per column) and an update pass; the cell pass reads F "
+                                                  "once more than the algorithmic bytes count")
+    # the Couette scale-up batch in the f~ formulation (multi-kernel stage)
+    ctx = make_ctx(vlb.VLB_FP32_BULK, stream.cuda_stream)
+    ctx.set_f(make_inputs(np.float32))
+    ctx.set_formulation(vlb.VLB_FTILDE)
+    ms = time_steps(ctx, torch, stream, 10, 2, DT, flush)
+    ctx.close()
+    cu = N_CELLS * len(KNS) * 320
+    out["ftilde_couette"] = {"workload": COUETTE_WORKLOAD + ", FP32 bulk, f~ formulation (Sec. VI.B); L2 flushed "
+                                                          "before each timed step", "value": cu / (float(ms.mean()) * 1e-3),
+                             "unit": "cell-velocity updates/s", "ms_per_step": float(ms.mean()), "steps": len(ms),
+                             "l2": "L2-resident copies (13 MB): a rate, not an HBM figure"}
+    # the ballistic case: HH(4;200) x HH(4;10), 16 stretched cells, Kn = 1000
+    spec, n = "HH(4;200)xHH(4;10)", 16
+    grid = dict(n_cells=n, r_in=1.0, r_out=2.0, stretch_A=0.95, stretch_delta=0.75)
+    ctx = vlb.Couette(spec, vlb.VLB_FP32_BULK, [grid], [(0.1, 1.0)], [(0.0, 1.0)], [1000.0], [vlb.VLB_TAU_KN_OVER_NT],
+                      stream=stream.cuda_stream)
+    ctx.init_equilibrium(1.0, 0.0, 0.0, 1.0)
+    ms = time_steps(ctx, torch, stream, 50, 5, 2e-5)
+    ctx.close()
+    bu = n * 400 * 20
+    out["ballistic_couette"] = {"workload": f"circular Couette, {spec} (8000 velocities), {n} stretched cells "
+                                            "(A = 0.95, delta = 0.75), Kn = 1000, FP32 bulk, the multi-kernel "
+                                            "large-set stage (Sec. VI.D.2)",
+                                "value": bu / (float(ms.mean()) * 1e-3), "unit": "cell-velocity updates/s",
+                                "ms_per_step": float(ms.mean()), "steps": len(ms),
+                                "l2": "1 MB copies: launch- and latency-bound, a rate"}
+    return out
 
 
 def l2_note(copy_bytes):
@@ -562,6 +665,7 @@ def run_gpu(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     couette = bench_couette(args, torch, stream, vlb, flush) if args.workload in ("all", "couette") else None
     batched = bench_batched(args, torch, stream, vlb, flush) if args.workload in ("all", "batched") else None
+    nxt = bench_next(args, torch, stream, vlb, flush, head) if (args.workload == "all" and not args.no_next) else None
     del flush
     steady = time_to_steady(args, torch) if (not args.no_time_to_steady and rank == 0) else None
 
@@ -573,6 +677,11 @@ def run_gpu(args):
         cpu = {"value": v, "unit": "cell-velocity updates/s", "cores": threads_used(), "kind": "oracle",
                "sample": f"{steps} RK3 steps of a {CH_NL} x 8-cell sample of the channel (all lambda rows, 8 "
                          f"xi-columns) in {dt:.1f} s ({cores} host cores visible, numpy single-threaded)"}
+        if not args.no_all_cores:
+            va, na, sa, da = oracle_all_cores(args.cpu_seconds)
+            cpu["all_cores"] = {"value": va, "unit": "cell-velocity updates/s", "cores": na, "kind": "oracle",
+                                "sample": f"the same sample in {na} single-threaded processes at once, "
+                                          f"{sa} RK3 steps in all within {da:.1f} s"}
     line = {
         "metric": METRIC, "value": head["value"], "unit": "cell-velocity updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
@@ -594,6 +703,7 @@ def run_gpu(args):
         "clocks": head["clocks"],
         "couette_scaleup": couette,
         "batched": batched,
+        "extensions": nxt,
     }
     if steady is not None:
         line["time_to_steady"] = steady
@@ -618,6 +728,8 @@ def main():
     ap.add_argument("--couette-steps", type=int, default=100, help="timed steps of the Couette scale-up batch")
     ap.add_argument("--batch-steps", type=int, default=10, help="timed steps of the batched Couette measurement")
     ap.add_argument("--no-time-to-steady", action="store_true", help="leave out the time-to-steady measurement")
+    ap.add_argument("--no-next", action="store_true", help="leave out the extension measurements")
+    ap.add_argument("--no-all-cores", action="store_true", help="leave out the all-core oracle figure")
     ap.add_argument("--tts-instances", type=int, default=24, help="held-out instances of the time-to-steady batch")
     ap.add_argument("--tts-threshold", type=float, default=1e-6, help="residual threshold of the time to steady")
     ap.add_argument("--tts-steps", type=int, default=20000, help="step horizon of the time-to-steady runs")
