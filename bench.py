@@ -562,8 +562,8 @@ def bench_couette(args, torch, stream, vlb, flush):
         "launch_shape": {"cells_per_cta": shape32[0], "threads": shape32[1], "persistent": bool(shape32[2])},
         "shakhov": {"value": units / (float(shk_ms.mean()) * 1e-3), "unit": "cell-velocity updates/s",
                     "ms_per_step": float(shk_ms.mean()), "prandtl": 2.0 / 3.0,
-                    "note": "FP32 bulk; each stage is the BGK stage kernel, a moments pass over F_prev and the "
-                            "Shakhov correction kernel"},
+                    "note": "FP32 bulk; each stage is the BGK stage kernel and the Shakhov correction kernel "
+                            "(the moments of F_prev and the heat-flux term in one pass)"},
         "fp64": {"value": units / (float(s64.mean()) * 1e-3), "unit": "cell-velocity updates/s",
                  "ms_per_step": float(s64.mean()), "launch_shape": {"cells_per_cta": shape64[0], "threads": shape64[1]},
                  "roofline": {"bound": "alu", "achieved": fp64_achieved, "peak": fp64_tflops, "unit": "TFLOP/s",

@@ -434,22 +434,16 @@ vlb_status run_stage(vlb_ctx* c, int k) {
   if (c->collision == 1) {  // Shakhov: the heat-flux term of F_prev, added to the BGK stage's output
     const double ccw[3] = {1.0, 0.25, 2.0 / 3.0};
     const double knf = c->kind == 1 ? c->cdesc.kn : -1.0;
-    cudaError_t e;
-    if (c->prec == VLB_FP64) {
-      e = launch_moments<double>(static_cast<const double*>(c->F[prev]), c->total_cells, c->Vp, c->margs, c->d_mom,
-                                 c->stream, c->cmap);
-      if (e == cudaSuccess)
-        e = launch_shakhov<double>(static_cast<double*>(c->F[out]), c->total_cells, c->Vp, c->margs, c->d_mom,
-                                   c->d_inst, c->n_inst, ccw[k - 1], 1.0 - c->prandtl, knf, c->stream, c->cmap);
-    } else {
-      e = launch_moments<float>(static_cast<const float*>(c->F[prev]), c->total_cells, c->Vp, c->margs, c->d_mom,
-                                c->stream, c->cmap);
-      if (e == cudaSuccess)
-        e = launch_shakhov<float>(static_cast<float*>(c->F[out]), c->total_cells, c->Vp, c->margs, c->d_mom,
-                                  c->d_inst, c->n_inst, ccw[k - 1], 1.0 - c->prandtl, knf, c->stream, c->cmap);
-    }
+    const cudaError_t e =
+        c->prec == VLB_FP64
+            ? launch_shakhov<double>(static_cast<double*>(c->F[out]), static_cast<const double*>(c->F[prev]),
+                                     c->total_cells, c->Vp, c->margs, c->d_inst, c->n_inst, ccw[k - 1],
+                                     1.0 - c->prandtl, knf, c->stream)
+            : launch_shakhov<float>(static_cast<float*>(c->F[out]), static_cast<const float*>(c->F[prev]),
+                                    c->total_cells, c->Vp, c->margs, c->d_inst, c->n_inst, ccw[k - 1],
+                                    1.0 - c->prandtl, knf, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "Shakhov correction launch");
-    c->launches += 2;
+    c->launches += 1;
   }
   c->last = out;
   c->stage_done = k;

@@ -530,54 +530,201 @@ cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, co
 //   G'' = [q0 (t3_0 / 5 - 2T/5 t1_0) + q1 (t3_1 / 5 - 2T/5 t1_1)] / T^2,
 //   t3_0 = A3 B0 + A1 B2, t1_0 = A1 B0, t3_1 = A2 B1 + A0 B3, t1_1 = A0 B1,
 // A_k, B_k the projections of xi^k g on axes 0 and 1.  Against the BGK stage that the stage
-// kernel has written, a stage of weight cc adds cc dt (1 - Pr) G[F_prev] / tau to F_out;
-// mom holds the moments of F_prev (launch_moments, caller cell order).  One CTA per cell.
+// kernel has written, a stage of weight cc adds cc dt (1 - Pr) G[F_prev] / tau to F_out.
+// One CTA of 128 threads per cell: the cell's n, u, T and q from F_prev (per-thread sums in
+// the bulk type, cross-thread sums in FP64), the projections A_k, B_k in FP64 by eight
+// threads, then G in the bulk type for every (velocity, field).
+// The model arrays a CTA indexes per thread, staged in shared memory: read from the kernel
+// parameters with a different index in every lane they would be serialised.
 template <typename real>
-__global__ void shakhov_kernel(real* Fout, long long cells, int Vp, const __grid_constant__ ModelArgs m,
-                               const double* mom, const InstDesc* inst, int n_inst, double cc, double omp,
-                               double kn_fixed, CellMap map) {
-  __shared__ double A[4][MAXQ], B[4][MAXQ];
+struct ModelSmem {
+  real p[2][MAXQ], w[2][MAXQ], tab[2][MAXQ * MAXN];
+};
+template <typename real>
+__device__ inline void stage_model(const ModelArgs& m, ModelSmem<real>& ms) {
+  for (int k = threadIdx.x; k < MAXQ; k += blockDim.x) {
+    if constexpr (sizeof(real) == 4) {
+      ms.p[0][k] = m.p0f[k], ms.p[1][k] = m.p1f[k], ms.w[0][k] = m.w0f[k], ms.w[1][k] = m.w1f[k];
+    } else {
+      ms.p[0][k] = m.p0[k], ms.p[1][k] = m.p1[k], ms.w[0][k] = m.w0[k], ms.w[1][k] = m.w1[k];
+    }
+  }
+  for (int k = threadIdx.x; k < MAXQ * MAXN; k += blockDim.x) {
+    if constexpr (sizeof(real) == 4) ms.tab[0][k] = m.tab0f[k], ms.tab[1][k] = m.tab1f[k];
+    else ms.tab[0][k] = m.tab0[k], ms.tab[1][k] = m.tab1[k];
+  }
+  __syncthreads();
+}
+// warp sums of three per-thread values in the bulk type, left in red[k][warp] as FP64 for
+// thread 0 to add up (the per-cell scalars are FP64 work of one thread: FP64 runs at a small
+// fraction of the FP32 rate)
+template <typename real>
+__device__ __forceinline__ void warp_sums3(real a, real b, real g, double (*red)[4], int lane, int wid) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    g += __shfl_xor_sync(0xffffffffu, g, o);
+  }
+  if (lane == 0) red[0][wid] = double(a), red[1][wid] = double(b), red[2][wid] = double(g);
+  __syncthreads();
+}
+// The tables A_k = [xi^k g] on axis 0 and B_k on axis 1 (k <= 3, xi_power_populations) for
+// the cell's u and T, by the whole CTA: the moment vector of each (axis, semi-axis) once, the
+// input vector of each (axis, k, semi-axis), then the rows of the node tables in parallel; in
+// the bulk type (the term they build is a correction of the collision).
+template <typename R>
+__device__ inline void power_tables(const ModelArgs& m, const ModelSmem<R>& ms, R u0, R u1, R T, R (*M)[MAXN + 3],
+                                    R (*OV)[MAXN], R (*A)[MAXQ], R (*B)[MAXQ]) {
+  const int tid = threadIdx.x;
+  if (tid < 4) {  // (axis, side): side 0 the positive semi-axis (or the whole line), side 1 the negative
+    const int ax = tid >> 1, side = tid & 1;
+    const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0;
+    const R u = ax ? u1 : u0;
+    if (kind == 1 || side == 0) eq_moment_vector<R>(kind, N + 3, (kind == 1 && side) ? -u : u, T, M[tid]);
+  }
+  __syncthreads();
+  if (tid < 16) {  // (axis, k, side), as xi_power_vector
+    const int ax = tid >> 3, k = (tid >> 1) & 3, side = tid & 1;
+    const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0;
+    const R u = ax ? u1 : u0;
+    R* out = OV[tid];
+    if (kind == 0) {
+      if (side == 0) {
+        R mm[MAXN + 3];
+        for (int l = 0; l <= N + 3; ++l) mm[l] = M[2 * ax][l];
+        for (int it = 0; it < k; ++it) {
+          const int top = N + k - it - 1;
+          R prev = R(0);
+          for (int l = 0; l <= top; ++l) {
+            const R cur = mm[l];
+            mm[l] = R(l + 1) * mm[l + 1] + prev - u * cur;
+            prev = cur;
+          }
+        }
+        for (int l = 0; l <= N; ++l) out[l] = mm[l];
+      }
+    } else {
+      const R v = side ? -u : u;
+      R c[4] = {R(1), R(0), R(0), R(0)};
+      for (int it = 0; it < k; ++it)
+        for (int i = it + 1; i >= 0; --i) c[i] = (i ? c[i - 1] : R(0)) - v * c[i];
+      const R sgn = (side && (k & 1)) ? R(-1) : R(1);
+      for (int s2 = 0; s2 <= N; ++s2) {
+        R acc = R(0);
+        for (int i = 0; i <= k; ++i) acc += c[i] * M[2 * ax + side][s2 + i];
+        out[s2] = sgn * acc;
+      }
+    }
+  }
+  __syncthreads();
+  const int nq = m.nq0 + m.nq1;
+  for (int x = tid; x < 4 * nq; x += blockDim.x) {
+    const int k = x / nq, r = x - k * nq, ax = r >= m.nq0 ? 1 : 0, node = r - ax * m.nq0;
+    const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0;
+    const R* tab = ms.tab[ax];
+    const int side = (kind == 1 && ms.p[ax][node] < R(0)) ? 1 : 0;
+    const R* v = OV[ax * 8 + k * 2 + side];
+    R g = R(0);
+    for (int s2 = 0; s2 <= N; ++s2) g += tab[node * MAXN + s2] * v[s2];
+    (ax ? B : A)[k][node] = g;
+  }
+  __syncthreads();
+}
+
+template <typename real>
+__global__ void __launch_bounds__(128) shakhov_kernel(real* Fout, const real* Fprev, long long cells, int Vp,
+                                                      const __grid_constant__ ModelArgs m, const InstDesc* inst,
+                                                      int n_inst, double cc, double omp, double kn_fixed) {
+  __shared__ real A[4][MAXQ], B[4][MAXQ], M[4][MAXN + 3], OV[16][MAXN];
+  __shared__ double red[3][4];  // warp partials
+  __shared__ real sc[4], scr[4];  // n, u0, u1, T of the cell; coef, q0 / T^2, q1 / T^2, 1 / (5 T)
+  __shared__ int sinst;           // the cell's instance
+  __shared__ ModelSmem<real> ms;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int V = m.nq0 * m.nq1;
+  stage_model<real>(m, ms);
   for (long long c = blockIdx.x; c < cells; c += gridDim.x) {
-    const double* o = mom + 9 * caller_cell(map, c);
-    const double n = o[0], u0 = o[1], u1 = o[2], T = o[3], q0 = o[7], q1 = o[8];
-    if (threadIdx.x < 8) {
-      const int t = threadIdx.x;
-      if (t < 4) xi_power_populations(m.kind0, m.N0, m.nq0, m.p0, m.tab0, u0, T, t, A[t]);
-      else xi_power_populations(m.kind1, m.N1, m.nq1, m.p1, m.tab1, u1, T, t - 4, B[t - 4]);
+    const real* f = Fprev + c * 2 * Vp;
+    if (wid == 0) {  // the instance of the cell (its Kn, tau convention and dt): the last with cell0 <= c
+      int last = 0;
+      for (int b0 = 0; b0 < n_inst; b0 += 32) {
+        const bool in = b0 + lane < n_inst && inst[b0 + lane].cell0 <= c;
+        const unsigned bal = __ballot_sync(0xffffffffu, in);
+        if (bal) last = b0 + 31 - __clz(bal);
+        if (bal != 0xffffffffu) break;
+      }
+      if (lane == 0) sinst = last;
     }
-    // the instance of the cell (its Kn, tau convention and dt): cells run over the instances in order
-    int lo = 0, hi = n_inst - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (inst[mid].cell0 <= c) lo = mid; else hi = mid - 1;
-    }
-    const InstDesc& d = inst[lo];
-    const double tau = kn_fixed > 0.0 ? kn_fixed / (n * T) : relaxation_time<double>(d.tau_mode, d.kn, n, T);
-    const double coef = cc * d.dt * omp / tau;
-    const double a0 = q0 / (T * T), a1 = q1 / (T * T);
-    __syncthreads();
-    const int V = m.nq0 * m.nq1;
-    for (int x = threadIdx.x; x < 2 * V; x += blockDim.x) {
-      const int v = x >> 1, f = x & 1;
+    // n and n u (Eq. macro_red), F = D + R
+    real a = real(0), b = real(0), g = real(0);
+    for (int v = tid; v < V; v += blockDim.x) {
       const int i = v / m.nq1, j = v - i * m.nq1;
-      const double t3a = A[3][i] * B[0][j] + A[1][i] * B[2][j], t1a = A[1][i] * B[0][j];
-      const double t3b = A[2][i] * B[1][j] + A[0][i] * B[3][j], t1b = A[0][i] * B[1][j];
-      const double G = f ? a0 * (0.2 * t3a - 0.4 * T * t1a) + a1 * (0.2 * t3b - 0.4 * T * t1b)
-                         : a0 * (t3a / (5.0 * T) - 0.8 * t1a) + a1 * (t3b / (5.0 * T) - 0.8 * t1b);
+      const real f1 = f[2 * v] + ms.w[0][i] * ms.w[1][j];
+      a += f1;
+      b += ms.p[0][i] * f1;
+      g += ms.p[1][j] * f1;
+    }
+    warp_sums3<real>(a, b, g, red, lane, wid);
+    if (tid == 0) {
+      const real n = real((red[0][0] + red[0][1]) + (red[0][2] + red[0][3]));
+      sc[0] = n;
+      sc[1] = real((red[1][0] + red[1][1]) + (red[1][2] + red[1][3])) / n;
+      sc[2] = real((red[2][0] + red[2][1]) + (red[2][2] + red[2][3])) / n;
+    }
+    __syncthreads();
+    // 3 n T = sum (xi0^2 + xi1^2) f' + f'',  q = sum [(xi0^2 + xi1^2) f' + f''] xi / 2
+    const real u0r = sc[1], u1r = sc[2];
+    a = b = g = real(0);
+    for (int v = tid; v < V; v += blockDim.x) {
+      const int i = v / m.nq1, j = v - i * m.nq1;
+      const real R = ms.w[0][i] * ms.w[1][j];
+      const real x0 = ms.p[0][i] - u0r, x1 = ms.p[1][j] - u1r;
+      const real e = (x0 * x0 + x1 * x1) * (f[2 * v] + R) + (f[2 * v + 1] + R);
+      a += e;
+      b += e * x0;
+      g += e * x1;
+    }
+    warp_sums3<real>(a, b, g, red, lane, wid);
+    if (tid == 0) {  // per-cell scalars in the bulk type from the FP64 sums
+      const real n = sc[0];
+      const real T = real((red[0][0] + red[0][1]) + (red[0][2] + red[0][3])) / (real(3) * n);
+      const real q0 = real(0.5 * ((red[1][0] + red[1][1]) + (red[1][2] + red[1][3])));
+      const real q1 = real(0.5 * ((red[2][0] + red[2][1]) + (red[2][2] + red[2][3])));
+      const InstDesc& d = inst[sinst];
+      const real tau = kn_fixed > 0.0 ? real(kn_fixed) / (n * T)
+                                      : relaxation_time<real>(d.tau_mode, real(d.kn), n, T);
+      const real iT2 = real(1) / (T * T);
+      sc[3] = T;
+      scr[0] = real(cc * d.dt * omp) / tau;
+      scr[1] = q0 * iT2;
+      scr[2] = q1 * iT2;
+      scr[3] = real(1) / (real(5) * T);
+    }
+    __syncthreads();
+    const real Tr = sc[3], coef = scr[0], a0 = scr[1], a1 = scr[2], i5T = scr[3];
+    power_tables<real>(m, ms, u0r, u1r, Tr, M, OV, A, B);
+    for (int x = tid; x < 2 * V; x += blockDim.x) {
+      const int v = x >> 1, fi = x & 1;
+      const int i = v / m.nq1, j = v - i * m.nq1;
+      const real t3a = A[3][i] * B[0][j] + A[1][i] * B[2][j], t1a = A[1][i] * B[0][j];
+      const real t3b = A[2][i] * B[1][j] + A[0][i] * B[3][j], t1b = A[0][i] * B[1][j];
+      const real G = fi ? a0 * (real(0.2) * t3a - real(0.4) * Tr * t1a) + a1 * (real(0.2) * t3b - real(0.4) * Tr * t1b)
+                        : a0 * (t3a * i5T - real(0.8) * t1a) + a1 * (t3b * i5T - real(0.8) * t1b);
       real* y = Fout + c * 2 * Vp + x;
-      *y = real(double(*y) + coef * G);
+      *y = *y + coef * G;
     }
     __syncthreads();
   }
 }
 
 template <typename real>
-cudaError_t launch_shakhov(real* Fout, long long cells, int Vp, const ModelArgs& m, const double* mom,
+cudaError_t launch_shakhov(real* Fout, const real* Fprev, long long cells, int Vp, const ModelArgs& m,
                            const InstDesc* inst, int n_inst, double cc, double one_minus_pr, double kn_fixed,
-                           cudaStream_t s, CellMap map) {
+                           cudaStream_t s) {
   const long long blocks = cells < 152 * 16 ? cells : 152 * 16;
-  shakhov_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(Fout, cells, Vp, m, mom, inst, n_inst, cc,
-                                                                    one_minus_pr, kn_fixed, map);
+  shakhov_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(Fout, Fprev, cells, Vp, m, inst, n_inst, cc,
+                                                                    one_minus_pr, kn_fixed);
   return cudaGetLastError();
 }
 
@@ -713,7 +860,7 @@ template cudaError_t launch_deviation<VLB_REAL>(const VLB_REAL*, VLB_REAL*, long
                                                 cudaStream_t, CellMap);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,
                                               cudaStream_t, CellMap);
-template cudaError_t launch_shakhov<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
-                                              const InstDesc*, int, double, double, double, cudaStream_t, CellMap);
+template cudaError_t launch_shakhov<VLB_REAL>(VLB_REAL*, const VLB_REAL*, long long, int, const ModelArgs&,
+                                              const InstDesc*, int, double, double, double, cudaStream_t);
 
 }  // namespace vlb

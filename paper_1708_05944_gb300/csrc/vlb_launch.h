@@ -107,12 +107,13 @@ cudaError_t launch_deviation(const real* src, real* dst, long long cells, int Vp
                              int to_deviation, cudaStream_t s, CellMap map = CellMap{});
 
 // Shakhov correction of a stage (see shakhov_kernel): F_out += cc dt (1 - Pr) G[F_prev] / tau per
-// cell, mom the moments of F_prev (launch_moments); kn_fixed > 0: tau = kn_fixed / (n T) for
-// every cell, else each cell's instance (Kn, tau convention); dt from the instance.
+// cell, the moments taken from F_prev by the same kernel (device cell order); kn_fixed > 0:
+// tau = kn_fixed / (n T) for every cell, else each cell's instance (Kn, tau convention); dt from
+// the instance.
 template <typename real>
-cudaError_t launch_shakhov(real* Fout, long long cells, int Vp, const ModelArgs& m, const double* mom,
+cudaError_t launch_shakhov(real* Fout, const real* Fprev, long long cells, int Vp, const ModelArgs& m,
                            const InstDesc* inst, int n_inst, double cc, double one_minus_pr, double kn_fixed,
-                           cudaStream_t s, CellMap map = CellMap{});
+                           cudaStream_t s);
 
 // Model tables of a Couette context beyond the fused kernels' 32 nodes per axis (device
 // pointers; tab rows have stride MAXN; K0 is d/dp on axis 0, Kt1 d/dp (p .) on axis 1).
