@@ -589,7 +589,7 @@ def time_to_steady(args, torch):
     from paper_1708_05944_gb300.inputs import HELDOUT_SEED, TRAIN_SEED, couette_instances
     kn_range = (-1.0, 1.0)
     t0 = time.perf_counter()
-    train = couette_instances(192, seed=TRAIN_SEED, n_min=64, n_max=64, log10_kn=kn_range)
+    train = couette_instances(args.tts_train, seed=TRAIN_SEED, n_min=64, n_max=64, log10_kn=kn_range)
     c = W.make_context(train)
     c.init_equilibrium()
     c.step_graph(0.0, 80_000)
@@ -639,7 +639,7 @@ def time_to_steady(args, torch):
     return {
         "workload": f"{len(held)} held-out Couette instances, {cells} cells in total (64..96 each), HH(4;8)xH(4;20), "
                     "log10 Kn ~ U[-1, 1], inner wall speed ~ U[0.01, 0.5], R_out/R_in ~ U[1.5, 4]; network trained on "
-                    "192 solver steady states on 64 cells",
+                    f"{len(train)} solver steady states on 64 cells",
         "criterion": f"max(L2_u, L2_n, L2_T) of Eq. (msites_steady) between checks {check} steps apart < {threshold:g}; "
                      f"horizon {horizon} steps",
         "runs": runs,
@@ -731,6 +731,7 @@ def main():
     ap.add_argument("--no-next", action="store_true", help="leave out the extension measurements")
     ap.add_argument("--no-all-cores", action="store_true", help="leave out the all-core oracle figure")
     ap.add_argument("--tts-instances", type=int, default=24, help="held-out instances of the time-to-steady batch")
+    ap.add_argument("--tts-train", type=int, default=192, help="solver steady states the warm start is trained on")
     ap.add_argument("--tts-threshold", type=float, default=1e-6, help="residual threshold of the time to steady")
     ap.add_argument("--tts-steps", type=int, default=20000, help="step horizon of the time-to-steady runs")
     args = ap.parse_args()
