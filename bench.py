@@ -60,7 +60,8 @@ WORKLOAD = (f"gradually expanding channel: {CH_NX} (xi) x {CH_NL} (lambda) cells
 # DRAM bytes (read + write) per launch of the channel stage kernel from one ncu capture, keyed by
 # the SHA-256 of the kernel's code at the time of the capture (a changed kernel reports null):
 # see profiles/ for the command and the scaling to the full grid
-CH_TRAFFIC = {"2136950b3e5fe6b7": 4.449e9, "430a6d91e4dc5596": 4.397e9, "70feb0c42dc71e10": 4.385e9}
+CH_TRAFFIC = {"2136950b3e5fe6b7": 4.449e9, "430a6d91e4dc5596": 4.397e9, "70feb0c42dc71e10": 4.385e9,
+              "26f60cccea2d0a70": 4.395e9}
 
 
 def dist_env():

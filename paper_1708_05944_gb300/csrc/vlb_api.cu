@@ -360,7 +360,7 @@ void channel_segments(const vlb_ctx* c, const ChanVariant& v, int* seglen, int* 
 }
 
 template <typename real>
-vlb_status do_chan_stage(vlb_ctx* c, int k, int prev, int out) {
+vlb_status do_chan_stage(vlb_ctx* c, int k, int prev, int out, bool clb = false) {
   ChanArgs<real> a{};
   a.Fprev = static_cast<const real*>(c->F[prev]);
   a.Fl = static_cast<const real*>(c->F[c->cur]);
@@ -369,7 +369,8 @@ vlb_status do_chan_stage(vlb_ctx* c, int k, int prev, int out) {
   a.ca = real(ca[k - 1]);
   a.ccdt = real(cc[k - 1] * c->inst[0].dt);
   a.tables = c->d_ctab;
-  if constexpr (sizeof(real) == 8) a.geo = c->d_cgeo; else a.geo = c->d_cgeof;
+  if constexpr (sizeof(real) == 8) a.geo = clb ? c->d_clbcgeo : c->d_cgeo;
+  else a.geo = clb ? c->d_clbcgeof : c->d_cgeof;
   a.nw = c->d_nw;
   a.err = c->d_err;
   a.nl = c->cdesc.nl;
@@ -384,7 +385,7 @@ vlb_status do_chan_stage(vlb_ctx* c, int k, int prev, int out) {
   const ChanVariant& v = c->cvariants[c->variant];
   channel_segments(c, v, &a.seglen, &a.nseg);
   const int grid = (a.nx / v.tp) * a.nseg;
-  cudaError_t e = launch_channel<real>(v, a, c->chan_kp.data(), c->nq0, c->nq1, grid, c->stream);
+  cudaError_t e = launch_channel<real>(v, a, c->chan_kp.data(), c->nq0, c->nq1, grid, c->stream, clb);
   if (e != cudaSuccess) return cuda_fail(c, e, "channel stage kernel launch");
   c->launches += 1;
   return VLB_OK;
@@ -419,7 +420,9 @@ vlb_status run_stage(vlb_ctx* c, int k) {
     prev = b2, out = b1;
   }
   vlb_status st;
-  if (c->kind == 1 && c->clb)
+  if (c->kind == 1 && c->clb && c->clb_march)
+    st = c->prec == VLB_FP64 ? do_chan_stage<double>(c, k, prev, out, true) : do_chan_stage<float>(c, k, prev, out, true);
+  else if (c->kind == 1 && c->clb)
     st = c->prec == VLB_FP64 ? do_clb_stage<double>(c, k, prev, out) : do_clb_stage<float>(c, k, prev, out);
   else if (c->kind == 1 && c->n_cvariants == 0)
     return fail(c, VLB_ERR_UNSUPPORTED, "no vielbein channel kernel for this velocity set (16x12 or 8x4 nodes): "
@@ -1154,7 +1157,7 @@ vlb_status vlb_set_channel_reservoirs(vlb_ctx* c, double n_in, double n_out, dou
   c->cdesc.flow = 0;
   vlb_status st = drop_channel_graphs(c);
   if (st != VLB_OK) return st;
-  if (c->clb) {
+  if (c->clb && !c->clb_march) {
     st = upload_clb_weq(c);
     if (st != VLB_OK) return st;
   }
@@ -1210,7 +1213,49 @@ static vlb_status set_channel_formulation(vlb_ctx* c, int formulation) {
   if (formulation == 2 && c->cdesc.flow) return fail(c, VLB_ERR_STATE, "the Cartesian split runs with reservoir ends");
   vlb_status st = drop_channel_graphs(c);
   if (st != VLB_OK) return st;
-  if (formulation == 2 && !c->d_clbgeo) {
+  const vlb_channel_grid& cg = c->chan_grid;
+  auto cphi = [&](double x) { return 0.5 * (tanh(2.0) - tanh(2.0 - 30.0 * x / cg.re_c)); };
+  auto cdphi = [&](double x) {
+    const double ch = cosh(2.0 - 30.0 * x / cg.re_c);
+    return 0.5 * (30.0 / cg.re_c) / (ch * ch);
+  };
+  auto cchi = [&](double x) {
+    return (1.0 + tanh(2.0) / 2.0) * x + cg.re_c / 60.0 * log(cosh(2.0 - 30.0 * x / cg.re_c) / cosh(2.0));
+  };
+  if (formulation == 2 && c->n_cvariants > 0 && !c->d_clbcgeo) {
+    // the marching kernel's records: V^lambda = a (p^x - lambda phi' p^y) at the row faces, a = 1 / (1 + phi)
+    // at the column centre; V^xi = (1 + phi) p^y at the column faces (Sec. VII.G)
+    const int nl = cg.n_lambda, nx = cg.n_xi;
+    const double A = cg.stretch_A, ea = atanh(A), L = cg.xi_out - cg.xi_in;
+    std::vector<double> lf(nl + 1);
+    for (int s2 = 0; s2 <= nl; ++s2) lf[s2] = s2 == nl ? 1.0 : tanh(double(s2) / nl * ea) / A;
+    std::vector<ChanCell<double>> gd(size_t(nl) * nx);
+    std::vector<ChanCell<float>> gf(size_t(nl) * nx);
+    for (int p = 0; p < nx; ++p) {
+      const double xc = cg.xi_in + L * (p + 0.5) / nx, xm = cg.xi_in + L * p / nx, xp = cg.xi_in + L * (p + 1) / nx;
+      const double a = 1.0 / (1.0 + cphi(xc)), dph = cdphi(xc);
+      for (int s2 = 0; s2 < nl; ++s2) {
+        ChanCell<double> g{};
+        g.am = g.ap = a;
+        g.glxl = a * lf[s2] * dph;
+        g.glxx = a * lf[s2 + 1] * dph;
+        g.bm = 1.0 + cphi(xm);
+        g.bp = 1.0 + cphi(xp);
+        g.cm = g.cp = 0.0;
+        g.idl = 1.0 / (lf[s2 + 1] - lf[s2]);
+        g.idx = 1.0 / (cchi(xp) - cchi(xm));
+        gd[size_t(s2) * nx + p] = g;
+        const double* src = &g.am;
+        float* dst = &gf[size_t(s2) * nx + p].am;
+        for (int q = 0; q < 12; ++q) dst[q] = float(src[q]);
+      }
+    }
+    VLB_CUDA(c, cudaMalloc(&c->d_clbcgeo, sizeof(ChanCell<double>) * gd.size()));
+    VLB_CUDA(c, cudaMalloc(&c->d_clbcgeof, sizeof(ChanCell<float>) * gf.size()));
+    VLB_CUDA(c, cudaMemcpy(c->d_clbcgeo, gd.data(), sizeof(ChanCell<double>) * gd.size(), cudaMemcpyHostToDevice));
+    VLB_CUDA(c, cudaMemcpy(c->d_clbcgeof, gf.data(), sizeof(ChanCell<float>) * gf.size(), cudaMemcpyHostToDevice));
+  }
+  if (formulation == 2 && c->n_cvariants == 0 && !c->d_clbgeo) {
     if (!c->d_lm) {
       st = setup_large(c);
       if (st != VLB_OK) return st;
@@ -1257,11 +1302,12 @@ static vlb_status set_channel_formulation(vlb_ctx* c, int formulation) {
     VLB_CUDA(c, cudaMalloc(&c->d_clbrec, cells * (c->nq0 + c->nq1 + 2) * c->esize));
     VLB_CUDA(c, cudaMalloc(&c->d_clbres, size_t(nl) * 2 * (c->nq0 + c->nq1) * c->esize));
   }
-  if (formulation == 2) {
+  if (formulation == 2 && c->n_cvariants == 0) {
     st = upload_clb_weq(c);
     if (st != VLB_OK) return st;
   }
   c->clb = formulation == 2;
+  c->clb_march = formulation == 2 && c->n_cvariants > 0;
   return VLB_OK;
 }
 
@@ -1965,6 +2011,8 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_lpart);
   cudaFree(c->d_tgeo);
   cudaFree(c->d_clbgeo);
+  cudaFree(c->d_clbcgeo);
+  cudaFree(c->d_clbcgeof);
   cudaFree(c->d_clbrec);
   cudaFree(c->d_clbres);
   delete c;

@@ -165,7 +165,7 @@ struct ChanSmem {
   static constexpr size_t mvs_off = al(resn_off + size_t(NEQ) * 2 * sizeof(real));
   static constexpr size_t red_off = al(mvs_off + size_t(TP + 2) * 4 * MAXN * sizeof(real));
   static constexpr size_t wred_off = al(red_off + size_t(NPR) * TP * S::NWC * 4 * sizeof(real));
-  static constexpr size_t nwv_off = al(wred_off + size_t(TP) * S::NWC * sizeof(real));
+  static constexpr size_t nwv_off = al(wred_off + size_t(2) * TP * S::NWC * sizeof(real));  // two wall sums
   static constexpr size_t bytes = al(nwv_off + size_t(TP) * sizeof(double));
   static_assert(sizeof(Tab) % 16 == 0, "tables are one bulk copy");
   static_assert(rowb % 16 == 0 && (TP * sizeof(ChanCell<real>)) % 16 == 0, "rows are bulk copies");
@@ -416,7 +416,14 @@ enum { G_AM = 0, G_AP, G_BM, G_BP, G_CM, G_CP, G_IDL, G_IDX, G_GLXL, G_GLXX };
 // (mma.sync TF32, three products per tile) on the column-group warps; false,
 // packed FP32x2 fmas with the split matrices of kp on the extra warps.  The
 // double-precision kernel contracts in FP64 on the column-group threads.
-template <typename real, int Q0, int Q1, int TP, bool TC>
+//
+// CLB runs the Cartesian-split formulation (Sec. VII.G, Eq. canalie_coord_beq_cons) on the
+// same march: momenta (p^x, p^y) on the model's axes, no force term, fluxes of F = D + R, and
+// the geometry record read as V^lambda = am p^x - glxl p^y at s - 1/2 and ap p^x - glxx p^y at
+// s + 1/2 (a = 1 / (1 + phi), glxl / glxx = a lambda phi' at the interfaces), V^xi = b p^y
+// (c = 0).  The lambda upwind side and the wall's incoming half-plane (Eq. canalie_coord_nw)
+// then depend on the column and the interface.
+template <typename real, int Q0, int Q1, int TP, bool TC, bool CLB = false>
 __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
     channel_stage_kernel(const __grid_constant__ ChanArgs<real> a, const __grid_constant__ ChanKP<Q0, Q1> kp) {
   using S = ChanShape<Q0, Q1>;
@@ -752,10 +759,21 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
   }
   // row sA+2's partials are the first the equilibrium warps take from the ring
   if (is_main && sA + 2 < min(nl, sB) && lane == 0) mbar_arrive(pready + (sA + 2) % L::NPR);
-  // lambda interface sA - 1/2
+  // lambda interface r - 1/2 from the window W0 .. W5 = F(r-3 .. r+2), upwind by V^lambda: the sign
+  // of p^lambda (vielbein), or of V^lambda = am p^x - glxl p^y of row r's record (Cartesian split)
+  auto lam_face = [&](const ChanCell<real>& g, bool lower) -> P {
+    if constexpr (CLB) {
+      const bool up = (lower ? g.am * pl - g.glxl * px : g.ap * pl - g.glxx * px) >= real(0);
+      return weno5p<real>(up ? W0 : W5, up ? W1 : W4, up ? W2 : W3, up ? W3 : W2, up ? W4 : W1, sc);
+    } else {
+      (void)g, (void)lower;
+      return lpos ? weno5p<real>(W0, W1, W2, W3, W4, sc) : weno5p<real>(W5, W4, W3, W2, W1, sc);
+    }
+  };
   P fm = p_set(real(0));
-  if (is_main) fm = lpos ? weno5p<real>(W0, W1, W2, W3, W4, sc) : weno5p<real>(W5, W4, W3, W2, W1, sc);
+  if (is_main) fm = lam_face(gring[(sA % NRING) * TP + c], true);
   P gh0 = p_set(real(0)), gh1 = p_set(real(0));  // wall ghosts of rows nl, nl+1 (and nl+2)
+  bool wout = false;                              // this velocity leaves through the wall
   __syncthreads();
 
   // ---- the equilibrium warps: rows sA+2 .. in order, each as soon as the column warps have
@@ -802,10 +820,20 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
     const P* xb = xif + (r & 1) * (TP + 1) * V;
     const P FL = xb[c * V + v], FR = xb[(c + 1) * V + v];
     const real Vm = gm[G_BM] * px - gm[G_CM] * pl, Vp = gm[G_BP] * px - gm[G_CP] * pl;
-    // chi flux differences (Sec. VII.B)
-    P adv = p_mul(p_set(pl * gm[G_IDL]), p_sub(p_mul(p_set(gm[G_AP]), fp), p_mul(p_set(gm[G_AM]), fm)));
-    adv = p_fma(p_set(gm[G_IDX]), p_sub(p_mul(p_set(Vp), FR), p_mul(p_set(Vm), FL)), adv);
-    if constexpr (F32) {
+    P adv;
+    if constexpr (CLB) {
+      // Eq. (canalie_coord_beq_cons): fluxes of F = D + R, V^lambda per interface (no force term
+      // balances the rest state's advection here)
+      const P R2 = p_set(Rij);
+      const real Vlm = gm[G_AM] * pl - gm[G_GLXL] * px, Vlp = gm[G_AP] * pl - gm[G_GLXX] * px;
+      adv = p_mul(p_set(gm[G_IDL]), p_sub(p_mul(p_set(Vlp), p_add(fp, R2)), p_mul(p_set(Vlm), p_add(fm, R2))));
+      adv = p_fma(p_set(gm[G_IDX]), p_sub(p_mul(p_set(Vp), p_add(FR, R2)), p_mul(p_set(Vm), p_add(FL, R2))), adv);
+    } else {
+      // chi flux differences (Sec. VII.B)
+      adv = p_mul(p_set(pl * gm[G_IDL]), p_sub(p_mul(p_set(gm[G_AP]), fp), p_mul(p_set(gm[G_AM]), fm)));
+      adv = p_fma(p_set(gm[G_IDX]), p_sub(p_mul(p_set(Vp), FR), p_mul(p_set(Vm), FL)), adv);
+    }
+    if constexpr (F32 && !CLB) {
       const real* lb = lbl + (r & 1) * TP * ROW;
       const real* lx = lbx + (r & 1) * TP * ROW;
       frc = p_add(p_load(lb + c * ROW + 2 * v), p_load(lx + c * ROW + 2 * v));
@@ -847,26 +875,44 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
         // W3 .. W5 = F(nl-3 .. nl-1); outgoing populations: quadratic extrapolation (Eq. extrapol)
         const P G0 = p_add(p_sub(p_mul(p_set(real(3)), W5), p_mul(p_set(real(3)), W4)), W3);
         const P G1 = p_add(p_sub(p_mul(p_set(real(6)), W5), p_mul(p_set(real(8)), W4)), p_mul(p_set(real(3)), W3));
-        real fl = real(0);
-        if (pl > real(0)) fl = weno5p<real>(W3, W4, W5, G0, G1, sc).x * pl;
+        real fl = real(0), fd = real(0);
+        if constexpr (CLB) {
+          // V^lambda at the wall interface (row nl-1's upper face); the outgoing flux is of F = D + R,
+          // the incoming one of f_eq(1, 0, T0), both over this column's half-planes (Eq. canalie_coord_nw)
+          const ChanCell<real>& gw = gring[((nl - 1) % NRING) * TP + c];
+          const real Vw = gw.ap * pl - gw.glxx * px;
+          if (Vw > real(0)) fl = (weno5p<real>(W3, W4, W5, G0, G1, sc).x + Rij) * Vw;
+          else fd = tb.gw0[i] * tb.gw1[j] * Vw;
+          wout = Vw > real(0);
+        } else {
+          if (pl > real(0)) fl = weno5p<real>(W3, W4, W5, G0, G1, sc).x * pl;
+          wout = pl > real(0);
+        }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) fl += __shfl_xor_sync(0xffffffffu, fl, o);
-        if (lane == 0) wred[c * NWC + wc] = fl;
+        for (int o = 16; o > 0; o >>= 1) {
+          fl += __shfl_xor_sync(0xffffffffu, fl, o);
+          if constexpr (CLB) fd += __shfl_xor_sync(0xffffffffu, fd, o);
+        }
+        if (lane == 0) wred[c * NWC + wc] = fl, wred[(TP + c) * NWC + wc] = fd;
         gh0 = G0;
         gh1 = G1;
       }
       sync_all();
       if (!is_main && lane == 0)
         for (int cc = ew; cc < TP; cc += NWC) {
-          double num = tb.ref_flux_pos;  // outgoing flux of R
-          for (int w = 0; w < NWC; ++w) num += double(wred[cc * NWC + w]);
-          const double nwc = -num / tb.wall_den;  // Eq. (nw)
+          double num = CLB ? 0.0 : tb.ref_flux_pos;  // vielbein: the outgoing flux of R, then of D
+          double den = CLB ? 0.0 : tb.wall_den;
+          for (int w = 0; w < NWC; ++w) {
+            num += double(wred[cc * NWC + w]);
+            if (CLB) den += double(wred[(TP + cc) * NWC + w]);
+          }
+          const double nwc = -num / den;  // Eq. (nw) / (canalie_coord_nw)
           nwv[cc] = nwc;
           a.nw[p0 + cc] = nwc;
           if (!isfinite(nwc)) atomicOr(a.err, ERR_NONFINITE);
         }
       sync_all();
-      if (is_main && !(pl > real(0))) {  // incoming: f_eq(n_w, 0, T0) - R (Eq. weno_populate)
+      if (is_main && !wout) {  // incoming: f_eq(n_w, 0, T0) - R (Eq. weno_populate)
         const real e = real(nwv[c]) * tb.gw0[i] * tb.gw1[j];
         gh0 = gh1 = p_make(e - Rij, e * T0 - Rij);
       }
@@ -899,9 +945,11 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
       const P FL = weno5p<real>(h[0], h[1], h[2], h[3], h[4], sc);
       // lambda interface s + 1/2 from the window, upwind by p^lambda (a > 0): independent of
       // the xi one, so the two interleave
-      fp = lpos ? weno5p<real>(W0, W1, W2, W3, W4, sc) : weno5p<real>(W5, W4, W3, W2, W1, sc);
+      fp = lam_face(gring[k0 * TP + c], false);
       xo[c * V + v] = FL;
-      if constexpr (F32 && TC) {
+      if constexpr (CLB) {
+        // no force term
+      } else if constexpr (F32 && TC) {
         // force subtasks of the row's cells on the tensor cores (mma.sync needs the
         // warp converged after the data-dependent WENO branches)
         __syncwarp();
@@ -928,7 +976,7 @@ __global__ void __launch_bounds__(ChanSmem<real, Q0, Q1, TP>::NT, 1)
         const P B = p_fma(p_set(pl * pl), s2, p_mul(p_set(-px), s1));
         frc = p_fma(p_set(gm[G_GLXX]), A, p_mul(p_set(-gm[G_GLXL]), B));
       }
-    } else if constexpr (F32 && !TC) {
+    } else if constexpr (F32 && !TC && !CLB) {
       // force tasks of the row's cells on the CUDA cores (lambda: one per (cell, column
       // j); xi: one per (cell, row i)) in units of 32 (one warp), then the strip's
       // right-edge xi interface, over the extra warps

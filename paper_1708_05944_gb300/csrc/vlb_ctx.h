@@ -94,6 +94,11 @@ struct vlb_ctx {
   bool clb = false;               // the Cartesian-split formulation (Sec. VII.G) is on
   ClbGeom clbg{};                 // its geometry (device arrays in d_clbgeo)
   void* d_clbgeo = nullptr;
+  // the Cartesian split on the marching channel kernel (shapes with a vielbein kernel): its
+  // geometry records, read as described at channel_stage_kernel
+  bool clb_march = false;
+  ChanCell<double>* d_clbcgeo = nullptr;
+  ChanCell<float>* d_clbcgeof = nullptr;
   void* d_clbrec = nullptr;       // per cell equilibrium record
   void* d_clbres = nullptr;       // per row and end: reservoir factors
   // CUDA graph of three RK3 steps (nine stage launches), replayed by vlb_step_graph

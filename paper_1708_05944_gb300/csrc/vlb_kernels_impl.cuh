@@ -175,10 +175,10 @@ cudaError_t stage_config(StageVariant v, const ModelArgs& m, int Vp, int* nbuf, 
 }
 
 // ---------------------------------------------------------------- channel dispatch
-template <typename real, int Q0, int Q1, int TP, bool TC>
+template <typename real, int Q0, int Q1, int TP, bool TC, bool CLB = false>
 static cudaError_t go_channel(const ChanArgs<real>& a, const void* kpb, int grid, cudaStream_t s) {
   using L = ChanSmem<real, Q0, Q1, TP>;
-  auto kern = channel_stage_kernel<real, Q0, Q1, TP, TC>;
+  auto kern = channel_stage_kernel<real, Q0, Q1, TP, TC, CLB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(L::bytes));
   if (e != cudaSuccess) return e;
   ChanKP<Q0, Q1> kp;
@@ -366,11 +366,12 @@ bool channel_tables(int nq0, int nq1, const AxisTables* ax, const ModelArgs& m, 
 
 template <typename real>
 cudaError_t launch_channel(ChanVariant v, const ChanArgs<real>& a, const void* kp, int nq0, int nq1, int grid,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool clb) {
 #define VLB_CH(q0, q1, TP_)                                                                  \
   if (nq0 == q0 && nq1 == q1 && v.tp == TP_)                                                 \
-    return (sizeof(real) == 4 && v.tc) ? go_channel<real, q0, q1, TP_, sizeof(real) == 4>(a, kp, grid, s) \
-                                       : go_channel<real, q0, q1, TP_, false>(a, kp, grid, s);
+    return clb ? go_channel<real, q0, q1, TP_, false, true>(a, kp, grid, s)                  \
+               : (sizeof(real) == 4 && v.tc) ? go_channel<real, q0, q1, TP_, sizeof(real) == 4>(a, kp, grid, s) \
+                                             : go_channel<real, q0, q1, TP_, false>(a, kp, grid, s);
   VLB_CH(16, 12, 4) VLB_CH(8, 4, 4) VLB_CH(8, 4, 8)
 #undef VLB_CH
   return cudaErrorInvalidValue;
@@ -849,7 +850,7 @@ template cudaError_t launch_init_equilibrium<VLB_REAL>(VLB_REAL*, long long, int
                                                        double, double, cudaStream_t);
 template size_t channel_smem_bytes<VLB_REAL>(ChanVariant, int, int);
 template cudaError_t launch_channel<VLB_REAL>(ChanVariant, const ChanArgs<VLB_REAL>&, const void*, int, int, int,
-                                              cudaStream_t);
+                                              cudaStream_t, bool);
 template bool channel_tables<VLB_REAL>(int, int, const AxisTables*, const ModelArgs&, double,
                                        std::vector<unsigned char>*);
 template cudaError_t launch_seed<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,

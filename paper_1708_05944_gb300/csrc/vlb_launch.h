@@ -69,9 +69,10 @@ bool channel_tables(int nq0, int nq1, const AxisTables* ax, const ModelArgs& m, 
 // axes; false if the shape has no channel kernel or a matrix lacks the reflection
 // symmetry the split relies on.
 bool channel_force_pairs(int nq0, int nq1, const AxisTables* ax, std::vector<unsigned char>* out);
+// clb: the Cartesian-split formulation on the same march (a.geo then holds its geometry records)
 template <typename real>
 cudaError_t launch_channel(ChanVariant v, const ChanArgs<real>& a, const void* kp, int nq0, int nq1, int grid,
-                           cudaStream_t s);
+                           cudaStream_t s, bool clb = false);
 
 // Order of a context's cells in device buffers against the caller's order.
 // Couette contexts keep the caller's order (nx = 0).  Channel contexts store cell

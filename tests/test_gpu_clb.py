@@ -112,3 +112,59 @@ def test_shakhov_on_the_cartesian_split():
     bgk = ClbChannelOracle(spec, ChannelGrid(nl, nx), 0.05, n_in=1.5, n_out=1.0).step(F0, 1e-3)
     assert rel_err(F, bgk) > 1e-9  # the heat-flux term is not negligible here
     c.close()
+
+
+@pytest.mark.parametrize("spec,nl,nx", [("HH(4;8)xH(4;12)", 11, 12), ("HH(3;4)xH(3;4)", 13, 16)])
+def test_marching_kernel_every_launch_shape(spec, nl, nx):
+    """Velocity sets with a vielbein kernel run the Cartesian split on the same march (the
+    geometry records read as V^lambda per face, no force, fluxes of F): every launch shape
+    against the oracle, FP64 over three stages with n_w per column, FP32 moments after one step."""
+    o = ClbChannelOracle(spec, ChannelGrid(nl, nx), 0.05, n_in=1.5, n_out=1.0)
+    F0 = o.initial_state()
+    F0 = F0 * perturbation(F0.shape, seed=35, amplitude=0.03)
+    dt = 1e-3
+    F1 = o.stage(1, dt, F0, F0)
+    nw1 = o.last_nw.copy()
+    F2 = o.stage(2, dt, F0, F1)
+    F3 = o.stage(3, dt, F0, F2)
+    on, oux, ouy, oT = o.moments(F3)
+    c = vlb.Channel(spec, vlb.VLB_FP64, nl, nx, 0.05, n_in=1.5, n_out=1.0)
+    c.set_formulation(vlb.VLB_CARTESIAN)
+    d = vlb.Channel(spec, vlb.VLB_FP32_BULK, nl, nx, 0.05, n_in=1.5, n_out=1.0)
+    d.set_formulation(vlb.VLB_CARTESIAN)
+    nvar = len(c.channel_variants())
+    assert nvar >= 2
+    for v in range(nvar):
+        c.set_variant(v)
+        c.set_f(to_lib(F0))
+        c.stage(dt, 1)
+        assert rel_err(to_oracle(c.read_f(), nl, nx), F1) < 1e-12, v
+        np.testing.assert_allclose(c.wall_density(), nw1, rtol=1e-12, atol=0)
+        c.stage(dt, 2)
+        c.stage(dt, 3)
+        assert rel_err(to_oracle(c.read_f(), nl, nx), F3) < 1e-12, v
+        d.set_variant(v)
+        d.set_f(to_lib(F0).astype(np.float32))
+        d.step(dt, 1)
+        n, ux, uy, T = (x.reshape(nx, nl).T for x in d.read_moments())
+        assert np.abs(n / on - 1).max() < 1e-5 and np.abs(T / oT - 1).max() < 1e-5, v
+        assert np.abs(ux - oux).max() < 1e-5 and np.abs(uy - ouy).max() < 1e-5, v
+    c.close()
+    d.close()
+
+
+def test_shakhov_on_the_marching_cartesian_split():
+    spec, nl, nx = "HH(4;8)xH(4;12)", 9, 12
+    o = ClbChannelOracle(spec, ChannelGrid(nl, nx), 0.05, n_in=1.5, n_out=1.0, prandtl=2.0 / 3.0)
+    F0 = o.initial_state()
+    F0 = F0 * perturbation(F0.shape, seed=36, amplitude=0.05)
+    c = vlb.Channel(spec, vlb.VLB_FP64, nl, nx, 0.05, n_in=1.5, n_out=1.0)
+    c.set_formulation(vlb.VLB_CARTESIAN)
+    c.set_collision(vlb.VLB_SHAKHOV, 2.0 / 3.0)
+    c.set_f(to_lib(F0))
+    F = F0
+    for k in (1, 2, 3):
+        F = o.stage(k, 1e-3, F0, F)
+        c.stage(1e-3, k)
+        assert rel_err(to_oracle(c.read_f(), nl, nx), F) < 1e-12
+    c.close()
