@@ -507,6 +507,17 @@ def bench_next(args, torch, stream, vlb, flush, head):
                       stream=stream.cuda_stream)
     ctx.init_equilibrium(1.0, 0.0, 0.0, 1.0)
     ms = time_steps(ctx, torch, stream, 50, 5, 2e-5)
+    # the same steps replayed from a CUDA graph (vlb_step_graph), 200 at a time
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        ctx.step_graph(2e-5, 200)
+        stream.synchronize()
+        t0, t1 = ev(), ev()
+        t0.record(stream)
+        ctx.step_graph(2e-5, 1000)
+        t1.record(stream)
+        stream.synchronize()
+    graph_ms = t0.elapsed_time(t1) / 1000
     ctx.close()
     bu = n * 400 * 20
     out["ballistic_couette"] = {"workload": f"circular Couette, {spec} (8000 velocities), {n} stretched cells "
@@ -514,6 +525,8 @@ def bench_next(args, torch, stream, vlb, flush, head):
                                             "large-set stage (Sec. VI.D.2)",
                                 "value": bu / (float(ms.mean()) * 1e-3), "unit": "cell-velocity updates/s",
                                 "ms_per_step": float(ms.mean()), "steps": len(ms),
+                                "graph": {"value": bu / (graph_ms * 1e-3), "unit": "cell-velocity updates/s",
+                                          "ms_per_step": graph_ms, "steps": 1000},
                                 "l2": "1 MB copies: launch- and latency-bound, a rate"}
     return out
 
