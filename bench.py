@@ -493,12 +493,14 @@ def bench_next(args, torch, stream, vlb, flush, head):
     ctx = make_ctx(vlb.VLB_FP32_BULK, stream.cuda_stream)
     ctx.set_f(make_inputs(np.float32))
     ctx.set_formulation(vlb.VLB_FTILDE)
+    tuned_ft, _ = ctx.autotune(DT, reps=10)
     ms = time_steps(ctx, torch, stream, 10, 2, DT, flush)
     ctx.close()
     cu = N_CELLS * len(KNS) * 320
     out["ftilde_couette"] = {"workload": COUETTE_WORKLOAD + ", FP32 bulk, f~ formulation (Sec. VI.B); L2 flushed "
                                                           "before each timed step", "value": cu / (float(ms.mean()) * 1e-3),
                              "unit": "cell-velocity updates/s", "ms_per_step": float(ms.mean()), "steps": len(ms),
+                             "launch_shape": {"variant": tuned_ft, "kernel": "the fused stage kernel's f~ instance"},
                              "l2": "L2-resident copies (13 MB): a rate, not an HBM figure"}
     # the ballistic case: HH(4;200) x HH(4;10), 16 stretched cells, Kn = 1000
     spec, n = "HH(4;200)xHH(4;10)", 16

@@ -144,6 +144,21 @@ void fill_force_tables(KArgs<real>& k, const std::vector<double>& K0, const std:
 
 cudaError_t stage_launch_config(vlb_ctx* c, int n_tiles, int* nbuf, int* grid) {
   const int v = c->variant;
+  if (c->ftilde && c->ft_fused) {  // the f~ kernel of launch shape 0 (plain or persistent)
+    if (c->cfg_ft_nbuf[v] == 0) {
+      int nb = 1, per_sm = 0;
+      const cudaError_t e = c->prec == VLB_FP64
+                                ? stage_config<double>(c->variants[v], c->margs, c->Vp, &nb, &per_sm, true)
+                                : stage_config<float>(c->variants[v], c->margs, c->Vp, &nb, &per_sm, true);
+      if (e != cudaSuccess) return e;
+      c->cfg_ft_nbuf[v] = nb;
+      c->cfg_ft_per_sm[v] = per_sm;
+    }
+    *nbuf = c->cfg_ft_nbuf[v];
+    const int cap = c->cfg_ft_per_sm[v] * c->sms;
+    *grid = c->variants[v].persist && cap > 0 && cap < n_tiles ? cap : n_tiles;
+    return cudaSuccess;
+  }
   if (c->cfg_nbuf[v] == 0) {  // first use of this launch shape
     cudaError_t e;
     if (c->sms == 0) {
@@ -239,11 +254,18 @@ vlb_status do_stage(vlb_ctx* c, int k, int prev, int out) {
   a.err = c->d_err;
   a.Vp = c->Vp;
   a.max_polls = 1ull << 26;
+  const bool ft = c->ftilde && c->ft_fused;
+  if (ft) {
+    a.geo = c->d_ftgeo;
+    a.geof = c->d_ftgeof;
+    a.sqrtg = static_cast<const real*>(c->d_ftsg);
+    a.forceR = static_cast<const real*>(c->d_ftfr);
+  }
   const KArgs<real>* kk;
   if constexpr (sizeof(real) == 4) kk = c->k32.get(); else kk = c->k64.get();
   int grid = 0;
   cudaError_t e = stage_launch_config(c, a.n_tiles, &a.nbuf, &grid);
-  if (e == cudaSuccess) e = launch_stage<real>(c->variants[c->variant], a, c->margs, *kk, grid, c->stream);
+  if (e == cudaSuccess) e = launch_stage<real>(c->variants[c->variant], a, c->margs, *kk, grid, c->stream, ft);
   if (e != cudaSuccess) return cuda_fail(c, e, "stage kernel launch");
   c->launches += 1;
   return VLB_OK;
@@ -429,7 +451,7 @@ vlb_status run_stage(vlb_ctx* c, int k) {
                                         "it runs the Cartesian split (vlb_set_formulation)");
   else if (c->kind == 1)
     st = c->prec == VLB_FP64 ? do_chan_stage<double>(c, k, prev, out) : do_chan_stage<float>(c, k, prev, out);
-  else if (c->large || c->ftilde)
+  else if (c->large || (c->ftilde && !c->ft_fused))
     st = c->prec == VLB_FP64 ? do_large_stage<double>(c, k, prev, out) : do_large_stage<float>(c, k, prev, out);
   else
     st = c->prec == VLB_FP64 ? do_stage<double>(c, k, prev, out) : do_stage<float>(c, k, prev, out);
@@ -1324,9 +1346,19 @@ vlb_status vlb_set_formulation(vlb_ctx* c, int formulation) {
     c->graph_variant[b] = -1;
   }
   if (formulation == 1) {
-    vlb_status st = ensure_multi_path(c);
-    if (st != VLB_OK) return st;
-    if (!c->d_tgeo) {  // per cell: sqrt(g), e_{s+1/2} / (d eta sqrt(g)), e_{s-1/2} / (...), 1 / R_s; per velocity forceR
+    // the fused stage kernel has an f~ instance of each velocity set's first launch shape
+    bool fused = !c->large;
+    if (fused) {
+      StageVariant first[16];
+      const int nf = c->prec == VLB_FP64 ? stage_variants<double>(c->nq0, c->nq1, first)
+                                         : stage_variants<float>(c->nq0, c->nq1, first);
+      fused = nf > 0 && c->n_variants >= 2 && c->variants[0].tc == first[0].tc && c->variants[0].nt == first[0].nt;
+    }
+    if (!fused) {
+      vlb_status st = ensure_multi_path(c);
+      if (st != VLB_OK) return st;
+    }
+    if (!c->d_tgeo || (fused && !c->d_ftgeo)) {  // per cell: sqrt(g), e_{s+1/2} / (d eta sqrt(g)), e_{s-1/2} / (...), 1 / R_s; per velocity forceR
       const size_t N = size_t(c->total_cells);
       std::vector<double> t(4 * N);
       for (int i = 0; i < c->n_inst; ++i) {
@@ -1364,14 +1396,56 @@ vlb_status vlb_set_formulation(vlb_ctx* c, int formulation) {
       for (int i = 0; i < nq0; ++i)
         for (int j = 0; j < nq1; ++j)
           t.push_back(a1.p[j] * a1.p[j] * k0w[i] * a1.w[j] - a0.p[i] * a0.w[i] * k1w[j]);
-      VLB_CUDA(c, cudaMalloc(&c->d_tgeo, t.size() * sizeof(double)));
-      VLB_CUDA(c, cudaMemcpy(c->d_tgeo, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
-      c->lm.sqrtg = c->d_tgeo, c->lm.advp = c->d_tgeo + N, c->lm.advm = c->d_tgeo + 2 * N, c->lm.inv_r = c->d_tgeo + 3 * N;
-      c->lm.forceR = c->d_tgeo + 4 * N;
+      if (!c->d_tgeo) {
+        VLB_CUDA(c, cudaMalloc(&c->d_tgeo, t.size() * sizeof(double)));
+        VLB_CUDA(c, cudaMemcpy(c->d_tgeo, t.data(), t.size() * sizeof(double), cudaMemcpyHostToDevice));
+        c->lm.sqrtg = c->d_tgeo, c->lm.advp = c->d_tgeo + N, c->lm.advm = c->d_tgeo + 2 * N, c->lm.inv_r = c->d_tgeo + 3 * N;
+        c->lm.forceR = c->d_tgeo + 4 * N;
+      }
+      if (fused && !c->d_ftgeo) {  // the fused kernel's records and arrays, in its bulk type
+        std::vector<GeoCell> gd(N);
+        std::vector<GeoCellF> gf(N);
+        for (size_t k = 0; k < N; ++k) {
+          gd[k] = GeoCell{t[N + k], t[2 * N + k], t[3 * N + k], 0.0};
+          gf[k] = GeoCellF{float(t[N + k]), float(t[2 * N + k]), float(t[3 * N + k]), 0.0f};
+        }
+        const size_t V = size_t(c->nq0) * c->nq1;
+        VLB_CUDA(c, cudaMalloc(&c->d_ftgeo, N * sizeof(GeoCell)));
+        VLB_CUDA(c, cudaMalloc(&c->d_ftgeof, N * sizeof(GeoCellF)));
+        VLB_CUDA(c, cudaMemcpy(c->d_ftgeo, gd.data(), N * sizeof(GeoCell), cudaMemcpyHostToDevice));
+        VLB_CUDA(c, cudaMemcpy(c->d_ftgeof, gf.data(), N * sizeof(GeoCellF), cudaMemcpyHostToDevice));
+        VLB_CUDA(c, cudaMalloc(&c->d_ftsg, N * c->esize));
+        VLB_CUDA(c, cudaMalloc(&c->d_ftfr, V * c->esize));
+        if (c->prec == VLB_FP64) {
+          VLB_CUDA(c, cudaMemcpy(c->d_ftsg, t.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+          VLB_CUDA(c, cudaMemcpy(c->d_ftfr, t.data() + 4 * N, V * sizeof(double), cudaMemcpyHostToDevice));
+        } else {
+          std::vector<float> sg(N), fr(V);
+          for (size_t k = 0; k < N; ++k) sg[k] = float(t[k]);
+          for (size_t k = 0; k < V; ++k) fr[k] = float(t[4 * N + k]);
+          VLB_CUDA(c, cudaMemcpy(c->d_ftsg, sg.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+          VLB_CUDA(c, cudaMemcpy(c->d_ftfr, fr.data(), V * sizeof(float), cudaMemcpyHostToDevice));
+        }
+      }
     }
+    c->lm.ftilde = 1;
+    c->ftilde = true;
+    c->ft_fused = fused;
+    if (fused && c->variant > 1) {
+      vlb_status st = vlb_set_variant(c, c->variants[c->variant].persist ? 1 : 0);
+      if (st != VLB_OK) return st;
+    } else if (fused) {
+      build_tiles(c);  // the tile list of the same launch shape, rebuilt for the f~ kernel's occupancy
+      VLB_CUDA(c, cudaMemcpy(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * c->tiles.size(), cudaMemcpyHostToDevice));
+    }
+    return VLB_OK;
   }
-  c->lm.ftilde = formulation;
-  c->ftilde = formulation == 1;
+  c->lm.ftilde = 0;
+  c->ftilde = false;
+  if (!c->large) {  // the chi kernel's tile list
+    build_tiles(c);
+    VLB_CUDA(c, cudaMemcpy(c->d_tiles, c->tiles.data(), sizeof(TileDesc) * c->tiles.size(), cudaMemcpyHostToDevice));
+  }
   return VLB_OK;
 }
 
@@ -1832,6 +1906,8 @@ vlb_status vlb_set_variant(vlb_ctx* c, int v) {
   if (!c) return fail(nullptr, VLB_ERR_INVALID, "null context");
   if (c->kind == 1 && c->n_cvariants == 0 && v == 0) return VLB_OK;  // a Cartesian-split-only channel
   if (v < 0 || v >= (c->kind == 1 ? c->n_cvariants : c->n_variants)) return fail(c, VLB_ERR_INVALID, "no such launch shape");
+  if (c->kind == 0 && c->ftilde && c->ft_fused && v > 1)
+    return fail(c, VLB_ERR_INVALID, "the f~ formulation runs launch shape 0 (variants 0 and 1)");
   VLB_CUDA(c, cudaStreamSynchronize(c->stream));
   c->variant = v;
   if (c->kind == 1 || c->large) return VLB_OK;
@@ -1854,7 +1930,7 @@ vlb_status vlb_autotune(vlb_ctx* c, double dt, int reps, int* chosen, double* be
   int best = 0;
   float best_t = 1e30f;
   const int keep_last = c->last;
-  const int nvar = c->kind == 1 ? std::max(1, c->n_cvariants) : c->n_variants;
+  const int nvar = c->kind == 1 ? std::max(1, c->n_cvariants) : (c->ftilde && c->ft_fused ? 2 : c->n_variants);
   for (int v = 0; v < nvar; ++v) {
     st = vlb_set_variant(c, v);
     if (st != VLB_OK) break;
@@ -2010,6 +2086,10 @@ void vlb_destroy(vlb_ctx* c) {
   cudaFree(c->d_lforce);
   cudaFree(c->d_lpart);
   cudaFree(c->d_tgeo);
+  cudaFree(c->d_ftgeo);
+  cudaFree(c->d_ftgeof);
+  cudaFree(c->d_ftsg);
+  cudaFree(c->d_ftfr);
   cudaFree(c->d_clbgeo);
   cudaFree(c->d_clbcgeo);
   cudaFree(c->d_clbcgeof);

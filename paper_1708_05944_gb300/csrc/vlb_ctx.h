@@ -69,8 +69,17 @@ struct vlb_ctx {
   void* d_lrec = nullptr;     // per cell equilibrium record
   void* d_lforce = nullptr;   // per cell force term
   double* d_lpart = nullptr;  // per cell and wall chunk sums
-  bool ftilde = false;        // the f~ formulation (on the multi-kernel path)
+  bool ftilde = false;        // the f~ formulation
   double* d_tgeo = nullptr;   // its per-cell geometry: sqrt(g), advp, advm, 1/R_s
+  // f~ on the fused stage kernel (velocity sets of the fused path): launch shapes 0 and 1 only,
+  // their own launch configurations, the geometry records (cp, cm = advp, advm; inv_rbar = 1/R_s),
+  // sqrt(g) per cell and the inertial term of R per velocity in the bulk type
+  bool ft_fused = false;
+  int cfg_ft_nbuf[2] = {}, cfg_ft_per_sm[2] = {};
+  GeoCell* d_ftgeo = nullptr;
+  GeoCellF* d_ftgeof = nullptr;
+  void* d_ftsg = nullptr;
+  void* d_ftfr = nullptr;
   double prandtl = 1.0;
   bool have_prev = false;
   size_t tile_cap = 0;

@@ -18,10 +18,10 @@ namespace vlb {
 // Tile buffers and resident CTAs per SM of a launch shape: one buffer for a launch
 // with one CTA per tile; a persistent launch takes two (staging its next tile while
 // it computes one) when that leaves as many CTAs resident as one buffer does.
-template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
+template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT, bool FT = false>
 static cudaError_t stage_buffers(int Vp, int persist, int* nbuf, int* per_sm) {
   using L = StageSmem<real, TC, NT>;
-  auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>;
+  auto kern = couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT, FT>;
   const size_t limit = 227 * 1024;
   const int top = persist && L::bytes(Vp, 2) <= limit ? 2 : 1;
   // the kernel's shared-memory limit is process-wide and shared by contexts of other row
@@ -42,10 +42,10 @@ static cudaError_t stage_buffers(int Vp, int persist, int* nbuf, int* per_sm) {
   return cudaSuccess;
 }
 
-template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT>
+template <typename real, int TC, int NT, int Q0, int Q1, bool EXACT, bool FT = false>
 static cudaError_t go_stage(const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int grid,
                             cudaStream_t s) {
-  couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT>
+  couette_stage_kernel<real, TC, Q0, Q1, NT, EXACT, FT>
       <<<grid, NT, StageSmem<real, TC, NT>::bytes(a.Vp, a.nbuf), s>>>(a, m, k);
   return cudaGetLastError();
 }
@@ -117,8 +117,23 @@ size_t stage_smem_bytes(StageVariant v, int Vp) {
 
 template <typename real>
 cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int grid,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool ft) {
   const int sh = shape_of(m.nq0, m.nq1);
+  if (ft) {  // the f~ kernels: the first launch shape of each shape's table
+#define VLB_FT(SH, TC_, NT_, q0, q1, ex) \
+  if (sh == SH && v.tc == TC_ && v.nt == NT_) return go_stage<real, TC_, NT_, q0, q1, ex, true>(a, m, k, grid, s);
+    if constexpr (sizeof(real) == 4) {
+      VLB_FT(SH_16x20, 4, 256, 16, 20, true) VLB_FT(SH_16x12, 16, 256, 16, 12, true)
+      VLB_FT(SH_8x4, 16, 64, 8, 4, true) VLB_FT(SH_SMALL, 16, 64, MAXQ, MAXQ, false)
+      VLB_FT(SH_GENERIC, 16, 256, MAXQ, MAXQ, false)
+    } else {
+      VLB_FT(SH_16x20, 4, 256, 16, 20, true) VLB_FT(SH_16x12, 8, 256, 16, 12, true)
+      VLB_FT(SH_8x4, 8, 64, 8, 4, true) VLB_FT(SH_SMALL, 8, 64, MAXQ, MAXQ, false)
+      VLB_FT(SH_GENERIC, 8, 256, MAXQ, MAXQ, false)
+    }
+#undef VLB_FT
+    return cudaErrorInvalidValue;
+  }
 #define VLB_CASE(SH, TC_, NT_, q0, q1, ex) \
   if (sh == SH && v.tc == TC_ && v.nt == NT_) return go_stage<real, TC_, NT_, q0, q1, ex>(a, m, k, grid, s);
   if constexpr (sizeof(real) == 4) {
@@ -145,8 +160,23 @@ cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelAr
 }
 
 template <typename real>
-cudaError_t stage_config(StageVariant v, const ModelArgs& m, int Vp, int* nbuf, int* per_sm) {
+cudaError_t stage_config(StageVariant v, const ModelArgs& m, int Vp, int* nbuf, int* per_sm, bool ft) {
   const int sh = shape_of(m.nq0, m.nq1);
+  if (ft) {
+#define VLB_FT(SH, TC_, NT_, q0, q1, ex) \
+  if (sh == SH && v.tc == TC_ && v.nt == NT_) return stage_buffers<real, TC_, NT_, q0, q1, ex, true>(Vp, v.persist, nbuf, per_sm);
+    if constexpr (sizeof(real) == 4) {
+      VLB_FT(SH_16x20, 4, 256, 16, 20, true) VLB_FT(SH_16x12, 16, 256, 16, 12, true)
+      VLB_FT(SH_8x4, 16, 64, 8, 4, true) VLB_FT(SH_SMALL, 16, 64, MAXQ, MAXQ, false)
+      VLB_FT(SH_GENERIC, 16, 256, MAXQ, MAXQ, false)
+    } else {
+      VLB_FT(SH_16x20, 4, 256, 16, 20, true) VLB_FT(SH_16x12, 8, 256, 16, 12, true)
+      VLB_FT(SH_8x4, 8, 64, 8, 4, true) VLB_FT(SH_SMALL, 8, 64, MAXQ, MAXQ, false)
+      VLB_FT(SH_GENERIC, 8, 256, MAXQ, MAXQ, false)
+    }
+#undef VLB_FT
+    return cudaErrorInvalidValue;
+  }
 #define VLB_CASE(SH, TC_, NT_, q0, q1, ex) \
   if (sh == SH && v.tc == TC_ && v.nt == NT_)      \
     return stage_buffers<real, TC_, NT_, q0, q1, ex>(Vp, v.persist, nbuf, per_sm);
@@ -845,7 +875,7 @@ template int stage_variants<VLB_REAL>(int, int, StageVariant*);
 template size_t stage_smem_bytes<VLB_REAL>(StageVariant, int);
 template bool stage_split_tables<VLB_REAL>(int, int);
 template cudaError_t launch_stage<VLB_REAL>(StageVariant, const StageArgs<VLB_REAL>&, const ModelArgs&,
-                                            const KArgs<VLB_REAL>&, int, cudaStream_t);
+                                            const KArgs<VLB_REAL>&, int, cudaStream_t, bool);
 template cudaError_t launch_init_equilibrium<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, double, double,
                                                        double, double, cudaStream_t);
 template size_t channel_smem_bytes<VLB_REAL>(ChanVariant, int, int);
@@ -856,7 +886,7 @@ template bool channel_tables<VLB_REAL>(int, int, const AxisTables*, const ModelA
 template cudaError_t launch_seed<VLB_REAL>(VLB_REAL*, long long, int, const ModelArgs&, const double*,
                                            const double*, const double*, const double*, const double*, cudaStream_t,
                                            CellMap);
-template cudaError_t stage_config<VLB_REAL>(StageVariant, const ModelArgs&, int, int*, int*);
+template cudaError_t stage_config<VLB_REAL>(StageVariant, const ModelArgs&, int, int*, int*, bool);
 template cudaError_t launch_deviation<VLB_REAL>(const VLB_REAL*, VLB_REAL*, long long, int, const ModelArgs&, int,
                                                 cudaStream_t, CellMap);
 template cudaError_t launch_moments<VLB_REAL>(const VLB_REAL*, long long, int, const ModelArgs&, double*,

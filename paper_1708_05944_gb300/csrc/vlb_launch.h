@@ -35,14 +35,15 @@ bool stage_split_tables(int nq0, int nq1);
 // buffers (StageArgs::nbuf) and resident CTAs per SM (0 if none fit).  Also
 // raises the kernel's dynamic shared-memory limit to what the configuration
 // needs, which its launches rely on; a context computes it once per shape.
+// ft: the f~ instance (the first launch shape of the velocity set's shape only).
 template <typename real>
-cudaError_t stage_config(StageVariant v, const ModelArgs& m, int Vp, int* nbuf, int* per_sm);
+cudaError_t stage_config(StageVariant v, const ModelArgs& m, int Vp, int* nbuf, int* per_sm, bool ft = false);
 
 // Launch one RK3 stage over a.n_tiles tiles of at most v.tc cells on `grid` CTAs
 // (a.nbuf as stage_config gave it).
 template <typename real>
 cudaError_t launch_stage(StageVariant v, const StageArgs<real>& a, const ModelArgs& m, const KArgs<real>& k, int grid,
-                         cudaStream_t s);
+                         cudaStream_t s, bool ft = false);
 
 // Launch shapes of the channel stage kernel: ts lambda rows per segment of a
 // CTA's march (0: chosen by the host from the SM count; at least n_lambda: one

@@ -39,6 +39,10 @@ struct StageArgs {
   double* nw;          // 2 per instance: inner, outer wall density
   const WallEq* wall;  // 2 per instance: inner, outer wall equilibrium
   const real* halo;    // 2 x 3 rows per instance: ghost cells of slab halo ends (InstDesc::halo)
+  // the f~ formulation (the FT kernels): sqrt(g) per global cell and the inertial term of R per
+  // velocity; geo / geof then hold e_{s+-1/2} / (d eta sqrt(g)) as cp / cm and 1 / R_s as inv_rbar
+  const real* sqrtg;
+  const real* forceR;
   unsigned* err;
   int Vp;              // velocities per cell row, padded (>= nq0 nq1, multiple of 4); a row holds 2 Vp reals
   int nbuf;            // tile buffers: 1, or 2 when a persistent CTA stages its next tile during this one
@@ -79,7 +83,12 @@ constexpr int stage_min_ctas(int real_bytes, int tc, int nt) {
   return (real_bytes == 4 && nt >= 256 && nt <= 384) ? (tc <= 8 ? 3 : 2) : 1;
 }
 
-template <typename real, int TC, int Q0MAX, int Q1MAX, int NT, bool EXACT>
+// FT: the f~ formulation (Sec. VI.B, Eqs. boltz_couette_cons / boltz_couette_str_cons).  The
+// stencils act on F~ = sqrt(g) (D + R), held during phase D as F~ - R so that the walls' ghost
+// rows (stored the same way) need no sqrt(g); the walls extrapolate F~; the flux difference
+// takes e / (d eta sqrt(g)) and the force 1 / R_s, with the rest state's own advection and
+// inertial term added (F~ is not a deviation).  The moments, equilibrium and BGK act on D.
+template <typename real, int TC, int Q0MAX, int Q1MAX, int NT, bool EXACT, bool FT = false>
 __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
     couette_stage_kernel(const __grid_constant__ StageArgs<real> a, const __grid_constant__ ModelArgs m,
                          const __grid_constant__ KArgs<real> kk) {
@@ -527,9 +536,16 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
       const int i = v / nq1, j = v - i * nq1;
       if (!(sgn * p0d[i] < 0.0)) continue;
       // the same pair reconstruction as phase D (field 0 enters n_w)
-      const pair_t<real> F0 = p_load(tile + sA * row + 2 * v);
-      const pair_t<real> F1 = p_load(tile + (sA + dir) * row + 2 * v);
-      const pair_t<real> F2 = p_load(tile + (sA + 2 * dir) * row + 2 * v);
+      pair_t<real> F0 = p_load(tile + sA * row + 2 * v);
+      pair_t<real> F1 = p_load(tile + (sA + dir) * row + 2 * v);
+      pair_t<real> F2 = p_load(tile + (sA + 2 * dir) * row + 2 * v);
+      if constexpr (FT) {  // F~ of the three wall-adjacent cells
+        const long long e0 = in.cell0 + (wall == 0 ? 0 : n - 1);
+        const pair_t<real> R2 = p_set(w0r[i] * w1r[j]);
+        F0 = p_mul(p_add(F0, R2), p_set(a.sqrtg[e0]));
+        F1 = p_mul(p_add(F1, R2), p_set(a.sqrtg[e0 + dir]));
+        F2 = p_mul(p_add(F2, R2), p_set(a.sqrtg[e0 + 2 * dir]));
+      }
       const pair_t<real> G0 = p_fma(F1, p_set(real(-3)), p_fma(F0, p_set(real(3)), F2));
       const pair_t<real> G1 = p_fma(F1, p_set(real(-8)), p_fma(F0, p_set(real(6)), p_mul(F2, p_set(real(3)))));
       num += double(weno5p<real>(F2, F1, F0, G0, G1, iw0[i] * iw1[j]).x) * p0d[i];
@@ -538,7 +554,7 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
     if (lane == 0) red[warp] = num;
     __syncthreads();
     if (tid == 0) {
-      double sacc = wall == 0 ? m.ref_flux_neg : m.ref_flux_pos;  // the outgoing flux of R
+      double sacc = FT ? 0.0 : (wall == 0 ? m.ref_flux_neg : m.ref_flux_pos);  // chi: the outgoing flux of R
       for (int w = 0; w < NW; ++w) sacc += red[w];
       const double nwv = -sacc / mw[0];
       mw[1] = nwv;
@@ -551,11 +567,23 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
       const int i = v / nq1, j = v - i * nq1;
       pair_t<real> g1, g2, g3;  // ghosts at distance 1, 2, 3 from the wall
       if (sgn * p0d[i] < 0.0) {
-        const pair_t<real> F0 = p_load(tile + sA * row + 2 * v);
-        const pair_t<real> F1 = p_load(tile + (sA + dir) * row + 2 * v);
-        const pair_t<real> F2 = p_load(tile + (sA + 2 * dir) * row + 2 * v);
+        pair_t<real> F0 = p_load(tile + sA * row + 2 * v);
+        pair_t<real> F1 = p_load(tile + (sA + dir) * row + 2 * v);
+        pair_t<real> F2 = p_load(tile + (sA + 2 * dir) * row + 2 * v);
+        if constexpr (FT) {
+          const long long e0 = in.cell0 + (wall == 0 ? 0 : n - 1);
+          const pair_t<real> R2 = p_set(w0r[i] * w1r[j]);
+          F0 = p_mul(p_add(F0, R2), p_set(a.sqrtg[e0]));
+          F1 = p_mul(p_add(F1, R2), p_set(a.sqrtg[e0 + dir]));
+          F2 = p_mul(p_add(F2, R2), p_set(a.sqrtg[e0 + 2 * dir]));
+        }
         g1 = p_fma(F1, p_set(real(-3)), p_fma(F0, p_set(real(3)), F2));
         g2 = p_fma(F1, p_set(real(-8)), p_fma(F0, p_set(real(6)), p_mul(F2, p_set(real(3)))));
+        if constexpr (FT) {  // stored as F~ - R
+          const pair_t<real> nR = p_set(-(w0r[i] * w1r[j]));
+          g1 = p_add(g1, nR);
+          g2 = p_add(g2, nR);
+        }
         g3 = g2;  // never read by an outgoing stencil
       } else {  // f_eq(n_w, u_w, T_w) - R
         const double e = nwd * gw0[i] * gw1[j], r = m.w0[i] * m.w1[j];
@@ -570,6 +598,16 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
   // phase D reads the ghost rows the walls wrote; an interior tile wrote nothing since the
   // barrier after phase A (warp 0's staging goes to the other buffer)
   if (c0 < 3 || c0 + TCe + 3 > n) __syncthreads();  // uniform across the CTA
+  real* sgs = nullptr;  // f~: sqrt(g) of the tile's slots, 1 past the walls (ghost rows hold F~ - R)
+  if constexpr (FT) {
+    __shared__ real sgs_[TC + 6];
+    sgs = sgs_;
+    for (int q = tid; q < TC + 6; q += NT) {
+      const int cell = c0 - 3 + q;
+      sgs_[q] = (cell >= 0 && cell < n) ? a.sqrtg[in.cell0 + cell] : real(1);
+    }
+    __syncthreads();
+  }
 
   // ==== phase D: WENO-5 fluxes along the cells, flux difference, BGK, RK3 combine (in place)
   const real dtr = F32 ? real(in.dt_f) : real(in.dt);
@@ -585,8 +623,16 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
     const P npr = p_set(-pr);
     real* S = tile + 2 * v;
     const real* Fl = a.Fl + size_t(in.cell0 + c0) * row + 2 * v;  // F_l of the owned cells, read once
-    P w0 = p_load(S), w1 = p_load(S + row), w2 = p_load(S + 2 * row), w3 = p_load(S + 3 * row);
-    P w4 = p_load(S + 4 * row), w5 = p_load(S + 5 * row);
+    // the advected value of slot q: D (chi), F~ - R = (D + R) sqrt(g) - R (f~)
+    const real Rr = w0r[i] * w1r[j];
+    auto adv_val = [&](const real* x, int q) -> P {
+      if constexpr (FT) return p_fma(p_load(x), p_set(sgs[q]), p_set(Rr * (sgs[q] - real(1))));
+      else return p_load(x);
+    };
+    P FRv = p_set(real(0));  // f~: the inertial term of R for this velocity
+    if constexpr (FT) FRv = p_set(a.forceR[v]);
+    P w0 = adv_val(S, 0), w1 = adv_val(S + row, 1), w2 = adv_val(S + 2 * row, 2), w3 = adv_val(S + 3 * row, 3);
+    P w4 = adv_val(S + 4 * row, 4), w5 = adv_val(S + 5 * row, 5);
     // upwind stencil: (w0..w4) for p^R >= 0, mirrored (w5..w1) otherwise
     P fm = weno5p<real>(p_sel(up, w0, w5), p_sel(up, w1, w4), p_sel(up, w2, w3), p_sel(up, w3, w2),
                         p_sel(up, w4, w1), sc);
@@ -597,18 +643,24 @@ __global__ void __launch_bounds__(NT, stage_min_ctas(int(sizeof(real)), TC, NT))
       if (t < TCe) {
         const P fl = fl_next;
         if (need_fl && t + 1 < TCe) fl_next = p_load(Fl + (t + 1) * row);
-        const P w6 = p_load(S + (t + 6) * row);
+        const P w6 = adv_val(S + (t + 6) * row, t + 6);
         const P fp = weno5p<real>(p_sel(up, w1, w6), p_sel(up, w2, w5), p_sel(up, w3, w4), p_sel(up, w4, w3),
                                   p_sel(up, w5, w2), sc);
         // -adv = -p^R (cp F_{s+1/2} - cm F_{s-1/2}); per-cell factors: shared-memory broadcasts
-        const P nadv = p_mul(p_fma(fp, ccp[t], p_mul(fm, cNcm[t])), npr);
+        P nadv = p_mul(p_fma(fp, ccp[t], p_mul(fm, cNcm[t])), npr);
+        P Dc = w3;  // the cell's D
+        if constexpr (FT) {
+          nadv = p_fma(p_mul(npr, p_set(Rr)), p_add(ccp[t], cNcm[t]), nadv);  // the advection of R
+          Dc = p_load(S + (t + 3) * row);
+        }
         // f_eq - R for both fields: (g, T g) - R
         const P deq = p_fma(p_mul(gRn[t * MAXQ + i], gP[t * MAXQ + j]), cT1[t], nrij);
-        const P force = p_load(lbuf + t * row + 2 * v);
+        P force = p_load(lbuf + t * row + 2 * v);
+        if constexpr (FT) force = p_sub(force, FRv);
         // L = -adv + force / Rbar - (D - D_eq) / tau
-        const P Lv = p_fma(p_sub(w3, deq), cNtau[t], p_fma(force, cIR[t], nadv));
-        P o = p_fma(Lv, p_set(cc), w3);
-        if (need_fl) o = p_fma(p_sub(fl, w3), p_set(ca), o);
+        const P Lv = p_fma(p_sub(Dc, deq), cNtau[t], p_fma(force, cIR[t], nadv));
+        P o = p_fma(Lv, p_set(cc), Dc);
+        if (need_fl) o = p_fma(p_sub(fl, Dc), p_set(ca), o);
         p_store(S + (t + 3) * row, o);  // in place: this column's slot t+3 is not read again
         w0 = w1;
         w1 = w2;

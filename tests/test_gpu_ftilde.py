@@ -90,3 +90,34 @@ def test_switching_back_and_refusals():
     assert vlb._lib.vlb_set_formulation(ch.h, vlb.VLB_FTILDE) == vlb.VLB_ERR_UNSUPPORTED
     c.close()
     ch.close()
+
+
+def test_fused_kernel_launch_shapes_and_ragged_instances():
+    """Velocity sets of the fused stage kernel run f~ on its f~ instance (launch shape 0, plain
+    and persistent): two ragged instances (stretched and equidistant) in one context against
+    their oracles over three stages; other launch shapes are refused."""
+    spec = "HH(4;8)xH(4;20)"
+    (oa, Fa, ga), (ob, Fb, gb) = case(spec, 12, 0.95, seed=20), case(spec, 30, 0.0, seed=21)
+    c = vlb.Couette(spec, vlb.VLB_FP64, [ga, gb], [(0.15, 1.0)] * 2, [(-0.05, 1.05)] * 2, [0.2, 0.2],
+                    [TAU_AOKI] * 2)
+    c.set_formulation(vlb.VLB_FTILDE)
+    dt = 5e-4
+    refs = []
+    for o, F0 in ((oa, Fa), (ob, Fb)):
+        F1 = o.stage(1, dt, F0, F0)
+        F2 = o.stage(2, dt, F0, F1)
+        refs.append((F1, F2, o.stage(3, dt, F0, F2)))
+    for v in (0, 1):
+        c.set_variant(v)
+        c.set_f(np.concatenate([to_lib(Fa), to_lib(Fb)], axis=0))
+        for k in (1, 2, 3):
+            c.stage(dt, k)
+            got = c.read_f()
+            assert rel_err(to_oracle(got[:12]), refs[0][k - 1]) < 1e-12, (v, k)
+            assert rel_err(to_oracle(got[12:]), refs[1][k - 1]) < 1e-12, (v, k)
+    with pytest.raises(vlb.VlbError) as e:
+        c.set_variant(2)
+    assert e.value.status == vlb.VLB_ERR_INVALID
+    c.set_formulation(vlb.VLB_CHI)
+    c.set_variant(2)  # every launch shape again on the chi formulation
+    c.close()
