@@ -121,3 +121,22 @@ def test_fused_kernel_launch_shapes_and_ragged_instances():
     c.set_formulation(vlb.VLB_CHI)
     c.set_variant(2)  # every launch shape again on the chi formulation
     c.close()
+
+
+def test_shakhov_on_the_ftilde_formulation():
+    """The Shakhov pass composes with the f~ stage of the fused kernel: FP64, three stages,
+    against the oracle's f~ operator with Pr = 2/3."""
+    spec, n = "HH(4;8)xH(4;20)", 12
+    o = CouetteOracle(spec, CouetteGrid(n, 1.0, 2.0, A=0.95), Wall(0.15, 1.0), Wall(-0.05, 1.05), 0.2, TAU_AOKI,
+                      formulation="ftilde", prandtl=2.0 / 3.0)
+    F0 = o.initial_equilibrium()
+    F0 = F0 * perturbation(F0.shape, seed=22, amplitude=0.05)
+    c = ctx(spec, vlb.VLB_FP64, dict(n_cells=n, r_in=1.0, r_out=2.0, stretch_A=0.95))
+    c.set_collision(vlb.VLB_SHAKHOV, 2.0 / 3.0)
+    c.set_f(to_lib(F0))
+    F = F0
+    for k in (1, 2, 3):
+        F = o.stage(k, 5e-4, F0, F)
+        c.stage(5e-4, k)
+        assert rel_err(to_oracle(c.read_f()), F) < 1e-12
+    c.close()
