@@ -272,6 +272,25 @@ def time_device(ctx, torch, stream, steps, warmup, flush, dt=DT):
     return step_ms, step_ms / 3.0
 
 
+def cpu_model():
+    """The host CPU's model from /proc/cpuinfo: the model name (x86), else the Arm part (Grace is
+    Neoverse V2, part 0xd4f)."""
+    names = {"0xd4f": "Neoverse V2", "0xd40": "Neoverse V1", "0xd0c": "Neoverse N1", "0xd49": "Neoverse N2"}
+    try:
+        with open("/proc/cpuinfo", encoding="utf-8") as f:
+            info = f.read().splitlines()
+    except OSError:
+        return "unknown"
+    for ln in info:
+        if ln.lower().startswith("model name"):
+            return ln.split(":", 1)[1].strip()
+    for ln in info:
+        if ln.startswith("CPU part"):
+            part = ln.split(":", 1)[1].strip()
+            return f"Arm {names.get(part, 'part ' + part)}"
+    return "unknown"
+
+
 def threads_used():
     # numpy element-wise work and einsum without BLAS run on one thread
     return 1
@@ -697,7 +716,8 @@ def run_gpu(args):
         v, steps, dt, cores = channel_oracle_sample(seconds_target=args.cpu_seconds)
         cpu = {"value": v, "unit": "cell-velocity updates/s", "cores": threads_used(), "kind": "oracle",
                "sample": f"{steps} RK3 steps of a {CH_NL} x 8-cell sample of the channel (all lambda rows, 8 "
-                         f"xi-columns) in {dt:.1f} s ({cores} host cores visible, numpy single-threaded)"}
+                         f"xi-columns) in {dt:.1f} s ({cores} host cores visible, numpy single-threaded)",
+               "cpu_model": cpu_model()}
         if not args.no_all_cores:
             va, na, sa, da = oracle_all_cores(args.cpu_seconds)
             cpu["all_cores"] = {"value": va, "unit": "cell-velocity updates/s", "cores": na, "kind": "oracle",
