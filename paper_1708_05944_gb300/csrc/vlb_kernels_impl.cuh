@@ -562,9 +562,9 @@ cudaError_t launch_seed(real* F, long long cells, int Vp, const ModelArgs& m, co
 //   t3_0 = A3 B0 + A1 B2, t1_0 = A1 B0, t3_1 = A2 B1 + A0 B3, t1_1 = A0 B1,
 // A_k, B_k the projections of xi^k g on axes 0 and 1.  Against the BGK stage that the stage
 // kernel has written, a stage of weight cc adds cc dt (1 - Pr) G[F_prev] / tau to F_out.
-// One CTA of 128 threads per cell: the cell's n, u, T and q from F_prev (per-thread sums in
-// the bulk type, cross-thread sums in FP64), the projections A_k, B_k in FP64 by eight
-// threads, then G in the bulk type for every (velocity, field).
+// One warp per cell: the cell's n, u, T and q from F_prev (sums and per-cell scalars in the
+// bulk type: they enter a correction term), the projections A_k, B_k by the warp, then G for
+// every (velocity, field).
 // The model arrays a CTA indexes per thread, staged in shared memory: read from the kernel
 // parameters with a different index in every lane they would be serialised.
 template <typename real>
@@ -586,35 +586,21 @@ __device__ inline void stage_model(const ModelArgs& m, ModelSmem<real>& ms) {
   }
   __syncthreads();
 }
-// warp sums of three per-thread values in the bulk type, left in red[k][warp] as FP64 for
-// thread 0 to add up (the per-cell scalars are FP64 work of one thread: FP64 runs at a small
-// fraction of the FP32 rate)
-template <typename real>
-__device__ __forceinline__ void warp_sums3(real a, real b, real g, double (*red)[4], int lane, int wid) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    a += __shfl_xor_sync(0xffffffffu, a, o);
-    b += __shfl_xor_sync(0xffffffffu, b, o);
-    g += __shfl_xor_sync(0xffffffffu, g, o);
-  }
-  if (lane == 0) red[0][wid] = double(a), red[1][wid] = double(b), red[2][wid] = double(g);
-  __syncthreads();
-}
 // The tables A_k = [xi^k g] on axis 0 and B_k on axis 1 (k <= 3, xi_power_populations) for
-// the cell's u and T, by the whole CTA: the moment vector of each (axis, semi-axis) once, the
+// the cell's u and T, by one warp: the moment vector of each (axis, semi-axis) once, the
 // input vector of each (axis, k, semi-axis), then the rows of the node tables in parallel; in
 // the bulk type (the term they build is a correction of the collision).
 template <typename R>
 __device__ inline void power_tables(const ModelArgs& m, const ModelSmem<R>& ms, R u0, R u1, R T, R (*M)[MAXN + 3],
                                     R (*OV)[MAXN], R (*A)[MAXQ], R (*B)[MAXQ]) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x & 31;
   if (tid < 4) {  // (axis, side): side 0 the positive semi-axis (or the whole line), side 1 the negative
     const int ax = tid >> 1, side = tid & 1;
     const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0;
     const R u = ax ? u1 : u0;
     if (kind == 1 || side == 0) eq_moment_vector<R>(kind, N + 3, (kind == 1 && side) ? -u : u, T, M[tid]);
   }
-  __syncthreads();
+  __syncwarp();
   if (tid < 16) {  // (axis, k, side), as xi_power_vector
     const int ax = tid >> 3, k = (tid >> 1) & 3, side = tid & 1;
     const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0;
@@ -648,9 +634,9 @@ __device__ inline void power_tables(const ModelArgs& m, const ModelSmem<R>& ms, 
       }
     }
   }
-  __syncthreads();
+  __syncwarp();
   const int nq = m.nq0 + m.nq1;
-  for (int x = tid; x < 4 * nq; x += blockDim.x) {
+  for (int x = tid; x < 4 * nq; x += 32) {
     const int k = x / nq, r = x - k * nq, ax = r >= m.nq0 ? 1 : 0, node = r - ax * m.nq0;
     const int kind = ax ? m.kind1 : m.kind0, N = ax ? m.N1 : m.N0;
     const R* tab = ms.tab[ax];
@@ -660,92 +646,75 @@ __device__ inline void power_tables(const ModelArgs& m, const ModelSmem<R>& ms, 
     for (int s2 = 0; s2 <= N; ++s2) g += tab[node * MAXN + s2] * v[s2];
     (ax ? B : A)[k][node] = g;
   }
-  __syncthreads();
+  __syncwarp();
 }
 
+// One warp per cell (four per CTA): no CTA barrier on a cell's chain, four times the cells in
+// flight of a CTA per cell.
 template <typename real>
 __global__ void __launch_bounds__(128) shakhov_kernel(real* Fout, const real* Fprev, long long cells, int Vp,
                                                       const __grid_constant__ ModelArgs m, const InstDesc* inst,
                                                       int n_inst, double cc, double omp, double kn_fixed) {
-  __shared__ real A[4][MAXQ], B[4][MAXQ], M[4][MAXN + 3], OV[16][MAXN];
-  __shared__ double red[3][4];  // warp partials
-  __shared__ real sc[4], scr[4];  // n, u0, u1, T of the cell; coef, q0 / T^2, q1 / T^2, 1 / (5 T)
-  __shared__ int sinst;           // the cell's instance
+  __shared__ real A[4][4][MAXQ], B[4][4][MAXQ], M[4][4][MAXN + 3], OV[4][16][MAXN];  // per warp
   __shared__ ModelSmem<real> ms;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int V = m.nq0 * m.nq1;
   stage_model<real>(m, ms);
-  for (long long c = blockIdx.x; c < cells; c += gridDim.x) {
+  auto wsum = [&](real x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  };
+  for (long long c = (long long)blockIdx.x * 4 + w; c < cells; c += (long long)gridDim.x * 4) {
     const real* f = Fprev + c * 2 * Vp;
-    if (wid == 0) {  // the instance of the cell (its Kn, tau convention and dt): the last with cell0 <= c
-      int last = 0;
-      for (int b0 = 0; b0 < n_inst; b0 += 32) {
-        const bool in = b0 + lane < n_inst && inst[b0 + lane].cell0 <= c;
-        const unsigned bal = __ballot_sync(0xffffffffu, in);
-        if (bal) last = b0 + 31 - __clz(bal);
-        if (bal != 0xffffffffu) break;
-      }
-      if (lane == 0) sinst = last;
+    // the instance of the cell (its Kn, tau convention and dt): the last with cell0 <= c
+    int ii = 0;
+    for (int b0 = 0; b0 < n_inst; b0 += 32) {
+      const bool in = b0 + lane < n_inst && inst[b0 + lane].cell0 <= c;
+      const unsigned bal = __ballot_sync(0xffffffffu, in);
+      if (bal) ii = b0 + 31 - __clz(bal);
+      if (bal != 0xffffffffu) break;
     }
-    // n and n u (Eq. macro_red), F = D + R
+    // n and n u (Eq. macro_red), F = D + R; every lane gets the sums
     real a = real(0), b = real(0), g = real(0);
-    for (int v = tid; v < V; v += blockDim.x) {
+    for (int v = lane; v < V; v += 32) {
       const int i = v / m.nq1, j = v - i * m.nq1;
       const real f1 = f[2 * v] + ms.w[0][i] * ms.w[1][j];
       a += f1;
       b += ms.p[0][i] * f1;
       g += ms.p[1][j] * f1;
     }
-    warp_sums3<real>(a, b, g, red, lane, wid);
-    if (tid == 0) {
-      const real n = real((red[0][0] + red[0][1]) + (red[0][2] + red[0][3]));
-      sc[0] = n;
-      sc[1] = real((red[1][0] + red[1][1]) + (red[1][2] + red[1][3])) / n;
-      sc[2] = real((red[2][0] + red[2][1]) + (red[2][2] + red[2][3])) / n;
-    }
-    __syncthreads();
+    const real n = wsum(a), u0 = wsum(b) / n, u1 = wsum(g) / n;
     // 3 n T = sum (xi0^2 + xi1^2) f' + f'',  q = sum [(xi0^2 + xi1^2) f' + f''] xi / 2
-    const real u0r = sc[1], u1r = sc[2];
     a = b = g = real(0);
-    for (int v = tid; v < V; v += blockDim.x) {
+    for (int v = lane; v < V; v += 32) {
       const int i = v / m.nq1, j = v - i * m.nq1;
       const real R = ms.w[0][i] * ms.w[1][j];
-      const real x0 = ms.p[0][i] - u0r, x1 = ms.p[1][j] - u1r;
+      const real x0 = ms.p[0][i] - u0, x1 = ms.p[1][j] - u1;
       const real e = (x0 * x0 + x1 * x1) * (f[2 * v] + R) + (f[2 * v + 1] + R);
       a += e;
       b += e * x0;
       g += e * x1;
     }
-    warp_sums3<real>(a, b, g, red, lane, wid);
-    if (tid == 0) {  // per-cell scalars in the bulk type from the FP64 sums
-      const real n = sc[0];
-      const real T = real((red[0][0] + red[0][1]) + (red[0][2] + red[0][3])) / (real(3) * n);
-      const real q0 = real(0.5 * ((red[1][0] + red[1][1]) + (red[1][2] + red[1][3])));
-      const real q1 = real(0.5 * ((red[2][0] + red[2][1]) + (red[2][2] + red[2][3])));
-      const InstDesc& d = inst[sinst];
-      const real tau = kn_fixed > 0.0 ? real(kn_fixed) / (n * T)
-                                      : relaxation_time<real>(d.tau_mode, real(d.kn), n, T);
-      const real iT2 = real(1) / (T * T);
-      sc[3] = T;
-      scr[0] = real(cc * d.dt * omp) / tau;
-      scr[1] = q0 * iT2;
-      scr[2] = q1 * iT2;
-      scr[3] = real(1) / (real(5) * T);
-    }
-    __syncthreads();
-    const real Tr = sc[3], coef = scr[0], a0 = scr[1], a1 = scr[2], i5T = scr[3];
-    power_tables<real>(m, ms, u0r, u1r, Tr, M, OV, A, B);
-    for (int x = tid; x < 2 * V; x += blockDim.x) {
+    const real T = wsum(a) / (real(3) * n), q0 = real(0.5) * wsum(b), q1 = real(0.5) * wsum(g);
+    const InstDesc& d = inst[ii];
+    const real tau = kn_fixed > 0.0 ? real(kn_fixed) / (n * T) : relaxation_time<real>(d.tau_mode, real(d.kn), n, T);
+    const real coef = real(cc * d.dt * omp) / tau;
+    const real iT2 = real(1) / (T * T), a0 = q0 * iT2, a1 = q1 * iT2, i5T = real(1) / (real(5) * T);
+    power_tables<real>(m, ms, u0, u1, T, M[w], OV[w], A[w], B[w]);
+    const real(*Aw)[MAXQ] = A[w];
+    const real(*Bw)[MAXQ] = B[w];
+    for (int x = lane; x < 2 * V; x += 32) {
       const int v = x >> 1, fi = x & 1;
       const int i = v / m.nq1, j = v - i * m.nq1;
-      const real t3a = A[3][i] * B[0][j] + A[1][i] * B[2][j], t1a = A[1][i] * B[0][j];
-      const real t3b = A[2][i] * B[1][j] + A[0][i] * B[3][j], t1b = A[0][i] * B[1][j];
-      const real G = fi ? a0 * (real(0.2) * t3a - real(0.4) * Tr * t1a) + a1 * (real(0.2) * t3b - real(0.4) * Tr * t1b)
+      const real t3a = Aw[3][i] * Bw[0][j] + Aw[1][i] * Bw[2][j], t1a = Aw[1][i] * Bw[0][j];
+      const real t3b = Aw[2][i] * Bw[1][j] + Aw[0][i] * Bw[3][j], t1b = Aw[0][i] * Bw[1][j];
+      const real G = fi ? a0 * (real(0.2) * t3a - real(0.4) * T * t1a) + a1 * (real(0.2) * t3b - real(0.4) * T * t1b)
                         : a0 * (t3a * i5T - real(0.8) * t1a) + a1 * (t3b * i5T - real(0.8) * t1b);
       real* y = Fout + c * 2 * Vp + x;
       *y = *y + coef * G;
     }
-    __syncthreads();
+    __syncwarp();  // A, B, M, OV of this warp are rewritten for its next cell
   }
 }
 
@@ -753,7 +722,8 @@ template <typename real>
 cudaError_t launch_shakhov(real* Fout, const real* Fprev, long long cells, int Vp, const ModelArgs& m,
                            const InstDesc* inst, int n_inst, double cc, double one_minus_pr, double kn_fixed,
                            cudaStream_t s) {
-  const long long blocks = cells < 152 * 16 ? cells : 152 * 16;
+  long long blocks = (cells + 3) / 4;
+  if (blocks > 152 * 16) blocks = 152 * 16;
   shakhov_kernel<real><<<int(blocks > 0 ? blocks : 1), 128, 0, s>>>(Fout, Fprev, cells, Vp, m, inst, n_inst, cc,
                                                                     one_minus_pr, kn_fixed);
   return cudaGetLastError();
