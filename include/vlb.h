@@ -207,8 +207,11 @@ vlb_status vlb_set_collision(vlb_ctx* ctx, int collision, double prandtl);
  * equidistant grid), the walls act on F~ (Sec. III.E; n_w then carries sqrt(g)), and the
  * force term takes 1 / R at the cell centre.  It conserves sum d eta sqrt(g) sum f' exactly
  * but does not hold f = const at the walls (the paper's point).  The distribution stays f in
- * every call.  VLB_FTILDE runs on the multi-kernel stage (any velocity set); not with slabs
- * or vlb_step_static_scratch.
+ * every call.  VLB_FTILDE runs on the fused stage kernel's f~ instance for velocity sets of
+ * the fused path, with launch shapes 0 and 1 only (the first shape, plain and persistent;
+ * switching selects one of them, vlb_set_variant refuses the others with VLB_ERR_INVALID and
+ * vlb_autotune times those two), and on the multi-kernel stage for larger sets; not with
+ * slabs or vlb_step_static_scratch.
  * Channel contexts: VLB_CHI (the vielbein stage of vlb_create_channel) or VLB_CARTESIAN, the
  * Cartesian-split channel the paper compares it with (Sec. VII.G, Eqs. canalie_coord_beq_cons,
  * canalie_coord_nw): the model's axes are read as the Cartesian momenta (p^x, p^y) (the
@@ -216,7 +219,8 @@ vlb_status vlb_set_collision(vlb_ctx* ctx, int collision, double prandtl);
  * term, V^lambda = (p^x - lambda phi' p^y) / (1 + phi), V^xi = (1 + phi) p^y, the wall's
  * incoming half-plane V^lambda < 0 is taken per column, and the fluxes are of F itself (the
  * rest state is not an exact steady state of this scheme); reservoir ends only, no
- * post-processing (VLB_ERR_STATE).  Errors: VLB_ERR_INVALID, VLB_ERR_UNSUPPORTED (f~ on a
+ * post-processing (VLB_ERR_STATE).  Velocity sets with a vielbein kernel (16 x 12 and 8 x 4
+ * nodes) run it on the same marching kernel and its launch shapes; others on a three-pass stage.  Errors: VLB_ERR_INVALID, VLB_ERR_UNSUPPORTED (f~ on a
  * channel, Cartesian on a Couette context), VLB_ERR_STATE. */
 vlb_status vlb_set_formulation(vlb_ctx* ctx, int formulation);
 
@@ -358,7 +362,8 @@ vlb_status vlb_load(vlb_ctx* ctx, const char* path);
  * shape computes the same stage; they differ in occupancy and load balance. */
 int vlb_variants(const vlb_ctx* ctx, int* tc, int* nt, int* persistent, int max);
 
-/* Select a launch shape by index (0 = default). */
+/* Select a launch shape by index (0 = default).  VLB_ERR_INVALID for an index out of range,
+ * or above 1 while a Couette context runs the f~ formulation on the fused kernel. */
 vlb_status vlb_set_variant(vlb_ctx* ctx, int variant);
 
 /* Time every launch shape on this context's own workload (reps launches of
